@@ -1,0 +1,213 @@
+"""Seeded synthetic inputs shaped like the workloads of the explicit MPM path.
+
+This module only lays out geometry and draws random numbers: where particles
+sit, their initial velocity and volume, the mesh and boundary description and
+the material constants.  It holds none of the method's arithmetic, and both
+the CUDA library and the FP64 oracle take their inputs from it unchanged.
+
+Every generator is deterministic: randomness comes from numpy's PCG64 seeded
+with ``1909133800 + k`` for workload ``k``.
+
+Face numbering (-x, +x, -y, +y, -z, +z) and boundary codes follow the C-ABI:
+FREE 0, ROLLER 1, FIXED 2, FRICTION 3.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+FREE, ROLLER, FIXED, FRICTION = 0, 1, 2, 3
+USF, USL = 0, 1
+FP64_PLAIN, FP32_MIXED = 0, 1
+LINEAR_ELASTIC, MOHR_COULOMB = 0, 1
+SEED_BASE = 1909133800
+
+
+@dataclass
+class Workload:
+    name: str
+    dim: int
+    ncells: tuple
+    h: float
+    origin: tuple
+    face_bc: tuple
+    face_mu: tuple
+    gravity: tuple
+    dt: float
+    scheme: int
+    precision: int
+    material: dict            # model, E, nu, rho, phi (rad), c, psi (rad)
+    pos: np.ndarray           # (n, dim) float64
+    vel: np.ndarray           # (n, dim) float64
+    vol: np.ndarray           # (n,) float64
+    coh: np.ndarray | None = None   # (n,) float64 per-particle cohesion, or None
+    steps: int = 1
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        return int(self.pos.shape[0])
+
+    @property
+    def num_nodes(self) -> int:
+        k = 1
+        for d in range(self.dim):
+            k *= self.ncells[d] + 1
+        return k
+
+
+def gauss_fill(cells: np.ndarray, h: float, origin, dim: int) -> np.ndarray:
+    """Two particles per axis in every listed cell, at the cell centre
+    +- h / (2 sqrt 3) (the 2-point Gauss positions).  Cells are visited in the
+    given order and the 2^dim points of a cell x fastest."""
+    cells = np.asarray(cells, np.int64).reshape(-1, dim)
+    g = 0.5 / math.sqrt(3.0)
+    offs = np.array([[(g if (a >> k) & 1 else -g) for k in range(dim)] for a in range(1 << dim)])
+    centres = (cells.astype(np.float64) + 0.5) * h + np.asarray(origin[:dim], np.float64)
+    pos = centres[:, None, :] + offs[None, :, :] * h
+    return pos.reshape(-1, dim)
+
+
+def box_cells(lo, hi) -> np.ndarray:
+    """All integer cells lo <= c < hi (per axis), x fastest."""
+    axes = [np.arange(l, u) for l, u in zip(lo, hi)]
+    grids = np.meshgrid(*axes[::-1], indexing="ij")
+    return np.stack([g.ravel() for g in grids[::-1]], axis=1)
+
+
+def _mc(phi_deg=30.0, c=0.0, psi_deg=0.0, E=10e6, nu=0.3, rho=1800.0):
+    return dict(model=MOHR_COULOMB, E=E, nu=nu, rho=rho, phi=math.radians(phi_deg), c=c,
+                psi=math.radians(psi_deg))
+
+
+def elastic_bar(precision: int = FP64_PLAIN, scheme: int = USF, steps: int = 2000) -> Workload:
+    """2D plane-strain bar, 64 x 4 quads of 0.1 m filled with 2 x 2 Gauss
+    particles (1024), E = 100 MPa, nu = 0, rho = 1000, left edge fixed, no
+    gravity, initial axial velocity v0 sin(pi x / 2L), v0 = 0.1 m/s."""
+    nx, ny, h = 64, 4, 0.1
+    L = nx * h
+    pos = gauss_fill(box_cells((0, 0), (nx, ny)), h, (0.0, 0.0), 2)
+    vel = np.zeros_like(pos)
+    vel[:, 0] = 0.1 * np.sin(np.pi * pos[:, 0] / (2.0 * L))
+    vol = np.full(pos.shape[0], h * h / 4.0)
+    return Workload(
+        name="elastic_bar_2d_64x4", dim=2, ncells=(nx, ny, 1), h=h, origin=(0.0, 0.0, 0.0),
+        face_bc=(FIXED, FREE, FREE, FREE, FREE, FREE), face_mu=(0.0,) * 6, gravity=(0.0, 0.0, 0.0),
+        dt=1e-5, scheme=scheme, precision=precision,
+        material=dict(model=LINEAR_ELASTIC, E=100e6, nu=0.0, rho=1000.0, phi=0.0, c=0.0, psi=0.0),
+        pos=pos, vel=vel, vol=vol, steps=steps, meta=dict(L=L, v0=0.1))
+
+
+def column3d(ncells=(200, 40, 100), col_cells=(40, 40, 40), h=0.005, precision=FP32_MIXED,
+             scheme=USL, steps=5000, name=None) -> Workload:
+    """3D dry granular column collapse on 8-node hexahedra: a column of
+    col_cells at the (x=0, y=0, z=0) corner filled with 8 Gauss particles per
+    cell; Mohr-Coulomb phi 30 deg, c 0, psi 0, E 10 MPa, nu 0.3, rho 1800;
+    gravity 9.81 along -z; rollers at x = 0 and both y faces, Coulomb base
+    mu = 0.4, free top and +x.  The default sizes are the 200 x 40 x 100 mesh
+    of 5 mm cells with a 0.2 m cube column (512,000 particles)."""
+    pos = gauss_fill(box_cells((0, 0, 0), col_cells), h, (0.0, 0.0, 0.0), 3)
+    vel = np.zeros_like(pos)
+    vol = np.full(pos.shape[0], h ** 3 / 8.0)
+    nm = name or f"granular_column_3d_{ncells[0]}x{ncells[1]}x{ncells[2]}_col{col_cells[0]}x{col_cells[1]}x{col_cells[2]}"
+    return Workload(
+        name=nm, dim=3, ncells=tuple(ncells), h=h, origin=(0.0, 0.0, 0.0),
+        face_bc=(ROLLER, FREE, ROLLER, ROLLER, FRICTION, FREE), face_mu=(0, 0, 0, 0, 0.4, 0),
+        gravity=(0.0, 0.0, -9.81), dt=1e-5, scheme=scheme, precision=precision, material=_mc(),
+        pos=pos, vel=vel, vol=vol, steps=steps)
+
+
+def column2d(width_cells: int, height_cells: int, h=0.0025, precision=FP32_MIXED, scheme=USL,
+             mesh_cells=None, steps=5000, name=None) -> Workload:
+    """2D plane-strain granular column (4 Gauss particles per quad) against
+    the left wall; rollers at both x faces, Coulomb base mu = 0.4; the same
+    Mohr-Coulomb set as the 3D column."""
+    W, H = int(width_cells), int(height_cells)
+    if mesh_cells is None:
+        mesh_cells = (3 * W + 2, H + 4)
+    pos = gauss_fill(box_cells((0, 0), (W, H)), h, (0.0, 0.0), 2)
+    vel = np.zeros_like(pos)
+    vol = np.full(pos.shape[0], h * h / 4.0)
+    return Workload(
+        name=name or f"granular_column_2d_{W}x{H}", dim=2, ncells=(mesh_cells[0], mesh_cells[1], 1), h=h,
+        origin=(0.0, 0.0, 0.0), face_bc=(ROLLER, ROLLER, FRICTION, FREE, FREE, FREE),
+        face_mu=(0, 0, 0.4, 0, 0, 0), gravity=(0.0, -9.81, 0.0), dt=1e-5, scheme=scheme,
+        precision=precision, material=_mc(), pos=pos, vel=vel, vol=vol, steps=steps)
+
+
+def columns2d_batch(count=256, seed=SEED_BASE + 3, h=0.0025, steps=5000):
+    """A set of independent 2D granular columns: particle count log-uniform
+    in [5e3, 6e4], aspect ratio uniform in [0.5, 4]; width W = round(sqrt(n /
+    (4a))) cells, height H = round(a W); mesh (2 + 3a) W by H + 4 cells."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(count):
+        n = float(np.exp(rng.uniform(np.log(5e3), np.log(6e4))))
+        a = float(rng.uniform(0.5, 4.0))
+        W = max(1, int(round(math.sqrt(n / (4.0 * a)))))
+        H = max(1, int(round(a * W)))
+        mesh = (int(round((2.0 + 3.0 * a) * W)), H + 4)
+        out.append(column2d(W, H, h=h, mesh_cells=mesh, steps=steps, name=f"column2d_{i}_{W}x{H}"))
+    return out
+
+
+def slope3d(ncells=(800, 200, 200), h=0.05, crest=8.0, plateau=8.5, seed=SEED_BASE + 5,
+            precision=FP32_MIXED, steps=2000) -> Workload:
+    """3D slope on hexahedra: the x-z section is a plateau of height `crest`
+    from x = 0 to `plateau`, then a 45-degree face down to z = 0, extruded
+    over the whole y width.  A cell is filled when its centre lies inside the
+    section; 8 Gauss particles per filled cell.  Cohesion: one lognormal draw
+    (mean 10 kPa, CoV 0.3) per filled cell in cell order, shared by its
+    particles.  phi 30 deg, psi 0, E 50 MPa, nu 0.3, rho 2000; fixed base,
+    rollers on the four sides, free top."""
+    nx, ny, nz = ncells
+    ix = np.arange(nx)
+    iz = np.arange(nz)
+    xc = (ix + 0.5) * h
+    zc = (iz + 0.5) * h
+    top = np.where(xc <= plateau, crest, crest - (xc - plateau))          # surface height at xc
+    inside = zc[:, None] < top[None, :]                                     # (nz, nx)
+    zz, xx = np.nonzero(inside)                                             # z-major, x fastest
+    nxz = xx.shape[0]
+    cells = np.empty((nxz * ny, 3), np.int64)
+    # cell order x fastest, then y, then z (lexicographic cell id order)
+    order = []
+    for k in np.unique(zz):
+        xs = xx[zz == k]
+        for j in range(ny):
+            order.append(np.stack([xs, np.full_like(xs, j), np.full_like(xs, k)], axis=1))
+    cells = np.concatenate(order, axis=0)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sig_ln = math.sqrt(math.log(1.0 + 0.3 ** 2))
+    mu_ln = math.log(10e3) - 0.5 * sig_ln ** 2
+    coh_cell = rng.lognormal(mu_ln, sig_ln, size=cells.shape[0])
+    pos = gauss_fill(cells, h, (0.0, 0.0, 0.0), 3)
+    coh = np.repeat(coh_cell, 8)
+    vel = np.zeros_like(pos)
+    vol = np.full(pos.shape[0], h ** 3 / 8.0)
+    return Workload(
+        name=f"slope_3d_{nx}x{ny}x{nz}", dim=3, ncells=(nx, ny, nz), h=h, origin=(0.0, 0.0, 0.0),
+        face_bc=(ROLLER, ROLLER, ROLLER, ROLLER, FIXED, FREE), face_mu=(0.0,) * 6,
+        gravity=(0.0, 0.0, -9.81), dt=1e-5, scheme=USL, precision=precision,
+        material=_mc(E=50e6, rho=2000.0, c=10e3), pos=pos, vel=vel, vol=vol, coh=coh, steps=steps,
+        meta=dict(crest=crest, plateau=plateau, filled_cells=int(cells.shape[0])))
+
+
+def random_particles(mesh_cells, h, n, seed, dim=3, margin=1, vel_scale=0.1, sig_scale=1e3):
+    """Uniform random particle positions inside the mesh (away from the
+    boundary by `margin` cells), random velocity and random symmetric stress:
+    inputs for brute-force and parity checks of a single transfer."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    lo = np.array([margin * h] * dim)
+    hi = np.array([(mesh_cells[k] - margin) * h for k in range(dim)])
+    pos = lo + (hi - lo) * rng.random((n, dim))
+    vel = vel_scale * rng.standard_normal((n, dim))
+    sig = np.zeros((n, 6))
+    if dim == 3:
+        sig[:] = sig_scale * rng.standard_normal((n, 6))
+    else:
+        sig[:, :4] = sig_scale * rng.standard_normal((n, 4))
+    vol = (h ** dim / 4.0) * (0.5 + rng.random(n))
+    return pos, vel, sig, vol

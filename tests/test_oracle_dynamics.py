@@ -1,0 +1,155 @@
+"""Pins of the oracle's explicit step (CODE OVERVIEW: explicit USF and USL;
+INTRODUCTION: nodal values reset each step, particles carry the state;
+ISOPARAMETRIC MESH: velocity and frictional conditions at the nodes).
+
+  * a single particle in free fall follows v_n = n g dt and
+    x_n = x0 + g dt^2 n (n + 1) / 2 exactly (both schemes, crossing cells);
+  * with free faces and no gravity total momentum is conserved; with gravity
+    it grows by dt g M per step (sum of grad N = 0 cancels internal forces);
+  * the fixed-free elastic bar (64 x 4 quads) matches the closed-form first
+    mode: period, tip amplitude and centre-of-mass velocity, with bounded
+    energy drift (tests/golden/bar_first_mode.json);
+  * a stiff elastic block under inclined gravity on a Coulomb base slides
+    with a = g (sin theta - mu cos theta); with mu > tan theta it sticks.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1909_13380_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "bar_first_mode.json")
+
+
+@pytest.mark.parametrize("scheme", [oracle.USF, oracle.USL])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_single_particle_free_fall(scheme, dim):
+    g = (0.7, -9.81, 0.0) if dim == 2 else (0.7, 0.4, -9.81)
+    h, dt = 0.01, 1e-3
+    mesh = oracle.Mesh(dim=dim, n=(40, 40, 40)[:dim] + (1,) * (3 - dim), h=h, g=g, dt=dt, scheme=scheme)
+    x0 = np.array([0.2031, 0.3507, 0.3313][:dim])
+    st = oracle.State.create(x0[None, :], np.zeros((1, dim)), [1e-6], rho=1000.0)
+    # a soft material keeps dt = 1e-3 below the elastic wave limit h / c
+    o = oracle.Oracle(mesh, oracle.Material(E=10.0, nu=0.2), st)
+    cells0 = o.cells()[0].copy()
+    n = 100
+    assert o.step(n) == oracle.OK
+    gv = np.array(g[:dim])
+    assert np.allclose(st.v[0, :dim], n * gv * dt, rtol=1e-12, atol=1e-14)
+    expect = x0 + gv * dt * dt * n * (n + 1) / 2.0
+    assert np.allclose(st.x[0, :dim], expect, rtol=1e-12, atol=1e-14)
+    assert not np.array_equal(o.cells()[0], cells0)   # it did cross cells
+
+
+@pytest.mark.parametrize("scheme", [oracle.USF, oracle.USL])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_momentum_conservation(scheme, dim):
+    ncells = (10, 9, 8)[:dim] + (1,) * (3 - dim)
+    h = 0.1
+    pos, vel, sig, vol = W.random_particles(ncells, h, 400, seed=31 + dim, dim=dim, margin=2,
+                                            vel_scale=0.5, sig_scale=1e4)
+    mesh = oracle.Mesh(dim=dim, n=ncells, h=h, dt=1e-5, scheme=scheme)
+    st = oracle.State.create(pos, vel, vol, rho=1000.0, sig0=sig)
+    o = oracle.Oracle(mesh, oracle.Material(E=1e7, nu=0.25), st)
+    p0 = o.conservation()["momentum"]
+    scale = np.sum(st.m[:, None] * np.abs(st.v))
+    assert o.step(20) == oracle.OK
+    p1 = o.conservation()["momentum"]
+    assert np.all(np.abs(p1 - p0) <= 1e-12 * scale)
+    # with gravity the momentum grows by dt g M per step
+    g = np.array([0.3, -9.81, 1.1])
+    g[dim:] = 0.0
+    o.mesh.g = tuple(g)
+    M = st.m.sum()
+    assert o.step(10) == oracle.OK
+    p2 = o.conservation()["momentum"]
+    assert np.allclose(p2 - p1, 10 * 1e-5 * g * M, rtol=1e-9, atol=1e-12 * scale)
+
+
+@pytest.mark.slow
+def test_elastic_bar_first_mode():
+    ref = json.load(open(GOLDEN))
+    wl = W.elastic_bar()
+    mesh = oracle.Mesh(dim=2, n=wl.ncells, h=wl.h, face_bc=wl.face_bc, dt=wl.dt, scheme=wl.scheme)
+    st = oracle.State.create(wl.pos, wl.vel, wl.vol, wl.material["rho"])
+    o = oracle.Oracle(mesh, oracle.Material(**wl.material), st)
+    c0 = o.conservation()
+    assert c0["mass"] == pytest.approx(ref["mass_per_unit_thickness"], rel=1e-14)
+    assert c0["ke"] == pytest.approx(ref["kinetic_energy_0_per_unit_thickness"], rel=1e-12)
+    x0 = st.x.copy()
+    tip = st.x[:, 0] > wl.meta["L"] - wl.h / 2
+    nsteps = int(math.ceil(2.05 * ref["period"] / wl.dt))
+    vcm, energy, utip = [], [], []
+    for s in range(nsteps):
+        assert o.step(1) == oracle.OK
+        c = o.conservation()
+        vcm.append(c["momentum"][0] / c["mass"])
+        energy.append(c["ke"] + c["se"])
+        utip.append(np.mean(st.x[tip, 0] - x0[tip, 0]))
+    vcm, energy, utip = map(np.array, (vcm, energy, utip))
+    t = (np.arange(nsteps) + 1) * wl.dt
+    w = ref["omega"]
+    # centre-of-mass velocity (2 v0 / pi) cos(w t) at the workload's 2000 steps
+    assert abs(vcm[1999] - ref["vcm_amplitude"] * math.cos(w * t[1999])) <= 1e-3 * ref["vcm_amplitude"]
+    # period from the zero crossings of the centre-of-mass velocity
+    zc = np.nonzero(np.diff(np.sign(vcm)))[0]
+    tz = t[zc] - vcm[zc] * (t[zc + 1] - t[zc]) / (vcm[zc + 1] - vcm[zc])
+    assert len(tz) >= 4
+    assert 2 * np.mean(np.diff(tz)) == pytest.approx(ref["period"], rel=1e-3)
+    assert utip.max() == pytest.approx(ref["tip_amplitude"], rel=5e-3)
+    assert (energy.max() - energy.min()) / energy[0] < 5e-3
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("scheme", [oracle.USF, oracle.USL])
+def test_block_on_frictional_base(scheme):
+    th, g, h = math.radians(30.0), 9.81, 0.05
+    pos = W.gauss_fill(W.box_cells((2, 0), (10, 4)), h, (0.0, 0.0), 2)
+    res = {}
+    for mu in (0.2, 0.8):
+        mesh = oracle.Mesh(dim=2, n=(40, 8, 1), h=h, face_bc=(0, 0, 3, 0, 0, 0), face_mu=(0, 0, mu, 0, 0, 0),
+                           g=(g * math.sin(th), -g * math.cos(th), 0.0), dt=1e-5, scheme=scheme)
+        st = oracle.State.create(pos, np.zeros_like(pos), np.full(len(pos), h * h / 4), 1000.0)
+        o = oracle.Oracle(mesh, oracle.Material(E=5e7, nu=0.3, rho=1000.0), st)
+        M = st.m.sum()
+        n = 5000
+        vs = []
+        for _ in range(n):
+            assert o.step(1) == oracle.OK
+            vs.append(np.sum(st.m * st.v[:, 0]) / M)
+        t = (np.arange(n) + 1) * 1e-5
+        res[mu] = (np.polyfit(t[n // 2:], np.array(vs[n // 2:]), 1)[0], vs[-1])
+        # the block never sinks into the base
+        assert st.x[:, 1].min() > 0.0
+    a_slip = g * (math.sin(th) - 0.2 * math.cos(th))
+    assert res[0.2][0] == pytest.approx(a_slip, rel=1e-2)
+    assert abs(res[0.8][0]) < 0.05 * a_slip
+    assert abs(res[0.8][1]) < 0.1 * abs(res[0.2][1])
+
+
+def test_node_constraints_by_hand():
+    mesh = oracle.Mesh(dim=3, n=(4, 4, 4), h=0.1, dt=1e-3,
+                       face_bc=(oracle.BC_FIXED, 0, oracle.BC_ROLLER, 0, oracle.BC_FRICTION, 0),
+                       face_mu=(0, 0, 0, 0, 0.5, 0))
+    v, a, vn = [1.0, 2.0, 3.0], [10.0, 20.0, 30.0], [1.01, 2.02, 3.03]
+    out = oracle.constrain_node(mesh, (0, 2, 2), v, a, vn)          # fixed face
+    assert all(np.all(x == 0) for x in out)
+    out = oracle.constrain_node(mesh, (2, 0, 2), v, a, vn)          # roller on -y
+    assert np.array_equal(out[2], [1.01, 0.0, 3.03]) and out[1][1] == 0.0
+    # base (-z, outward -z): moving into the wall at 0.2 m/s -> contact
+    v0, a0 = np.array([0.1, 0.0, -0.1]), np.array([0.0, 0.0, -100.0])
+    vn0 = v0 + a0 * 1e-3                                             # (0.1, 0, -0.2)
+    v, a, vn = oracle.constrain_node(mesh, (2, 2, 0), v0, a0, vn0)
+    # Coulomb cap mu * 0.2 = 0.1 >= |vt| = 0.1 -> stick
+    assert np.allclose(vn, 0.0) and np.allclose(a, (vn - v0) / 1e-3)
+    vn0 = np.array([0.3, 0.0, -0.2])
+    v, a, vn = oracle.constrain_node(mesh, (2, 2, 0), v0, a0, vn0)
+    assert np.allclose(vn, [0.2, 0.0, 0.0]) and np.allclose(a, (vn - v0) / 1e-3)
+    # moving away from the base: untouched
+    vn0 = np.array([0.3, 0.0, 0.2])
+    v, a, vn = oracle.constrain_node(mesh, (2, 2, 0), v0, a0, vn0)
+    assert np.array_equal(vn, vn0) and np.array_equal(a, a0)
