@@ -1,0 +1,386 @@
+#!/usr/bin/env python
+"""Throughput of the explicit MPM step on GB300.
+
+Default workload: 3D dry granular column collapse, 200 x 40 x 100 hexahedra of
+5 mm, 0.2 m cube column with 8 particles per cell (512,000 particles),
+Mohr-Coulomb, Coulomb base friction, FP32 mixed precision, USL.  A "step" is
+one explicit MPM time step of the whole path (binning sort, P2G, nodal solve
+with boundary conditions, G2P with stress update and relocation).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Timing: W untimed steps, then K steps each bracketed by CUDA events on the
+library's stream, with a 256 MiB buffer written between steps (L2 flushed);
+max over ranks.  Prints one JSON line (rank 0).  With N > 1 (torchrun) every
+rank runs an independent replica of the workload on its own GPU (replicas
+only: the path has no cross-instance exchange), so value = N x per-rank work
+/ max time ("weak" scaling).
+
+--impl reference times the FP64 CPU oracle (the parity reference) on the
+host cores on the same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes as C
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1909_13380_gb300 import workloads as W  # noqa: E402
+
+METRIC = "particle-steps/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_column3d_512k.txt")
+KERNEL_SRC = os.path.join(ROOT, "paper_1909_13380_gb300", "csrc", "mpm_fp32.cu")
+
+
+def make_workload(name: str):
+    if name == "column3d":
+        return W.column3d()
+    if name == "column3d_small":
+        return W.column3d(ncells=(40, 16, 24), col_cells=(12, 12, 12))
+    if name == "bar":
+        return W.elastic_bar(precision=W.FP32_MIXED)
+    if name == "slope":
+        return W.slope3d()
+    if name == "slope_1_64":
+        return W.slope3d(ncells=(200, 50, 50), h=0.2, crest=8.0, plateau=8.5)
+    raise SystemExit(f"unknown workload {name}")
+
+
+# Algorithmic bytes per particle (what the method must move once: each
+# particle word read once and each mutable word written once, plus the
+# share of node traffic), FP32 mixed path.
+def algorithmic_bytes(dim: int, coh: bool):
+    ns = 6 if dim == 3 else 4
+    read = 4 + 4 * dim + 4 * dim + 4 * ns + 4 * ns + 12 + (4 if coh else 0)   # cell, off, v, sig, eps, m, V, epsp
+    write = read - 4 - (4 if coh else 0)                                      # all but m (and coh)
+    nodes_per_particle = 0.15 if dim == 3 else 1.3 / 4
+    p2g = 4 + 4 * dim + 4 * dim + 4 * ns + 8 + nodes_per_particle * 4 * (1 + 2 * dim)
+    g2p = read + write + nodes_per_particle * 4 * 2 * dim
+    step = (212 if dim == 3 else 174) + (4 if coh else 0)
+    return {"p2g": p2g, "g2p": g2p, "step": step}
+
+
+def load_peak():
+    try:
+        with open(PEAKS_FILE) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_hash() -> str:
+    with open(KERNEL_SRC, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def load_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel source (else None)."""
+    try:
+        kv = {}
+        for line in open(TRAFFIC_FILE):
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("kernel_source_sha256_16") != kernel_hash():
+            return None
+        return float(kv[f"{kernel}_dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) >= 9:
+                rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def reduce_max(value: float, world: int, device):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def cpu_oracle_rate(wl, budget_s: float, max_steps: int):
+    """Oracle particle-steps/s on the host: steps of the full workload from its
+    initial state until `budget_s` of CPU time or `max_steps` steps."""
+    import oracle
+    o = oracle.from_workload(wl)
+    t0 = time.perf_counter()
+    k = 0
+    while k < max_steps:
+        o.step(1)
+        k += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return wl.n * k / dt, k, dt
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    wl = make_workload(args.workload)
+    import oracle
+    o = oracle.from_workload(wl)
+    t_w0 = time.perf_counter()
+    for _ in range(args.warmup):
+        o.step(1)
+    t_step = (time.perf_counter() - t_w0) / max(args.warmup, 1)
+    k = args.steps
+    cap = max(1, int(math.ceil(120.0 / max(t_step, 1e-6))))
+    k_timed = min(k, cap)
+    t0 = time.perf_counter()
+    for _ in range(k_timed):
+        o.step(1)
+    dt = time.perf_counter() - t0
+    value = wl.n * k_timed / dt
+    sample = (f"steps {args.warmup + 1}..{args.warmup + k_timed} of the full {wl.n}-particle workload, "
+              f"FP64 oracle, one thread" + ("" if k_timed == k else f" (capped at {k_timed} of {k} steps)"))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
+            "steps": k_timed, "warmup": args.warmup, "ms_per_step": 1e3 * dt / k_timed,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": wl.name, "particles": wl.n},
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gb300(args):
+    import torch
+    from paper_1909_13380_gb300 import mpm
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=device)
+    wl = make_workload(args.workload)
+    stream = torch.cuda.Stream(device=device)
+    sptr = C.c_void_p(stream.cuda_stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
+
+    # ---- device-timed steps -------------------------------------------------
+    sim = mpm.Simulation(wl, stream=sptr)
+    mpm.mpm_set_phase_timing(sim.h, True)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            sim.step(1)
+            flush.zero_()
+    stream.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    sampler.start()
+    barrier(world)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    phases = []
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            sim.step(1)
+            ev[i][1].record(stream)
+            phases.append(mpm.mpm_phase_times(sim.h))
+            flush.zero_()
+    stream.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_dev = sum(step_ms) / 1e3
+    status = sim.sync()
+    if status != mpm.MPM_OK:
+        raise SystemExit(f"step failed: {mpm.STATUS_NAMES.get(status, status)}")
+    t_max = reduce_max(t_dev, world, device)
+    value = world * wl.n * args.steps / t_max
+    ph = np.array(phases)
+    ph_mean = ph.mean(axis=0)
+    names = ["sort", "tile_bounds", "p2g", "g2p"] if wl.scheme == W.USL else \
+        ["sort", "tile_bounds", "p2g_mom", "g2p_stress", "p2g_force", "g2p_advect"]
+    ab = algorithmic_bytes(wl.dim, wl.coh is not None)
+    peak, peak_kind = load_peak()
+    kernels = {"p2g": ph_mean[2], "g2p": ph_mean[3]}
+    dom = max(kernels, key=kernels.get)
+    achieved = ab[dom] * wl.n / (kernels[dom] * 1e-3) / 1e9
+    traffic = load_traffic(dom)
+    step_gbs = ab["step"] * wl.n / (t_dev / args.steps) / 1e9
+    mpm.mpm_set_phase_timing(sim.h, False)
+    sim.close()
+
+    # ---- plain FP64 GPU step on the same workload ---------------------------
+    fp64 = None
+    if not args.no_fp64:
+        k64 = max(1, min(args.steps, 10))
+        s64 = mpm.Simulation(wl, precision=W.FP64_PLAIN, stream=sptr)
+        with torch.cuda.stream(stream):
+            s64.step(1)
+            e64 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k64)]
+            for i in range(k64):
+                e64[i][0].record(stream)
+                s64.step(1)
+                e64[i][1].record(stream)
+                flush.zero_()
+        stream.synchronize()
+        ms64 = sum(a.elapsed_time(b) for a, b in e64) / k64
+        s64.close()
+        fp64 = {"value": wl.n / (ms64 * 1e-3), "unit": METRIC, "ms_per_step": ms64, "steps": k64,
+                "fp32_mixed_speedup": (wl.n * args.steps / t_dev) / (wl.n / (ms64 * 1e-3))}
+
+    # ---- end to end through the C-ABI with host buffers ---------------------
+    e2e = None
+    if not args.no_e2e:
+        ns = 6 if wl.dim == 3 else 4
+        h2d = wl.n * 4 * (2 + 2 * wl.dim + 2 * ns + 3 + (1 if wl.coh is not None else 0))
+        d2h = wl.n * 8 * (2 * wl.dim + 6 + 6 + 1 + 1 + 1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s = mpm.Simulation(wl, stream=sptr)
+        s.step(args.steps)
+        snap, st = s.read()
+        s.close()
+        t1 = time.perf_counter()
+        e2e = {"value": wl.n * args.steps / (t1 - t0), "unit": METRIC,
+               "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(d2h / args.steps),
+               "seconds": t1 - t0, "includes": "mesh creation, host->device upload, K steps, device->host read"}
+
+    # ---- CPU oracle baseline (rank 0, N = 1) ---------------------------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, k, dt = cpu_oracle_rate(wl, budget_s=args.cpu_budget, max_steps=args.steps)
+        cpu = {"value": rate, "unit": METRIC, "cores": 1, "kind": "oracle",
+               "sample": f"first {k} steps of the full {wl.n}-particle workload from its initial state, "
+                         f"FP64 oracle, one thread, {dt:.1f} s"}
+
+    if rank == 0:
+        key_bits = int(math.ceil(math.log2(wl_keyspace(wl) + 1)))
+        per_step = 5 * int(math.ceil(key_bits / 8)) + 1 + (2 if wl.scheme == W.USL else 4) + 1
+        line = {
+            "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl.name, "particles": wl.n, "scheme": "USL" if wl.scheme == W.USL else "USF",
+                       "precision": "fp32_mixed", "l2": "flushed between timed steps (256 MiB write)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": {"bound": "hbm", "kernel": f"{dom}_tile", "achieved": achieved, "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                         "algorithmic_bytes_per_particle": ab[dom], "ms_per_launch": kernels[dom]},
+            "step_roofline": {"achieved": step_gbs, "frac": step_gbs / peak, "unit": "GB/s",
+                              "algorithmic_bytes_per_particle": ab["step"]},
+            "phases_ms": dict(zip(names, [float(x) for x in ph_mean])),
+            "clocks": clocks, "gpu_launches": per_step * args.steps,
+            "e2e": e2e, "fp64_plain": fp64, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def wl_keyspace(wl):
+    T = (8, 8, 4) if wl.dim == 3 else (16, 16, 1)
+    nt = 1
+    for k in range(3):
+        nt *= -(-wl.ncells[k] // T[k])
+    return nt * 256
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--workload", default="column3d",
+                    choices=["column3d", "column3d_small", "bar", "slope", "slope_1_64"])
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gb300(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,217 @@
+/*
+ * mpm.h -- C ABI of the GB300 explicit material point method library
+ * (libmpm.so).  Plain C types only: no C++ or PyTorch types cross it.
+ *
+ * The operation is one explicit MPM time step as described in Kumar et al.,
+ * "Scalable and modular material point method for large-scale simulations"
+ * (arXiv 1909.13380):
+ *   INTRODUCTION   particles carry all state; the equations are solved on the
+ *                  nodes of a fixed background mesh, whose nodal values are
+ *                  reset every step; particle->node and node->particle
+ *                  transfers use the same shape functions.
+ *   CODE OVERVIEW  Node (mass, momentum, velocity, acceleration, forces;
+ *                  persistent friction/velocity constraints), Cell with the
+ *                  linear 4-node quadrilateral / 8-node hexahedron, Material
+ *                  (stress from a strain increment), Mesh, and the explicit
+ *                  USF / USL algorithms.
+ *   DATA STRUCTURES  6-component Voigt stress/strain.
+ *   ISOPARAMETRIC MESH  nodal velocity and frictional boundary conditions;
+ *                  locating particles in cells.
+ * The paper prints no equations; the library computes the textbook explicit
+ * MPM (Sulsky et al. 1994; USF/USL after Bardenhagen 2002) with a
+ * Mohr-Coulomb return in principal stresses (de Souza Neto et al. 2008).
+ *
+ * Conventions
+ *   - Faces are numbered -x, +x, -y, +y, -z, +z.  Vectors have `dim`
+ *     components; stresses and strains have 6 Voigt components
+ *     (xx, yy, zz, xy, yz, xz) with tensor (not engineering) shear strain,
+ *     also in 2D (plane strain: strain zz = 0, stress zz kept; yz = xz = 0).
+ *   - Tension is positive.  Angles are in radians.
+ *   - Cells are Cartesian cubes/squares of side h; node (i,j,k) sits at
+ *     origin + (i,j,k) h.  A particle's cell is floor((x - origin)/h) per
+ *     axis; a particle on a face belongs to the higher cell, and one at or
+ *     beyond the upper mesh bound has left the mesh.
+ *   - Host pointers are copied; the caller keeps ownership.  The library
+ *     owns all device memory of a handle and frees it in mpm_destroy.
+ *   - Every call returns an mpm_status.  MPM_ERR_ARG leaves the handle as it
+ *     was; every other error is sticky per handle until mpm_destroy.
+ *     mpm_last_error gives a message.  Device-side conditions
+ *     (a particle left the mesh, a non-finite value) are latched in a device
+ *     status word and reported at the next synchronising call.
+ *   - A handle is not thread-safe; different handles may be used from
+ *     different host threads.
+ */
+#ifndef MPM_GB300_H
+#define MPM_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mpm_ctx *mpm_handle;
+
+typedef enum {
+  MPM_OK = 0,
+  MPM_ERR_ARG = -1,       /* malformed argument; nothing was changed */
+  MPM_ERR_OOM = -2,       /* device allocation failed */
+  MPM_ERR_CUDA = -3,      /* a CUDA runtime call or launch failed */
+  MPM_ERR_LEFT_MESH = -4, /* a particle left the mesh; it is dropped from the step */
+  MPM_ERR_NONFINITE = -5, /* a particle state became NaN/Inf */
+  MPM_ERR_TIMEOUT = -6,   /* a bounded device wait gave up */
+  MPM_ERR_STATE = -7      /* call not valid in the handle's current state */
+} mpm_status;
+
+enum { MPM_BC_FREE = 0, MPM_BC_ROLLER = 1, MPM_BC_FIXED = 2, MPM_BC_FRICTION = 3 };
+enum { MPM_USF = 0, MPM_USL = 1 };
+enum { MPM_FP64_PLAIN = 0, MPM_FP32_MIXED = 1 };
+enum { MPM_LINEAR_ELASTIC = 0, MPM_MOHR_COULOMB = 1 };
+
+/* Background mesh and step parameters (CODE OVERVIEW: Mesh, Node, Cell;
+ * the explicit USF/USL algorithm).
+ *   dim        2 (4-node quads, plane strain) or 3 (8-node hexahedra)
+ *   ncells     cells per axis (ncells[2] ignored in 2D); each >= 1
+ *   h          cell size (> 0); origin: coordinates of node (0,0,0)
+ *   face_bc    per face: MPM_BC_FREE / ROLLER (normal velocity 0) /
+ *              FIXED (all velocity 0) / FRICTION (Coulomb, coefficient
+ *              face_mu; contact only while the node moves into the face)
+ *   gravity    body acceleration; dt: time step (> 0)
+ *   scheme     MPM_USF or MPM_USL
+ *   precision  MPM_FP64_PLAIN: FP64 global positions, unsorted particles,
+ *              FP64 atomics on a dense node grid.
+ *              MPM_FP32_MIXED: FP32 state with each position held as an
+ *              integer cell plus an FP32 offset, particles binned by cell
+ *              every step, deterministic tile reductions with compensated
+ *              sums, FP64 only in the Mohr-Coulomb return near the apex and
+ *              in the conservation sums.
+ *   mass_tol   a node is active when its mass exceeds this (e.g. 1e-12 kg)
+ *   stream     cudaStream_t to enqueue on (NULL: the legacy default stream) */
+typedef struct {
+  int32_t dim;
+  int32_t ncells[3];
+  double h;
+  double origin[3];
+  int32_t face_bc[6];
+  double face_mu[6];
+  double gravity[3];
+  double dt;
+  int32_t scheme;
+  int32_t precision;
+  double mass_tol;
+  void *stream;
+} mpm_mesh_desc;
+
+/* Material of the particles (CODE OVERVIEW: Material).  Linear elastic uses
+ * E, nu; Mohr-Coulomb adds friction angle phi, cohesion c and dilation
+ * angle psi (perfect plasticity).  rho gives particle mass rho * volume. */
+typedef struct {
+  int32_t model;
+  double E, nu, rho;
+  double phi, c, psi;
+} mpm_material;
+
+/* Create a mesh.  Validates desc (MPM_ERR_ARG on nonsense) and allocates the
+ * node/tile storage on the current CUDA device.  *out receives the handle. */
+mpm_status mpm_create_mesh(const mpm_mesh_desc *desc, mpm_handle *out);
+
+/* Add n particles (CODE OVERVIEW: material points with a Material).
+ *   pos, vel   n*dim doubles, row-major (host)
+ *   vol        n doubles, initial volume (area per unit thickness in 2D)
+ *   mat        material; every call on a handle must pass the same one
+ *   cohesion   n doubles overriding mat->c per particle, or NULL
+ *   stress0    n*6 initial stresses, or NULL for zero
+ *   first_id   out: id of the first new particle (ids are 0,1,2,... in
+ *              insertion order), may be NULL
+ * Particles outside the mesh are rejected (MPM_ERR_ARG, none added).  The
+ * initial cell is computed on the host in FP64 by the rule above.  Must not
+ * be called while steps are in flight (it synchronises the stream). */
+mpm_status mpm_add_particles(mpm_handle h, int64_t n, const double *pos, const double *vel,
+                             const double *vol, const mpm_material *mat, const double *cohesion,
+                             const double *stress0, int64_t *first_id);
+
+/* Enqueue nsteps explicit steps on desc.stream and return without waiting.
+ * Returns a latched error, if any, or MPM_OK.  Zero particles is valid. */
+mpm_status mpm_step(mpm_handle h, int64_t nsteps);
+
+/* Wait for enqueued work and return the latched device status. */
+mpm_status mpm_sync(mpm_handle h);
+
+/* Number of particles added so far (live or not). */
+mpm_status mpm_num_particles(mpm_handle h, int64_t *n);
+
+/* Copy particle state to host arrays in insertion order (synchronises).
+ * Any pointer may be NULL.  pos/vel: n*dim; stress/strain: n*6; vol, epsp
+ * (accumulated equivalent plastic strain): n; cell: n linear cell ids
+ * ix + nx*(iy + ny*iz), -1 for particles that left the mesh. */
+mpm_status mpm_read_particles(mpm_handle h, double *pos, double *vel, double *stress,
+                              double *strain, double *vol, double *epsp, int64_t *cell);
+
+/* FP64 global sums over live particles (deterministic order): out[0] mass,
+ * out[1..3] momentum, out[4] kinetic energy, out[5] strain energy
+ * sum 1/2 V sigma:eps, out[6] number of live particles.  Synchronises. */
+mpm_status mpm_conservation(mpm_handle h, double out[7]);
+
+/* Particle binning (step a1 of the path; ISOPARAMETRIC MESH: locating the
+ * particles in cells), FP32_MIXED handles only.  Runs the binning of the
+ * current particle storage and copies to the host: key[n] the binning key of
+ * each stored particle (tile-major cell id, see below; dead particles carry
+ * the largest key) and perm[n] the stable sort permutation (perm[q] is the
+ * storage slot of the q-th particle in key order; ties keep storage order).
+ * Tile-major key: tiles of TX x TY x TZ cells (16 x 16 in 2D, 8 x 8 x 4 in
+ * 3D), tile t = tx + NTX*(ty + NTY*tz), local l = lx + TX*(ly + TY*lz),
+ * key = t * (TX*TY*TZ) + l; dead key = NT * (TX*TY*TZ).  tile_dims receives
+ * (TX, TY, TZ) if not NULL. */
+mpm_status mpm_read_binning(mpm_handle h, int32_t *key, int32_t *perm, int32_t *tile_dims);
+
+/* Per-phase device timing of the FP32_MIXED step (measurement support; the
+ * paper reports wall times only, BENCHMARK AND PERFORMANCE).  When enabled,
+ * every enqueued step records CUDA events (cudaEventRecordExternal, so they
+ * also fire inside the captured step graph) at its phase boundaries.
+ * mpm_phase_times synchronises and writes the durations in milliseconds of
+ * the most recent step's phases to ms[0..*nphase-1]:
+ *   USL: binning sort, tile bounds, P2G, G2P (+ carry of dead particles)
+ *   USF: binning sort, tile bounds, P2G mass/momentum, G2P stress,
+ *        P2G internal force, G2P advection (+ carry of dead particles)
+ * ms must hold MPM_MAX_PHASES floats.  MPM_ERR_STATE on FP64_PLAIN handles
+ * or when timing is off or no step ran since it was enabled. */
+#define MPM_MAX_PHASES 8
+mpm_status mpm_set_phase_timing(mpm_handle h, int32_t enable);
+mpm_status mpm_phase_times(mpm_handle h, float *ms, int32_t *nphase);
+
+/* Human-readable description of the last error on h (never NULL). */
+const char *mpm_last_error(mpm_handle h);
+
+/* Free all device storage of h.  NULL is accepted. */
+mpm_status mpm_destroy(mpm_handle h);
+
+/* ---- standalone path primitives ---------------------------------------- */
+
+/* Stable LSD radix sort by key on the device (the binning step a1 as a
+ * primitive).  d_keys: n uint32 keys < 2^key_bits (device, unchanged);
+ * d_perm: n int32 out (device), perm[q] = index of the q-th smallest key,
+ * equal keys in index order.  key_bits in 1..32.  Allocates its scratch with
+ * cudaMallocAsync on `stream` and frees it before returning (the call
+ * synchronises the stream). */
+mpm_status mpm_sort_keys(const uint32_t *d_keys, int32_t *d_perm, int64_t n, int32_t key_bits,
+                         void *stream);
+
+/* Material-point stress update on the GPU (CODE OVERVIEW: Material, "the
+ * updated stresses for a given strain tensor"), for n independent points.
+ *   sig, deps   n*6 host doubles: stress before, strain increment
+ *   cohesion    n host doubles or NULL (mat->c)
+ *   sig_out     n*6 host doubles out; depsp_out n doubles out (equivalent
+ *               plastic strain increment), may be NULL
+ *   precision   MPM_FP64_PLAIN computes in FP64; MPM_FP32_MIXED rounds the
+ *               inputs to FP32 and computes as the FP32 step does (FP64
+ *               only near the Mohr-Coulomb apex).
+ * Synchronous; allocates and frees its own device buffers. */
+mpm_status mpm_material_update(const mpm_material *mat, int32_t precision, int64_t n,
+                               const double *sig, const double *deps, const double *cohesion,
+                               double *sig_out, double *depsp_out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPM_GB300_H */

@@ -321,3 +321,11 @@ def constrain_node(mesh: Mesh, ijk, v, a, vn):
     c = np.array(ijk, np.int32)
     lib().oracle_constrain_node(C.byref(mesh.c_struct()), _ip(c), _dp(v), _dp(a), _dp(vn))
     return v, a, vn
+
+
+def from_workload(wl, scheme=None) -> Oracle:
+    """Oracle on a workload from paper_1909_13380_gb300.workloads (inputs only)."""
+    mesh = Mesh(dim=wl.dim, n=wl.ncells, h=wl.h, origin=wl.origin, face_bc=wl.face_bc, face_mu=wl.face_mu,
+                g=wl.gravity, dt=wl.dt, scheme=wl.scheme if scheme is None else scheme)
+    st = State.create(wl.pos, wl.vel, wl.vol, wl.material["rho"], coh=wl.coh)
+    return Oracle(mesh, Material(**wl.material), st)

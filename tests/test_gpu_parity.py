@@ -1,0 +1,274 @@
+"""GPU parity: the CUDA path through the C-ABI against the FP64 oracle on the
+same seeded inputs (sizes that span several tiles with ragged tails, and the
+full 512,000-particle column in the configuration the benchmark times).
+
+Bars: cells and binning bit-exact; FP64 GPU within 1e-9 relative L2 of the
+oracle; FP32 mixed within 1e-5 per step from an identical state and 1e-3
+after a run (tests/helpers.py).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1909_13380_gb300 import workloads as W
+from tests import helpers as H
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - collected only with -m gpu on a GPU machine
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1909_13380_gb300 import mpm  # noqa: E402
+
+
+def run_gpu(wl, steps, precision=None, scheme=None):
+    with mpm.Simulation(wl, precision=precision, scheme=scheme) as sim:
+        if steps:
+            sim.step(steps)
+        snap, st = sim.read()
+        return snap, st
+
+
+def run_oracle(wl, steps, scheme=None):
+    o = H.oracle_from_workload(wl, scheme)
+    st = o.step(steps) if steps else oracle.OK
+    return H.oracle_snapshot(o, wl.dim), st
+
+
+@pytest.mark.parametrize("precision", [W.FP64_PLAIN, W.FP32_MIXED])
+def test_initial_cells_bit_exact(precision):
+    wl = H.small_column(precision=precision)
+    gpu, st = run_gpu(wl, 0)
+    ref, _ = run_oracle(wl, 0)
+    assert st == mpm.MPM_OK
+    assert np.array_equal(gpu["cell"], ref["cell"])
+
+
+def test_fp64_bar_matches_oracle():
+    wl = W.elastic_bar()
+    start, _ = run_oracle(wl, 0)
+    gpu, st = run_gpu(wl, wl.steps)
+    ref, rst = run_oracle(wl, wl.steps)
+    assert st == mpm.MPM_OK and rst == oracle.OK
+    err = H.compare(gpu, ref, start, 2)
+    assert max(err.values()) <= H.TOL_RUN_FP64, err
+    assert np.array_equal(gpu["cell"], ref["cell"])
+
+
+@pytest.mark.parametrize("scheme", [W.USF, W.USL])
+def test_fp32_bar(scheme):
+    wl = W.elastic_bar(precision=W.FP32_MIXED, scheme=scheme)
+    start, _ = run_oracle(wl, 0, scheme)
+    g1, _ = run_gpu(wl, 1)
+    r1, _ = run_oracle(wl, 1, scheme)
+    e1 = H.compare(g1, r1, start, 2)
+    assert max(e1.values()) <= H.TOL_STEP_FP32, e1
+    gpu, st = run_gpu(wl, wl.steps)
+    ref, _ = run_oracle(wl, wl.steps, scheme)
+    assert st == mpm.MPM_OK
+    err = H.compare(gpu, ref, start, 2)
+    assert max(err.values()) <= H.TOL_RUN_FP32, err
+
+
+@pytest.mark.parametrize("scheme", [W.USL, W.USF])
+def test_small_column_fp64(scheme):
+    wl = H.small_column(precision=W.FP64_PLAIN, scheme=scheme)
+    start, _ = run_oracle(wl, 0, scheme)
+    gpu, st = run_gpu(wl, 200)
+    ref, _ = run_oracle(wl, 200, scheme)
+    assert st == mpm.MPM_OK
+    err = H.compare(gpu, ref, start, 3)
+    assert max(err.values()) <= H.TOL_RUN_FP64, err
+    ndiff, nout = H.cell_mismatch_in_band(gpu, ref, wl.h, 1e-6)
+    assert nout == 0
+
+
+@pytest.mark.parametrize("scheme", [W.USL, W.USF])
+def test_small_column_fp32(scheme):
+    wl = H.small_column(precision=W.FP32_MIXED, scheme=scheme)
+    start, _ = run_oracle(wl, 0, scheme)
+    g1, _ = run_gpu(wl, 1)
+    r1, _ = run_oracle(wl, 1, scheme)
+    e1 = H.compare(g1, r1, start, 3)
+    assert max(e1.values()) <= H.TOL_STEP_FP32, e1
+    gpu, st = run_gpu(wl, 300)
+    ref, _ = run_oracle(wl, 300, scheme)
+    assert st == mpm.MPM_OK
+    err = H.compare(gpu, ref, start, 3)
+    assert max(err.values()) <= H.TOL_RUN_FP32, err
+    ndiff, nout = H.cell_mismatch_in_band(gpu, ref, wl.h, 1e-4)
+    assert nout == 0
+
+
+def test_full_column_per_step_parity():
+    """512,000 particles, FP32 USL, the benchmark's launch configuration:
+    one step from the initial state, then one step from a developed state
+    (the GPU's own state after 60 steps), each against the oracle."""
+    wl = W.column3d()
+    start, _ = run_oracle(wl, 0)
+    with mpm.Simulation(wl) as sim:
+        sim.step(1)
+        g1, st = sim.read()
+        assert st == mpm.MPM_OK
+        r1, _ = run_oracle(wl, 1)
+        e1 = H.compare(g1, r1, start, 3)
+        assert max(e1.values()) <= H.TOL_STEP_FP32, e1
+        sim.step(59)
+        s60, st = sim.read()
+        assert st == mpm.MPM_OK
+        sim.step(1)
+        g61, _ = sim.read()
+    o = H.oracle_from_gpu(wl, s60)
+    assert o.step(1) == oracle.OK
+    r61 = H.oracle_snapshot(o, 3)
+    e61 = H.compare(g61, r61, s60, 3)
+    assert max(e61.values()) <= H.TOL_STEP_FP32, e61
+    assert H.cell_mismatch_in_band(g61, r61, wl.h, 1e-4)[1] == 0
+
+
+def test_binning_is_the_stable_sort_of_the_keys():
+    wl = H.small_column()
+    with mpm.Simulation(wl) as sim:
+        sim.step(37)
+        key, perm, td = sim.binning()
+        snap, _ = sim.read(fields=("cell", "pos"))
+    assert np.array_equal(perm, np.argsort(key, kind="stable").astype(np.int32))
+    # keys are the tile-major ids of the cells
+    nc = wl.ncells
+    c = snap["cell"]
+    ix, iy, iz = c % nc[0], (c // nc[0]) % nc[1], c // (nc[0] * nc[1])
+    nt = [-(-nc[k] // td[k]) for k in range(3)]
+    t = ix // td[0] + nt[0] * (iy // td[1] + nt[1] * (iz // td[2]))
+    loc = ix % td[0] + td[0] * (iy % td[1] + td[1] * (iz % td[2]))
+    expect = t * (td[0] * td[1] * td[2]) + loc
+    assert np.array_equal(np.sort(key), np.sort(expect.astype(np.int32)))
+    # the oracle's locate of each stored (cell, offset) gives the stored cell
+    cells = oracle.locate(oracle.Mesh(dim=3, n=nc, h=wl.h), snap["pos"])
+    lin = cells[:, 0] + nc[0] * (cells[:, 1] + nc[1] * cells[:, 2])
+    bad = lin != c
+    if bad.any():
+        frac = snap["pos"][bad] / wl.h
+        assert np.abs(frac - np.round(frac)).min(axis=1).max() < 1e-9
+
+
+@pytest.mark.parametrize("n", [0, 1, 31, 33, 4095, 4096, 4097, 100_003])
+@pytest.mark.parametrize("bits", [1, 8, 13, 20, 32])
+def test_sort_keys_primitive(n, bits):
+    rng = np.random.default_rng(n * 31 + bits)
+    hi = (1 << bits) if bits < 32 else (1 << 32)
+    keys = rng.integers(0, min(hi, 50) if n % 2 else hi, size=n, dtype=np.uint64).astype(np.uint32)
+    dk = torch.from_numpy(keys.view(np.int32)).cuda()
+    dp = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
+    mpm.mpm_sort_keys(dk, dp, n, bits)
+    torch.cuda.synchronize()
+    got = dp[:n].cpu().numpy()
+    assert np.array_equal(got, np.argsort(keys, kind="stable").astype(np.int32))
+
+
+def _trials(rng, n, scale, c):
+    out = []
+    for i in range(n):
+        if i % 4 == 3:   # near the apex c cot(phi)
+            pa = c / math.tan(math.radians(30.0))
+            s = rng.normal(0, 1e-4 * scale, 6)
+            s[:3] += pa + rng.normal(0, 1e-4 * scale)
+        else:
+            s = rng.normal(0, scale, 6)
+            s[:3] += rng.normal(-scale, scale)
+        out.append(s)
+    return np.array(out)
+
+
+@pytest.mark.parametrize("c", [0.0, 10e3])
+def test_material_update_against_oracle(c):
+    rng = np.random.default_rng(17)
+    n = 4000
+    sig = _trials(rng, n, 3e4, c)
+    de = rng.normal(0, 2e-4, (n, 6))
+    mat_o = oracle.Material(model=oracle.MOHR_COULOMB, E=10e6, nu=0.3, rho=1800.0, phi=math.radians(30), c=c,
+                            psi=0.0)
+    mat_g = mpm.make_material(model=mpm.MPM_MOHR_COULOMB, E=10e6, nu=0.3, rho=1800.0, phi=math.radians(30),
+                              c=c, psi=0.0)
+    ref = np.array([oracle.stress_update(mat_o, c, sig[i], de[i])[0] for i in range(n)])
+    out64, _ = mpm.mpm_material_update(mat_g, mpm.MPM_FP64_PLAIN, sig, de)
+    scale = np.abs(ref).max(axis=1, keepdims=True) + 1.0
+    assert np.all(np.abs(out64 - ref) <= 1e-9 * scale)
+    # FP32 inputs are rounded first: compare with the oracle on the rounded inputs
+    sig32 = sig.astype(np.float32).astype(np.float64)
+    de32 = de.astype(np.float32).astype(np.float64)
+    ref32 = np.array([oracle.stress_update(mat_o, c, sig32[i], de32[i])[0] for i in range(n)])
+    out32, _ = mpm.mpm_material_update(mat_g, mpm.MPM_FP32_MIXED, sig, de)
+    assert H.rel_l2(out32, ref32) <= H.TOL_STEP_FP32
+    assert np.all(np.abs(out32 - ref32) <= 2e-4 * scale)
+
+
+@pytest.mark.parametrize("precision", [W.FP64_PLAIN, W.FP32_MIXED])
+def test_particle_leaving_the_mesh(precision):
+    pos = np.array([[0.05, 0.05], [0.0995, 0.05], [0.05, 0.02]])
+    vel = np.array([[0.0, 0.0], [200.0, 0.0], [0.0, 0.0]])
+    wl = W.Workload(name="leave", dim=2, ncells=(10, 10, 1), h=0.01, origin=(0, 0, 0), face_bc=(0,) * 6,
+                    face_mu=(0,) * 6, gravity=(0, 0, 0), dt=1e-5, scheme=W.USL, precision=precision,
+                    material=dict(model=0, E=1e3, nu=0.2, rho=1000.0, phi=0, c=0, psi=0), pos=pos, vel=vel,
+                    vol=np.full(3, 2.5e-5))
+    with mpm.Simulation(wl) as sim:
+        sim.step(5)
+        assert sim.sync() == mpm.MPM_ERR_LEFT_MESH
+        snap, st = sim.read()
+    assert st == mpm.MPM_ERR_LEFT_MESH
+    assert snap["cell"][1] == -1 and snap["cell"][0] >= 0 and snap["cell"][2] >= 0
+    assert np.all(np.isfinite(snap["pos"][[0, 2]]))
+
+
+@pytest.mark.parametrize("precision", [W.FP64_PLAIN, W.FP32_MIXED])
+def test_empty_and_single_particle(precision):
+    wl = W.elastic_bar(precision=precision)
+    empty = W.Workload(**{**wl.__dict__, "pos": wl.pos[:0], "vel": wl.vel[:0], "vol": wl.vol[:0]})
+    with mpm.Simulation(empty) as sim:
+        sim.step(3)
+        assert sim.sync() == mpm.MPM_OK
+        cons, _ = sim.conservation()
+        assert cons["alive"] == 0
+    # one particle in free fall, crossing cells: v = n g dt, x = x0 + g dt^2 n(n+1)/2
+    g = (0.7, 0.4, -9.81)
+    one = W.Workload(name="one", dim=3, ncells=(40, 40, 40), h=0.01, origin=(0, 0, 0), face_bc=(0,) * 6,
+                     face_mu=(0,) * 6, gravity=g, dt=1e-3, scheme=W.USL, precision=precision,
+                     material=dict(model=0, E=10.0, nu=0.2, rho=1000.0, phi=0, c=0, psi=0),
+                     pos=np.array([[0.2031, 0.3507, 0.3313]]), vel=np.zeros((1, 3)), vol=np.array([1e-6]))
+    with mpm.Simulation(one) as sim:
+        sim.step(100)
+        snap, st = sim.read()
+    assert st == mpm.MPM_OK
+    tol = 1e-12 if precision == W.FP64_PLAIN else 1e-5
+    assert np.allclose(snap["vel"][0], 100 * np.array(g) * 1e-3, rtol=tol, atol=tol)
+    expect = one.pos[0] + np.array(g) * 1e-6 * 100 * 101 / 2
+    assert np.allclose(snap["pos"][0], expect, rtol=0, atol=tol * 0.5)
+
+
+def test_fp32_step_is_deterministic():
+    wl = H.small_column()
+    a, _ = run_gpu(wl, 120)
+    b, _ = run_gpu(wl, 120)
+    for k in a:
+        assert np.array_equal(a[k], b[k], equal_nan=True), k
+
+
+@pytest.mark.parametrize("precision", [W.FP64_PLAIN, W.FP32_MIXED])
+def test_conservation_sums(precision):
+    wl = H.small_column(precision=precision)
+    with mpm.Simulation(wl) as sim:
+        sim.step(50)
+        cons, st = sim.conservation()
+        snap, _ = sim.read()
+    o = H.oracle_from_gpu(wl, snap)
+    if precision == W.FP32_MIXED:
+        o.state.m[:] = (wl.material["rho"] * wl.vol).astype(np.float32)
+    ref = o.conservation()
+    assert cons["alive"] == ref["alive"] == wl.n
+    assert cons["mass"] == pytest.approx(ref["mass"], rel=1e-12)
+    assert np.allclose(cons["momentum"], ref["momentum"], rtol=1e-9, atol=1e-12 * ref["mass"])
+    assert cons["ke"] == pytest.approx(ref["ke"], rel=1e-9)
+    # mass is carried exactly by the particles
+    assert cons["mass"] == pytest.approx((wl.material["rho"] * wl.vol).sum(), rel=1e-6)
