@@ -272,11 +272,12 @@ def run_gb300(args):
     value = world * wl.n * args.steps / t_max
     ph = np.array(phases)
     ph_mean = ph.mean(axis=0)
-    names = ["sort", "tile_bounds", "p2g", "g2p"] if wl.scheme == W.USL else \
-        ["sort", "tile_bounds", "p2g_mom", "g2p_stress", "p2g_force", "g2p_advect"]
+    names = ["binning", "p2g", "node", "g2p"] if wl.scheme == W.USL else \
+        ["binning", "p2g_mom", "node_v", "g2p_stress", "p2g_force", "node_a", "g2p_advect"]
     ab = algorithmic_bytes(wl.dim, wl.coh is not None)
     peak, peak_kind = load_peak()
-    kernels = {"p2g": ph_mean[2], "g2p": ph_mean[3]}
+    kernels = {"p2g": ph_mean[1], "g2p": ph_mean[3]} if wl.scheme == W.USL else \
+        {"p2g": ph_mean[1] + ph_mean[4], "g2p": ph_mean[3] + ph_mean[6]}
     dom = max(kernels, key=kernels.get)
     achieved = ab[dom] * wl.n / (kernels[dom] * 1e-3) / 1e9
     traffic = load_traffic(dom)
@@ -329,8 +330,8 @@ def run_gb300(args):
                          f"FP64 oracle, one thread, {dt:.1f} s"}
 
     if rank == 0:
-        key_bits = int(math.ceil(math.log2(wl_keyspace(wl) + 1)))
-        per_step = 5 * int(math.ceil(key_bits / 8)) + 1 + (2 if wl.scheme == W.USL else 4) + 1
+        # binning: bin_movers, bin_scan, bin_bucket, bin_tiles; then the step kernels
+        per_step = 4 + (3 if wl.scheme == W.USL else 6)
         line = {
             "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
@@ -338,7 +339,7 @@ def run_gb300(args):
             "config": {"workload": wl.name, "particles": wl.n, "scheme": "USL" if wl.scheme == W.USL else "USF",
                        "precision": "fp32_mixed", "l2": "flushed between timed steps (256 MiB write)",
                        "parallelism": "replicas" if world > 1 else "single"},
-            "roofline": {"bound": "hbm", "kernel": f"{dom}_tile", "achieved": achieved, "peak": peak,
+            "roofline": {"bound": "hbm", "kernel": {"p2g": "p2g_tile", "g2p": "g2p"}[dom], "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                          "algorithmic_bytes_per_particle": ab[dom], "ms_per_launch": kernels[dom]},
             "step_roofline": {"achieved": step_gbs, "frac": step_gbs / peak, "unit": "GB/s",
@@ -352,14 +353,6 @@ def run_gb300(args):
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
-
-
-def wl_keyspace(wl):
-    T = (8, 8, 4) if wl.dim == 3 else (16, 16, 1)
-    nt = 1
-    for k in range(3):
-        nt *= -(-wl.ncells[k] // T[k])
-    return nt * 256
 
 
 def main(argv=None):

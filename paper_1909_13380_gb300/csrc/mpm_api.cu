@@ -3,7 +3,8 @@
 // Host side of the library: validates descriptors, owns device storage,
 // computes each particle's initial cell on the host in FP64 (cell =
 // floor((x - origin)/h) per axis; the offset from the cell centre, in cell
-// units, is rounded to FP32 for the mixed path), enqueues steps on the
+// units, is rounded to FP32 for the mixed path), bins the particles once with
+// a full stable radix sort when they are added, enqueues steps on the
 // handle's stream (replaying a captured CUDA graph per step when the stream
 // allows capture), and converts the state back to FP64 in insertion order.
 #include <cuda_runtime.h>
@@ -34,12 +35,14 @@ struct mpm_ctx {
   // FP32 mixed
   Geo geo;
   int key_bits = 1;
+  int64_t nnodes = 0;
   void *bufmem[2] = {nullptr, nullptr};
   PBuf buf[2];
-  int cur = 0;
+  int cur = 0;  // state buf[cur], old tile ranges tile_start[cur]
   StepBufs s{};
+  uint32_t *keys2 = nullptr;  // binning outputs of mpm_read_binning
+  int32_t *perm2 = nullptr;
   void *sort_scratch = nullptr;
-  size_t sort_scratch_bytes = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   bool timing = false;
   bool timed_step = false;
@@ -49,8 +52,8 @@ struct mpm_ctx {
   void *pmem64 = nullptr;
   void *nmem64 = nullptr;
   // shared
-  int32_t *d_status = nullptr;  // FP64 path status word (FP32 path uses s.ctr[8])
-  double *d_cons = nullptr;     // 7 + partials
+  int32_t *d_status = nullptr;  // FP64 path status word (FP32 path: s.ctr[C_STATUS])
+  double *d_cons = nullptr;     // 8 results + partials
 };
 
 namespace {
@@ -68,23 +71,21 @@ mpm_status cuda_fail(mpm_ctx *h, cudaError_t e, const char *where) {
   return fail(h, MPM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
-#define CK(expr, where)                                 \
-  do {                                                  \
-    cudaError_t _e = (expr);                            \
+#define CK(expr, where)                                    \
+  do {                                                     \
+    cudaError_t _e = (expr);                               \
     if (_e != cudaSuccess) return cuda_fail(h, _e, where); \
   } while (0)
 
 size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
 
 int nfields32(int dim, bool coh) {
-  // off[D] vel[D] sig[NS] eps[NS] mass vol epsp (coh)
+  // off[D] vel[D] sig[NS] eps[NS] mass jm1 epsp (coh)
   const int ns = dim == 3 ? 6 : 4;
   return 2 * dim + 2 * ns + 3 + (coh ? 1 : 0);
 }
 
-size_t buf32_bytes(int dim, bool coh, int64_t cap) {
-  return al256(4 * cap) * (2 + nfields32(dim, coh));
-}
+size_t buf32_bytes(int dim, bool coh, int64_t cap) { return al256(4 * cap) * (2 + nfields32(dim, coh)); }
 
 void carve32(void *mem, int dim, bool coh, int64_t cap, PBuf &b) {
   char *p = (char *)mem;
@@ -98,7 +99,7 @@ void carve32(void *mem, int dim, bool coh, int64_t cap, PBuf &b) {
   for (int i = 0; i < ns; ++i) { b.sig[i] = (float *)p; p += f; }
   for (int i = 0; i < ns; ++i) { b.eps[i] = (float *)p; p += f; }
   b.mass = (float *)p; p += f;
-  b.vol = (float *)p; p += f;
+  b.jm1 = (float *)p; p += f;
   b.epsp = (float *)p; p += f;
   b.coh = coh ? (float *)p : nullptr;
 }
@@ -124,9 +125,7 @@ void carve64(void *mem, int dim, bool coh, int64_t cap, D64State &P) {
   P.alive = (int32_t *)p;
 }
 
-size_t buf64_bytes(int dim, bool coh, int64_t cap) {
-  return al256(8 * cap) * nfields64(dim, coh) + al256(4 * cap);
-}
+size_t buf64_bytes(int dim, bool coh, int64_t cap) { return al256(8 * cap) * nfields64(dim, coh) + al256(4 * cap); }
 
 template <typename T>
 MatConst<T> mat_const(const mpm_material &m) {
@@ -151,20 +150,33 @@ void destroy_graphs(mpm_ctx *h) {
     }
 }
 
+int tile_dim(int dim, int k) {
+  if (dim == 3) return k == 0 ? Tile<3>::TX : k == 1 ? Tile<3>::TY : Tile<3>::TZ;
+  return k == 0 ? Tile<2>::TX : k == 1 ? Tile<2>::TY : 1;
+}
+
+BinLaunch bin_launch(mpm_ctx *h, int cur, uint32_t *keys_out, int32_t *perm_out) {
+  BinLaunch B;
+  B.n = h->n;
+  B.ntiles = h->geo.ntiles;
+  B.knew = h->buf[cur].key;
+  B.kold = h->s.keys_sorted;
+  B.old_start = h->s.tile_start[cur];
+  B.new_start = h->s.tile_start[cur ^ 1];
+  B.s = h->s;
+  B.keys_out = keys_out;
+  B.perm_out = perm_out;
+  B.grid = 2 * h->nsm;
+  return B;
+}
+
 // One FP32 step from buf[cur] to buf[cur ^ 1] (enqueue only).
 cudaError_t enqueue_f32_step(mpm_ctx *h, int cur) {
   cudaError_t e;
   cudaEvent_t *ev = h->timing ? h->ev : nullptr;
   if ((e = phase_mark(ev, 0, h->st)) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(h->s.ctr, 0, 8 * sizeof(int32_t), h->st)) != cudaSuccess) return e;
-  if ((e = sort_pairs(h->buf[cur].key, nullptr, h->s.keys_sorted, h->s.perm, h->n, h->key_bits,
-                      h->sort_scratch, h->st)) != cudaSuccess)
-    return e;
+  if ((e = bin_step(bin_launch(h, cur, h->s.keys_sorted, h->s.perm), h->st)) != cudaSuccess) return e;
   if ((e = phase_mark(ev, 1, h->st)) != cudaSuccess) return e;
-  if ((e = tile_bounds(h->s.keys_sorted, h->n, h->geo.ntiles, h->s.tile_start, h->s.active, h->s.ctr,
-                       h->st)) != cudaSuccess)
-    return e;
-  if ((e = phase_mark(ev, 2, h->st)) != cudaSuccess) return e;
   F32Launch L;
   L.dim = h->d.dim;
   L.scheme = h->d.scheme;
@@ -175,7 +187,10 @@ cudaError_t enqueue_f32_step(mpm_ctx *h, int cur) {
   L.A = h->buf[cur];
   L.B = h->buf[cur ^ 1];
   L.s = h->s;
-  L.grid = 2 * h->nsm;
+  L.tile_start = h->s.tile_start[cur ^ 1];
+  L.node_stride[0] = (int64_t)h->d.ncells[0] + 1;
+  L.node_stride[1] = L.node_stride[0] * ((int64_t)h->d.ncells[1] + 1);
+  L.grid = 4 * h->nsm;
   L.ev = ev;
   return f32_step(L, h->st);
 }
@@ -190,7 +205,7 @@ mpm_status device_status(mpm_ctx *h) {
   int32_t st = 0;
   cudaError_t e;
   if (h->d.precision == MPM_FP32_MIXED)
-    e = cudaMemcpyAsync(&st, h->s.ctr + 8, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st);
+    e = cudaMemcpyAsync(&st, h->s.ctr + C_STATUS, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st);
   else
     e = cudaMemcpyAsync(&st, h->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
@@ -199,6 +214,17 @@ mpm_status device_status(mpm_ctx *h) {
   if (st & ST_LEFT_MESH) return fail(h, MPM_ERR_LEFT_MESH, "a particle left the mesh");
   if (st & ST_TIMEOUT) return fail(h, MPM_ERR_TIMEOUT, "a bounded device wait gave up");
   return h->sticky;
+}
+
+void free_ptr(void *&p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+template <typename T>
+void free_t(T *&p) {
+  if (p) cudaFree((void *)p);
+  p = nullptr;
 }
 
 }  // namespace
@@ -219,9 +245,13 @@ mpm_status mpm_create_mesh(const mpm_mesh_desc *desc, mpm_handle *out) {
     if (d.face_bc[f] < MPM_BC_FREE || d.face_bc[f] > MPM_BC_FRICTION) return MPM_ERR_ARG;
     if (d.face_bc[f] == MPM_BC_FRICTION && !(d.face_mu[f] >= 0)) return MPM_ERR_ARG;
   }
+  int64_t nn = 1;
+  for (int k = 0; k < d.dim; ++k) nn *= (int64_t)d.ncells[k] + 1;
+  if (nn >= ((int64_t)1 << 34)) return MPM_ERR_ARG;
   mpm_ctx *h = new mpm_ctx();
   h->d = d;
   if (d.dim == 2) h->d.ncells[2] = 1;
+  h->nnodes = nn;
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -241,16 +271,14 @@ mpm_status mpm_create_mesh(const mpm_mesh_desc *desc, mpm_handle *out) {
   if (d.precision == MPM_FP32_MIXED && e == cudaSuccess) {
     Geo &g = h->geo;
     memset(&g, 0, sizeof(g));
-    const int T[3] = {d.dim == 3 ? Tile<3>::TX : Tile<2>::TX, d.dim == 3 ? Tile<3>::TY : Tile<2>::TY,
-                      d.dim == 3 ? Tile<3>::TZ : 1};
     int64_t nt = 1;
     for (int k = 0; k < 3; ++k) {
       g.nc[k] = h->d.ncells[k];
-      g.nt[k] = (g.nc[k] + T[k] - 1) / T[k];
+      g.nt[k] = (g.nc[k] + tile_dim(d.dim, k) - 1) / tile_dim(d.dim, k);
       nt *= g.nt[k];
     }
-    if (nt * CELLS_PER_TILE >= (int64_t)1 << 31) {
-      delete h;
+    if ((nt + 1) * CELLS_PER_TILE >= (int64_t)1 << 31) {
+      mpm_destroy(h);
       return MPM_ERR_ARG;
     }
     g.ntiles = (int)nt;
@@ -262,6 +290,7 @@ mpm_status mpm_create_mesh(const mpm_mesh_desc *desc, mpm_handle *out) {
     g.inv_h = (float)(1.0 / d.h);
     g.dt = (float)d.dt;
     g.mass_tol = (float)d.mass_tol;
+    g.inv_rho = 1.f;
     for (int k = 0; k < 3; ++k) g.g[k] = (float)d.gravity[k];
     for (int f = 0; f < 6; ++f) {
       g.bc[f] = d.face_bc[f];
@@ -270,16 +299,28 @@ mpm_status mpm_create_mesh(const mpm_mesh_desc *desc, mpm_handle *out) {
     const int bn = d.dim == 3 ? box_nodes<3>() : box_nodes<2>();
     const size_t s1 = sizeof(float) * (size_t)nt * bn * (1 + 2 * d.dim);
     const size_t s2 = d.scheme == MPM_USF ? sizeof(float) * (size_t)nt * bn * d.dim : 0;
-    if (e == cudaSuccess) e = cudaMalloc(&h->s.slots1, s1);
-    if (e == cudaSuccess && s2) e = cudaMalloc(&h->s.slots2, s2);
-    if (e == cudaSuccess) e = cudaMalloc(&h->s.tile_start, sizeof(int32_t) * (nt + 2));
-    if (e == cudaSuccess) e = cudaMalloc(&h->s.active, sizeof(int32_t) * nt);
-    if (e == cudaSuccess) e = cudaMalloc(&h->s.ctr, sizeof(int32_t) * 16);
-    if (e == cudaSuccess) e = cudaMemset(h->s.ctr, 0, sizeof(int32_t) * 16);
+    StepBufs &S = h->s;
+    const size_t ti = sizeof(int32_t) * (nt + 2);
+    if (e == cudaSuccess) e = cudaMalloc(&S.slots1, s1);
+    if (e == cudaSuccess && s2) e = cudaMalloc(&S.slots2, s2);
+    for (int p = 0; p < 2 && e == cudaSuccess; ++p) e = cudaMalloc(&S.tile_start[p], ti);
+    if (e == cudaSuccess) e = cudaMalloc(&S.in_cnt, ti);
+    if (e == cudaSuccess) e = cudaMalloc(&S.out_cnt, ti);
+    if (e == cudaSuccess) e = cudaMalloc(&S.bucket_start, ti);
+    if (e == cudaSuccess) e = cudaMalloc(&S.bucket_fill, ti);
+    if (e == cudaSuccess) e = cudaMalloc(&S.active, ti);
+    if (e == cudaSuccess) e = cudaMalloc(&S.ctr, sizeof(int32_t) * C_NCTR);
+    for (int p = 0; p < 2 && e == cudaSuccess; ++p) e = cudaMemset(S.tile_start[p], 0, ti);
+    if (e == cudaSuccess) e = cudaMemset(S.in_cnt, 0, ti);
+    if (e == cudaSuccess) e = cudaMemset(S.out_cnt, 0, ti);
+    if (e == cudaSuccess) e = cudaMemset(S.bucket_fill, 0, ti);
+    if (e == cudaSuccess) e = cudaMemset(S.ctr, 0, sizeof(int32_t) * C_NCTR);
+    for (int k = 0; k < d.dim && e == cudaSuccess; ++k) {
+      e = cudaMalloc(&S.node_v[k], sizeof(float) * nn);
+      if (e == cudaSuccess) e = cudaMalloc(&S.node_a[k], sizeof(float) * nn);
+    }
     if (e == cudaSuccess) e = f32_prepare(d.dim);
   } else if (e == cudaSuccess) {
-    int64_t nn = 1;
-    for (int k = 0; k < d.dim; ++k) nn *= (int64_t)d.ncells[k] + 1;
     h->L64.nnodes = nn;
     const size_t f = al256(sizeof(double) * nn);
     e = cudaMalloc(&h->nmem64, f * (1 + 5 * d.dim));
@@ -302,20 +343,21 @@ mpm_status mpm_create_mesh(const mpm_mesh_desc *desc, mpm_handle *out) {
   return MPM_OK;
 }
 
-mpm_status mpm_add_particles(mpm_handle h, int64_t n, const double *pos, const double *vel,
-                             const double *vol, const mpm_material *mat, const double *cohesion,
-                             const double *stress0, int64_t *first_id) {
+mpm_status mpm_add_particles(mpm_handle h, int64_t n, const double *pos, const double *vel, const double *vol,
+                             const mpm_material *mat, const double *cohesion, const double *stress0,
+                             int64_t *first_id) {
   mpm_status s0 = check_handle(h);
   if (s0 != MPM_OK) return s0;
   if (n < 0 || !mat || (n > 0 && (!pos || !vel || !vol))) return fail(h, MPM_ERR_ARG, "add_particles: bad arguments");
-  if (mat->model != MPM_LINEAR_ELASTIC && mat->model != MPM_MOHR_COULOMB) return fail(h, MPM_ERR_ARG, "unknown material model");
+  if (mat->model != MPM_LINEAR_ELASTIC && mat->model != MPM_MOHR_COULOMB)
+    return fail(h, MPM_ERR_ARG, "unknown material model");
   if (!(mat->E > 0) || !(mat->nu > -1.0 && mat->nu < 0.5) || !(mat->rho > 0))
     return fail(h, MPM_ERR_ARG, "material constants out of range");
   if (h->has_mat && memcmp(&h->mat, mat, sizeof(mpm_material)) != 0)
     return fail(h, MPM_ERR_ARG, "one material per mesh: a different material was passed");
   if (h->n > 0 && (cohesion != nullptr) != h->has_coh)
     return fail(h, MPM_ERR_ARG, "per-particle cohesion must be given for all particles or none");
-  if (h->n + n >= ((int64_t)1 << 31)) return fail(h, MPM_ERR_ARG, "too many particles");
+  if (h->n + n >= ((int64_t)1 << 31) - 1) return fail(h, MPM_ERR_ARG, "too many particles");
   const int D = h->d.dim;
   const mpm_mesh_desc &d = h->d;
   // initial cells (FP64, host): floor((x - origin)/h); reject outside points
@@ -340,7 +382,9 @@ mpm_status mpm_add_particles(mpm_handle h, int64_t n, const double *pos, const d
   const bool coh = cohesion != nullptr;
   const int64_t n0 = h->n, n1 = h->n + n;
   const int ns = D == 3 ? 6 : 4;
-  // host staging in the device layout
+  auto cp = [&](void *dst, const void *src, size_t bytes) -> cudaError_t {
+    return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, h->st) : cudaSuccess;
+  };
   if (h->d.precision == MPM_FP32_MIXED) {
     const int64_t cap = n1;
     void *nm[2] = {nullptr, nullptr};
@@ -348,43 +392,39 @@ mpm_status mpm_add_particles(mpm_handle h, int64_t n, const double *pos, const d
     PBuf nb[2];
     carve32(nm[0], D, coh, cap, nb[0]);
     carve32(nm[1], D, coh, cap, nb[1]);
+    // nb[1] gathers old + new particles unsorted; nb[0] receives them binned
     const PBuf &ob = h->buf[h->cur];
-    // copy existing particles field by field
-    auto cp = [&](void *dst, const void *src, size_t bytes) -> cudaError_t {
-      return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, h->st) : cudaSuccess;
-    };
     if (n0 > 0) {
       const size_t b4 = 4 * n0;
-      CK(cp(nb[0].key, ob.key, b4), "copy");
-      CK(cp(nb[0].id, ob.id, b4), "copy");
+      CK(cp(nb[1].key, ob.key, b4), "copy");
+      CK(cp(nb[1].id, ob.id, b4), "copy");
       for (int k = 0; k < D; ++k) {
-        CK(cp(nb[0].off[k], ob.off[k], b4), "copy");
-        CK(cp(nb[0].vel[k], ob.vel[k], b4), "copy");
+        CK(cp(nb[1].off[k], ob.off[k], b4), "copy");
+        CK(cp(nb[1].vel[k], ob.vel[k], b4), "copy");
       }
       for (int i = 0; i < ns; ++i) {
-        CK(cp(nb[0].sig[i], ob.sig[i], b4), "copy");
-        CK(cp(nb[0].eps[i], ob.eps[i], b4), "copy");
+        CK(cp(nb[1].sig[i], ob.sig[i], b4), "copy");
+        CK(cp(nb[1].eps[i], ob.eps[i], b4), "copy");
       }
-      CK(cp(nb[0].mass, ob.mass, b4), "copy");
-      CK(cp(nb[0].vol, ob.vol, b4), "copy");
-      CK(cp(nb[0].epsp, ob.epsp, b4), "copy");
-      if (coh) CK(cp(nb[0].coh, ob.coh, b4), "copy");
+      CK(cp(nb[1].mass, ob.mass, b4), "copy");
+      CK(cp(nb[1].jm1, ob.jm1, b4), "copy");
+      CK(cp(nb[1].epsp, ob.epsp, b4), "copy");
+      if (coh) CK(cp(nb[1].coh, ob.coh, b4), "copy");
     }
-    // new particles
-    const int T[3] = {D == 3 ? Tile<3>::TX : Tile<2>::TX, D == 3 ? Tile<3>::TY : Tile<2>::TY, D == 3 ? Tile<3>::TZ : 1};
     std::vector<uint32_t> key(n);
     std::vector<int32_t> id(n);
     std::vector<float> f((size_t)n);
     for (int64_t p = 0; p < n; ++p) {
       int c[3] = {0, 0, 0};
       for (int k = 0; k < D; ++k) c[k] = cell[p * D + k];
-      const int t = c[0] / T[0] + h->geo.nt[0] * (c[1] / T[1] + h->geo.nt[1] * (c[2] / T[2]));
-      const int l = c[0] % T[0] + T[0] * (c[1] % T[1] + T[1] * (c[2] % T[2]));
+      const int T0 = tile_dim(D, 0), T1 = tile_dim(D, 1), T2 = tile_dim(D, 2);
+      const int t = c[0] / T0 + h->geo.nt[0] * (c[1] / T1 + h->geo.nt[1] * (c[2] / T2));
+      const int l = c[0] % T0 + T0 * (c[1] % T1 + T1 * (c[2] % T2));
       key[p] = (uint32_t)t * CELLS_PER_TILE + (uint32_t)l;
       id[p] = (int32_t)(n0 + p);
     }
-    CK(cudaMemcpyAsync(nb[0].key + n0, key.data(), 4 * n, cudaMemcpyHostToDevice, h->st), "upload");
-    CK(cudaMemcpyAsync(nb[0].id + n0, id.data(), 4 * n, cudaMemcpyHostToDevice, h->st), "upload");
+    CK(cudaMemcpyAsync(nb[1].key + n0, key.data(), 4 * n, cudaMemcpyHostToDevice, h->st), "upload");
+    CK(cudaMemcpyAsync(nb[1].id + n0, id.data(), 4 * n, cudaMemcpyHostToDevice, h->st), "upload");
     auto up = [&](float *dst, auto get) -> cudaError_t {
       for (int64_t p = 0; p < n; ++p) f[p] = get(p);
       cudaError_t e = cudaMemcpyAsync(dst + n0, f.data(), 4 * n, cudaMemcpyHostToDevice, h->st);
@@ -392,42 +432,58 @@ mpm_status mpm_add_particles(mpm_handle h, int64_t n, const double *pos, const d
       return e;
     };
     for (int k = 0; k < D; ++k) {
-      CK(up(nb[0].off[k], [&](int64_t p) {
+      CK(up(nb[1].off[k], [&](int64_t p) {
            float u = (float)off[p * D + k];
            if (u >= 0.5f) u = nextafterf(0.5f, 0.f);
            if (u < -0.5f) u = -0.5f;
            return u;
          }), "upload");
-      CK(up(nb[0].vel[k], [&](int64_t p) { return (float)vel[p * D + k]; }), "upload");
+      CK(up(nb[1].vel[k], [&](int64_t p) { return (float)vel[p * D + k]; }), "upload");
     }
     for (int i = 0; i < ns; ++i) {
-      CK(up(nb[0].sig[i], [&](int64_t p) { return stress0 ? (float)stress0[p * 6 + i] : 0.f; }), "upload");
-      CK(up(nb[0].eps[i], [&](int64_t) { return 0.f; }), "upload");
+      CK(up(nb[1].sig[i], [&](int64_t p) { return stress0 ? (float)stress0[p * 6 + i] : 0.f; }), "upload");
+      CK(up(nb[1].eps[i], [&](int64_t) { return 0.f; }), "upload");
     }
-    CK(up(nb[0].mass, [&](int64_t p) { return (float)(mat->rho * vol[p]); }), "upload");
-    CK(up(nb[0].vol, [&](int64_t p) { return (float)vol[p]; }), "upload");
-    CK(up(nb[0].epsp, [&](int64_t) { return 0.f; }), "upload");
-    if (coh) CK(up(nb[0].coh, [&](int64_t p) { return (float)cohesion[p]; }), "upload");
-    CK(cudaStreamSynchronize(h->st), "upload");
-    for (int b = 0; b < 2; ++b)
-      if (h->bufmem[b]) cudaFree(h->bufmem[b]);
+    CK(up(nb[1].mass, [&](int64_t p) { return (float)(mat->rho * vol[p]); }), "upload");
+    CK(up(nb[1].jm1, [&](int64_t) { return 0.f; }), "upload");
+    CK(up(nb[1].epsp, [&](int64_t) { return 0.f; }), "upload");
+    if (coh) CK(up(nb[1].coh, [&](int64_t p) { return (float)cohesion[p]; }), "upload");
+    // per-particle scratch of the binning
+    StepBufs &S = h->s;
+    free_t(S.keys_sorted);
+    free_t(S.perm);
+    free_t(S.movers);
+    free_t(S.bucket);
+    free_t(S.bucket_sorted);
+    free_t(h->keys2);
+    free_t(h->perm2);
+    free_ptr(h->sort_scratch);
+    CK(cudaMalloc(&S.keys_sorted, 4 * cap), "scratch");
+    CK(cudaMalloc(&S.perm, 4 * cap), "scratch");
+    CK(cudaMalloc(&S.movers, 4 * cap), "scratch");
+    CK(cudaMalloc(&S.bucket, 4 * cap), "scratch");
+    CK(cudaMalloc(&S.bucket_sorted, 4 * cap), "scratch");
+    CK(cudaMalloc(&h->keys2, 4 * cap), "scratch");
+    CK(cudaMalloc(&h->perm2, 4 * cap), "scratch");
+    CK(cudaMalloc(&h->sort_scratch, sort_scratch_bytes(cap)), "scratch");
+    // full stable binning once: sort keys, gather the state in key order
+    CK(sort_pairs(nb[1].key, nullptr, S.keys_sorted, S.perm, n1, h->key_bits, h->sort_scratch, h->st), "binning");
+    CK(permute_state(D, n1, nb[1], nb[0], S.perm, h->st), "binning");
+    CK(tile_bounds(S.keys_sorted, n1, h->geo.ntiles, S.tile_start[0], h->st), "binning");
+    const size_t ti = sizeof(int32_t) * (h->geo.ntiles + 2);
+    CK(cudaMemsetAsync(S.in_cnt, 0, ti, h->st), "binning");
+    CK(cudaMemsetAsync(S.out_cnt, 0, ti, h->st), "binning");
+    CK(cudaMemsetAsync(S.bucket_fill, 0, ti, h->st), "binning");
+    CK(cudaMemsetAsync(S.ctr, 0, sizeof(int32_t) * C_STATUS, h->st), "binning");
+    CK(cudaStreamSynchronize(h->st), "binning");
+    for (int b = 0; b < 2; ++b) free_ptr(h->bufmem[b]);
     h->bufmem[0] = nm[0];
     h->bufmem[1] = nm[1];
     h->buf[0] = nb[0];
     h->buf[1] = nb[1];
     h->cur = 0;
-    // step scratch
-    if (h->s.keys_sorted) cudaFree(h->s.keys_sorted);
-    if (h->s.perm) cudaFree(h->s.perm);
-    if (h->sort_scratch) cudaFree(h->sort_scratch);
-    h->s.keys_sorted = nullptr;
-    h->s.perm = nullptr;
-    h->sort_scratch = nullptr;
-    CK(cudaMalloc(&h->s.keys_sorted, 4 * cap), "scratch");
-    CK(cudaMalloc(&h->s.perm, 4 * cap), "scratch");
-    h->sort_scratch_bytes = sort_scratch_bytes(cap);
-    CK(cudaMalloc(&h->sort_scratch, h->sort_scratch_bytes), "scratch");
     h->cap = cap;
+    h->geo.inv_rho = (float)(1.0 / mat->rho);
   } else {
     const int64_t cap = n1;
     void *nmem = nullptr;
@@ -435,9 +491,6 @@ mpm_status mpm_add_particles(mpm_handle h, int64_t n, const double *pos, const d
     D64State P;
     carve64(nmem, D, coh, cap, P);
     const D64State &O = h->L64.P;
-    auto cp = [&](void *dst, const void *src, size_t bytes) -> cudaError_t {
-      return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, h->st) : cudaSuccess;
-    };
     if (n0 > 0) {
       const size_t b8 = 8 * n0;
       for (int k = 0; k < D; ++k) {
@@ -476,7 +529,7 @@ mpm_status mpm_add_particles(mpm_handle h, int64_t n, const double *pos, const d
     std::vector<int32_t> one((size_t)n, 1);
     CK(cudaMemcpyAsync(P.alive + n0, one.data(), 4 * n, cudaMemcpyHostToDevice, h->st), "upload");
     CK(cudaStreamSynchronize(h->st), "upload");
-    if (h->pmem64) cudaFree(h->pmem64);
+    free_ptr(h->pmem64);
     h->pmem64 = nmem;
     h->L64.P = P;
     h->cap = cap;
@@ -555,8 +608,8 @@ mpm_status mpm_num_particles(mpm_handle h, int64_t *n) {
   return MPM_OK;
 }
 
-mpm_status mpm_read_particles(mpm_handle h, double *pos, double *vel, double *stress, double *strain,
-                              double *vol, double *epsp, int64_t *cell) {
+mpm_status mpm_read_particles(mpm_handle h, double *pos, double *vel, double *stress, double *strain, double *vol,
+                              double *epsp, int64_t *cell) {
   mpm_status s0 = check_handle(h);
   if (s0 != MPM_OK) return s0;
   const int64_t n = h->n;
@@ -566,16 +619,21 @@ mpm_status mpm_read_particles(mpm_handle h, double *pos, double *vel, double *st
     double *tmp = nullptr;
     CK(cudaMallocAsync((void **)&tmp, sizeof(double) * 6 * n, h->st), "read scratch");
     const PBuf &P = h->buf[h->cur];
-    struct Item { void *host; int width; int which; };
-    const Item items[7] = {{pos, D, 0}, {vel, D, 1}, {stress, 6, 2}, {strain, 6, 3}, {vol, 1, 4}, {epsp, 1, 5}, {cell, 1, 6}};
+    struct Item {
+      void *host;
+      int width;
+      int which;
+    };
+    const Item items[7] = {{pos, D, 0},  {vel, D, 1},  {stress, 6, 2}, {strain, 6, 3},
+                           {vol, 1, 4},  {epsp, 1, 5}, {cell, 1, 6}};
     cudaError_t e = cudaSuccess;
     for (const Item &it : items) {
       if (!it.host || e != cudaSuccess) continue;
       double *o[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
       o[it.which] = tmp;
-      e = f32_export(D, n, P, h->geo, h->d.origin, h->d.h, o[0], o[1], o[2], o[3], o[4], o[5], (int64_t *)o[6], h->st);
-      if (e == cudaSuccess)
-        e = cudaMemcpyAsync(it.host, tmp, sizeof(double) * it.width * n, cudaMemcpyDeviceToHost, h->st);
+      e = f32_export(D, n, P, h->geo, h->d.origin, h->d.h, h->mat.rho, o[0], o[1], o[2], o[3], o[4], o[5],
+                     (int64_t *)o[6], h->st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(it.host, tmp, sizeof(double) * it.width * n, cudaMemcpyDeviceToHost, h->st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
     }
     cudaFreeAsync(tmp, h->st);
@@ -591,23 +649,23 @@ mpm_status mpm_read_particles(mpm_handle h, double *pos, double *vel, double *st
       if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
       return e;
     };
+    if (cell)
+      for (int64_t p = 0; p < n; ++p) cell[p] = 0;
     for (int k = 0; k < D; ++k) {
       if (pos || cell) {
         CK(get(P.x[k]), "read");
         if (pos)
           for (int64_t p = 0; p < n; ++p) pos[p * D + k] = col[p];
-        if (cell)
+        if (cell) {
+          int64_t mul = 1;
+          for (int j = 0; j < k; ++j) mul *= h->d.ncells[j];
           for (int64_t p = 0; p < n; ++p) {
-            if (k == 0) cell[p] = 0;
             const double s = (col[p] - h->d.origin[k]) / h->d.h;
-            int64_t c = (int64_t)floor(s);
+            const double c = floor(s);
             if (!alive[p] || !(s >= 0) || c >= h->d.ncells[k]) cell[p] = -1;
-            if (cell[p] >= 0) {
-              int64_t mul = 1;
-              for (int j = 0; j < k; ++j) mul *= h->d.ncells[j];
-              cell[p] += c * mul;
-            }
+            if (cell[p] >= 0) cell[p] += (int64_t)c * mul;
           }
+        }
       }
       if (vel) {
         CK(get(P.v[k]), "read");
@@ -657,16 +715,14 @@ mpm_status mpm_conservation(mpm_handle h, double out[7]) {
     return device_status(h);
   }
   if (h->d.precision == MPM_FP32_MIXED)
-    CK(f32_conservation(h->d.dim, h->n, h->buf[h->cur], h->geo.dead_key, h->d_cons, h->d_cons + 8, h->st), "conservation");
+    CK(f32_conservation(h->d.dim, h->n, h->buf[h->cur], h->geo.dead_key, h->geo.inv_rho, h->d_cons, h->d_cons + 8,
+                        h->st),
+       "conservation");
   else
     CK(d64_conservation(h->L64, h->d_cons, h->d_cons + 8, h->st), "conservation");
   double tmp[8];
   CK(cudaMemcpyAsync(tmp, h->d_cons, sizeof(double) * 7, cudaMemcpyDeviceToHost, h->st), "conservation");
   CK(cudaStreamSynchronize(h->st), "conservation");
-  if (h->d.dim == 2) {
-    // momentum components are (x, y); keep the 3-vector layout
-    tmp[3] = 0.0;
-  }
   for (int i = 0; i < 7; ++i) out[i] = tmp[i];
   return device_status(h);
 }
@@ -675,15 +731,14 @@ mpm_status mpm_read_binning(mpm_handle h, int32_t *key, int32_t *perm, int32_t *
   mpm_status s0 = check_handle(h);
   if (s0 != MPM_OK) return s0;
   if (h->d.precision != MPM_FP32_MIXED) return fail(h, MPM_ERR_STATE, "read_binning: FP32_MIXED handles only");
-  if (tile_dims) {
-    tile_dims[0] = h->d.dim == 3 ? Tile<3>::TX : Tile<2>::TX;
-    tile_dims[1] = h->d.dim == 3 ? Tile<3>::TY : Tile<2>::TY;
-    tile_dims[2] = h->d.dim == 3 ? Tile<3>::TZ : 1;
-  }
+  if (tile_dims)
+    for (int k = 0; k < 3; ++k) tile_dims[k] = tile_dim(h->d.dim, k);
   if (h->n == 0) return device_status(h);
-  CK(sort_pairs(h->buf[h->cur].key, nullptr, h->s.keys_sorted, h->s.perm, h->n, h->key_bits, h->sort_scratch, h->st), "binning");
+  // the production binning of the stored particles, written to scratch so
+  // that the next step's binning (which reads the previous binning) is intact
+  CK(bin_step(bin_launch(h, h->cur, h->keys2, h->perm2), h->st), "binning");
   if (key) CK(cudaMemcpyAsync(key, h->buf[h->cur].key, 4 * h->n, cudaMemcpyDeviceToHost, h->st), "binning");
-  if (perm) CK(cudaMemcpyAsync(perm, h->s.perm, 4 * h->n, cudaMemcpyDeviceToHost, h->st), "binning");
+  if (perm) CK(cudaMemcpyAsync(perm, h->perm2, 4 * h->n, cudaMemcpyDeviceToHost, h->st), "binning");
   CK(cudaStreamSynchronize(h->st), "binning");
   return device_status(h);
 }
@@ -708,7 +763,7 @@ mpm_status mpm_phase_times(mpm_handle h, float *ms, int32_t *nphase) {
   if (s0 != MPM_OK) return s0;
   if (!ms || !nphase) return fail(h, MPM_ERR_ARG, "phase_times: null output");
   if (!h->timing || !h->timed_step) return fail(h, MPM_ERR_STATE, "phase_times: no timed step");
-  const int np = h->d.scheme == MPM_USL ? 4 : 6;
+  const int np = h->d.scheme == MPM_USL ? 4 : 7;
   CK(cudaEventSynchronize(h->ev[np]), "phase timing");
   for (int i = 0; i < np; ++i) CK(cudaEventElapsedTime(&ms[i], h->ev[i], h->ev[i + 1]), "phase timing");
   *nphase = np;
@@ -724,9 +779,11 @@ mpm_status mpm_destroy(mpm_handle h) {
   if (!h) return MPM_OK;
   if (h->st) cudaStreamSynchronize(h->st);
   destroy_graphs(h);
-  void *ptrs[] = {h->bufmem[0], h->bufmem[1], h->s.keys_sorted, h->s.perm, h->s.tile_start, h->s.active,
-                  h->s.ctr, h->s.slots1, h->s.slots2, h->sort_scratch, h->pmem64, h->nmem64, h->d_status,
-                  h->d_cons};
+  StepBufs &S = h->s;
+  void *ptrs[] = {h->bufmem[0], h->bufmem[1], S.keys_sorted, S.perm, S.tile_start[0], S.tile_start[1], S.in_cnt,
+                  S.out_cnt, S.bucket_start, S.bucket_fill, S.movers, S.bucket, S.bucket_sorted, S.active, S.ctr,
+                  S.slots1, S.slots2, S.node_v[0], S.node_v[1], S.node_v[2], S.node_a[0], S.node_a[1], S.node_a[2],
+                  h->keys2, h->perm2, h->sort_scratch, h->pmem64, h->nmem64, h->d_status, h->d_cons};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (int i = 0; i <= MPM_MAX_PHASES; ++i)
@@ -771,7 +828,8 @@ mpm_status mpm_material_update(const mpm_material *mat, int32_t precision, int64
     e = cudaMemcpyAsync(ds, sig, nb * 6, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dd, deps, nb * 6, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && cohesion) e = cudaMemcpyAsync(dc, cohesion, nb, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = material_update_f64(mat_const<double>(*mat), n, ds, dd, cohesion ? dc : nullptr, dout, dep, st);
+    if (e == cudaSuccess)
+      e = material_update_f64(mat_const<double>(*mat), n, ds, dd, cohesion ? dc : nullptr, dout, dep, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(sig_out, dout, nb * 6, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess && depsp_out) e = cudaMemcpyAsync(depsp_out, dep, nb, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -793,7 +851,8 @@ mpm_status mpm_material_update(const mpm_material *mat, int32_t precision, int64
     if (e == cudaSuccess) e = cudaMemcpyAsync(dd, hd.data(), nb * 6, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && cohesion) e = cudaMemcpyAsync(dc, hc.data(), nb, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
-      e = material_update_f32(mat_const<float>(*mat), mat_const<double>(*mat), n, ds, dd, cohesion ? dc : nullptr, dout, dep, st);
+      e = material_update_f32(mat_const<float>(*mat), mat_const<double>(*mat), n, ds, dd, cohesion ? dc : nullptr,
+                              dout, dep, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(ho.data(), dout, nb * 6, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(he.data(), dep, nb, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);

@@ -338,15 +338,18 @@ __device__ __forceinline__ void elastic_trial(const MatConst<T> &m, const T sig[
   for (int i = 3; i < 6; ++i) st[i] = sig[i] + G2 * de[i];
 }
 
-// Distance of the trial principal stresses from the apex within which the
-// FP32 path redoes the return in FP64: 1e-3 (|p| + c cot(phi) + 1 kPa).
+// Distance of the trial stress from the apex c cot(phi) within which the
+// FP32 path redoes the return in FP64: 1e-3 (|p| + c cot(phi)).  Inside it the
+// principal stresses minus the apex pressure lose more than three of FP32's
+// seven digits to cancellation.  The band is relative only: with c = 0 the
+// apex is the zero stress and FP32 loses nothing near it.
 __device__ __forceinline__ bool near_apex(const float st[6], const MatConst<float> &m, float c) {
   if (!(m.sphi > 0.f)) return false;
   const float pa = c * m.cphi / m.sphi;
   const float p = (st[0] + st[1] + st[2]) * (1.f / 3.f);
   const float d0 = st[0] - pa, d1 = st[1] - pa, d2 = st[2] - pa;
   const float dist2 = d0 * d0 + d1 * d1 + d2 * d2 + 2.f * (st[3] * st[3] + st[4] * st[4] + st[5] * st[5]);
-  const float band = 1e-3f * (fabsf(p) + pa + 1e3f);
+  const float band = 1e-3f * (fabsf(p) + pa);
   return dist2 < band * band;
 }
 

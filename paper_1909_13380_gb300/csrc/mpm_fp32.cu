@@ -1,27 +1,28 @@
-// mpm_fp32.cu -- FP32 mixed-precision explicit MPM step on tiles of 256 cells.
+// mpm_fp32.cu -- FP32 mixed-precision explicit MPM step.
 //
 // Paper (arXiv 1909.13380): INTRODUCTION (particle <-> node transfers with the
 // same shape functions, nodal values reset each step), CODE OVERVIEW (Node,
-// Cell with linear quad/hex, Material, USF/USL), DATA STRUCTURES (nodal
-// updates aggregate the particles of all cells around a node and must be
-// protected against races -- the paper uses a mutex per node),
-// ISOPARAMETRIC MESH (nodal velocity and frictional conditions).
+// Cell with linear quad/hex, Material, USF/USL), DATA STRUCTURES (a node
+// aggregates the particles of all cells around it and must be protected
+// against races -- the paper uses a mutex per node), ISOPARAMETRIC MESH
+// (nodal velocity and frictional conditions).
 //
-// GPU design (replaces the per-node mutex): particles are binned by a
-// tile-major cell key (mpm_sort.cu).  One CTA owns one tile:
-//   p2g_tile   loads the tile's particles in key order (coalesced), evaluates
-//              every particle's corner contributions once, reduces them per
-//              cell in a fixed sequential order through a shared-memory
-//              staging buffer (compensated sums), sums cells into the tile's
-//              node box, and writes that box to the tile's own slot -- no
-//              atomics, no zeroing pass, bit-reproducible.
-//   g2p_tile   rebuilds the final node values of its box by summing the slots
-//              of the (at most 2^D) tiles that share each node, in ascending
-//              tile order (so every tile sees bit-identical node values),
-//              applies the boundary conditions, then streams its particles
-//              once: FLIP velocity, advection, strain, stress, volume and
-//              relocation into the new cell, writing the new state in key
-//              order so the next step's reads stay coalesced.
+// GPU design (replaces the per-node mutex), after the binning of mpm_bin.cu:
+//   p2g_tile   one CTA per 4x4x4 (8x8) cell tile: loads the tile's particles
+//              in binning order (coalesced), evaluates each particle's corner
+//              contributions once, sums them per cell in a fixed sequential
+//              order through a shared-memory staging buffer (compensated
+//              sums), sums cells into the tile's node box and writes the box
+//              to the tile's own slot -- no atomics, bit-reproducible;
+//   node_tile  one CTA per tile: final nodal values of the box, summing the
+//              slots of the (at most 2^D) tiles that share each node in
+//              ascending tile order, then v = P/m, a = f/m + g, v' = v + a dt
+//              and the boundary conditions; written to dense node arrays
+//              (nodes shared by boxes get bit-identical values);
+//   g2p        one thread per particle in binning order: FLIP velocity,
+//              advection, strain, stress, volume and relocation into the new
+//              cell, written in binning order so the next step reads
+//              contiguously.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -30,38 +31,30 @@
 namespace mpm {
 namespace {
 
-constexpr int NT = 256;  // threads per tile CTA
-constexpr int NWARP = NT / 32;
+constexpr int P2G_T = 128;  // threads per P2G CTA
+constexpr int P2G_W = P2G_T / 32;
+constexpr int NODE_T = 128;
+constexpr int G2P_T = 256;
 
-template <int D>
-struct P2GArgs {
+struct TileArgs {
   Geo geo;
-  PBuf A;              // particle storage (read through perm)
-  PBuf B;              // FORCE mode: stress/volume already updated, key order
+  PBuf A;  // particle storage of the step (read through perm)
+  PBuf B;  // output storage (binning order)
   const uint32_t *keys;
   const int32_t *perm;
   const int32_t *tile_start;
   const int32_t *active;
   int32_t *ctr;
   int work_slot;
-  float *slots;
-};
-
-template <int D>
-struct G2PArgs {
-  Geo geo;
+  const float *slots1;
+  const float *slots2;
+  float *slots_out;
+  int nch1;
+  float *nv[3];
+  float *na[3];
+  int64_t ns0, ns1;  // node strides
   MatConst<float> mat;
   MatConst<double> matd;
-  PBuf A, B;
-  const uint32_t *keys;
-  const int32_t *perm;
-  const int32_t *tile_start;
-  const int32_t *active;
-  int32_t *ctr;
-  int work_slot;
-  const float *slots1;  // m, P (and f_int in USL)
-  const float *slots2;  // f_int (USF advect)
-  int nch1;
 };
 
 __device__ __forceinline__ int next_tile(int32_t *ctr, int slot) {
@@ -74,11 +67,12 @@ __device__ __forceinline__ int next_tile(int32_t *ctr, int slot) {
 }
 
 // Start of warp w's share of [s, e): the first cell boundary at or after
-// s + w (e - s) / NWARP, so that no cell is split between warps.
+// s + w (e - s) / NW, so that no cell is split between warps.
+template <int NW>
 __device__ __forceinline__ int warp_split(const uint32_t *keys, int s, int e, int w) {
   if (w <= 0) return s;
-  if (w >= NWARP) return e;
-  int p = s + (int)(((int64_t)(e - s) * w) / NWARP);
+  if (w >= NW) return e;
+  int p = s + (int)(((int64_t)(e - s) * w) / NW);
   if (p <= s) p = s + 1;
   const int lane = threadIdx.x & 31;
   for (;;) {
@@ -91,7 +85,6 @@ __device__ __forceinline__ int warp_split(const uint32_t *keys, int s, int e, in
   }
 }
 
-template <int D>
 __device__ __forceinline__ void tile_coords(const Geo &g, int t, int tc[3]) {
   tc[0] = t % g.nt[0];
   tc[1] = (t / g.nt[0]) % g.nt[1];
@@ -106,36 +99,70 @@ __device__ __forceinline__ void local_coords(uint32_t key, int lc[3]) {
   lc[2] = l / (Tile<D>::TX * Tile<D>::TY);
 }
 
+// Corner weights of the linear element at natural coordinates xi = 2u:
+// w0[k] = (1 - xi_k)/2, w1[k] = (1 + xi_k)/2.  N_a and its gradient are
+// products of these (shape_fn in mpm_device.cuh writes them out in full).
+template <int D>
+__device__ __forceinline__ void corner_weights(const float u[D], float w0[D], float w1[D]) {
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    w0[k] = 0.5f - u[k];
+    w1[k] = 0.5f + u[k];
+  }
+}
+
+template <int D>
+__device__ __forceinline__ void corner_shape(int a, const float w0[D], const float w1[D], float inv_h, float &N,
+                                             float G[D]) {
+  float w[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) w[k] = ((a >> k) & 1) ? w1[k] : w0[k];
+  N = w[0];
+#pragma unroll
+  for (int k = 1; k < D; ++k) N *= w[k];
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    float g = ((a >> k) & 1) ? inv_h : -inv_h;
+#pragma unroll
+    for (int j = 0; j < D; ++j)
+      if (j != k) g *= w[j];
+    G[k] = g;
+  }
+}
+
 // ---------------------------------------------------------------------------
-// P2G: contributions of a particle to its cell's 2^D nodes.
-// value index v = corner * NCH + channel;  channels: USL (m, P_k, f_k),
-// MOM (m, P_k), FORCE (f_k) with f_k = -V sum_j sig_kj dN/dx_j.
+// P2G: value index v = corner * NCH + channel; channels USL (m, P_k, f_k),
+// MOM (m, P_k), FORCE (f_k), f_k = -V sum_j sig_kj dN/dx_j.
 // ---------------------------------------------------------------------------
 template <int D, int MODE>
-__global__ void __launch_bounds__(NT, 2) p2g_tile(P2GArgs<D> A) {
+constexpr size_t p2g_smem() {
+  return sizeof(float) * (CELLS_PER_TILE * (1 << D) * p2g_channels<D, MODE>() + P2G_W * 32 * 33);
+}
+
+template <int D, int MODE>
+__global__ void __launch_bounds__(P2G_T, 4) p2g_tile(TileArgs A) {
   constexpr int NC = 1 << D;
   constexpr int NCH = p2g_channels<D, MODE>();
   constexpr int NV = NC * NCH;
   constexpr int NPASS = (NV + 31) / 32;
   constexpr int BN = box_nodes<D>();
-  constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY;
+  constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ;
   constexpr bool HAS_M = MODE != P2G_FORCE;
   constexpr bool HAS_F = MODE != P2G_MOM;
   extern __shared__ float sm[];
-  float *cellP = sm;                               // [256][NV]
-  float *stage = sm + CELLS_PER_TILE * NV;         // [NWARP][32][33]
+  float *cellP = sm;  // [64][NV]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float *wst = stage + warp * 32 * 33;
+  float *wst = sm + CELLS_PER_TILE * NV + warp * 32 * 33;  // [32][33]
   const Geo &g = A.geo;
 
   for (;;) {
     const int wi = next_tile(A.ctr, A.work_slot);
-    if (wi >= A.ctr[0]) break;
+    if (wi >= A.ctr[C_ACTIVE]) break;
     const int t = A.active[wi];
     const int s = A.tile_start[t], e = A.tile_start[t + 1];
-    for (int i = threadIdx.x; i < CELLS_PER_TILE * NV; i += NT) cellP[i] = 0.f;
-    const int ws = warp_split(A.keys, s, e, warp);
-    const int we = warp_split(A.keys, s, e, warp + 1);
+    for (int i = threadIdx.x; i < CELLS_PER_TILE * NV; i += P2G_T) cellP[i] = 0.f;
+    const int ws = warp_split<P2G_W>(A.keys, s, e, warp);
+    const int we = warp_split<P2G_W>(A.keys, s, e, warp + 1);
     __syncthreads();
 
     for (int b0 = ws; b0 < we; b0 += 32) {
@@ -143,25 +170,32 @@ __global__ void __launch_bounds__(NT, 2) p2g_tile(P2GArgs<D> A) {
       const bool valid = q < we;
       const int nb = min(32, we - b0);
       int lc = CELLS_PER_TILE + lane;
-      float N[NC], G[NC][D];
+      float w0[D], w1[D];
       float mm = 0.f, mv[D], sv[D][D];
-      if (valid) {
-        const uint32_t key = A.keys[q];
-        lc = key & (CELLS_PER_TILE - 1);
-        const int j = A.perm[q];
-        float xi[D];
 #pragma unroll
-        for (int k = 0; k < D; ++k) xi[k] = 2.f * A.A.off[k][j];
-        shape_fn<D, float>(xi, g.inv_h, N, G);
+      for (int k = 0; k < D; ++k) {
+        w0[k] = w1[k] = mv[k] = 0.f;
+#pragma unroll
+        for (int j = 0; j < D; ++j) sv[k][j] = 0.f;
+      }
+      if (valid) {
+        lc = A.keys[q] & (CELLS_PER_TILE - 1);
+        const int j = A.perm[q];
+        float u[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) u[k] = A.A.off[k][j];
+        corner_weights<D>(u, w0, w1);
+        mm = A.A.mass[j];
         if (HAS_M) {
-          mm = A.A.mass[j];
 #pragma unroll
           for (int k = 0; k < D; ++k) mv[k] = mm * A.A.vel[k][j];
         }
         if (HAS_F) {
+          // FORCE (USF) reads the stress updated earlier this step, stored in
+          // binning order; USL reads the stress at the start of the step
           const PBuf &S = (MODE == P2G_FORCE) ? A.B : A.A;
           const int js = (MODE == P2G_FORCE) ? q : j;
-          const float nV = -S.vol[js];
+          const float nV = -mm * g.inv_rho * (1.f + S.jm1[js]);
           if (D == 3) {
             const float sxx = S.sig[0][js], syy = S.sig[1][js], szz = S.sig[2][js];
             const float sxy = S.sig[3][js], syz = S.sig[4][js], sxz = S.sig[5][js];
@@ -187,27 +221,29 @@ __global__ void __launch_bounds__(NT, 2) p2g_tile(P2GArgs<D> A) {
 
 #pragma unroll
       for (int pass = 0; pass < NPASS; ++pass) {
-        // stage this pass's 32 values of my particle: wst[v][lane]
+        // stage this pass's values of my particle: wst[v][lane]
 #pragma unroll
-        for (int vv = 0; vv < 32; ++vv) {
-          const int v = pass * 32 + vv;
-          if (v < NV) {
-            const int a = v / NCH, ch = v % NCH;
-            float val = 0.f;
-            if (valid) {
-              if (HAS_M && ch == 0) {
-                val = mm * N[a];
-              } else if (HAS_M && ch <= D) {
-                val = mv[ch - 1] * N[a];
-              } else {
-                const int k = HAS_M ? ch - 1 - D : ch;
-                float f = 0.f;
+        for (int a = 0; a < NC; ++a) {
+          if (a * NCH + NCH <= pass * 32 || a * NCH >= pass * 32 + 32) continue;
+          float N, G[D];
+          corner_shape<D>(a, w0, w1, g.inv_h, N, G);
 #pragma unroll
-                for (int jj = 0; jj < D; ++jj) f += sv[k][jj] * G[a][jj];
-                val = f;
-              }
+          for (int ch = 0; ch < NCH; ++ch) {
+            const int v = a * NCH + ch;
+            if (v < pass * 32 || v >= pass * 32 + 32) continue;
+            float val;
+            if (HAS_M && ch == 0) {
+              val = mm * N;
+            } else if (HAS_M && ch <= D) {
+              val = mv[ch - 1] * N;
+            } else {
+              const int k = HAS_M ? ch - 1 - D : ch;
+              float f = 0.f;
+#pragma unroll
+              for (int jj = 0; jj < D; ++jj) f += sv[k][jj] * G[jj];
+              val = f;
             }
-            wst[vv * 33 + lane] = val;
+            wst[(v - pass * 32) * 33 + lane] = val;
           }
         }
         __syncwarp();
@@ -229,7 +265,7 @@ __global__ void __launch_bounds__(NT, 2) p2g_tile(P2GArgs<D> A) {
     __syncthreads();
 
     // cells -> node box (ascending local cell order), compensated; -> slot
-    for (int b = threadIdx.x; b < BN; b += NT) {
+    for (int b = threadIdx.x; b < BN; b += P2G_T) {
       const int bx = b % (TX + 1);
       const int by = (b / (TX + 1)) % (TY + 1);
       const int bz = D == 3 ? b / ((TX + 1) * (TY + 1)) : 0;
@@ -243,21 +279,21 @@ __global__ void __launch_bounds__(NT, 2) p2g_tile(P2GArgs<D> A) {
 #pragma unroll
           for (int dx = 1; dx >= 0; --dx) {
             const int cx = bx - dx, cy = by - dy, cz = bz - dz;
-            if (cx < 0 || cx >= TX || cy < 0 || cy >= TY || cz < 0 || cz >= Tile<D>::TZ) continue;
+            if (cx < 0 || cx >= TX || cy < 0 || cy >= TY || cz < 0 || cz >= TZ) continue;
             const int cl = cx + TX * (cy + TY * cz);
             const int a = dx + 2 * dy + 4 * dz;
 #pragma unroll
             for (int ch = 0; ch < NCH; ++ch) acc[ch].add(cellP[cl * NV + a * NCH + ch]);
           }
 #pragma unroll
-      for (int ch = 0; ch < NCH; ++ch) A.slots[((int64_t)t * NCH + ch) * BN + b] = acc[ch].value();
+      for (int ch = 0; ch < NCH; ++ch) A.slots_out[((int64_t)t * NCH + ch) * BN + b] = acc[ch].value();
     }
     __syncthreads();
   }
 }
 
 // ---------------------------------------------------------------------------
-// G2P
+// Nodes
 // ---------------------------------------------------------------------------
 template <int D>
 __device__ __forceinline__ int node_faces(const Geo &g, const int I[3]) {
@@ -270,12 +306,11 @@ __device__ __forceinline__ int node_faces(const Geo &g, const int I[3]) {
   return m;
 }
 
-// Sum channel `ch` of node I over the slots of every active tile whose box
-// holds it, in ascending tile order.
-template <int D>
-__device__ __forceinline__ void gather_node(const Geo &g, const int32_t *tile_start, const float *slots,
-                                            int nch, const int I[3], const int tc[3], float *out,
-                                            int nout) {
+// Sum channels of node I over the slots of every active tile whose box holds
+// it, in ascending tile order (every tile computes a shared node the same way).
+template <int D, int NOUT>
+__device__ __forceinline__ void gather_node(const Geo &g, const int32_t *tile_start, const float *slots, int nch,
+                                            const int I[3], const int tc[3], float out[NOUT]) {
   constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ;
   constexpr int BN = box_nodes<D>();
   const int T[3] = {TX, TY, TZ};
@@ -289,265 +324,284 @@ __device__ __forceinline__ void gather_node(const Geo &g, const int32_t *tile_st
       if (l == T[k] && tc[k] + 1 < g.nt[k]) hi[k] = tc[k] + 1;
     }
   }
-  TwoAcc<float> acc[2 * 3 + 1];
-  for (int c = 0; c < nout; ++c) acc[c].init();
+  TwoAcc<float> acc[NOUT];
+#pragma unroll
+  for (int c = 0; c < NOUT; ++c) acc[c].init();
   for (int z = lo[2]; z <= hi[2]; ++z)
     for (int y = lo[1]; y <= hi[1]; ++y)
       for (int x = lo[0]; x <= hi[0]; ++x) {
         const int t2 = x + g.nt[0] * (y + g.nt[1] * z);
         if (tile_start[t2 + 1] <= tile_start[t2]) continue;
         const int bx = I[0] - x * TX, by = I[1] - y * TY, bz = D == 3 ? I[2] - z * TZ : 0;
-        if (bx < 0 || bx > TX || by < 0 || by > TY || bz < 0 || bz > (D == 3 ? TZ : 0)) continue;
         const int bl = bx + (TX + 1) * (by + (TY + 1) * bz);
-        for (int c = 0; c < nout; ++c) acc[c].add(slots[((int64_t)t2 * nch + c) * BN + bl]);
+#pragma unroll
+        for (int c = 0; c < NOUT; ++c) acc[c].add(slots[((int64_t)t2 * nch + c) * BN + bl]);
       }
-  for (int c = 0; c < nout; ++c) out[c] = acc[c].value();
+#pragma unroll
+  for (int c = 0; c < NOUT; ++c) out[c] = acc[c].value();
 }
 
-template <int D, int GMODE>
-__global__ void __launch_bounds__(NT, 2) g2p_tile(G2PArgs<D> A) {
-  constexpr int NC = 1 << D;
+template <int D, int NMODE>
+__global__ void __launch_bounds__(NODE_T) node_tile(TileArgs A) {
   constexpr int BN = box_nodes<D>();
   constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ;
-  constexpr int NS = nstress<D>();
-  __shared__ float sV[BN][D];   // v' (USL, USF advect) or v (USF stress)
-  __shared__ float sA[BN][D];   // a
   const Geo &g = A.geo;
-
   for (;;) {
     const int wi = next_tile(A.ctr, A.work_slot);
-    if (wi >= A.ctr[0]) break;
+    if (wi >= A.ctr[C_ACTIVE]) break;
     const int t = A.active[wi];
-    const int s = A.tile_start[t], e = A.tile_start[t + 1];
     int tc[3];
-    tile_coords<D>(g, t, tc);
-
-    // node box: final nodal values and boundary conditions
-    for (int b = threadIdx.x; b < BN; b += NT) {
+    tile_coords(g, t, tc);
+    for (int b = threadIdx.x; b < BN; b += NODE_T) {
       const int bx = b % (TX + 1);
       const int by = (b / (TX + 1)) % (TY + 1);
       const int bz = D == 3 ? b / ((TX + 1) * (TY + 1)) : 0;
       const int I[3] = {tc[0] * TX + bx, tc[1] * TY + by, D == 3 ? tc[2] * TZ + bz : 0};
-      float v[D], a[D], vn[D];
-#pragma unroll
-      for (int k = 0; k < D; ++k) v[k] = a[k] = vn[k] = 0.f;
       bool inside = true;
 #pragma unroll
       for (int k = 0; k < D; ++k) inside = inside && I[k] <= g.nc[k];
-      if (inside) {
-        float ch1[1 + 2 * D];
-        const int n1 = GMODE == G2P_USL ? 1 + 2 * D : 1 + D;
-        gather_node<D>(g, A.tile_start, A.slots1, A.nch1, I, tc, ch1, n1);
-        const float m = ch1[0];
-        const int faces = node_faces<D>(g, I);
-        if (m > g.mass_tol) {
-          const float inv_m = 1.f / m;
+      if (!inside) continue;
+      float v[D], a[D], vn[D];
 #pragma unroll
-          for (int k = 0; k < D; ++k) v[k] = ch1[1 + k] * inv_m;
-          if (GMODE == G2P_USL) {
+      for (int k = 0; k < D; ++k) v[k] = a[k] = vn[k] = 0.f;
+      float c1[1 + 2 * D];
+      if (NMODE == NODE_USL)
+        gather_node<D, 1 + 2 * D>(g, A.tile_start, A.slots1, A.nch1, I, tc, c1);
+      else
+        gather_node<D, 1 + D>(g, A.tile_start, A.slots1, A.nch1, I, tc, c1);
+      const float m = c1[0];
+      const int faces = node_faces<D>(g, I);
+      if (m > g.mass_tol) {
+        const float inv_m = 1.f / m;
 #pragma unroll
-            for (int k = 0; k < D; ++k) {
-              a[k] = ch1[1 + D + k] * inv_m + g.g[k];
-              vn[k] = v[k] + a[k] * g.dt;
-            }
-            bc_full<D, float>(faces, g.bc, g.mu, g.dt, v, a, vn);
-          } else if (GMODE == G2P_USF_STRESS) {
-            bc_velocity<D, float>(faces, g.bc, v);
-          } else {
-            float f[3];
-            gather_node<D>(g, A.tile_start, A.slots2, D, I, tc, f, D);
-            bc_velocity<D, float>(faces, g.bc, v);
+        for (int k = 0; k < D; ++k) v[k] = c1[1 + k] * inv_m;
+        if (NMODE == NODE_USL) {
 #pragma unroll
-            for (int k = 0; k < D; ++k) {
-              a[k] = f[k] * inv_m + g.g[k];
-              vn[k] = v[k] + a[k] * g.dt;
-            }
-            bc_full<D, float>(faces, g.bc, g.mu, g.dt, v, a, vn);
+          for (int k = 0; k < D; ++k) {
+            a[k] = c1[1 + D + k] * inv_m + g.g[k];
+            vn[k] = v[k] + a[k] * g.dt;
           }
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < D; ++k) {
-        sV[b][k] = GMODE == G2P_USF_STRESS ? v[k] : vn[k];
-        sA[b][k] = a[k];
-      }
-    }
-    __syncthreads();
-
-    for (int q = s + threadIdx.x; q < e; q += NT) {
-      const uint32_t key = A.keys[q];
-      const int j = A.perm[q];
-      int lc[3];
-      local_coords<D>(key, lc);
-      float u[D], xi[D];
-#pragma unroll
-      for (int k = 0; k < D; ++k) {
-        u[k] = A.A.off[k][j];
-        xi[k] = 2.f * u[k];
-      }
-      float N[NC], G[NC][D];
-      shape_fn<D, float>(xi, g.inv_h, N, G);
-      float dv[D], vb[D], L[D][D];
-#pragma unroll
-      for (int k = 0; k < D; ++k) {
-        dv[k] = vb[k] = 0.f;
-#pragma unroll
-        for (int l = 0; l < D; ++l) L[k][l] = 0.f;
-      }
-#pragma unroll
-      for (int a = 0; a < NC; ++a) {
-        const int b = (lc[0] + (a & 1)) + (TX + 1) * ((lc[1] + ((a >> 1) & 1)) + (TY + 1) * (D == 3 ? lc[2] + ((a >> 2) & 1) : 0));
-#pragma unroll
-        for (int k = 0; k < D; ++k) {
-          const float vk = sV[b][k];
-          if (GMODE != G2P_USF_STRESS) {
-            dv[k] += N[a] * sA[b][k];
-            vb[k] += N[a] * vk;
-          }
-#pragma unroll
-          for (int l = 0; l < D; ++l) L[k][l] += vk * G[a][l];
-        }
-      }
-
-      int status = 0;
-      if (GMODE != G2P_USF_ADVECT) {
-        // strain increment, volume, stress
-        float de[6] = {0, 0, 0, 0, 0, 0};
-        de[0] = L[0][0] * g.dt;
-        de[1] = L[1][1] * g.dt;
-        de[3] = 0.5f * (L[0][1] + L[1][0]) * g.dt;
-        if (D == 3) {
-          de[2] = L[D - 1][D - 1] * g.dt;
-          de[4] = 0.5f * (L[1][D - 1] + L[D - 1][1]) * g.dt;
-          de[5] = 0.5f * (L[0][D - 1] + L[D - 1][0]) * g.dt;
-        }
-        float sg[6], ep[NS];
-        if (D == 3) {
-#pragma unroll
-          for (int i = 0; i < 6; ++i) sg[i] = A.A.sig[i][j];
+          bc_full<D, float>(faces, g.bc, g.mu, g.dt, v, a, vn);
+        } else if (NMODE == NODE_USF_V) {
+          bc_velocity<D, float>(faces, g.bc, v);
         } else {
-          sg[0] = A.A.sig[0][j]; sg[1] = A.A.sig[1][j]; sg[2] = A.A.sig[2][j]; sg[3] = A.A.sig[3][j];
-          sg[4] = sg[5] = 0.f;
-        }
+          float f[D];
+          gather_node<D, D>(g, A.tile_start, A.slots2, D, I, tc, f);
+          bc_velocity<D, float>(faces, g.bc, v);
 #pragma unroll
-        for (int i = 0; i < NS; ++i) ep[i] = A.A.eps[i][j] + de[i];
-        float vol = A.A.vol[j] * (1.f + de[0] + de[1] + de[2]);
-        float epsp = A.A.epsp[j];
-        const float coh = A.A.coh ? A.A.coh[j] : A.mat.c;
-        material_update(A.mat, A.matd, coh, sg, de, epsp);
-#pragma unroll
-        for (int i = 0; i < NS; ++i) {
-          A.B.sig[i][q] = sg[i];
-          A.B.eps[i][q] = ep[i];
-          if (!isfinite(sg[i])) status |= ST_NONFINITE;
+          for (int k = 0; k < D; ++k) {
+            a[k] = f[k] * inv_m + g.g[k];
+            vn[k] = v[k] + a[k] * g.dt;
+          }
+          bc_full<D, float>(faces, g.bc, g.mu, g.dt, v, a, vn);
         }
-        A.B.vol[q] = vol;
-        A.B.epsp[q] = epsp;
       }
-      if (GMODE != G2P_USF_STRESS) {
-        // FLIP velocity, advection in cell units, relocation
-        int cell[3] = {tc[0] * TX + lc[0], tc[1] * TY + lc[1], D == 3 ? tc[2] * TZ + lc[2] : 0};
-        bool dead = false;
+      const int64_t gi = I[0] + A.ns0 * I[1] + A.ns1 * I[2];
 #pragma unroll
-        for (int k = 0; k < D; ++k) {
-          const float vk = A.A.vel[k][j] + g.dt * dv[k];
-          A.B.vel[k][q] = vk;
-          if (!isfinite(vk)) status |= ST_NONFINITE;
-          float un = u[k] + g.dt * vb[k] * g.inv_h;
-          if (!isfinite(un)) {
-            status |= ST_NONFINITE;
-            dead = true;
-            un = 0.f;
-          }
-          // relocation: one cell crossing is an exact subtraction (Sterbenz),
-          // so the offset stays in [-0.5, 0.5) and the cell is exact
-          if (un >= 0.5f) {
-            un -= 1.f;
-            cell[k] += 1;
-          } else if (un < -0.5f) {
-            un += 1.f;
-            cell[k] -= 1;
-          }
-          if (!(un >= -0.5f && un < 0.5f)) {  // more than one cell per step
-            const float sh = floorf(un + 0.5f);
-            un -= sh;
-            cell[k] += (int)sh;
-            if (un >= 0.5f) {
-              un -= 1.f;
-              cell[k] += 1;
-            } else if (un < -0.5f) {
-              un += 1.f;
-              cell[k] -= 1;
-            }
-          }
-          if (cell[k] < 0 || cell[k] >= g.nc[k]) dead = true;
-          A.B.off[k][q] = un;
-        }
-        uint32_t nkey = g.dead_key;
-        if (!dead) {
-          const int t2 = cell[0] / TX + g.nt[0] * (cell[1] / TY + g.nt[1] * (D == 3 ? cell[2] / TZ : 0));
-          const int l2 = cell[0] % TX + TX * (cell[1] % TY + TY * (D == 3 ? cell[2] % TZ : 0));
-          nkey = (uint32_t)t2 * CELLS_PER_TILE + (uint32_t)l2;
-        } else {
-          status |= ST_LEFT_MESH;
-        }
-        A.B.key[q] = nkey;
-        A.B.mass[q] = A.A.mass[j];
-        A.B.id[q] = A.A.id[j];
-        if (A.A.coh) A.B.coh[q] = A.A.coh[j];
+      for (int k = 0; k < D; ++k) {
+        A.nv[k][gi] = NMODE == NODE_USF_V ? v[k] : vn[k];
+        if (NMODE != NODE_USF_V) A.na[k][gi] = a[k];
       }
-      if (status) atomicOr(&A.ctr[8], status);
     }
     __syncthreads();
   }
 }
 
-// Particles that left the mesh sit after all tiles in key order: carried over.
-template <int D>
-__global__ void copy_dead(PBuf A, PBuf B, const int32_t *perm, const int32_t *tile_start, int ntiles,
-                          int64_t n) {
-  const int s = tile_start[ntiles];
+// ---------------------------------------------------------------------------
+// G2P: one thread per particle in binning order
+// ---------------------------------------------------------------------------
+template <int D, int GMODE>
+__global__ void __launch_bounds__(G2P_T) g2p(TileArgs A, int64_t n) {
+  constexpr int NC = 1 << D;
+  constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ;
   constexpr int NS = nstress<D>();
-  for (int64_t q = s + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
-    const int j = perm[q];
-    B.key[q] = A.key[j];
-    B.id[q] = A.id[j];
+  const Geo &g = A.geo;
+  const int64_t q = (int64_t)blockIdx.x * G2P_T + threadIdx.x;
+  if (q >= n) return;
+  const int j = A.perm[q];
+  const int dead_start = A.ctr[C_DEAD_START];
+  if (q >= dead_start) {  // left the mesh earlier: carried over unchanged
+    if (GMODE != G2P_USF_STRESS) {
+      A.B.key[q] = A.A.key[j];
+      A.B.id[q] = A.A.id[j];
+      A.B.mass[q] = A.A.mass[j];
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        A.B.off[k][q] = A.A.off[k][j];
+        A.B.vel[k][q] = A.A.vel[k][j];
+      }
+      if (A.A.coh) A.B.coh[q] = A.A.coh[j];
+    }
+    if (GMODE != G2P_USF_ADVECT) {
+#pragma unroll
+      for (int i = 0; i < NS; ++i) {
+        A.B.sig[i][q] = A.A.sig[i][j];
+        A.B.eps[i][q] = A.A.eps[i][j];
+      }
+      A.B.jm1[q] = A.A.jm1[j];
+      A.B.epsp[q] = A.A.epsp[j];
+    }
+    return;
+  }
+  const uint32_t key = A.keys[q];
+  const int t = key >> LOCAL_BITS;
+  int tc[3], lc[3];
+  tile_coords(g, t, tc);
+  local_coords<D>(key, lc);
+  int cell[3] = {tc[0] * TX + lc[0], tc[1] * TY + lc[1], D == 3 ? tc[2] * TZ + lc[2] : 0};
+  float u[D], w0[D], w1[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) u[k] = A.A.off[k][j];
+  corner_weights<D>(u, w0, w1);
+  float dv[D], vb[D], L[D][D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    dv[k] = vb[k] = 0.f;
+#pragma unroll
+    for (int l = 0; l < D; ++l) L[k][l] = 0.f;
+  }
+  const int64_t gi0 = cell[0] + A.ns0 * cell[1] + A.ns1 * cell[2];
+#pragma unroll
+  for (int a = 0; a < NC; ++a) {
+    float N, G[D];
+    corner_shape<D>(a, w0, w1, g.inv_h, N, G);
+    const int64_t gi = gi0 + (a & 1) + A.ns0 * ((a >> 1) & 1) + (D == 3 ? A.ns1 * ((a >> 2) & 1) : 0);
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-      B.off[k][q] = A.off[k][j];
-      B.vel[k][q] = A.vel[k][j];
+      const float vk = A.nv[k][gi];
+      if (GMODE != G2P_USF_STRESS) {
+        dv[k] += N * A.na[k][gi];
+        vb[k] += N * vk;
+      }
+#pragma unroll
+      for (int l = 0; l < D; ++l) L[k][l] += vk * G[l];
+    }
+  }
+
+  int status = 0;
+  if (GMODE != G2P_USF_ADVECT) {
+    // strain increment, volume ratio, stress
+    float de[6] = {0, 0, 0, 0, 0, 0};
+    de[0] = L[0][0] * g.dt;
+    de[1] = L[1][1] * g.dt;
+    de[3] = 0.5f * (L[0][1] + L[1][0]) * g.dt;
+    if (D == 3) {
+      de[2] = L[D - 1][D - 1] * g.dt;
+      de[4] = 0.5f * (L[1][D - 1] + L[D - 1][1]) * g.dt;
+      de[5] = 0.5f * (L[0][D - 1] + L[D - 1][0]) * g.dt;
+    }
+    float sg[6];
+    if (D == 3) {
+#pragma unroll
+      for (int i = 0; i < 6; ++i) sg[i] = A.A.sig[i][j];
+    } else {
+      sg[0] = A.A.sig[0][j];
+      sg[1] = A.A.sig[1][j];
+      sg[2] = A.A.sig[2][j];
+      sg[3] = A.A.sig[3][j];
+      sg[4] = sg[5] = 0.f;
     }
 #pragma unroll
+    for (int i = 0; i < NS; ++i) A.B.eps[i][q] = A.A.eps[i][j] + de[i];
+    // V = V0 (1 + jm1):  (1 + jm1)(1 + tr) - 1 = jm1 + tr + jm1 tr
+    const float tr = de[0] + de[1] + de[2];
+    const float jm1 = A.A.jm1[j];
+    A.B.jm1[q] = jm1 + (tr + jm1 * tr);
+    float epsp = A.A.epsp[j];
+    const float coh = A.A.coh ? A.A.coh[j] : A.mat.c;
+    material_update(A.mat, A.matd, coh, sg, de, epsp);
+#pragma unroll
     for (int i = 0; i < NS; ++i) {
-      B.sig[i][q] = A.sig[i][j];
-      B.eps[i][q] = A.eps[i][j];
+      A.B.sig[i][q] = sg[i];
+      if (!isfinite(sg[i])) status |= ST_NONFINITE;
     }
-    B.mass[q] = A.mass[j];
-    B.vol[q] = A.vol[j];
-    B.epsp[q] = A.epsp[j];
-    if (A.coh) B.coh[q] = A.coh[j];
+    A.B.epsp[q] = epsp;
   }
+  if (GMODE != G2P_USF_STRESS) {
+    // FLIP velocity, advection in cell units, relocation
+    bool dead = false;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const float vk = A.A.vel[k][j] + g.dt * dv[k];
+      A.B.vel[k][q] = vk;
+      if (!isfinite(vk)) status |= ST_NONFINITE;
+      float un = u[k] + g.dt * vb[k] * g.inv_h;
+      if (!isfinite(un)) {
+        status |= ST_NONFINITE;
+        dead = true;
+        un = 0.f;
+      }
+      // one cell crossing is an exact subtraction (Sterbenz), so the offset
+      // stays in [-0.5, 0.5) and the cell is exact
+      if (un >= 0.5f) {
+        un -= 1.f;
+        cell[k] += 1;
+      } else if (un < -0.5f) {
+        un += 1.f;
+        cell[k] -= 1;
+      }
+      if (!(un >= -0.5f && un < 0.5f)) {  // more than one cell per step
+        const float sh = floorf(un + 0.5f);
+        un -= sh;
+        cell[k] += (int)sh;
+        if (un >= 0.5f) {
+          un -= 1.f;
+          cell[k] += 1;
+        } else if (un < -0.5f) {
+          un += 1.f;
+          cell[k] -= 1;
+        }
+      }
+      if (cell[k] < 0 || cell[k] >= g.nc[k]) dead = true;
+      A.B.off[k][q] = un;
+    }
+    uint32_t nkey = g.dead_key;
+    if (!dead) {
+      const int t2 = cell[0] / TX + g.nt[0] * (cell[1] / TY + g.nt[1] * (D == 3 ? cell[2] / TZ : 0));
+      const int l2 = cell[0] % TX + TX * (cell[1] % TY + TY * (D == 3 ? cell[2] % TZ : 0));
+      nkey = (uint32_t)t2 * CELLS_PER_TILE + (uint32_t)l2;
+    } else {
+      status |= ST_LEFT_MESH;
+    }
+    A.B.key[q] = nkey;
+    A.B.mass[q] = A.A.mass[j];
+    A.B.id[q] = A.A.id[j];
+    if (A.A.coh) A.B.coh[q] = A.A.coh[j];
+  }
+  if (status) atomicOr(&A.ctr[C_STATUS], status);
 }
 
-template <int D, int MODE>
-constexpr size_t p2g_smem() {
-  return sizeof(float) * (CELLS_PER_TILE * (1 << D) * p2g_channels<D, MODE>() + NWARP * 32 * 33);
-}
-
-template <int D, int MODE>
-cudaError_t launch_p2g(const F32Launch &L, float *slots, int work_slot, cudaStream_t st) {
-  P2GArgs<D> a;
+TileArgs make_args(const F32Launch &L, int work_slot) {
+  TileArgs a;
   a.geo = L.geo;
   a.A = L.A;
   a.B = L.B;
   a.keys = L.s.keys_sorted;
   a.perm = L.s.perm;
-  a.tile_start = L.s.tile_start;
+  a.tile_start = L.tile_start;
   a.active = L.s.active;
   a.ctr = L.s.ctr;
   a.work_slot = work_slot;
-  a.slots = slots;
-  p2g_tile<D, MODE><<<L.grid, NT, p2g_smem<D, MODE>(), st>>>(a);
+  a.slots1 = L.s.slots1;
+  a.slots2 = L.s.slots2;
+  a.slots_out = nullptr;
+  a.nch1 = 0;
+  for (int k = 0; k < 3; ++k) {
+    a.nv[k] = L.s.node_v[k];
+    a.na[k] = L.s.node_a[k];
+  }
+  a.ns0 = L.node_stride[0];
+  a.ns1 = L.node_stride[1];
+  a.mat = L.mat;
+  a.matd = L.matd;
+  return a;
+}
+
+template <int D, int MODE>
+cudaError_t launch_p2g(const F32Launch &L, float *slots, int work_slot, cudaStream_t st) {
+  TileArgs a = make_args(L, work_slot);
+  a.slots_out = slots;
+  p2g_tile<D, MODE><<<L.grid, P2G_T, p2g_smem<D, MODE>(), st>>>(a);
   return cudaGetLastError();
 }
 
@@ -557,59 +611,58 @@ cudaError_t prepare_p2g() {
                               (int)p2g_smem<D, MODE>());
 }
 
-template <int D, int GMODE>
-cudaError_t launch_g2p(const F32Launch &L, int work_slot, int nch1, cudaStream_t st) {
-  G2PArgs<D> a;
-  a.geo = L.geo;
-  a.mat = L.mat;
-  a.matd = L.matd;
-  a.A = L.A;
-  a.B = L.B;
-  a.keys = L.s.keys_sorted;
-  a.perm = L.s.perm;
-  a.tile_start = L.s.tile_start;
-  a.active = L.s.active;
-  a.ctr = L.s.ctr;
-  a.work_slot = work_slot;
-  a.slots1 = L.s.slots1;
-  a.slots2 = L.s.slots2;
+template <int D, int NMODE>
+cudaError_t launch_node(const F32Launch &L, int work_slot, int nch1, cudaStream_t st) {
+  TileArgs a = make_args(L, work_slot);
   a.nch1 = nch1;
-  g2p_tile<D, GMODE><<<L.grid, NT, 0, st>>>(a);
+  node_tile<D, NMODE><<<L.grid, NODE_T, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int D, int GMODE>
+cudaError_t launch_g2p(const F32Launch &L, cudaStream_t st) {
+  TileArgs a = make_args(L, 0);
+  const int64_t blocks = (L.n + G2P_T - 1) / G2P_T;
+  g2p<D, GMODE><<<(unsigned)blocks, G2P_T, 0, st>>>(a, L.n);
   return cudaGetLastError();
 }
 
 template <int D>
 cudaError_t step_dim(const F32Launch &L, cudaStream_t st) {
   cudaError_t e;
-  const int blocks = L.grid;
-  // phase events 0..2 are recorded by the caller (start, after sort, after
-  // tile bounds); the tile kernels add 3.. after each launch
+  // phase events 0 (start) and 1 (after binning) are recorded by the
+  // caller; 2.. follow each kernel here
   if (L.scheme == 1) {  // USL
-    if ((e = launch_p2g<D, P2G_USL>(L, L.s.slots1, 1, st)) != cudaSuccess) return e;
+    if ((e = launch_p2g<D, P2G_USL>(L, L.s.slots1, C_WORK_P2G, st)) != cudaSuccess) return e;
+    if ((e = phase_mark(L.ev, 2, st)) != cudaSuccess) return e;
+    if ((e = launch_node<D, NODE_USL>(L, C_WORK_NODE, 1 + 2 * D, st)) != cudaSuccess) return e;
     if ((e = phase_mark(L.ev, 3, st)) != cudaSuccess) return e;
-    if ((e = launch_g2p<D, G2P_USL>(L, 2, 1 + 2 * D, st)) != cudaSuccess) return e;
-  } else {  // USF
-    if ((e = launch_p2g<D, P2G_MOM>(L, L.s.slots1, 1, st)) != cudaSuccess) return e;
-    if ((e = phase_mark(L.ev, 3, st)) != cudaSuccess) return e;
-    if ((e = launch_g2p<D, G2P_USF_STRESS>(L, 2, 1 + D, st)) != cudaSuccess) return e;
-    if ((e = phase_mark(L.ev, 4, st)) != cudaSuccess) return e;
-    if ((e = launch_p2g<D, P2G_FORCE>(L, L.s.slots2, 3, st)) != cudaSuccess) return e;
-    if ((e = phase_mark(L.ev, 5, st)) != cudaSuccess) return e;
-    if ((e = launch_g2p<D, G2P_USF_ADVECT>(L, 4, 1 + D, st)) != cudaSuccess) return e;
+    if ((e = launch_g2p<D, G2P_USL>(L, st)) != cudaSuccess) return e;
+    return phase_mark(L.ev, 4, st);
   }
-  copy_dead<D><<<blocks, 256, 0, st>>>(L.A, L.B, L.s.perm, L.s.tile_start, L.geo.ntiles, L.n);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  return phase_mark(L.ev, L.scheme == 1 ? 4 : 6, st);
+  // USF
+  if ((e = launch_p2g<D, P2G_MOM>(L, L.s.slots1, C_WORK_P2G, st)) != cudaSuccess) return e;
+  if ((e = phase_mark(L.ev, 2, st)) != cudaSuccess) return e;
+  if ((e = launch_node<D, NODE_USF_V>(L, C_WORK_NODE, 1 + D, st)) != cudaSuccess) return e;
+  if ((e = phase_mark(L.ev, 3, st)) != cudaSuccess) return e;
+  if ((e = launch_g2p<D, G2P_USF_STRESS>(L, st)) != cudaSuccess) return e;
+  if ((e = phase_mark(L.ev, 4, st)) != cudaSuccess) return e;
+  if ((e = launch_p2g<D, P2G_FORCE>(L, L.s.slots2, C_WORK_P2G2, st)) != cudaSuccess) return e;
+  if ((e = phase_mark(L.ev, 5, st)) != cudaSuccess) return e;
+  if ((e = launch_node<D, NODE_USF_A>(L, C_WORK_NODE2, 1 + D, st)) != cudaSuccess) return e;
+  if ((e = phase_mark(L.ev, 6, st)) != cudaSuccess) return e;
+  if ((e = launch_g2p<D, G2P_USF_ADVECT>(L, st)) != cudaSuccess) return e;
+  return phase_mark(L.ev, 7, st);
 }
 
 // ---------------------------------------------------------------------------
-// Conservation sums (FP64, deterministic two-level), export, keys
+// Conservation sums (FP64, deterministic two-level), export
 // ---------------------------------------------------------------------------
 constexpr int CONS_BLOCKS = 1024;
 constexpr int CONS_VALS = 7;
 
 template <int D>
-__global__ void cons_partial(int64_t n, PBuf P, uint32_t dead_key, double *part) {
+__global__ void cons_partial(int64_t n, PBuf P, uint32_t dead_key, float inv_rho, double *part) {
   constexpr int NS = nstress<D>();
   double acc[CONS_VALS] = {0, 0, 0, 0, 0, 0, 0};
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
@@ -626,12 +679,9 @@ __global__ void cons_partial(int64_t n, PBuf P, uint32_t dead_key, double *part)
     acc[4] += 0.5 * m * ke;
     double se = 0;
 #pragma unroll
-    for (int i = 0; i < NS; ++i) {
-      const int i6 = (D == 2 && i == 3) ? 3 : i;
-      const double w = (i6 >= 3) ? 2.0 : 1.0;
-      se += w * (double)P.sig[i][q] * (double)P.eps[i][q];
-    }
-    acc[5] += 0.5 * (double)P.vol[q] * se;
+    for (int i = 0; i < NS; ++i) se += (i >= 3 ? 2.0 : 1.0) * (double)P.sig[i][q] * (double)P.eps[i][q];
+    const double vol = m * (double)inv_rho * (1.0 + (double)P.jm1[q]);
+    acc[5] += 0.5 * vol * se;
     acc[6] += 1.0;
   }
   __shared__ double red[CONS_VALS][256];
@@ -656,8 +706,9 @@ __global__ void cons_final(const double *part, int nb, double *out) {
 }
 
 template <int D>
-__global__ void export_k(int64_t n, PBuf P, Geo g, double o0, double o1, double o2, double h, double *pos,
-                         double *vel, double *sig, double *eps, double *vol, double *epsp, int64_t *cell) {
+__global__ void export_k(int64_t n, PBuf P, Geo g, double o0, double o1, double o2, double h, double rho,
+                         double *pos, double *vel, double *sig, double *eps, double *vol, double *epsp,
+                         int64_t *cell) {
   constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ;
   constexpr int NS = nstress<D>();
   const double org[3] = {o0, o1, o2};
@@ -667,12 +718,8 @@ __global__ void export_k(int64_t n, PBuf P, Geo g, double o0, double o1, double 
     const bool dead = key >= g.dead_key;
     int c[3] = {0, 0, 0};
     if (!dead) {
-      const int t = key / CELLS_PER_TILE;
-      int tc[3];
-      tc[0] = t % g.nt[0];
-      tc[1] = (t / g.nt[0]) % g.nt[1];
-      tc[2] = t / (g.nt[0] * g.nt[1]);
-      int lc[3];
+      int tc[3], lc[3];
+      tile_coords(g, (int)(key >> LOCAL_BITS), tc);
       local_coords<D>(key, lc);
       c[0] = tc[0] * TX + lc[0];
       c[1] = tc[1] * TY + lc[1];
@@ -699,15 +746,10 @@ __global__ void export_k(int64_t n, PBuf P, Geo g, double o0, double o1, double 
         if (eps) eps[id * 6 + i] = e6[i];
       }
     }
-    if (vol) vol[id] = P.vol[q];
+    if (vol) vol[id] = (double)P.mass[q] / rho * (1.0 + (double)P.jm1[q]);
     if (epsp) epsp[id] = P.epsp[q];
     if (cell) cell[id] = dead ? -1 : (int64_t)c[0] + (int64_t)g.nc[0] * ((int64_t)c[1] + (int64_t)g.nc[1] * c[2]);
   }
-}
-
-__global__ void keys_copy(int64_t n, const uint32_t *src, uint32_t *dst) {
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
-    dst[q] = src[q];
 }
 
 __global__ void mat_update_f32_k(MatConst<float> m, MatConst<double> md, int64_t n, const float *sig,
@@ -746,38 +788,32 @@ cudaError_t f32_step(const F32Launch &L, cudaStream_t st) {
   return L.dim == 3 ? step_dim<3>(L, st) : step_dim<2>(L, st);
 }
 
-cudaError_t f32_conservation(int dim, int64_t n, const PBuf &P, uint32_t dead_key, double *d_out,
+cudaError_t f32_conservation(int dim, int64_t n, const PBuf &P, uint32_t dead_key, float inv_rho, double *d_out,
                              double *d_partials, cudaStream_t st) {
   if (dim == 3)
-    cons_partial<3><<<CONS_BLOCKS, 256, 0, st>>>(n, P, dead_key, d_partials);
+    cons_partial<3><<<CONS_BLOCKS, 256, 0, st>>>(n, P, dead_key, inv_rho, d_partials);
   else
-    cons_partial<2><<<CONS_BLOCKS, 256, 0, st>>>(n, P, dead_key, d_partials);
+    cons_partial<2><<<CONS_BLOCKS, 256, 0, st>>>(n, P, dead_key, inv_rho, d_partials);
   cons_final<<<1, 32, 0, st>>>(d_partials, CONS_BLOCKS, d_out);
   return cudaGetLastError();
 }
 
 cudaError_t f32_export(int dim, int64_t n, const PBuf &P, const Geo &g, const double origin[3], double h,
-                       double *pos, double *vel, double *sig, double *eps, double *vol, double *epsp,
+                       double rho, double *pos, double *vel, double *sig, double *eps, double *vol, double *epsp,
                        int64_t *cell, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
   if (dim == 3)
-    export_k<3><<<blocks, 256, 0, st>>>(n, P, g, origin[0], origin[1], origin[2], h, pos, vel, sig, eps, vol, epsp, cell);
+    export_k<3><<<blocks, 256, 0, st>>>(n, P, g, origin[0], origin[1], origin[2], h, rho, pos, vel, sig, eps, vol,
+                                        epsp, cell);
   else
-    export_k<2><<<blocks, 256, 0, st>>>(n, P, g, origin[0], origin[1], origin[2], h, pos, vel, sig, eps, vol, epsp, cell);
+    export_k<2><<<blocks, 256, 0, st>>>(n, P, g, origin[0], origin[1], origin[2], h, rho, pos, vel, sig, eps, vol,
+                                        epsp, cell);
   return cudaGetLastError();
 }
 
-cudaError_t f32_keys(int dim, int64_t n, const PBuf &P, uint32_t *keys_out, cudaStream_t st) {
-  (void)dim;
-  if (n <= 0) return cudaSuccess;
-  keys_copy<<<1024, 256, 0, st>>>(n, P.key, keys_out);
-  return cudaGetLastError();
-}
-
-cudaError_t material_update_f32(const MatConst<float> &m, const MatConst<double> &md, int64_t n,
-                                const float *sig, const float *de, const float *coh, float *out,
-                                float *depsp, cudaStream_t st) {
+cudaError_t material_update_f32(const MatConst<float> &m, const MatConst<double> &md, int64_t n, const float *sig,
+                                const float *de, const float *coh, float *out, float *depsp, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
   mat_update_f32_k<<<blocks, 256, 0, st>>>(m, md, n, sig, de, coh, out, depsp);

@@ -9,15 +9,19 @@
 
 namespace mpm {
 
-// Tiles of the FP32 path: 256 cells each, 8 x 8 x 4 hexahedra or 16 x 16 quads.
+// Tiles of the FP32 path: 64 cells each, 4 x 4 x 4 hexahedra or 8 x 8 quads.
+// Binning key = tile * 64 + local cell, tile = tx + NTX (ty + NTY tz),
+// local = lx + TX (ly + TY lz); particles that left the mesh carry the key
+// NT * 64 (a virtual tile after all real ones).
 template <int D> struct Tile;
 template <> struct Tile<3> {
-  static constexpr int TX = 8, TY = 8, TZ = 4;
+  static constexpr int TX = 4, TY = 4, TZ = 4;
 };
 template <> struct Tile<2> {
-  static constexpr int TX = 16, TY = 16, TZ = 1;
+  static constexpr int TX = 8, TY = 8, TZ = 1;
 };
-constexpr int CELLS_PER_TILE = 256;
+constexpr int CELLS_PER_TILE = 64;
+constexpr int LOCAL_BITS = 6;
 template <int D> constexpr int box_x() { return Tile<D>::TX + 1; }
 template <int D> constexpr int box_y() { return Tile<D>::TY + 1; }
 template <int D> constexpr int box_z() { return D == 3 ? Tile<D>::TZ + 1 : 1; }
@@ -29,12 +33,16 @@ enum { P2G_USL = 0, P2G_MOM = 1, P2G_FORCE = 2 };
 template <int D, int MODE> constexpr int p2g_channels() {
   return MODE == P2G_USL ? 1 + 2 * D : MODE == P2G_MOM ? 1 + D : D;
 }
+// Node kernels: USL (v', a), USF velocity stage (v), USF force stage (v', a).
+enum { NODE_USL = 0, NODE_USF_V = 1, NODE_USF_A = 2 };
 // G2P kernels: USL (full update), USF stress stage, USF advection stage.
 enum { G2P_USL = 0, G2P_USF_STRESS = 1, G2P_USF_ADVECT = 2 };
 
 // FP32 particle storage, SoA; every field has n entries.  Offsets are in cell
 // units, centred: the particle sits at origin + (cell + 0.5 + off) h with
-// off in [-0.5, 0.5).  Stresses/strains: 6 comps in 3D, (xx,yy,zz,xy) in 2D.
+// off in [-0.5, 0.5).  Volume is held as jm1 = V / V0 - 1 with V0 = m / rho,
+// so that the tiny per-step volume changes keep FP32's relative precision.
+// Stresses/strains: 6 comps in 3D, (xx, yy, zz, xy) in 2D.
 struct PBuf {
   uint32_t *key;
   int32_t *id;
@@ -42,7 +50,7 @@ struct PBuf {
   float *vel[3];
   float *sig[6];
   float *eps[6];
-  float *mass, *vol, *epsp, *coh;  // coh may be nullptr
+  float *mass, *jm1, *epsp, *coh;  // coh may be nullptr
 };
 
 struct Geo {
@@ -50,33 +58,75 @@ struct Geo {
   int nt[3];   // tiles per axis
   int ntiles;
   uint32_t dead_key;
-  float h, inv_h, dt, mass_tol;
+  float h, inv_h, dt, mass_tol, inv_rho;
   float g[3];
   int bc[6];
   float mu[6];
 };
 
-// Device scratch of one binning + step of the FP32 path.
+// Counters of a step (int32, in StepBufs::ctr).
+enum {
+  C_ACTIVE = 0,     // active (non-empty) tiles this step
+  C_MOVERS = 1,     // particles that changed tile (appended by bin_movers)
+  C_MOVERS_SNAP = 2,
+  C_WORK_BIN = 3,   // dynamic tile counters of the per-tile kernels
+  C_WORK_P2G = 4,
+  C_WORK_NODE = 5,
+  C_WORK_P2G2 = 6,
+  C_WORK_NODE2 = 7,
+  C_STATUS = 8,     // sticky device status bits (ST_*)
+  C_BIN_ITEMS = 9,  // active tiles + 1 if the dead range is non-empty
+  C_DEAD_START = 10,
+  C_NCTR = 16
+};
+
+// Device storage of the FP32 path's binning and step.
 struct StepBufs {
-  uint32_t *keys_sorted;  // n
-  int32_t *perm;          // n
-  int32_t *tile_start;    // ntiles + 2
-  int32_t *active;        // ntiles
-  int32_t *ctr;           // [0] active tiles, [1..7] work counters, [8] status
-  float *slots1;          // ntiles * box * channels (P2G USL / MOM)
-  float *slots2;          // ntiles * box * D        (P2G FORCE, USF)
+  uint32_t *keys_sorted;   // n: keys in binning order (old keys for the next binning)
+  int32_t *perm;           // n: storage slot of the q-th particle in binning order
+  int32_t *tile_start[2];  // ntiles + 2 each: old / new tile ranges (parity = step parity)
+  int32_t *in_cnt;         // ntiles + 1: particles entering each tile
+  int32_t *out_cnt;        // ntiles + 1: particles leaving each tile
+  int32_t *bucket_start;   // ntiles + 2
+  int32_t *bucket_fill;    // ntiles + 1
+  int32_t *movers;         // n: storage slots of tile movers
+  int32_t *bucket;         // n: movers grouped by destination tile
+  int32_t *bucket_sorted;  // n: scratch for large buckets
+  int32_t *active;         // ntiles: active tile list
+  int32_t *ctr;            // C_NCTR counters
+  float *slots1;           // ntiles * box * channels (P2G USL / MOM)
+  float *slots2;           // ntiles * box * D        (P2G FORCE, USF)
+  float *node_v[3];        // dense node arrays: v' (or v in the USF velocity stage)
+  float *node_a[3];        // dense node arrays: a
 };
 
 // --- radix sort (mpm_sort.cu) ---------------------------------------------
-// Scratch bytes for sorting n keys of key_bits bits.
 size_t sort_scratch_bytes(int64_t n);
 // Stable LSD sort: keys_in (unchanged) -> keys_out sorted, perm_out
 // (index of the q-th smallest).  vals_in == nullptr means identity.
 cudaError_t sort_pairs(const uint32_t *keys_in, const int32_t *vals_in, uint32_t *keys_out,
                        int32_t *perm_out, int64_t n, int key_bits, void *scratch, cudaStream_t st);
-// tile_start / active tile list from sorted keys.
+// tile_start[u] = first position with key >= u * 64 (u = 0..ntiles), [ntiles+1] = n.
 cudaError_t tile_bounds(const uint32_t *keys_sorted, int64_t n, int ntiles, int32_t *tile_start,
-                        int32_t *active, int32_t *ctr, cudaStream_t st);
+                        cudaStream_t st);
+
+// --- incremental binning (mpm_bin.cu) ----------------------------------------
+struct BinLaunch {
+  int64_t n;
+  int ntiles;
+  const uint32_t *knew;      // keys of the stored particles (storage order)
+  const uint32_t *kold;      // keys of the previous binning (storage order)
+  const int32_t *old_start;  // previous tile ranges
+  int32_t *new_start;        // out
+  StepBufs s;
+  uint32_t *keys_out;        // out: keys in binning order
+  int32_t *perm_out;         // out: permutation
+  int grid;
+};
+cudaError_t bin_step(const BinLaunch &B, cudaStream_t st);
+// Gather every field of A into B in the order perm (B[q] = A[perm[q]]).
+cudaError_t permute_state(int dim, int64_t n, const PBuf &A, const PBuf &B, const int32_t *perm,
+                          cudaStream_t st);
 
 // --- FP32 tile kernels (mpm_fp32.cu) ----------------------------------------
 struct F32Launch {
@@ -85,10 +135,12 @@ struct F32Launch {
   Geo geo;
   MatConst<float> mat;
   MatConst<double> matd;
-  PBuf A, B;  // A: state at the start of the step (storage order), B: out (sorted order)
+  PBuf A, B;  // A: state at the start of the step (storage order), B: out (binning order)
   StepBufs s;
-  int grid;   // persistent grid size for the tile kernels
-  cudaEvent_t *ev;  // optional phase events (recorded after each tile kernel), or nullptr
+  const int32_t *tile_start;  // this step's tile ranges (binning order)
+  int64_t node_stride[2];     // (nx+1), (nx+1)(ny+1)
+  int grid;                   // persistent grid size for the per-tile kernels
+  cudaEvent_t *ev;            // optional phase events, or nullptr
 };
 // Record a phase boundary (works inside stream capture as an external node).
 inline cudaError_t phase_mark(cudaEvent_t *ev, int i, cudaStream_t st) {
@@ -96,12 +148,11 @@ inline cudaError_t phase_mark(cudaEvent_t *ev, int i, cudaStream_t st) {
 }
 cudaError_t f32_prepare(int dim);                           // once per process and dim
 cudaError_t f32_step(const F32Launch &L, cudaStream_t st);  // everything after binning
-cudaError_t f32_conservation(int dim, int64_t n, const PBuf &P, uint32_t dead_key, double *d_out,
-                             double *d_partials, cudaStream_t st);
+cudaError_t f32_conservation(int dim, int64_t n, const PBuf &P, uint32_t dead_key, float inv_rho,
+                             double *d_out, double *d_partials, cudaStream_t st);
 cudaError_t f32_export(int dim, int64_t n, const PBuf &P, const Geo &g, const double origin[3], double h,
-                       double *pos, double *vel, double *sig, double *eps, double *vol, double *epsp,
-                       int64_t *cell, cudaStream_t st);
-cudaError_t f32_keys(int dim, int64_t n, const PBuf &P, uint32_t *keys_out, cudaStream_t st);
+                       double rho, double *pos, double *vel, double *sig, double *eps, double *vol,
+                       double *epsp, int64_t *cell, cudaStream_t st);
 
 // --- FP64 plain kernels (mpm_fp64.cu) ----------------------------------------
 struct D64State {

@@ -183,22 +183,22 @@ __global__ void __launch_bounds__(RS_THREADS) rs_downsweep(const uint32_t *__res
   }
 }
 
+// tile_start[u] = lower bound of u * 64 in the sorted keys.
 __global__ void k_tile_bounds(const uint32_t *__restrict__ keys, int64_t n, int ntiles,
-                              int32_t *__restrict__ tile_start, int32_t *__restrict__ active,
-                              int32_t *__restrict__ ctr) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int t = min((int)(keys[i] >> 8), ntiles);
-  const int tp = i == 0 ? -1 : min((int)(keys[i - 1] >> 8), ntiles);
-  for (int u = tp + 1; u <= t; ++u) tile_start[u] = (int32_t)i;
-  if (t != tp && t < ntiles) active[atomicAdd(&ctr[0], 1)] = t;
-  if (i == n - 1)
-    for (int u = t + 1; u <= ntiles + 1; ++u) tile_start[u] = (int32_t)n;
-}
-
-__global__ void k_tile_bounds_empty(int ntiles, int32_t *tile_start) {
-  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u <= ntiles + 1; u += gridDim.x * blockDim.x)
-    tile_start[u] = 0;
+                              int32_t *__restrict__ tile_start) {
+  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u <= ntiles + 1; u += gridDim.x * blockDim.x) {
+    if (u == ntiles + 1) {
+      tile_start[u] = (int32_t)n;
+      continue;
+    }
+    const uint32_t target = (uint32_t)u << LOCAL_BITS;
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (keys[mid] < target) lo = mid + 1; else hi = mid;
+    }
+    tile_start[u] = (int32_t)lo;
+  }
 }
 
 }  // namespace
@@ -244,12 +244,8 @@ cudaError_t sort_pairs(const uint32_t *keys_in, const int32_t *vals_in, uint32_t
 }
 
 cudaError_t tile_bounds(const uint32_t *keys_sorted, int64_t n, int ntiles, int32_t *tile_start,
-                        int32_t *active, int32_t *ctr, cudaStream_t st) {
-  if (n <= 0) {
-    k_tile_bounds_empty<<<(ntiles + 2 + 255) / 256, 256, 0, st>>>(ntiles, tile_start);
-    return cudaGetLastError();
-  }
-  k_tile_bounds<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(keys_sorted, n, ntiles, tile_start, active, ctr);
+                        cudaStream_t st) {
+  k_tile_bounds<<<(ntiles + 2 + 255) / 256, 256, 0, st>>>(keys_sorted, n, ntiles, tile_start);
   return cudaGetLastError();
 }
 

@@ -58,18 +58,35 @@ def rel_l2(a, b, floor=0.0):
     return float(np.linalg.norm(a - b) / den)
 
 
-def compare(gpu, ref, start, dim):
-    """Relative-L2 errors of a GPU snapshot against the oracle's, with
-    positions/volumes measured from `start` (the common initial snapshot)."""
+STATE_KEYS = ("pos", "vel", "stress", "vol")     # per-step check: the state itself
+RUN_KEYS = ("disp", "vel", "stress", "dvol")      # after a run: increments too
+
+
+def compare(gpu, ref, start, dim, h=None):
+    """Relative-L2 errors of a GPU snapshot against the oracle's.
+
+    pos/vol: the state (positions measured from the mesh origin);
+    disp/dvol: increments since `start`, the common initial snapshot -- a
+    single FP32 step moves a particle by ~1e-5 cells, close to the 3e-8-cell
+    resolution of its FP32 offset, so increments are only meaningful over a
+    run; off_cells: largest position difference in cell units."""
     live = (gpu["cell"] >= 0) & (ref["cell"] >= 0)
     out = {
+        "pos": rel_l2(gpu["pos"][live], ref["pos"][live]),
         "disp": rel_l2((gpu["pos"] - start["pos"])[live], (ref["pos"] - start["pos"])[live]),
         "vel": rel_l2(gpu["vel"][live], ref["vel"][live]),
         "stress": rel_l2(gpu["stress"][live], ref["stress"][live]),
+        "vol": rel_l2(gpu["vol"][live], ref["vol"][live]),
         "dvol": rel_l2((gpu["vol"] - start["vol"])[live], (ref["vol"] - start["vol"])[live],
                        floor=1e-3 * np.linalg.norm(start["vol"])),
     }
+    if h is not None:
+        out["off_cells"] = float(np.abs(gpu["pos"][live] - ref["pos"][live]).max() / h) if live.any() else 0.0
     return out
+
+
+def worst(err, keys):
+    return max(err[k] for k in keys)
 
 
 def cell_mismatch_in_band(gpu, ref, h, band_frac):

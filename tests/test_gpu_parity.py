@@ -65,12 +65,12 @@ def test_fp32_bar(scheme):
     g1, _ = run_gpu(wl, 1)
     r1, _ = run_oracle(wl, 1, scheme)
     e1 = H.compare(g1, r1, start, 2)
-    assert max(e1.values()) <= H.TOL_STEP_FP32, e1
+    assert H.worst(e1, H.STATE_KEYS) <= H.TOL_STEP_FP32, e1
     gpu, st = run_gpu(wl, wl.steps)
     ref, _ = run_oracle(wl, wl.steps, scheme)
     assert st == mpm.MPM_OK
     err = H.compare(gpu, ref, start, 2)
-    assert max(err.values()) <= H.TOL_RUN_FP32, err
+    assert H.worst(err, H.RUN_KEYS) <= H.TOL_RUN_FP32, err
 
 
 @pytest.mark.parametrize("scheme", [W.USL, W.USF])
@@ -93,12 +93,12 @@ def test_small_column_fp32(scheme):
     g1, _ = run_gpu(wl, 1)
     r1, _ = run_oracle(wl, 1, scheme)
     e1 = H.compare(g1, r1, start, 3)
-    assert max(e1.values()) <= H.TOL_STEP_FP32, e1
+    assert H.worst(e1, H.STATE_KEYS) <= H.TOL_STEP_FP32, e1
     gpu, st = run_gpu(wl, 300)
     ref, _ = run_oracle(wl, 300, scheme)
     assert st == mpm.MPM_OK
     err = H.compare(gpu, ref, start, 3)
-    assert max(err.values()) <= H.TOL_RUN_FP32, err
+    assert H.worst(err, H.RUN_KEYS) <= H.TOL_RUN_FP32, err
     ndiff, nout = H.cell_mismatch_in_band(gpu, ref, wl.h, 1e-4)
     assert nout == 0
 
@@ -115,7 +115,7 @@ def test_full_column_per_step_parity():
         assert st == mpm.MPM_OK
         r1, _ = run_oracle(wl, 1)
         e1 = H.compare(g1, r1, start, 3)
-        assert max(e1.values()) <= H.TOL_STEP_FP32, e1
+        assert H.worst(e1, H.STATE_KEYS) <= H.TOL_STEP_FP32, e1
         sim.step(59)
         s60, st = sim.read()
         assert st == mpm.MPM_OK
@@ -125,7 +125,7 @@ def test_full_column_per_step_parity():
     assert o.step(1) == oracle.OK
     r61 = H.oracle_snapshot(o, 3)
     e61 = H.compare(g61, r61, s60, 3)
-    assert max(e61.values()) <= H.TOL_STEP_FP32, e61
+    assert H.worst(e61, H.STATE_KEYS) <= H.TOL_STEP_FP32, e61
     assert H.cell_mismatch_in_band(g61, r61, wl.h, 1e-4)[1] == 0
 
 
@@ -272,3 +272,31 @@ def test_conservation_sums(precision):
     assert cons["ke"] == pytest.approx(ref["ke"], rel=1e-9)
     # mass is carried exactly by the particles
     assert cons["mass"] == pytest.approx((wl.material["rho"] * wl.vol).sum(), rel=1e-6)
+
+
+def test_binning_with_mass_tile_crossing():
+    """1,600 particles cross a tile boundary in one step (more arrivals than
+    the shared-memory bucket holds): the incremental binning still equals the
+    stable sort of the keys, step after step, and P2G conserves the mass."""
+    h = 1.0
+    cells = W.box_cells((6, 0), (8, 8))
+    pos = np.repeat((cells + 0.5) * h, 200, axis=0)
+    rng = np.random.default_rng(3)
+    pos += rng.uniform(-0.45, 0.45, pos.shape) * h
+    vel = np.tile([0.9, 0.0], (pos.shape[0], 1))
+    wl = W.Workload(name="crossing", dim=2, ncells=(32, 8, 1), h=h, origin=(0, 0, 0), face_bc=(0,) * 6,
+                    face_mu=(0,) * 6, gravity=(0, 0, 0), dt=1.0, scheme=W.USL, precision=W.FP32_MIXED,
+                    material=dict(model=0, E=1e-6, nu=0.2, rho=1.0, phi=0, c=0, psi=0), pos=pos, vel=vel,
+                    vol=np.full(pos.shape[0], 1.0 / 200))
+    with mpm.Simulation(wl) as sim:
+        for step in range(4):
+            key, perm, td = sim.binning()
+            assert np.array_equal(perm, np.argsort(key, kind="stable").astype(np.int32)), step
+            sim.step(1)
+            assert sim.sync() == mpm.MPM_OK
+            cons, _ = sim.conservation()
+            assert cons["alive"] == wl.n
+            assert cons["mass"] == pytest.approx(wl.n * np.float32(1.0 / 200), rel=1e-6)
+        snap, _ = sim.read(fields=("pos",))
+    # everything moved about 4 x 0.9 cells to the right
+    assert abs(np.mean(snap["pos"][:, 0] - pos[:, 0]) - 3.6) < 0.05
