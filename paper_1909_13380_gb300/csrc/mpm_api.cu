@@ -166,7 +166,7 @@ BinLaunch bin_launch(mpm_ctx *h, int cur, uint32_t *keys_out, int32_t *perm_out)
   B.s = h->s;
   B.keys_out = keys_out;
   B.perm_out = perm_out;
-  B.grid = 2 * h->nsm;
+  B.grid = 8 * h->nsm;
   return B;
 }
 
@@ -190,7 +190,7 @@ cudaError_t enqueue_f32_step(mpm_ctx *h, int cur) {
   L.tile_start = h->s.tile_start[cur ^ 1];
   L.node_stride[0] = (int64_t)h->d.ncells[0] + 1;
   L.node_stride[1] = L.node_stride[0] * ((int64_t)h->d.ncells[1] + 1);
-  L.grid = 4 * h->nsm;
+  L.grid = 8 * h->nsm;
   L.ev = ev;
   return f32_step(L, h->st);
 }
@@ -309,6 +309,7 @@ mpm_status mpm_create_mesh(const mpm_mesh_desc *desc, mpm_handle *out) {
     if (e == cudaSuccess) e = cudaMalloc(&S.bucket_start, ti);
     if (e == cudaSuccess) e = cudaMalloc(&S.bucket_fill, ti);
     if (e == cudaSuccess) e = cudaMalloc(&S.active, ti);
+    if (e == cudaSuccess) e = cudaMalloc(&S.scan_tot, sizeof(int32_t) * 3 * ((nt + 1) / 1024 + 1));
     if (e == cudaSuccess) e = cudaMalloc(&S.ctr, sizeof(int32_t) * C_NCTR);
     for (int p = 0; p < 2 && e == cudaSuccess; ++p) e = cudaMemset(S.tile_start[p], 0, ti);
     if (e == cudaSuccess) e = cudaMemset(S.in_cnt, 0, ti);
@@ -781,7 +782,8 @@ mpm_status mpm_destroy(mpm_handle h) {
   destroy_graphs(h);
   StepBufs &S = h->s;
   void *ptrs[] = {h->bufmem[0], h->bufmem[1], S.keys_sorted, S.perm, S.tile_start[0], S.tile_start[1], S.in_cnt,
-                  S.out_cnt, S.bucket_start, S.bucket_fill, S.movers, S.bucket, S.bucket_sorted, S.active, S.ctr,
+                  S.out_cnt, S.bucket_start, S.bucket_fill, S.movers, S.bucket, S.bucket_sorted, S.active,
+                  S.scan_tot, S.ctr,
                   S.slots1, S.slots2, S.node_v[0], S.node_v[1], S.node_v[2], S.node_a[0], S.node_a[1], S.node_a[2],
                   h->keys2, h->perm2, h->sort_scratch, h->pmem64, h->nmem64, h->d_status, h->d_cons};
   for (void *p : ptrs)

@@ -12,7 +12,8 @@
 //   bin_movers  compares each stored particle's new key with the key it was
 //               binned under last step and lists the particles that changed
 //               tile (counts per tile in and out);
-//   bin_scan    one CTA: new tile ranges = old ranges - leavers + arrivals
+//   bin_scan_*  two passes over the tiles: new tile ranges = old ranges -
+//               leavers + arrivals
 //               (exclusive scan over tiles), arrival bucket offsets, the
 //               active tile list, counter resets;
 //   bin_bucket  groups the arrivals by destination tile;
@@ -35,8 +36,8 @@ namespace {
 constexpr int BT = 256;          // bin_tiles threads
 constexpr int BT_WARPS = BT / 32;
 constexpr int BUCKET_SMEM = 1024;
-constexpr int SCAN_T = 1024;
-constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_T = 256;
+constexpr int SCAN_ITEMS = 4;
 
 __global__ void bin_movers(const uint32_t *__restrict__ knew, const uint32_t *__restrict__ kold, int64_t n,
                            int ntiles, int32_t *__restrict__ in_cnt, int32_t *__restrict__ out_cnt,
@@ -82,65 +83,117 @@ __device__ __forceinline__ int cta_excl(int v, int *wsum, int &total) {
   return base + inc - v;
 }
 
-__global__ void __launch_bounds__(SCAN_T) bin_scan(int64_t n, int ntiles, const int32_t *__restrict__ old_start,
-                                                   int32_t *__restrict__ new_start, int32_t *__restrict__ in_cnt,
-                                                   int32_t *__restrict__ out_cnt, int32_t *__restrict__ bstart,
-                                                   int32_t *__restrict__ bfill, int32_t *__restrict__ active,
-                                                   int32_t *__restrict__ ctr) {
+// Per tile e (tiles plus the dead range): new count = old count - leavers +
+// arrivals; arrivals; active flag.
+__device__ __forceinline__ void tile_counts(int e, int ntiles, const int32_t *old_start, const int32_t *in_cnt,
+                                            const int32_t *out_cnt, int &cn, int &cb, int &ca) {
+  const int in = in_cnt[e], out = out_cnt[e];
+  cn = (old_start[e + 1] - old_start[e]) - out + in;
+  cb = in;
+  ca = (e < ntiles && cn > 0) ? 1 : 0;
+}
+
+// Scan over tiles, pass 1: block totals of (count, arrivals, active).
+__global__ void __launch_bounds__(SCAN_T) bin_scan_totals(int ntiles, const int32_t *__restrict__ old_start,
+                                                          const int32_t *__restrict__ in_cnt,
+                                                          const int32_t *__restrict__ out_cnt,
+                                                          int32_t *__restrict__ tot) {
   __shared__ int wsum[32];
-  int carry_n = 0, carry_b = 0, carry_a = 0;
-  const int m = ntiles + 1;  // tiles plus the dead range
-  for (int c0 = 0; c0 < m; c0 += SCAN_T * SCAN_ITEMS) {
-    int cn[SCAN_ITEMS], cb[SCAN_ITEMS], ca[SCAN_ITEMS];
-    int sn = 0, sb = 0, sa = 0;
-    const int e0 = c0 + threadIdx.x * SCAN_ITEMS;
+  const int m = ntiles + 1;
+  const int e0 = blockIdx.x * SCAN_T * SCAN_ITEMS + threadIdx.x * SCAN_ITEMS;
+  int sn = 0, sb = 0, sa = 0;
 #pragma unroll
-    for (int r = 0; r < SCAN_ITEMS; ++r) {
-      const int e = e0 + r;
-      cn[r] = cb[r] = ca[r] = 0;
-      if (e < m) {
-        const int in = in_cnt[e], out = out_cnt[e];
-        cn[r] = (old_start[e + 1] - old_start[e]) - out + in;
-        cb[r] = in;
-        ca[r] = (e < ntiles && cn[r] > 0) ? 1 : 0;
-        in_cnt[e] = 0;
-        out_cnt[e] = 0;
-        bfill[e] = 0;
-      }
-      sn += cn[r];
-      sb += cb[r];
-      sa += ca[r];
+  for (int r = 0; r < SCAN_ITEMS; ++r) {
+    const int e = e0 + r;
+    if (e < m) {
+      int cn, cb, ca;
+      tile_counts(e, ntiles, old_start, in_cnt, out_cnt, cn, cb, ca);
+      sn += cn;
+      sb += cb;
+      sa += ca;
     }
-    int tn, tb, ta;
-    int pn = cta_excl(sn, wsum, tn) + carry_n;
-    int pb = cta_excl(sb, wsum, tb) + carry_b;
-    int pa = cta_excl(sa, wsum, ta) + carry_a;
-#pragma unroll
-    for (int r = 0; r < SCAN_ITEMS; ++r) {
-      const int e = e0 + r;
-      if (e < m) {
-        new_start[e] = pn;
-        bstart[e] = pb;
-        if (ca[r]) active[pa] = e;
-      }
-      pn += cn[r];
-      pb += cb[r];
-      pa += ca[r];
-    }
-    carry_n += tn;
-    carry_b += tb;
-    carry_a += ta;
   }
+  int tn, tb, ta;
+  cta_excl(sn, wsum, tn);
+  cta_excl(sb, wsum, tb);
+  cta_excl(sa, wsum, ta);
   if (threadIdx.x == 0) {
-    new_start[m] = (int32_t)n;
-    bstart[m] = carry_b;
-    const int dead_start = new_start[ntiles];
-    ctr[C_ACTIVE] = carry_a;
-    ctr[C_DEAD_START] = dead_start;
-    ctr[C_BIN_ITEMS] = carry_a + ((int64_t)dead_start < n ? 1 : 0);
+    tot[3 * blockIdx.x + 0] = tn;
+    tot[3 * blockIdx.x + 1] = tb;
+    tot[3 * blockIdx.x + 2] = ta;
+  }
+}
+
+// Scan over tiles, pass 2: each block adds the totals of the blocks before
+// it, scans its own tiles, writes new ranges, arrival offsets and the active
+// list, and clears the per-tile counters for the next step.
+__global__ void __launch_bounds__(SCAN_T) bin_scan_apply(int64_t n, int ntiles, const int32_t *__restrict__ old_start,
+                                                         int32_t *__restrict__ new_start, int32_t *__restrict__ in_cnt,
+                                                         int32_t *__restrict__ out_cnt, int32_t *__restrict__ bstart,
+                                                         int32_t *__restrict__ bfill, int32_t *__restrict__ active,
+                                                         const int32_t *__restrict__ tot, int32_t *__restrict__ ctr) {
+  __shared__ int wsum[32];
+  const int m = ntiles + 1;
+  int on = 0, ob = 0, oa = 0;
+  for (int b = threadIdx.x; b < (int)blockIdx.x; b += SCAN_T) {
+    on += tot[3 * b];
+    ob += tot[3 * b + 1];
+    oa += tot[3 * b + 2];
+  }
+  int t0, t1, t2;
+  cta_excl(on, wsum, t0);
+  cta_excl(ob, wsum, t1);
+  cta_excl(oa, wsum, t2);
+  on = t0;
+  ob = t1;
+  oa = t2;
+  const int e0 = blockIdx.x * SCAN_T * SCAN_ITEMS + threadIdx.x * SCAN_ITEMS;
+  int cn[SCAN_ITEMS], cb[SCAN_ITEMS], ca[SCAN_ITEMS];
+  int sn = 0, sb = 0, sa = 0;
+#pragma unroll
+  for (int r = 0; r < SCAN_ITEMS; ++r) {
+    const int e = e0 + r;
+    cn[r] = cb[r] = ca[r] = 0;
+    if (e < m) tile_counts(e, ntiles, old_start, in_cnt, out_cnt, cn[r], cb[r], ca[r]);
+    sn += cn[r];
+    sb += cb[r];
+    sa += ca[r];
+  }
+  int tn, tb, ta;
+  int pn = cta_excl(sn, wsum, tn) + on;
+  int pb = cta_excl(sb, wsum, tb) + ob;
+  int pa = cta_excl(sa, wsum, ta) + oa;
+#pragma unroll
+  for (int r = 0; r < SCAN_ITEMS; ++r) {
+    const int e = e0 + r;
+    if (e < m) {
+      new_start[e] = pn;
+      bstart[e] = pb;
+      if (ca[r]) active[pa] = e;
+      in_cnt[e] = 0;
+      out_cnt[e] = 0;
+      bfill[e] = 0;
+    }
+    pn += cn[r];
+    pb += cb[r];
+    pa += ca[r];
+  }
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
     ctr[C_MOVERS_SNAP] = ctr[C_MOVERS];
     ctr[C_MOVERS] = 0;
     ctr[C_WORK_BIN] = ctr[C_WORK_P2G] = ctr[C_WORK_NODE] = ctr[C_WORK_P2G2] = ctr[C_WORK_NODE2] = 0;
+  }
+  if (blockIdx.x == gridDim.x - 1) {
+    __syncthreads();  // new_start of the dead range written by this block
+    if (threadIdx.x == 0) {
+      const int nact = oa + ta;
+      new_start[m] = (int32_t)n;
+      bstart[m] = ob + tb;
+      const int dead_start = new_start[ntiles];
+      ctr[C_ACTIVE] = nact;
+      ctr[C_DEAD_START] = dead_start;
+      ctr[C_BIN_ITEMS] = nact + ((int64_t)dead_start < n ? 1 : 0);
+    }
   }
 }
 
@@ -320,8 +373,10 @@ cudaError_t bin_step(const BinLaunch &B, cudaStream_t st) {
   if (B.n <= 0) return cudaSuccess;
   const int gridp = (int)((B.n + 255) / 256 < B.grid * 4 ? (B.n + 255) / 256 : B.grid * 4);
   bin_movers<<<gridp, 256, 0, st>>>(B.knew, B.kold, B.n, B.ntiles, B.s.in_cnt, B.s.out_cnt, B.s.movers, B.s.ctr);
-  bin_scan<<<1, SCAN_T, 0, st>>>(B.n, B.ntiles, B.old_start, B.new_start, B.s.in_cnt, B.s.out_cnt,
-                                 B.s.bucket_start, B.s.bucket_fill, B.s.active, B.s.ctr);
+  const int sblocks = (B.ntiles + 1 + SCAN_T * SCAN_ITEMS - 1) / (SCAN_T * SCAN_ITEMS);
+  bin_scan_totals<<<sblocks, SCAN_T, 0, st>>>(B.ntiles, B.old_start, B.s.in_cnt, B.s.out_cnt, B.s.scan_tot);
+  bin_scan_apply<<<sblocks, SCAN_T, 0, st>>>(B.n, B.ntiles, B.old_start, B.new_start, B.s.in_cnt, B.s.out_cnt,
+                                             B.s.bucket_start, B.s.bucket_fill, B.s.active, B.s.scan_tot, B.s.ctr);
   bin_bucket<<<B.grid, 256, 0, st>>>(B.knew, B.ntiles, B.s.movers, B.s.bucket_start, B.s.bucket_fill, B.s.bucket,
                                      B.s.ctr);
   bin_tiles<<<B.grid, BT, 0, st>>>(B);

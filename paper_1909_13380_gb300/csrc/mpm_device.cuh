@@ -169,7 +169,8 @@ __device__ __forceinline__ void jacobi_rot(T A[3][3], T Q[3][3]) {
   if (apq == T(0)) return;
   const T theta = (A[q][q] - A[p][p]) / (T(2) * apq);
   const T t = (theta >= T(0) ? T(1) : T(-1)) / (fabs(theta) + sqrt(theta * theta + T(1)));
-  const T c = T(1) / sqrt(t * t + T(1));
+  // any c, s with c^2 + s^2 = 1 keep Q orthogonal; rsqrt is exact enough here
+  const T c = sizeof(T) == 4 ? (T)rsqrtf((float)(t * t + T(1))) : T(1) / sqrt(t * t + T(1));
   const T s = t * c;
   const T aop = A[o][p], aoq = A[o][q];
   A[p][p] -= t * apq;
@@ -192,8 +193,11 @@ __device__ __forceinline__ void eig_sym3(const T s[6], T lam[3], T Q[3][3]) {
   for (int r = 0; r < 3; ++r)
 #pragma unroll
     for (int c = 0; c < 3; ++c) Q[r][c] = (r == c) ? T(1) : T(0);
-  const T tol = sizeof(T) == 4 ? T(1e-13) : T(1e-32);
-  for (int sweep = 0; sweep < (sizeof(T) == 4 ? 10 : 20); ++sweep) {
+  // stop when the off-diagonal mass is below (1e-6)^2 (FP32) or (1e-16)^2
+  // (FP64) of the diagonal; Jacobi converges quadratically, so the sweep
+  // that crosses the bound leaves far less in practice
+  const T tol = sizeof(T) == 4 ? T(1e-12) : T(1e-32);
+  for (int sweep = 0; sweep < (sizeof(T) == 4 ? 6 : 20); ++sweep) {
     const T off = A[0][1] * A[0][1] + A[0][2] * A[0][2] + A[1][2] * A[1][2];
     const T dia = A[0][0] * A[0][0] + A[1][1] * A[1][1] + A[2][2] * A[2][2];
     if (off <= tol * dia || off == T(0)) break;
@@ -296,6 +300,29 @@ __device__ __forceinline__ int mc_principal(const MatConst<T> &m, T c, const T s
   return branch;
 }
 
+// Clearly inside the yield surface?  Principal stresses from the closed form
+// of a symmetric 3x3 (mean p, J2, J3 and the Lode angle: s_k = p + 2 sqrt(J2/3)
+// cos(theta - 2 pi k / 3)), then the yield function with a margin larger than
+// the error of that form in FP32 (worst near repeated eigenvalues, where the
+// arc-cosine loses about half the digits).  Only a cheap filter: a trial that
+// is not clearly elastic goes through the full Jacobi return, so the result
+// is the same as without the filter.
+__device__ __forceinline__ bool clearly_elastic(const MatConst<float> &m, float c, const float s[6]) {
+  const float p = (s[0] + s[1] + s[2]) * (1.f / 3.f);
+  const float d0 = s[0] - p, d1 = s[1] - p, d2 = s[2] - p;
+  const float j2 = 0.5f * (d0 * d0 + d1 * d1 + d2 * d2) + s[3] * s[3] + s[4] * s[4] + s[5] * s[5];
+  const float j3 = d0 * (d1 * d2 - s[4] * s[4]) - s[3] * (s[3] * d2 - s[4] * s[5]) + s[5] * (s[3] * s[4] - d1 * s[5]);
+  const float r = sqrtf(j2 * (1.f / 3.f));
+  float c3 = r > 0.f ? j3 / (2.f * r * r * r) : 0.f;
+  c3 = fminf(1.f, fmaxf(-1.f, c3));
+  const float th = acosf(c3) * (1.f / 3.f);
+  const float s1 = p + 2.f * r * cosf(th);
+  const float s3 = p + 2.f * r * cosf(th + 2.0943951f);
+  const float f = (s1 - s3) + (s1 + s3) * m.sphi - 2.f * c * m.cphi;
+  const float margin = 4e-3f * (r + fabsf(p)) + 1e-3f * c;
+  return f < -margin;
+}
+
 // Trial stress -> returned stress (Voigt 6) for Mohr-Coulomb in precision T.
 template <typename T>
 __device__ __forceinline__ int mc_return(const MatConst<T> &m, T c, const T st[6], T out[6], T &depsp) {
@@ -361,6 +388,11 @@ __device__ __forceinline__ void material_update(const MatConst<float> &m, const 
   float st[6];
   elastic_trial<float>(m, sig, de, st);
   if (m.model != 1) {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) sig[i] = st[i];
+    return;
+  }
+  if (clearly_elastic(m, c, st)) {
 #pragma unroll
     for (int i = 0; i < 6; ++i) sig[i] = st[i];
     return;

@@ -247,16 +247,18 @@ __global__ void __launch_bounds__(P2G_T, 4) p2g_tile(TileArgs A) {
           }
         }
         __syncwarp();
-        // lane = value index: sum the batch in particle order, flush at run ends
+        // lane = value index: sum the batch in particle order (at most 32
+        // terms, plain FP32), flush at run ends
         const int v = pass * 32 + lane;
-        TwoAcc<float> acc;
-        acc.init();
+        const float *row = wst + lane * 33;
+        float acc = 0.f;
+#pragma unroll 8
         for (int k = 0; k < nb; ++k) {
-          if (v < NV) acc.add(wst[lane * 33 + k]);
+          acc += row[k];
           if ((ends >> k) & 1u) {
             const int ck = __shfl_sync(0xffffffffu, lc, k);
-            if (v < NV) cellP[ck * NV + v] += acc.value();
-            acc.init();
+            if (v < NV) cellP[ck * NV + v] += acc;
+            acc = 0.f;
           }
         }
         __syncwarp();
@@ -411,7 +413,7 @@ __global__ void __launch_bounds__(NODE_T) node_tile(TileArgs A) {
 // G2P: one thread per particle in binning order
 // ---------------------------------------------------------------------------
 template <int D, int GMODE>
-__global__ void __launch_bounds__(G2P_T) g2p(TileArgs A, int64_t n) {
+__global__ void __launch_bounds__(G2P_T, 3) g2p(TileArgs A, int64_t n) {
   constexpr int NC = 1 << D;
   constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ;
   constexpr int NS = nstress<D>();
