@@ -196,6 +196,28 @@ mpm_status mpm_destroy(mpm_handle h);
 mpm_status mpm_sort_keys(const uint32_t *d_keys, int32_t *d_perm, int64_t n, int32_t key_bits,
                          void *stream);
 
+/* The same stable key sort as mpm_sort_keys for callers that cannot
+ * allocate device memory: for example a host program whose own allocator
+ * already holds all of the GPU's free memory, or a loop that must not
+ * allocate once it is running.  The paper has no counterpart; this is a
+ * service of this library.
+ *   The scratch is a fixed array in the library's device memory (about
+ *   22 MiB, held on every GPU that loads the library until the process
+ *   exits), so this call allocates and frees nothing.  n above
+ *   MPM_SORT_STATIC_MAX_KEYS is rejected with MPM_ERR_ARG before any device
+ *   work.  The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.
+ *   The call only enqueues work on `stream` and returns; d_perm is ready
+ *   when the stream reaches that point.  All calls share the one array, so
+ *   calls whose work overlaps on the GPU (different streams, or different
+ *   host threads) race and give wrong results: order them on one stream.
+ *   Every scratch word is written before it is read, so nothing needs to
+ *   be cleared between calls. */
+#define MPM_SORT_STATIC_MAX_KEYS (1 << 20)
+mpm_status mpm_sort_keys_static(const uint32_t *d_keys, int32_t *d_perm, int64_t n, int32_t key_bits,
+                                void *stream);
+
 /* Material-point stress update on the GPU (CODE OVERVIEW: Material, "the
  * updated stresses for a given strain tensor"), for n independent points.
  *   sig, deps   n*6 host doubles: stress before, strain increment

@@ -18,7 +18,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmpm.so")
-SOURCES = ["mpm_api.cu", "mpm_sort.cu", "mpm_bin.cu", "mpm_fp32.cu", "mpm_fp64.cu"]
+SOURCES = ["mpm_api.cu", "mpm_sort.cu", "mpm_bin.cu", "mpm_fp32.cu", "mpm_fp64.cu", "mpm_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

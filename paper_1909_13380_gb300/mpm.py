@@ -97,6 +97,7 @@ def load():
             "mpm_read_binning": [vp, i32p, i32p, i32p],
             "mpm_destroy": [vp],
             "mpm_sort_keys": [vp, vp, C.c_int64, C.c_int32, vp],
+            "mpm_sort_keys_static": [vp, vp, C.c_int64, C.c_int32, vp],
             "mpm_material_update": [C.POINTER(mpm_material), C.c_int32, C.c_int64, dp, dp, dp, dp, dp, vp],
             "mpm_set_phase_timing": [vp, C.c_int32],
             "mpm_phase_times": [vp, C.POINTER(C.c_float), i32p],
@@ -258,6 +259,20 @@ def mpm_sort_keys(d_keys, d_perm, n: int, key_bits: int, stream=None):
     st = load().mpm_sort_keys(C.c_void_p(kp), C.c_void_p(pp), int(n), int(key_bits),
                               stream if stream is not None else current_stream())
     _check(None, st, "mpm_sort_keys")
+
+
+MPM_SORT_STATIC_MAX_KEYS = 1 << 20
+
+
+def mpm_sort_keys_static(d_keys, d_perm, n: int, key_bits: int, stream=None):
+    """The sort without any device allocation (fixed library scratch, at most
+    MPM_SORT_STATIC_MAX_KEYS keys).  Only enqueues on the stream: synchronise
+    before reading d_perm."""
+    kp = d_keys.data_ptr() if hasattr(d_keys, "data_ptr") else int(d_keys)
+    pp = d_perm.data_ptr() if hasattr(d_perm, "data_ptr") else int(d_perm)
+    st = load().mpm_sort_keys_static(C.c_void_p(kp), C.c_void_p(pp), int(n), int(key_bits),
+                                     stream if stream is not None else current_stream())
+    _check(None, st, "mpm_sort_keys_static")
 
 
 def mpm_material_update(mat: mpm_material, precision: int, sig, deps, cohesion=None, stream=None):
