@@ -316,10 +316,11 @@ mpm_status mpm_create_mesh(const mpm_mesh_desc *desc, mpm_handle *out) {
     if (e == cudaSuccess) e = cudaMemset(S.out_cnt, 0, ti);
     if (e == cudaSuccess) e = cudaMemset(S.bucket_fill, 0, ti);
     if (e == cudaSuccess) e = cudaMemset(S.ctr, 0, sizeof(int32_t) * C_NCTR);
-    for (int k = 0; k < d.dim && e == cudaSuccess; ++k) {
-      e = cudaMalloc(&S.node_v[k], sizeof(float) * nn);
-      if (e == cudaSuccess) e = cudaMalloc(&S.node_a[k], sizeof(float) * nn);
+    if (2 * nn >= ((int64_t)1 << 31)) {  // node records are indexed with 32-bit ints
+      mpm_destroy(h);
+      return MPM_ERR_ARG;
     }
+    if (e == cudaSuccess) e = cudaMalloc(&S.node, sizeof(float4) * nn * (d.dim == 3 ? 2 : 1));
     if (e == cudaSuccess) e = f32_prepare(d.dim);
   } else if (e == cudaSuccess) {
     h->L64.nnodes = nn;
@@ -784,7 +785,7 @@ mpm_status mpm_destroy(mpm_handle h) {
   void *ptrs[] = {h->bufmem[0], h->bufmem[1], S.keys_sorted, S.perm, S.tile_start[0], S.tile_start[1], S.in_cnt,
                   S.out_cnt, S.bucket_start, S.bucket_fill, S.movers, S.bucket, S.bucket_sorted, S.active,
                   S.scan_tot, S.ctr,
-                  S.slots1, S.slots2, S.node_v[0], S.node_v[1], S.node_v[2], S.node_a[0], S.node_a[1], S.node_a[2],
+                  S.slots1, S.slots2, S.node,
                   h->keys2, h->perm2, h->sort_scratch, h->pmem64, h->nmem64, h->d_status, h->d_cons};
   for (void *p : ptrs)
     if (p) cudaFree(p);

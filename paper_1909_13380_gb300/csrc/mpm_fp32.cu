@@ -50,9 +50,8 @@ struct TileArgs {
   const float *slots2;
   float *slots_out;
   int nch1;
-  float *nv[3];
-  float *na[3];
-  int64_t ns0, ns1;  // node strides
+  float4 *node;      // dense node values (layout in StepBufs::node)
+  int ns0, ns1;      // node strides: (nx+1), (nx+1)(ny+1)
   MatConst<float> mat;
   MatConst<double> matd;
 };
@@ -398,11 +397,13 @@ __global__ void __launch_bounds__(NODE_T) node_tile(TileArgs A) {
           bc_full<D, float>(faces, g.bc, g.mu, g.dt, v, a, vn);
         }
       }
-      const int64_t gi = I[0] + A.ns0 * I[1] + A.ns1 * I[2];
-#pragma unroll
-      for (int k = 0; k < D; ++k) {
-        A.nv[k][gi] = NMODE == NODE_USF_V ? v[k] : vn[k];
-        if (NMODE != NODE_USF_V) A.na[k][gi] = a[k];
+      const int gi = I[0] + A.ns0 * I[1] + A.ns1 * I[2];
+      const float *w = NMODE == NODE_USF_V ? v : vn;
+      if (D == 3) {
+        A.node[2 * gi] = make_float4(w[0], w[1], w[D - 1], 0.f);
+        A.node[2 * gi + 1] = make_float4(a[0], a[1], a[D - 1], 0.f);
+      } else {
+        A.node[gi] = make_float4(w[0], w[1], a[0], a[1]);
       }
     }
     __syncthreads();
@@ -462,21 +463,39 @@ __global__ void __launch_bounds__(G2P_T, 3) g2p(TileArgs A, int64_t n) {
 #pragma unroll
     for (int l = 0; l < D; ++l) L[k][l] = 0.f;
   }
-  const int64_t gi0 = cell[0] + A.ns0 * cell[1] + A.ns1 * cell[2];
+  const int gi0 = cell[0] + A.ns0 * cell[1] + A.ns1 * cell[2];
 #pragma unroll
   for (int a = 0; a < NC; ++a) {
     float N, G[D];
     corner_shape<D>(a, w0, w1, g.inv_h, N, G);
-    const int64_t gi = gi0 + (a & 1) + A.ns0 * ((a >> 1) & 1) + (D == 3 ? A.ns1 * ((a >> 2) & 1) : 0);
+    const int gi = gi0 + (a & 1) + A.ns0 * ((a >> 1) & 1) + (D == 3 ? A.ns1 * ((a >> 2) & 1) : 0);
+    float nv[D], na[D];
+    if (D == 3) {
+      const float4 r0 = A.node[2 * gi];
+      nv[0] = r0.x;
+      nv[1] = r0.y;
+      nv[D - 1] = r0.z;
+      if (GMODE != G2P_USF_STRESS) {
+        const float4 r1 = A.node[2 * gi + 1];
+        na[0] = r1.x;
+        na[1] = r1.y;
+        na[D - 1] = r1.z;
+      }
+    } else {
+      const float4 r0 = A.node[gi];
+      nv[0] = r0.x;
+      nv[1] = r0.y;
+      na[0] = r0.z;
+      na[1] = r0.w;
+    }
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-      const float vk = A.nv[k][gi];
       if (GMODE != G2P_USF_STRESS) {
-        dv[k] += N * A.na[k][gi];
-        vb[k] += N * vk;
+        dv[k] += N * na[k];
+        vb[k] += N * nv[k];
       }
 #pragma unroll
-      for (int l = 0; l < D; ++l) L[k][l] += vk * G[l];
+      for (int l = 0; l < D; ++l) L[k][l] += nv[k] * G[l];
     }
   }
 
@@ -588,12 +607,9 @@ TileArgs make_args(const F32Launch &L, int work_slot) {
   a.slots2 = L.s.slots2;
   a.slots_out = nullptr;
   a.nch1 = 0;
-  for (int k = 0; k < 3; ++k) {
-    a.nv[k] = L.s.node_v[k];
-    a.na[k] = L.s.node_a[k];
-  }
-  a.ns0 = L.node_stride[0];
-  a.ns1 = L.node_stride[1];
+  a.node = L.s.node;
+  a.ns0 = (int)L.node_stride[0];
+  a.ns1 = (int)L.node_stride[1];
   a.mat = L.mat;
   a.matd = L.matd;
   return a;

@@ -97,8 +97,9 @@ struct StepBufs {
   int32_t *ctr;            // C_NCTR counters
   float *slots1;           // ntiles * box * channels (P2G USL / MOM)
   float *slots2;           // ntiles * box * D        (P2G FORCE, USF)
-  float *node_v[3];        // dense node arrays: v' (or v in the USF velocity stage)
-  float *node_a[3];        // dense node arrays: a
+  // dense node values, one 16-byte record per node in 2D (v'x v'y ax ay) and
+  // two in 3D (v'x v'y v'z -, ax ay az -); v' is v in the USF velocity stage
+  float4 *node;
 };
 
 // --- radix sort (mpm_sort.cu) ---------------------------------------------
