@@ -179,6 +179,43 @@ mpm_status mpm_read_binning(mpm_handle h, int32_t *key, int32_t *perm, int32_t *
 mpm_status mpm_set_phase_timing(mpm_handle h, int32_t enable);
 mpm_status mpm_phase_times(mpm_handle h, float *ms, int32_t *nphase);
 
+/* Estimated device bytes a FP32_MIXED or FP64_PLAIN mesh of desc holding n
+ * particles (with per-particle cohesion if has_cohesion) allocates; for
+ * admission control by free memory. */
+mpm_status mpm_footprint(const mpm_mesh_desc *desc, int64_t n, int32_t has_cohesion, int64_t *bytes);
+
+/* ---- batched steps of independent meshes (serving) ---------------------
+ * A batch advances many independent FP32_MIXED meshes together: every phase
+ * of the step is one kernel launch over all admitted meshes (their tiles and
+ * particles form one work list), and a batched step is one CUDA graph
+ * replay.  Meshes share no data, so each mesh's result is bit-identical to
+ * stepping it alone.  The paper has no batching; it runs one simulation per
+ * process (CODE OVERVIEW, DATA STRUCTURES).
+ *   mpm_batch_create   stream: cudaStream_t for all batch work (NULL: a
+ *                      private stream)
+ *   mpm_batch_admit    adds an idle FP32_MIXED mesh (its pending work is
+ *                      finished first); from then on the mesh's own calls
+ *                      run on the batch stream and mpm_step on it returns
+ *                      MPM_ERR_STATE until it is evicted.  *slot receives a
+ *                      stable slot id.
+ *   mpm_batch_evict    removes the mesh of a slot (after the batch's pending
+ *                      work); the mesh keeps its state and can be read,
+ *                      stepped alone or admitted again.
+ *   mpm_batch_step     enqueues nsteps batched steps of every admitted mesh.
+ *   mpm_batch_poll     synchronises and writes, for slots 0..nslots-1, the
+ *                      latched status of the slot's mesh (MPM_OK,
+ *                      MPM_ERR_LEFT_MESH, MPM_ERR_NONFINITE) or
+ *                      MPM_ERR_STATE for an empty slot.
+ *   mpm_batch_destroy  evicts every mesh (they stay valid) and frees the batch.
+ * A batch is not thread-safe. */
+typedef struct mpm_batch_ctx *mpm_batch;
+mpm_status mpm_batch_create(void *stream, mpm_batch *out);
+mpm_status mpm_batch_admit(mpm_batch b, mpm_handle mesh, int32_t *slot);
+mpm_status mpm_batch_evict(mpm_batch b, int32_t slot);
+mpm_status mpm_batch_step(mpm_batch b, int64_t nsteps);
+mpm_status mpm_batch_poll(mpm_batch b, int32_t nslots, int32_t *slot_status);
+mpm_status mpm_batch_destroy(mpm_batch b);
+
 /* Human-readable description of the last error on h (never NULL). */
 const char *mpm_last_error(mpm_handle h);
 

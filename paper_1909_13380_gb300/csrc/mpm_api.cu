@@ -4,9 +4,10 @@
 // computes each particle's initial cell on the host in FP64 (cell =
 // floor((x - origin)/h) per axis; the offset from the cell centre, in cell
 // units, is rounded to FP32 for the mixed path), bins the particles once with
-// a full stable radix sort when they are added, enqueues steps on the
-// handle's stream (replaying a captured CUDA graph per step when the stream
-// allows capture), and converts the state back to FP64 in insertion order.
+// a full stable radix sort when they are added, and enqueues steps.  The FP32
+// kernels run over a table of instances: a mesh stepped alone is a group of
+// one, a batch groups its meshes by dimension and scheme.  A step (or batched
+// step) is replayed from a captured CUDA graph when the stream allows capture.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -21,6 +22,27 @@
 
 using namespace mpm;
 
+namespace {
+
+// Device tables of one group of instances (two step parities).
+struct GroupDev {
+  int ninst = 0, cap = 0;
+  InstArgs *tab[2] = {nullptr, nullptr};
+  int32_t *pfx = nullptr;     // pblk | sblk | mblk | bin_items | act_items (cap + 1 each) | work
+  int32_t *status = nullptr;  // cap
+  GroupArgs ga[2];
+};
+
+void free_group(GroupDev &g) {
+  for (int p = 0; p < 2; ++p)
+    if (g.tab[p]) cudaFree(g.tab[p]);
+  if (g.pfx) cudaFree(g.pfx);
+  if (g.status) cudaFree(g.status);
+  g = GroupDev();
+}
+
+}  // namespace
+
 struct mpm_ctx {
   mpm_mesh_desc d;
   mpm_material mat;
@@ -28,6 +50,8 @@ struct mpm_ctx {
   bool has_coh = false;
   bool own_stream = false;
   cudaStream_t st = nullptr;
+  cudaStream_t st_saved = nullptr;  // own stream while admitted to a batch
+  mpm_batch_ctx *batch = nullptr;
   int64_t n = 0, cap = 0;
   int nsm = 152;
   std::string err;
@@ -43,6 +67,9 @@ struct mpm_ctx {
   uint32_t *keys2 = nullptr;  // binning outputs of mpm_read_binning
   int32_t *perm2 = nullptr;
   void *sort_scratch = nullptr;
+  GroupDev grp;       // this mesh as a group of one (tables indexed by absolute parity)
+  GroupDev grp_bin;   // the same with scratch binning outputs (mpm_read_binning)
+  bool grp_valid = false;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   bool timing = false;
   bool timed_step = false;
@@ -54,6 +81,23 @@ struct mpm_ctx {
   // shared
   int32_t *d_status = nullptr;  // FP64 path status word (FP32 path: s.ctr[C_STATUS])
   double *d_cons = nullptr;     // 8 results + partials
+};
+
+struct mpm_batch_ctx {
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  int nsm = 152;
+  std::vector<mpm_ctx *> slots;  // nullptr: empty slot
+  struct Group {
+    int dim, scheme;
+    std::vector<mpm_ctx *> mem;
+    std::vector<int> slot;
+    GroupDev dev;
+  };
+  std::vector<Group> groups;
+  bool dirty = true;
+  int bpar = 0;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -79,29 +123,18 @@ mpm_status cuda_fail(mpm_ctx *h, cudaError_t e, const char *where) {
 
 size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
 
-int nfields32(int dim, bool coh) {
-  // off[D] vel[D] sig[NS] eps[NS] mass jm1 epsp (coh)
-  const int ns = dim == 3 ? 6 : 4;
-  return 2 * dim + 2 * ns + 3 + (coh ? 1 : 0);
+// One allocation holds the PBUF_FIELDS fields (the last one only with
+// per-particle cohesion), each al256(4 cap) bytes apart.
+size_t buf32_bytes(int dim, bool coh, int64_t cap) {
+  (void)dim;
+  return al256(4 * cap) * (PBUF_FIELDS - (coh ? 0 : 1));
 }
 
-size_t buf32_bytes(int dim, bool coh, int64_t cap) { return al256(4 * cap) * (2 + nfields32(dim, coh)); }
-
 void carve32(void *mem, int dim, bool coh, int64_t cap, PBuf &b) {
-  char *p = (char *)mem;
-  const size_t f = al256(4 * cap);
-  memset(&b, 0, sizeof(b));
-  b.key = (uint32_t *)p; p += f;
-  b.id = (int32_t *)p; p += f;
-  for (int k = 0; k < dim; ++k) { b.off[k] = (float *)p; p += f; }
-  for (int k = 0; k < dim; ++k) { b.vel[k] = (float *)p; p += f; }
-  const int ns = dim == 3 ? 6 : 4;
-  for (int i = 0; i < ns; ++i) { b.sig[i] = (float *)p; p += f; }
-  for (int i = 0; i < ns; ++i) { b.eps[i] = (float *)p; p += f; }
-  b.mass = (float *)p; p += f;
-  b.jm1 = (float *)p; p += f;
-  b.epsp = (float *)p; p += f;
-  b.coh = coh ? (float *)p : nullptr;
+  (void)dim;
+  b.base = (char *)mem;
+  b.stride = (int64_t)al256(4 * cap);
+  b.has_coh = coh ? 1 : 0;
 }
 
 int nfields64(int dim, bool coh) {
@@ -142,57 +175,100 @@ MatConst<T> mat_const(const mpm_material &m) {
   return c;
 }
 
-void destroy_graphs(mpm_ctx *h) {
-  for (int i = 0; i < 2; ++i)
-    if (h->graph[i]) {
-      cudaGraphExecDestroy(h->graph[i]);
-      h->graph[i] = nullptr;
-    }
-}
-
 int tile_dim(int dim, int k) {
   if (dim == 3) return k == 0 ? Tile<3>::TX : k == 1 ? Tile<3>::TY : Tile<3>::TZ;
   return k == 0 ? Tile<2>::TX : k == 1 ? Tile<2>::TY : 1;
 }
 
-BinLaunch bin_launch(mpm_ctx *h, int cur, uint32_t *keys_out, int32_t *perm_out) {
-  BinLaunch B;
-  B.n = h->n;
-  B.ntiles = h->geo.ntiles;
-  B.knew = h->buf[cur].key;
-  B.kold = h->s.keys_sorted;
-  B.old_start = h->s.tile_start[cur];
-  B.new_start = h->s.tile_start[cur ^ 1];
-  B.s = h->s;
-  B.keys_out = keys_out;
-  B.perm_out = perm_out;
-  B.grid = 8 * h->nsm;
-  return B;
+void destroy_graphs(cudaGraphExec_t g[2]) {
+  for (int i = 0; i < 2; ++i)
+    if (g[i]) {
+      cudaGraphExecDestroy(g[i]);
+      g[i] = nullptr;
+    }
 }
 
-// One FP32 step from buf[cur] to buf[cur ^ 1] (enqueue only).
-cudaError_t enqueue_f32_step(mpm_ctx *h, int cur) {
+// Instance arguments of mesh h whose state is in buf[c].
+InstArgs make_inst(const mpm_ctx *h, int c, bool scratch_out) {
+  InstArgs I;
+  memset(&I, 0, sizeof(I));
+  I.n = h->n;
+  I.ntiles = h->geo.ntiles;
+  I.geo = h->geo;
+  I.mat = mat_const<float>(h->mat);
+  I.matd = mat_const<double>(h->mat);
+  I.A = h->buf[c];
+  I.B = h->buf[c ^ 1];
+  I.s = h->s;
+  I.old_start = h->s.tile_start[c];
+  I.new_start = h->s.tile_start[c ^ 1];
+  I.keys_out = scratch_out ? h->keys2 : h->s.keys_sorted;
+  I.perm_out = scratch_out ? h->perm2 : h->s.perm;
+  I.ns0 = h->d.ncells[0] + 1;
+  I.ns1 = I.ns0 * (h->d.ncells[1] + 1);
+  return I;
+}
+
+// Upload the tables of a group.  relative: table p holds each member at its
+// current parity flipped p times (batches); otherwise table p holds every
+// member at absolute parity p (a mesh stepped alone).
+cudaError_t build_group(GroupDev &g, const std::vector<mpm_ctx *> &mem, bool relative, bool scratch_out, int nsm,
+                        cudaStream_t st) {
+  const int n = (int)mem.size();
   cudaError_t e;
-  cudaEvent_t *ev = h->timing ? h->ev : nullptr;
-  if ((e = phase_mark(ev, 0, h->st)) != cudaSuccess) return e;
-  if ((e = bin_step(bin_launch(h, cur, h->s.keys_sorted, h->s.perm), h->st)) != cudaSuccess) return e;
-  if ((e = phase_mark(ev, 1, h->st)) != cudaSuccess) return e;
-  F32Launch L;
-  L.dim = h->d.dim;
-  L.scheme = h->d.scheme;
-  L.n = h->n;
-  L.geo = h->geo;
-  L.mat = mat_const<float>(h->mat);
-  L.matd = mat_const<double>(h->mat);
-  L.A = h->buf[cur];
-  L.B = h->buf[cur ^ 1];
-  L.s = h->s;
-  L.tile_start = h->s.tile_start[cur ^ 1];
-  L.node_stride[0] = (int64_t)h->d.ncells[0] + 1;
-  L.node_stride[1] = L.node_stride[0] * ((int64_t)h->d.ncells[1] + 1);
-  L.grid = 8 * h->nsm;
-  L.ev = ev;
-  return f32_step(L, h->st);
+  if (n > g.cap) {
+    free_group(g);
+    const int cap = n < 8 ? 8 : n;
+    for (int p = 0; p < 2; ++p)
+      if ((e = cudaMalloc(&g.tab[p], sizeof(InstArgs) * cap)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&g.pfx, sizeof(int32_t) * (5 * (cap + 1) + W_COUNT))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&g.status, sizeof(int32_t) * cap)) != cudaSuccess) return e;
+    if ((e = cudaMemset(g.pfx, 0, sizeof(int32_t) * (5 * (cap + 1) + W_COUNT))) != cudaSuccess) return e;
+    g.cap = cap;
+  }
+  g.ninst = n;
+  std::vector<InstArgs> tab[2];
+  std::vector<int32_t> pre(3 * (g.cap + 1), 0);
+  int32_t *pb = pre.data(), *sb = pb + (g.cap + 1), *mb = sb + (g.cap + 1);
+  for (int i = 0; i < n; ++i) {
+    const mpm_ctx *h = mem[i];
+    for (int p = 0; p < 2; ++p) tab[p].push_back(make_inst(h, relative ? (h->cur ^ p) : p, scratch_out));
+    pb[i + 1] = pb[i] + (int32_t)((h->n + 255) / 256);
+    sb[i + 1] = sb[i] + (h->geo.ntiles + 1 + 1023) / 1024;
+    int64_t m = h->n / 65536;
+    mb[i + 1] = mb[i] + (int32_t)(m < 1 ? 1 : (m > 16 ? 16 : m));
+  }
+  for (int p = 0; p < 2 && n > 0; ++p)
+    if ((e = cudaMemcpyAsync(g.tab[p], tab[p].data(), sizeof(InstArgs) * n, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+      return e;
+  if ((e = cudaMemcpyAsync(g.pfx, pre.data(), sizeof(int32_t) * pre.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return e;
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+  for (int p = 0; p < 2; ++p) {
+    GroupArgs &G = g.ga[p];
+    G.inst = g.tab[p];
+    G.ninst = n;
+    G.pblk = g.pfx;
+    G.sblk = g.pfx + (g.cap + 1);
+    G.mblk = g.pfx + 2 * (g.cap + 1);
+    G.bin_items = g.pfx + 3 * (g.cap + 1);
+    G.act_items = g.pfx + 4 * (g.cap + 1);
+    G.work = g.pfx + 5 * (g.cap + 1);
+    G.nblk_p = pb[n];
+    G.nblk_s = sb[n];
+    G.nblk_m = mb[n];
+    G.grid = 8 * nsm;
+  }
+  return cudaSuccess;
+}
+
+// One FP32 step of a group (enqueue only); phase events if ev.
+cudaError_t enqueue_group_step(int dim, int scheme, const GroupArgs &G, cudaEvent_t *ev, cudaStream_t st) {
+  cudaError_t e;
+  if ((e = phase_mark(ev, 0, st)) != cudaSuccess) return e;
+  if ((e = bin_group(dim, G, st)) != cudaSuccess) return e;
+  if ((e = phase_mark(ev, 1, st)) != cudaSuccess) return e;
+  return f32_group_step(dim, scheme, G, ev, st);
 }
 
 mpm_status check_handle(mpm_ctx *h) {
@@ -216,6 +292,13 @@ mpm_status device_status(mpm_ctx *h) {
   return h->sticky;
 }
 
+mpm_status status_of_bits(int32_t st) {
+  if (st & ST_NONFINITE) return MPM_ERR_NONFINITE;
+  if (st & ST_LEFT_MESH) return MPM_ERR_LEFT_MESH;
+  if (st & ST_TIMEOUT) return MPM_ERR_TIMEOUT;
+  return MPM_OK;
+}
+
 void free_ptr(void *&p) {
   if (p) cudaFree(p);
   p = nullptr;
@@ -225,6 +308,14 @@ template <typename T>
 void free_t(T *&p) {
   if (p) cudaFree((void *)p);
   p = nullptr;
+}
+
+// Device bytes of the FP32 step storage that does not scale with particles.
+int64_t f32_fixed_bytes(const mpm_mesh_desc &d, int64_t nt, int64_t nn) {
+  const int bn = d.dim == 3 ? box_nodes<3>() : box_nodes<2>();
+  int64_t b = 4 * nt * bn * (1 + 2 * d.dim) + (d.scheme == MPM_USF ? 4 * nt * bn * d.dim : 0);
+  b += 7 * 4 * (nt + 2) + 16 * nn * (d.dim == 3 ? 2 : 1) + 4096;
+  return b;
 }
 
 }  // namespace
@@ -247,7 +338,7 @@ mpm_status mpm_create_mesh(const mpm_mesh_desc *desc, mpm_handle *out) {
   }
   int64_t nn = 1;
   for (int k = 0; k < d.dim; ++k) nn *= (int64_t)d.ncells[k] + 1;
-  if (nn >= ((int64_t)1 << 34)) return MPM_ERR_ARG;
+  if (2 * nn >= ((int64_t)1 << 31)) return MPM_ERR_ARG;  // node records use 32-bit indices
   mpm_ctx *h = new mpm_ctx();
   h->d = d;
   if (d.dim == 2) h->d.ncells[2] = 1;
@@ -316,10 +407,6 @@ mpm_status mpm_create_mesh(const mpm_mesh_desc *desc, mpm_handle *out) {
     if (e == cudaSuccess) e = cudaMemset(S.out_cnt, 0, ti);
     if (e == cudaSuccess) e = cudaMemset(S.bucket_fill, 0, ti);
     if (e == cudaSuccess) e = cudaMemset(S.ctr, 0, sizeof(int32_t) * C_NCTR);
-    if (2 * nn >= ((int64_t)1 << 31)) {  // node records are indexed with 32-bit ints
-      mpm_destroy(h);
-      return MPM_ERR_ARG;
-    }
     if (e == cudaSuccess) e = cudaMalloc(&S.node, sizeof(float4) * nn * (d.dim == 3 ? 2 : 1));
     if (e == cudaSuccess) e = f32_prepare(d.dim);
   } else if (e == cudaSuccess) {
@@ -345,11 +432,30 @@ mpm_status mpm_create_mesh(const mpm_mesh_desc *desc, mpm_handle *out) {
   return MPM_OK;
 }
 
+mpm_status mpm_footprint(const mpm_mesh_desc *desc, int64_t n, int32_t has_cohesion, int64_t *bytes) {
+  if (!desc || !bytes || n < 0 || (desc->dim != 2 && desc->dim != 3)) return MPM_ERR_ARG;
+  const mpm_mesh_desc &d = *desc;
+  int64_t nn = 1, nt = 1;
+  for (int k = 0; k < d.dim; ++k) {
+    if (d.ncells[k] < 1) return MPM_ERR_ARG;
+    nn *= (int64_t)d.ncells[k] + 1;
+    nt *= (d.ncells[k] + tile_dim(d.dim, k) - 1) / tile_dim(d.dim, k);
+  }
+  const bool coh = has_cohesion != 0;
+  if (d.precision == MPM_FP32_MIXED)
+    *bytes = 2 * (int64_t)buf32_bytes(d.dim, coh, n) + 7 * 4 * n + (int64_t)sort_scratch_bytes(n) +
+             f32_fixed_bytes(d, nt, nn);
+  else
+    *bytes = (int64_t)buf64_bytes(d.dim, coh, n) + 8 * nn * (1 + 5 * d.dim) + 65536;
+  return MPM_OK;
+}
+
 mpm_status mpm_add_particles(mpm_handle h, int64_t n, const double *pos, const double *vel, const double *vol,
                              const mpm_material *mat, const double *cohesion, const double *stress0,
                              int64_t *first_id) {
   mpm_status s0 = check_handle(h);
   if (s0 != MPM_OK) return s0;
+  if (h->batch) return fail(h, MPM_ERR_STATE, "add_particles: the mesh is admitted to a batch");
   if (n < 0 || !mat || (n > 0 && (!pos || !vel || !vol))) return fail(h, MPM_ERR_ARG, "add_particles: bad arguments");
   if (mat->model != MPM_LINEAR_ELASTIC && mat->model != MPM_MOHR_COULOMB)
     return fail(h, MPM_ERR_ARG, "unknown material model");
@@ -396,23 +502,9 @@ mpm_status mpm_add_particles(mpm_handle h, int64_t n, const double *pos, const d
     carve32(nm[1], D, coh, cap, nb[1]);
     // nb[1] gathers old + new particles unsorted; nb[0] receives them binned
     const PBuf &ob = h->buf[h->cur];
-    if (n0 > 0) {
-      const size_t b4 = 4 * n0;
-      CK(cp(nb[1].key, ob.key, b4), "copy");
-      CK(cp(nb[1].id, ob.id, b4), "copy");
-      for (int k = 0; k < D; ++k) {
-        CK(cp(nb[1].off[k], ob.off[k], b4), "copy");
-        CK(cp(nb[1].vel[k], ob.vel[k], b4), "copy");
-      }
-      for (int i = 0; i < ns; ++i) {
-        CK(cp(nb[1].sig[i], ob.sig[i], b4), "copy");
-        CK(cp(nb[1].eps[i], ob.eps[i], b4), "copy");
-      }
-      CK(cp(nb[1].mass, ob.mass, b4), "copy");
-      CK(cp(nb[1].jm1, ob.jm1, b4), "copy");
-      CK(cp(nb[1].epsp, ob.epsp, b4), "copy");
-      if (coh) CK(cp(nb[1].coh, ob.coh, b4), "copy");
-    }
+    if (n0 > 0)
+      for (int fi = 0; fi < PBUF_FIELDS - (coh ? 0 : 1); ++fi)
+        CK(cp(nb[1].fld(fi), ob.fld(fi), 4 * n0), "copy");
     std::vector<uint32_t> key(n);
     std::vector<int32_t> id(n);
     std::vector<float> f((size_t)n);
@@ -425,8 +517,8 @@ mpm_status mpm_add_particles(mpm_handle h, int64_t n, const double *pos, const d
       key[p] = (uint32_t)t * CELLS_PER_TILE + (uint32_t)l;
       id[p] = (int32_t)(n0 + p);
     }
-    CK(cudaMemcpyAsync(nb[1].key + n0, key.data(), 4 * n, cudaMemcpyHostToDevice, h->st), "upload");
-    CK(cudaMemcpyAsync(nb[1].id + n0, id.data(), 4 * n, cudaMemcpyHostToDevice, h->st), "upload");
+    CK(cudaMemcpyAsync(nb[1].key() + n0, key.data(), 4 * n, cudaMemcpyHostToDevice, h->st), "upload");
+    CK(cudaMemcpyAsync(nb[1].id() + n0, id.data(), 4 * n, cudaMemcpyHostToDevice, h->st), "upload");
     auto up = [&](float *dst, auto get) -> cudaError_t {
       for (int64_t p = 0; p < n; ++p) f[p] = get(p);
       cudaError_t e = cudaMemcpyAsync(dst + n0, f.data(), 4 * n, cudaMemcpyHostToDevice, h->st);
@@ -434,22 +526,22 @@ mpm_status mpm_add_particles(mpm_handle h, int64_t n, const double *pos, const d
       return e;
     };
     for (int k = 0; k < D; ++k) {
-      CK(up(nb[1].off[k], [&](int64_t p) {
+      CK(up(nb[1].off(k), [&](int64_t p) {
            float u = (float)off[p * D + k];
            if (u >= 0.5f) u = nextafterf(0.5f, 0.f);
            if (u < -0.5f) u = -0.5f;
            return u;
          }), "upload");
-      CK(up(nb[1].vel[k], [&](int64_t p) { return (float)vel[p * D + k]; }), "upload");
+      CK(up(nb[1].vel(k), [&](int64_t p) { return (float)vel[p * D + k]; }), "upload");
     }
     for (int i = 0; i < ns; ++i) {
-      CK(up(nb[1].sig[i], [&](int64_t p) { return stress0 ? (float)stress0[p * 6 + i] : 0.f; }), "upload");
-      CK(up(nb[1].eps[i], [&](int64_t) { return 0.f; }), "upload");
+      CK(up(nb[1].sig(i), [&](int64_t p) { return stress0 ? (float)stress0[p * 6 + i] : 0.f; }), "upload");
+      CK(up(nb[1].eps(i), [&](int64_t) { return 0.f; }), "upload");
     }
-    CK(up(nb[1].mass, [&](int64_t p) { return (float)(mat->rho * vol[p]); }), "upload");
-    CK(up(nb[1].jm1, [&](int64_t) { return 0.f; }), "upload");
-    CK(up(nb[1].epsp, [&](int64_t) { return 0.f; }), "upload");
-    if (coh) CK(up(nb[1].coh, [&](int64_t p) { return (float)cohesion[p]; }), "upload");
+    CK(up(nb[1].mass(), [&](int64_t p) { return (float)(mat->rho * vol[p]); }), "upload");
+    CK(up(nb[1].jm1(), [&](int64_t) { return 0.f; }), "upload");
+    CK(up(nb[1].epsp(), [&](int64_t) { return 0.f; }), "upload");
+    if (coh) CK(up(nb[1].coh(), [&](int64_t p) { return (float)cohesion[p]; }), "upload");
     // per-particle scratch of the binning
     StepBufs &S = h->s;
     free_t(S.keys_sorted);
@@ -469,7 +561,7 @@ mpm_status mpm_add_particles(mpm_handle h, int64_t n, const double *pos, const d
     CK(cudaMalloc(&h->perm2, 4 * cap), "scratch");
     CK(cudaMalloc(&h->sort_scratch, sort_scratch_bytes(cap)), "scratch");
     // full stable binning once: sort keys, gather the state in key order
-    CK(sort_pairs(nb[1].key, nullptr, S.keys_sorted, S.perm, n1, h->key_bits, h->sort_scratch, h->st), "binning");
+    CK(sort_pairs(nb[1].key(), nullptr, S.keys_sorted, S.perm, n1, h->key_bits, h->sort_scratch, h->st), "binning");
     CK(permute_state(D, n1, nb[1], nb[0], S.perm, h->st), "binning");
     CK(tile_bounds(S.keys_sorted, n1, h->geo.ntiles, S.tile_start[0], h->st), "binning");
     const size_t ti = sizeof(int32_t) * (h->geo.ntiles + 2);
@@ -536,7 +628,8 @@ mpm_status mpm_add_particles(mpm_handle h, int64_t n, const double *pos, const d
     h->L64.P = P;
     h->cap = cap;
   }
-  destroy_graphs(h);
+  destroy_graphs(h->graph);
+  h->grp_valid = false;
   h->n = n1;
   h->has_coh = coh;
   h->mat = *mat;
@@ -548,19 +641,26 @@ mpm_status mpm_add_particles(mpm_handle h, int64_t n, const double *pos, const d
 mpm_status mpm_step(mpm_handle h, int64_t nsteps) {
   mpm_status s0 = check_handle(h);
   if (s0 != MPM_OK) return s0;
+  if (h->batch) return fail(h, MPM_ERR_STATE, "step: the mesh is admitted to a batch");
   if (nsteps < 0) return fail(h, MPM_ERR_ARG, "nsteps < 0");
   if (nsteps == 0 || h->n == 0) return h->sticky;
   if (h->d.precision == MPM_FP32_MIXED) {
+    if (!h->grp_valid) {
+      std::vector<mpm_ctx *> one(1, h);
+      CK(build_group(h->grp, one, false, false, h->nsm, h->st), "group tables");
+      h->grp_valid = true;
+    }
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(h->st, &cs);
     const bool use_graph = cs == cudaStreamCaptureStatusNone;
+    cudaEvent_t *ev = h->timing ? h->ev : nullptr;
     for (int64_t s = 0; s < nsteps; ++s) {
       const int cur = h->cur;
       if (use_graph) {
         if (!h->graph[cur]) {
           cudaGraph_t g = nullptr;
           CK(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal), "graph capture");
-          cudaError_t e = enqueue_f32_step(h, cur);
+          cudaError_t e = enqueue_group_step(h->d.dim, h->d.scheme, h->grp.ga[cur], ev, h->st);
           cudaError_t e2 = cudaStreamEndCapture(h->st, &g);
           if (e != cudaSuccess) return cuda_fail(h, e, "step enqueue");
           CK(e2, "graph capture");
@@ -570,7 +670,7 @@ mpm_status mpm_step(mpm_handle h, int64_t nsteps) {
         }
         CK(cudaGraphLaunch(h->graph[cur], h->st), "graph launch");
       } else {
-        CK(enqueue_f32_step(h, cur), "step enqueue");
+        CK(enqueue_group_step(h->d.dim, h->d.scheme, h->grp.ga[cur], ev, h->st), "step enqueue");
       }
       h->cur ^= 1;
     }
@@ -738,8 +838,10 @@ mpm_status mpm_read_binning(mpm_handle h, int32_t *key, int32_t *perm, int32_t *
   if (h->n == 0) return device_status(h);
   // the production binning of the stored particles, written to scratch so
   // that the next step's binning (which reads the previous binning) is intact
-  CK(bin_step(bin_launch(h, h->cur, h->keys2, h->perm2), h->st), "binning");
-  if (key) CK(cudaMemcpyAsync(key, h->buf[h->cur].key, 4 * h->n, cudaMemcpyDeviceToHost, h->st), "binning");
+  std::vector<mpm_ctx *> one(1, h);
+  CK(build_group(h->grp_bin, one, false, true, h->nsm, h->st), "binning tables");
+  CK(bin_group(h->d.dim, h->grp_bin.ga[h->cur], h->st), "binning");
+  if (key) CK(cudaMemcpyAsync(key, h->buf[h->cur].key(), 4 * h->n, cudaMemcpyDeviceToHost, h->st), "binning");
   if (perm) CK(cudaMemcpyAsync(perm, h->perm2, 4 * h->n, cudaMemcpyDeviceToHost, h->st), "binning");
   CK(cudaStreamSynchronize(h->st), "binning");
   return device_status(h);
@@ -756,7 +858,7 @@ mpm_status mpm_set_phase_timing(mpm_handle h, int32_t enable) {
     for (int i = 0; i <= MPM_MAX_PHASES; ++i) CK(cudaEventCreate(&h->ev[i]), "phase timing");
   h->timing = on;
   h->timed_step = false;
-  destroy_graphs(h);  // recapture with / without the event nodes
+  destroy_graphs(h->graph);  // recapture with / without the event nodes
   return MPM_OK;
 }
 
@@ -779,14 +881,20 @@ const char *mpm_last_error(mpm_handle h) {
 
 mpm_status mpm_destroy(mpm_handle h) {
   if (!h) return MPM_OK;
+  if (h->batch) {  // leave the batch first
+    mpm_batch_ctx *b = h->batch;
+    for (size_t i = 0; i < b->slots.size(); ++i)
+      if (b->slots[i] == h) mpm_batch_evict(b, (int32_t)i);
+  }
   if (h->st) cudaStreamSynchronize(h->st);
-  destroy_graphs(h);
+  destroy_graphs(h->graph);
+  free_group(h->grp);
+  free_group(h->grp_bin);
   StepBufs &S = h->s;
   void *ptrs[] = {h->bufmem[0], h->bufmem[1], S.keys_sorted, S.perm, S.tile_start[0], S.tile_start[1], S.in_cnt,
                   S.out_cnt, S.bucket_start, S.bucket_fill, S.movers, S.bucket, S.bucket_sorted, S.active,
-                  S.scan_tot, S.ctr,
-                  S.slots1, S.slots2, S.node,
-                  h->keys2, h->perm2, h->sort_scratch, h->pmem64, h->nmem64, h->d_status, h->d_cons};
+                  S.scan_tot, S.ctr, S.slots1, S.slots2, S.node, h->keys2, h->perm2, h->sort_scratch,
+                  h->pmem64, h->nmem64, h->d_status, h->d_cons};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (int i = 0; i <= MPM_MAX_PHASES; ++i)
@@ -795,6 +903,161 @@ mpm_status mpm_destroy(mpm_handle h) {
   delete h;
   return MPM_OK;
 }
+
+// ---- batches ---------------------------------------------------------------
+
+mpm_status mpm_batch_create(void *stream, mpm_batch *out) {
+  if (!out) return MPM_ERR_ARG;
+  *out = nullptr;
+  mpm_batch_ctx *b = new mpm_batch_ctx();
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (stream) {
+    b->st = (cudaStream_t)stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess) {
+      delete b;
+      return MPM_ERR_CUDA;
+    }
+    b->own_stream = true;
+  }
+  *out = b;
+  return MPM_OK;
+}
+
+mpm_status mpm_batch_admit(mpm_batch b, mpm_handle h, int32_t *slot) {
+  if (!b || !h) return MPM_ERR_ARG;
+  mpm_status s0 = check_handle(h);
+  if (s0 != MPM_OK) return s0;
+  if (h->d.precision != MPM_FP32_MIXED) return fail(h, MPM_ERR_ARG, "batch: FP32_MIXED meshes only");
+  if (h->batch) return fail(h, MPM_ERR_STATE, "batch: the mesh is already admitted to a batch");
+  CK(cudaStreamSynchronize(h->st), "batch admit");
+  CK(cudaStreamSynchronize(b->st), "batch admit");
+  h->st_saved = h->st;
+  h->st = b->st;
+  h->batch = b;
+  int s = -1;
+  for (size_t i = 0; i < b->slots.size(); ++i)
+    if (!b->slots[i]) {
+      s = (int)i;
+      break;
+    }
+  if (s < 0) {
+    s = (int)b->slots.size();
+    b->slots.push_back(nullptr);
+  }
+  b->slots[s] = h;
+  b->dirty = true;
+  if (slot) *slot = s;
+  return MPM_OK;
+}
+
+mpm_status mpm_batch_evict(mpm_batch b, int32_t slot) {
+  if (!b || slot < 0 || slot >= (int32_t)b->slots.size() || !b->slots[slot]) return MPM_ERR_ARG;
+  if (cudaStreamSynchronize(b->st) != cudaSuccess) return MPM_ERR_CUDA;
+  mpm_ctx *h = b->slots[slot];
+  h->st = h->st_saved;
+  h->batch = nullptr;
+  b->slots[slot] = nullptr;
+  b->dirty = true;
+  return MPM_OK;
+}
+
+mpm_status mpm_batch_step(mpm_batch b, int64_t nsteps) {
+  if (!b || nsteps < 0) return MPM_ERR_ARG;
+  if (nsteps == 0) return MPM_OK;
+  if (b->dirty) {
+    if (cudaStreamSynchronize(b->st) != cudaSuccess) return MPM_ERR_CUDA;
+    destroy_graphs(b->graph);
+    for (auto &g : b->groups) free_group(g.dev);
+    b->groups.clear();
+    for (size_t i = 0; i < b->slots.size(); ++i) {
+      mpm_ctx *h = b->slots[i];
+      if (!h || h->n == 0) continue;
+      mpm_batch_ctx::Group *gp = nullptr;
+      for (auto &g : b->groups)
+        if (g.dim == h->d.dim && g.scheme == h->d.scheme) gp = &g;
+      if (!gp) {
+        b->groups.push_back(mpm_batch_ctx::Group{h->d.dim, h->d.scheme, {}, {}, GroupDev()});
+        gp = &b->groups.back();
+      }
+      gp->mem.push_back(h);
+      gp->slot.push_back((int)i);
+    }
+    for (auto &g : b->groups)
+      if (build_group(g.dev, g.mem, true, false, b->nsm, b->st) != cudaSuccess) return MPM_ERR_CUDA;
+    b->bpar = 0;
+    b->dirty = false;
+  }
+  if (b->groups.empty()) return MPM_OK;
+  for (int64_t s = 0; s < nsteps; ++s) {
+    const int p = b->bpar;
+    if (!b->graph[p]) {
+      cudaGraph_t g = nullptr;
+      if (cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return MPM_ERR_CUDA;
+      cudaError_t e = cudaSuccess;
+      for (auto &gr : b->groups)
+        if (e == cudaSuccess) e = enqueue_group_step(gr.dim, gr.scheme, gr.dev.ga[p], nullptr, b->st);
+      cudaError_t e2 = cudaStreamEndCapture(b->st, &g);
+      if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return MPM_ERR_CUDA;
+      }
+      e = cudaGraphInstantiate(&b->graph[p], g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return MPM_ERR_CUDA;
+    }
+    if (cudaGraphLaunch(b->graph[p], b->st) != cudaSuccess) return MPM_ERR_CUDA;
+    b->bpar ^= 1;
+    for (auto &gr : b->groups)
+      for (mpm_ctx *h : gr.mem) h->cur ^= 1;
+  }
+  return MPM_OK;
+}
+
+mpm_status mpm_batch_poll(mpm_batch b, int32_t nslots, int32_t *slot_status) {
+  if (!b || nslots < 0 || (nslots > 0 && !slot_status)) return MPM_ERR_ARG;
+  for (int i = 0; i < nslots; ++i) slot_status[i] = MPM_ERR_STATE;
+  std::vector<int32_t> bits;
+  for (auto &gr : b->groups) {
+    if (b->dirty) break;
+    if (gather_status(gr.dev.tab[0], gr.dev.ninst, gr.dev.status, b->st) != cudaSuccess) return MPM_ERR_CUDA;
+    bits.resize(gr.dev.ninst);
+    if (cudaMemcpyAsync(bits.data(), gr.dev.status, sizeof(int32_t) * gr.dev.ninst, cudaMemcpyDeviceToHost, b->st) !=
+        cudaSuccess)
+      return MPM_ERR_CUDA;
+    if (cudaStreamSynchronize(b->st) != cudaSuccess) return MPM_ERR_CUDA;
+    for (int k = 0; k < gr.dev.ninst; ++k)
+      if (gr.slot[k] < nslots) slot_status[gr.slot[k]] = status_of_bits(bits[k]);
+  }
+  if (cudaStreamSynchronize(b->st) != cudaSuccess) return MPM_ERR_CUDA;
+  // meshes admitted since the last batched step (or with no particles)
+  for (int i = 0; i < nslots && i < (int)b->slots.size(); ++i) {
+    mpm_ctx *h = b->slots[i];
+    if (h && slot_status[i] == MPM_ERR_STATE) {
+      int32_t st = 0;
+      if (cudaMemcpy(&st, h->s.ctr + C_STATUS, sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return MPM_ERR_CUDA;
+      slot_status[i] = status_of_bits(st);
+    }
+  }
+  return MPM_OK;
+}
+
+mpm_status mpm_batch_destroy(mpm_batch b) {
+  if (!b) return MPM_OK;
+  for (size_t i = 0; i < b->slots.size(); ++i)
+    if (b->slots[i]) mpm_batch_evict(b, (int32_t)i);
+  cudaStreamSynchronize(b->st);
+  destroy_graphs(b->graph);
+  for (auto &g : b->groups) free_group(g.dev);
+  if (b->own_stream) cudaStreamDestroy(b->st);
+  delete b;
+  return MPM_OK;
+}
+
+// ---- standalone primitives ---------------------------------------------------
 
 mpm_status mpm_sort_keys(const uint32_t *d_keys, int32_t *d_perm, int64_t n, int32_t key_bits, void *stream) {
   if (n < 0 || key_bits < 1 || key_bits > 32 || (n > 0 && (!d_keys || !d_perm))) return MPM_ERR_ARG;

@@ -9,22 +9,26 @@
 // GPU form of the neighbourhood idea.  The particle state is stored in the
 // previous step's binning order and a particle moves at most one cell per
 // step, so the new binning is the old one plus a few movers:
-//   bin_movers  compares each stored particle's new key with the key it was
-//               binned under last step and lists the particles that changed
-//               tile (counts per tile in and out);
-//   bin_scan_*  two passes over the tiles: new tile ranges = old ranges -
-//               leavers + arrivals
-//               (exclusive scan over tiles), arrival bucket offsets, the
-//               active tile list, counter resets;
-//   bin_bucket  groups the arrivals by destination tile;
-//   bin_tiles   one CTA per tile: the tile's particles are the stayers of its
-//               old range plus its arrivals; a stable counting sort by local
-//               cell, in storage order, writes the permutation and the keys
-//               in binning order.
+//   bin_movers       compares each stored particle's new key with the key it
+//                    was binned under last step and lists the particles that
+//                    changed tile (counts per tile in and out);
+//   bin_scan_totals,
+//   bin_scan_apply   two passes over the tiles: new tile ranges = old ranges
+//                    - leavers + arrivals (exclusive scan over tiles), arrival
+//                    bucket offsets, the active tile list, counter resets;
+//   bin_bucket       groups the arrivals by destination tile;
+//   group_prefix     work prefixes over the instances of the group;
+//   bin_tiles        one CTA per tile: the tile's particles are the stayers
+//                    of its old range plus its arrivals; a stable counting
+//                    sort by local cell, in storage order, writes the
+//                    permutation and the keys in binning order.
 // The result is exactly the stable sort of the new keys by storage position
 // (arrivals from lower tiles precede the stayers, arrivals from higher tiles
 // follow them), i.e. the same permutation a full stable radix sort gives, at
 // the cost of reading each key twice instead of several sort passes.
+// Every kernel runs over a table of independent instances (a single mesh is
+// a table of one); blocks and work items map to instances through prefix
+// arrays.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -33,23 +37,35 @@
 namespace mpm {
 namespace {
 
-constexpr int BT = 256;          // bin_tiles threads
+constexpr int BT = 256;  // bin_tiles threads
 constexpr int BT_WARPS = BT / 32;
 constexpr int BUCKET_SMEM = 1024;
 constexpr int SCAN_T = 256;
 constexpr int SCAN_ITEMS = 4;
+constexpr int SCAN_CHUNK = SCAN_T * SCAN_ITEMS;  // tiles per scan block
 
-__global__ void bin_movers(const uint32_t *__restrict__ knew, const uint32_t *__restrict__ kold, int64_t n,
-                           int ntiles, int32_t *__restrict__ in_cnt, int32_t *__restrict__ out_cnt,
-                           int32_t *__restrict__ movers, int32_t *__restrict__ ctr) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int tn = min((int)(knew[i] >> LOCAL_BITS), ntiles);
-    const int to = min((int)(kold[i] >> LOCAL_BITS), ntiles);
-    if (tn != to) {
-      atomicAdd(&in_cnt[tn], 1);
-      atomicAdd(&out_cnt[to], 1);
-      movers[atomicAdd(&ctr[C_MOVERS], 1)] = (int32_t)i;
-    }
+// Instance of item x: the largest i with prefix[i] <= x (prefix[0] = 0).
+__device__ __forceinline__ int find_inst(const int32_t *prefix, int ninst, int x) {
+  int lo = 0, hi = ninst - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (prefix[mid] <= x) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void bin_movers(GroupArgs G) {
+  const int i = find_inst(G.pblk, G.ninst, blockIdx.x);
+  const InstArgs &I = G.inst[i];
+  const int64_t p = (int64_t)(blockIdx.x - G.pblk[i]) * blockDim.x + threadIdx.x;
+  if (p >= I.n) return;
+  const int ntiles = I.ntiles;
+  const int tn = min((int)(I.A.key()[p] >> LOCAL_BITS), ntiles);
+  const int to = min((int)(I.s.keys_sorted[p] >> LOCAL_BITS), ntiles);
+  if (tn != to) {
+    atomicAdd(&I.s.in_cnt[tn], 1);
+    atomicAdd(&I.s.out_cnt[to], 1);
+    I.s.movers[atomicAdd(&I.s.ctr[C_MOVERS], 1)] = (int32_t)p;
   }
 }
 
@@ -85,29 +101,28 @@ __device__ __forceinline__ int cta_excl(int v, int *wsum, int &total) {
 
 // Per tile e (tiles plus the dead range): new count = old count - leavers +
 // arrivals; arrivals; active flag.
-__device__ __forceinline__ void tile_counts(int e, int ntiles, const int32_t *old_start, const int32_t *in_cnt,
-                                            const int32_t *out_cnt, int &cn, int &cb, int &ca) {
-  const int in = in_cnt[e], out = out_cnt[e];
-  cn = (old_start[e + 1] - old_start[e]) - out + in;
+__device__ __forceinline__ void tile_counts(const InstArgs &I, int e, int &cn, int &cb, int &ca) {
+  const int in = I.s.in_cnt[e], out = I.s.out_cnt[e];
+  cn = (I.old_start[e + 1] - I.old_start[e]) - out + in;
   cb = in;
-  ca = (e < ntiles && cn > 0) ? 1 : 0;
+  ca = (e < I.ntiles && cn > 0) ? 1 : 0;
 }
 
-// Scan over tiles, pass 1: block totals of (count, arrivals, active).
-__global__ void __launch_bounds__(SCAN_T) bin_scan_totals(int ntiles, const int32_t *__restrict__ old_start,
-                                                          const int32_t *__restrict__ in_cnt,
-                                                          const int32_t *__restrict__ out_cnt,
-                                                          int32_t *__restrict__ tot) {
+// Scan over tiles, pass 1: chunk totals of (count, arrivals, active).
+__global__ void __launch_bounds__(SCAN_T) bin_scan_totals(GroupArgs G) {
   __shared__ int wsum[32];
-  const int m = ntiles + 1;
-  const int e0 = blockIdx.x * SCAN_T * SCAN_ITEMS + threadIdx.x * SCAN_ITEMS;
+  const int i = find_inst(G.sblk, G.ninst, blockIdx.x);
+  const InstArgs &I = G.inst[i];
+  const int c = blockIdx.x - G.sblk[i];
+  const int m = I.ntiles + 1;
+  const int e0 = c * SCAN_CHUNK + threadIdx.x * SCAN_ITEMS;
   int sn = 0, sb = 0, sa = 0;
 #pragma unroll
   for (int r = 0; r < SCAN_ITEMS; ++r) {
     const int e = e0 + r;
     if (e < m) {
       int cn, cb, ca;
-      tile_counts(e, ntiles, old_start, in_cnt, out_cnt, cn, cb, ca);
+      tile_counts(I, e, cn, cb, ca);
       sn += cn;
       sb += cb;
       sa += ca;
@@ -118,27 +133,27 @@ __global__ void __launch_bounds__(SCAN_T) bin_scan_totals(int ntiles, const int3
   cta_excl(sb, wsum, tb);
   cta_excl(sa, wsum, ta);
   if (threadIdx.x == 0) {
-    tot[3 * blockIdx.x + 0] = tn;
-    tot[3 * blockIdx.x + 1] = tb;
-    tot[3 * blockIdx.x + 2] = ta;
+    I.s.scan_tot[3 * c + 0] = tn;
+    I.s.scan_tot[3 * c + 1] = tb;
+    I.s.scan_tot[3 * c + 2] = ta;
   }
 }
 
-// Scan over tiles, pass 2: each block adds the totals of the blocks before
-// it, scans its own tiles, writes new ranges, arrival offsets and the active
-// list, and clears the per-tile counters for the next step.
-__global__ void __launch_bounds__(SCAN_T) bin_scan_apply(int64_t n, int ntiles, const int32_t *__restrict__ old_start,
-                                                         int32_t *__restrict__ new_start, int32_t *__restrict__ in_cnt,
-                                                         int32_t *__restrict__ out_cnt, int32_t *__restrict__ bstart,
-                                                         int32_t *__restrict__ bfill, int32_t *__restrict__ active,
-                                                         const int32_t *__restrict__ tot, int32_t *__restrict__ ctr) {
+// Scan over tiles, pass 2: each chunk adds the totals of the chunks before it,
+// scans its own tiles, writes new ranges, arrival offsets and the active list,
+// and clears the per-tile counters for the next step.
+__global__ void __launch_bounds__(SCAN_T) bin_scan_apply(GroupArgs G) {
   __shared__ int wsum[32];
-  const int m = ntiles + 1;
+  const int i = find_inst(G.sblk, G.ninst, blockIdx.x);
+  const InstArgs &I = G.inst[i];
+  const int c = blockIdx.x - G.sblk[i];
+  const int nchunks = G.sblk[i + 1] - G.sblk[i];
+  const int m = I.ntiles + 1;
   int on = 0, ob = 0, oa = 0;
-  for (int b = threadIdx.x; b < (int)blockIdx.x; b += SCAN_T) {
-    on += tot[3 * b];
-    ob += tot[3 * b + 1];
-    oa += tot[3 * b + 2];
+  for (int b = threadIdx.x; b < c; b += SCAN_T) {
+    on += I.s.scan_tot[3 * b];
+    ob += I.s.scan_tot[3 * b + 1];
+    oa += I.s.scan_tot[3 * b + 2];
   }
   int t0, t1, t2;
   cta_excl(on, wsum, t0);
@@ -147,14 +162,14 @@ __global__ void __launch_bounds__(SCAN_T) bin_scan_apply(int64_t n, int ntiles, 
   on = t0;
   ob = t1;
   oa = t2;
-  const int e0 = blockIdx.x * SCAN_T * SCAN_ITEMS + threadIdx.x * SCAN_ITEMS;
+  const int e0 = c * SCAN_CHUNK + threadIdx.x * SCAN_ITEMS;
   int cn[SCAN_ITEMS], cb[SCAN_ITEMS], ca[SCAN_ITEMS];
   int sn = 0, sb = 0, sa = 0;
 #pragma unroll
   for (int r = 0; r < SCAN_ITEMS; ++r) {
     const int e = e0 + r;
     cn[r] = cb[r] = ca[r] = 0;
-    if (e < m) tile_counts(e, ntiles, old_start, in_cnt, out_cnt, cn[r], cb[r], ca[r]);
+    if (e < m) tile_counts(I, e, cn[r], cb[r], ca[r]);
     sn += cn[r];
     sb += cb[r];
     sa += ca[r];
@@ -167,57 +182,87 @@ __global__ void __launch_bounds__(SCAN_T) bin_scan_apply(int64_t n, int ntiles, 
   for (int r = 0; r < SCAN_ITEMS; ++r) {
     const int e = e0 + r;
     if (e < m) {
-      new_start[e] = pn;
-      bstart[e] = pb;
-      if (ca[r]) active[pa] = e;
-      in_cnt[e] = 0;
-      out_cnt[e] = 0;
-      bfill[e] = 0;
+      I.new_start[e] = pn;
+      I.s.bucket_start[e] = pb;
+      if (ca[r]) I.s.active[pa] = e;
+      I.s.in_cnt[e] = 0;
+      I.s.out_cnt[e] = 0;
+      I.s.bucket_fill[e] = 0;
     }
     pn += cn[r];
     pb += cb[r];
     pa += ca[r];
   }
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    ctr[C_MOVERS_SNAP] = ctr[C_MOVERS];
-    ctr[C_MOVERS] = 0;
-    ctr[C_WORK_BIN] = ctr[C_WORK_P2G] = ctr[C_WORK_NODE] = ctr[C_WORK_P2G2] = ctr[C_WORK_NODE2] = 0;
+  if (threadIdx.x == 0 && c == 0) {
+    I.s.ctr[C_MOVERS_SNAP] = I.s.ctr[C_MOVERS];
+    I.s.ctr[C_MOVERS] = 0;
   }
-  if (blockIdx.x == gridDim.x - 1) {
+  if (c == nchunks - 1) {
     __syncthreads();  // new_start of the dead range written by this block
     if (threadIdx.x == 0) {
       const int nact = oa + ta;
-      new_start[m] = (int32_t)n;
-      bstart[m] = ob + tb;
-      const int dead_start = new_start[ntiles];
-      ctr[C_ACTIVE] = nact;
-      ctr[C_DEAD_START] = dead_start;
-      ctr[C_BIN_ITEMS] = nact + ((int64_t)dead_start < n ? 1 : 0);
+      I.new_start[m] = (int32_t)I.n;
+      I.s.bucket_start[m] = ob + tb;
+      const int dead_start = I.new_start[I.ntiles];
+      I.s.ctr[C_ACTIVE] = nact;
+      I.s.ctr[C_DEAD_START] = dead_start;
+      I.s.ctr[C_BIN_ITEMS] = nact + ((int64_t)dead_start < I.n ? 1 : 0);
     }
   }
 }
 
-__global__ void bin_bucket(const uint32_t *__restrict__ knew, int ntiles, const int32_t *__restrict__ movers,
-                           const int32_t *__restrict__ bstart, int32_t *__restrict__ bfill,
-                           int32_t *__restrict__ bucket, const int32_t *__restrict__ ctr) {
-  const int nm = ctr[C_MOVERS_SNAP];
-  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < nm; m += gridDim.x * blockDim.x) {
-    const int i = movers[m];
-    const int tn = min((int)(knew[i] >> LOCAL_BITS), ntiles);
-    bucket[bstart[tn] + atomicAdd(&bfill[tn], 1)] = i;
+__global__ void bin_bucket(GroupArgs G) {
+  const int i = find_inst(G.mblk, G.ninst, blockIdx.x);
+  const InstArgs &I = G.inst[i];
+  const int lb = blockIdx.x - G.mblk[i];
+  const int nb = G.mblk[i + 1] - G.mblk[i];
+  const int nm = I.s.ctr[C_MOVERS_SNAP];
+  for (int m = lb * blockDim.x + threadIdx.x; m < nm; m += nb * blockDim.x) {
+    const int p = I.s.movers[m];
+    const int tn = min((int)(I.A.key()[p] >> LOCAL_BITS), I.ntiles);
+    I.s.bucket[I.s.bucket_start[tn] + atomicAdd(&I.s.bucket_fill[tn], 1)] = p;
   }
 }
 
-__device__ __forceinline__ int next_work(int32_t *ctr, int slot) {
+// Prefixes of the binning tiles and the active tiles over the instances, and
+// reset of the group's dynamic work counters.
+__global__ void group_prefix(GroupArgs G) {
+  __shared__ int wsum[32];
+  int cb = 0, ca = 0;
+  for (int c0 = 0; c0 < G.ninst; c0 += blockDim.x) {
+    const int j = c0 + threadIdx.x;
+    int b = 0, a = 0;
+    if (j < G.ninst) {
+      b = G.inst[j].s.ctr[C_BIN_ITEMS];
+      a = G.inst[j].s.ctr[C_ACTIVE];
+    }
+    int tb, ta;
+    const int pb = cta_excl(b, wsum, tb) + cb;
+    const int pa = cta_excl(a, wsum, ta) + ca;
+    if (j < G.ninst) {
+      G.bin_items[j] = pb;
+      G.act_items[j] = pa;
+    }
+    cb += tb;
+    ca += ta;
+  }
+  if (threadIdx.x == 0) {
+    G.bin_items[G.ninst] = cb;
+    G.act_items[G.ninst] = ca;
+  }
+  if (threadIdx.x < W_COUNT) G.work[threadIdx.x] = 0;
+}
+
+__device__ __forceinline__ int next_work(int32_t *work, int slot) {
   __shared__ int s_w;
-  if (threadIdx.x == 0) s_w = atomicAdd(&ctr[slot], 1);
+  if (threadIdx.x == 0) s_w = atomicAdd(&work[slot], 1);
   __syncthreads();
   const int w = s_w;
   __syncthreads();
   return w;
 }
 
-__global__ void __launch_bounds__(BT) bin_tiles(BinLaunch B) {
+__global__ void __launch_bounds__(BT) bin_tiles(GroupArgs G) {
   __shared__ int cnt[CELLS_PER_TILE];
   __shared__ int base[CELLS_PER_TILE];
   __shared__ int running[CELLS_PER_TILE];
@@ -227,40 +272,45 @@ __global__ void __launch_bounds__(BT) bin_tiles(BinLaunch B) {
   __shared__ int s_nl;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t lt_mask = (1u << lane) - 1u;
-  const int ntiles = B.ntiles;
-  for (int i = tid; i < BT_WARPS * (CELLS_PER_TILE + 1); i += BT) (&wcnt[0][0])[i] = 0;
+  for (int k = tid; k < BT_WARPS * (CELLS_PER_TILE + 1); k += BT) (&wcnt[0][0])[k] = 0;
   __syncthreads();
+  const int total = G.bin_items[G.ninst];
 
   for (;;) {
-    const int w = next_work(B.s.ctr, C_WORK_BIN);
-    if (w >= B.s.ctr[C_BIN_ITEMS]) break;
-    const int t = (w < B.s.ctr[C_ACTIVE]) ? B.s.active[w] : ntiles;
-    const int os = B.old_start[t], oe = B.old_start[t + 1];
-    const int bs = B.s.bucket_start[t], be = B.s.bucket_start[t + 1];
+    const int w = next_work(G.work, W_BIN);
+    if (w >= total) break;
+    const int ii = find_inst(G.bin_items, G.ninst, w);
+    const InstArgs &I = G.inst[ii];
+    const int local = w - G.bin_items[ii];
+    const int ntiles = I.ntiles;
+    const int t = (local < I.s.ctr[C_ACTIVE]) ? I.s.active[local] : ntiles;
+    const int os = I.old_start[t], oe = I.old_start[t + 1];
+    const int bs = I.s.bucket_start[t], be = I.s.bucket_start[t + 1];
     const int nbk = be - bs;
-    const int ns = B.new_start[t];
+    const int ns = I.new_start[t];
+    const uint32_t *knew = I.A.key();
 
     // arrivals sorted by storage position (positions are distinct)
     const int *sorted;
     if (nbk <= BUCKET_SMEM) {
-      for (int i = tid; i < nbk; i += BT) sb_in[i] = B.s.bucket[bs + i];
+      for (int k = tid; k < nbk; k += BT) sb_in[k] = I.s.bucket[bs + k];
       __syncthreads();
-      for (int i = tid; i < nbk; i += BT) {
-        const int p = sb_in[i];
+      for (int k = tid; k < nbk; k += BT) {
+        const int p = sb_in[k];
         int r = 0;
         for (int j = 0; j < nbk; ++j) r += sb_in[j] < p;
         sb_out[r] = p;
       }
       sorted = sb_out;
     } else {
-      const int32_t *src = B.s.bucket + bs;
-      for (int i = tid; i < nbk; i += BT) {
-        const int p = src[i];
+      const int32_t *src = I.s.bucket + bs;
+      for (int k = tid; k < nbk; k += BT) {
+        const int p = src[k];
         int r = 0;
         for (int j = 0; j < nbk; ++j) r += src[j] < p;
-        B.s.bucket_sorted[bs + r] = p;
+        I.s.bucket_sorted[bs + r] = p;
       }
-      sorted = B.s.bucket_sorted + bs;
+      sorted = I.s.bucket_sorted + bs;
     }
     if (tid < CELLS_PER_TILE) {
       cnt[tid] = 0;
@@ -287,7 +337,7 @@ __global__ void __launch_bounds__(BT) bin_tiles(BinLaunch B) {
       if (s < S) {
         const bool in_range = s >= nl && s < nl + nr;
         const int pos = in_range ? os + (s - nl) : sorted[s < nl ? s : s - nr];
-        const uint32_t k = B.knew[pos];
+        const uint32_t k = knew[pos];
         if (!in_range || (int)min((int)(k >> LOCAL_BITS), ntiles) == t)
           d = (t == ntiles) ? 0 : (int)(k & (CELLS_PER_TILE - 1));
       }
@@ -314,7 +364,7 @@ __global__ void __launch_bounds__(BT) bin_tiles(BinLaunch B) {
       if (s < S) {
         const bool in_range = s >= nl && s < nl + nr;
         pos = in_range ? os + (s - nl) : sorted[s < nl ? s : s - nr];
-        k = B.knew[pos];
+        k = knew[pos];
         if (!in_range || (int)min((int)(k >> LOCAL_BITS), ntiles) == t)
           d = (t == ntiles) ? 0 : (int)(k & (CELLS_PER_TILE - 1));
       }
@@ -325,8 +375,8 @@ __global__ void __launch_bounds__(BT) bin_tiles(BinLaunch B) {
       if (d < CELLS_PER_TILE) {
         int dst = ns + base[d] + running[d] + rank;
         for (int k2 = 0; k2 < warp; ++k2) dst += wcnt[k2][d];
-        B.perm_out[dst] = pos;
-        B.keys_out[dst] = k;
+        I.perm_out[dst] = pos;
+        I.keys_out[dst] = k;
       }
       __syncthreads();
       if (tid <= CELLS_PER_TILE) {
@@ -348,38 +398,36 @@ __global__ void permute_k(int64_t n, PBuf A, PBuf B, const int32_t *__restrict__
   constexpr int NS = nstress<D>();
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
     const int j = perm[q];
-    B.key[q] = A.key[j];
-    B.id[q] = A.id[j];
+    B.key()[q] = A.key()[j];
+    B.id()[q] = A.id()[j];
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-      B.off[k][q] = A.off[k][j];
-      B.vel[k][q] = A.vel[k][j];
+      B.off(k)[q] = A.off(k)[j];
+      B.vel(k)[q] = A.vel(k)[j];
     }
 #pragma unroll
     for (int i = 0; i < NS; ++i) {
-      B.sig[i][q] = A.sig[i][j];
-      B.eps[i][q] = A.eps[i][j];
+      B.sig(i)[q] = A.sig(i)[j];
+      B.eps(i)[q] = A.eps(i)[j];
     }
-    B.mass[q] = A.mass[j];
-    B.jm1[q] = A.jm1[j];
-    B.epsp[q] = A.epsp[j];
-    if (A.coh) B.coh[q] = A.coh[j];
+    B.mass()[q] = A.mass()[j];
+    B.jm1()[q] = A.jm1()[j];
+    B.epsp()[q] = A.epsp()[j];
+    if (A.coh()) B.coh()[q] = A.coh()[j];
   }
 }
 
 }  // namespace
 
-cudaError_t bin_step(const BinLaunch &B, cudaStream_t st) {
-  if (B.n <= 0) return cudaSuccess;
-  const int gridp = (int)((B.n + 255) / 256 < B.grid * 4 ? (B.n + 255) / 256 : B.grid * 4);
-  bin_movers<<<gridp, 256, 0, st>>>(B.knew, B.kold, B.n, B.ntiles, B.s.in_cnt, B.s.out_cnt, B.s.movers, B.s.ctr);
-  const int sblocks = (B.ntiles + 1 + SCAN_T * SCAN_ITEMS - 1) / (SCAN_T * SCAN_ITEMS);
-  bin_scan_totals<<<sblocks, SCAN_T, 0, st>>>(B.ntiles, B.old_start, B.s.in_cnt, B.s.out_cnt, B.s.scan_tot);
-  bin_scan_apply<<<sblocks, SCAN_T, 0, st>>>(B.n, B.ntiles, B.old_start, B.new_start, B.s.in_cnt, B.s.out_cnt,
-                                             B.s.bucket_start, B.s.bucket_fill, B.s.active, B.s.scan_tot, B.s.ctr);
-  bin_bucket<<<B.grid, 256, 0, st>>>(B.knew, B.ntiles, B.s.movers, B.s.bucket_start, B.s.bucket_fill, B.s.bucket,
-                                     B.s.ctr);
-  bin_tiles<<<B.grid, BT, 0, st>>>(B);
+cudaError_t bin_group(int dim, const GroupArgs &G, cudaStream_t st) {
+  (void)dim;
+  if (G.ninst <= 0 || G.nblk_p <= 0) return cudaSuccess;
+  bin_movers<<<G.nblk_p, 256, 0, st>>>(G);
+  bin_scan_totals<<<G.nblk_s, SCAN_T, 0, st>>>(G);
+  bin_scan_apply<<<G.nblk_s, SCAN_T, 0, st>>>(G);
+  bin_bucket<<<G.nblk_m, 256, 0, st>>>(G);
+  group_prefix<<<1, 256, 0, st>>>(G);
+  bin_tiles<<<G.grid, BT, 0, st>>>(G);
   return cudaGetLastError();
 }
 

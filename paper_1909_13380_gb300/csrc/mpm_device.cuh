@@ -380,6 +380,19 @@ __device__ __forceinline__ bool near_apex(const float st[6], const MatConst<floa
   return dist2 < band * band;
 }
 
+// The FP64 return near the apex, kept out of line: it is rare, and inlining
+// it would raise the register count of every kernel that updates stresses.
+static __device__ __noinline__ void mc_return_apex_band(const MatConst<double> &md, float c, float st[6], float out[6],
+                                                 float &epsp) {
+  double sd[6], od[6], dd;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) sd[i] = (double)st[i];
+  mc_return<double>(md, (double)c, sd, od, dd);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) out[i] = (float)od[i];
+  epsp += (float)dd;
+}
+
 // Full material update of one particle: sigma <- return(sigma + D:de).
 // FP32 path: FP32 arithmetic except the Mohr-Coulomb return inside the apex
 // band, which runs in FP64.  FP64 path: everything in FP64.
@@ -398,13 +411,7 @@ __device__ __forceinline__ void material_update(const MatConst<float> &m, const 
     return;
   }
   if (near_apex(st, m, c)) {
-    double sd[6], od[6], dd;
-#pragma unroll
-    for (int i = 0; i < 6; ++i) sd[i] = (double)st[i];
-    mc_return<double>(md, (double)c, sd, od, dd);
-#pragma unroll
-    for (int i = 0; i < 6; ++i) sig[i] = (float)od[i];
-    epsp += (float)dd;
+    mc_return_apex_band(md, c, st, sig, epsp);
   } else {
     float d;
     mc_return<float>(m, c, st, sig, d);

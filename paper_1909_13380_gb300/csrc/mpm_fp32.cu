@@ -36,25 +36,15 @@ constexpr int P2G_W = P2G_T / 32;
 constexpr int NODE_T = 128;
 constexpr int G2P_T = 256;
 
-struct TileArgs {
-  Geo geo;
-  PBuf A;  // particle storage of the step (read through perm)
-  PBuf B;  // output storage (binning order)
-  const uint32_t *keys;
-  const int32_t *perm;
-  const int32_t *tile_start;
-  const int32_t *active;
-  int32_t *ctr;
-  int work_slot;
-  const float *slots1;
-  const float *slots2;
-  float *slots_out;
-  int nch1;
-  float4 *node;      // dense node values (layout in StepBufs::node)
-  int ns0, ns1;      // node strides: (nx+1), (nx+1)(ny+1)
-  MatConst<float> mat;
-  MatConst<double> matd;
-};
+// Instance of item x: the largest i with prefix[i] <= x (prefix[0] = 0).
+__device__ __forceinline__ int find_inst(const int32_t *prefix, int ninst, int x) {
+  int lo = 0, hi = ninst - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (prefix[mid] <= x) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
 
 __device__ __forceinline__ int next_tile(int32_t *ctr, int slot) {
   __shared__ int s_w;
@@ -139,7 +129,7 @@ constexpr size_t p2g_smem() {
 }
 
 template <int D, int MODE>
-__global__ void __launch_bounds__(P2G_T, 4) p2g_tile(TileArgs A) {
+__global__ void __launch_bounds__(P2G_T, 4) p2g_tile(GroupArgs G, int work_slot) {
   constexpr int NC = 1 << D;
   constexpr int NCH = p2g_channels<D, MODE>();
   constexpr int NV = NC * NCH;
@@ -152,16 +142,20 @@ __global__ void __launch_bounds__(P2G_T, 4) p2g_tile(TileArgs A) {
   float *cellP = sm;  // [64][NV]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float *wst = sm + CELLS_PER_TILE * NV + warp * 32 * 33;  // [32][33]
-  const Geo &g = A.geo;
+  const int total = G.act_items[G.ninst];
 
   for (;;) {
-    const int wi = next_tile(A.ctr, A.work_slot);
-    if (wi >= A.ctr[C_ACTIVE]) break;
-    const int t = A.active[wi];
-    const int s = A.tile_start[t], e = A.tile_start[t + 1];
+    const int wi = next_tile(G.work, work_slot);
+    if (wi >= total) break;
+    const int ii = find_inst(G.act_items, G.ninst, wi);
+    const InstArgs &I = G.inst[ii];
+    const Geo &g = I.geo;
+    float *slots_out = MODE == P2G_FORCE ? I.s.slots2 : I.s.slots1;
+    const int t = I.s.active[wi - G.act_items[ii]];
+    const int s = I.new_start[t], e = I.new_start[t + 1];
     for (int i = threadIdx.x; i < CELLS_PER_TILE * NV; i += P2G_T) cellP[i] = 0.f;
-    const int ws = warp_split<P2G_W>(A.keys, s, e, warp);
-    const int we = warp_split<P2G_W>(A.keys, s, e, warp + 1);
+    const int ws = warp_split<P2G_W>(I.keys_out, s, e, warp);
+    const int we = warp_split<P2G_W>(I.keys_out, s, e, warp + 1);
     __syncthreads();
 
     for (int b0 = ws; b0 < we; b0 += 32) {
@@ -178,33 +172,33 @@ __global__ void __launch_bounds__(P2G_T, 4) p2g_tile(TileArgs A) {
         for (int j = 0; j < D; ++j) sv[k][j] = 0.f;
       }
       if (valid) {
-        lc = A.keys[q] & (CELLS_PER_TILE - 1);
-        const int j = A.perm[q];
+        lc = I.keys_out[q] & (CELLS_PER_TILE - 1);
+        const int j = I.perm_out[q];
         float u[D];
 #pragma unroll
-        for (int k = 0; k < D; ++k) u[k] = A.A.off[k][j];
+        for (int k = 0; k < D; ++k) u[k] = I.A.off(k)[j];
         corner_weights<D>(u, w0, w1);
-        mm = A.A.mass[j];
+        mm = I.A.mass()[j];
         if (HAS_M) {
 #pragma unroll
-          for (int k = 0; k < D; ++k) mv[k] = mm * A.A.vel[k][j];
+          for (int k = 0; k < D; ++k) mv[k] = mm * I.A.vel(k)[j];
         }
         if (HAS_F) {
           // FORCE (USF) reads the stress updated earlier this step, stored in
           // binning order; USL reads the stress at the start of the step
-          const PBuf &S = (MODE == P2G_FORCE) ? A.B : A.A;
+          const PBuf &S = (MODE == P2G_FORCE) ? I.B : I.A;
           const int js = (MODE == P2G_FORCE) ? q : j;
-          const float nV = -mm * g.inv_rho * (1.f + S.jm1[js]);
+          const float nV = -mm * g.inv_rho * (1.f + S.jm1()[js]);
           if (D == 3) {
-            const float sxx = S.sig[0][js], syy = S.sig[1][js], szz = S.sig[2][js];
-            const float sxy = S.sig[3][js], syz = S.sig[4][js], sxz = S.sig[5][js];
+            const float sxx = S.sig(0)[js], syy = S.sig(1)[js], szz = S.sig(2)[js];
+            const float sxy = S.sig(3)[js], syz = S.sig(4)[js], sxz = S.sig(5)[js];
             const float t3[3][3] = {{sxx, sxy, sxz}, {sxy, syy, syz}, {sxz, syz, szz}};
 #pragma unroll
             for (int a = 0; a < D; ++a)
 #pragma unroll
               for (int b = 0; b < D; ++b) sv[a][b] = nV * t3[a][b];
           } else {
-            const float sxx = S.sig[0][js], syy = S.sig[1][js], sxy = S.sig[3][js];
+            const float sxx = S.sig(0)[js], syy = S.sig(1)[js], sxy = S.sig(3)[js];
             const float t2[2][2] = {{sxx, sxy}, {sxy, syy}};
 #pragma unroll
             for (int a = 0; a < D; ++a)
@@ -287,7 +281,7 @@ __global__ void __launch_bounds__(P2G_T, 4) p2g_tile(TileArgs A) {
             for (int ch = 0; ch < NCH; ++ch) acc[ch].add(cellP[cl * NV + a * NCH + ch]);
           }
 #pragma unroll
-      for (int ch = 0; ch < NCH; ++ch) A.slots_out[((int64_t)t * NCH + ch) * BN + b] = acc[ch].value();
+      for (int ch = 0; ch < NCH; ++ch) slots_out[((int64_t)t * NCH + ch) * BN + b] = acc[ch].value();
     }
     __syncthreads();
   }
@@ -343,35 +337,39 @@ __device__ __forceinline__ void gather_node(const Geo &g, const int32_t *tile_st
 }
 
 template <int D, int NMODE>
-__global__ void __launch_bounds__(NODE_T) node_tile(TileArgs A) {
+__global__ void __launch_bounds__(NODE_T) node_tile(GroupArgs G, int work_slot) {
   constexpr int BN = box_nodes<D>();
   constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ;
-  const Geo &g = A.geo;
+  constexpr int NCH1 = NMODE == NODE_USL ? 1 + 2 * D : 1 + D;
+  const int total = G.act_items[G.ninst];
   for (;;) {
-    const int wi = next_tile(A.ctr, A.work_slot);
-    if (wi >= A.ctr[C_ACTIVE]) break;
-    const int t = A.active[wi];
+    const int wi = next_tile(G.work, work_slot);
+    if (wi >= total) break;
+    const int ii = find_inst(G.act_items, G.ninst, wi);
+    const InstArgs &I = G.inst[ii];
+    const Geo &g = I.geo;
+    const int t = I.s.active[wi - G.act_items[ii]];
     int tc[3];
     tile_coords(g, t, tc);
     for (int b = threadIdx.x; b < BN; b += NODE_T) {
       const int bx = b % (TX + 1);
       const int by = (b / (TX + 1)) % (TY + 1);
       const int bz = D == 3 ? b / ((TX + 1) * (TY + 1)) : 0;
-      const int I[3] = {tc[0] * TX + bx, tc[1] * TY + by, D == 3 ? tc[2] * TZ + bz : 0};
+      const int Ig[3] = {tc[0] * TX + bx, tc[1] * TY + by, D == 3 ? tc[2] * TZ + bz : 0};
       bool inside = true;
 #pragma unroll
-      for (int k = 0; k < D; ++k) inside = inside && I[k] <= g.nc[k];
+      for (int k = 0; k < D; ++k) inside = inside && Ig[k] <= g.nc[k];
       if (!inside) continue;
       float v[D], a[D], vn[D];
 #pragma unroll
       for (int k = 0; k < D; ++k) v[k] = a[k] = vn[k] = 0.f;
       float c1[1 + 2 * D];
       if (NMODE == NODE_USL)
-        gather_node<D, 1 + 2 * D>(g, A.tile_start, A.slots1, A.nch1, I, tc, c1);
+        gather_node<D, 1 + 2 * D>(g, I.new_start, I.s.slots1, NCH1, Ig, tc, c1);
       else
-        gather_node<D, 1 + D>(g, A.tile_start, A.slots1, A.nch1, I, tc, c1);
+        gather_node<D, 1 + D>(g, I.new_start, I.s.slots1, NCH1, Ig, tc, c1);
       const float m = c1[0];
-      const int faces = node_faces<D>(g, I);
+      const int faces = node_faces<D>(g, Ig);
       if (m > g.mass_tol) {
         const float inv_m = 1.f / m;
 #pragma unroll
@@ -387,7 +385,7 @@ __global__ void __launch_bounds__(NODE_T) node_tile(TileArgs A) {
           bc_velocity<D, float>(faces, g.bc, v);
         } else {
           float f[D];
-          gather_node<D, D>(g, A.tile_start, A.slots2, D, I, tc, f);
+          gather_node<D, D>(g, I.new_start, I.s.slots2, D, Ig, tc, f);
           bc_velocity<D, float>(faces, g.bc, v);
 #pragma unroll
           for (int k = 0; k < D; ++k) {
@@ -397,13 +395,13 @@ __global__ void __launch_bounds__(NODE_T) node_tile(TileArgs A) {
           bc_full<D, float>(faces, g.bc, g.mu, g.dt, v, a, vn);
         }
       }
-      const int gi = I[0] + A.ns0 * I[1] + A.ns1 * I[2];
+      const int gi = Ig[0] + I.ns0 * Ig[1] + I.ns1 * Ig[2];
       const float *w = NMODE == NODE_USF_V ? v : vn;
       if (D == 3) {
-        A.node[2 * gi] = make_float4(w[0], w[1], w[D - 1], 0.f);
-        A.node[2 * gi + 1] = make_float4(a[0], a[1], a[D - 1], 0.f);
+        I.s.node[2 * gi] = make_float4(w[0], w[1], w[D - 1], 0.f);
+        I.s.node[2 * gi + 1] = make_float4(a[0], a[1], a[D - 1], 0.f);
       } else {
-        A.node[gi] = make_float4(w[0], w[1], a[0], a[1]);
+        I.s.node[gi] = make_float4(w[0], w[1], a[0], a[1]);
       }
     }
     __syncthreads();
@@ -414,39 +412,41 @@ __global__ void __launch_bounds__(NODE_T) node_tile(TileArgs A) {
 // G2P: one thread per particle in binning order
 // ---------------------------------------------------------------------------
 template <int D, int GMODE>
-__global__ void __launch_bounds__(G2P_T, 3) g2p(TileArgs A, int64_t n) {
+__global__ void __launch_bounds__(G2P_T, 3) g2p(GroupArgs G) {
   constexpr int NC = 1 << D;
   constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ;
   constexpr int NS = nstress<D>();
-  const Geo &g = A.geo;
-  const int64_t q = (int64_t)blockIdx.x * G2P_T + threadIdx.x;
-  if (q >= n) return;
-  const int j = A.perm[q];
-  const int dead_start = A.ctr[C_DEAD_START];
+  const int ii = find_inst(G.pblk, G.ninst, blockIdx.x);
+  const InstArgs &I = G.inst[ii];
+  const Geo &g = I.geo;
+  const int64_t q = (int64_t)(blockIdx.x - G.pblk[ii]) * G2P_T + threadIdx.x;
+  if (q >= I.n) return;
+  const int j = I.perm_out[q];
+  const int dead_start = I.s.ctr[C_DEAD_START];
   if (q >= dead_start) {  // left the mesh earlier: carried over unchanged
     if (GMODE != G2P_USF_STRESS) {
-      A.B.key[q] = A.A.key[j];
-      A.B.id[q] = A.A.id[j];
-      A.B.mass[q] = A.A.mass[j];
+      I.B.key()[q] = I.A.key()[j];
+      I.B.id()[q] = I.A.id()[j];
+      I.B.mass()[q] = I.A.mass()[j];
 #pragma unroll
       for (int k = 0; k < D; ++k) {
-        A.B.off[k][q] = A.A.off[k][j];
-        A.B.vel[k][q] = A.A.vel[k][j];
+        I.B.off(k)[q] = I.A.off(k)[j];
+        I.B.vel(k)[q] = I.A.vel(k)[j];
       }
-      if (A.A.coh) A.B.coh[q] = A.A.coh[j];
+      if (I.A.coh()) I.B.coh()[q] = I.A.coh()[j];
     }
     if (GMODE != G2P_USF_ADVECT) {
 #pragma unroll
       for (int i = 0; i < NS; ++i) {
-        A.B.sig[i][q] = A.A.sig[i][j];
-        A.B.eps[i][q] = A.A.eps[i][j];
+        I.B.sig(i)[q] = I.A.sig(i)[j];
+        I.B.eps(i)[q] = I.A.eps(i)[j];
       }
-      A.B.jm1[q] = A.A.jm1[j];
-      A.B.epsp[q] = A.A.epsp[j];
+      I.B.jm1()[q] = I.A.jm1()[j];
+      I.B.epsp()[q] = I.A.epsp()[j];
     }
     return;
   }
-  const uint32_t key = A.keys[q];
+  const uint32_t key = I.keys_out[q];
   const int t = key >> LOCAL_BITS;
   int tc[3], lc[3];
   tile_coords(g, t, tc);
@@ -454,7 +454,7 @@ __global__ void __launch_bounds__(G2P_T, 3) g2p(TileArgs A, int64_t n) {
   int cell[3] = {tc[0] * TX + lc[0], tc[1] * TY + lc[1], D == 3 ? tc[2] * TZ + lc[2] : 0};
   float u[D], w0[D], w1[D];
 #pragma unroll
-  for (int k = 0; k < D; ++k) u[k] = A.A.off[k][j];
+  for (int k = 0; k < D; ++k) u[k] = I.A.off(k)[j];
   corner_weights<D>(u, w0, w1);
   float dv[D], vb[D], L[D][D];
 #pragma unroll
@@ -463,26 +463,26 @@ __global__ void __launch_bounds__(G2P_T, 3) g2p(TileArgs A, int64_t n) {
 #pragma unroll
     for (int l = 0; l < D; ++l) L[k][l] = 0.f;
   }
-  const int gi0 = cell[0] + A.ns0 * cell[1] + A.ns1 * cell[2];
+  const int gi0 = cell[0] + I.ns0 * cell[1] + I.ns1 * cell[2];
 #pragma unroll
   for (int a = 0; a < NC; ++a) {
     float N, G[D];
     corner_shape<D>(a, w0, w1, g.inv_h, N, G);
-    const int gi = gi0 + (a & 1) + A.ns0 * ((a >> 1) & 1) + (D == 3 ? A.ns1 * ((a >> 2) & 1) : 0);
+    const int gi = gi0 + (a & 1) + I.ns0 * ((a >> 1) & 1) + (D == 3 ? I.ns1 * ((a >> 2) & 1) : 0);
     float nv[D], na[D];
     if (D == 3) {
-      const float4 r0 = A.node[2 * gi];
+      const float4 r0 = I.s.node[2 * gi];
       nv[0] = r0.x;
       nv[1] = r0.y;
       nv[D - 1] = r0.z;
       if (GMODE != G2P_USF_STRESS) {
-        const float4 r1 = A.node[2 * gi + 1];
+        const float4 r1 = I.s.node[2 * gi + 1];
         na[0] = r1.x;
         na[1] = r1.y;
         na[D - 1] = r1.z;
       }
     } else {
-      const float4 r0 = A.node[gi];
+      const float4 r0 = I.s.node[gi];
       nv[0] = r0.x;
       nv[1] = r0.y;
       na[0] = r0.z;
@@ -500,9 +500,9 @@ __global__ void __launch_bounds__(G2P_T, 3) g2p(TileArgs A, int64_t n) {
   }
 
   int status = 0;
+  // strain increment de = sym(L) dt
+  float de[6] = {0, 0, 0, 0, 0, 0};
   if (GMODE != G2P_USF_ADVECT) {
-    // strain increment, volume ratio, stress
-    float de[6] = {0, 0, 0, 0, 0, 0};
     de[0] = L[0][0] * g.dt;
     de[1] = L[1][1] * g.dt;
     de[3] = 0.5f * (L[0][1] + L[1][0]) * g.dt;
@@ -511,40 +511,15 @@ __global__ void __launch_bounds__(G2P_T, 3) g2p(TileArgs A, int64_t n) {
       de[4] = 0.5f * (L[1][D - 1] + L[D - 1][1]) * g.dt;
       de[5] = 0.5f * (L[0][D - 1] + L[D - 1][0]) * g.dt;
     }
-    float sg[6];
-    if (D == 3) {
-#pragma unroll
-      for (int i = 0; i < 6; ++i) sg[i] = A.A.sig[i][j];
-    } else {
-      sg[0] = A.A.sig[0][j];
-      sg[1] = A.A.sig[1][j];
-      sg[2] = A.A.sig[2][j];
-      sg[3] = A.A.sig[3][j];
-      sg[4] = sg[5] = 0.f;
-    }
-#pragma unroll
-    for (int i = 0; i < NS; ++i) A.B.eps[i][q] = A.A.eps[i][j] + de[i];
-    // V = V0 (1 + jm1):  (1 + jm1)(1 + tr) - 1 = jm1 + tr + jm1 tr
-    const float tr = de[0] + de[1] + de[2];
-    const float jm1 = A.A.jm1[j];
-    A.B.jm1[q] = jm1 + (tr + jm1 * tr);
-    float epsp = A.A.epsp[j];
-    const float coh = A.A.coh ? A.A.coh[j] : A.mat.c;
-    material_update(A.mat, A.matd, coh, sg, de, epsp);
-#pragma unroll
-    for (int i = 0; i < NS; ++i) {
-      A.B.sig[i][q] = sg[i];
-      if (!isfinite(sg[i])) status |= ST_NONFINITE;
-    }
-    A.B.epsp[q] = epsp;
   }
+  // kinematics first (stored before the stress update to keep live ranges
+  // short): FLIP velocity, advection in cell units, relocation
   if (GMODE != G2P_USF_STRESS) {
-    // FLIP velocity, advection in cell units, relocation
     bool dead = false;
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-      const float vk = A.A.vel[k][j] + g.dt * dv[k];
-      A.B.vel[k][q] = vk;
+      const float vk = I.A.vel(k)[j] + g.dt * dv[k];
+      I.B.vel(k)[q] = vk;
       if (!isfinite(vk)) status |= ST_NONFINITE;
       float un = u[k] + g.dt * vb[k] * g.inv_h;
       if (!isfinite(un)) {
@@ -574,7 +549,7 @@ __global__ void __launch_bounds__(G2P_T, 3) g2p(TileArgs A, int64_t n) {
         }
       }
       if (cell[k] < 0 || cell[k] >= g.nc[k]) dead = true;
-      A.B.off[k][q] = un;
+      I.B.off(k)[q] = un;
     }
     uint32_t nkey = g.dead_key;
     if (!dead) {
@@ -584,42 +559,46 @@ __global__ void __launch_bounds__(G2P_T, 3) g2p(TileArgs A, int64_t n) {
     } else {
       status |= ST_LEFT_MESH;
     }
-    A.B.key[q] = nkey;
-    A.B.mass[q] = A.A.mass[j];
-    A.B.id[q] = A.A.id[j];
-    if (A.A.coh) A.B.coh[q] = A.A.coh[j];
+    I.B.key()[q] = nkey;
+    I.B.mass()[q] = I.A.mass()[j];
+    I.B.id()[q] = I.A.id()[j];
+    if (I.A.coh()) I.B.coh()[q] = I.A.coh()[j];
   }
-  if (status) atomicOr(&A.ctr[C_STATUS], status);
-}
-
-TileArgs make_args(const F32Launch &L, int work_slot) {
-  TileArgs a;
-  a.geo = L.geo;
-  a.A = L.A;
-  a.B = L.B;
-  a.keys = L.s.keys_sorted;
-  a.perm = L.s.perm;
-  a.tile_start = L.tile_start;
-  a.active = L.s.active;
-  a.ctr = L.s.ctr;
-  a.work_slot = work_slot;
-  a.slots1 = L.s.slots1;
-  a.slots2 = L.s.slots2;
-  a.slots_out = nullptr;
-  a.nch1 = 0;
-  a.node = L.s.node;
-  a.ns0 = (int)L.node_stride[0];
-  a.ns1 = (int)L.node_stride[1];
-  a.mat = L.mat;
-  a.matd = L.matd;
-  return a;
+  if (GMODE != G2P_USF_ADVECT) {
+    // strain, volume ratio, stress
+    float sg[6];
+    if (D == 3) {
+#pragma unroll
+      for (int i = 0; i < 6; ++i) sg[i] = I.A.sig(i)[j];
+    } else {
+      sg[0] = I.A.sig(0)[j];
+      sg[1] = I.A.sig(1)[j];
+      sg[2] = I.A.sig(2)[j];
+      sg[3] = I.A.sig(3)[j];
+      sg[4] = sg[5] = 0.f;
+    }
+#pragma unroll
+    for (int i = 0; i < NS; ++i) I.B.eps(i)[q] = I.A.eps(i)[j] + de[i];
+    // V = V0 (1 + jm1):  (1 + jm1)(1 + tr) - 1 = jm1 + tr + jm1 tr
+    const float tr = de[0] + de[1] + de[2];
+    const float jm1 = I.A.jm1()[j];
+    I.B.jm1()[q] = jm1 + (tr + jm1 * tr);
+    float epsp = I.A.epsp()[j];
+    const float coh = I.A.coh() ? I.A.coh()[j] : I.mat.c;
+    material_update(I.mat, I.matd, coh, sg, de, epsp);
+#pragma unroll
+    for (int i = 0; i < NS; ++i) {
+      I.B.sig(i)[q] = sg[i];
+      if (!isfinite(sg[i])) status |= ST_NONFINITE;
+    }
+    I.B.epsp()[q] = epsp;
+  }
+  if (status) atomicOr(&I.s.ctr[C_STATUS], status);
 }
 
 template <int D, int MODE>
-cudaError_t launch_p2g(const F32Launch &L, float *slots, int work_slot, cudaStream_t st) {
-  TileArgs a = make_args(L, work_slot);
-  a.slots_out = slots;
-  p2g_tile<D, MODE><<<L.grid, P2G_T, p2g_smem<D, MODE>(), st>>>(a);
+cudaError_t launch_p2g(const GroupArgs &G, int work_slot, cudaStream_t st) {
+  p2g_tile<D, MODE><<<G.grid, P2G_T, p2g_smem<D, MODE>(), st>>>(G, work_slot);
   return cudaGetLastError();
 }
 
@@ -630,47 +609,43 @@ cudaError_t prepare_p2g() {
 }
 
 template <int D, int NMODE>
-cudaError_t launch_node(const F32Launch &L, int work_slot, int nch1, cudaStream_t st) {
-  TileArgs a = make_args(L, work_slot);
-  a.nch1 = nch1;
-  node_tile<D, NMODE><<<L.grid, NODE_T, 0, st>>>(a);
+cudaError_t launch_node(const GroupArgs &G, int work_slot, cudaStream_t st) {
+  node_tile<D, NMODE><<<G.grid, NODE_T, 0, st>>>(G, work_slot);
   return cudaGetLastError();
 }
 
 template <int D, int GMODE>
-cudaError_t launch_g2p(const F32Launch &L, cudaStream_t st) {
-  TileArgs a = make_args(L, 0);
-  const int64_t blocks = (L.n + G2P_T - 1) / G2P_T;
-  g2p<D, GMODE><<<(unsigned)blocks, G2P_T, 0, st>>>(a, L.n);
+cudaError_t launch_g2p(const GroupArgs &G, cudaStream_t st) {
+  g2p<D, GMODE><<<G.nblk_p, G2P_T, 0, st>>>(G);
   return cudaGetLastError();
 }
 
 template <int D>
-cudaError_t step_dim(const F32Launch &L, cudaStream_t st) {
+cudaError_t step_dim(int scheme, const GroupArgs &G, cudaEvent_t *ev, cudaStream_t st) {
   cudaError_t e;
   // phase events 0 (start) and 1 (after binning) are recorded by the
   // caller; 2.. follow each kernel here
-  if (L.scheme == 1) {  // USL
-    if ((e = launch_p2g<D, P2G_USL>(L, L.s.slots1, C_WORK_P2G, st)) != cudaSuccess) return e;
-    if ((e = phase_mark(L.ev, 2, st)) != cudaSuccess) return e;
-    if ((e = launch_node<D, NODE_USL>(L, C_WORK_NODE, 1 + 2 * D, st)) != cudaSuccess) return e;
-    if ((e = phase_mark(L.ev, 3, st)) != cudaSuccess) return e;
-    if ((e = launch_g2p<D, G2P_USL>(L, st)) != cudaSuccess) return e;
-    return phase_mark(L.ev, 4, st);
+  if (scheme == 1) {  // USL
+    if ((e = launch_p2g<D, P2G_USL>(G, W_P2G, st)) != cudaSuccess) return e;
+    if ((e = phase_mark(ev, 2, st)) != cudaSuccess) return e;
+    if ((e = launch_node<D, NODE_USL>(G, W_NODE, st)) != cudaSuccess) return e;
+    if ((e = phase_mark(ev, 3, st)) != cudaSuccess) return e;
+    if ((e = launch_g2p<D, G2P_USL>(G, st)) != cudaSuccess) return e;
+    return phase_mark(ev, 4, st);
   }
   // USF
-  if ((e = launch_p2g<D, P2G_MOM>(L, L.s.slots1, C_WORK_P2G, st)) != cudaSuccess) return e;
-  if ((e = phase_mark(L.ev, 2, st)) != cudaSuccess) return e;
-  if ((e = launch_node<D, NODE_USF_V>(L, C_WORK_NODE, 1 + D, st)) != cudaSuccess) return e;
-  if ((e = phase_mark(L.ev, 3, st)) != cudaSuccess) return e;
-  if ((e = launch_g2p<D, G2P_USF_STRESS>(L, st)) != cudaSuccess) return e;
-  if ((e = phase_mark(L.ev, 4, st)) != cudaSuccess) return e;
-  if ((e = launch_p2g<D, P2G_FORCE>(L, L.s.slots2, C_WORK_P2G2, st)) != cudaSuccess) return e;
-  if ((e = phase_mark(L.ev, 5, st)) != cudaSuccess) return e;
-  if ((e = launch_node<D, NODE_USF_A>(L, C_WORK_NODE2, 1 + D, st)) != cudaSuccess) return e;
-  if ((e = phase_mark(L.ev, 6, st)) != cudaSuccess) return e;
-  if ((e = launch_g2p<D, G2P_USF_ADVECT>(L, st)) != cudaSuccess) return e;
-  return phase_mark(L.ev, 7, st);
+  if ((e = launch_p2g<D, P2G_MOM>(G, W_P2G, st)) != cudaSuccess) return e;
+  if ((e = phase_mark(ev, 2, st)) != cudaSuccess) return e;
+  if ((e = launch_node<D, NODE_USF_V>(G, W_NODE, st)) != cudaSuccess) return e;
+  if ((e = phase_mark(ev, 3, st)) != cudaSuccess) return e;
+  if ((e = launch_g2p<D, G2P_USF_STRESS>(G, st)) != cudaSuccess) return e;
+  if ((e = phase_mark(ev, 4, st)) != cudaSuccess) return e;
+  if ((e = launch_p2g<D, P2G_FORCE>(G, W_P2G2, st)) != cudaSuccess) return e;
+  if ((e = phase_mark(ev, 5, st)) != cudaSuccess) return e;
+  if ((e = launch_node<D, NODE_USF_A>(G, W_NODE2, st)) != cudaSuccess) return e;
+  if ((e = phase_mark(ev, 6, st)) != cudaSuccess) return e;
+  if ((e = launch_g2p<D, G2P_USF_ADVECT>(G, st)) != cudaSuccess) return e;
+  return phase_mark(ev, 7, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -684,21 +659,21 @@ __global__ void cons_partial(int64_t n, PBuf P, uint32_t dead_key, float inv_rho
   constexpr int NS = nstress<D>();
   double acc[CONS_VALS] = {0, 0, 0, 0, 0, 0, 0};
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
-    if (P.key[q] >= dead_key) continue;
-    const double m = P.mass[q];
+    if (P.key()[q] >= dead_key) continue;
+    const double m = P.mass()[q];
     acc[0] += m;
     double ke = 0;
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-      const double v = P.vel[k][q];
+      const double v = P.vel(k)[q];
       acc[1 + k] += m * v;
       ke += v * v;
     }
     acc[4] += 0.5 * m * ke;
     double se = 0;
 #pragma unroll
-    for (int i = 0; i < NS; ++i) se += (i >= 3 ? 2.0 : 1.0) * (double)P.sig[i][q] * (double)P.eps[i][q];
-    const double vol = m * (double)inv_rho * (1.0 + (double)P.jm1[q]);
+    for (int i = 0; i < NS; ++i) se += (i >= 3 ? 2.0 : 1.0) * (double)P.sig(i)[q] * (double)P.eps(i)[q];
+    const double vol = m * (double)inv_rho * (1.0 + (double)P.jm1()[q]);
     acc[5] += 0.5 * vol * se;
     acc[6] += 1.0;
   }
@@ -731,8 +706,8 @@ __global__ void export_k(int64_t n, PBuf P, Geo g, double o0, double o1, double 
   constexpr int NS = nstress<D>();
   const double org[3] = {o0, o1, o2};
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t id = P.id[q];
-    const uint32_t key = P.key[q];
+    const int64_t id = P.id()[q];
+    const uint32_t key = P.key()[q];
     const bool dead = key >= g.dead_key;
     int c[3] = {0, 0, 0};
     if (!dead) {
@@ -747,16 +722,16 @@ __global__ void export_k(int64_t n, PBuf P, Geo g, double o0, double o1, double 
 #pragma unroll
       for (int k = 0; k < D; ++k)
         pos[id * D + k] = dead ? __longlong_as_double(0x7ff8000000000000ll)
-                               : org[k] + ((double)c[k] + 0.5 + (double)P.off[k][q]) * h;
+                               : org[k] + ((double)c[k] + 0.5 + (double)P.off(k)[q]) * h;
     if (vel)
 #pragma unroll
-      for (int k = 0; k < D; ++k) vel[id * D + k] = P.vel[k][q];
+      for (int k = 0; k < D; ++k) vel[id * D + k] = P.vel(k)[q];
     if (sig || eps) {
       double s6[6] = {0, 0, 0, 0, 0, 0}, e6[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
       for (int i = 0; i < NS; ++i) {
-        s6[i] = P.sig[i][q];
-        e6[i] = P.eps[i][q];
+        s6[i] = P.sig(i)[q];
+        e6[i] = P.eps(i)[q];
       }
 #pragma unroll
       for (int i = 0; i < 6; ++i) {
@@ -764,8 +739,8 @@ __global__ void export_k(int64_t n, PBuf P, Geo g, double o0, double o1, double 
         if (eps) eps[id * 6 + i] = e6[i];
       }
     }
-    if (vol) vol[id] = (double)P.mass[q] / rho * (1.0 + (double)P.jm1[q]);
-    if (epsp) epsp[id] = P.epsp[q];
+    if (vol) vol[id] = (double)P.mass()[q] / rho * (1.0 + (double)P.jm1()[q]);
+    if (epsp) epsp[id] = P.epsp()[q];
     if (cell) cell[id] = dead ? -1 : (int64_t)c[0] + (int64_t)g.nc[0] * ((int64_t)c[1] + (int64_t)g.nc[1] * c[2]);
   }
 }
@@ -801,9 +776,20 @@ cudaError_t f32_prepare(int dim) {
   return prepare_p2g<2, P2G_FORCE>();
 }
 
-cudaError_t f32_step(const F32Launch &L, cudaStream_t st) {
-  if (L.n <= 0) return cudaSuccess;
-  return L.dim == 3 ? step_dim<3>(L, st) : step_dim<2>(L, st);
+__global__ void gather_status_k(const InstArgs *tab, int ninst, int32_t *out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ninst; i += gridDim.x * blockDim.x)
+    out[i] = tab[i].s.ctr[C_STATUS];
+}
+
+cudaError_t gather_status(const InstArgs *tab, int ninst, int32_t *out, cudaStream_t st) {
+  if (ninst <= 0) return cudaSuccess;
+  gather_status_k<<<(ninst + 255) / 256, 256, 0, st>>>(tab, ninst, out);
+  return cudaGetLastError();
+}
+
+cudaError_t f32_group_step(int dim, int scheme, const GroupArgs &G, cudaEvent_t *ev, cudaStream_t st) {
+  if (G.ninst <= 0 || G.nblk_p <= 0) return cudaSuccess;
+  return dim == 3 ? step_dim<3>(scheme, G, ev, st) : step_dim<2>(scheme, G, ev, st);
 }
 
 cudaError_t f32_conservation(int dim, int64_t n, const PBuf &P, uint32_t dead_key, float inv_rho, double *d_out,

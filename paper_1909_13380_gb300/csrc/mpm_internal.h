@@ -43,14 +43,27 @@ enum { G2P_USL = 0, G2P_USF_STRESS = 1, G2P_USF_ADVECT = 2 };
 // off in [-0.5, 0.5).  Volume is held as jm1 = V / V0 - 1 with V0 = m / rho,
 // so that the tiny per-step volume changes keep FP32's relative precision.
 // Stresses/strains: 6 comps in 3D, (xx, yy, zz, xy) in 2D.
+// All fields live in one allocation, field f at base + f * stride (stride a
+// multiple of 256 bytes), so a buffer is described by two values:
+//   0 key, 1 id, 2-4 offset, 5-7 velocity, 8-13 stress, 14-19 strain,
+//   20 mass, 21 J-1, 22 plastic strain, 23 cohesion (when present).
+// 2D leaves the z offset/velocity and the last two stress/strain slots unused.
+constexpr int PBUF_FIELDS = 24;
 struct PBuf {
-  uint32_t *key;
-  int32_t *id;
-  float *off[3];
-  float *vel[3];
-  float *sig[6];
-  float *eps[6];
-  float *mass, *jm1, *epsp, *coh;  // coh may be nullptr
+  char *base;
+  int64_t stride;
+  int has_coh;
+  __host__ __device__ __forceinline__ uint32_t *key() const { return (uint32_t *)base; }
+  __host__ __device__ __forceinline__ int32_t *id() const { return (int32_t *)(base + stride); }
+  __host__ __device__ __forceinline__ float *fld(int f) const { return (float *)(base + f * stride); }
+  __host__ __device__ __forceinline__ float *off(int k) const { return fld(2 + k); }
+  __host__ __device__ __forceinline__ float *vel(int k) const { return fld(5 + k); }
+  __host__ __device__ __forceinline__ float *sig(int i) const { return fld(8 + i); }
+  __host__ __device__ __forceinline__ float *eps(int i) const { return fld(14 + i); }
+  __host__ __device__ __forceinline__ float *mass() const { return fld(20); }
+  __host__ __device__ __forceinline__ float *jm1() const { return fld(21); }
+  __host__ __device__ __forceinline__ float *epsp() const { return fld(22); }
+  __host__ __device__ __forceinline__ float *coh() const { return has_coh ? fld(23) : nullptr; }
 };
 
 struct Geo {
@@ -112,44 +125,59 @@ cudaError_t sort_pairs(const uint32_t *keys_in, const int32_t *vals_in, uint32_t
 cudaError_t tile_bounds(const uint32_t *keys_sorted, int64_t n, int ntiles, int32_t *tile_start,
                         cudaStream_t st);
 
-// --- incremental binning (mpm_bin.cu) ----------------------------------------
-struct BinLaunch {
-  int64_t n;
+// --- one FP32 step over a group of instances ---------------------------------
+// Every FP32 kernel works on a table of instances (a single mesh is a group of
+// one).  Instances share no data, so each instance's result does not depend
+// on what else is in the group.
+struct InstArgs {
+  int64_t n;        // particles
   int ntiles;
-  const uint32_t *knew;      // keys of the stored particles (storage order)
-  const uint32_t *kold;      // keys of the previous binning (storage order)
-  const int32_t *old_start;  // previous tile ranges
-  int32_t *new_start;        // out
-  StepBufs s;
-  uint32_t *keys_out;        // out: keys in binning order
-  int32_t *perm_out;         // out: permutation
-  int grid;
-};
-cudaError_t bin_step(const BinLaunch &B, cudaStream_t st);
-// Gather every field of A into B in the order perm (B[q] = A[perm[q]]).
-cudaError_t permute_state(int dim, int64_t n, const PBuf &A, const PBuf &B, const int32_t *perm,
-                          cudaStream_t st);
-
-// --- FP32 tile kernels (mpm_fp32.cu) ----------------------------------------
-struct F32Launch {
-  int dim, scheme;
-  int64_t n;
   Geo geo;
   MatConst<float> mat;
   MatConst<double> matd;
-  PBuf A, B;  // A: state at the start of the step (storage order), B: out (binning order)
+  PBuf A, B;        // A: state at the start of the step (storage order), B: out (binning order)
   StepBufs s;
-  const int32_t *tile_start;  // this step's tile ranges (binning order)
-  int64_t node_stride[2];     // (nx+1), (nx+1)(ny+1)
-  int grid;                   // persistent grid size for the per-tile kernels
-  cudaEvent_t *ev;            // optional phase events, or nullptr
+  const int32_t *old_start;  // previous tile ranges
+  int32_t *new_start;        // this step's tile ranges (written by the binning)
+  uint32_t *keys_out;        // binning order keys (s.keys_sorted, or scratch)
+  int32_t *perm_out;         // binning permutation (s.perm, or scratch)
+  int ns0, ns1;              // node strides (nx+1), (nx+1)(ny+1)
 };
+
+// Per-group launch description.  The prefix arrays map a block (or a work
+// item) to its instance: entry i is the first block (item) of instance i and
+// entry ninst the total.
+enum { W_BIN = 0, W_P2G = 1, W_NODE = 2, W_P2G2 = 3, W_NODE2 = 4, W_COUNT = 8 };
+struct GroupArgs {
+  const InstArgs *inst;     // device table
+  int ninst;
+  const int32_t *pblk;      // blocks of the per-particle kernels (host-computed)
+  const int32_t *sblk;      // blocks of the tile scan (host-computed)
+  const int32_t *mblk;      // blocks of the mover bucketing (host-computed)
+  int32_t *bin_items;       // device-computed prefix of binning tiles
+  int32_t *act_items;       // device-computed prefix of active tiles
+  int32_t *work;            // W_COUNT dynamic work counters
+  int nblk_p, nblk_s, nblk_m;
+  int grid;                 // CTAs of the per-tile kernels
+};
+
 // Record a phase boundary (works inside stream capture as an external node).
 inline cudaError_t phase_mark(cudaEvent_t *ev, int i, cudaStream_t st) {
   return ev ? cudaEventRecordWithFlags(ev[i], st, cudaEventRecordExternal) : cudaSuccess;
 }
-cudaError_t f32_prepare(int dim);                           // once per process and dim
-cudaError_t f32_step(const F32Launch &L, cudaStream_t st);  // everything after binning
+
+// --- incremental binning (mpm_bin.cu) ----------------------------------------
+cudaError_t bin_group(int dim, const GroupArgs &G, cudaStream_t st);
+// Gather every field of A into B in the order perm (B[q] = A[perm[q]]).
+cudaError_t permute_state(int dim, int64_t n, const PBuf &A, const PBuf &B, const int32_t *perm,
+                          cudaStream_t st);
+
+// --- FP32 step kernels (mpm_fp32.cu) -----------------------------------------
+cudaError_t f32_prepare(int dim);  // once per process and dim
+// Everything after the binning; phase events 2.. after each kernel if ev.
+cudaError_t f32_group_step(int dim, int scheme, const GroupArgs &G, cudaEvent_t *ev, cudaStream_t st);
+// out[i] = latched status bits of instance i of the table.
+cudaError_t gather_status(const InstArgs *tab, int ninst, int32_t *out, cudaStream_t st);
 cudaError_t f32_conservation(int dim, int64_t n, const PBuf &P, uint32_t dead_key, float inv_rho,
                              double *d_out, double *d_partials, cudaStream_t st);
 cudaError_t f32_export(int dim, int64_t n, const PBuf &P, const Geo &g, const double origin[3], double h,

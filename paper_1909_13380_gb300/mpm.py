@@ -98,6 +98,13 @@ def load():
             "mpm_destroy": [vp],
             "mpm_sort_keys": [vp, vp, C.c_int64, C.c_int32, vp],
             "mpm_sort_keys_static": [vp, vp, C.c_int64, C.c_int32, vp],
+            "mpm_footprint": [C.POINTER(mpm_mesh_desc), C.c_int64, C.c_int32, i64p],
+            "mpm_batch_create": [vp, C.POINTER(vp)],
+            "mpm_batch_admit": [vp, vp, i32p],
+            "mpm_batch_evict": [vp, C.c_int32],
+            "mpm_batch_step": [vp, C.c_int64],
+            "mpm_batch_poll": [vp, C.c_int32, i32p],
+            "mpm_batch_destroy": [vp],
             "mpm_material_update": [C.POINTER(mpm_material), C.c_int32, C.c_int64, dp, dp, dp, dp, dp, vp],
             "mpm_set_phase_timing": [vp, C.c_int32],
             "mpm_phase_times": [vp, C.POINTER(C.c_float), i32p],
@@ -273,6 +280,43 @@ def mpm_sort_keys_static(d_keys, d_perm, n: int, key_bits: int, stream=None):
     st = load().mpm_sort_keys_static(C.c_void_p(kp), C.c_void_p(pp), int(n), int(key_bits),
                                      stream if stream is not None else current_stream())
     _check(None, st, "mpm_sort_keys_static")
+
+
+def mpm_footprint(desc: mpm_mesh_desc, n: int, has_cohesion: bool = False) -> int:
+    out = C.c_int64()
+    _check(None, load().mpm_footprint(C.byref(desc), int(n), int(bool(has_cohesion)), C.byref(out)), "mpm_footprint")
+    return out.value
+
+
+def mpm_batch_create(stream=None):
+    b = C.c_void_p()
+    _check(None, load().mpm_batch_create(stream, C.byref(b)), "mpm_batch_create")
+    return b
+
+
+def mpm_batch_admit(b, h) -> int:
+    slot = C.c_int32()
+    st = load().mpm_batch_admit(b, h, C.byref(slot))
+    _check(h, st, "mpm_batch_admit")
+    return slot.value
+
+
+def mpm_batch_evict(b, slot: int):
+    _check(None, load().mpm_batch_evict(b, int(slot)), "mpm_batch_evict")
+
+
+def mpm_batch_step(b, nsteps: int):
+    _check(None, load().mpm_batch_step(b, int(nsteps)), "mpm_batch_step")
+
+
+def mpm_batch_poll(b, nslots: int):
+    out = (C.c_int32 * max(1, nslots))()
+    _check(None, load().mpm_batch_poll(b, int(nslots), out), "mpm_batch_poll")
+    return [int(out[i]) for i in range(nslots)]
+
+
+def mpm_batch_destroy(b):
+    load().mpm_batch_destroy(b)
 
 
 def mpm_material_update(mat: mpm_material, precision: int, sig, deps, cohesion=None, stream=None):
