@@ -330,8 +330,9 @@ def run_gb300(args):
                          f"FP64 oracle, one thread, {dt:.1f} s"}
 
     if rank == 0:
-        # binning: bin_movers, bin_scan, bin_bucket, bin_tiles; then the step kernels
-        per_step = 4 + (3 if wl.scheme == W.USL else 6)
+        # binning: bin_movers, bin_scan_totals, bin_scan_apply, bin_bucket,
+        # group_prefix, bin_tiles; then p2g, node, g2p (USF: twice each)
+        per_step = 6 + (3 if wl.scheme == W.USL else 6)
         line = {
             "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,

@@ -144,8 +144,11 @@ __global__ void __launch_bounds__(SCAN_T) bin_scan_totals(GroupArgs G) {
 // and clears the per-tile counters for the next step.
 __global__ void __launch_bounds__(SCAN_T) bin_scan_apply(GroupArgs G) {
   __shared__ int wsum[32];
+  __shared__ InstArgs sI;
   const int i = find_inst(G.sblk, G.ninst, blockIdx.x);
-  const InstArgs &I = G.inst[i];
+  copy_inst(G.inst, i, &sI);
+  __syncthreads();
+  const InstArgs &I = sI;
   const int c = blockIdx.x - G.sblk[i];
   const int nchunks = G.sblk[i + 1] - G.sblk[i];
   const int m = I.ntiles + 1;
@@ -212,8 +215,11 @@ __global__ void __launch_bounds__(SCAN_T) bin_scan_apply(GroupArgs G) {
 }
 
 __global__ void bin_bucket(GroupArgs G) {
+  __shared__ InstArgs sI;
   const int i = find_inst(G.mblk, G.ninst, blockIdx.x);
-  const InstArgs &I = G.inst[i];
+  copy_inst(G.inst, i, &sI);
+  __syncthreads();
+  const InstArgs &I = sI;
   const int lb = blockIdx.x - G.mblk[i];
   const int nb = G.mblk[i + 1] - G.mblk[i];
   const int nm = I.s.ctr[C_MOVERS_SNAP];
@@ -270,6 +276,7 @@ __global__ void __launch_bounds__(BT) bin_tiles(GroupArgs G) {
   __shared__ int sb_in[BUCKET_SMEM];
   __shared__ int sb_out[BUCKET_SMEM];
   __shared__ int s_nl;
+  __shared__ InstArgs sI;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t lt_mask = (1u << lane) - 1u;
   for (int k = tid; k < BT_WARPS * (CELLS_PER_TILE + 1); k += BT) (&wcnt[0][0])[k] = 0;
@@ -280,7 +287,9 @@ __global__ void __launch_bounds__(BT) bin_tiles(GroupArgs G) {
     const int w = next_work(G.work, W_BIN);
     if (w >= total) break;
     const int ii = find_inst(G.bin_items, G.ninst, w);
-    const InstArgs &I = G.inst[ii];
+    copy_inst(G.inst, ii, &sI);
+    __syncthreads();
+    const InstArgs &I = sI;
     const int local = w - G.bin_items[ii];
     const int ntiles = I.ntiles;
     const int t = (local < I.s.ctr[C_ACTIVE]) ? I.s.active[local] : ntiles;

@@ -143,20 +143,22 @@ __global__ void __launch_bounds__(P2G_T, 4) p2g_tile(GroupArgs G, int work_slot)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float *wst = sm + CELLS_PER_TILE * NV + warp * 32 * 33;  // [32][33]
   const int total = G.act_items[G.ninst];
+  __shared__ InstArgs sI;
 
   for (;;) {
     const int wi = next_tile(G.work, work_slot);
     if (wi >= total) break;
     const int ii = find_inst(G.act_items, G.ninst, wi);
-    const InstArgs &I = G.inst[ii];
+    copy_inst(G.inst, ii, &sI);
+    for (int i = threadIdx.x; i < CELLS_PER_TILE * NV; i += P2G_T) cellP[i] = 0.f;
+    __syncthreads();
+    const InstArgs &I = sI;
     const Geo &g = I.geo;
     float *slots_out = MODE == P2G_FORCE ? I.s.slots2 : I.s.slots1;
     const int t = I.s.active[wi - G.act_items[ii]];
     const int s = I.new_start[t], e = I.new_start[t + 1];
-    for (int i = threadIdx.x; i < CELLS_PER_TILE * NV; i += P2G_T) cellP[i] = 0.f;
     const int ws = warp_split<P2G_W>(I.keys_out, s, e, warp);
     const int we = warp_split<P2G_W>(I.keys_out, s, e, warp + 1);
-    __syncthreads();
 
     for (int b0 = ws; b0 < we; b0 += 32) {
       const int q = b0 + lane;
@@ -342,11 +344,14 @@ __global__ void __launch_bounds__(NODE_T) node_tile(GroupArgs G, int work_slot) 
   constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ;
   constexpr int NCH1 = NMODE == NODE_USL ? 1 + 2 * D : 1 + D;
   const int total = G.act_items[G.ninst];
+  __shared__ InstArgs sI;
   for (;;) {
     const int wi = next_tile(G.work, work_slot);
     if (wi >= total) break;
     const int ii = find_inst(G.act_items, G.ninst, wi);
-    const InstArgs &I = G.inst[ii];
+    copy_inst(G.inst, ii, &sI);
+    __syncthreads();
+    const InstArgs &I = sI;
     const Geo &g = I.geo;
     const int t = I.s.active[wi - G.act_items[ii]];
     int tc[3];
@@ -416,8 +421,11 @@ __global__ void __launch_bounds__(G2P_T, 3) g2p(GroupArgs G) {
   constexpr int NC = 1 << D;
   constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ;
   constexpr int NS = nstress<D>();
+  __shared__ InstArgs sI;
   const int ii = find_inst(G.pblk, G.ninst, blockIdx.x);
-  const InstArgs &I = G.inst[ii];
+  copy_inst(G.inst, ii, &sI);
+  __syncthreads();
+  const InstArgs &I = sI;
   const Geo &g = I.geo;
   const int64_t q = (int64_t)(blockIdx.x - G.pblk[ii]) * G2P_T + threadIdx.x;
   if (q >= I.n) return;
@@ -499,26 +507,39 @@ __global__ void __launch_bounds__(G2P_T, 3) g2p(GroupArgs G) {
     }
   }
 
-  int status = 0;
-  // strain increment de = sym(L) dt
-  float de[6] = {0, 0, 0, 0, 0, 0};
-  if (GMODE != G2P_USF_ADVECT) {
-    de[0] = L[0][0] * g.dt;
-    de[1] = L[1][1] * g.dt;
-    de[3] = 0.5f * (L[0][1] + L[1][0]) * g.dt;
-    if (D == 3) {
-      de[2] = L[D - 1][D - 1] * g.dt;
-      de[4] = 0.5f * (L[1][D - 1] + L[D - 1][1]) * g.dt;
-      de[5] = 0.5f * (L[0][D - 1] + L[D - 1][0]) * g.dt;
-    }
+  // Every load of the particle's state is issued before the first store: the
+  // compiler cannot tell A from B, so a load placed after a store would wait
+  // for the value before it (one memory latency per field).
+  constexpr bool KIN = GMODE != G2P_USF_STRESS, STR = GMODE != G2P_USF_ADVECT;
+  float v0[D], sg[6], ep[6], jm1 = 0.f, epsp = 0.f, mass = 0.f, coh = I.mat.c;
+  int32_t pid = 0;
+  const bool has_coh = I.A.coh() != nullptr;
+  if (KIN) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) v0[k] = I.A.vel(k)[j];
+    mass = I.A.mass()[j];
+    pid = I.A.id()[j];
   }
-  // kinematics first (stored before the stress update to keep live ranges
-  // short): FLIP velocity, advection in cell units, relocation
-  if (GMODE != G2P_USF_STRESS) {
+  if (has_coh && (KIN || STR)) coh = I.A.coh()[j];
+  if (STR) {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) sg[i] = ep[i] = 0.f;
+#pragma unroll
+    for (int i = 0; i < NS; ++i) {
+      sg[i] = I.A.sig(i)[j];
+      ep[i] = I.A.eps(i)[j];
+    }
+    jm1 = I.A.jm1()[j];
+    epsp = I.A.epsp()[j];
+  }
+
+  int status = 0;
+  // FLIP velocity, advection in cell units, relocation
+  if (KIN) {
     bool dead = false;
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-      const float vk = I.A.vel(k)[j] + g.dt * dv[k];
+      const float vk = v0[k] + g.dt * dv[k];
       I.B.vel(k)[q] = vk;
       if (!isfinite(vk)) status |= ST_NONFINITE;
       float un = u[k] + g.dt * vb[k] * g.inv_h;
@@ -560,31 +581,26 @@ __global__ void __launch_bounds__(G2P_T, 3) g2p(GroupArgs G) {
       status |= ST_LEFT_MESH;
     }
     I.B.key()[q] = nkey;
-    I.B.mass()[q] = I.A.mass()[j];
-    I.B.id()[q] = I.A.id()[j];
-    if (I.A.coh()) I.B.coh()[q] = I.A.coh()[j];
+    I.B.mass()[q] = mass;
+    I.B.id()[q] = pid;
+    if (has_coh) I.B.coh()[q] = coh;
   }
-  if (GMODE != G2P_USF_ADVECT) {
-    // strain, volume ratio, stress
-    float sg[6];
+  if (STR) {
+    // strain increment de = sym(L) dt, strain, volume ratio, stress
+    float de[6] = {0, 0, 0, 0, 0, 0};
+    de[0] = L[0][0] * g.dt;
+    de[1] = L[1][1] * g.dt;
+    de[3] = 0.5f * (L[0][1] + L[1][0]) * g.dt;
     if (D == 3) {
-#pragma unroll
-      for (int i = 0; i < 6; ++i) sg[i] = I.A.sig(i)[j];
-    } else {
-      sg[0] = I.A.sig(0)[j];
-      sg[1] = I.A.sig(1)[j];
-      sg[2] = I.A.sig(2)[j];
-      sg[3] = I.A.sig(3)[j];
-      sg[4] = sg[5] = 0.f;
+      de[2] = L[D - 1][D - 1] * g.dt;
+      de[4] = 0.5f * (L[1][D - 1] + L[D - 1][1]) * g.dt;
+      de[5] = 0.5f * (L[0][D - 1] + L[D - 1][0]) * g.dt;
     }
 #pragma unroll
-    for (int i = 0; i < NS; ++i) I.B.eps(i)[q] = I.A.eps(i)[j] + de[i];
+    for (int i = 0; i < NS; ++i) I.B.eps(i)[q] = ep[i] + de[i];
     // V = V0 (1 + jm1):  (1 + jm1)(1 + tr) - 1 = jm1 + tr + jm1 tr
     const float tr = de[0] + de[1] + de[2];
-    const float jm1 = I.A.jm1()[j];
     I.B.jm1()[q] = jm1 + (tr + jm1 * tr);
-    float epsp = I.A.epsp()[j];
-    const float coh = I.A.coh() ? I.A.coh()[j] : I.mat.c;
     material_update(I.mat, I.matd, coh, sg, de, epsp);
 #pragma unroll
     for (int i = 0; i < NS; ++i) {

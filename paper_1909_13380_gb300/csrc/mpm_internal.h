@@ -144,6 +144,18 @@ struct InstArgs {
   int ns0, ns1;              // node strides (nx+1), (nx+1)(ny+1)
 };
 
+// Copy the table entry of instance ii into the block's shared copy (every
+// thread of the block takes part; the caller synchronises before reading it).
+// Kernels read instance constants from the shared copy: global stores cannot
+// alias shared memory, so the compiler need not reload pointers and strides
+// after every store, as it must for an entry read through a global pointer.
+__device__ __forceinline__ void copy_inst(const InstArgs *tab, int ii, InstArgs *dst) {
+  static_assert(sizeof(InstArgs) % 8 == 0, "InstArgs is copied as 8-byte words");
+  const unsigned long long *src = reinterpret_cast<const unsigned long long *>(tab + ii);
+  unsigned long long *d = reinterpret_cast<unsigned long long *>(dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(InstArgs) / 8); i += blockDim.x) d[i] = __ldg(src + i);
+}
+
 // Per-group launch description.  The prefix arrays map a block (or a work
 // item) to its instance: entry i is the first block (item) of instance i and
 // entry ninst the total.
