@@ -16,6 +16,15 @@ rank runs an independent replica of the workload on its own GPU (replicas
 only: the path has no cross-instance exchange), so value = N x per-rank work
 / max time ("weak" scaling).
 
+Beside the headline the line carries: the plain FP64 GPU step on the same
+workload ("fp64_plain"); an end-to-end run through the C-ABI from host
+buffers ("e2e"); 256 independent 2D granular columns (5k-60k particles each)
+advanced by batched steps, against stepping them one at a time ("batched");
+a serving session ("serving"): a Poisson stream (20/s) of mixed 2D/3D column
+and slope requests of 1e4-4e6 particles served with continuous batching in
+FP32 and one at a time in plain FP64, with p50/p99 per-step and end-to-end
+latency; and the FP64 CPU oracle on a bounded sample ("cpu_baseline").
+
 --impl reference times the FP64 CPU oracle (the parity reference) on the
 host cores on the same workload and metric.
 """
@@ -225,6 +234,78 @@ def run_reference(args):
     return 0
 
 
+def run_batched(args, flush, stream):
+    """256 independent 2D granular columns (5k-60k particles each) advanced by
+    batched steps (one launch per phase over all of them), against stepping
+    the same meshes one after another."""
+    import torch
+    from paper_1909_13380_gb300 import mpm
+    wls = W.columns2d_batch(count=args.batch_count)
+    ntot = sum(w.n for w in wls)
+    sims = [mpm.Simulation(w, stream=C.c_void_p(stream.cuda_stream)) for w in wls]
+    b = mpm.mpm_batch_create(stream.cuda_stream)
+    k = max(1, min(args.steps, 20))
+    try:
+        for s_ in sims:
+            mpm.mpm_batch_admit(b, s_.h)
+        with torch.cuda.stream(stream):
+            mpm.mpm_batch_step(b, args.warmup)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+            for i in range(k):
+                ev[i][0].record(stream)
+                mpm.mpm_batch_step(b, 1)
+                ev[i][1].record(stream)
+                flush.zero_()
+        stream.synchronize()
+        ms = [a.elapsed_time(c) for a, c in ev]
+        status = mpm.mpm_batch_poll(b, len(sims))
+        for i in range(len(sims)):
+            mpm.mpm_batch_evict(b, i)
+        # the same meshes stepped one at a time (each mesh its own launches)
+        with torch.cuda.stream(stream):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for s_ in sims:
+                s_.step(1)
+            e1.record(stream)
+        stream.synchronize()
+        ms_seq = e0.elapsed_time(e1)
+    finally:
+        mpm.mpm_batch_destroy(b)
+        for s_ in sims:
+            s_.close()
+    ms_step = float(np.median(ms))
+    return {"workload": f"{len(wls)} independent 2D granular columns, 5k-60k particles each (log-uniform)",
+            "particles": int(ntot), "value": ntot / (ms_step * 1e-3), "unit": METRIC,
+            "ms_per_batched_step": ms_step, "steps": k,
+            "one_at_a_time": {"value": ntot / (ms_seq * 1e-3), "ms_per_step_of_all": ms_seq},
+            "batching_speedup": ms_seq / ms_step,
+            "failed": int(sum(1 for x in status if x != mpm.MPM_OK)),
+            "gpu_launches_per_batched_step": 9}
+
+
+def run_serving(args):
+    """Poisson stream of mixed 2D/3D column and slope requests served with
+    continuous batching (FP32 mixed) and one at a time in plain FP64."""
+    from paper_1909_13380_gb300 import serve
+    reqs = W.serving_requests(count=args.serve_requests, step_scale=args.serve_step_scale)
+    wls32 = [r.workload() for r in reqs]
+    out = {"requests": len(reqs), "arrival_rate_per_s": 20.0,
+           "sample": f"{len(reqs)} requests, 1e4-4e6 particles (log-uniform), 1000-20000 steps (log-uniform) "
+                     f"x {args.serve_step_scale:g}, kinds {'/'.join(W.REQUEST_KINDS)}"}
+    for name, kw in (("fp32_continuous_batching", dict(batched=True)),
+                     ("fp64_one_at_a_time", dict(precision=W.FP64_PLAIN, batched=False))):
+        eng = serve.GpuEngine(**kw)
+        try:
+            done, lat, total = serve.Server(eng, chunk=args.serve_chunk).run(reqs, wls32)
+        finally:
+            eng.shutdown()
+        rep = serve.report(done, lat, total)
+        rep["h2d_bytes"], rep["d2h_bytes"] = eng.h2d, eng.d2h
+        out[name] = rep
+    return out
+
+
 def run_gb300(args):
     import torch
     from paper_1909_13380_gb300 import mpm
@@ -321,6 +402,13 @@ def run_gb300(args):
                "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(d2h / args.steps),
                "seconds": t1 - t0, "includes": "mesh creation, host->device upload, K steps, device->host read"}
 
+    # ---- batched small meshes and the serving loop (rank 0) -----------------
+    batched = serving = None
+    if rank == 0 and not args.no_batch:
+        batched = run_batched(args, flush, stream)
+    if rank == 0 and not args.no_serving:
+        serving = run_serving(args)
+
     # ---- CPU oracle baseline (rank 0, N = 1) ---------------------------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -347,7 +435,7 @@ def run_gb300(args):
                               "algorithmic_bytes_per_particle": ab["step"]},
             "phases_ms": dict(zip(names, [float(x) for x in ph_mean])),
             "clocks": clocks, "gpu_launches": per_step * args.steps,
-            "e2e": e2e, "fp64_plain": fp64, "cpu_baseline": cpu,
+            "e2e": e2e, "fp64_plain": fp64, "batched": batched, "serving": serving, "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -368,6 +456,12 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-batch", action="store_true", help="skip the 256 batched 2D columns")
+    ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving session")
+    ap.add_argument("--serve-requests", type=int, default=32)
+    ap.add_argument("--serve-step-scale", type=float, default=1.0 / 50)
+    ap.add_argument("--serve-chunk", type=int, default=16)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3

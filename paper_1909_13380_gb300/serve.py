@@ -1,0 +1,264 @@
+"""Serving loop: continuous batching of independent explicit MPM simulations.
+
+Requests (a mesh, its particles and a step count) arrive over time.  Each is
+admitted as soon as the device has memory for it (its footprint against the
+free HBM), its state stays resident, and every admitted simulation advances
+in the same batched steps -- one launch per phase over all of them, replayed
+from a CUDA graph -- until it has taken its steps; then its result (particle
+positions, velocities and stresses) is read back and its memory released.
+Admission happens between chunks of batched steps, so requests that arrive
+while others run join them without waiting for the batch to drain, and the
+upload of a newly arrived request overlaps the running chunk.
+
+The paper runs one simulation per process (CODE OVERVIEW, DATA STRUCTURES);
+this loop is the serving form of the same explicit step.  All arithmetic runs
+in the CUDA library; this module only schedules.
+
+`Server.run` is written against a small engine interface (`GpuEngine` below)
+so that its scheduling can be tested on the host with a fake engine.
+"""
+from __future__ import annotations
+
+import collections
+import time
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import workloads as W
+
+RESULT_FIELDS = ("pos", "vel", "stress")
+ERR_OOM = -2          # MPM_ERR_OOM: the request does not fit the free device memory
+
+
+@dataclass
+class Finished:
+    rid: int
+    kind: str
+    n: int
+    steps: int
+    arrival: float
+    admitted: float
+    finished: float
+    status: int
+    result: dict | None = None
+
+    @property
+    def e2e(self) -> float:
+        return self.finished - self.arrival
+
+
+@dataclass
+class _Active:
+    rid: int
+    sim: object
+    remaining: int
+    admitted: float
+
+
+class GpuEngine:
+    """The CUDA library behind the serving loop.  `batched` selects
+    continuous batching (one batch over every admitted FP32 simulation) or
+    one simulation at a time (any precision)."""
+
+    def __init__(self, precision=W.FP32_MIXED, batched=True, reserve_bytes=2 << 30):
+        import torch
+
+        from . import mpm
+        self.torch, self.mpm = torch, mpm
+        self.precision = precision
+        self.batched = batched
+        self.reserve = int(reserve_bytes)
+        self.side = torch.cuda.Stream()          # uploads and result reads (and unbatched steps)
+        self.bstream = torch.cuda.Stream()       # batched steps
+        self.batch = mpm.mpm_batch_create(self.bstream.cuda_stream) if batched else None
+        self.h2d = 0
+        self.d2h = 0
+
+    def footprint(self, wl) -> int:
+        d = self.mpm.make_desc(wl.dim, wl.ncells, wl.h, precision=self.precision, scheme=wl.scheme)
+        return self.mpm.mpm_footprint(d, wl.n, wl.coh is not None)
+
+    def free_bytes(self) -> int:
+        return int(self.torch.cuda.mem_get_info()[0]) - self.reserve
+
+    def create(self, wl):
+        sim = self.mpm.Simulation(wl, precision=self.precision, stream=self.side.cuda_stream)
+        self.h2d += wl.pos.nbytes + wl.vel.nbytes + wl.vol.nbytes + (wl.coh.nbytes if wl.coh is not None else 0)
+        return sim
+
+    def admit(self, sim) -> int:
+        return self.mpm.mpm_batch_admit(self.batch, sim.h)
+
+    def evict(self, slot: int):
+        self.mpm.mpm_batch_evict(self.batch, slot)
+
+    def launch(self, k: int, sims):
+        """Enqueue k steps of the admitted simulations (batched) or of the
+        one simulation given; returns a handle for `wait`."""
+        torch = self.torch
+        st = self.bstream if self.batched else self.side
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        if self.batched:
+            self.mpm.mpm_batch_step(self.batch, k)
+        else:
+            for s in sims:
+                s.step(k)
+        e1.record(st)
+        return (e0, e1)
+
+    def wait(self, handle, nslots: int, sims):
+        """Wait for a launch; returns (device ms, per-slot status)."""
+        e0, e1 = handle
+        e1.synchronize()
+        if self.batched:
+            status = self.mpm.mpm_batch_poll(self.batch, nslots)
+        else:
+            status = [s.sync() for s in sims]
+        return e0.elapsed_time(e1), status
+
+    def read(self, sim):
+        snap, st = sim.read(RESULT_FIELDS)
+        self.d2h += sum(a.nbytes for a in snap.values())
+        return snap, st
+
+    def close(self, sim):
+        sim.close()
+
+    def shutdown(self):
+        if self.batch is not None:
+            self.mpm.mpm_batch_destroy(self.batch)
+            self.batch = None
+
+
+class Server:
+    """Continuous batching over an engine.  chunk: batched steps between two
+    admission points; keep_results: return each request's result arrays."""
+
+    def __init__(self, engine, chunk=16, keep_results=False, max_active=4096, clock=time.perf_counter,
+                 sleep=time.sleep):
+        self.eng = engine
+        self.chunk = int(chunk)
+        self.keep = keep_results
+        self.max_active = max_active
+        self.clock = clock
+        self.sleep = sleep
+
+    def run(self, requests, workloads):
+        """Serve `requests` (sorted by arrival) whose inputs are `workloads`
+        (prepared by the caller: the client builds a request before it
+        arrives).  Returns (finished requests, per-step latencies in ms with
+        their step counts, session seconds)."""
+        eng = self.eng
+        order = sorted(range(len(requests)), key=lambda i: requests[i].arrival)
+        queue = collections.deque()
+        active: dict[int, _Active] = {}
+        single: list[_Active] = []        # one-at-a-time engines
+        done: list[Finished] = []
+        lat: list[tuple[float, int]] = []
+        nxt = 0
+        t0 = self.clock()
+        nslots = 0
+
+        def now():
+            return self.clock() - t0
+
+        def arrivals():
+            nonlocal nxt
+            while nxt < len(order) and requests[order[nxt]].arrival <= now():
+                queue.append(order[nxt])
+                nxt += 1
+
+        def admit_ready(staged):
+            # FIFO by free memory: the head waits until it fits
+            while queue and len(active) + len(staged) + len(single) < self.max_active:
+                if not eng.batched and (single or staged):
+                    break
+                i = queue[0]
+                if eng.footprint(workloads[i]) > eng.free_bytes():
+                    if active or single or staged:
+                        break                     # wait for memory to free up
+                    queue.popleft()               # larger than the whole free device
+                    r = requests[i]
+                    t = now()
+                    done.append(Finished(i, r.kind, workloads[i].n, r.steps, r.arrival, t, t, ERR_OOM))
+                    continue
+                queue.popleft()
+                staged.append((i, eng.create(workloads[i]), now()))
+
+        def finish(a: _Active, status: int):
+            snap = None
+            if self.keep or status == 0:
+                snap, st = eng.read(a.sim)
+                status = status or st
+            eng.close(a.sim)
+            r = requests[a.rid]
+            done.append(Finished(a.rid, r.kind, workloads[a.rid].n, r.steps, r.arrival, a.admitted, now(),
+                                 status, snap if self.keep else None))
+
+        staged: list = []
+        while nxt < len(order) or queue or active or single or staged:
+            arrivals()
+            admit_ready(staged)
+            for i, sim, t_adm in staged:
+                a = _Active(i, sim, requests[i].steps, t_adm)
+                if eng.batched:
+                    slot = eng.admit(sim)
+                    active[slot] = a
+                    nslots = max(nslots, slot + 1)
+                else:
+                    single.append(a)
+            staged = []
+            running = list(active.values()) if eng.batched else single
+            if not running:
+                if nxt < len(order):
+                    self.sleep(max(0.0, requests[order[nxt]].arrival - now()))
+                continue
+            k = min(self.chunk, min(a.remaining for a in running))
+            h = eng.launch(k, [a.sim for a in running])
+            # arrivals during the chunk are uploaded while it runs
+            arrivals()
+            admit_ready(staged)
+            ms, status = eng.wait(h, nslots, [a.sim for a in running])
+            lat.append((ms / k, k))
+            if eng.batched:
+                for slot in list(active):
+                    a = active[slot]
+                    a.remaining -= k
+                    st = status[slot]
+                    if a.remaining == 0 or st != 0:
+                        eng.evict(slot)
+                        del active[slot]
+                        finish(a, st)
+            else:
+                a = single[0]
+                a.remaining -= k
+                if a.remaining == 0 or status[0] != 0:
+                    single.pop(0)
+                    finish(a, status[0])
+        return done, lat, now()
+
+
+def percentiles(values, weights=None):
+    v = np.asarray(values, np.float64)
+    if v.size == 0:
+        return {"p50": None, "p99": None, "mean": None}
+    if weights is not None:
+        v = np.repeat(v, np.asarray(weights, np.int64))
+    return {"p50": float(np.percentile(v, 50)), "p99": float(np.percentile(v, 99)), "mean": float(v.mean())}
+
+
+def report(done, lat, session_s):
+    """Summary of a session: throughput and p50 / p99 latencies."""
+    ps = sum(f.n * f.steps for f in done)
+    return {
+        "requests": len(done),
+        "failed": sum(1 for f in done if f.status != 0),
+        "particle_steps": int(ps),
+        "session_s": session_s,
+        "particle_steps_per_s": ps / session_s if session_s > 0 else None,
+        "step_ms": percentiles([x for x, _ in lat], [k for _, k in lat]),
+        "e2e_s": percentiles([f.e2e for f in done]),
+        "queue_s": percentiles([f.admitted - f.arrival for f in done]),
+    }

@@ -195,6 +195,106 @@ def slope3d(ncells=(800, 200, 200), h=0.05, crest=8.0, plateau=8.5, seed=SEED_BA
         meta=dict(crest=crest, plateau=plateau, filled_cells=int(cells.shape[0])))
 
 
+def slope2d(ncells, h=0.05, crest=8.0, plateau=8.5, seed=SEED_BASE + 6, precision=FP32_MIXED,
+            steps=2000, name=None) -> Workload:
+    """2D plane-strain slope on quads, the x-y section of `slope3d` (y up):
+    plateau of height `crest` up to x = `plateau`, then a 45-degree face;
+    4 Gauss particles per filled cell; lognormal cohesion per filled cell
+    (mean 10 kPa, CoV 0.3); fixed base, rollers on both sides."""
+    nx, ny = ncells[0], ncells[1]
+    xc = (np.arange(nx) + 0.5) * h
+    yc = (np.arange(ny) + 0.5) * h
+    top = np.where(xc <= plateau, crest, crest - (xc - plateau))
+    inside = yc[:, None] < top[None, :]                                     # (ny, nx)
+    yy, xx = np.nonzero(inside)                                             # y-major, x fastest
+    cells = np.stack([xx, yy], axis=1)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sig_ln = math.sqrt(math.log(1.0 + 0.3 ** 2))
+    mu_ln = math.log(10e3) - 0.5 * sig_ln ** 2
+    coh = np.repeat(rng.lognormal(mu_ln, sig_ln, size=cells.shape[0]), 4)
+    pos = gauss_fill(cells, h, (0.0, 0.0), 2)
+    vel = np.zeros_like(pos)
+    vol = np.full(pos.shape[0], h * h / 4.0)
+    return Workload(
+        name=name or f"slope_2d_{nx}x{ny}", dim=2, ncells=(nx, ny, 1), h=h, origin=(0.0, 0.0, 0.0),
+        face_bc=(ROLLER, ROLLER, FIXED, FREE, FREE, FREE), face_mu=(0.0,) * 6,
+        gravity=(0.0, -9.81, 0.0), dt=1e-5, scheme=USL, precision=precision,
+        material=_mc(E=50e6, rho=2000.0, c=10e3), pos=pos, vel=vel, vol=vol, coh=coh, steps=steps,
+        meta=dict(crest=crest, plateau=plateau, filled_cells=int(cells.shape[0])))
+
+
+REQUEST_KINDS = ("column2d", "column3d", "slope2d", "slope3d")
+
+
+def request_workload(kind: str, n_target: float, seed: int, steps: int, precision=FP32_MIXED) -> Workload:
+    """One serving request of about `n_target` particles.
+      column2d  aspect a ~ U[0.5, 4]; W = sqrt(n / 4a), H = a W cells of 2.5 mm
+      column3d  aspect a ~ U[0.5, 4]; W x W x aW cells of 5 mm, mesh as the
+                200 x 40 x 100 column ((2 + 3a) W long, W wide, H + 4 high)
+      slope2d   plateau and face of height Hc, Hc = sqrt(n / 6) cells of 5 cm
+      slope3d   the same section extruded over Hc / 2 cells."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = float(n_target)
+    if kind == "column2d":
+        a = float(rng.uniform(0.5, 4.0))
+        W = max(1, int(round(math.sqrt(n / (4.0 * a)))))
+        H = max(1, int(round(a * W)))
+        return column2d(W, H, mesh_cells=(int(round((2.0 + 3.0 * a) * W)), H + 4), precision=precision,
+                        steps=steps, name=f"column2d_{W}x{H}")
+    if kind == "column3d":
+        a = float(rng.uniform(0.5, 4.0))
+        W = max(1, int(round((n / (8.0 * a)) ** (1.0 / 3.0))))
+        H = max(1, int(round(a * W)))
+        return column3d(ncells=(int(round((2.0 + 3.0 * a) * W)), W, H + 4), col_cells=(W, W, H),
+                        precision=precision, steps=steps, name=f"column3d_{W}x{W}x{H}")
+    hs = 0.05
+    if kind == "slope2d":
+        Hc = max(2, int(round(math.sqrt(n / 6.0))))
+        return slope2d((2 * Hc + Hc // 2, Hc + 4), h=hs, crest=Hc * hs, plateau=Hc * hs,
+                       seed=int(rng.integers(1 << 31)), precision=precision, steps=steps,
+                       name=f"slope2d_H{Hc}")
+    if kind == "slope3d":
+        Hc = max(2, int(round((n / 6.0) ** (1.0 / 3.0))))
+        wl = slope3d(ncells=(2 * Hc + Hc // 2, max(1, Hc // 2), Hc + 4), h=hs, crest=Hc * hs, plateau=Hc * hs,
+                     seed=int(rng.integers(1 << 31)), precision=precision, steps=steps)
+        wl.name = f"slope3d_H{Hc}"
+        return wl
+    raise ValueError(kind)
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival: float      # seconds after the start of the session
+    kind: str
+    n_target: int
+    steps: int
+    seed: int
+
+    def workload(self, precision=FP32_MIXED) -> Workload:
+        return request_workload(self.kind, self.n_target, self.seed, self.steps, precision)
+
+
+def serving_requests(count=32, rate=20.0, n_range=(1e4, 4e6), steps_range=(1000, 20000), step_scale=1.0 / 50,
+                     seed=SEED_BASE + 4, kinds=REQUEST_KINDS):
+    """A Poisson stream of mixed requests: exponential inter-arrival times of
+    mean 1 / rate, kind uniform over `kinds`, particle count and step count
+    log-uniform over their ranges; the step count is then multiplied by
+    `step_scale` (at least 1), which keeps a bounded session's offered load
+    below the GPU's capacity."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t = 0.0
+    out = []
+    for i in range(count):
+        t += float(rng.exponential(1.0 / rate))
+        kind = kinds[int(rng.integers(len(kinds)))]
+        n = int(round(math.exp(rng.uniform(math.log(n_range[0]), math.log(n_range[1])))))
+        st = math.exp(rng.uniform(math.log(steps_range[0]), math.log(steps_range[1])))
+        steps = max(1, int(round(st * step_scale)))
+        out.append(Request(i, t, kind, n, steps, int(rng.integers(1 << 31))))
+    return out
+
+
 def random_particles(mesh_cells, h, n, seed, dim=3, margin=1, vel_scale=0.1, sig_scale=1e3):
     """Uniform random particle positions inside the mesh (away from the
     boundary by `margin` cells), random velocity and random symmetric stress:
