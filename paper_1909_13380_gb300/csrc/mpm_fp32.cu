@@ -8,12 +8,13 @@
 // (nodal velocity and frictional conditions).
 //
 // GPU design (replaces the per-node mutex), after the binning of mpm_bin.cu:
-//   p2g_tile   one CTA per 4x4x4 (8x8) cell tile: loads the tile's particles
-//              in binning order (coalesced), evaluates each particle's corner
-//              contributions once, sums them per cell in a fixed sequential
-//              order through a shared-memory staging buffer (compensated
-//              sums), sums cells into the tile's node box and writes the box
-//              to the tile's own slot -- no atomics, bit-reproducible;
+//   p2g_tile   one CTA per 4x4x4 (8x8) cell tile, one thread per (cell,
+//              corner): stages the tile's particles (binning order,
+//              coalesced) in shared memory, each thread sums its corner's
+//              contributions over its cell's particles in order in
+//              registers, cells are summed into the tile's node box
+//              (compensated sums) and the box is written to the tile's own
+//              slot -- no atomics, bit-reproducible;
 //   node_tile  one CTA per tile: final nodal values of the box, summing the
 //              slots of the (at most 2^D) tiles that share each node in
 //              ascending tile order, then v = P/m, a = f/m + g, v' = v + a dt
@@ -31,8 +32,6 @@
 namespace mpm {
 namespace {
 
-constexpr int P2G_T = 128;  // threads per P2G CTA
-constexpr int P2G_W = P2G_T / 32;
 constexpr int NODE_T = 128;
 constexpr int G2P_T = 256;
 
@@ -53,25 +52,6 @@ __device__ __forceinline__ int next_tile(int32_t *ctr, int slot) {
   const int w = s_w;
   __syncthreads();
   return w;
-}
-
-// Start of warp w's share of [s, e): the first cell boundary at or after
-// s + w (e - s) / NW, so that no cell is split between warps.
-template <int NW>
-__device__ __forceinline__ int warp_split(const uint32_t *keys, int s, int e, int w) {
-  if (w <= 0) return s;
-  if (w >= NW) return e;
-  int p = s + (int)(((int64_t)(e - s) * w) / NW);
-  if (p <= s) p = s + 1;
-  const int lane = threadIdx.x & 31;
-  for (;;) {
-    if (p >= e) return e;
-    const int q = p + lane;
-    const bool brk = (q >= e) || (keys[q] != keys[q - 1]);
-    const unsigned m = __ballot_sync(0xffffffffu, brk);
-    if (m) return p + __ffs(m) - 1;
-    p += 32;
-  }
 }
 
 __device__ __forceinline__ void tile_coords(const Geo &g, int t, int tc[3]) {
@@ -120,70 +100,95 @@ __device__ __forceinline__ void corner_shape(int a, const float w0[D], const flo
 }
 
 // ---------------------------------------------------------------------------
-// P2G: value index v = corner * NCH + channel; channels USL (m, P_k, f_k),
-// MOM (m, P_k), FORCE (f_k), f_k = -V sum_j sig_kj dN/dx_j.
+// P2G: one CTA per tile, one thread per (cell, corner).  The tile's particles
+// (binning order, so grouped by cell) are staged in shared memory in chunks
+// of one particle per thread: offset u, and the per-particle factors of the
+// channels -- m and m v (mass, momentum), nV sig with nV = -V (internal
+// force f_k = -V sum_j sig_kj dN/dx_j).  Then the thread of (cell c, corner
+// a) runs over the particles of c in binning order and accumulates its
+// corner's channels in registers: each (cell, corner, channel) sum is a plain
+// sequential FP32 sum, independent of the launch.  Cell sums go to the node
+// box (compensated, ascending cell order) and the box to the tile's slot.
+// Value index v = corner * NCH + channel; channels USL (m, P_k, f_k), MOM
+// (m, P_k), FORCE (f_k).
 // ---------------------------------------------------------------------------
 template <int D, int MODE>
-constexpr size_t p2g_smem() {
-  return sizeof(float) * (CELLS_PER_TILE * (1 << D) * p2g_channels<D, MODE>() + P2G_W * 32 * 33);
-}
+struct P2GRec {
+  static constexpr bool HAS_M = MODE != P2G_FORCE, HAS_F = MODE != P2G_MOM;
+  static constexpr int NSV = D == 3 ? 6 : 3;                   // nV sig (xx yy zz xy yz xz | xx yy xy)
+  static constexpr int NF = D + (HAS_M ? 1 + D : 0) + (HAS_F ? NSV : 0);
+  static constexpr int NQ = (NF + 3) / 4;                      // float4 chunks per particle
+  static constexpr int CH = CELLS_PER_TILE << D;               // threads = particles per chunk
+  static constexpr int NV = (1 << D) * p2g_channels<D, MODE>();
+  static constexpr size_t REC_BYTES = sizeof(float4) * NQ * CH;
+  static constexpr size_t CELLP_BYTES = sizeof(float) * CELLS_PER_TILE * NV;
+  static constexpr size_t SMEM = (REC_BYTES > CELLP_BYTES ? REC_BYTES : CELLP_BYTES);
+};
 
 template <int D, int MODE>
-__global__ void __launch_bounds__(P2G_T, 4) p2g_tile(GroupArgs G, int work_slot) {
+constexpr size_t p2g_smem() {
+  return P2GRec<D, MODE>::SMEM;
+}
+
+// Slot of particle i of a chunk: the low three bits are XORed with the next
+// three, so that the cells of a warp, whose current particles are often a
+// multiple of eight apart, read different shared-memory banks.
+__device__ __forceinline__ int rec_slot(int i) { return (i & ~7) | ((i ^ (i >> 3)) & 7); }
+
+template <int D, int MODE>
+__global__ void __launch_bounds__(CELLS_PER_TILE << D, (D == 3 ? 2 : 4)) p2g_tile(GroupArgs G, int work_slot) {
+  using R = P2GRec<D, MODE>;
   constexpr int NC = 1 << D;
   constexpr int NCH = p2g_channels<D, MODE>();
-  constexpr int NV = NC * NCH;
-  constexpr int NPASS = (NV + 31) / 32;
+  constexpr int NV = R::NV;
+  constexpr int CH = R::CH;
+  constexpr int NQ = R::NQ;
   constexpr int BN = box_nodes<D>();
   constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ;
-  constexpr bool HAS_M = MODE != P2G_FORCE;
-  constexpr bool HAS_F = MODE != P2G_MOM;
-  extern __shared__ float sm[];
-  float *cellP = sm;  // [64][NV]
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float *wst = sm + CELLS_PER_TILE * NV + warp * 32 * 33;  // [32][33]
-  const int total = G.act_items[G.ninst];
+  constexpr bool HAS_M = R::HAS_M, HAS_F = R::HAS_F;
+  extern __shared__ float4 sm4[];
+  float4 *rec = sm4;                          // [NQ][CH] float4
+  float *cellP = reinterpret_cast<float *>(sm4);  // [64][NV], after the chunks
+  __shared__ int cs[CELLS_PER_TILE], ce[CELLS_PER_TILE], stamp[CELLS_PER_TILE];
   __shared__ InstArgs sI;
+  const int tid = threadIdx.x;
+  const int my_cell = tid / NC, my_corner = tid % NC;
+  if (tid < CELLS_PER_TILE) stamp[tid] = -1;
+  int chunk_id = 0;
+  const int total = G.act_items[G.ninst];
 
   for (;;) {
     const int wi = next_tile(G.work, work_slot);
     if (wi >= total) break;
     const int ii = find_inst(G.act_items, G.ninst, wi);
     copy_inst(G.inst, ii, &sI);
-    for (int i = threadIdx.x; i < CELLS_PER_TILE * NV; i += P2G_T) cellP[i] = 0.f;
     __syncthreads();
     const InstArgs &I = sI;
     const Geo &g = I.geo;
     float *slots_out = MODE == P2G_FORCE ? I.s.slots2 : I.s.slots1;
     const int t = I.s.active[wi - G.act_items[ii]];
     const int s = I.new_start[t], e = I.new_start[t + 1];
-    const int ws = warp_split<P2G_W>(I.keys_out, s, e, warp);
-    const int we = warp_split<P2G_W>(I.keys_out, s, e, warp + 1);
+    float w0[D], w1[D], acc[NCH];
+#pragma unroll
+    for (int ch = 0; ch < NCH; ++ch) acc[ch] = 0.f;
 
-    for (int b0 = ws; b0 < we; b0 += 32) {
-      const int q = b0 + lane;
-      const bool valid = q < we;
-      const int nb = min(32, we - b0);
-      int lc = CELLS_PER_TILE + lane;
-      float w0[D], w1[D];
-      float mm = 0.f, mv[D], sv[D][D];
-#pragma unroll
-      for (int k = 0; k < D; ++k) {
-        w0[k] = w1[k] = mv[k] = 0.f;
-#pragma unroll
-        for (int j = 0; j < D; ++j) sv[k][j] = 0.f;
-      }
-      if (valid) {
-        lc = I.keys_out[q] & (CELLS_PER_TILE - 1);
+    for (int c0 = s; c0 < e; c0 += CH) {
+      // ---- stage this chunk: particle q = c0 + tid
+      const int q = c0 + tid;
+      const int c1 = min(e, c0 + CH);
+      if (q < c1) {
         const int j = I.perm_out[q];
-        float u[D];
+        const int lc = I.keys_out[q] & (CELLS_PER_TILE - 1);
+        float f[4 * NQ];
 #pragma unroll
-        for (int k = 0; k < D; ++k) u[k] = I.A.off(k)[j];
-        corner_weights<D>(u, w0, w1);
-        mm = I.A.mass()[j];
+        for (int k = 0; k < 4 * NQ; ++k) f[k] = 0.f;
+#pragma unroll
+        for (int k = 0; k < D; ++k) f[k] = I.A.off(k)[j];
+        const float mm = I.A.mass()[j];
         if (HAS_M) {
+          f[D] = mm;
 #pragma unroll
-          for (int k = 0; k < D; ++k) mv[k] = mm * I.A.vel(k)[j];
+          for (int k = 0; k < D; ++k) f[D + 1 + k] = mm * I.A.vel(k)[j];
         }
         if (HAS_F) {
           // FORCE (USF) reads the stress updated earlier this step, stored in
@@ -191,84 +196,90 @@ __global__ void __launch_bounds__(P2G_T, 4) p2g_tile(GroupArgs G, int work_slot)
           const PBuf &S = (MODE == P2G_FORCE) ? I.B : I.A;
           const int js = (MODE == P2G_FORCE) ? q : j;
           const float nV = -mm * g.inv_rho * (1.f + S.jm1()[js]);
+          constexpr int o = HAS_M ? 2 * D + 1 : D;
           if (D == 3) {
-            const float sxx = S.sig(0)[js], syy = S.sig(1)[js], szz = S.sig(2)[js];
-            const float sxy = S.sig(3)[js], syz = S.sig(4)[js], sxz = S.sig(5)[js];
-            const float t3[3][3] = {{sxx, sxy, sxz}, {sxy, syy, syz}, {sxz, syz, szz}};
 #pragma unroll
-            for (int a = 0; a < D; ++a)
-#pragma unroll
-              for (int b = 0; b < D; ++b) sv[a][b] = nV * t3[a][b];
+            for (int k = 0; k < 6; ++k) f[o + k] = nV * S.sig(k)[js];
           } else {
-            const float sxx = S.sig(0)[js], syy = S.sig(1)[js], sxy = S.sig(3)[js];
-            const float t2[2][2] = {{sxx, sxy}, {sxy, syy}};
-#pragma unroll
-            for (int a = 0; a < D; ++a)
-#pragma unroll
-              for (int b = 0; b < D; ++b) sv[a][b] = nV * t2[a][b];
+            f[o] = nV * S.sig(0)[js];
+            f[o + 1] = nV * S.sig(1)[js];
+            f[o + 2] = nV * S.sig(3)[js];
           }
         }
+        const int sl = rec_slot(tid);
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) rec[k * CH + sl] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
+        // run boundaries of the cell within the chunk
+        const bool first = q == c0 || (int)(I.keys_out[q - 1] & (CELLS_PER_TILE - 1)) != lc;
+        const bool last = q == c1 - 1 || (int)(I.keys_out[q + 1] & (CELLS_PER_TILE - 1)) != lc;
+        if (first) {
+          cs[lc] = tid;
+          stamp[lc] = chunk_id;
+        }
+        if (last) ce[lc] = tid + 1;
       }
-      // run ends inside this batch: lane k ends a run when the next lane's
-      // cell differs or it is the last valid lane
-      const int lc_next = __shfl_down_sync(0xffffffffu, lc, 1);
-      const unsigned ends = __ballot_sync(0xffffffffu, valid && (lane == nb - 1 || lc_next != lc));
-
+      __syncthreads();
+      // ---- accumulate my (cell, corner) over the cell's particles in order
+      if (stamp[my_cell] == chunk_id) {
+        const int i0 = cs[my_cell], i1 = ce[my_cell];
+        for (int i = i0; i < i1; ++i) {
+          const int sl = rec_slot(i);
+          float f[4 * NQ];
 #pragma unroll
-      for (int pass = 0; pass < NPASS; ++pass) {
-        // stage this pass's values of my particle: wst[v][lane]
+          for (int k = 0; k < NQ; ++k) {
+            const float4 r = rec[k * CH + sl];
+            f[4 * k] = r.x;
+            f[4 * k + 1] = r.y;
+            f[4 * k + 2] = r.z;
+            f[4 * k + 3] = r.w;
+          }
+          float u[D];
 #pragma unroll
-        for (int a = 0; a < NC; ++a) {
-          if (a * NCH + NCH <= pass * 32 || a * NCH >= pass * 32 + 32) continue;
-          float N, G[D];
-          corner_shape<D>(a, w0, w1, g.inv_h, N, G);
+          for (int k = 0; k < D; ++k) u[k] = f[k];
+          corner_weights<D>(u, w0, w1);
+          float N, Gr[D];
+          corner_shape<D>(my_corner, w0, w1, g.inv_h, N, Gr);
+          if (HAS_M) {
+            acc[0] = fmaf(f[D], N, acc[0]);
 #pragma unroll
-          for (int ch = 0; ch < NCH; ++ch) {
-            const int v = a * NCH + ch;
-            if (v < pass * 32 || v >= pass * 32 + 32) continue;
-            float val;
-            if (HAS_M && ch == 0) {
-              val = mm * N;
-            } else if (HAS_M && ch <= D) {
-              val = mv[ch - 1] * N;
+            for (int k = 0; k < D; ++k) acc[1 + k] = fmaf(f[D + 1 + k], N, acc[1 + k]);
+          }
+          if (HAS_F) {
+            constexpr int o = HAS_M ? 2 * D + 1 : D;
+            constexpr int a0 = HAS_M ? 1 + D : 0;
+            if (D == 3) {
+              // nV sig: xx yy zz xy yz xz
+              const float t3[3][3] = {{f[o], f[o + 3], f[o + 5]}, {f[o + 3], f[o + 1], f[o + 4]},
+                                      {f[o + 5], f[o + 4], f[o + 2]}};
+#pragma unroll
+              for (int k = 0; k < D; ++k)
+#pragma unroll
+                for (int jj = 0; jj < D; ++jj) acc[a0 + k] = fmaf(t3[k][jj], Gr[jj], acc[a0 + k]);
             } else {
-              const int k = HAS_M ? ch - 1 - D : ch;
-              float f = 0.f;
+              const float t2[2][2] = {{f[o], f[o + 2]}, {f[o + 2], f[o + 1]}};
 #pragma unroll
-              for (int jj = 0; jj < D; ++jj) f += sv[k][jj] * G[jj];
-              val = f;
+              for (int k = 0; k < D; ++k)
+#pragma unroll
+                for (int jj = 0; jj < D; ++jj) acc[a0 + k] = fmaf(t2[k][jj], Gr[jj], acc[a0 + k]);
             }
-            wst[(v - pass * 32) * 33 + lane] = val;
           }
         }
-        __syncwarp();
-        // lane = value index: sum the batch in particle order (at most 32
-        // terms, plain FP32), flush at run ends
-        const int v = pass * 32 + lane;
-        const float *row = wst + lane * 33;
-        float acc = 0.f;
-#pragma unroll 8
-        for (int k = 0; k < nb; ++k) {
-          acc += row[k];
-          if ((ends >> k) & 1u) {
-            const int ck = __shfl_sync(0xffffffffu, lc, k);
-            if (v < NV) cellP[ck * NV + v] += acc;
-            acc = 0.f;
-          }
-        }
-        __syncwarp();
       }
+      ++chunk_id;
+      __syncthreads();  // the next chunk overwrites the records
     }
-    __syncthreads();
 
-    // cells -> node box (ascending local cell order), compensated; -> slot
-    for (int b = threadIdx.x; b < BN; b += P2G_T) {
+    // ---- cells -> node box (ascending local cell order), compensated; -> slot
+#pragma unroll
+    for (int ch = 0; ch < NCH; ++ch) cellP[my_cell * NV + my_corner * NCH + ch] = acc[ch];
+    __syncthreads();
+    for (int b = tid; b < BN; b += CH) {
       const int bx = b % (TX + 1);
       const int by = (b / (TX + 1)) % (TY + 1);
       const int bz = D == 3 ? b / ((TX + 1) * (TY + 1)) : 0;
-      TwoAcc<float> acc[NCH];
+      TwoAcc<float> ta[NCH];
 #pragma unroll
-      for (int ch = 0; ch < NCH; ++ch) acc[ch].init();
+      for (int ch = 0; ch < NCH; ++ch) ta[ch].init();
 #pragma unroll
       for (int dz = (D == 3 ? 1 : 0); dz >= 0; --dz)
 #pragma unroll
@@ -280,10 +291,10 @@ __global__ void __launch_bounds__(P2G_T, 4) p2g_tile(GroupArgs G, int work_slot)
             const int cl = cx + TX * (cy + TY * cz);
             const int a = dx + 2 * dy + 4 * dz;
 #pragma unroll
-            for (int ch = 0; ch < NCH; ++ch) acc[ch].add(cellP[cl * NV + a * NCH + ch]);
+            for (int ch = 0; ch < NCH; ++ch) ta[ch].add(cellP[cl * NV + a * NCH + ch]);
           }
 #pragma unroll
-      for (int ch = 0; ch < NCH; ++ch) slots_out[((int64_t)t * NCH + ch) * BN + b] = acc[ch].value();
+      for (int ch = 0; ch < NCH; ++ch) slots_out[((int64_t)t * NCH + ch) * BN + b] = ta[ch].value();
     }
     __syncthreads();
   }
@@ -614,7 +625,7 @@ __global__ void __launch_bounds__(G2P_T, 3) g2p(GroupArgs G) {
 
 template <int D, int MODE>
 cudaError_t launch_p2g(const GroupArgs &G, int work_slot, cudaStream_t st) {
-  p2g_tile<D, MODE><<<G.grid, P2G_T, p2g_smem<D, MODE>(), st>>>(G, work_slot);
+  p2g_tile<D, MODE><<<G.grid, CELLS_PER_TILE << D, p2g_smem<D, MODE>(), st>>>(G, work_slot);
   return cudaGetLastError();
 }
 
