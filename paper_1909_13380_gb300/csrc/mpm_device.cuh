@@ -210,6 +210,114 @@ __device__ __forceinline__ void eig_sym3(const T s[6], T lam[3], T Q[3][3]) {
   lam[2] = A[2][2];
 }
 
+// Symmetric 3x3 eigen-decomposition in closed form with deflation (FP32).
+// Work on the normalised deviator A = (s - p I) / r, r = sqrt(J2 / 3), whose
+// eigenvalues are 2 cos(theta + 2 pi k / 3), cos(3 theta) = det(A) / 2.  Of
+// the largest and the smallest, take the one farther from the middle value:
+// its gap to both others is at least sqrt(3) / 2, so it is insensitive to the
+// error of the arc-cosine (a stationary point of the cosine where the other
+// two meet) and its eigenvector, the cross product of two rows of A - mu I
+// (the pair of largest norm), is well conditioned.  The remaining pair is the
+// 2x2 problem in the plane orthogonal to that vector, solved by one exact
+// rotation (stable tangent formula), which keeps a near-double pair accurate.
+// Eigenvalues come back as p + r mu, eigenvectors as the columns of Q.
+__device__ __forceinline__ void eig_sym3_closed(const float s[6], float lam[3], float Q[3][3]) {
+  const float p = (s[0] + s[1] + s[2]) * (1.f / 3.f);
+  const float d0 = s[0] - p, d1 = s[1] - p, d2 = s[2] - p;
+  const float j2 = 0.5f * (d0 * d0 + d1 * d1 + d2 * d2) + s[3] * s[3] + s[4] * s[4] + s[5] * s[5];
+  if (!(j2 > 1e-30f)) {  // isotropic (or a deviator below any stress of interest)
+    lam[0] = s[0];
+    lam[1] = s[1];
+    lam[2] = s[2];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) Q[r][c] = (r == c) ? 1.f : 0.f;
+    return;
+  }
+  const float r = sqrtf(j2 * (1.f / 3.f));
+  const float ir = 1.f / r;
+  const float A[3][3] = {{d0 * ir, s[3] * ir, s[5] * ir}, {s[3] * ir, d1 * ir, s[4] * ir}, {s[5] * ir, s[4] * ir, d2 * ir}};
+  const float det = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[1][2]) - A[0][1] * (A[0][1] * A[2][2] - A[1][2] * A[0][2]) +
+                    A[0][2] * (A[0][1] * A[1][2] - A[1][1] * A[0][2]);
+  const float c3 = fminf(1.f, fmaxf(-1.f, 0.5f * det));
+  const float th = acosf(c3) * (1.f / 3.f);
+  float sn, cs;
+  sincosf(th, &sn, &cs);
+  const float sq3 = 1.7320508f;
+  const float mu1 = 2.f * cs, mu3 = -cs - sq3 * sn, mu2 = -cs + sq3 * sn;
+  const float mud0 = (mu1 - mu2 >= mu2 - mu3) ? mu1 : mu3;
+  // eigenvector of the distinct value: largest cross product of two rows
+  float R[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) R[i][j] = A[i][j] - (i == j ? mud0 : 0.f);
+  float n[3], best = -1.f;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int a = k == 2 ? 1 : 0, b = k == 0 ? 1 : 2;  // row pairs (0,1) (0,2) (1,2)
+    const float cx = R[a][1] * R[b][2] - R[a][2] * R[b][1];
+    const float cy = R[a][2] * R[b][0] - R[a][0] * R[b][2];
+    const float cz = R[a][0] * R[b][1] - R[a][1] * R[b][0];
+    const float m2 = cx * cx + cy * cy + cz * cz;
+    if (m2 > best) {
+      best = m2;
+      n[0] = cx;
+      n[1] = cy;
+      n[2] = cz;
+    }
+  }
+  if (!(best > 1e-30f)) {  // cannot happen for a rank-2 A - mu I; keep the iterative solver as a guard
+    eig_sym3<float>(s, lam, Q);
+    return;
+  }
+  const float inr = rsqrtf(best);
+  n[0] *= inr;
+  n[1] *= inr;
+  n[2] *= inr;
+  // orthonormal basis e1, e2 of the plane orthogonal to n
+  float e1[3];
+  if (fabsf(n[0]) >= fabsf(n[1])) {
+    const float k = rsqrtf(n[0] * n[0] + n[2] * n[2]);
+    e1[0] = -n[2] * k;
+    e1[1] = 0.f;
+    e1[2] = n[0] * k;
+  } else {
+    const float k = rsqrtf(n[1] * n[1] + n[2] * n[2]);
+    e1[0] = 0.f;
+    e1[1] = n[2] * k;
+    e1[2] = -n[1] * k;
+  }
+  const float e2[3] = {n[1] * e1[2] - n[2] * e1[1], n[2] * e1[0] - n[0] * e1[2], n[0] * e1[1] - n[1] * e1[0]};
+  float An[3], A1[3], A2[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    An[i] = A[i][0] * n[0] + A[i][1] * n[1] + A[i][2] * n[2];
+    A1[i] = A[i][0] * e1[0] + A[i][1] * e1[1] + A[i][2] * e1[2];
+    A2[i] = A[i][0] * e2[0] + A[i][1] * e2[1] + A[i][2] * e2[2];
+  }
+  const float mud = n[0] * An[0] + n[1] * An[1] + n[2] * An[2];  // Rayleigh quotient
+  const float b11 = e1[0] * A1[0] + e1[1] * A1[1] + e1[2] * A1[2];
+  const float b22 = e2[0] * A2[0] + e2[1] * A2[1] + e2[2] * A2[2];
+  const float b12 = e1[0] * A2[0] + e1[1] * A2[1] + e1[2] * A2[2];
+  float t = 0.f;
+  if (b12 != 0.f) {
+    const float tj = (b22 - b11) / (2.f * b12);
+    t = (tj >= 0.f ? 1.f : -1.f) / (fabsf(tj) + sqrtf(tj * tj + 1.f));
+  }
+  const float c = rsqrtf(t * t + 1.f), sr = t * c;
+  lam[0] = p + r * mud;
+  lam[1] = p + r * (b11 - t * b12);
+  lam[2] = p + r * (b22 + t * b12);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    Q[i][0] = n[i];
+    Q[i][1] = c * e1[i] - sr * e2[i];
+    Q[i][2] = sr * e1[i] + c * e2[i];
+  }
+}
+
 // Principal stresses sorted s1 >= s2 >= s3 with their eigenvector columns
 // (stable for ties: a swap only when strictly smaller).
 template <typename T>
@@ -305,8 +413,8 @@ __device__ __forceinline__ int mc_principal(const MatConst<T> &m, T c, const T s
 // cos(theta - 2 pi k / 3)), then the yield function with a margin larger than
 // the error of that form in FP32 (worst near repeated eigenvalues, where the
 // arc-cosine loses about half the digits).  Only a cheap filter: a trial that
-// is not clearly elastic goes through the full Jacobi return, so the result
-// is the same as without the filter.
+// is not clearly elastic goes through the full return (accurate eigenpairs,
+// then the yield check), so the result is the same as without the filter.
 __device__ __forceinline__ bool clearly_elastic(const MatConst<float> &m, float c, const float s[6]) {
   const float p = (s[0] + s[1] + s[2]) * (1.f / 3.f);
   const float d0 = s[0] - p, d1 = s[1] - p, d2 = s[2] - p;
@@ -327,7 +435,10 @@ __device__ __forceinline__ bool clearly_elastic(const MatConst<float> &m, float 
 template <typename T>
 __device__ __forceinline__ int mc_return(const MatConst<T> &m, T c, const T st[6], T out[6], T &depsp) {
   T lam[3], Q[3][3];
-  eig_sym3<T>(st, lam, Q);
+  if constexpr (sizeof(T) == 4)
+    eig_sym3_closed(st, lam, Q);
+  else
+    eig_sym3<T>(st, lam, Q);
   sort3_desc<T>(lam, Q);
   T r[3];
   const int br = mc_principal<T>(m, c, lam, r, depsp);

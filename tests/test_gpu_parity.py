@@ -300,3 +300,51 @@ def test_binning_with_mass_tile_crossing():
         snap, _ = sim.read(fields=("pos",))
     # everything moved about 4 x 0.9 cells to the right
     assert abs(np.mean(snap["pos"][:, 0] - pos[:, 0]) - 3.6) < 0.05
+
+
+def _degenerate_trials(rng, n, scale):
+    """Stress states with repeated or nearly repeated principal values in a
+    random frame: axisymmetric (the lateral pair equal, as in a column at
+    rest), the other pair equal, near-hydrostatic, and exactly diagonal."""
+    out = []
+    for i in range(n):
+        k = i % 5
+        if k == 0:
+            lam = np.array([-1.0, -1.0, -2.5])
+        elif k == 1:
+            lam = np.array([-1.0, -1.0 - rng.uniform(0, 1e-5), -3.0])
+        elif k == 2:
+            lam = np.array([-0.5, -3.0 + rng.uniform(0, 1e-5), -3.0])
+        elif k == 3:
+            lam = -2.0 + rng.normal(0, 1e-6, 3)
+        else:
+            lam = rng.normal(-1.0, 1.0, 3)
+        q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+        if k == 4:
+            q = np.eye(3)
+        S = (q * lam) @ q.T * scale
+        out.append([S[0, 0], S[1, 1], S[2, 2], S[0, 1], S[1, 2], S[0, 2]])
+    return np.array(out)
+
+
+@pytest.mark.parametrize("c", [0.0, 10e3])
+def test_material_update_degenerate_spectra(c):
+    """The FP32 return uses a closed-form eigen-decomposition with deflation;
+    repeated and nearly repeated principal stresses must come out as
+    accurately as well-separated ones."""
+    rng = np.random.default_rng(23)
+    n = 4000
+    sig = _degenerate_trials(rng, n, 3e4)
+    de = rng.normal(0, 2e-4, (n, 6))
+    de[::3] = 0.0   # returns of the trial state itself
+    mat_o = oracle.Material(model=oracle.MOHR_COULOMB, E=10e6, nu=0.3, rho=1800.0, phi=math.radians(30), c=c,
+                            psi=0.0)
+    mat_g = mpm.make_material(model=mpm.MPM_MOHR_COULOMB, E=10e6, nu=0.3, rho=1800.0, phi=math.radians(30),
+                              c=c, psi=0.0)
+    sig32 = sig.astype(np.float32).astype(np.float64)
+    de32 = de.astype(np.float32).astype(np.float64)
+    ref32 = np.array([oracle.stress_update(mat_o, c, sig32[i], de32[i])[0] for i in range(n)])
+    out32, _ = mpm.mpm_material_update(mat_g, mpm.MPM_FP32_MIXED, sig, de)
+    scale = np.abs(ref32).max(axis=1, keepdims=True) + 1.0
+    assert H.rel_l2(out32, ref32) <= H.TOL_STEP_FP32
+    assert np.all(np.abs(out32 - ref32) <= 2e-4 * scale)
