@@ -281,7 +281,7 @@ def run_batched(args, flush, stream):
             "one_at_a_time": {"value": ntot / (ms_seq * 1e-3), "ms_per_step_of_all": ms_seq},
             "batching_speedup": ms_seq / ms_step,
             "failed": int(sum(1 for x in status if x != mpm.MPM_OK)),
-            "gpu_launches_per_batched_step": 9}
+            "gpu_launches_per_batched_step": 8}
 
 
 def run_serving(args):
@@ -418,9 +418,9 @@ def run_gb300(args):
                          f"FP64 oracle, one thread, {dt:.1f} s"}
 
     if rank == 0:
-        # binning: bin_movers, bin_scan_totals, bin_scan_apply, bin_bucket,
-        # group_prefix, bin_tiles; then p2g, node, g2p (USF: twice each)
-        per_step = 6 + (3 if wl.scheme == W.USL else 6)
+        # binning: bin_scan_totals, bin_scan_apply, bin_bucket, group_prefix,
+        # bin_tiles; then p2g_tile, node_tile, g2p (USF: twice each)
+        per_step = 5 + (3 if wl.scheme == W.USL else 6)
         line = {
             "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,

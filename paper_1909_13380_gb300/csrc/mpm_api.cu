@@ -838,9 +838,19 @@ mpm_status mpm_read_binning(mpm_handle h, int32_t *key, int32_t *perm, int32_t *
   if (h->n == 0) return device_status(h);
   // the production binning of the stored particles, written to scratch so
   // that the next step's binning (which reads the previous binning) is intact
+  // (the binning consumes the mover counts left by the last G2P: recount
+  // them from the keys before and after, so the next step finds them intact)
   std::vector<mpm_ctx *> one(1, h);
   CK(build_group(h->grp_bin, one, false, true, h->nsm, h->st), "binning tables");
-  CK(bin_group(h->d.dim, h->grp_bin.ga[h->cur], h->st), "binning");
+  const GroupArgs &G = h->grp_bin.ga[h->cur];
+  const size_t ti = sizeof(int32_t) * (h->geo.ntiles + 2);
+  for (int pass = 0; pass < 2; ++pass) {
+    CK(cudaMemsetAsync(h->s.in_cnt, 0, ti, h->st), "binning");
+    CK(cudaMemsetAsync(h->s.out_cnt, 0, ti, h->st), "binning");
+    CK(cudaMemsetAsync(h->s.ctr + C_MOVERS, 0, sizeof(int32_t), h->st), "binning");
+    CK(count_movers(G, h->st), "binning");
+    if (pass == 0) CK(bin_group(h->d.dim, G, h->st), "binning");
+  }
   if (key) CK(cudaMemcpyAsync(key, h->buf[h->cur].key(), 4 * h->n, cudaMemcpyDeviceToHost, h->st), "binning");
   if (perm) CK(cudaMemcpyAsync(perm, h->perm2, 4 * h->n, cudaMemcpyDeviceToHost, h->st), "binning");
   CK(cudaStreamSynchronize(h->st), "binning");

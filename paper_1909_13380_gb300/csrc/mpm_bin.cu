@@ -428,10 +428,15 @@ __global__ void permute_k(int64_t n, PBuf A, PBuf B, const int32_t *__restrict__
 
 }  // namespace
 
+cudaError_t count_movers(const GroupArgs &G, cudaStream_t st) {
+  if (G.ninst <= 0 || G.nblk_p <= 0) return cudaSuccess;
+  bin_movers<<<G.nblk_p, 256, 0, st>>>(G);
+  return cudaGetLastError();
+}
+
 cudaError_t bin_group(int dim, const GroupArgs &G, cudaStream_t st) {
   (void)dim;
   if (G.ninst <= 0 || G.nblk_p <= 0) return cudaSuccess;
-  bin_movers<<<G.nblk_p, 256, 0, st>>>(G);
   bin_scan_totals<<<G.nblk_s, SCAN_T, 0, st>>>(G);
   bin_scan_apply<<<G.nblk_s, SCAN_T, 0, st>>>(G);
   bin_bucket<<<G.nblk_m, 256, 0, st>>>(G);

@@ -23,7 +23,8 @@
 //   g2p        one thread per particle in binning order: FLIP velocity,
 //              advection, strain, stress, volume and relocation into the new
 //              cell, written in binning order so the next step reads
-//              contiguously.
+//              contiguously; particles that change tile are counted and
+//              listed for the next step's binning.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -595,6 +596,21 @@ __global__ void __launch_bounds__(G2P_T, 3) g2p(GroupArgs G) {
     I.B.mass()[q] = mass;
     I.B.id()[q] = pid;
     if (has_coh) I.B.coh()[q] = coh;
+    // tile movers for the next step's binning; one append per warp
+    const int tn = min((int)(nkey >> LOCAL_BITS), I.ntiles);
+    const bool mover = tn != t;
+    const unsigned am = __activemask();
+    const unsigned mv = __ballot_sync(am, mover);
+    if (mover) {
+      const int lane = threadIdx.x & 31;
+      const int leader = __ffs(mv) - 1;
+      int base = 0;
+      if (lane == leader) base = atomicAdd(&I.s.ctr[C_MOVERS], __popc(mv));
+      base = __shfl_sync(mv, base, leader);
+      atomicAdd(&I.s.in_cnt[tn], 1);
+      atomicAdd(&I.s.out_cnt[t], 1);
+      I.s.movers[base + __popc(mv & ((1u << lane) - 1u))] = (int32_t)q;
+    }
   }
   if (STR) {
     // strain increment de = sym(L) dt, strain, volume ratio, stress

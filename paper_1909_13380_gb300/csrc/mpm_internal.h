@@ -80,7 +80,7 @@ struct Geo {
 // Counters of a step (int32, in StepBufs::ctr).
 enum {
   C_ACTIVE = 0,     // active (non-empty) tiles this step
-  C_MOVERS = 1,     // particles that changed tile (appended by bin_movers)
+  C_MOVERS = 1,     // particles that changed tile (appended by G2P, or bin_movers)
   C_MOVERS_SNAP = 2,
   C_WORK_BIN = 3,   // dynamic tile counters of the per-tile kernels
   C_WORK_P2G = 4,
@@ -179,7 +179,13 @@ inline cudaError_t phase_mark(cudaEvent_t *ev, int i, cudaStream_t st) {
 }
 
 // --- incremental binning (mpm_bin.cu) ----------------------------------------
+// The binning of a step starts from the tile movers (particles whose key left
+// their tile), counted per tile and listed by the previous step's G2P; it
+// consumes (zeroes) those counts.  count_movers recounts them from the keys
+// (A's keys against the previous binning's keys), for callers that have just
+// zeroed the counters (a binning into scratch buffers).
 cudaError_t bin_group(int dim, const GroupArgs &G, cudaStream_t st);
+cudaError_t count_movers(const GroupArgs &G, cudaStream_t st);
 // Gather every field of A into B in the order perm (B[q] = A[perm[q]]).
 cudaError_t permute_state(int dim, int64_t n, const PBuf &A, const PBuf &B, const int32_t *perm,
                           cudaStream_t st);
