@@ -101,13 +101,14 @@ __device__ __forceinline__ void corner_shape(int a, const float w0[D], const flo
 }
 
 // ---------------------------------------------------------------------------
-// P2G: one CTA per tile, one thread per (cell, corner).  The tile's particles
+// P2G: one CTA per tile; each thread owns CPT corners of one cell (3D: two
+// corners, 256 threads; 2D: one corner, 256 threads).  The tile's particles
 // (binning order, so grouped by cell) are staged in shared memory in chunks
 // of one particle per thread: offset u, and the per-particle factors of the
 // channels -- m and m v (mass, momentum), nV sig with nV = -V (internal
 // force f_k = -V sum_j sig_kj dN/dx_j).  Then the thread of (cell c, corner
 // a) runs over the particles of c in binning order and accumulates its
-// corner's channels in registers: each (cell, corner, channel) sum is a plain
+// corners' channels in registers: each (cell, corner, channel) sum is a plain
 // sequential FP32 sum, independent of the launch.  Cell sums go to the node
 // box (compensated, ascending cell order) and the box to the tile's slot.
 // Value index v = corner * NCH + channel; channels USL (m, P_k, f_k), MOM
@@ -119,7 +120,9 @@ struct P2GRec {
   static constexpr int NSV = D == 3 ? 6 : 3;                   // nV sig (xx yy zz xy yz xz | xx yy xy)
   static constexpr int NF = D + (HAS_M ? 1 + D : 0) + (HAS_F ? NSV : 0);
   static constexpr int NQ = (NF + 3) / 4;                      // float4 chunks per particle
-  static constexpr int CH = CELLS_PER_TILE << D;               // threads = particles per chunk
+  static constexpr int CPT = D == 3 ? 2 : 1;                   // corners per thread
+  static constexpr int CPC = (1 << D) / CPT;                   // threads per cell
+  static constexpr int CH = CELLS_PER_TILE * CPC;              // threads = particles per chunk
   static constexpr int NV = (1 << D) * p2g_channels<D, MODE>();
   static constexpr size_t REC_BYTES = sizeof(float4) * NQ * CH;
   static constexpr size_t CELLP_BYTES = sizeof(float) * CELLS_PER_TILE * NV;
@@ -130,6 +133,10 @@ template <int D, int MODE>
 constexpr size_t p2g_smem() {
   return P2GRec<D, MODE>::SMEM;
 }
+template <int D>
+constexpr int p2g_threads() {
+  return P2GRec<D, P2G_USL>::CH;
+}
 
 // Slot of particle i of a chunk: the low three bits are XORed with the next
 // three, so that the cells of a warp, whose current particles are often a
@@ -137,41 +144,52 @@ constexpr size_t p2g_smem() {
 __device__ __forceinline__ int rec_slot(int i) { return (i & ~7) | ((i ^ (i >> 3)) & 7); }
 
 template <int D, int MODE>
-__global__ void __launch_bounds__(CELLS_PER_TILE << D, (D == 3 ? 2 : 4)) p2g_tile(GroupArgs G, int work_slot) {
+__global__ void __launch_bounds__(P2GRec<D, MODE>::CH, 4) p2g_tile(GroupArgs G, int work_slot) {
   using R = P2GRec<D, MODE>;
-  constexpr int NC = 1 << D;
   constexpr int NCH = p2g_channels<D, MODE>();
   constexpr int NV = R::NV;
   constexpr int CH = R::CH;
   constexpr int NQ = R::NQ;
+  constexpr int CPT = R::CPT, CPC = R::CPC;
   constexpr int BN = box_nodes<D>();
   constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ;
   constexpr bool HAS_M = R::HAS_M, HAS_F = R::HAS_F;
   extern __shared__ float4 sm4[];
-  float4 *rec = sm4;                          // [NQ][CH] float4
+  float4 *rec = sm4;                              // [NQ][CH] float4
   float *cellP = reinterpret_cast<float *>(sm4);  // [64][NV], after the chunks
   __shared__ int cs[CELLS_PER_TILE], ce[CELLS_PER_TILE], stamp[CELLS_PER_TILE];
+  __shared__ int s_work[2];
   __shared__ InstArgs sI;
   const int tid = threadIdx.x;
-  const int my_cell = tid / NC, my_corner = tid % NC;
+  const int my_cell = tid / CPC, my_cp = tid % CPC;  // corners my_cp + r * CPC
   if (tid < CELLS_PER_TILE) stamp[tid] = -1;
-  int chunk_id = 0;
+  if (tid == 0) s_work[0] = atomicAdd(&G.work[work_slot], 1);
+  __syncthreads();
+  int chunk_id = 0, loaded = -1;
   const int total = G.act_items[G.ninst];
 
-  for (;;) {
-    const int wi = next_tile(G.work, work_slot);
+  for (int it = 0;; ++it) {
+    const int wi = s_work[it & 1];
     if (wi >= total) break;
+    // the next work item is fetched now and published at the end of this one
+    int wnext = 0;
+    if (tid == 0) wnext = atomicAdd(&G.work[work_slot], 1);
     const int ii = find_inst(G.act_items, G.ninst, wi);
-    copy_inst(G.inst, ii, &sI);
-    __syncthreads();
+    if (ii != loaded) {  // uniform
+      copy_inst(G.inst, ii, &sI);
+      loaded = ii;
+      __syncthreads();
+    }
     const InstArgs &I = sI;
     const Geo &g = I.geo;
     float *slots_out = MODE == P2G_FORCE ? I.s.slots2 : I.s.slots1;
     const int t = I.s.active[wi - G.act_items[ii]];
     const int s = I.new_start[t], e = I.new_start[t + 1];
-    float w0[D], w1[D], acc[NCH];
+    float w0[D], w1[D], acc[CPT][NCH];
 #pragma unroll
-    for (int ch = 0; ch < NCH; ++ch) acc[ch] = 0.f;
+    for (int r = 0; r < CPT; ++r)
+#pragma unroll
+      for (int ch = 0; ch < NCH; ++ch) acc[r][ch] = 0.f;
 
     for (int c0 = s; c0 < e; c0 += CH) {
       // ---- stage this chunk: particle q = c0 + tid
@@ -220,7 +238,7 @@ __global__ void __launch_bounds__(CELLS_PER_TILE << D, (D == 3 ? 2 : 4)) p2g_til
         if (last) ce[lc] = tid + 1;
       }
       __syncthreads();
-      // ---- accumulate my (cell, corner) over the cell's particles in order
+      // ---- accumulate my (cell, corner) pairs over the cell's particles in order
       if (stamp[my_cell] == chunk_id) {
         const int i0 = cs[my_cell], i1 = ce[my_cell];
         for (int i = i0; i < i1; ++i) {
@@ -228,40 +246,43 @@ __global__ void __launch_bounds__(CELLS_PER_TILE << D, (D == 3 ? 2 : 4)) p2g_til
           float f[4 * NQ];
 #pragma unroll
           for (int k = 0; k < NQ; ++k) {
-            const float4 r = rec[k * CH + sl];
-            f[4 * k] = r.x;
-            f[4 * k + 1] = r.y;
-            f[4 * k + 2] = r.z;
-            f[4 * k + 3] = r.w;
+            const float4 rv = rec[k * CH + sl];
+            f[4 * k] = rv.x;
+            f[4 * k + 1] = rv.y;
+            f[4 * k + 2] = rv.z;
+            f[4 * k + 3] = rv.w;
           }
           float u[D];
 #pragma unroll
           for (int k = 0; k < D; ++k) u[k] = f[k];
           corner_weights<D>(u, w0, w1);
-          float N, Gr[D];
-          corner_shape<D>(my_corner, w0, w1, g.inv_h, N, Gr);
-          if (HAS_M) {
-            acc[0] = fmaf(f[D], N, acc[0]);
 #pragma unroll
-            for (int k = 0; k < D; ++k) acc[1 + k] = fmaf(f[D + 1 + k], N, acc[1 + k]);
-          }
-          if (HAS_F) {
-            constexpr int o = HAS_M ? 2 * D + 1 : D;
-            constexpr int a0 = HAS_M ? 1 + D : 0;
-            if (D == 3) {
-              // nV sig: xx yy zz xy yz xz
-              const float t3[3][3] = {{f[o], f[o + 3], f[o + 5]}, {f[o + 3], f[o + 1], f[o + 4]},
-                                      {f[o + 5], f[o + 4], f[o + 2]}};
+          for (int r = 0; r < CPT; ++r) {
+            float N, Gr[D];
+            corner_shape<D>(my_cp + r * CPC, w0, w1, g.inv_h, N, Gr);
+            if (HAS_M) {
+              acc[r][0] = fmaf(f[D], N, acc[r][0]);
 #pragma unroll
-              for (int k = 0; k < D; ++k)
+              for (int k = 0; k < D; ++k) acc[r][1 + k] = fmaf(f[D + 1 + k], N, acc[r][1 + k]);
+            }
+            if (HAS_F) {
+              constexpr int o = HAS_M ? 2 * D + 1 : D;
+              constexpr int a0 = HAS_M ? 1 + D : 0;
+              if (D == 3) {
+                // nV sig: xx yy zz xy yz xz
+                const float t3[3][3] = {{f[o], f[o + 3], f[o + 5]}, {f[o + 3], f[o + 1], f[o + 4]},
+                                        {f[o + 5], f[o + 4], f[o + 2]}};
 #pragma unroll
-                for (int jj = 0; jj < D; ++jj) acc[a0 + k] = fmaf(t3[k][jj], Gr[jj], acc[a0 + k]);
-            } else {
-              const float t2[2][2] = {{f[o], f[o + 2]}, {f[o + 2], f[o + 1]}};
+                for (int k = 0; k < D; ++k)
 #pragma unroll
-              for (int k = 0; k < D; ++k)
+                  for (int jj = 0; jj < D; ++jj) acc[r][a0 + k] = fmaf(t3[k][jj], Gr[jj], acc[r][a0 + k]);
+              } else {
+                const float t2[2][2] = {{f[o], f[o + 2]}, {f[o + 2], f[o + 1]}};
 #pragma unroll
-                for (int jj = 0; jj < D; ++jj) acc[a0 + k] = fmaf(t2[k][jj], Gr[jj], acc[a0 + k]);
+                for (int k = 0; k < D; ++k)
+#pragma unroll
+                  for (int jj = 0; jj < D; ++jj) acc[r][a0 + k] = fmaf(t2[k][jj], Gr[jj], acc[r][a0 + k]);
+              }
             }
           }
         }
@@ -272,7 +293,9 @@ __global__ void __launch_bounds__(CELLS_PER_TILE << D, (D == 3 ? 2 : 4)) p2g_til
 
     // ---- cells -> node box (ascending local cell order), compensated; -> slot
 #pragma unroll
-    for (int ch = 0; ch < NCH; ++ch) cellP[my_cell * NV + my_corner * NCH + ch] = acc[ch];
+    for (int r = 0; r < CPT; ++r)
+#pragma unroll
+      for (int ch = 0; ch < NCH; ++ch) cellP[my_cell * NV + (my_cp + r * CPC) * NCH + ch] = acc[r][ch];
     __syncthreads();
     for (int b = tid; b < BN; b += CH) {
       const int bx = b % (TX + 1);
@@ -297,6 +320,7 @@ __global__ void __launch_bounds__(CELLS_PER_TILE << D, (D == 3 ? 2 : 4)) p2g_til
 #pragma unroll
       for (int ch = 0; ch < NCH; ++ch) slots_out[((int64_t)t * NCH + ch) * BN + b] = ta[ch].value();
     }
+    if (tid == 0) s_work[(it + 1) & 1] = wnext;
     __syncthreads();
   }
 }
@@ -641,7 +665,7 @@ __global__ void __launch_bounds__(G2P_T, 3) g2p(GroupArgs G) {
 
 template <int D, int MODE>
 cudaError_t launch_p2g(const GroupArgs &G, int work_slot, cudaStream_t st) {
-  p2g_tile<D, MODE><<<G.grid, CELLS_PER_TILE << D, p2g_smem<D, MODE>(), st>>>(G, work_slot);
+  p2g_tile<D, MODE><<<G.grid, p2g_threads<D>(), p2g_smem<D, MODE>(), st>>>(G, work_slot);
   return cudaGetLastError();
 }
 
