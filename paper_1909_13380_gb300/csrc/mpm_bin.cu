@@ -259,14 +259,6 @@ __global__ void group_prefix(GroupArgs G) {
   if (threadIdx.x < W_COUNT) G.work[threadIdx.x] = 0;
 }
 
-__device__ __forceinline__ int next_work(int32_t *work, int slot) {
-  __shared__ int s_w;
-  if (threadIdx.x == 0) s_w = atomicAdd(&work[slot], 1);
-  __syncthreads();
-  const int w = s_w;
-  __syncthreads();
-  return w;
-}
 
 __global__ void __launch_bounds__(BT) bin_tiles(GroupArgs G) {
   __shared__ int cnt[CELLS_PER_TILE];
@@ -279,16 +271,25 @@ __global__ void __launch_bounds__(BT) bin_tiles(GroupArgs G) {
   __shared__ InstArgs sI;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t lt_mask = (1u << lane) - 1u;
+  __shared__ int s_work[2];
   for (int k = tid; k < BT_WARPS * (CELLS_PER_TILE + 1); k += BT) (&wcnt[0][0])[k] = 0;
+  if (tid == 0) s_work[0] = atomicAdd(&G.work[W_BIN], 1);
   __syncthreads();
   const int total = G.bin_items[G.ninst];
+  int loaded = -1;
 
-  for (;;) {
-    const int w = next_work(G.work, W_BIN);
+  for (int it = 0;; ++it) {
+    const int w = s_work[it & 1];
     if (w >= total) break;
+    // the next work item is fetched now and published at the end of this one
+    int wnext = 0;
+    if (tid == 0) wnext = atomicAdd(&G.work[W_BIN], 1);
     const int ii = find_inst(G.bin_items, G.ninst, w);
-    copy_inst(G.inst, ii, &sI);
-    __syncthreads();
+    if (ii != loaded) {  // uniform
+      copy_inst(G.inst, ii, &sI);
+      loaded = ii;
+      __syncthreads();
+    }
     const InstArgs &I = sI;
     const int local = w - G.bin_items[ii];
     const int ntiles = I.ntiles;
@@ -399,6 +400,8 @@ __global__ void __launch_bounds__(BT) bin_tiles(GroupArgs G) {
       }
       __syncthreads();
     }
+    if (tid == 0) s_work[(it + 1) & 1] = wnext;
+    __syncthreads();
   }
 }
 

@@ -46,15 +46,6 @@ __device__ __forceinline__ int find_inst(const int32_t *prefix, int ninst, int x
   return lo;
 }
 
-__device__ __forceinline__ int next_tile(int32_t *ctr, int slot) {
-  __shared__ int s_w;
-  if (threadIdx.x == 0) s_w = atomicAdd(&ctr[slot], 1);
-  __syncthreads();
-  const int w = s_w;
-  __syncthreads();
-  return w;
-}
-
 __device__ __forceinline__ void tile_coords(const Geo &g, int t, int tc[3]) {
   tc[0] = t % g.nt[0];
   tc[1] = (t / g.nt[0]) % g.nt[1];
@@ -339,15 +330,14 @@ __device__ __forceinline__ int node_faces(const Geo &g, const int I[3]) {
   return m;
 }
 
-// Sum channels of node I over the slots of every active tile whose box holds
-// it, in ascending tile order (every tile computes a shared node the same way).
-template <int D, int NOUT>
-__device__ __forceinline__ void gather_node(const Geo &g, const int32_t *tile_start, const float *slots, int nch,
-                                            const int I[3], const int tc[3], float out[NOUT]) {
+// Active tiles whose box holds node I, in ascending tile order: bit i of the
+// result is the i-th tile of the (at most 2 x 2 x 2) block lo..hi, *first
+// the lowest active tile index (-1 if none).
+template <int D>
+__device__ __forceinline__ unsigned node_tiles(const Geo &g, const int32_t *tile_start, const int I[3], const int tc[3],
+                                               int lo[3], int hi[3], int &first) {
   constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ;
-  constexpr int BN = box_nodes<D>();
   const int T[3] = {TX, TY, TZ};
-  int lo[3], hi[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     lo[k] = hi[k] = tc[k];
@@ -357,14 +347,38 @@ __device__ __forceinline__ void gather_node(const Geo &g, const int32_t *tile_st
       if (l == T[k] && tc[k] + 1 < g.nt[k]) hi[k] = tc[k] + 1;
     }
   }
+  unsigned act = 0;
+  int idx = 0;
+  first = -1;
+  for (int z = lo[2]; z <= hi[2]; ++z)
+    for (int y = lo[1]; y <= hi[1]; ++y)
+      for (int x = lo[0]; x <= hi[0]; ++x, ++idx) {
+        const int t2 = x + g.nt[0] * (y + g.nt[1] * z);
+        if (tile_start[t2 + 1] > tile_start[t2]) {
+          act |= 1u << idx;
+          if (first < 0) first = t2;
+        }
+      }
+  return act;
+}
+
+// Sum channels of node I over the slots of the active tiles `act` (from
+// node_tiles), in ascending tile order, so that the value does not depend on
+// which tile computes it.
+template <int D, int NOUT>
+__device__ __forceinline__ void gather_node(const Geo &g, const float *slots, int nch, const int I[3], const int lo[3],
+                                            const int hi[3], unsigned act, float out[NOUT]) {
+  constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ;
+  constexpr int BN = box_nodes<D>();
   TwoAcc<float> acc[NOUT];
 #pragma unroll
   for (int c = 0; c < NOUT; ++c) acc[c].init();
+  int idx = 0;
   for (int z = lo[2]; z <= hi[2]; ++z)
     for (int y = lo[1]; y <= hi[1]; ++y)
-      for (int x = lo[0]; x <= hi[0]; ++x) {
+      for (int x = lo[0]; x <= hi[0]; ++x, ++idx) {
+        if (!((act >> idx) & 1u)) continue;
         const int t2 = x + g.nt[0] * (y + g.nt[1] * z);
-        if (tile_start[t2 + 1] <= tile_start[t2]) continue;
         const int bx = I[0] - x * TX, by = I[1] - y * TY, bz = D == 3 ? I[2] - z * TZ : 0;
         const int bl = bx + (TX + 1) * (by + (TY + 1) * bz);
 #pragma unroll
@@ -374,25 +388,45 @@ __device__ __forceinline__ void gather_node(const Geo &g, const int32_t *tile_st
   for (int c = 0; c < NOUT; ++c) out[c] = acc[c].value();
 }
 
+// Work items dealt to the warps of the grid in turn (the work per item is
+// uniform): a 32-node slice of an active tile's box when there are few
+// active tiles, a whole box (four slices in turn) when there are enough to
+// fill the grid.  The nodes whose lowest active holder is the tile -- every
+// node is computed once -- get v = P/m, a = f/m + g, v' = v + a dt and the
+// boundary conditions, written to the dense node records.
 template <int D, int NMODE>
 __global__ void __launch_bounds__(NODE_T) node_tile(GroupArgs G, int work_slot) {
   constexpr int BN = box_nodes<D>();
   constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ;
   constexpr int NCH1 = NMODE == NODE_USL ? 1 + 2 * D : 1 + D;
-  const int total = G.act_items[G.ninst];
-  __shared__ InstArgs sI;
-  for (;;) {
-    const int wi = next_tile(G.work, work_slot);
-    if (wi >= total) break;
-    const int ii = find_inst(G.act_items, G.ninst, wi);
-    copy_inst(G.inst, ii, &sI);
-    __syncthreads();
-    const InstArgs &I = sI;
+  constexpr int NW = NODE_T / 32;
+  constexpr int NSL = (BN + 31) / 32;  // slices per tile
+  __shared__ InstArgs sI[NW];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const InstArgs &I = sI[warp];
+  (void)work_slot;
+  int loaded = -1;
+  const int stride = gridDim.x * NW;
+  const int nact = G.act_items[G.ninst];
+  const int split = nact * NSL <= 2 * stride ? NSL : 1;  // items per tile
+  const int total = nact * split;
+  for (int wi = blockIdx.x * NW + warp; wi < total; wi += stride) {
+    const int item = wi / split, slice0 = wi % split;
+    const int ii = find_inst(G.act_items, G.ninst, item);
+    if (ii != loaded) {  // warp-uniform
+      const unsigned long long *src = reinterpret_cast<const unsigned long long *>(G.inst + ii);
+      unsigned long long *dst = reinterpret_cast<unsigned long long *>(&sI[warp]);
+      for (int i = lane; i < (int)(sizeof(InstArgs) / 8); i += 32) dst[i] = __ldg(src + i);
+      __syncwarp();
+      loaded = ii;
+    }
     const Geo &g = I.geo;
-    const int t = I.s.active[wi - G.act_items[ii]];
+    const int t = I.s.active[item - G.act_items[ii]];
     int tc[3];
     tile_coords(g, t, tc);
-    for (int b = threadIdx.x; b < BN; b += NODE_T) {
+    for (int sl = slice0; sl < (split == 1 ? NSL : slice0 + 1); ++sl) do {  // one node per lane
+      const int b = sl * 32 + lane;
+      if (b >= BN) break;  // break: nothing to write for this lane
       const int bx = b % (TX + 1);
       const int by = (b / (TX + 1)) % (TY + 1);
       const int bz = D == 3 ? b / ((TX + 1) * (TY + 1)) : 0;
@@ -400,15 +434,18 @@ __global__ void __launch_bounds__(NODE_T) node_tile(GroupArgs G, int work_slot) 
       bool inside = true;
 #pragma unroll
       for (int k = 0; k < D; ++k) inside = inside && Ig[k] <= g.nc[k];
-      if (!inside) continue;
+      if (!inside) break;
+      int lo[3], hi[3], first;
+      const unsigned act = node_tiles<D>(g, I.new_start, Ig, tc, lo, hi, first);
+      if (first != t) break;  // a lower active tile computes this node
       float v[D], a[D], vn[D];
 #pragma unroll
       for (int k = 0; k < D; ++k) v[k] = a[k] = vn[k] = 0.f;
       float c1[1 + 2 * D];
       if (NMODE == NODE_USL)
-        gather_node<D, 1 + 2 * D>(g, I.new_start, I.s.slots1, NCH1, Ig, tc, c1);
+        gather_node<D, 1 + 2 * D>(g, I.s.slots1, NCH1, Ig, lo, hi, act, c1);
       else
-        gather_node<D, 1 + D>(g, I.new_start, I.s.slots1, NCH1, Ig, tc, c1);
+        gather_node<D, 1 + D>(g, I.s.slots1, NCH1, Ig, lo, hi, act, c1);
       const float m = c1[0];
       const int faces = node_faces<D>(g, Ig);
       if (m > g.mass_tol) {
@@ -426,7 +463,7 @@ __global__ void __launch_bounds__(NODE_T) node_tile(GroupArgs G, int work_slot) 
           bc_velocity<D, float>(faces, g.bc, v);
         } else {
           float f[D];
-          gather_node<D, D>(g, I.new_start, I.s.slots2, D, Ig, tc, f);
+          gather_node<D, D>(g, I.s.slots2, D, Ig, lo, hi, act, f);
           bc_velocity<D, float>(faces, g.bc, v);
 #pragma unroll
           for (int k = 0; k < D; ++k) {
@@ -444,8 +481,8 @@ __global__ void __launch_bounds__(NODE_T) node_tile(GroupArgs G, int work_slot) 
       } else {
         I.s.node[gi] = make_float4(w[0], w[1], a[0], a[1]);
       }
-    }
-    __syncthreads();
+    } while (0);
+    __syncwarp();  // the instance copy may be replaced next
   }
 }
 
