@@ -53,7 +53,12 @@ from paper_1909_13380_gb300 import workloads as W  # noqa: E402
 METRIC = "particle-steps/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_column3d_512k.txt")
+# ncu DRAM traffic summaries by workload: (file, particles it was taken on)
+TRAFFIC_FILES = {
+    "column3d": (os.path.join(ROOT, "profiles", "dram_traffic_column3d_512k.txt"), 512000),
+    "slope_1_64": (os.path.join(ROOT, "profiles", "dram_traffic_slope3d_1m.txt"), 1000000),
+    "slope": (os.path.join(ROOT, "profiles", "dram_traffic_slope3d_1m.txt"), 1000000),
+}
 KERNEL_SRC = os.path.join(ROOT, "paper_1909_13380_gb300", "csrc", "mpm_fp32.cu")
 
 
@@ -98,20 +103,31 @@ def kernel_hash() -> str:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def load_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
-    was taken on the current kernel source (else None)."""
+def load_traffic(kernel: str, workload: str, n: int):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary of the
+    workload, if it was taken on the current kernel source (else None).  The
+    64M-particle slope is too large to capture under the profiling size rule:
+    its figure is the 1M-particle slope's scaled by the particle count (the
+    traffic is per particle).  Returns (bytes, source) or (None, None)."""
+    if workload not in TRAFFIC_FILES:
+        return None, None
+    path, n_file = TRAFFIC_FILES[workload]
     try:
         kv = {}
-        for line in open(TRAFFIC_FILE):
+        for line in open(path):
             if ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
                 kv[k.strip()] = v.strip()
         if kv.get("kernel_source_sha256_16") != kernel_hash():
-            return None
-        return float(kv[f"{kernel}_dram_bytes_per_launch"])
+            return None, None
+        b = float(kv[f"{kernel}_dram_bytes_per_launch"])
+        src = os.path.relpath(path, ROOT)
+        if n != n_file:
+            b *= n / n_file
+            src += f" (scaled by {n}/{n_file} particles)"
+        return b, src
     except Exception:
-        return None
+        return None, None
 
 
 class ClockSampler:
@@ -189,7 +205,8 @@ def barrier(world: int):
 
 def cpu_oracle_rate(wl, budget_s: float, max_steps: int):
     """Oracle particle-steps/s on the host: steps of the full workload from its
-    initial state until `budget_s` of CPU time or `max_steps` steps."""
+    initial state until `budget_s` of CPU time or `max_steps` steps.  Returns
+    the rate, the steps, the seconds and the oracle (for the accuracy check)."""
     import oracle
     o = oracle.from_workload(wl)
     t0 = time.perf_counter()
@@ -200,7 +217,46 @@ def cpu_oracle_rate(wl, budget_s: float, max_steps: int):
         if time.perf_counter() - t0 >= budget_s:
             break
     dt = time.perf_counter() - t0
-    return wl.n * k / dt, k, dt
+    return wl.n * k / dt, k, dt, o
+
+
+def _rel_l2(a, b):
+    a = np.asarray(a, np.float64).ravel()
+    b = np.asarray(b, np.float64).ravel()
+    den = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / den) if den > 0 else float(np.linalg.norm(a))
+
+
+def accuracy_vs_oracle(wl, o, k, stream):
+    """Relative L2 errors of the GPU state after the oracle's k steps from the
+    same initial state: displacement, velocity, stress, volume change, and the
+    count of particles whose cell differs."""
+    from paper_1909_13380_gb300 import mpm
+    d = wl.dim
+    s = o.state
+    cells = o.cells()
+    nc = o.mesh.n
+    ref_cell = np.where(cells[:, 0] >= 0, cells[:, 0] + nc[0] * (cells[:, 1] + nc[1] * cells[:, 2]), -1)
+    out = {"reference": "FP64 CPU oracle, same seeded initial state", "steps": k,
+           "note": "state errors (pos, vel, stress, vol) and increments since step 0 (disp, dvol); the "
+                   "GPU's increments are taken from its own step-0 state, which for FP32 holds the inputs "
+                   "rounded (offset to 3e-8 cells, V0 = m/rho from an FP32 mass)"}
+    for name, prec in (("fp32_mixed", W.FP32_MIXED), ("fp64_plain", W.FP64_PLAIN)):
+        with mpm.Simulation(wl, precision=prec, stream=stream) as g:
+            s0, _ = g.read(("pos", "vol"))
+            g.step(k)
+            snap, st = g.read(("pos", "vel", "stress", "vol", "cell"))
+        out[name] = {
+            "pos_rel_l2": _rel_l2(snap["pos"], s.x[:, :d]),
+            "vel_rel_l2": _rel_l2(snap["vel"], s.v[:, :d]),
+            "stress_rel_l2": _rel_l2(snap["stress"], s.sig),
+            "vol_rel_l2": _rel_l2(snap["vol"], s.vol),
+            "disp_rel_l2": _rel_l2(snap["pos"] - s0["pos"], s.x[:, :d] - wl.pos),
+            "dvol_rel_l2": _rel_l2(snap["vol"] - s0["vol"], s.vol - wl.vol),
+            "cells_differing": int((snap["cell"] != ref_cell).sum()),
+            "status": mpm.STATUS_NAMES.get(st, st),
+        }
+    return out
 
 
 def run_reference(args):
@@ -361,7 +417,7 @@ def run_gb300(args):
         {"p2g": ph_mean[1] + ph_mean[4], "g2p": ph_mean[3] + ph_mean[6]}
     dom = max(kernels, key=kernels.get)
     achieved = ab[dom] * wl.n / (kernels[dom] * 1e-3) / 1e9
-    traffic = load_traffic(dom)
+    traffic, traffic_src = load_traffic(dom, args.workload, wl.n)
     step_gbs = ab["step"] * wl.n / (t_dev / args.steps) / 1e9
     mpm.mpm_set_phase_timing(sim.h, False)
     sim.close()
@@ -410,12 +466,13 @@ def run_gb300(args):
         serving = run_serving(args)
 
     # ---- CPU oracle baseline (rank 0, N = 1) ---------------------------------
-    cpu = None
+    cpu = accuracy = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        rate, k, dt = cpu_oracle_rate(wl, budget_s=args.cpu_budget, max_steps=args.steps)
+        rate, k, dt, o = cpu_oracle_rate(wl, budget_s=args.cpu_budget, max_steps=args.steps)
         cpu = {"value": rate, "unit": METRIC, "cores": 1, "kind": "oracle",
                "sample": f"first {k} steps of the full {wl.n}-particle workload from its initial state, "
                          f"FP64 oracle, one thread, {dt:.1f} s"}
+        accuracy = accuracy_vs_oracle(wl, o, k, sptr)
 
     if rank == 0:
         # binning: bin_scan_totals, bin_scan_apply, bin_bucket, group_prefix,
@@ -430,12 +487,14 @@ def run_gb300(args):
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": {"bound": "hbm", "kernel": {"p2g": "p2g_tile", "g2p": "g2p"}[dom], "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                         "traffic_source": traffic_src,
                          "algorithmic_bytes_per_particle": ab[dom], "ms_per_launch": kernels[dom]},
             "step_roofline": {"achieved": step_gbs, "frac": step_gbs / peak, "unit": "GB/s",
                               "algorithmic_bytes_per_particle": ab["step"]},
             "phases_ms": dict(zip(names, [float(x) for x in ph_mean])),
             "clocks": clocks, "gpu_launches": per_step * args.steps,
             "e2e": e2e, "fp64_plain": fp64, "batched": batched, "serving": serving, "cpu_baseline": cpu,
+            "accuracy": accuracy,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -35,6 +35,9 @@ namespace {
 
 constexpr int NODE_T = 128;
 constexpr int G2P_T = 256;
+#ifndef MPM_G2P_MINB
+#define MPM_G2P_MINB 4  // resident G2P CTAs per SM the register budget is sized for
+#endif
 
 // Instance of item x: the largest i with prefix[i] <= x (prefix[0] = 0).
 __device__ __forceinline__ int find_inst(const int32_t *prefix, int ninst, int x) {
@@ -490,7 +493,7 @@ __global__ void __launch_bounds__(NODE_T) node_tile(GroupArgs G, int work_slot) 
 // G2P: one thread per particle in binning order
 // ---------------------------------------------------------------------------
 template <int D, int GMODE>
-__global__ void __launch_bounds__(G2P_T, 3) g2p(GroupArgs G) {
+__global__ void __launch_bounds__(G2P_T, MPM_G2P_MINB) g2p(GroupArgs G) {
   constexpr int NC = 1 << D;
   constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ;
   constexpr int NS = nstress<D>();
