@@ -8,18 +8,19 @@
 // (nodal velocity and frictional conditions).
 //
 // GPU design (replaces the per-node mutex), after the binning of mpm_bin.cu:
-//   p2g_tile   one CTA per 4x4x4 (8x8) cell tile, one thread per (cell,
-//              corner): stages the tile's particles (binning order,
-//              coalesced) in shared memory, each thread sums its corner's
-//              contributions over its cell's particles in order in
+//   p2g_tile   one CTA per 4x4x4 (8x8) cell tile, each thread owning
+//              corners of one cell: stages the tile's particles (binning
+//              order, coalesced) in shared memory, each thread sums its
+//              corners' contributions over its cell's particles in order in
 //              registers, cells are summed into the tile's node box
 //              (compensated sums) and the box is written to the tile's own
 //              slot -- no atomics, bit-reproducible;
-//   node_tile  one CTA per tile: final nodal values of the box, summing the
-//              slots of the (at most 2^D) tiles that share each node in
-//              ascending tile order, then v = P/m, a = f/m + g, v' = v + a dt
-//              and the boundary conditions; written to dense node arrays
-//              (nodes shared by boxes get bit-identical values);
+//   node_tile  one warp per slice of a tile's box: final nodal values,
+//              summing the slots of the (at most 2^D) tiles that share each
+//              node in ascending tile order, then v = P/m, a = f/m + g,
+//              v' = v + a dt and the boundary conditions; each node is
+//              computed once (by its lowest active tile) into dense node
+//              records;
 //   g2p        one thread per particle in binning order: FLIP velocity,
 //              advection, strain, stress, volume and relocation into the new
 //              cell, written in binning order so the next step reads
