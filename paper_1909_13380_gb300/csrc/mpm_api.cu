@@ -15,6 +15,7 @@
 #include <string.h>
 
 #include <string>
+#include <algorithm>
 #include <vector>
 
 #include "../../include/mpm.h"
@@ -258,6 +259,9 @@ cudaError_t build_group(GroupDev &g, const std::vector<mpm_ctx *> &mem, bool rel
     G.nblk_s = sb[n];
     G.nblk_m = mb[n];
     G.grid = 8 * nsm;
+    int max_m = 0;
+    for (int i = 0; i < n; ++i) max_m = std::max(max_m, mem[i]->geo.ntiles + 1);
+    G.scan_one = max_m <= SCAN1_MAX ? 1 : 0;
   }
   return cudaSuccess;
 }

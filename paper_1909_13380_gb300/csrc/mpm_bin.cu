@@ -9,15 +9,17 @@
 // GPU form of the neighbourhood idea.  The particle state is stored in the
 // previous step's binning order and a particle moves at most one cell per
 // step, so the new binning is the old one plus a few movers:
-//   bin_movers       compares each stored particle's new key with the key it
-//                    was binned under last step and lists the particles that
-//                    changed tile (counts per tile in and out);
+//   (G2P of the previous step counts and lists the particles that changed
+//   tile; bin_movers recounts them from the keys when a caller needs it)
 //   bin_scan_totals,
 //   bin_scan_apply   two passes over the tiles: new tile ranges = old ranges
 //                    - leavers + arrivals (exclusive scan over tiles), arrival
 //                    bucket offsets, the active tile list, counter resets;
-//   bin_bucket       groups the arrivals by destination tile;
 //   group_prefix     work prefixes over the instances of the group;
+//   bin_scan_one     (instead of the three above when every instance has at
+//                    most SCAN1_MAX tiles) one CTA per instance scans all of
+//                    its tiles; the last CTA to finish computes the prefixes;
+//   bin_bucket       groups the arrivals by destination tile;
 //   bin_tiles        one CTA per tile: the tile's particles are the stayers
 //                    of its old range plus its arrivals; a stable counting
 //                    sort by local cell, in storage order, writes the
@@ -43,6 +45,7 @@ constexpr int BUCKET_SMEM = 1024;
 constexpr int SCAN_T = 256;
 constexpr int SCAN_ITEMS = 4;
 constexpr int SCAN_CHUNK = SCAN_T * SCAN_ITEMS;  // tiles per scan block
+constexpr int SCAN1_T = 1024;                    // one-CTA scan
 
 // Instance of item x: the largest i with prefix[i] <= x (prefix[0] = 0).
 __device__ __forceinline__ int find_inst(const int32_t *prefix, int ninst, int x) {
@@ -232,15 +235,15 @@ __global__ void bin_bucket(GroupArgs G) {
 
 // Prefixes of the binning tiles and the active tiles over the instances, and
 // reset of the group's dynamic work counters.
-__global__ void group_prefix(GroupArgs G) {
-  __shared__ int wsum[32];
+__device__ __forceinline__ void group_prefix_body(const GroupArgs &G, int *wsum) {
   int cb = 0, ca = 0;
   for (int c0 = 0; c0 < G.ninst; c0 += blockDim.x) {
     const int j = c0 + threadIdx.x;
     int b = 0, a = 0;
     if (j < G.ninst) {
-      b = G.inst[j].s.ctr[C_BIN_ITEMS];
-      a = G.inst[j].s.ctr[C_ACTIVE];
+      const int32_t *ctr = G.inst[j].s.ctr;
+      b = __ldcg(ctr + C_BIN_ITEMS);
+      a = __ldcg(ctr + C_ACTIVE);
     }
     int tb, ta;
     const int pb = cta_excl(b, wsum, tb) + cb;
@@ -257,6 +260,81 @@ __global__ void group_prefix(GroupArgs G) {
     G.act_items[G.ninst] = ca;
   }
   if (threadIdx.x < W_COUNT) G.work[threadIdx.x] = 0;
+}
+
+__global__ void group_prefix(GroupArgs G) {
+  __shared__ int wsum[32];
+  group_prefix_body(G, wsum);
+}
+
+// One CTA per instance (instances of at most SCAN1_MAX tiles): the whole scan
+// over the instance's tiles in chunks with running offsets -- new ranges,
+// arrival offsets, the active list, counter resets -- and the CTA that
+// finishes last (counted on a work counter, no waiting) computes the group's
+// prefixes.  Replaces bin_scan_totals + bin_scan_apply + group_prefix.
+__global__ void __launch_bounds__(SCAN1_T) bin_scan_one(GroupArgs G) {
+  __shared__ int wsum[32];
+  __shared__ int s_last;
+  __shared__ InstArgs sI;
+  copy_inst(G.inst, blockIdx.x, &sI);
+  __syncthreads();
+  const InstArgs &I = sI;
+  const int m = I.ntiles + 1;
+  int on = 0, ob = 0, oa = 0;
+  for (int c0 = 0; c0 < m; c0 += SCAN1_T * SCAN_ITEMS) {
+    const int e0 = c0 + threadIdx.x * SCAN_ITEMS;
+    int cn[SCAN_ITEMS], cb[SCAN_ITEMS], ca[SCAN_ITEMS];
+    int sn = 0, sb = 0, sa = 0;
+#pragma unroll
+    for (int r = 0; r < SCAN_ITEMS; ++r) {
+      const int e = e0 + r;
+      cn[r] = cb[r] = ca[r] = 0;
+      if (e < m) tile_counts(I, e, cn[r], cb[r], ca[r]);
+      sn += cn[r];
+      sb += cb[r];
+      sa += ca[r];
+    }
+    int tn, tb, ta;
+    int pn = cta_excl(sn, wsum, tn) + on;
+    int pb = cta_excl(sb, wsum, tb) + ob;
+    int pa = cta_excl(sa, wsum, ta) + oa;
+#pragma unroll
+    for (int r = 0; r < SCAN_ITEMS; ++r) {
+      const int e = e0 + r;
+      if (e < m) {
+        I.new_start[e] = pn;
+        I.s.bucket_start[e] = pb;
+        if (ca[r]) I.s.active[pa] = e;
+        I.s.in_cnt[e] = 0;
+        I.s.out_cnt[e] = 0;
+        I.s.bucket_fill[e] = 0;
+      }
+      pn += cn[r];
+      pb += cb[r];
+      pa += ca[r];
+    }
+    on += tn;
+    ob += tb;
+    oa += ta;
+  }
+  __syncthreads();  // new_start of the dead range is written
+  if (threadIdx.x == 0) {
+    I.s.ctr[C_MOVERS_SNAP] = I.s.ctr[C_MOVERS];
+    I.s.ctr[C_MOVERS] = 0;
+    I.new_start[m] = (int32_t)I.n;
+    I.s.bucket_start[m] = ob;
+    const int dead_start = I.new_start[I.ntiles];
+    I.s.ctr[C_ACTIVE] = oa;
+    I.s.ctr[C_DEAD_START] = dead_start;
+    I.s.ctr[C_BIN_ITEMS] = oa + ((int64_t)dead_start < I.n ? 1 : 0);
+    __threadfence();
+    s_last = atomicAdd(&G.work[W_SCAN_DONE], 1) == G.ninst - 1;
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    group_prefix_body(G, wsum);
+  }
 }
 
 
@@ -440,10 +518,14 @@ cudaError_t count_movers(const GroupArgs &G, cudaStream_t st) {
 cudaError_t bin_group(int dim, const GroupArgs &G, cudaStream_t st) {
   (void)dim;
   if (G.ninst <= 0 || G.nblk_p <= 0) return cudaSuccess;
-  bin_scan_totals<<<G.nblk_s, SCAN_T, 0, st>>>(G);
-  bin_scan_apply<<<G.nblk_s, SCAN_T, 0, st>>>(G);
+  if (G.scan_one) {
+    bin_scan_one<<<G.ninst, SCAN1_T, 0, st>>>(G);
+  } else {
+    bin_scan_totals<<<G.nblk_s, SCAN_T, 0, st>>>(G);
+    bin_scan_apply<<<G.nblk_s, SCAN_T, 0, st>>>(G);
+    group_prefix<<<1, 256, 0, st>>>(G);
+  }
   bin_bucket<<<G.nblk_m, 256, 0, st>>>(G);
-  group_prefix<<<1, 256, 0, st>>>(G);
   bin_tiles<<<G.grid, BT, 0, st>>>(G);
   return cudaGetLastError();
 }

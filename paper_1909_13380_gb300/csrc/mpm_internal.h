@@ -156,10 +156,14 @@ __device__ __forceinline__ void copy_inst(const InstArgs *tab, int ii, InstArgs 
   for (int i = threadIdx.x; i < (int)(sizeof(InstArgs) / 8); i += blockDim.x) d[i] = __ldg(src + i);
 }
 
+// Largest tile count (plus the dead range) scanned by one CTA per instance;
+// larger instances take the two-pass scan over many CTAs.
+constexpr int SCAN1_MAX = 4096;
+
 // Per-group launch description.  The prefix arrays map a block (or a work
 // item) to its instance: entry i is the first block (item) of instance i and
 // entry ninst the total.
-enum { W_BIN = 0, W_P2G = 1, W_NODE = 2, W_P2G2 = 3, W_NODE2 = 4, W_COUNT = 8 };
+enum { W_BIN = 0, W_P2G = 1, W_NODE = 2, W_P2G2 = 3, W_NODE2 = 4, W_SCAN_DONE = 5, W_COUNT = 8 };
 struct GroupArgs {
   const InstArgs *inst;     // device table
   int ninst;
@@ -170,6 +174,7 @@ struct GroupArgs {
   int32_t *act_items;       // device-computed prefix of active tiles
   int32_t *work;            // W_COUNT dynamic work counters
   int nblk_p, nblk_s, nblk_m;
+  int scan_one;             // every instance has at most SCAN1_MAX tiles: one-CTA scans
   int grid;                 // CTAs of the per-tile kernels
 };
 
