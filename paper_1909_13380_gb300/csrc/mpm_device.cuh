@@ -431,6 +431,22 @@ __device__ __forceinline__ bool clearly_elastic(const MatConst<float> &m, float 
   return f < -margin;
 }
 
+// Elastic for certain, without trigonometry?  With the principal deviatoric
+// stresses 2 r cos(theta + 2 pi k / 3), r = sqrt(J2 / 3), the yield function
+// is f = 2 r (sqrt(3) sin(psi) + sin(phi) cos(psi)) + 2 p sin(phi)
+// - 2 c cos(phi) with psi = theta + pi / 3, and over every Lode angle
+// sqrt(3) sin(psi) + sin(phi) cos(psi) <= sqrt(3 + sin^2(phi)).  A trial
+// whose bound stays below zero by more than the FP32 rounding of p and J2 is
+// inside the surface whatever its Lode angle.
+__device__ __forceinline__ bool bounded_elastic(const MatConst<float> &m, float c, const float s[6]) {
+  const float p = (s[0] + s[1] + s[2]) * (1.f / 3.f);
+  const float d0 = s[0] - p, d1 = s[1] - p, d2 = s[2] - p;
+  const float j2 = 0.5f * (d0 * d0 + d1 * d1 + d2 * d2) + s[3] * s[3] + s[4] * s[4] + s[5] * s[5];
+  const float r = sqrtf(j2 * (1.f / 3.f));
+  const float fmax = 2.f * r * sqrtf(3.f + m.sphi * m.sphi) + 2.f * p * m.sphi - 2.f * c * m.cphi;
+  return fmax < -1e-4f * (r + fabsf(p) + c);
+}
+
 // Trial stress -> returned stress (Voigt 6) for Mohr-Coulomb in precision T.
 template <typename T>
 __device__ __forceinline__ int mc_return(const MatConst<T> &m, T c, const T st[6], T out[6], T &depsp) {
@@ -493,7 +509,7 @@ __device__ __forceinline__ bool near_apex(const float st[6], const MatConst<floa
 
 // The FP64 return near the apex, kept out of line: it is rare, and inlining
 // it would raise the register count of every kernel that updates stresses.
-static __device__ __noinline__ void mc_return_apex_band(const MatConst<double> &md, float c, float st[6], float out[6],
+static __device__ __noinline__ void mc_return_apex_band(const MatConst<double> &md, float c, const float st[6], float out[6],
                                                  float &epsp) {
   double sd[6], od[6], dd;
 #pragma unroll
@@ -504,18 +520,11 @@ static __device__ __noinline__ void mc_return_apex_band(const MatConst<double> &
   epsp += (float)dd;
 }
 
-// Full material update of one particle: sigma <- return(sigma + D:de).
-// FP32 path: FP32 arithmetic except the Mohr-Coulomb return inside the apex
-// band, which runs in FP64.  FP64 path: everything in FP64.
-__device__ __forceinline__ void material_update(const MatConst<float> &m, const MatConst<double> &md,
-                                                float c, float sig[6], const float de[6], float &epsp) {
-  float st[6];
-  elastic_trial<float>(m, sig, de, st);
-  if (m.model != 1) {
-#pragma unroll
-    for (int i = 0; i < 6; ++i) sig[i] = st[i];
-    return;
-  }
+// The Mohr-Coulomb return of a trial that the trigonometry-free bound could
+// not clear, kept out of line: the common elastic case then does not carry
+// its registers.  Writes sig (returned stress) and adds to epsp.
+static __device__ __noinline__ void mc_update_f32(const MatConst<float> &m, const MatConst<double> &md, float c,
+                                                  const float st[6], float sig[6], float &epsp) {
   if (clearly_elastic(m, c, st)) {
 #pragma unroll
     for (int i = 0; i < 6; ++i) sig[i] = st[i];
@@ -528,6 +537,21 @@ __device__ __forceinline__ void material_update(const MatConst<float> &m, const 
     mc_return<float>(m, c, st, sig, d);
     epsp += d;
   }
+}
+
+// Full material update of one particle: sigma <- return(sigma + D:de).
+// FP32 path: FP32 arithmetic except the Mohr-Coulomb return inside the apex
+// band, which runs in FP64.  FP64 path: everything in FP64.
+__device__ __forceinline__ void material_update(const MatConst<float> &m, const MatConst<double> &md,
+                                                float c, float sig[6], const float de[6], float &epsp) {
+  float st[6];
+  elastic_trial<float>(m, sig, de, st);
+  if (m.model != 1 || bounded_elastic(m, c, st)) {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) sig[i] = st[i];
+    return;
+  }
+  mc_update_f32(m, md, c, st, sig, epsp);
 }
 
 __device__ __forceinline__ void material_update(const MatConst<double> &m, double c, double sig[6],
