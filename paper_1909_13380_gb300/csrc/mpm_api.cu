@@ -318,7 +318,7 @@ void free_t(T *&p) {
 int64_t f32_fixed_bytes(const mpm_mesh_desc &d, int64_t nt, int64_t nn) {
   const int bn = d.dim == 3 ? box_nodes<3>() : box_nodes<2>();
   int64_t b = 4 * nt * bn * (1 + 2 * d.dim) + (d.scheme == MPM_USF ? 4 * nt * bn * d.dim : 0);
-  b += 7 * 4 * (nt + 2) + 16 * nn * (d.dim == 3 ? 2 : 1) + 4096;
+  b += 6 * 4 * (nt + 2) + 16 * (nt + 2) + 16 * nn * (d.dim == 3 ? 2 : 1) + 4096;
   return b;
 }
 
@@ -403,7 +403,7 @@ mpm_status mpm_create_mesh(const mpm_mesh_desc *desc, mpm_handle *out) {
     if (e == cudaSuccess) e = cudaMalloc(&S.out_cnt, ti);
     if (e == cudaSuccess) e = cudaMalloc(&S.bucket_start, ti);
     if (e == cudaSuccess) e = cudaMalloc(&S.bucket_fill, ti);
-    if (e == cudaSuccess) e = cudaMalloc(&S.active, ti);
+    if (e == cudaSuccess) e = cudaMalloc(&S.active, sizeof(int4) * (nt + 2));
     if (e == cudaSuccess) e = cudaMalloc(&S.scan_tot, sizeof(int32_t) * 3 * ((nt + 1) / 1024 + 1));
     if (e == cudaSuccess) e = cudaMalloc(&S.ctr, sizeof(int32_t) * C_NCTR);
     for (int p = 0; p < 2 && e == cudaSuccess; ++p) e = cudaMemset(S.tile_start[p], 0, ti);

@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(SCAN_T) bin_scan_apply(GroupArgs G) {
     if (e < m) {
       I.new_start[e] = pn;
       I.s.bucket_start[e] = pb;
-      if (ca[r]) I.s.active[pa] = e;
+      if (ca[r]) I.s.active[pa] = make_int4(e, pn, pn + cn[r], 0);
       I.s.in_cnt[e] = 0;
       I.s.out_cnt[e] = 0;
       I.s.bucket_fill[e] = 0;
@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(SCAN1_T) bin_scan_one(GroupArgs G) {
       if (e < m) {
         I.new_start[e] = pn;
         I.s.bucket_start[e] = pb;
-        if (ca[r]) I.s.active[pa] = e;
+        if (ca[r]) I.s.active[pa] = make_int4(e, pn, pn + cn[r], 0);
         I.s.in_cnt[e] = 0;
         I.s.out_cnt[e] = 0;
         I.s.bucket_fill[e] = 0;
@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(BT) bin_tiles(GroupArgs G) {
     const InstArgs &I = sI;
     const int local = w - G.bin_items[ii];
     const int ntiles = I.ntiles;
-    const int t = (local < I.s.ctr[C_ACTIVE]) ? I.s.active[local] : ntiles;
+    const int t = (local < I.s.ctr[C_ACTIVE]) ? I.s.active[local].x : ntiles;
     const int os = I.old_start[t], oe = I.old_start[t + 1];
     const int bs = I.s.bucket_start[t], be = I.s.bucket_start[t + 1];
     const int nbk = be - bs;

@@ -178,8 +178,8 @@ __global__ void __launch_bounds__(P2GRec<D, MODE>::CH, 4) p2g_tile(GroupArgs G, 
     const InstArgs &I = sI;
     const Geo &g = I.geo;
     float *slots_out = MODE == P2G_FORCE ? I.s.slots2 : I.s.slots1;
-    const int t = I.s.active[wi - G.act_items[ii]];
-    const int s = I.new_start[t], e = I.new_start[t + 1];
+    const int4 ar = I.s.active[wi - G.act_items[ii]];
+    const int t = ar.x, s = ar.y, e = ar.z;
     float w0[D], w1[D], acc[CPT][NCH];
 #pragma unroll
     for (int r = 0; r < CPT; ++r)
@@ -425,7 +425,7 @@ __global__ void __launch_bounds__(NODE_T) node_tile(GroupArgs G, int work_slot) 
       loaded = ii;
     }
     const Geo &g = I.geo;
-    const int t = I.s.active[item - G.act_items[ii]];
+    const int t = I.s.active[item - G.act_items[ii]].x;
     int tc[3];
     tile_coords(g, t, tc);
     for (int sl = slice0; sl < (split == 1 ? NSL : slice0 + 1); ++sl) do {  // one node per lane

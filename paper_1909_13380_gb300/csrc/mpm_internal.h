@@ -105,7 +105,7 @@ struct StepBufs {
   int32_t *movers;         // n: storage slots of tile movers
   int32_t *bucket;         // n: movers grouped by destination tile
   int32_t *bucket_sorted;  // n: scratch for large buckets
-  int32_t *active;         // ntiles: active tile list
+  int4 *active;            // ntiles: active tiles in ascending order, (tile, new start, new end, -)
   int32_t *scan_tot;       // 3 per block of the tile scan
   int32_t *ctr;            // C_NCTR counters
   float *slots1;           // ntiles * box * channels (P2G USL / MOM)
