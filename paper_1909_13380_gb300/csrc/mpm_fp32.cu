@@ -490,6 +490,15 @@ __global__ void __launch_bounds__(NODE_T) node_tile(GroupArgs G, int work_slot) 
   }
 }
 
+// 4-byte asynchronous global -> shared copies (each thread later reads only
+// what it copied itself, so a wait on its own copies is all it needs).
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 // ---------------------------------------------------------------------------
 // G2P: one thread per particle in binning order
 // ---------------------------------------------------------------------------
@@ -508,6 +517,20 @@ __global__ void __launch_bounds__(G2P_T, MPM_G2P_MINB) g2p(GroupArgs G) {
   if (q >= I.n) return;
   const int j = I.perm_out[q];
   const int dead_start = I.s.ctr[C_DEAD_START];
+  // the stress-stage fields travel to this thread's shared-memory column while
+  // the node gather and the kinematics run, without holding registers
+  constexpr bool KIN = GMODE != G2P_USF_STRESS, STR = GMODE != G2P_USF_ADVECT;
+  __shared__ float stg[2 * NS + 2][G2P_T];
+  if (STR && q < dead_start) {
+#pragma unroll
+    for (int i = 0; i < NS; ++i) {
+      cp_async4(&stg[i][threadIdx.x], I.A.sig(i) + j);
+      cp_async4(&stg[NS + i][threadIdx.x], I.A.eps(i) + j);
+    }
+    cp_async4(&stg[2 * NS][threadIdx.x], I.A.jm1() + j);
+    cp_async4(&stg[2 * NS + 1][threadIdx.x], I.A.epsp() + j);
+    cp_async_commit();
+  }
   if (q >= dead_start) {  // left the mesh earlier: carried over unchanged
     if (GMODE != G2P_USF_STRESS) {
       I.B.key()[q] = I.A.key()[j];
@@ -587,7 +610,6 @@ __global__ void __launch_bounds__(G2P_T, MPM_G2P_MINB) g2p(GroupArgs G) {
   // Every load of the particle's state is issued before the first store: the
   // compiler cannot tell A from B, so a load placed after a store would wait
   // for the value before it (one memory latency per field).
-  constexpr bool KIN = GMODE != G2P_USF_STRESS, STR = GMODE != G2P_USF_ADVECT;
   float v0[D], sg[6], ep[6], jm1 = 0.f, epsp = 0.f, mass = 0.f, coh = I.mat.c;
   int32_t pid = 0;
   const bool has_coh = I.A.coh() != nullptr;
@@ -599,15 +621,16 @@ __global__ void __launch_bounds__(G2P_T, MPM_G2P_MINB) g2p(GroupArgs G) {
   }
   if (has_coh && (KIN || STR)) coh = I.A.coh()[j];
   if (STR) {
+    cp_async_wait_all();
 #pragma unroll
     for (int i = 0; i < 6; ++i) sg[i] = ep[i] = 0.f;
 #pragma unroll
     for (int i = 0; i < NS; ++i) {
-      sg[i] = I.A.sig(i)[j];
-      ep[i] = I.A.eps(i)[j];
+      sg[i] = stg[i][threadIdx.x];
+      ep[i] = stg[NS + i][threadIdx.x];
     }
-    jm1 = I.A.jm1()[j];
-    epsp = I.A.epsp()[j];
+    jm1 = stg[2 * NS][threadIdx.x];
+    epsp = stg[2 * NS + 1][threadIdx.x];
   }
 
   int status = 0;
