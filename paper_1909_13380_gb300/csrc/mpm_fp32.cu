@@ -517,18 +517,32 @@ __global__ void __launch_bounds__(G2P_T, MPM_G2P_MINB) g2p(GroupArgs G) {
   if (q >= I.n) return;
   const int j = I.perm_out[q];
   const int dead_start = I.s.ctr[C_DEAD_START];
-  // the stress-stage fields travel to this thread's shared-memory column while
-  // the node gather and the kinematics run, without holding registers
+  // the particle's state (all but its offset) travels to this thread's
+  // shared-memory column while the node gather runs, without holding
+  // registers: stress-stage fields (sig, eps, J-1, eps_p), then kinematic
+  // ones (velocity, mass, id), then cohesion
   constexpr bool KIN = GMODE != G2P_USF_STRESS, STR = GMODE != G2P_USF_ADVECT;
-  __shared__ float stg[2 * NS + 2][G2P_T];
-  if (STR && q < dead_start) {
+  constexpr int S_VEL = STR ? 2 * NS + 2 : 0, S_MASS = S_VEL + D, S_ID = S_MASS + 1;
+  constexpr int S_COH = KIN ? S_ID + 1 : S_VEL;
+  __shared__ float stg[S_COH + 1][G2P_T];
+  const bool has_coh = I.A.coh() != nullptr;
+  if (q < dead_start) {
+    if (STR) {
 #pragma unroll
-    for (int i = 0; i < NS; ++i) {
-      cp_async4(&stg[i][threadIdx.x], I.A.sig(i) + j);
-      cp_async4(&stg[NS + i][threadIdx.x], I.A.eps(i) + j);
+      for (int i = 0; i < NS; ++i) {
+        cp_async4(&stg[i][threadIdx.x], I.A.sig(i) + j);
+        cp_async4(&stg[NS + i][threadIdx.x], I.A.eps(i) + j);
+      }
+      cp_async4(&stg[2 * NS][threadIdx.x], I.A.jm1() + j);
+      cp_async4(&stg[2 * NS + 1][threadIdx.x], I.A.epsp() + j);
     }
-    cp_async4(&stg[2 * NS][threadIdx.x], I.A.jm1() + j);
-    cp_async4(&stg[2 * NS + 1][threadIdx.x], I.A.epsp() + j);
+    if (KIN) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) cp_async4(&stg[S_VEL + k][threadIdx.x], I.A.vel(k) + j);
+      cp_async4(&stg[S_MASS][threadIdx.x], I.A.mass() + j);
+      cp_async4(&stg[S_ID][threadIdx.x], I.A.id() + j);
+    }
+    if (has_coh) cp_async4(&stg[S_COH][threadIdx.x], I.A.coh() + j);
     cp_async_commit();
   }
   if (q >= dead_start) {  // left the mesh earlier: carried over unchanged
@@ -612,16 +626,15 @@ __global__ void __launch_bounds__(G2P_T, MPM_G2P_MINB) g2p(GroupArgs G) {
   // for the value before it (one memory latency per field).
   float v0[D], sg[6], ep[6], jm1 = 0.f, epsp = 0.f, mass = 0.f, coh = I.mat.c;
   int32_t pid = 0;
-  const bool has_coh = I.A.coh() != nullptr;
+  cp_async_wait_all();
   if (KIN) {
 #pragma unroll
-    for (int k = 0; k < D; ++k) v0[k] = I.A.vel(k)[j];
-    mass = I.A.mass()[j];
-    pid = I.A.id()[j];
+    for (int k = 0; k < D; ++k) v0[k] = stg[S_VEL + k][threadIdx.x];
+    mass = stg[S_MASS][threadIdx.x];
+    pid = __float_as_int(stg[S_ID][threadIdx.x]);
   }
-  if (has_coh && (KIN || STR)) coh = I.A.coh()[j];
+  if (has_coh) coh = stg[S_COH][threadIdx.x];
   if (STR) {
-    cp_async_wait_all();
 #pragma unroll
     for (int i = 0; i < 6; ++i) sg[i] = ep[i] = 0.f;
 #pragma unroll
