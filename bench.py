@@ -17,7 +17,8 @@ only: the path has no cross-instance exchange), so value = N x per-rank work
 / max time ("weak" scaling).
 
 Beside the headline the line carries: the plain FP64 GPU step on the same
-workload ("fp64_plain"); an end-to-end run through the C-ABI from host
+workload ("fp64_plain"); the same workload with the other update order, USF
+("other_scheme"); an end-to-end run through the C-ABI from host
 buffers ("e2e"); 256 independent 2D granular columns (5k-60k particles each)
 advanced by batched steps, against stepping them one at a time ("batched");
 a serving session ("serving"): a Poisson stream (20/s) of mixed 2D/3D column
@@ -96,6 +97,17 @@ def load_peak():
             return float(json.load(f)["hbm_gbs"]), "measured"
     except Exception:
         return FALLBACK_HBM_GBS, "fallback"
+
+
+def binning_launches(wl) -> int:
+    """Kernels of one binning: the one-CTA scan path (scan, bucket, tiles)
+    for meshes of at most 4096 tiles, else the two-pass scan path (totals,
+    apply, group prefix, bucket, tiles)."""
+    td = (4, 4, 4) if wl.dim == 3 else (8, 8, 1)
+    nt = 1
+    for k in range(3):
+        nt *= -(-int(wl.ncells[k]) // td[k])
+    return 3 if nt + 1 <= 4096 else 5
 
 
 def kernel_hash() -> str:
@@ -337,7 +349,7 @@ def run_batched(args, flush, stream):
             "one_at_a_time": {"value": ntot / (ms_seq * 1e-3), "ms_per_step_of_all": ms_seq},
             "batching_speedup": ms_seq / ms_step,
             "failed": int(sum(1 for x in status if x != mpm.MPM_OK)),
-            "gpu_launches_per_batched_step": 8}
+            "gpu_launches_per_batched_step": max(binning_launches(w) for w in wls) + 3}
 
 
 def run_serving(args):
@@ -441,6 +453,28 @@ def run_gb300(args):
         fp64 = {"value": wl.n / (ms64 * 1e-3), "unit": METRIC, "ms_per_step": ms64, "steps": k64,
                 "fp32_mixed_speedup": (wl.n * args.steps / t_dev) / (wl.n / (ms64 * 1e-3))}
 
+    # ---- the other update order (USF when the headline is USL) --------------
+    other = None
+    if not args.no_usf:
+        osch = W.USF if wl.scheme == W.USL else W.USL
+        ko = max(1, min(args.steps, 20))
+        so = mpm.Simulation(wl, scheme=osch, stream=sptr)
+        with torch.cuda.stream(stream):
+            so.step(args.warmup)
+            eo = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(ko)]
+            for i in range(ko):
+                eo[i][0].record(stream)
+                so.step(1)
+                eo[i][1].record(stream)
+                flush.zero_()
+        stream.synchronize()
+        mso = sum(a.elapsed_time(b) for a, b in eo) / ko
+        sto = so.sync()
+        so.close()
+        other = {"scheme": "USF" if osch == W.USF else "USL", "value": wl.n / (mso * 1e-3), "unit": METRIC,
+                 "ms_per_step": mso, "steps": ko, "status": mpm.STATUS_NAMES.get(sto, sto),
+                 "gpu_launches_per_step": binning_launches(wl) + (6 if osch == W.USF else 3)}
+
     # ---- end to end through the C-ABI with host buffers ---------------------
     e2e = None
     if not args.no_e2e:
@@ -475,9 +509,9 @@ def run_gb300(args):
         accuracy = accuracy_vs_oracle(wl, o, k, sptr)
 
     if rank == 0:
-        # binning: bin_scan_totals, bin_scan_apply, bin_bucket, group_prefix,
-        # bin_tiles; then p2g_tile, node_tile, g2p (USF: twice each)
-        per_step = 5 + (3 if wl.scheme == W.USL else 6)
+        # binning (three or five kernels); then p2g_tile, node_tile, g2p
+        # (USF: twice each)
+        per_step = binning_launches(wl) + (3 if wl.scheme == W.USL else 6)
         line = {
             "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
@@ -493,7 +527,8 @@ def run_gb300(args):
                               "algorithmic_bytes_per_particle": ab["step"]},
             "phases_ms": dict(zip(names, [float(x) for x in ph_mean])),
             "clocks": clocks, "gpu_launches": per_step * args.steps,
-            "e2e": e2e, "fp64_plain": fp64, "batched": batched, "serving": serving, "cpu_baseline": cpu,
+            "e2e": e2e, "fp64_plain": fp64, "other_scheme": other, "batched": batched, "serving": serving,
+            "cpu_baseline": cpu,
             "accuracy": accuracy,
         }
         print(json.dumps(line), flush=True)
@@ -513,6 +548,7 @@ def main(argv=None):
                     choices=["column3d", "column3d_small", "bar", "slope", "slope_1_64"])
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-usf", action="store_true", help="skip the other update order (USF)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-batch", action="store_true", help="skip the 256 batched 2D columns")
