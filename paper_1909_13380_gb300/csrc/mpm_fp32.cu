@@ -335,11 +335,13 @@ __device__ __forceinline__ int node_faces(const Geo &g, const int I[3]) {
 }
 
 // Active tiles whose box holds node I, in ascending tile order: bit i of the
-// result is the i-th tile of the (at most 2 x 2 x 2) block lo..hi, *first
-// the lowest active tile index (-1 if none).
+// result is the i-th tile of the (at most 2 x 2 x 2) block lo..hi, `first`
+// the lowest active tile index (-1 if none).  Activity comes from the
+// 3 x 3 x 3 neighbourhood mask of tile tc (bit (dz + 1) 9 + (dy + 1) 3 +
+// (dx + 1) set when that neighbour has particles).
 template <int D>
-__device__ __forceinline__ unsigned node_tiles(const Geo &g, const int32_t *tile_start, const int I[3], const int tc[3],
-                                               int lo[3], int hi[3], int &first) {
+__device__ __forceinline__ unsigned node_tiles_mask(const Geo &g, unsigned nmask, const int I[3], const int tc[3],
+                                                    int lo[3], int hi[3], int &first) {
   constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ;
   const int T[3] = {TX, TY, TZ};
 #pragma unroll
@@ -357,17 +359,17 @@ __device__ __forceinline__ unsigned node_tiles(const Geo &g, const int32_t *tile
   for (int z = lo[2]; z <= hi[2]; ++z)
     for (int y = lo[1]; y <= hi[1]; ++y)
       for (int x = lo[0]; x <= hi[0]; ++x, ++idx) {
-        const int t2 = x + g.nt[0] * (y + g.nt[1] * z);
-        if (tile_start[t2 + 1] > tile_start[t2]) {
+        const int nb = (z - tc[2] + 1) * 9 + (y - tc[1] + 1) * 3 + (x - tc[0] + 1);
+        if ((nmask >> nb) & 1u) {
           act |= 1u << idx;
-          if (first < 0) first = t2;
+          if (first < 0) first = x + g.nt[0] * (y + g.nt[1] * z);
         }
       }
   return act;
 }
 
 // Sum channels of node I over the slots of the active tiles `act` (from
-// node_tiles), in ascending tile order, so that the value does not depend on
+// node_tiles_mask), in ascending tile order, so that the value does not depend on
 // which tile computes it.
 template <int D, int NOUT>
 __device__ __forceinline__ void gather_node(const Geo &g, const float *slots, int nch, const int I[3], const int lo[3],
@@ -428,6 +430,20 @@ __global__ void __launch_bounds__(NODE_T) node_tile(GroupArgs G, int work_slot) 
     const int t = I.s.active[item - G.act_items[ii]].x;
     int tc[3];
     tile_coords(g, t, tc);
+    // activity of the 27 tiles around t, one lane each
+    bool nact = false;
+    if (lane < 27) {
+      const int d[3] = {lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1};
+      const int n3[3] = {tc[0] + d[0], tc[1] + d[1], tc[2] + d[2]};
+      bool in = D == 3 || d[2] == 0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) in = in && n3[k] >= 0 && n3[k] < g.nt[k];
+      if (in) {
+        const int t2 = n3[0] + g.nt[0] * (n3[1] + g.nt[1] * n3[2]);
+        nact = I.new_start[t2 + 1] > I.new_start[t2];
+      }
+    }
+    const unsigned nmask = __ballot_sync(0xffffffffu, nact);
     for (int sl = slice0; sl < (split == 1 ? NSL : slice0 + 1); ++sl) do {  // one node per lane
       const int b = sl * 32 + lane;
       if (b >= BN) break;  // break: nothing to write for this lane
@@ -440,7 +456,7 @@ __global__ void __launch_bounds__(NODE_T) node_tile(GroupArgs G, int work_slot) 
       for (int k = 0; k < D; ++k) inside = inside && Ig[k] <= g.nc[k];
       if (!inside) break;
       int lo[3], hi[3], first;
-      const unsigned act = node_tiles<D>(g, I.new_start, Ig, tc, lo, hi, first);
+      const unsigned act = node_tiles_mask<D>(g, nmask, Ig, tc, lo, hi, first);
       if (first != t) break;  // a lower active tile computes this node
       float v[D], a[D], vn[D];
 #pragma unroll
