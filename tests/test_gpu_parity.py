@@ -129,8 +129,11 @@ def test_full_column_per_step_parity():
     assert H.cell_mismatch_in_band(g61, r61, wl.h, 1e-4)[1] == 0
 
 
-def test_binning_is_the_stable_sort_of_the_keys():
-    wl = H.small_column()
+@pytest.mark.parametrize("mesh", ["small", "wide"])
+def test_binning_is_the_stable_sort_of_the_keys(mesh):
+    # small: 240 tiles (the one-CTA tile scan); wide: 4320 tiles (the
+    # two-pass scan over many CTAs)
+    wl = H.small_column() if mesh == "small" else W.column3d(ncells=(120, 48, 48), col_cells=(12, 12, 12))
     with mpm.Simulation(wl) as sim:
         sim.step(37)
         key, perm, td = sim.binning()
