@@ -158,7 +158,7 @@ mpm_status mpm_conservation(mpm_handle h, double out[7]);
  * each stored particle (tile-major cell id, see below; dead particles carry
  * the largest key) and perm[n] the stable sort permutation (perm[q] is the
  * storage slot of the q-th particle in key order; ties keep storage order).
- * Tile-major key: tiles of TX x TY x TZ cells (16 x 16 in 2D, 8 x 8 x 4 in
+ * Tile-major key: tiles of TX x TY x TZ cells (8 x 8 in 2D, 4 x 4 x 4 in
  * 3D), tile t = tx + NTX*(ty + NTY*tz), local l = lx + TX*(ly + TY*lz),
  * key = t * (TX*TY*TZ) + l; dead key = NT * (TX*TY*TZ).  tile_dims receives
  * (TX, TY, TZ) if not NULL. */
@@ -170,9 +170,9 @@ mpm_status mpm_read_binning(mpm_handle h, int32_t *key, int32_t *perm, int32_t *
  * also fire inside the captured step graph) at its phase boundaries.
  * mpm_phase_times synchronises and writes the durations in milliseconds of
  * the most recent step's phases to ms[0..*nphase-1]:
- *   USL: binning sort, tile bounds, P2G, G2P (+ carry of dead particles)
- *   USF: binning sort, tile bounds, P2G mass/momentum, G2P stress,
- *        P2G internal force, G2P advection (+ carry of dead particles)
+ *   USL (4): binning, P2G, nodal solve, G2P (+ carry of dead particles)
+ *   USF (7): binning, P2G mass/momentum, nodal velocity, G2P stress,
+ *            P2G internal force, nodal solve, G2P advection
  * ms must hold MPM_MAX_PHASES floats.  MPM_ERR_STATE on FP64_PLAIN handles
  * or when timing is off or no step ran since it was enabled. */
 #define MPM_MAX_PHASES 8
