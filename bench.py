@@ -32,6 +32,7 @@ host cores on the same workload and metric.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import ctypes as C
 import hashlib
 import json
@@ -352,25 +353,45 @@ def run_batched(args, flush, stream):
             "gpu_launches_per_batched_step": max(binning_launches(w) for w in wls) + 3}
 
 
-def run_serving(args):
-    """Poisson stream of mixed 2D/3D column and slope requests served with
-    continuous batching (FP32 mixed) and one at a time in plain FP64."""
+def serve_session(reqs, wls, chunk):
+    """One session of `reqs` with continuous batching (FP32 mixed) and one at
+    a time in plain FP64."""
     from paper_1909_13380_gb300 import serve
-    reqs = W.serving_requests(count=args.serve_requests, step_scale=args.serve_step_scale)
-    wls32 = [r.workload() for r in reqs]
-    out = {"requests": len(reqs), "arrival_rate_per_s": 20.0,
-           "sample": f"{len(reqs)} requests, 1e4-4e6 particles (log-uniform), 1000-20000 steps (log-uniform) "
-                     f"x {args.serve_step_scale:g}, kinds {'/'.join(W.REQUEST_KINDS)}"}
+    out = {}
     for name, kw in (("fp32_continuous_batching", dict(batched=True)),
                      ("fp64_one_at_a_time", dict(precision=W.FP64_PLAIN, batched=False))):
         eng = serve.GpuEngine(**kw)
         try:
-            done, lat, total = serve.Server(eng, chunk=args.serve_chunk).run(reqs, wls32)
+            done, lat, total = serve.Server(eng, chunk=chunk).run(reqs, wls)
         finally:
             eng.shutdown()
         rep = serve.report(done, lat, total)
         rep["h2d_bytes"], rep["d2h_bytes"] = eng.h2d, eng.d2h
         out[name] = rep
+    return out
+
+
+def run_serving(args):
+    """Poisson stream of mixed 2D/3D column and slope requests served with
+    continuous batching (FP32 mixed) and one at a time in plain FP64, at
+    20 requests/s; with --serve-rates, the same requests at other rates too
+    (arrival times scaled)."""
+    reqs = W.serving_requests(count=args.serve_requests, step_scale=args.serve_step_scale)
+    wls32 = [r.workload() for r in reqs]
+    out = {"requests": len(reqs), "arrival_rate_per_s": 20.0,
+           "sample": f"{len(reqs)} requests, 1e4-4e6 particles (log-uniform), 1000-20000 steps (log-uniform) "
+                     f"x {args.serve_step_scale:g}, kinds {'/'.join(W.REQUEST_KINDS)}"}
+    out.update(serve_session(reqs, wls32, args.serve_chunk))
+    rates = [float(x) for x in args.serve_rates.split(",") if x] if args.serve_rates else []
+    if rates:
+        sweep = []
+        for rate in rates:
+            scaled = [dataclasses.replace(r, arrival=r.arrival * 20.0 / rate) for r in reqs]
+            res = serve_session(scaled, wls32, args.serve_chunk)
+            sweep.append({"arrival_rate_per_s": rate, **{
+                k: {m: res[k][m] for m in ("session_s", "utilisation", "step_ms", "e2e_s", "queue_s")}
+                for k in res}})
+        out["rate_sweep"] = sweep
     return out
 
 
@@ -557,6 +578,7 @@ def main(argv=None):
     ap.add_argument("--serve-requests", type=int, default=32)
     ap.add_argument("--serve-step-scale", type=float, default=1.0 / 50)
     ap.add_argument("--serve-chunk", type=int, default=16)
+    ap.add_argument("--serve-rates", default="", help="also serve the requests at these arrival rates, e.g. 2,5,10,20")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3

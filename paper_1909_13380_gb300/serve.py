@@ -250,8 +250,10 @@ def percentiles(values, weights=None):
 
 
 def report(done, lat, session_s):
-    """Summary of a session: throughput and p50 / p99 latencies."""
+    """Summary of a session: throughput, p50 / p99 latencies, and the
+    utilisation (device time of the steps over the session time)."""
     ps = sum(f.n * f.steps for f in done)
+    busy = sum(ms * k for ms, k in lat) * 1e-3
     return {
         "requests": len(done),
         "failed": sum(1 for f in done if f.status != 0),
@@ -261,4 +263,6 @@ def report(done, lat, session_s):
         "step_ms": percentiles([x for x, _ in lat], [k for _, k in lat]),
         "e2e_s": percentiles([f.e2e for f in done]),
         "queue_s": percentiles([f.admitted - f.arrival for f in done]),
+        "gpu_busy_s": busy,
+        "utilisation": busy / session_s if session_s > 0 else None,
     }

@@ -148,3 +148,11 @@ def test_request_larger_than_the_device_is_rejected():
     assert len(big) > 0
     assert all(f.status == 0 for f in done if f.rid not in big)
     assert sorted(f.rid for f in done) == list(range(len(reqs)))
+
+
+def test_utilisation_is_device_time_over_session():
+    reqs, wls, eng, done, lat, total = session(True)
+    rep = serve.report(done, lat, total)
+    busy = sum(ms * k for ms, k in lat) * 1e-3
+    assert rep["gpu_busy_s"] == busy
+    assert 0.0 < rep["utilisation"] <= 1.0 + 1e-12
