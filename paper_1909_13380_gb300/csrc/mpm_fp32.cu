@@ -36,6 +36,9 @@ namespace {
 
 constexpr int NODE_T = 128;
 constexpr int G2P_T = 256;
+#ifndef MPM_P2G_MINB
+#define MPM_P2G_MINB 4  // resident P2G CTAs per SM the register budget is sized for
+#endif
 #ifndef MPM_G2P_MINB
 #define MPM_G2P_MINB 4  // resident G2P CTAs per SM the register budget is sized for
 #endif
@@ -139,7 +142,7 @@ constexpr int p2g_threads() {
 __device__ __forceinline__ int rec_slot(int i) { return (i & ~7) | ((i ^ (i >> 3)) & 7); }
 
 template <int D, int MODE>
-__global__ void __launch_bounds__(P2GRec<D, MODE>::CH, 4) p2g_tile(GroupArgs G, int work_slot) {
+__global__ void __launch_bounds__(P2GRec<D, MODE>::CH, MPM_P2G_MINB) p2g_tile(GroupArgs G, int work_slot) {
   using R = P2GRec<D, MODE>;
   constexpr int NCH = p2g_channels<D, MODE>();
   constexpr int NV = R::NV;
