@@ -101,14 +101,9 @@ def load_peak():
 
 
 def binning_launches(wl) -> int:
-    """Kernels of one binning: the one-CTA scan path (scan, bucket, tiles)
-    for meshes of at most 4096 tiles, else the two-pass scan path (totals,
-    apply, group prefix, bucket, tiles)."""
-    td = (4, 4, 4) if wl.dim == 3 else (8, 8, 1)
-    nt = 1
-    for k in range(3):
-        nt *= -(-int(wl.ncells[k]) // td[k])
-    return 3 if nt + 1 <= 4096 else 5
+    """Kernels of one binning: a tile scan (one CTA per mesh, or one pass with
+    look-back), the arrival bucketing and the per-tile counting sort."""
+    return 3
 
 
 def kernel_hash() -> str:
@@ -530,7 +525,7 @@ def run_gb300(args):
         accuracy = accuracy_vs_oracle(wl, o, k, sptr)
 
     if rank == 0:
-        # binning (three or five kernels); then p2g_tile, node_tile, g2p
+        # binning (three kernels); then p2g_tile, node_tile, g2p
         # (USF: twice each)
         per_step = binning_launches(wl) + (3 if wl.scheme == W.USL else 6)
         line = {

@@ -404,7 +404,9 @@ mpm_status mpm_create_mesh(const mpm_mesh_desc *desc, mpm_handle *out) {
     if (e == cudaSuccess) e = cudaMalloc(&S.bucket_start, ti);
     if (e == cudaSuccess) e = cudaMalloc(&S.bucket_fill, ti);
     if (e == cudaSuccess) e = cudaMalloc(&S.active, sizeof(int4) * (nt + 2));
-    if (e == cudaSuccess) e = cudaMalloc(&S.scan_tot, sizeof(int32_t) * 3 * ((nt + 1) / 1024 + 1));
+    const size_t stb = sizeof(int32_t) * 8 * ((nt + 1) / 1024 + 2);
+    if (e == cudaSuccess) e = cudaMalloc(&S.scan_tot, stb);
+    if (e == cudaSuccess) e = cudaMemset(S.scan_tot, 0, stb);
     if (e == cudaSuccess) e = cudaMalloc(&S.ctr, sizeof(int32_t) * C_NCTR);
     for (int p = 0; p < 2 && e == cudaSuccess; ++p) e = cudaMemset(S.tile_start[p], 0, ti);
     if (e == cudaSuccess) e = cudaMemset(S.in_cnt, 0, ti);

@@ -11,14 +11,13 @@
 // step, so the new binning is the old one plus a few movers:
 //   (G2P of the previous step counts and lists the particles that changed
 //   tile; bin_movers recounts them from the keys when a caller needs it)
-//   bin_scan_totals,
-//   bin_scan_apply   two passes over the tiles: new tile ranges = old ranges
-//                    - leavers + arrivals (exclusive scan over tiles), arrival
-//                    bucket offsets, the active tile list, counter resets;
-//   group_prefix     work prefixes over the instances of the group;
-//   bin_scan_one     (instead of the three above when every instance has at
-//                    most SCAN1_MAX tiles) one CTA per instance scans all of
-//                    its tiles; the last CTA to finish computes the prefixes;
+//   bin_scan_lb      one pass over the tiles (decoupled look-back): new tile
+//                    ranges = old ranges - leavers + arrivals (exclusive scan
+//                    over tiles), arrival bucket offsets, the active tile
+//                    list, counter resets; the last block to finish computes
+//                    the work prefixes over the instances of the group;
+//   bin_scan_one     (instead, when every instance has at most SCAN1_MAX
+//                    tiles) one CTA per instance scans all of its tiles;
 //   bin_bucket       groups the arrivals by destination tile;
 //   bin_tiles        one CTA per tile: the tile's particles are the stayers
 //                    of its old range plus its arrivals; a stable counting
@@ -111,128 +110,6 @@ __device__ __forceinline__ void tile_counts(const InstArgs &I, int e, int &cn, i
   ca = (e < I.ntiles && cn > 0) ? 1 : 0;
 }
 
-// Scan over tiles, pass 1: chunk totals of (count, arrivals, active).
-__global__ void __launch_bounds__(SCAN_T) bin_scan_totals(GroupArgs G) {
-  __shared__ int wsum[32];
-  const int i = find_inst(G.sblk, G.ninst, blockIdx.x);
-  const InstArgs &I = G.inst[i];
-  const int c = blockIdx.x - G.sblk[i];
-  const int m = I.ntiles + 1;
-  const int e0 = c * SCAN_CHUNK + threadIdx.x * SCAN_ITEMS;
-  int sn = 0, sb = 0, sa = 0;
-#pragma unroll
-  for (int r = 0; r < SCAN_ITEMS; ++r) {
-    const int e = e0 + r;
-    if (e < m) {
-      int cn, cb, ca;
-      tile_counts(I, e, cn, cb, ca);
-      sn += cn;
-      sb += cb;
-      sa += ca;
-    }
-  }
-  int tn, tb, ta;
-  cta_excl(sn, wsum, tn);
-  cta_excl(sb, wsum, tb);
-  cta_excl(sa, wsum, ta);
-  if (threadIdx.x == 0) {
-    I.s.scan_tot[3 * c + 0] = tn;
-    I.s.scan_tot[3 * c + 1] = tb;
-    I.s.scan_tot[3 * c + 2] = ta;
-  }
-}
-
-// Scan over tiles, pass 2: each chunk adds the totals of the chunks before it,
-// scans its own tiles, writes new ranges, arrival offsets and the active list,
-// and clears the per-tile counters for the next step.
-__global__ void __launch_bounds__(SCAN_T) bin_scan_apply(GroupArgs G) {
-  __shared__ int wsum[32];
-  __shared__ InstArgs sI;
-  const int i = find_inst(G.sblk, G.ninst, blockIdx.x);
-  copy_inst(G.inst, i, &sI);
-  __syncthreads();
-  const InstArgs &I = sI;
-  const int c = blockIdx.x - G.sblk[i];
-  const int nchunks = G.sblk[i + 1] - G.sblk[i];
-  const int m = I.ntiles + 1;
-  int on = 0, ob = 0, oa = 0;
-  for (int b = threadIdx.x; b < c; b += SCAN_T) {
-    on += I.s.scan_tot[3 * b];
-    ob += I.s.scan_tot[3 * b + 1];
-    oa += I.s.scan_tot[3 * b + 2];
-  }
-  int t0, t1, t2;
-  cta_excl(on, wsum, t0);
-  cta_excl(ob, wsum, t1);
-  cta_excl(oa, wsum, t2);
-  on = t0;
-  ob = t1;
-  oa = t2;
-  const int e0 = c * SCAN_CHUNK + threadIdx.x * SCAN_ITEMS;
-  int cn[SCAN_ITEMS], cb[SCAN_ITEMS], ca[SCAN_ITEMS];
-  int sn = 0, sb = 0, sa = 0;
-#pragma unroll
-  for (int r = 0; r < SCAN_ITEMS; ++r) {
-    const int e = e0 + r;
-    cn[r] = cb[r] = ca[r] = 0;
-    if (e < m) tile_counts(I, e, cn[r], cb[r], ca[r]);
-    sn += cn[r];
-    sb += cb[r];
-    sa += ca[r];
-  }
-  int tn, tb, ta;
-  int pn = cta_excl(sn, wsum, tn) + on;
-  int pb = cta_excl(sb, wsum, tb) + ob;
-  int pa = cta_excl(sa, wsum, ta) + oa;
-#pragma unroll
-  for (int r = 0; r < SCAN_ITEMS; ++r) {
-    const int e = e0 + r;
-    if (e < m) {
-      I.new_start[e] = pn;
-      I.s.bucket_start[e] = pb;
-      if (ca[r]) I.s.active[pa] = make_int4(e, pn, pn + cn[r], 0);
-      I.s.in_cnt[e] = 0;
-      I.s.out_cnt[e] = 0;
-      I.s.bucket_fill[e] = 0;
-    }
-    pn += cn[r];
-    pb += cb[r];
-    pa += ca[r];
-  }
-  if (threadIdx.x == 0 && c == 0) {
-    I.s.ctr[C_MOVERS_SNAP] = I.s.ctr[C_MOVERS];
-    I.s.ctr[C_MOVERS] = 0;
-  }
-  if (c == nchunks - 1) {
-    __syncthreads();  // new_start of the dead range written by this block
-    if (threadIdx.x == 0) {
-      const int nact = oa + ta;
-      I.new_start[m] = (int32_t)I.n;
-      I.s.bucket_start[m] = ob + tb;
-      const int dead_start = I.new_start[I.ntiles];
-      I.s.ctr[C_ACTIVE] = nact;
-      I.s.ctr[C_DEAD_START] = dead_start;
-      I.s.ctr[C_BIN_ITEMS] = nact + ((int64_t)dead_start < I.n ? 1 : 0);
-    }
-  }
-}
-
-__global__ void bin_bucket(GroupArgs G) {
-  __shared__ InstArgs sI;
-  const int i = find_inst(G.mblk, G.ninst, blockIdx.x);
-  copy_inst(G.inst, i, &sI);
-  __syncthreads();
-  const InstArgs &I = sI;
-  const int lb = blockIdx.x - G.mblk[i];
-  const int nb = G.mblk[i + 1] - G.mblk[i];
-  const int nm = I.s.ctr[C_MOVERS_SNAP];
-  for (int m = lb * blockDim.x + threadIdx.x; m < nm; m += nb * blockDim.x) {
-    const int p = I.s.movers[m];
-    const int tn = min((int)(I.A.key()[p] >> LOCAL_BITS), I.ntiles);
-    I.s.bucket[I.s.bucket_start[tn] + atomicAdd(&I.s.bucket_fill[tn], 1)] = p;
-  }
-}
-
 // Prefixes of the binning tiles and the active tiles over the instances, and
 // reset of the group's dynamic work counters.
 __device__ __forceinline__ void group_prefix_body(const GroupArgs &G, int *wsum) {
@@ -262,9 +139,170 @@ __device__ __forceinline__ void group_prefix_body(const GroupArgs &G, int *wsum)
   if (threadIdx.x < W_COUNT) G.work[threadIdx.x] = 0;
 }
 
-__global__ void group_prefix(GroupArgs G) {
+// Scan over tiles in one pass with decoupled look-back (Merrill & Garland,
+// "Single-pass parallel prefix scan with decoupled look-back", 2016).  Each
+// block takes a ticket in start order, which names its chunk of SCAN_CHUNK
+// tiles; it publishes its chunk's totals of (count, arrivals, active), then
+// one warp reads the chunks before it 32 at a time, adding their published
+// totals up to the nearest one that has published its inclusive prefix.  A block waits only
+// on chunks whose blocks took lower tickets and are therefore already
+// running, so every wait ends; each wait is nonetheless bounded, and gives up
+// with ST_TIMEOUT set.  Then it writes new ranges, arrival offsets, the active
+// list and the counter resets of its tiles, and the block that finishes last
+// computes the group's prefixes and clears the chunk flags for the next step.
+// Per chunk k, scan_tot[8k .. 8k+7] = flag (0 none, 1 totals, 2 inclusive),
+// totals (3), inclusive prefix (3), unused.
+constexpr int LB_SPIN_LIMIT = 1 << 20;
+
+__device__ __forceinline__ int ld_volatile(const int32_t *p) { return *(const volatile int32_t *)p; }
+
+__global__ void __launch_bounds__(SCAN_T) bin_scan_lb(GroupArgs G) {
   __shared__ int wsum[32];
-  group_prefix_body(G, wsum);
+  __shared__ int s_ticket, s_last;
+  __shared__ int s_excl[3];
+  __shared__ InstArgs sI;
+  if (threadIdx.x == 0) s_ticket = atomicAdd(&G.work[W_SCAN_TICKET], 1);
+  __syncthreads();
+  const int tk = s_ticket;
+  const int i = find_inst(G.sblk, G.ninst, tk);
+  copy_inst(G.inst, i, &sI);
+  __syncthreads();
+  const InstArgs &I = sI;
+  const int c = tk - G.sblk[i];
+  const int nchunks = G.sblk[i + 1] - G.sblk[i];
+  const int m = I.ntiles + 1;
+  int32_t *st = I.s.scan_tot;
+  const int e0 = c * SCAN_CHUNK + threadIdx.x * SCAN_ITEMS;
+  int cn[SCAN_ITEMS], cb[SCAN_ITEMS], ca[SCAN_ITEMS];
+  int sn = 0, sb = 0, sa = 0;
+#pragma unroll
+  for (int r = 0; r < SCAN_ITEMS; ++r) {
+    const int e = e0 + r;
+    cn[r] = cb[r] = ca[r] = 0;
+    if (e < m) tile_counts(I, e, cn[r], cb[r], ca[r]);
+    sn += cn[r];
+    sb += cb[r];
+    sa += ca[r];
+  }
+  int tn, tb, ta;
+  int pn = cta_excl(sn, wsum, tn);
+  int pb = cta_excl(sb, wsum, tb);
+  int pa = cta_excl(sa, wsum, ta);
+  if (threadIdx.x < 32) {  // warp 0: publish, look back 32 chunks at a time, publish the prefix
+    const int lane = threadIdx.x;
+    int32_t *me = st + 8 * c;
+    int en = 0, eb = 0, ea = 0;
+    if (c > 0) {
+      if (lane == 0) {
+        me[1] = tn;
+        me[2] = tb;
+        me[3] = ta;
+        __threadfence();
+        atomicExch(me, 1);
+      }
+      for (int hi = c - 1; hi >= 0; hi -= 32) {
+        const int q = hi - lane;  // lane 0 is the nearest predecessor
+        int f = 0;
+        if (q >= 0) {
+          for (int it = 0; it < LB_SPIN_LIMIT && f == 0; ++it) f = ld_volatile(st + 8 * q);
+          if (f == 0) atomicOr(&I.s.ctr[C_STATUS], ST_TIMEOUT);  // gave up: this step is invalid
+        }
+        __threadfence();
+        const unsigned inc = __ballot_sync(0xffffffffu, q >= 0 && f == 2);
+        const int upto = inc ? __ffs(inc) - 1 : 31;
+        int vn = 0, vb = 0, va = 0;
+        if (q >= 0 && lane <= upto && f != 0) {
+          const int o = (f == 2) ? 4 : 1;
+          vn = ld_volatile(st + 8 * q + o);
+          vb = ld_volatile(st + 8 * q + o + 1);
+          va = ld_volatile(st + 8 * q + o + 2);
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+          vn += __shfl_xor_sync(0xffffffffu, vn, d);
+          vb += __shfl_xor_sync(0xffffffffu, vb, d);
+          va += __shfl_xor_sync(0xffffffffu, va, d);
+        }
+        en += vn;
+        eb += vb;
+        ea += va;
+        if (inc) break;
+      }
+    }
+    if (lane == 0) {
+      me[4] = en + tn;
+      me[5] = eb + tb;
+      me[6] = ea + ta;
+      __threadfence();
+      atomicExch(me, 2);
+      s_excl[0] = en;
+      s_excl[1] = eb;
+      s_excl[2] = ea;
+    }
+  }
+  __syncthreads();
+  const int on = s_excl[0], ob = s_excl[1], oa = s_excl[2];
+  pn += on;
+  pb += ob;
+  pa += oa;
+#pragma unroll
+  for (int r = 0; r < SCAN_ITEMS; ++r) {
+    const int e = e0 + r;
+    if (e < m) {
+      I.new_start[e] = pn;
+      I.s.bucket_start[e] = pb;
+      if (ca[r]) I.s.active[pa] = make_int4(e, pn, pn + cn[r], 0);
+      I.s.in_cnt[e] = 0;
+      I.s.out_cnt[e] = 0;
+      I.s.bucket_fill[e] = 0;
+    }
+    pn += cn[r];
+    pb += cb[r];
+    pa += ca[r];
+  }
+  if (threadIdx.x == 0 && c == 0) {
+    I.s.ctr[C_MOVERS_SNAP] = I.s.ctr[C_MOVERS];
+    I.s.ctr[C_MOVERS] = 0;
+  }
+  __syncthreads();  // new_start of the dead range is written (last chunk)
+  if (threadIdx.x == 0) {
+    if (c == nchunks - 1) {
+      const int nact = oa + ta;
+      I.new_start[m] = (int32_t)I.n;
+      I.s.bucket_start[m] = ob + tb;
+      const int dead_start = I.new_start[I.ntiles];
+      I.s.ctr[C_ACTIVE] = nact;
+      I.s.ctr[C_DEAD_START] = dead_start;
+      I.s.ctr[C_BIN_ITEMS] = nact + ((int64_t)dead_start < I.n ? 1 : 0);
+    }
+    __threadfence();
+    s_last = atomicAdd(&G.work[W_SCAN_DONE], 1) == G.nblk_s - 1;
+  }
+  __syncthreads();
+  if (s_last) {  // every chunk of the group has finished its look-back
+    __threadfence();
+    for (int ii = 0; ii < G.ninst; ++ii) {
+      int32_t *sti = G.inst[ii].s.scan_tot;
+      for (int k = threadIdx.x; k < G.sblk[ii + 1] - G.sblk[ii]; k += blockDim.x) sti[8 * k] = 0;
+    }
+    group_prefix_body(G, wsum);
+  }
+}
+
+__global__ void bin_bucket(GroupArgs G) {
+  __shared__ InstArgs sI;
+  const int i = find_inst(G.mblk, G.ninst, blockIdx.x);
+  copy_inst(G.inst, i, &sI);
+  __syncthreads();
+  const InstArgs &I = sI;
+  const int lb = blockIdx.x - G.mblk[i];
+  const int nb = G.mblk[i + 1] - G.mblk[i];
+  const int nm = I.s.ctr[C_MOVERS_SNAP];
+  for (int m = lb * blockDim.x + threadIdx.x; m < nm; m += nb * blockDim.x) {
+    const int p = I.s.movers[m];
+    const int tn = min((int)(I.A.key()[p] >> LOCAL_BITS), I.ntiles);
+    I.s.bucket[I.s.bucket_start[tn] + atomicAdd(&I.s.bucket_fill[tn], 1)] = p;
+  }
 }
 
 // One CTA per instance (instances of at most SCAN1_MAX tiles): the whole scan
@@ -518,13 +556,10 @@ cudaError_t count_movers(const GroupArgs &G, cudaStream_t st) {
 cudaError_t bin_group(int dim, const GroupArgs &G, cudaStream_t st) {
   (void)dim;
   if (G.ninst <= 0 || G.nblk_p <= 0) return cudaSuccess;
-  if (G.scan_one) {
+  if (G.scan_one)
     bin_scan_one<<<G.ninst, SCAN1_T, 0, st>>>(G);
-  } else {
-    bin_scan_totals<<<G.nblk_s, SCAN_T, 0, st>>>(G);
-    bin_scan_apply<<<G.nblk_s, SCAN_T, 0, st>>>(G);
-    group_prefix<<<1, 256, 0, st>>>(G);
-  }
+  else
+    bin_scan_lb<<<G.nblk_s, SCAN_T, 0, st>>>(G);
   bin_bucket<<<G.nblk_m, 256, 0, st>>>(G);
   bin_tiles<<<G.grid, BT, 0, st>>>(G);
   return cudaGetLastError();

@@ -106,7 +106,7 @@ struct StepBufs {
   int32_t *bucket;         // n: movers grouped by destination tile
   int32_t *bucket_sorted;  // n: scratch for large buckets
   int4 *active;            // ntiles: active tiles in ascending order, (tile, new start, new end, -)
-  int32_t *scan_tot;       // 3 per block of the tile scan
+  int32_t *scan_tot;       // 8 per chunk of the tile scan (look-back flag, totals, prefix)
   int32_t *ctr;            // C_NCTR counters
   float *slots1;           // ntiles * box * channels (P2G USL / MOM)
   float *slots2;           // ntiles * box * D        (P2G FORCE, USF)
@@ -163,7 +163,7 @@ constexpr int SCAN1_MAX = 4096;
 // Per-group launch description.  The prefix arrays map a block (or a work
 // item) to its instance: entry i is the first block (item) of instance i and
 // entry ninst the total.
-enum { W_BIN = 0, W_P2G = 1, W_NODE = 2, W_P2G2 = 3, W_NODE2 = 4, W_SCAN_DONE = 5, W_COUNT = 8 };
+enum { W_BIN = 0, W_P2G = 1, W_NODE = 2, W_P2G2 = 3, W_NODE2 = 4, W_SCAN_DONE = 5, W_SCAN_TICKET = 6, W_COUNT = 8 };
 struct GroupArgs {
   const InstArgs *inst;     // device table
   int ninst;
