@@ -35,12 +35,16 @@ namespace mpm {
 namespace {
 
 constexpr int NODE_T = 128;
-constexpr int G2P_T = 256;
+#ifndef MPM_G2P_T
+#define MPM_G2P_T 128
+#endif
+constexpr int G2P_T = MPM_G2P_T;        // G2P threads per CTA
+constexpr int G2P_SUB = 256 / G2P_T;    // G2P CTAs per 256-particle block of the group prefix
 #ifndef MPM_P2G_MINB
 #define MPM_P2G_MINB 4  // resident P2G CTAs per SM the register budget is sized for
 #endif
 #ifndef MPM_G2P_MINB
-#define MPM_G2P_MINB 4  // resident G2P CTAs per SM the register budget is sized for
+#define MPM_G2P_MINB 8  // resident G2P CTAs per SM the register budget is sized for
 #endif
 
 // Instance of item x: the largest i with prefix[i] <= x (prefix[0] = 0).
@@ -527,12 +531,13 @@ __global__ void __launch_bounds__(G2P_T, MPM_G2P_MINB) g2p(GroupArgs G) {
   constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ;
   constexpr int NS = nstress<D>();
   __shared__ InstArgs sI;
-  const int ii = find_inst(G.pblk, G.ninst, blockIdx.x);
+  const int unit = blockIdx.x / G2P_SUB;
+  const int ii = find_inst(G.pblk, G.ninst, unit);
   copy_inst(G.inst, ii, &sI);
   __syncthreads();
   const InstArgs &I = sI;
   const Geo &g = I.geo;
-  const int64_t q = (int64_t)(blockIdx.x - G.pblk[ii]) * G2P_T + threadIdx.x;
+  const int64_t q = (int64_t)(unit - G.pblk[ii]) * 256 + (blockIdx.x % G2P_SUB) * G2P_T + threadIdx.x;
   if (q >= I.n) return;
   const int j = I.perm_out[q];
   const int dead_start = I.s.ctr[C_DEAD_START];
@@ -779,7 +784,7 @@ cudaError_t launch_node(const GroupArgs &G, int work_slot, cudaStream_t st) {
 
 template <int D, int GMODE>
 cudaError_t launch_g2p(const GroupArgs &G, cudaStream_t st) {
-  g2p<D, GMODE><<<G.nblk_p, G2P_T, 0, st>>>(G);
+  g2p<D, GMODE><<<G.nblk_p * G2P_SUB, G2P_T, 0, st>>>(G);
   return cudaGetLastError();
 }
 
