@@ -351,3 +351,26 @@ def test_material_update_degenerate_spectra(c):
     scale = np.abs(ref32).max(axis=1, keepdims=True) + 1.0
     assert H.rel_l2(out32, ref32) <= H.TOL_STEP_FP32
     assert np.all(np.abs(out32 - ref32) <= 2e-4 * scale)
+
+
+@pytest.mark.parametrize("kind", ["column2d", "slope2d", "slope3d"])
+@pytest.mark.parametrize("scheme", [W.USL, W.USF])
+def test_request_kinds_fp32(kind, scheme):
+    """The other workload kinds the serving loop runs -- 2D Mohr-Coulomb
+    column with base friction, 2D and 3D slopes with per-particle cohesion and
+    a fixed base -- against the oracle: one step, then a run."""
+    wl = W.request_workload(kind, 6e3 if kind != "slope3d" else 1.2e4, seed=W.SEED_BASE + 61, steps=120)
+    wl.scheme = scheme
+    d = wl.dim
+    start, _ = run_oracle(wl, 0, scheme)
+    g1, _ = run_gpu(wl, 1)
+    r1, _ = run_oracle(wl, 1, scheme)
+    e1 = H.compare(g1, r1, start, d)
+    assert H.worst(e1, H.STATE_KEYS) <= H.TOL_STEP_FP32, e1
+    gpu, st = run_gpu(wl, wl.steps)
+    ref, _ = run_oracle(wl, wl.steps, scheme)
+    assert st == mpm.MPM_OK
+    err = H.compare(gpu, ref, start, d)
+    assert H.worst(err, H.RUN_KEYS) <= H.TOL_RUN_FP32, err
+    ndiff, nout = H.cell_mismatch_in_band(gpu, ref, wl.h, 1e-4)
+    assert nout == 0
