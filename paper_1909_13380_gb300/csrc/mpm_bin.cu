@@ -309,7 +309,7 @@ __global__ void bin_bucket(GroupArgs G) {
 // over the instance's tiles in chunks with running offsets -- new ranges,
 // arrival offsets, the active list, counter resets -- and the CTA that
 // finishes last (counted on a work counter, no waiting) computes the group's
-// prefixes.  Replaces bin_scan_totals + bin_scan_apply + group_prefix.
+// prefixes.  For meshes this small it needs no look-back at all.
 __global__ void __launch_bounds__(SCAN1_T) bin_scan_one(GroupArgs G) {
   __shared__ int wsum[32];
   __shared__ int s_last;

@@ -523,7 +523,11 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // ---------------------------------------------------------------------------
-// G2P: one thread per particle in binning order
+// G2P: one thread per particle in binning order, G2P_T-thread CTAs.  Right
+// after reading its storage slot, each thread starts cp.async copies of its
+// particle's state (all but the offset) into its own shared-memory column;
+// they land while the node gather runs, and the thread waits only on its own
+// copies.
 // ---------------------------------------------------------------------------
 template <int D, int GMODE>
 __global__ void __launch_bounds__(G2P_T, MPM_G2P_MINB) g2p(GroupArgs G) {
