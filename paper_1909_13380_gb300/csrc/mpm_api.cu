@@ -377,6 +377,8 @@ mpm_status mpm_create_mesh(const mpm_mesh_desc *desc, mpm_handle *out) {
       return MPM_ERR_ARG;
     }
     g.ntiles = (int)nt;
+    g.div_nt0 = make_fastdiv(g.nt[0]);
+    g.div_nt01 = make_fastdiv(g.nt[0] * g.nt[1]);
     g.dead_key = (uint32_t)(nt * CELLS_PER_TILE);
     int bits = 1;
     while (((uint64_t)1 << bits) <= g.dead_key) ++bits;

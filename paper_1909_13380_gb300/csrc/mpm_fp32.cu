@@ -58,9 +58,12 @@ __device__ __forceinline__ int find_inst(const int32_t *prefix, int ninst, int x
 }
 
 __device__ __forceinline__ void tile_coords(const Geo &g, int t, int tc[3]) {
-  tc[0] = t % g.nt[0];
-  tc[1] = (t / g.nt[0]) % g.nt[1];
-  tc[2] = t / (g.nt[0] * g.nt[1]);
+  const int tz = g.div_nt01.div(t);
+  const int r = t - tz * (g.nt[0] * g.nt[1]);
+  const int ty = g.div_nt0.div(r);
+  tc[0] = r - ty * g.nt[0];
+  tc[1] = ty;
+  tc[2] = tz;
 }
 
 template <int D>

@@ -66,9 +66,31 @@ struct PBuf {
   __host__ __device__ __forceinline__ float *coh() const { return has_coh ? fld(23) : nullptr; }
 };
 
+// Division of 0 <= n < 2^26 by an invariant d >= 1 as a multiply and a
+// shift (Granlund & Montgomery, "Division by invariant integers using
+// multiplication", 1994): with l = ceil(log2 d), s = 32 + l and
+// m = floor(2^s / d) + 1, floor(n m / 2^s) = floor(n / d) for every n < 2^32;
+// n < 2^26 keeps n m below 2^64.
+struct FastDiv {
+  unsigned long long m;
+  int s;
+  __host__ __device__ __forceinline__ int div(int n) const {
+    return (int)(((unsigned long long)(unsigned)n * m) >> s);
+  }
+};
+inline FastDiv make_fastdiv(int d) {
+  int l = 0;
+  while ((1LL << l) < (long long)d) ++l;
+  FastDiv f;
+  f.s = 32 + l;
+  f.m = (unsigned long long)(((unsigned __int128)1 << f.s) / (unsigned)d) + 1;
+  return f;
+}
+
 struct Geo {
   int nc[3];   // cells per axis (nc[2] = 1 in 2D)
   int nt[3];   // tiles per axis
+  FastDiv div_nt0, div_nt01;  // division by nt[0] and by nt[0] nt[1]
   int ntiles;
   uint32_t dead_key;
   float h, inv_h, dt, mass_tol, inv_rho;
