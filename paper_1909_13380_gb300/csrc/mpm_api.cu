@@ -124,6 +124,17 @@ mpm_status cuda_fail(mpm_ctx *h, cudaError_t e, const char *where) {
 
 size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
 
+// Device allocations that an error return must release: freed on scope exit
+// unless handed over with release().
+struct DevGuard {
+  void *p[2] = {nullptr, nullptr};
+  ~DevGuard() {
+    for (void *q : p)
+      if (q) cudaFree(q);
+  }
+  void release() { p[0] = p[1] = nullptr; }
+};
+
 // One allocation holds the PBUF_FIELDS fields (the last one only with
 // per-particle cohesion), each al256(4 cap) bytes apart.
 size_t buf32_bytes(int dim, bool coh, int64_t cap) {
@@ -503,7 +514,8 @@ mpm_status mpm_add_particles(mpm_handle h, int64_t n, const double *pos, const d
   };
   if (h->d.precision == MPM_FP32_MIXED) {
     const int64_t cap = n1;
-    void *nm[2] = {nullptr, nullptr};
+    DevGuard guard;
+    void **nm = guard.p;
     for (int b = 0; b < 2; ++b) CK(cudaMalloc(&nm[b], buf32_bytes(D, coh, cap)), "particle storage");
     PBuf nb[2];
     carve32(nm[0], D, coh, cap, nb[0]);
@@ -581,6 +593,7 @@ mpm_status mpm_add_particles(mpm_handle h, int64_t n, const double *pos, const d
     for (int b = 0; b < 2; ++b) free_ptr(h->bufmem[b]);
     h->bufmem[0] = nm[0];
     h->bufmem[1] = nm[1];
+    guard.release();
     h->buf[0] = nb[0];
     h->buf[1] = nb[1];
     h->cur = 0;
@@ -588,7 +601,8 @@ mpm_status mpm_add_particles(mpm_handle h, int64_t n, const double *pos, const d
     h->geo.inv_rho = (float)(1.0 / mat->rho);
   } else {
     const int64_t cap = n1;
-    void *nmem = nullptr;
+    DevGuard guard;
+    void *&nmem = guard.p[0];
     CK(cudaMalloc(&nmem, buf64_bytes(D, coh, cap)), "particle storage");
     D64State P;
     carve64(nmem, D, coh, cap, P);
@@ -633,6 +647,7 @@ mpm_status mpm_add_particles(mpm_handle h, int64_t n, const double *pos, const d
     CK(cudaStreamSynchronize(h->st), "upload");
     free_ptr(h->pmem64);
     h->pmem64 = nmem;
+    guard.release();
     h->L64.P = P;
     h->cap = cap;
   }
