@@ -378,17 +378,20 @@ def run_batched(args, flush, stream):
             "gpu_launches_per_batched_step": max(binning_launches(w) for w in wls) + 3}
 
 
-def serve_session(reqs, wls, chunk):
+def serve_session(reqs, chunk):
     """One session of `reqs` with continuous batching (FP32 mixed) and one at
-    a time in plain FP64."""
+    a time in plain FP64.  Request inputs are built on a background thread a
+    few requests ahead of their arrival and dropped once on the device."""
     from paper_1909_13380_gb300 import serve
     out = {}
     for name, kw in (("fp32_continuous_batching", dict(batched=True)),
                      ("fp64_one_at_a_time", dict(precision=W.FP64_PLAIN, batched=False))):
         eng = serve.GpuEngine(**kw)
+        stream = serve.RequestStream(reqs, lambda r: r.workload(), ahead=16)
         try:
-            done, lat, total = serve.Server(eng, chunk=chunk).run(reqs, wls)
+            done, lat, total = serve.Server(eng, chunk=chunk).run(reqs, stream)
         finally:
+            stream.close()
             eng.shutdown()
         rep = serve.report(done, lat, total)
         rep["h2d_bytes"], rep["d2h_bytes"] = eng.h2d, eng.d2h
@@ -402,17 +405,16 @@ def run_serving(args):
     20 requests/s; with --serve-rates, the same requests at other rates too
     (arrival times scaled)."""
     reqs = W.serving_requests(count=args.serve_requests, step_scale=args.serve_step_scale)
-    wls32 = [r.workload() for r in reqs]
     out = {"requests": len(reqs), "arrival_rate_per_s": 20.0,
            "sample": f"{len(reqs)} requests, 1e4-4e6 particles (log-uniform), 1000-20000 steps (log-uniform) "
                      f"x {args.serve_step_scale:g}, kinds {'/'.join(W.REQUEST_KINDS)}"}
-    out.update(serve_session(reqs, wls32, args.serve_chunk))
+    out.update(serve_session(reqs, args.serve_chunk))
     rates = [float(x) for x in args.serve_rates.split(",") if x] if args.serve_rates else []
     if rates:
         sweep = []
         for rate in rates:
             scaled = [dataclasses.replace(r, arrival=r.arrival * 20.0 / rate) for r in reqs]
-            res = serve_session(scaled, wls32, args.serve_chunk)
+            res = serve_session(scaled, args.serve_chunk)
             sweep.append({"arrival_rate_per_s": rate, **{
                 k: {m: res[k][m] for m in ("session_s", "utilisation", "step_ms", "e2e_s", "queue_s")}
                 for k in res}})

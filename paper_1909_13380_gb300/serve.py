@@ -160,6 +160,10 @@ class Server:
         nxt = 0
         t0 = self.clock()
         nslots = 0
+        nparts: dict[int, int] = {}
+        # a workload source may drop a request's host arrays once it is on
+        # the device (see RequestStream)
+        release = getattr(workloads, "release", lambda i: None)
 
         def now():
             return self.clock() - t0
@@ -183,9 +187,12 @@ class Server:
                     r = requests[i]
                     t = now()
                     done.append(Finished(i, r.kind, workloads[i].n, r.steps, r.arrival, t, t, ERR_OOM))
+                    release(i)
                     continue
                 queue.popleft()
+                nparts[i] = workloads[i].n
                 staged.append((i, eng.create(workloads[i]), now()))
+                release(i)                        # the inputs are on the device now
 
         def finish(a: _Active, status: int):
             snap = None
@@ -194,7 +201,7 @@ class Server:
                 status = status or st
             eng.close(a.sim)
             r = requests[a.rid]
-            done.append(Finished(a.rid, r.kind, workloads[a.rid].n, r.steps, r.arrival, a.admitted, now(),
+            done.append(Finished(a.rid, r.kind, nparts[a.rid], r.steps, r.arrival, a.admitted, now(),
                                  status, snap if self.keep else None))
 
         staged: list = []
@@ -238,6 +245,62 @@ class Server:
                     single.pop(0)
                     finish(a, status[0])
         return done, lat, now()
+
+
+class RequestStream:
+    """Workloads of a request stream built on a background thread in arrival
+    order, at most `ahead` requests before they are consumed (a client that
+    prepares its request before sending it), and dropped once the server has
+    put them on the device -- so a long session does not hold every
+    request's particle arrays in host memory at once.  `build(request)`
+    returns the workload."""
+
+    def __init__(self, requests, build, ahead=8):
+        import threading
+        self.reqs = requests
+        self.build = build
+        self.ahead = ahead
+        self.order = sorted(range(len(requests)), key=lambda i: requests[i].arrival)
+        self.pos = {i: k for k, i in enumerate(self.order)}
+        self.ready: dict[int, object] = {}
+        self.consumed = 0                 # requests released so far
+        self.cv = threading.Condition()
+        self.stop = False
+        self.thread = threading.Thread(target=self._run, daemon=True)
+        self.thread.start()
+
+    def _run(self):
+        for k, i in enumerate(self.order):
+            with self.cv:
+                while not self.stop and k >= self.consumed + self.ahead:
+                    self.cv.wait()
+                if self.stop:
+                    return
+            wl = self.build(self.reqs[i])
+            with self.cv:
+                self.ready[i] = wl
+                self.cv.notify_all()
+
+    def __getitem__(self, i):
+        with self.cv:
+            while i not in self.ready:
+                self.cv.wait()
+            return self.ready[i]
+
+    def __len__(self):
+        return len(self.reqs)
+
+    def release(self, i):
+        with self.cv:
+            if self.ready.pop(i, None) is not None:
+                self.consumed += 1
+                self.cv.notify_all()
+
+    def close(self):
+        with self.cv:
+            self.stop = True
+            self.cv.notify_all()
+        self.thread.join(timeout=60)
 
 
 def percentiles(values, weights=None):

@@ -156,3 +156,30 @@ def test_utilisation_is_device_time_over_session():
     busy = sum(ms * k for ms, k in lat) * 1e-3
     assert rep["gpu_busy_s"] == busy
     assert 0.0 < rep["utilisation"] <= 1.0 + 1e-12
+
+
+def test_request_stream_builds_ahead_and_drops_released():
+    reqs = W.serving_requests(count=30, rate=50.0, n_range=(1e3, 5e4), steps_range=(5, 200), step_scale=1.0)
+    built = []
+
+    def build(r):
+        built.append(r.rid)
+        return TinyWl(r.n_target, r.steps)
+
+    stream = serve.RequestStream(reqs, build, ahead=4)
+    clock = [0.0]
+
+    def sleep(dt):
+        clock[0] += dt
+
+    eng = FakeEngine(True, 10_000_000, clock)
+    try:
+        done, lat, total = serve.Server(eng, chunk=8, keep_results=True, clock=lambda: clock[0],
+                                        sleep=sleep).run(reqs, stream)
+    finally:
+        stream.close()
+    assert sorted(f.rid for f in done) == list(range(len(reqs)))
+    assert all(f.result["steps"] == reqs[f.rid].steps for f in done)
+    assert all(f.n == reqs[f.rid].n_target for f in done)
+    assert sorted(built) == list(range(len(reqs)))
+    assert len(stream.ready) == 0          # every request's arrays were dropped after admission
