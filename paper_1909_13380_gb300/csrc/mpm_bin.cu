@@ -161,6 +161,8 @@ __global__ void __launch_bounds__(SCAN_T) bin_scan_lb(GroupArgs G) {
   __shared__ int s_ticket, s_last;
   __shared__ int s_excl[3];
   __shared__ InstArgs sI;
+  pdl_trigger();
+  pdl_wait();
   if (threadIdx.x == 0) s_ticket = atomicAdd(&G.work[W_SCAN_TICKET], 1);
   __syncthreads();
   const int tk = s_ticket;
@@ -291,8 +293,10 @@ __global__ void __launch_bounds__(SCAN_T) bin_scan_lb(GroupArgs G) {
 
 __global__ void bin_bucket(GroupArgs G) {
   __shared__ InstArgs sI;
-  const int i = find_inst(G.mblk, G.ninst, blockIdx.x);
+  pdl_trigger();
+  const int i = find_inst(G.mblk, G.ninst, blockIdx.x);  // host-written tables
   copy_inst(G.inst, i, &sI);
+  pdl_wait();
   __syncthreads();
   const InstArgs &I = sI;
   const int lb = blockIdx.x - G.mblk[i];
@@ -314,7 +318,9 @@ __global__ void __launch_bounds__(SCAN1_T) bin_scan_one(GroupArgs G) {
   __shared__ int wsum[32];
   __shared__ int s_last;
   __shared__ InstArgs sI;
-  copy_inst(G.inst, blockIdx.x, &sI);
+  pdl_trigger();
+  copy_inst(G.inst, blockIdx.x, &sI);  // host-written table
+  pdl_wait();
   __syncthreads();
   const InstArgs &I = sI;
   const int m = I.ntiles + 1;
@@ -388,7 +394,9 @@ __global__ void __launch_bounds__(BT) bin_tiles(GroupArgs G) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t lt_mask = (1u << lane) - 1u;
   __shared__ int s_work[2];
+  pdl_trigger();
   for (int k = tid; k < BT_WARPS * (CELLS_PER_TILE + 1); k += BT) (&wcnt[0][0])[k] = 0;
+  pdl_wait();
   if (tid == 0) s_work[0] = atomicAdd(&G.work[W_BIN], 1);
   __syncthreads();
   const int total = G.bin_items[G.ninst];
@@ -556,13 +564,11 @@ cudaError_t count_movers(const GroupArgs &G, cudaStream_t st) {
 cudaError_t bin_group(int dim, const GroupArgs &G, cudaStream_t st) {
   (void)dim;
   if (G.ninst <= 0 || G.nblk_p <= 0) return cudaSuccess;
-  if (G.scan_one)
-    bin_scan_one<<<G.ninst, SCAN1_T, 0, st>>>(G);
-  else
-    bin_scan_lb<<<G.nblk_s, SCAN_T, 0, st>>>(G);
-  bin_bucket<<<G.nblk_m, 256, 0, st>>>(G);
-  bin_tiles<<<G.grid, BT, 0, st>>>(G);
-  return cudaGetLastError();
+  cudaError_t e = G.scan_one ? launch_dep(bin_scan_one, G.ninst, SCAN1_T, 0, st, G)
+                             : launch_dep(bin_scan_lb, G.nblk_s, SCAN_T, 0, st, G);
+  if (e == cudaSuccess) e = launch_dep(bin_bucket, G.nblk_m, 256, 0, st, G);
+  if (e == cudaSuccess) e = launch_dep(bin_tiles, G.grid, BT, 0, st, G);
+  return e;
 }
 
 cudaError_t permute_state(int dim, int64_t n, const PBuf &A, const PBuf &B, const int32_t *perm, cudaStream_t st) {

@@ -167,7 +167,9 @@ __global__ void __launch_bounds__(P2GRec<D, MODE>::CH, MPM_P2G_MINB) p2g_tile(Gr
   __shared__ InstArgs sI;
   const int tid = threadIdx.x;
   const int my_cell = tid / CPC, my_cp = tid % CPC;  // corners my_cp + r * CPC
+  pdl_trigger();
   if (tid < CELLS_PER_TILE) stamp[tid] = -1;
+  pdl_wait();
   if (tid == 0) s_work[0] = atomicAdd(&G.work[work_slot], 1);
   __syncthreads();
   int chunk_id = 0, loaded = -1;
@@ -421,6 +423,8 @@ __global__ void __launch_bounds__(NODE_T) node_tile(GroupArgs G, int work_slot) 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const InstArgs &I = sI[warp];
   (void)work_slot;
+  pdl_trigger();
+  pdl_wait();
   int loaded = -1;
   const int stride = gridDim.x * NW;
   const int nact = G.act_items[G.ninst];
@@ -538,9 +542,11 @@ __global__ void __launch_bounds__(G2P_T, MPM_G2P_MINB) g2p(GroupArgs G) {
   constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ;
   constexpr int NS = nstress<D>();
   __shared__ InstArgs sI;
+  pdl_trigger();
   const int unit = blockIdx.x / G2P_SUB;
-  const int ii = find_inst(G.pblk, G.ninst, unit);
+  const int ii = find_inst(G.pblk, G.ninst, unit);  // host-written tables
   copy_inst(G.inst, ii, &sI);
+  pdl_wait();
   __syncthreads();
   const InstArgs &I = sI;
   const Geo &g = I.geo;
@@ -773,8 +779,7 @@ __global__ void __launch_bounds__(G2P_T, MPM_G2P_MINB) g2p(GroupArgs G) {
 
 template <int D, int MODE>
 cudaError_t launch_p2g(const GroupArgs &G, int work_slot, cudaStream_t st) {
-  p2g_tile<D, MODE><<<G.grid, p2g_threads<D>(), p2g_smem<D, MODE>(), st>>>(G, work_slot);
-  return cudaGetLastError();
+  return launch_dep(p2g_tile<D, MODE>, G.grid, p2g_threads<D>(), p2g_smem<D, MODE>(), st, G, work_slot);
 }
 
 template <int D, int MODE>
@@ -785,14 +790,12 @@ cudaError_t prepare_p2g() {
 
 template <int D, int NMODE>
 cudaError_t launch_node(const GroupArgs &G, int work_slot, cudaStream_t st) {
-  node_tile<D, NMODE><<<G.grid, NODE_T, 0, st>>>(G, work_slot);
-  return cudaGetLastError();
+  return launch_dep(node_tile<D, NMODE>, G.grid, NODE_T, 0, st, G, work_slot);
 }
 
 template <int D, int GMODE>
 cudaError_t launch_g2p(const GroupArgs &G, cudaStream_t st) {
-  g2p<D, GMODE><<<G.nblk_p * G2P_SUB, G2P_T, 0, st>>>(G);
-  return cudaGetLastError();
+  return launch_dep(g2p<D, GMODE>, G.nblk_p * G2P_SUB, G2P_T, 0, st, G);
 }
 
 template <int D>

@@ -200,6 +200,39 @@ struct GroupArgs {
   int grid;                 // CTAs of the per-tile kernels
 };
 
+// Programmatic dependent launch.  The kernels of a step are launched with
+// launch_dep(), which lets a kernel's CTAs be scheduled while the kernel
+// before it in the stream is still running, hiding the launch and the CTA
+// ramp between dependent kernels.  A CTA so launched runs only code that
+// reads what the host wrote before the step (the group's instance table and
+// block prefixes), then pdl_wait(): it returns once the preceding kernel has
+// completed and its writes are visible (that kernel passed its own pdl_wait,
+// so every earlier kernel has completed too).  Every CTA calls pdl_wait()
+// before it touches any other memory or exits, otherwise the grid could
+// complete ahead of its predecessor.  pdl_trigger() releases the next kernel
+// once every CTA of this grid has called it or exited; a kernel is released
+// only when all of its predecessor's CTAs are running, so the waits always
+// end.  Without a preceding kernel (a graph's first node, a copy, an event
+// node) both are no-ops and the launch is an ordinary stream-ordered one.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_dep(void (*kern)(KArgs...), int grid, int block, size_t smem, cudaStream_t st,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // Record a phase boundary (works inside stream capture as an external node).
 inline cudaError_t phase_mark(cudaEvent_t *ev, int i, cudaStream_t st) {
   return ev ? cudaEventRecordWithFlags(ev[i], st, cudaEventRecordExternal) : cudaSuccess;
