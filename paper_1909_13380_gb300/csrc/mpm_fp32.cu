@@ -148,8 +148,9 @@ constexpr int p2g_threads() {
 // multiple of eight apart, read different shared-memory banks.
 __device__ __forceinline__ int rec_slot(int i) { return (i & ~7) | ((i ^ (i >> 3)) & 7); }
 
-template <int D, int MODE>
-__global__ void __launch_bounds__(P2GRec<D, MODE>::CH, MPM_P2G_MINB) p2g_tile(GroupArgs G, int work_slot) {
+template <int D, int MODE, bool ONE>
+__global__ void __launch_bounds__(P2GRec<D, MODE>::CH, MPM_P2G_MINB)
+    p2g_tile(const __grid_constant__ GroupArgs G, int work_slot) {
   using R = P2GRec<D, MODE>;
   constexpr int NCH = p2g_channels<D, MODE>();
   constexpr int NV = R::NV;
@@ -181,16 +182,16 @@ __global__ void __launch_bounds__(P2GRec<D, MODE>::CH, MPM_P2G_MINB) p2g_tile(Gr
     // the next work item is fetched now and published at the end of this one
     int wnext = 0;
     if (tid == 0) wnext = atomicAdd(&G.work[work_slot], 1);
-    const int ii = find_inst(G.act_items, G.ninst, wi);
-    if (ii != loaded) {  // uniform
+    const int ii = ONE ? 0 : find_inst(G.act_items, G.ninst, wi);
+    if (!ONE && ii != loaded) {  // uniform
       copy_inst(G.inst, ii, &sI);
       loaded = ii;
       __syncthreads();
     }
-    const InstArgs &I = sI;
+    const InstArgs &I = inst_ref<ONE>(G, sI);
     const Geo &g = I.geo;
     float *slots_out = MODE == P2G_FORCE ? I.s.slots2 : I.s.slots1;
-    const int4 ar = I.s.active[wi - G.act_items[ii]];
+    const int4 ar = I.s.active[ONE ? wi : wi - G.act_items[ii]];
     const int t = ar.x, s = ar.y, e = ar.z;
     float w0[D], w1[D], acc[CPT][NCH];
 #pragma unroll
@@ -412,8 +413,8 @@ __device__ __forceinline__ void gather_node(const Geo &g, const float *slots, in
 // fill the grid.  The nodes whose lowest active holder is the tile -- every
 // node is computed once -- get v = P/m, a = f/m + g, v' = v + a dt and the
 // boundary conditions, written to the dense node records.
-template <int D, int NMODE>
-__global__ void __launch_bounds__(NODE_T) node_tile(GroupArgs G, int work_slot) {
+template <int D, int NMODE, bool ONE>
+__global__ void __launch_bounds__(NODE_T) node_tile(const __grid_constant__ GroupArgs G, int work_slot) {
   constexpr int BN = box_nodes<D>();
   constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ;
   constexpr int NCH1 = NMODE == NODE_USL ? 1 + 2 * D : 1 + D;
@@ -421,7 +422,7 @@ __global__ void __launch_bounds__(NODE_T) node_tile(GroupArgs G, int work_slot) 
   constexpr int NSL = (BN + 31) / 32;  // slices per tile
   __shared__ InstArgs sI[NW];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const InstArgs &I = sI[warp];
+  const InstArgs &I = inst_ref<ONE>(G, sI[warp]);
   (void)work_slot;
   pdl_trigger();
   pdl_wait();
@@ -432,8 +433,8 @@ __global__ void __launch_bounds__(NODE_T) node_tile(GroupArgs G, int work_slot) 
   const int total = nact * split;
   for (int wi = blockIdx.x * NW + warp; wi < total; wi += stride) {
     const int item = wi / split, slice0 = wi % split;
-    const int ii = find_inst(G.act_items, G.ninst, item);
-    if (ii != loaded) {  // warp-uniform
+    const int ii = ONE ? 0 : find_inst(G.act_items, G.ninst, item);
+    if (!ONE && ii != loaded) {  // warp-uniform
       const unsigned long long *src = reinterpret_cast<const unsigned long long *>(G.inst + ii);
       unsigned long long *dst = reinterpret_cast<unsigned long long *>(&sI[warp]);
       for (int i = lane; i < (int)(sizeof(InstArgs) / 8); i += 32) dst[i] = __ldg(src + i);
@@ -441,7 +442,7 @@ __global__ void __launch_bounds__(NODE_T) node_tile(GroupArgs G, int work_slot) 
       loaded = ii;
     }
     const Geo &g = I.geo;
-    const int t = I.s.active[item - G.act_items[ii]].x;
+    const int t = I.s.active[ONE ? item : item - G.act_items[ii]].x;
     int tc[3];
     tile_coords(g, t, tc);
     // activity of the 27 tiles around t, one lane each
@@ -516,7 +517,7 @@ __global__ void __launch_bounds__(NODE_T) node_tile(GroupArgs G, int work_slot) 
         I.s.node[gi] = make_float4(w[0], w[1], a[0], a[1]);
       }
     } while (0);
-    __syncwarp();  // the instance copy may be replaced next
+    if (!ONE) __syncwarp();  // the instance copy may be replaced next
   }
 }
 
@@ -536,21 +537,21 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // they land while the node gather runs, and the thread waits only on its own
 // copies.
 // ---------------------------------------------------------------------------
-template <int D, int GMODE>
-__global__ void __launch_bounds__(G2P_T, MPM_G2P_MINB) g2p(GroupArgs G) {
+template <int D, int GMODE, bool ONE>
+__global__ void __launch_bounds__(G2P_T, MPM_G2P_MINB) g2p(const __grid_constant__ GroupArgs G) {
   constexpr int NC = 1 << D;
   constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ;
   constexpr int NS = nstress<D>();
   __shared__ InstArgs sI;
   pdl_trigger();
   const int unit = blockIdx.x / G2P_SUB;
-  const int ii = find_inst(G.pblk, G.ninst, unit);  // host-written tables
-  copy_inst(G.inst, ii, &sI);
+  const int ii = ONE ? 0 : find_inst(G.pblk, G.ninst, unit);  // host-written tables
+  if (!ONE) copy_inst(G.inst, ii, &sI);
   pdl_wait();
-  __syncthreads();
-  const InstArgs &I = sI;
+  if (!ONE) __syncthreads();
+  const InstArgs &I = inst_ref<ONE>(G, sI);
   const Geo &g = I.geo;
-  const int64_t q = (int64_t)(unit - G.pblk[ii]) * 256 + (blockIdx.x % G2P_SUB) * G2P_T + threadIdx.x;
+  const int64_t q = (int64_t)(unit - (ONE ? 0 : G.pblk[ii])) * 256 + (blockIdx.x % G2P_SUB) * G2P_T + threadIdx.x;
   if (q >= I.n) return;
   const int j = I.perm_out[q];
   const int dead_start = I.s.ctr[C_DEAD_START];
@@ -779,23 +780,30 @@ __global__ void __launch_bounds__(G2P_T, MPM_G2P_MINB) g2p(GroupArgs G) {
 
 template <int D, int MODE>
 cudaError_t launch_p2g(const GroupArgs &G, int work_slot, cudaStream_t st) {
-  return launch_dep(p2g_tile<D, MODE>, G.grid, p2g_threads<D>(), p2g_smem<D, MODE>(), st, G, work_slot);
+  return G.ninst == 1
+             ? launch_dep(p2g_tile<D, MODE, true>, G.grid, p2g_threads<D>(), p2g_smem<D, MODE>(), st, G, work_slot)
+             : launch_dep(p2g_tile<D, MODE, false>, G.grid, p2g_threads<D>(), p2g_smem<D, MODE>(), st, G, work_slot);
 }
 
 template <int D, int MODE>
 cudaError_t prepare_p2g() {
-  return cudaFuncSetAttribute(p2g_tile<D, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(p2g_tile<D, MODE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)p2g_smem<D, MODE>());
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(p2g_tile<D, MODE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)p2g_smem<D, MODE>());
 }
 
 template <int D, int NMODE>
 cudaError_t launch_node(const GroupArgs &G, int work_slot, cudaStream_t st) {
-  return launch_dep(node_tile<D, NMODE>, G.grid, NODE_T, 0, st, G, work_slot);
+  return G.ninst == 1 ? launch_dep(node_tile<D, NMODE, true>, G.grid, NODE_T, 0, st, G, work_slot)
+                      : launch_dep(node_tile<D, NMODE, false>, G.grid, NODE_T, 0, st, G, work_slot);
 }
 
 template <int D, int GMODE>
 cudaError_t launch_g2p(const GroupArgs &G, cudaStream_t st) {
-  return launch_dep(g2p<D, GMODE>, G.nblk_p * G2P_SUB, G2P_T, 0, st, G);
+  return G.ninst == 1 ? launch_dep(g2p<D, GMODE, true>, G.nblk_p * G2P_SUB, G2P_T, 0, st, G)
+                      : launch_dep(g2p<D, GMODE, false>, G.nblk_p * G2P_SUB, G2P_T, 0, st, G);
 }
 
 template <int D>

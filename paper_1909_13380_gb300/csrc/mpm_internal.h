@@ -198,7 +198,22 @@ struct GroupArgs {
   int nblk_p, nblk_s, nblk_m;
   int scan_one;             // every instance has at most SCAN1_MAX tiles: one-CTA scans
   int grid;                 // CTAs of the per-tile kernels
+  InstArgs one;             // a group of one: its table entry (inst[0]) by value
 };
+
+// The instance a kernel of the step reads.  For a group of one it is the copy
+// inside the kernel's parameters (passed __grid_constant__): its constants are
+// constant-bank operands of the arithmetic and cost no load instruction.
+// Otherwise it is the block's (or warp's) shared-memory copy of its table
+// entry, which costs a shared load wherever a constant is not kept in a
+// register.
+template <bool ONE>
+__device__ __forceinline__ const InstArgs &inst_ref(const GroupArgs &G, const InstArgs &shared_copy) {
+  if constexpr (ONE)
+    return G.one;
+  else
+    return shared_copy;
+}
 
 // Programmatic dependent launch.  The kernels of a step are launched with
 // launch_dep(), which lets a kernel's CTAs be scheduled while the kernel
