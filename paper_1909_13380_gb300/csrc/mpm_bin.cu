@@ -17,7 +17,8 @@
 //                    list, counter resets; the last block to finish computes
 //                    the work prefixes over the instances of the group;
 //   bin_scan_one     (instead, when every instance has at most SCAN1_MAX
-//                    tiles) one CTA per instance scans all of its tiles;
+//                    tiles) one CTA per instance scans all of its tiles in
+//                    one pass;
 //   bin_bucket       groups the arrivals by destination tile;
 //   bin_tiles        one CTA per tile: the tile's particles are the stayers
 //                    of its old range plus its arrivals; a stable counting
@@ -44,7 +45,9 @@ constexpr int BUCKET_SMEM = 1024;
 constexpr int SCAN_T = 256;
 constexpr int SCAN_ITEMS = 4;
 constexpr int SCAN_CHUNK = SCAN_T * SCAN_ITEMS;  // tiles per scan block
-constexpr int SCAN1_T = 1024;                    // one-CTA scan
+constexpr int SCAN1_T = 1024;                    // one-CTA scan: threads
+constexpr int SCAN1_K = 16;                      // one-CTA scan: tiles per thread at most
+static_assert(SCAN1_T * SCAN1_K == SCAN1_MAX, "the one-CTA scan covers SCAN1_MAX tiles");
 
 // Instance of item x: the largest i with prefix[i] <= x (prefix[0] = 0).
 __device__ __forceinline__ int find_inst(const int32_t *prefix, int ninst, int x) {
@@ -99,6 +102,31 @@ __device__ __forceinline__ int cta_excl(int v, int *wsum, int &total) {
   const int base = w ? wsum[w - 1] : 0;
   __syncthreads();
   return base + inc - v;
+}
+
+// The same for three values per thread at once (three scans, one set of
+// barriers); v becomes the three prefixes.
+__device__ __forceinline__ void cta_excl3(int v[3], int (*wsum)[32], int total[3]) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int inc[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    inc[k] = warp_incl(v[k]);
+    if (lane == 31) wsum[k][w] = inc[k];
+  }
+  __syncthreads();
+  if (w < 3) {
+    int s = lane < nw ? wsum[w][lane] : 0;
+    s = warp_incl(s);
+    if (lane < nw) wsum[w][lane] = s;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    total[k] = wsum[k][nw - 1];
+    v[k] = (w ? wsum[k][w - 1] : 0) + inc[k] - v[k];
+  }
+  __syncthreads();
 }
 
 // Per tile e (tiles plus the dead range): new count = old count - leavers +
@@ -156,7 +184,8 @@ constexpr int LB_SPIN_LIMIT = 1 << 20;
 
 __device__ __forceinline__ int ld_volatile(const int32_t *p) { return *(const volatile int32_t *)p; }
 
-__global__ void __launch_bounds__(SCAN_T) bin_scan_lb(GroupArgs G) {
+template <bool ONE>
+__global__ void __launch_bounds__(SCAN_T) bin_scan_lb(const __grid_constant__ GroupArgs G) {
   __shared__ int wsum[32];
   __shared__ int s_ticket, s_last;
   __shared__ int s_excl[3];
@@ -166,12 +195,14 @@ __global__ void __launch_bounds__(SCAN_T) bin_scan_lb(GroupArgs G) {
   if (threadIdx.x == 0) s_ticket = atomicAdd(&G.work[W_SCAN_TICKET], 1);
   __syncthreads();
   const int tk = s_ticket;
-  const int i = find_inst(G.sblk, G.ninst, tk);
-  copy_inst(G.inst, i, &sI);
-  __syncthreads();
-  const InstArgs &I = sI;
-  const int c = tk - G.sblk[i];
-  const int nchunks = G.sblk[i + 1] - G.sblk[i];
+  const int i = ONE ? 0 : find_inst(G.sblk, G.ninst, tk);
+  if (!ONE) {
+    copy_inst(G.inst, i, &sI);
+    __syncthreads();
+  }
+  const InstArgs &I = inst_ref<ONE>(G, sI);
+  const int c = ONE ? tk : tk - G.sblk[i];
+  const int nchunks = ONE ? G.nblk_s : G.sblk[i + 1] - G.sblk[i];
   const int m = I.ntiles + 1;
   int32_t *st = I.s.scan_tot;
   const int e0 = c * SCAN_CHUNK + threadIdx.x * SCAN_ITEMS;
@@ -291,16 +322,17 @@ __global__ void __launch_bounds__(SCAN_T) bin_scan_lb(GroupArgs G) {
   }
 }
 
-__global__ void bin_bucket(GroupArgs G) {
+template <bool ONE>
+__global__ void bin_bucket(const __grid_constant__ GroupArgs G) {
   __shared__ InstArgs sI;
   pdl_trigger();
-  const int i = find_inst(G.mblk, G.ninst, blockIdx.x);  // host-written tables
-  copy_inst(G.inst, i, &sI);
+  const int i = ONE ? 0 : find_inst(G.mblk, G.ninst, blockIdx.x);  // host-written tables
+  if (!ONE) copy_inst(G.inst, i, &sI);
   pdl_wait();
-  __syncthreads();
-  const InstArgs &I = sI;
-  const int lb = blockIdx.x - G.mblk[i];
-  const int nb = G.mblk[i + 1] - G.mblk[i];
+  if (!ONE) __syncthreads();
+  const InstArgs &I = inst_ref<ONE>(G, sI);
+  const int lb = ONE ? blockIdx.x : blockIdx.x - G.mblk[i];
+  const int nb = ONE ? G.nblk_m : G.mblk[i + 1] - G.mblk[i];
   const int nm = I.s.ctr[C_MOVERS_SNAP];
   for (int m = lb * blockDim.x + threadIdx.x; m < nm; m += nb * blockDim.x) {
     const int p = I.s.movers[m];
@@ -310,79 +342,112 @@ __global__ void bin_bucket(GroupArgs G) {
 }
 
 // One CTA per instance (instances of at most SCAN1_MAX tiles): the whole scan
-// over the instance's tiles in chunks with running offsets -- new ranges,
-// arrival offsets, the active list, counter resets -- and the CTA that
-// finishes last (counted on a work counter, no waiting) computes the group's
-// prefixes.  For meshes this small it needs no look-back at all.
-__global__ void __launch_bounds__(SCAN1_T) bin_scan_one(GroupArgs G) {
-  __shared__ int wsum[32];
+// over the instance's tiles in one pass -- new ranges, arrival offsets, the
+// active list, counter resets.  Warp w owns the K consecutive 32-tile chunks
+// from tile 32 K w (K = ceil(tiles / SCAN1_T) <= SCAN1_K); lane l holds tile
+// l of each chunk, so every load and store is coalesced and all the loads
+// are in flight at once.  The warps' totals go through one CTA scan, then
+// each warp scans its chunks in order with a running offset.  For a group of
+// one the CTA then writes the group's prefixes itself; otherwise the CTA that
+// finishes last (counted on a work counter, no waiting) computes them.
+template <bool ONE>
+__global__ void __launch_bounds__(SCAN1_T) bin_scan_one(const __grid_constant__ GroupArgs G) {
+  __shared__ int wsum3[3][32];
   __shared__ int s_last;
   __shared__ InstArgs sI;
   pdl_trigger();
-  copy_inst(G.inst, blockIdx.x, &sI);  // host-written table
+  if (!ONE) copy_inst(G.inst, blockIdx.x, &sI);  // host-written table
   pdl_wait();
-  __syncthreads();
-  const InstArgs &I = sI;
+  if (!ONE) __syncthreads();
+  const InstArgs &I = inst_ref<ONE>(G, sI);
   const int m = I.ntiles + 1;
-  int on = 0, ob = 0, oa = 0;
-  for (int c0 = 0; c0 < m; c0 += SCAN1_T * SCAN_ITEMS) {
-    const int e0 = c0 + threadIdx.x * SCAN_ITEMS;
-    int cn[SCAN_ITEMS], cb[SCAN_ITEMS], ca[SCAN_ITEMS];
-    int sn = 0, sb = 0, sa = 0;
+  const int lane = threadIdx.x & 31;
+  const int K = (m + SCAN1_T - 1) / SCAN1_T;       // <= SCAN1_K: the host checks m <= SCAN1_MAX
+  const int seg0 = (threadIdx.x >> 5) * K * 32;  // this warp's first tile
+  int cn[SCAN1_K], cb[SCAN1_K];
+  int v[3] = {0, 0, 0};  // this lane's count, arrivals, active tiles
 #pragma unroll
-    for (int r = 0; r < SCAN_ITEMS; ++r) {
-      const int e = e0 + r;
-      cn[r] = cb[r] = ca[r] = 0;
-      if (e < m) tile_counts(I, e, cn[r], cb[r], ca[r]);
-      sn += cn[r];
-      sb += cb[r];
-      sa += ca[r];
+  for (int r = 0; r < SCAN1_K; ++r) {
+    const int e = seg0 + r * 32 + lane;
+    cn[r] = cb[r] = 0;
+    if (r < K && e < m) {
+      const int in = I.s.in_cnt[e], out = I.s.out_cnt[e];
+      cn[r] = (I.old_start[e + 1] - I.old_start[e]) - out + in;
+      cb[r] = in;
+      v[2] += (e < I.ntiles && cn[r] > 0) ? 1 : 0;
     }
-    int tn, tb, ta;
-    int pn = cta_excl(sn, wsum, tn) + on;
-    int pb = cta_excl(sb, wsum, tb) + ob;
-    int pa = cta_excl(sa, wsum, ta) + oa;
+    v[0] += cn[r];
+    v[1] += cb[r];
+  }
+  // offsets of the warps: a CTA scan of the warp totals (held by lane 0)
+  int tot[3];
 #pragma unroll
-    for (int r = 0; r < SCAN_ITEMS; ++r) {
-      const int e = e0 + r;
+  for (int k = 0; k < 3; ++k) {
+    v[k] = __reduce_add_sync(0xffffffffu, v[k]);
+    if (lane) v[k] = 0;
+  }
+  cta_excl3(v, wsum3, tot);
+  int on = __shfl_sync(0xffffffffu, v[0], 0);
+  int ob = __shfl_sync(0xffffffffu, v[1], 0);
+  int oa = __shfl_sync(0xffffffffu, v[2], 0);
+  const unsigned lt_mask = (1u << lane) - 1u;
+#pragma unroll
+  for (int r = 0; r < SCAN1_K; ++r) {
+    if (r < K) {  // warp-uniform
+      const int e = seg0 + r * 32 + lane;
+      const int in_n = warp_incl(cn[r]), in_b = warp_incl(cb[r]);
+      const bool act = e < I.ntiles && cn[r] > 0;
+      const unsigned am = __ballot_sync(0xffffffffu, act);
       if (e < m) {
+        const int pn = on + in_n - cn[r];
         I.new_start[e] = pn;
-        I.s.bucket_start[e] = pb;
-        if (ca[r]) I.s.active[pa] = make_int4(e, pn, pn + cn[r], 0);
+        I.s.bucket_start[e] = ob + in_b - cb[r];
+        if (act) I.s.active[oa + __popc(am & lt_mask)] = make_int4(e, pn, pn + cn[r], 0);
         I.s.in_cnt[e] = 0;
         I.s.out_cnt[e] = 0;
         I.s.bucket_fill[e] = 0;
       }
-      pn += cn[r];
-      pb += cb[r];
-      pa += ca[r];
+      on += __shfl_sync(0xffffffffu, in_n, 31);
+      ob += __shfl_sync(0xffffffffu, in_b, 31);
+      oa += __popc(am);
     }
-    on += tn;
-    ob += tb;
-    oa += ta;
   }
+  const int ob_all = tot[1], oa_all = tot[2];
   __syncthreads();  // new_start of the dead range is written
   if (threadIdx.x == 0) {
     I.s.ctr[C_MOVERS_SNAP] = I.s.ctr[C_MOVERS];
     I.s.ctr[C_MOVERS] = 0;
     I.new_start[m] = (int32_t)I.n;
-    I.s.bucket_start[m] = ob;
+    I.s.bucket_start[m] = ob_all;
     const int dead_start = I.new_start[I.ntiles];
-    I.s.ctr[C_ACTIVE] = oa;
+    I.s.ctr[C_ACTIVE] = oa_all;
     I.s.ctr[C_DEAD_START] = dead_start;
-    I.s.ctr[C_BIN_ITEMS] = oa + ((int64_t)dead_start < I.n ? 1 : 0);
-    __threadfence();
-    s_last = atomicAdd(&G.work[W_SCAN_DONE], 1) == G.ninst - 1;
+    const int bin_items = oa_all + ((int64_t)dead_start < I.n ? 1 : 0);
+    I.s.ctr[C_BIN_ITEMS] = bin_items;
+    if (ONE) {  // the group's prefixes are this instance's counts
+      G.bin_items[0] = 0;
+      G.bin_items[1] = bin_items;
+      G.act_items[0] = 0;
+      G.act_items[1] = oa_all;
+    } else {
+      __threadfence();
+      s_last = atomicAdd(&G.work[W_SCAN_DONE], 1) == G.ninst - 1;
+    }
+  }
+  if (ONE) {
+    if (threadIdx.x < W_COUNT) G.work[threadIdx.x] = 0;
+    return;
   }
   __syncthreads();
   if (s_last) {
     __threadfence();
-    group_prefix_body(G, wsum);
+    group_prefix_body(G, wsum3[0]);
   }
 }
 
 
-__global__ void __launch_bounds__(BT) bin_tiles(GroupArgs G) {
+template <bool ONE>
+__global__ void __launch_bounds__(BT) bin_tiles(const __grid_constant__ GroupArgs G) {
   __shared__ int cnt[CELLS_PER_TILE];
   __shared__ int base[CELLS_PER_TILE];
   __shared__ int running[CELLS_PER_TILE];
@@ -408,14 +473,14 @@ __global__ void __launch_bounds__(BT) bin_tiles(GroupArgs G) {
     // the next work item is fetched now and published at the end of this one
     int wnext = 0;
     if (tid == 0) wnext = atomicAdd(&G.work[W_BIN], 1);
-    const int ii = find_inst(G.bin_items, G.ninst, w);
-    if (ii != loaded) {  // uniform
+    const int ii = ONE ? 0 : find_inst(G.bin_items, G.ninst, w);
+    if (!ONE && ii != loaded) {  // uniform
       copy_inst(G.inst, ii, &sI);
       loaded = ii;
       __syncthreads();
     }
-    const InstArgs &I = sI;
-    const int local = w - G.bin_items[ii];
+    const InstArgs &I = inst_ref<ONE>(G, sI);
+    const int local = ONE ? w : w - G.bin_items[ii];
     const int ntiles = I.ntiles;
     const int t = (local < I.s.ctr[C_ACTIVE]) ? I.s.active[local].x : ntiles;
     const int os = I.old_start[t], oe = I.old_start[t + 1];
@@ -553,6 +618,15 @@ __global__ void permute_k(int64_t n, PBuf A, PBuf B, const int32_t *__restrict__
   }
 }
 
+template <bool ONE>
+cudaError_t bin_launch(const GroupArgs &G, cudaStream_t st) {
+  cudaError_t e = G.scan_one ? launch_dep(bin_scan_one<ONE>, G.ninst, SCAN1_T, 0, st, G)
+                             : launch_dep(bin_scan_lb<ONE>, G.nblk_s, SCAN_T, 0, st, G);
+  if (e == cudaSuccess) e = launch_dep(bin_bucket<ONE>, G.nblk_m, 256, 0, st, G);
+  if (e == cudaSuccess) e = launch_dep(bin_tiles<ONE>, G.grid, BT, 0, st, G);
+  return e;
+}
+
 }  // namespace
 
 cudaError_t count_movers(const GroupArgs &G, cudaStream_t st) {
@@ -564,11 +638,7 @@ cudaError_t count_movers(const GroupArgs &G, cudaStream_t st) {
 cudaError_t bin_group(int dim, const GroupArgs &G, cudaStream_t st) {
   (void)dim;
   if (G.ninst <= 0 || G.nblk_p <= 0) return cudaSuccess;
-  cudaError_t e = G.scan_one ? launch_dep(bin_scan_one, G.ninst, SCAN1_T, 0, st, G)
-                             : launch_dep(bin_scan_lb, G.nblk_s, SCAN_T, 0, st, G);
-  if (e == cudaSuccess) e = launch_dep(bin_bucket, G.nblk_m, 256, 0, st, G);
-  if (e == cudaSuccess) e = launch_dep(bin_tiles, G.grid, BT, 0, st, G);
-  return e;
+  return G.ninst == 1 ? bin_launch<true>(G, st) : bin_launch<false>(G, st);
 }
 
 cudaError_t permute_state(int dim, int64_t n, const PBuf &A, const PBuf &B, const int32_t *perm, cudaStream_t st) {

@@ -179,8 +179,8 @@ __device__ __forceinline__ void copy_inst(const InstArgs *tab, int ii, InstArgs 
 }
 
 // Largest tile count (plus the dead range) scanned by one CTA per instance;
-// larger instances take the two-pass scan over many CTAs.
-constexpr int SCAN1_MAX = 4096;
+// larger instances take the look-back scan over many CTAs.
+constexpr int SCAN1_MAX = 16384;
 
 // Per-group launch description.  The prefix arrays map a block (or a work
 // item) to its instance: entry i is the first block (item) of instance i and

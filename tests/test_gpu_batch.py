@@ -57,6 +57,30 @@ def test_batch_results_equal_alone_runs():
             s.close()
 
 
+def test_batch_with_a_mesh_past_the_one_cta_scan():
+    # a 16,640-tile mesh sends its whole group through the look-back tile
+    # scan over many CTAs; the small mesh beside it must not notice
+    wls = [W.column3d(ncells=(260, 64, 64), col_cells=(12, 12, 12), name="column3d_16640_tiles"),
+           H.small_column()]
+    steps = 30
+    sims = [mpm.Simulation(w) for w in wls]
+    b = mpm.mpm_batch_create()
+    try:
+        for s in sims:
+            mpm.mpm_batch_admit(b, s.h)
+        mpm.mpm_batch_step(b, steps)
+        assert mpm.mpm_batch_poll(b, len(wls)) == [mpm.MPM_OK] * len(wls)
+        for wl, s in zip(wls, sims):
+            snap, st = s.read()
+            assert st == mpm.MPM_OK
+            ref, _ = alone(wl, steps)
+            assert equal(snap, ref), wl.name
+    finally:
+        mpm.mpm_batch_destroy(b)
+        for s in sims:
+            s.close()
+
+
 def test_admission_and_eviction_mid_run():
     wls = mix()[:4]
     sims = [mpm.Simulation(w) for w in wls]

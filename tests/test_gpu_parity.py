@@ -129,11 +129,16 @@ def test_full_column_per_step_parity():
     assert H.cell_mismatch_in_band(g61, r61, wl.h, 1e-4)[1] == 0
 
 
-@pytest.mark.parametrize("mesh", ["small", "wide"])
+WIDE_MESH = {"wide": (120, 48, 48), "wider": (260, 64, 64)}
+
+
+@pytest.mark.parametrize("mesh", ["small", "wide", "wider"])
 def test_binning_is_the_stable_sort_of_the_keys(mesh):
-    # small: 240 tiles (the one-CTA tile scan); wide: 4320 tiles (the
-    # two-pass scan over many CTAs)
-    wl = H.small_column() if mesh == "small" else W.column3d(ncells=(120, 48, 48), col_cells=(12, 12, 12))
+    # small: 240 tiles (the one-CTA tile scan, one tile per thread); wide:
+    # 4320 tiles (one-CTA scan, five tiles per thread, the last thread's run
+    # ragged); wider: 16,640 tiles, past the one-CTA scan's 16,384 (the
+    # look-back scan over many CTAs)
+    wl = H.small_column() if mesh == "small" else W.column3d(ncells=WIDE_MESH[mesh], col_cells=(12, 12, 12))
     with mpm.Simulation(wl) as sim:
         sim.step(37)
         key, perm, td = sim.binning()
