@@ -273,6 +273,10 @@ cudaError_t build_group(GroupDev &g, const std::vector<mpm_ctx *> &mem, bool rel
     int max_m = 0;
     for (int i = 0; i < n; ++i) max_m = std::max(max_m, mem[i]->geo.ntiles + 1);
     G.scan_one = max_m <= SCAN1_MAX ? 1 : 0;
+    // the apex band of the FP32 return is empty without cohesion
+    G.apex = 0;
+    for (int i = 0; i < n; ++i)
+      if (mem[i]->mat.model == MPM_MOHR_COULOMB && (mem[i]->has_coh || (float)mem[i]->mat.c != 0.f)) G.apex = 1;
     if (n == 1)
       G.one = tab[p][0];
     else

@@ -296,6 +296,7 @@ __global__ void __launch_bounds__(SCAN_T) bin_scan_lb(const __grid_constant__ Gr
   if (threadIdx.x == 0 && c == 0) {
     I.s.ctr[C_MOVERS_SNAP] = I.s.ctr[C_MOVERS];
     I.s.ctr[C_MOVERS] = 0;
+    I.s.ctr[C_APEX] = 0;
   }
   __syncthreads();  // new_start of the dead range is written (last chunk)
   if (threadIdx.x == 0) {
@@ -417,6 +418,7 @@ __global__ void __launch_bounds__(SCAN1_T) bin_scan_one(const __grid_constant__ 
   if (threadIdx.x == 0) {
     I.s.ctr[C_MOVERS_SNAP] = I.s.ctr[C_MOVERS];
     I.s.ctr[C_MOVERS] = 0;
+    I.s.ctr[C_APEX] = 0;
     I.new_start[m] = (int32_t)I.n;
     I.s.bucket_start[m] = ob_all;
     const int dead_start = I.new_start[I.ntiles];

@@ -498,7 +498,7 @@ __device__ __forceinline__ void elastic_trial(const MatConst<T> &m, const T sig[
 // seven digits to cancellation.  The band is relative only: with c = 0 the
 // apex is the zero stress and FP32 loses nothing near it.
 __device__ __forceinline__ bool near_apex(const float st[6], const MatConst<float> &m, float c) {
-  if (!(m.sphi > 0.f)) return false;
+  if (!(m.sphi > 0.f) || c == 0.f) return false;  // c = 0: |sigma|^2 >= 3 p^2, the band is empty
   const float pa = c * m.cphi / m.sphi;
   const float p = (st[0] + st[1] + st[2]) * (1.f / 3.f);
   const float d0 = st[0] - pa, d1 = st[1] - pa, d2 = st[2] - pa;
@@ -508,7 +508,8 @@ __device__ __forceinline__ bool near_apex(const float st[6], const MatConst<floa
 }
 
 // The FP64 return near the apex, kept out of line: it is rare, and inlining
-// it would raise the register count of every kernel that updates stresses.
+// it would raise the register count of the kernel that calls it.  (The step
+// runs it in a kernel of its own over the particles G2P queued.)
 static __device__ __noinline__ void mc_return_apex_band(const MatConst<double> &md, float c, const float st[6], float out[6],
                                                  float &epsp) {
   double sd[6], od[6], dd;
@@ -520,38 +521,33 @@ static __device__ __noinline__ void mc_return_apex_band(const MatConst<double> &
   epsp += (float)dd;
 }
 
-// The Mohr-Coulomb return of a trial that the trigonometry-free bound could
-// not clear, kept out of line: the common elastic case then does not carry
-// its registers.  Writes sig (returned stress) and adds to epsp.
-static __device__ __noinline__ void mc_update_f32(const MatConst<float> &m, const MatConst<double> &md, float c,
-                                                  const float st[6], float sig[6], float &epsp) {
-  if (clearly_elastic(m, c, st)) {
-#pragma unroll
-    for (int i = 0; i < 6; ++i) sig[i] = st[i];
-    return;
-  }
-  if (near_apex(st, m, c)) {
-    mc_return_apex_band(md, c, st, sig, epsp);
-  } else {
-    float d;
-    mc_return<float>(m, c, st, sig, d);
-    epsp += d;
-  }
-}
-
-// Full material update of one particle: sigma <- return(sigma + D:de).
-// FP32 path: FP32 arithmetic except the Mohr-Coulomb return inside the apex
-// band, which runs in FP64.  FP64 path: everything in FP64.
-__device__ __forceinline__ void material_update(const MatConst<float> &m, const MatConst<double> &md,
-                                                float c, float sig[6], const float de[6], float &epsp) {
+// FP32 material update of one particle, sigma <- return(sigma + D:de), all
+// in line (no call: a call site makes the caller save its live registers to
+// the stack and constrains register allocation around it).  Returns true,
+// with sig = the trial stress and epsp unchanged, for a trial inside the apex
+// band: the caller completes it with mc_return_apex_band (FP64).
+__device__ __forceinline__ bool material_update_inline(const MatConst<float> &m, float c, float sig[6],
+                                                       const float de[6], float &epsp) {
   float st[6];
   elastic_trial<float>(m, sig, de, st);
-  if (m.model != 1 || bounded_elastic(m, c, st)) {
 #pragma unroll
-    for (int i = 0; i < 6; ++i) sig[i] = st[i];
-    return;
+  for (int i = 0; i < 6; ++i) sig[i] = st[i];
+  if (m.model != 1 || bounded_elastic(m, c, st) || clearly_elastic(m, c, st)) return false;
+  if (near_apex(st, m, c)) return true;
+  float d;
+  mc_return<float>(m, c, st, sig, d);
+  epsp += d;
+  return false;
+}
+
+// Full FP32 material update: FP32 arithmetic except the Mohr-Coulomb return
+// inside the apex band, which runs in FP64.  The FP64 path: everything in FP64.
+__device__ __forceinline__ void material_update(const MatConst<float> &m, const MatConst<double> &md,
+                                                float c, float sig[6], const float de[6], float &epsp) {
+  if (material_update_inline(m, c, sig, de, epsp)) {
+    const float st[6] = {sig[0], sig[1], sig[2], sig[3], sig[4], sig[5]};
+    mc_return_apex_band(md, c, st, sig, epsp);
   }
-  mc_update_f32(m, md, c, st, sig, epsp);
 }
 
 __device__ __forceinline__ void material_update(const MatConst<double> &m, double c, double sig[6],

@@ -105,6 +105,40 @@ __device__ __forceinline__ void corner_shape(int a, const float w0[D], const flo
   }
 }
 
+// Shape values and gradients of the corners a P2G thread owns, at offset u.
+// The corners share their x and y bits (bits 0 and 1 of cp; sx, sy = +1 for
+// the upper node of the cell along that axis) and, in 3D, are the lower (r =
+// 0) and the upper (r = 1) node along z.  ThreadCorners holds the factors
+// they share; corner(r) forms the products of corner_shape in the same order,
+// so the values are identical to it.
+template <int D>
+struct ThreadCorners {
+  float wxy, gx, gy, gz, wz[2];
+  __device__ __forceinline__ ThreadCorners(const float *u, int cp, float inv_h) {
+    const bool ux = cp & 1, uy = cp & 2;  // upper node along x, y (predicates, loop-invariant)
+    const float wx = ux ? 0.5f + u[0] : 0.5f - u[0], wy = uy ? 0.5f + u[1] : 0.5f - u[1];
+    wxy = wx * wy;
+    const float tx = inv_h * wy, ty = inv_h * wx;  // (-a) b = -(a b) exactly
+    gx = ux ? tx : -tx;
+    gy = uy ? ty : -ty;
+    gz = D == 3 ? ty * wy : 0.f;
+    wz[0] = D == 3 ? 0.5f - u[D - 1] : 1.f;
+    wz[1] = D == 3 ? 0.5f + u[D - 1] : 1.f;
+  }
+  __device__ __forceinline__ void corner(int r, float &N, float G[D]) const {
+    if constexpr (D == 2) {
+      N = wxy;
+      G[0] = gx;
+      G[1] = gy;
+    } else {
+      N = wxy * wz[r];
+      G[0] = gx * wz[r];
+      G[1] = gy * wz[r];
+      G[2] = r ? gz : -gz;
+    }
+  }
+};
+
 // ---------------------------------------------------------------------------
 // P2G: one CTA per tile; each thread owns CPT corners of one cell (3D: two
 // corners, 256 threads; 2D: one corner, 256 threads).  The tile's particles
@@ -193,7 +227,7 @@ __global__ void __launch_bounds__(P2GRec<D, MODE>::CH, MPM_P2G_MINB)
     float *slots_out = MODE == P2G_FORCE ? I.s.slots2 : I.s.slots1;
     const int4 ar = I.s.active[ONE ? wi : wi - G.act_items[ii]];
     const int t = ar.x, s = ar.y, e = ar.z;
-    float w0[D], w1[D], acc[CPT][NCH];
+    float acc[CPT][NCH];
 #pragma unroll
     for (int r = 0; r < CPT; ++r)
 #pragma unroll
@@ -260,14 +294,12 @@ __global__ void __launch_bounds__(P2GRec<D, MODE>::CH, MPM_P2G_MINB)
             f[4 * k + 2] = rv.z;
             f[4 * k + 3] = rv.w;
           }
-          float u[D];
-#pragma unroll
-          for (int k = 0; k < D; ++k) u[k] = f[k];
-          corner_weights<D>(u, w0, w1);
+          static_assert(CPT == (D == 3 ? 2 : 1) && CPC == 4, "corners my_cp + 4 r: z bit = r");
+          const ThreadCorners<D> tc(f, my_cp, g.inv_h);
 #pragma unroll
           for (int r = 0; r < CPT; ++r) {
             float N, Gr[D];
-            corner_shape<D>(my_cp + r * CPC, w0, w1, g.inv_h, N, Gr);
+            tc.corner(r, N, Gr);
             if (HAS_M) {
               acc[r][0] = fmaf(f[D], N, acc[r][0]);
 #pragma unroll
@@ -767,7 +799,9 @@ __global__ void __launch_bounds__(G2P_T, MPM_G2P_MINB) g2p(const __grid_constant
     // V = V0 (1 + jm1):  (1 + jm1)(1 + tr) - 1 = jm1 + tr + jm1 tr
     const float tr = de[0] + de[1] + de[2];
     I.B.jm1()[q] = jm1 + (tr + jm1 * tr);
-    material_update(I.mat, I.matd, coh, sg, de, epsp);
+    // a trial in the apex band keeps its trial stress here and is queued for
+    // the FP64 return (apex_band_k, right after this kernel)
+    if (material_update_inline(I.mat, coh, sg, de, epsp)) I.s.bucket_sorted[atomicAdd(&I.s.ctr[C_APEX], 1)] = (int32_t)q;
 #pragma unroll
     for (int i = 0; i < NS; ++i) {
       I.B.sig(i)[q] = sg[i];
@@ -776,6 +810,39 @@ __global__ void __launch_bounds__(G2P_T, MPM_G2P_MINB) g2p(const __grid_constant
     I.B.epsp()[q] = epsp;
   }
   if (status) atomicOr(&I.s.ctr[C_STATUS], status);
+}
+
+// FP64 apex-band returns of the particles G2P queued (rare: trials within
+// 1e-3 (|p| + c cot phi) of the apex, cohesive materials only).  G2P stored
+// their trial stress; this completes it in place and adds the plastic strain
+// increment.  Every CTA walks every instance's queue with a grid stride.
+constexpr int APEX_T = 128;
+template <int D, bool ONE>
+__global__ void __launch_bounds__(APEX_T) apex_band_k(const __grid_constant__ GroupArgs G) {
+  constexpr int NS = nstress<D>();
+  pdl_trigger();
+  pdl_wait();
+  for (int ii = 0; ii < G.ninst; ++ii) {
+    const InstArgs &I = ONE ? G.one : G.inst[ii];
+    const int cnt = I.s.ctr[C_APEX];
+    for (int e = blockIdx.x * APEX_T + threadIdx.x; e < cnt; e += gridDim.x * APEX_T) {
+      const int q = I.s.bucket_sorted[e];
+      const float c = I.A.coh() ? I.A.coh()[I.perm_out[q]] : I.mat.c;
+      float st[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, out[6];
+#pragma unroll
+      for (int i = 0; i < NS; ++i) st[i] = I.B.sig(i)[q];
+      float epsp = I.B.epsp()[q];
+      mc_return_apex_band(I.matd, c, st, out, epsp);
+      int status = 0;
+#pragma unroll
+      for (int i = 0; i < NS; ++i) {
+        I.B.sig(i)[q] = out[i];
+        if (!isfinite(out[i])) status |= ST_NONFINITE;
+      }
+      I.B.epsp()[q] = epsp;
+      if (status) atomicOr(&I.s.ctr[C_STATUS], status);
+    }
+  }
 }
 
 template <int D, int MODE>
@@ -802,8 +869,12 @@ cudaError_t launch_node(const GroupArgs &G, int work_slot, cudaStream_t st) {
 
 template <int D, int GMODE>
 cudaError_t launch_g2p(const GroupArgs &G, cudaStream_t st) {
-  return G.ninst == 1 ? launch_dep(g2p<D, GMODE, true>, G.nblk_p * G2P_SUB, G2P_T, 0, st, G)
-                      : launch_dep(g2p<D, GMODE, false>, G.nblk_p * G2P_SUB, G2P_T, 0, st, G);
+  const int nb = G.nblk_p * G2P_SUB;
+  cudaError_t e = G.ninst == 1 ? launch_dep(g2p<D, GMODE, true>, nb, G2P_T, 0, st, G)
+                               : launch_dep(g2p<D, GMODE, false>, nb, G2P_T, 0, st, G);
+  if (e != cudaSuccess || !G.apex || GMODE == G2P_USF_ADVECT) return e;
+  return G.ninst == 1 ? launch_dep(apex_band_k<D, true>, G.grid / 8, APEX_T, 0, st, G)
+                      : launch_dep(apex_band_k<D, false>, G.grid / 8, APEX_T, 0, st, G);
 }
 
 template <int D>

@@ -112,6 +112,7 @@ enum {
   C_STATUS = 8,     // sticky device status bits (ST_*)
   C_BIN_ITEMS = 9,  // active tiles + 1 if the dead range is non-empty
   C_DEAD_START = 10,
+  C_APEX = 11,      // particles queued by G2P for the FP64 apex-band return (in StepBufs::bucket_sorted)
   C_NCTR = 16
 };
 
@@ -126,7 +127,7 @@ struct StepBufs {
   int32_t *bucket_fill;    // ntiles + 1
   int32_t *movers;         // n: storage slots of tile movers
   int32_t *bucket;         // n: movers grouped by destination tile
-  int32_t *bucket_sorted;  // n: scratch for large buckets
+  int32_t *bucket_sorted;  // n: scratch for large buckets (binning), then the apex-band queue (G2P)
   int4 *active;            // ntiles: active tiles in ascending order, (tile, new start, new end, -)
   int32_t *scan_tot;       // 8 per chunk of the tile scan (look-back flag, totals, prefix)
   int32_t *ctr;            // C_NCTR counters
@@ -198,6 +199,7 @@ struct GroupArgs {
   int nblk_p, nblk_s, nblk_m;
   int scan_one;             // every instance has at most SCAN1_MAX tiles: one-CTA scans
   int grid;                 // CTAs of the per-tile kernels
+  int apex;                 // some instance can reach the FP64 apex band (cohesion > 0): run apex_band_k
   InstArgs one;             // a group of one: its table entry (inst[0]) by value
 };
 

@@ -337,7 +337,8 @@ def mpm_material_update(mat: mpm_material, precision: int, sig, deps, cohesion=N
 class Simulation:
     """One mesh handle built from a workload description (see workloads.py)."""
 
-    def __init__(self, wl, precision=None, scheme=None, stream=None, mass_tol=1e-12):
+    def __init__(self, wl, precision=None, scheme=None, stream=None, mass_tol=1e-12, stress0=None):
+        """stress0: optional (n, 6) initial stresses (Voigt xx yy zz xy yz xz; zeros if None)."""
         self.wl = wl
         self.dim = wl.dim
         self.precision = wl.precision if precision is None else precision
@@ -350,7 +351,7 @@ class Simulation:
         self.h = mpm_create_mesh(self.desc)
         try:
             if wl.n:
-                mpm_add_particles(self.h, wl.pos, wl.vel, wl.vol, self.mat, wl.coh)
+                mpm_add_particles(self.h, wl.pos, wl.vel, wl.vol, self.mat, wl.coh, stress0)
         except Exception:
             mpm_destroy(self.h)
             raise

@@ -6,6 +6,7 @@ Bars: cells and binning bit-exact; FP64 GPU within 1e-9 relative L2 of the
 oracle; FP32 mixed within 1e-5 per step from an identical state and 1e-3
 after a run (tests/helpers.py).
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -174,6 +175,41 @@ def test_sort_keys_primitive(n, bits):
     torch.cuda.synchronize()
     got = dp[:n].cpu().numpy()
     assert np.array_equal(got, np.argsort(keys, kind="stable").astype(np.int32))
+
+
+def test_apex_band_returns_inside_a_step():
+    # A cohesive block in hydrostatic tension just past the apex c cot(phi),
+    # with a small deviator and tiny strain increments: every trial of the
+    # step lies in the apex band, so G2P queues it and the FP64 apex-band
+    # kernel completes it.  One step from the same state as the oracle.
+    c, phi = 10e3, math.radians(30.0)
+    pa = c / math.tan(phi)
+    base = H.small_column()
+    rng = np.random.default_rng(23)
+    n = base.n
+    wl = dataclasses.replace(base, name="cohesive_block_at_apex", gravity=(0.0, 0.0, 0.0),
+                             face_bc=(W.FREE,) * 6, face_mu=(0.0,) * 6,
+                             material=dict(base.material, c=c), vel=rng.normal(0.0, 2e-5, (n, 3)))
+    s0 = np.zeros((n, 6))
+    s0[:, :3] = pa * (1.0 + 2e-4)
+    s0 += rng.normal(0.0, 1e-5 * pa, (n, 6))
+    with mpm.Simulation(wl, stress0=s0) as sim:
+        g0, _ = sim.read()
+        sim.step(1)
+        g1, st = sim.read()
+    assert st == mpm.MPM_OK
+    o = H.oracle_from_gpu(wl, g0)
+    assert o.step(1) == oracle.OK
+    r1 = H.oracle_snapshot(o, 3)
+    err = H.compare(g1, r1, g0, 3)
+    assert H.worst(err, H.STATE_KEYS) <= H.TOL_STEP_FP32, err
+    # most trials went back to the apex region, so the band was exercised
+    # (particles near the free faces, where the tension is unbalanced, strain
+    # more and leave it)
+    apex = np.array([pa, pa, pa, 0.0, 0.0, 0.0])
+    at_apex = np.linalg.norm(r1["stress"] - apex, axis=1) < 2e-3 * pa
+    assert at_apex.mean() > 0.4
+    assert (g1["epsp"][at_apex] > g0["epsp"][at_apex]).all()
 
 
 def _trials(rng, n, scale, c):
