@@ -337,7 +337,7 @@ void free_t(T *&p) {
 int64_t f32_fixed_bytes(const mpm_mesh_desc &d, int64_t nt, int64_t nn) {
   const int bn = d.dim == 3 ? box_nodes<3>() : box_nodes<2>();
   int64_t b = 4 * nt * bn * (1 + 2 * d.dim) + (d.scheme == MPM_USF ? 4 * nt * bn * d.dim : 0);
-  b += 6 * 4 * (nt + 2) + 16 * (nt + 2) + 16 * nn * (d.dim == 3 ? 2 : 1) + 4096;
+  b += 6 * 4 * (nt + 2) + 2 * 16 * (nt + 2) + 16 * nn * (d.dim == 3 ? 2 : 1) + 4096;
   return b;
 }
 
@@ -425,6 +425,7 @@ mpm_status mpm_create_mesh(const mpm_mesh_desc *desc, mpm_handle *out) {
     if (e == cudaSuccess) e = cudaMalloc(&S.bucket_start, ti);
     if (e == cudaSuccess) e = cudaMalloc(&S.bucket_fill, ti);
     if (e == cudaSuccess) e = cudaMalloc(&S.active, sizeof(int4) * (nt + 2));
+    if (e == cudaSuccess) e = cudaMalloc(&S.bin_rec, sizeof(int4) * (nt + 2));
     const size_t stb = sizeof(int32_t) * 8 * ((nt + 1) / 1024 + 2);
     if (e == cudaSuccess) e = cudaMalloc(&S.scan_tot, stb);
     if (e == cudaSuccess) e = cudaMemset(S.scan_tot, 0, stb);
@@ -934,7 +935,7 @@ mpm_status mpm_destroy(mpm_handle h) {
   StepBufs &S = h->s;
   void *ptrs[] = {h->bufmem[0], h->bufmem[1], S.keys_sorted, S.perm, S.tile_start[0], S.tile_start[1], S.in_cnt,
                   S.out_cnt, S.bucket_start, S.bucket_fill, S.movers, S.bucket, S.bucket_sorted, S.active,
-                  S.scan_tot, S.ctr, S.slots1, S.slots2, S.node, h->keys2, h->perm2, h->sort_scratch,
+                  S.bin_rec, S.scan_tot, S.ctr, S.slots1, S.slots2, S.node, h->keys2, h->perm2, h->sort_scratch,
                   h->pmem64, h->nmem64, h->d_status, h->d_cons};
   for (void *p : ptrs)
     if (p) cudaFree(p);

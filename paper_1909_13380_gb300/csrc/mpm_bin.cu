@@ -46,7 +46,7 @@ constexpr int SCAN_T = 256;
 constexpr int SCAN_ITEMS = 4;
 constexpr int SCAN_CHUNK = SCAN_T * SCAN_ITEMS;  // tiles per scan block
 constexpr int SCAN1_T = 1024;                    // one-CTA scan: threads
-constexpr int SCAN1_K = 16;                      // one-CTA scan: tiles per thread at most
+constexpr int SCAN1_K = MPM_SCAN1_K;             // one-CTA scan: tiles per thread at most
 static_assert(SCAN1_T * SCAN1_K == SCAN1_MAX, "the one-CTA scan covers SCAN1_MAX tiles");
 
 // Instance of item x: the largest i with prefix[i] <= x (prefix[0] = 0).
@@ -186,7 +186,7 @@ __device__ __forceinline__ int ld_volatile(const int32_t *p) { return *(const vo
 
 template <bool ONE>
 __global__ void __launch_bounds__(SCAN_T) bin_scan_lb(const __grid_constant__ GroupArgs G) {
-  __shared__ int wsum[32];
+  __shared__ int wsum3[3][32];
   __shared__ int s_ticket, s_last;
   __shared__ int s_excl[3];
   __shared__ InstArgs sI;
@@ -217,10 +217,10 @@ __global__ void __launch_bounds__(SCAN_T) bin_scan_lb(const __grid_constant__ Gr
     sb += cb[r];
     sa += ca[r];
   }
-  int tn, tb, ta;
-  int pn = cta_excl(sn, wsum, tn);
-  int pb = cta_excl(sb, wsum, tb);
-  int pa = cta_excl(sa, wsum, ta);
+  int pv[3] = {sn, sb, sa}, tot3[3];
+  cta_excl3(pv, wsum3, tot3);
+  int pn = pv[0], pb = pv[1], pa = pv[2];
+  const int tn = tot3[0], tb = tot3[1], ta = tot3[2];
   if (threadIdx.x < 32) {  // warp 0: publish, look back 32 chunks at a time, publish the prefix
     const int lane = threadIdx.x;
     int32_t *me = st + 8 * c;
@@ -284,7 +284,10 @@ __global__ void __launch_bounds__(SCAN_T) bin_scan_lb(const __grid_constant__ Gr
     if (e < m) {
       I.new_start[e] = pn;
       I.s.bucket_start[e] = pb;
-      if (ca[r]) I.s.active[pa] = make_int4(e, pn, pn + cn[r], 0);
+      if (ca[r] || (e == I.ntiles && cn[r] > 0)) {  // a binning item (the dead range comes last)
+        I.s.active[pa] = make_int4(e, pn, pn + cn[r], 0);
+        I.s.bin_rec[pa] = make_int4(I.old_start[e], I.old_start[e + 1], pb, pb + cb[r]);
+      }
       I.s.in_cnt[e] = 0;
       I.s.out_cnt[e] = 0;
       I.s.bucket_fill[e] = 0;
@@ -319,7 +322,7 @@ __global__ void __launch_bounds__(SCAN_T) bin_scan_lb(const __grid_constant__ Gr
       int32_t *sti = G.inst[ii].s.scan_tot;
       for (int k = threadIdx.x; k < G.sblk[ii + 1] - G.sblk[ii]; k += blockDim.x) sti[8 * k] = 0;
     }
-    group_prefix_body(G, wsum);
+    group_prefix_body(G, wsum3[0]);
   }
 }
 
@@ -400,10 +403,14 @@ __global__ void __launch_bounds__(SCAN1_T) bin_scan_one(const __grid_constant__ 
       const bool act = e < I.ntiles && cn[r] > 0;
       const unsigned am = __ballot_sync(0xffffffffu, act);
       if (e < m) {
-        const int pn = on + in_n - cn[r];
+        const int pn = on + in_n - cn[r], pb = ob + in_b - cb[r];
         I.new_start[e] = pn;
-        I.s.bucket_start[e] = ob + in_b - cb[r];
-        if (act) I.s.active[oa + __popc(am & lt_mask)] = make_int4(e, pn, pn + cn[r], 0);
+        I.s.bucket_start[e] = pb;
+        if (act || (e == I.ntiles && cn[r] > 0)) {  // a binning item (the dead range comes last)
+          const int k = oa + __popc(am & lt_mask);
+          I.s.active[k] = make_int4(e, pn, pn + cn[r], 0);
+          I.s.bin_rec[k] = make_int4(I.old_start[e], I.old_start[e + 1], pb, pb + cb[r]);
+        }
         I.s.in_cnt[e] = 0;
         I.s.out_cnt[e] = 0;
         I.s.bucket_fill[e] = 0;
@@ -464,9 +471,10 @@ __global__ void __launch_bounds__(BT) bin_tiles(const __grid_constant__ GroupArg
   pdl_trigger();
   for (int k = tid; k < BT_WARPS * (CELLS_PER_TILE + 1); k += BT) (&wcnt[0][0])[k] = 0;
   pdl_wait();
-  if (tid == 0) s_work[0] = atomicAdd(&G.work[W_BIN], 1);
-  __syncthreads();
+  // items: first the CTA's own (blockIdx.x), then gridDim.x + the work counter
   const int total = G.bin_items[G.ninst];
+  if (tid == 0) s_work[0] = blockIdx.x;
+  __syncthreads();
   int loaded = -1;
 
   for (int it = 0;; ++it) {
@@ -474,7 +482,7 @@ __global__ void __launch_bounds__(BT) bin_tiles(const __grid_constant__ GroupArg
     if (w >= total) break;
     // the next work item is fetched now and published at the end of this one
     int wnext = 0;
-    if (tid == 0) wnext = atomicAdd(&G.work[W_BIN], 1);
+    if (tid == 0) wnext = (int)gridDim.x + atomicAdd(&G.work[W_BIN], 1);
     const int ii = ONE ? 0 : find_inst(G.bin_items, G.ninst, w);
     if (!ONE && ii != loaded) {  // uniform
       copy_inst(G.inst, ii, &sI);
@@ -484,11 +492,10 @@ __global__ void __launch_bounds__(BT) bin_tiles(const __grid_constant__ GroupArg
     const InstArgs &I = inst_ref<ONE>(G, sI);
     const int local = ONE ? w : w - G.bin_items[ii];
     const int ntiles = I.ntiles;
-    const int t = (local < I.s.ctr[C_ACTIVE]) ? I.s.active[local].x : ntiles;
-    const int os = I.old_start[t], oe = I.old_start[t + 1];
-    const int bs = I.s.bucket_start[t], be = I.s.bucket_start[t + 1];
+    const int4 item = I.s.active[local], rec = I.s.bin_rec[local];  // one round of loads
+    const int t = item.x, ns = item.y;
+    const int os = rec.x, oe = rec.y, bs = rec.z, be = rec.w;
     const int nbk = be - bs;
-    const int ns = I.new_start[t];
     const uint32_t *knew = I.A.key();
 
     // arrivals sorted by storage position (positions are distinct)

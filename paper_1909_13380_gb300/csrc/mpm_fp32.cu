@@ -205,17 +205,18 @@ __global__ void __launch_bounds__(P2GRec<D, MODE>::CH, MPM_P2G_MINB)
   pdl_trigger();
   if (tid < CELLS_PER_TILE) stamp[tid] = -1;
   pdl_wait();
-  if (tid == 0) s_work[0] = atomicAdd(&G.work[work_slot], 1);
+  // items: first the CTA's own (blockIdx.x), then gridDim.x + the work counter
+  const int total = G.act_items[G.ninst];
+  if (tid == 0) s_work[0] = blockIdx.x;
   __syncthreads();
   int chunk_id = 0, loaded = -1;
-  const int total = G.act_items[G.ninst];
 
   for (int it = 0;; ++it) {
     const int wi = s_work[it & 1];
     if (wi >= total) break;
     // the next work item is fetched now and published at the end of this one
     int wnext = 0;
-    if (tid == 0) wnext = atomicAdd(&G.work[work_slot], 1);
+    if (tid == 0) wnext = (int)gridDim.x + atomicAdd(&G.work[work_slot], 1);
     const int ii = ONE ? 0 : find_inst(G.act_items, G.ninst, wi);
     if (!ONE && ii != loaded) {  // uniform
       copy_inst(G.inst, ii, &sI);

@@ -128,7 +128,9 @@ struct StepBufs {
   int32_t *movers;         // n: storage slots of tile movers
   int32_t *bucket;         // n: movers grouped by destination tile
   int32_t *bucket_sorted;  // n: scratch for large buckets (binning), then the apex-band queue (G2P)
-  int4 *active;            // ntiles: active tiles in ascending order, (tile, new start, new end, -)
+  int4 *active;            // ntiles + 2: active tiles in ascending order, (tile, new start, new end, -),
+                           // then the dead range (tile = ntiles) when it is not empty: the binning items
+  int4 *bin_rec;           // ntiles + 2: per binning item (old start, old end, bucket start, bucket end)
   int32_t *scan_tot;       // 8 per chunk of the tile scan (look-back flag, totals, prefix)
   int32_t *ctr;            // C_NCTR counters
   float *slots1;           // ntiles * box * channels (P2G USL / MOM)
@@ -179,9 +181,13 @@ __device__ __forceinline__ void copy_inst(const InstArgs *tab, int ii, InstArgs 
   for (int i = threadIdx.x; i < (int)(sizeof(InstArgs) / 8); i += blockDim.x) d[i] = __ldg(src + i);
 }
 
-// Largest tile count (plus the dead range) scanned by one CTA per instance;
-// larger instances take the look-back scan over many CTAs.
-constexpr int SCAN1_MAX = 16384;
+// Largest tile count (plus the dead range) scanned by one CTA per instance
+// (1024 threads, at most MPM_SCAN1_K tiles each); larger instances take the
+// look-back scan over many CTAs.
+#ifndef MPM_SCAN1_K
+#define MPM_SCAN1_K 4
+#endif
+constexpr int SCAN1_MAX = 1024 * MPM_SCAN1_K;
 
 // Per-group launch description.  The prefix arrays map a block (or a work
 // item) to its instance: entry i is the first block (item) of instance i and

@@ -58,8 +58,9 @@ def test_batch_results_equal_alone_runs():
 
 
 def test_batch_with_a_mesh_past_the_one_cta_scan():
-    # a 16,640-tile mesh sends its whole group through the look-back tile
-    # scan over many CTAs; the small mesh beside it must not notice
+    # a 16,640-tile mesh (past the one-CTA scan's 4096) sends its whole group
+    # through the look-back tile scan over many CTAs; the small mesh beside
+    # it must not notice
     wls = [W.column3d(ncells=(260, 64, 64), col_cells=(12, 12, 12), name="column3d_16640_tiles"),
            H.small_column()]
     steps = 30

@@ -130,15 +130,15 @@ def test_full_column_per_step_parity():
     assert H.cell_mismatch_in_band(g61, r61, wl.h, 1e-4)[1] == 0
 
 
-WIDE_MESH = {"wide": (120, 48, 48), "wider": (260, 64, 64)}
+WIDE_MESH = {"mid": (100, 40, 48), "wide": (120, 48, 48), "wider": (260, 64, 64)}
 
 
-@pytest.mark.parametrize("mesh", ["small", "wide", "wider"])
+@pytest.mark.parametrize("mesh", ["small", "mid", "wide", "wider"])
 def test_binning_is_the_stable_sort_of_the_keys(mesh):
-    # small: 240 tiles (the one-CTA tile scan, one tile per thread); wide:
-    # 4320 tiles (one-CTA scan, five tiles per thread, the last thread's run
-    # ragged); wider: 16,640 tiles, past the one-CTA scan's 16,384 (the
-    # look-back scan over many CTAs)
+    # small: 240 tiles (the one-CTA tile scan, one tile per thread); mid:
+    # 3000 tiles (one-CTA scan, three 32-tile chunks per warp, the last warp's
+    # ragged); wide: 4320 tiles, past the one-CTA scan's 4096 (the look-back
+    # scan over five CTAs); wider: 16,640 tiles (look-back over 17 CTAs)
     wl = H.small_column() if mesh == "small" else W.column3d(ncells=WIDE_MESH[mesh], col_cells=(12, 12, 12))
     with mpm.Simulation(wl) as sim:
         sim.step(37)
