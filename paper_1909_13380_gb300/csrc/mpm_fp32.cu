@@ -453,6 +453,11 @@ __global__ void __launch_bounds__(NODE_T) node_tile(const __grid_constant__ Grou
   constexpr int NCH1 = NMODE == NODE_USL ? 1 + 2 * D : 1 + D;
   constexpr int NW = NODE_T / 32;
   constexpr int NSL = (BN + 31) / 32;  // slices per tile
+  constexpr int NOWN = CELLS_PER_TILE / 32;  // slices of the nodes at local 1..T on every axis
+  static_assert(CELLS_PER_TILE % 32 == 0, "owned-node slices");
+  // neighbourhood-mask bits of the lower neighbours (offsets in {-1, 0}^D, not all 0)
+  constexpr unsigned LOWER = D == 3 ? (1u << 0) | (1u << 1) | (1u << 3) | (1u << 4) | (1u << 9) | (1u << 10) | (1u << 12)
+                                    : (1u << 9) | (1u << 10) | (1u << 12);
   __shared__ InstArgs sI[NW];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const InstArgs &I = inst_ref<ONE>(G, sI[warp]);
@@ -492,12 +497,18 @@ __global__ void __launch_bounds__(NODE_T) node_tile(const __grid_constant__ Grou
       }
     }
     const unsigned nmask = __ballot_sync(0xffffffffu, nact);
-    for (int sl = slice0; sl < (split == 1 ? NSL : slice0 + 1); ++sl) do {  // one node per lane
+    // One warp walking a whole box whose lower neighbours are all active
+    // computes just the nodes at local 1..T on every axis: a node on a lower
+    // face (a local coordinate 0) is held by the active lower neighbour
+    // along that axis, whose index is lower.  Otherwise, and for one slice
+    // per warp, the walk is in box order with the ownership test below.
+    const bool own_only = split == 1 && (nmask & LOWER) == LOWER;  // warp-uniform
+    for (int sl = slice0; sl < (split == 1 ? (own_only ? NOWN : NSL) : slice0 + 1); ++sl) do {  // a node per lane
       const int b = sl * 32 + lane;
       if (b >= BN) break;  // break: nothing to write for this lane
-      const int bx = b % (TX + 1);
-      const int by = (b / (TX + 1)) % (TY + 1);
-      const int bz = D == 3 ? b / ((TX + 1) * (TY + 1)) : 0;
+      const int bx = own_only ? 1 + b % TX : b % (TX + 1);
+      const int by = own_only ? 1 + (b / TX) % TY : (b / (TX + 1)) % (TY + 1);
+      const int bz = D == 3 ? (own_only ? 1 + b / (TX * TY) : b / ((TX + 1) * (TY + 1))) : 0;
       const int Ig[3] = {tc[0] * TX + bx, tc[1] * TY + by, D == 3 ? tc[2] * TZ + bz : 0};
       bool inside = true;
 #pragma unroll
