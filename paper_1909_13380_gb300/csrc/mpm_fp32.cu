@@ -447,7 +447,7 @@ __device__ __forceinline__ void gather_node(const Geo &g, const float *slots, in
 // node is computed once -- get v = P/m, a = f/m + g, v' = v + a dt and the
 // boundary conditions, written to the dense node records.
 template <int D, int NMODE, bool ONE>
-__global__ void __launch_bounds__(NODE_T) node_tile(const __grid_constant__ GroupArgs G, int work_slot) {
+__global__ void __launch_bounds__(NODE_T, 8) node_tile(const __grid_constant__ GroupArgs G, int work_slot) {
   constexpr int BN = box_nodes<D>();
   constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ;
   constexpr int NCH1 = NMODE == NODE_USL ? 1 + 2 * D : 1 + D;
