@@ -42,6 +42,66 @@ void free_group(GroupDev &g) {
   g = GroupDev();
 }
 
+// FP64 inputs of add_particles, uploaded as given (row-major, as the ABI
+// takes them); stress0 and cohesion may be null.
+struct NewParticles {
+  const double *pos, *vel, *vol, *stress0, *coh;
+};
+
+// The FP32 storage of new particles p (slot n0 + p) from their FP64 inputs:
+// cell = floor((x - origin) / h) and offset s - cell - 0.5 in FP64 (the same
+// IEEE operations as the oracle's locate), the offset rounded to FP32 and
+// kept inside [-0.5, 0.5); key, id, FP32 velocity, stress (zero without
+// stress0), mass = rho V, cohesion; strain, J-1 and eps_p zero.  Points
+// outside the mesh (or not finite) are counted in *bad and leave their slot
+// unwritten.
+template <int D>
+__global__ void init_particles_k(int64_t n, int64_t n0, PBuf P, Geo g, double o0, double o1, double o2, double h,
+                                 double rho, NewParticles in, int32_t *bad) {
+  constexpr int NS = nstress<D>();
+  constexpr int T[3] = {Tile<D>::TX, Tile<D>::TY, Tile<D>::TZ};
+  const double org[3] = {o0, o1, o2};
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    int c[3] = {0, 0, 0};
+    float u[3] = {0.f, 0.f, 0.f};
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const double sk = (in.pos[p * D + k] - org[k]) / h;
+      const double f = floor(sk);
+      ok = ok && sk >= 0.0 && f < (double)g.nc[k];
+      c[k] = ok ? (int)f : 0;
+      float uk = (float)(sk - f - 0.5);
+      if (uk >= 0.5f) uk = __int_as_float(0x3effffff);  // the float below 0.5
+      if (uk < -0.5f) uk = -0.5f;
+      u[k] = uk;
+    }
+    if (!ok) {
+      atomicAdd(bad, 1);
+      continue;
+    }
+    const int64_t q = n0 + p;
+    const int t = c[0] / T[0] + g.nt[0] * (c[1] / T[1] + g.nt[1] * (c[2] / T[2]));
+    const int l = c[0] % T[0] + T[0] * (c[1] % T[1] + T[1] * (c[2] % T[2]));
+    P.key()[q] = (uint32_t)t * CELLS_PER_TILE + (uint32_t)l;
+    P.id()[q] = (int32_t)q;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      P.off(k)[q] = u[k];
+      P.vel(k)[q] = (float)in.vel[p * D + k];
+    }
+#pragma unroll
+    for (int i = 0; i < NS; ++i) {
+      P.sig(i)[q] = in.stress0 ? (float)in.stress0[p * 6 + i] : 0.f;
+      P.eps(i)[q] = 0.f;
+    }
+    P.mass()[q] = (float)(rho * in.vol[p]);
+    P.jm1()[q] = 0.f;
+    P.epsp()[q] = 0.f;
+    if (in.coh) P.coh()[q] = (float)in.coh[p];
+  }
+}
+
 }  // namespace
 
 struct mpm_ctx {
@@ -496,18 +556,15 @@ mpm_status mpm_add_particles(mpm_handle h, int64_t n, const double *pos, const d
   if (h->n + n >= ((int64_t)1 << 31) - 1) return fail(h, MPM_ERR_ARG, "too many particles");
   const int D = h->d.dim;
   const mpm_mesh_desc &d = h->d;
-  // initial cells (FP64, host): floor((x - origin)/h); reject outside points
-  std::vector<int32_t> cell((size_t)n * D);
-  std::vector<double> off((size_t)n * D);
-  for (int64_t p = 0; p < n; ++p)
-    for (int k = 0; k < D; ++k) {
-      const double s = (pos[p * D + k] - d.origin[k]) / d.h;
-      if (!(s >= 0.0)) return fail(h, MPM_ERR_ARG, "a particle lies outside the mesh");
-      const double f = floor(s);
-      if (f >= (double)d.ncells[k]) return fail(h, MPM_ERR_ARG, "a particle lies outside the mesh");
-      cell[p * D + k] = (int32_t)f;
-      off[p * D + k] = s - f - 0.5;
-    }
+  // FP64 storage: reject points outside the mesh on the host (the FP32
+  // storage is converted and checked on the device, init_particles_k)
+  if (h->d.precision != MPM_FP32_MIXED)
+    for (int64_t p = 0; p < n; ++p)
+      for (int k = 0; k < D; ++k) {
+        const double s = (pos[p * D + k] - d.origin[k]) / d.h;
+        if (!(s >= 0.0) || floor(s) >= (double)d.ncells[k])
+          return fail(h, MPM_ERR_ARG, "a particle lies outside the mesh");
+      }
   if (n == 0) {
     if (first_id) *first_id = h->n;
     h->mat = *mat;
@@ -534,43 +591,44 @@ mpm_status mpm_add_particles(mpm_handle h, int64_t n, const double *pos, const d
     if (n0 > 0)
       for (int fi = 0; fi < PBUF_FIELDS - (coh ? 0 : 1); ++fi)
         CK(cp(nb[1].fld(fi), ob.fld(fi), 4 * n0), "copy");
-    std::vector<uint32_t> key(n);
-    std::vector<int32_t> id(n);
-    std::vector<float> f((size_t)n);
-    for (int64_t p = 0; p < n; ++p) {
-      int c[3] = {0, 0, 0};
-      for (int k = 0; k < D; ++k) c[k] = cell[p * D + k];
-      const int T0 = tile_dim(D, 0), T1 = tile_dim(D, 1), T2 = tile_dim(D, 2);
-      const int t = c[0] / T0 + h->geo.nt[0] * (c[1] / T1 + h->geo.nt[1] * (c[2] / T2));
-      const int l = c[0] % T0 + T0 * (c[1] % T1 + T1 * (c[2] % T2));
-      key[p] = (uint32_t)t * CELLS_PER_TILE + (uint32_t)l;
-      id[p] = (int32_t)(n0 + p);
+    // the FP64 inputs go up once; one kernel forms every FP32 field
+    {
+      const size_t w = (size_t)D * 2 + 1 + (stress0 ? 6 : 0) + (coh ? 1 : 0);  // doubles per particle
+      double *in64 = nullptr;
+      int32_t *bad = nullptr;
+      CK(cudaMallocAsync((void **)&in64, sizeof(double) * w * n + 256, h->st), "upload scratch");
+      NewParticles np;
+      double *at = in64;
+      auto put = [&](const double *src, size_t cnt, const double *&dst) -> cudaError_t {
+        dst = at;
+        at += cnt;
+        return cudaMemcpyAsync(at - cnt, src, sizeof(double) * cnt, cudaMemcpyHostToDevice, h->st);
+      };
+      cudaError_t e = put(pos, (size_t)n * D, np.pos);
+      if (e == cudaSuccess) e = put(vel, (size_t)n * D, np.vel);
+      if (e == cudaSuccess) e = put(vol, (size_t)n, np.vol);
+      np.stress0 = np.coh = nullptr;
+      if (e == cudaSuccess && stress0) e = put(stress0, (size_t)n * 6, np.stress0);
+      if (e == cudaSuccess && coh) e = put(cohesion, (size_t)n, np.coh);
+      bad = (int32_t *)at;  // 256 spare bytes after the inputs
+      if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(int32_t), h->st);
+      const int blocks = (int)std::min<int64_t>((n + 255) / 256, 8192);
+      if (e == cudaSuccess) {
+        if (D == 3)
+          init_particles_k<3><<<blocks, 256, 0, h->st>>>(n, n0, nb[1], h->geo, d.origin[0], d.origin[1], d.origin[2],
+                                                         d.h, mat->rho, np, bad);
+        else
+          init_particles_k<2><<<blocks, 256, 0, h->st>>>(n, n0, nb[1], h->geo, d.origin[0], d.origin[1], d.origin[2],
+                                                         d.h, mat->rho, np, bad);
+        e = cudaGetLastError();
+      }
+      int32_t nbad = 0;
+      if (e == cudaSuccess) e = cudaMemcpyAsync(&nbad, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st);
+      cudaFreeAsync(in64, h->st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+      CK(e, "upload");
+      if (nbad) return fail(h, MPM_ERR_ARG, "a particle lies outside the mesh");
     }
-    CK(cudaMemcpyAsync(nb[1].key() + n0, key.data(), 4 * n, cudaMemcpyHostToDevice, h->st), "upload");
-    CK(cudaMemcpyAsync(nb[1].id() + n0, id.data(), 4 * n, cudaMemcpyHostToDevice, h->st), "upload");
-    auto up = [&](float *dst, auto get) -> cudaError_t {
-      for (int64_t p = 0; p < n; ++p) f[p] = get(p);
-      cudaError_t e = cudaMemcpyAsync(dst + n0, f.data(), 4 * n, cudaMemcpyHostToDevice, h->st);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);  // f is reused
-      return e;
-    };
-    for (int k = 0; k < D; ++k) {
-      CK(up(nb[1].off(k), [&](int64_t p) {
-           float u = (float)off[p * D + k];
-           if (u >= 0.5f) u = nextafterf(0.5f, 0.f);
-           if (u < -0.5f) u = -0.5f;
-           return u;
-         }), "upload");
-      CK(up(nb[1].vel(k), [&](int64_t p) { return (float)vel[p * D + k]; }), "upload");
-    }
-    for (int i = 0; i < ns; ++i) {
-      CK(up(nb[1].sig(i), [&](int64_t p) { return stress0 ? (float)stress0[p * 6 + i] : 0.f; }), "upload");
-      CK(up(nb[1].eps(i), [&](int64_t) { return 0.f; }), "upload");
-    }
-    CK(up(nb[1].mass(), [&](int64_t p) { return (float)(mat->rho * vol[p]); }), "upload");
-    CK(up(nb[1].jm1(), [&](int64_t) { return 0.f; }), "upload");
-    CK(up(nb[1].epsp(), [&](int64_t) { return 0.f; }), "upload");
-    if (coh) CK(up(nb[1].coh(), [&](int64_t p) { return (float)cohesion[p]; }), "upload");
     // per-particle scratch of the binning
     StepBufs &S = h->s;
     free_t(S.keys_sorted);
@@ -750,27 +808,32 @@ mpm_status mpm_read_particles(mpm_handle h, double *pos, double *vel, double *st
   const int D = h->d.dim;
   if (n == 0) return device_status(h);
   if (h->d.precision == MPM_FP32_MIXED) {
-    double *tmp = nullptr;
-    CK(cudaMallocAsync((void **)&tmp, sizeof(double) * 6 * n, h->st), "read scratch");
+    // one export of every requested field into device scratch, then the copies
     const PBuf &P = h->buf[h->cur];
     struct Item {
       void *host;
       int width;
-      int which;
     };
-    const Item items[7] = {{pos, D, 0},  {vel, D, 1},  {stress, 6, 2}, {strain, 6, 3},
-                           {vol, 1, 4},  {epsp, 1, 5}, {cell, 1, 6}};
-    cudaError_t e = cudaSuccess;
-    for (const Item &it : items) {
-      if (!it.host || e != cudaSuccess) continue;
-      double *o[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-      o[it.which] = tmp;
-      e = f32_export(D, n, P, h->geo, h->d.origin, h->d.h, h->mat.rho, o[0], o[1], o[2], o[3], o[4], o[5],
-                     (int64_t *)o[6], h->st);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(it.host, tmp, sizeof(double) * it.width * n, cudaMemcpyDeviceToHost, h->st);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
-    }
+    const Item items[7] = {{pos, D}, {vel, D}, {stress, 6}, {strain, 6}, {vol, 1}, {epsp, 1}, {cell, 1}};
+    size_t words = 0;
+    for (const Item &it : items)
+      if (it.host) words += (size_t)it.width * n;
+    double *tmp = nullptr;
+    CK(cudaMallocAsync((void **)&tmp, sizeof(double) * words, h->st), "read scratch");
+    double *o[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    size_t at = 0;
+    for (int i = 0; i < 7; ++i)
+      if (items[i].host) {
+        o[i] = tmp + at;
+        at += (size_t)items[i].width * n;
+      }
+    cudaError_t e = f32_export(D, n, P, h->geo, h->d.origin, h->d.h, h->mat.rho, o[0], o[1], o[2], o[3], o[4], o[5],
+                               (int64_t *)o[6], h->st);
+    for (int i = 0; i < 7 && e == cudaSuccess; ++i)
+      if (items[i].host)
+        e = cudaMemcpyAsync(items[i].host, o[i], sizeof(double) * items[i].width * n, cudaMemcpyDeviceToHost, h->st);
     cudaFreeAsync(tmp, h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
     if (e != cudaSuccess) return cuda_fail(h, e, "read_particles");
   } else {
     const D64State &P = h->L64.P;

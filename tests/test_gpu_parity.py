@@ -48,6 +48,49 @@ def test_initial_cells_bit_exact(precision):
     assert np.array_equal(gpu["cell"], ref["cell"])
 
 
+@pytest.mark.parametrize("precision", [W.FP64_PLAIN, W.FP32_MIXED])
+def test_initial_state_matches_the_inputs(precision):
+    # the FP32 storage is formed on the device from the FP64 inputs: offsets
+    # round to FP32 once, so positions read back lie within the offset's
+    # resolution (2^-24 cells) of the inputs; mass and velocity are the
+    # inputs rounded to FP32
+    wl = H.small_column(precision=precision)
+    rng = np.random.default_rng(3)
+    wl = dataclasses.replace(wl, vel=rng.normal(0.0, 0.1, wl.vel.shape))
+    s0 = rng.normal(0.0, 1e3, (wl.n, 6))
+    with mpm.Simulation(wl, stress0=s0) as sim:
+        g, st = sim.read()
+    assert st == mpm.MPM_OK
+    tol = 1e-15 if precision == W.FP64_PLAIN else 2.0 ** -24
+    assert np.abs(g["pos"] - wl.pos).max() <= tol * wl.h * 1.01
+    f32 = (lambda a: a) if precision == W.FP64_PLAIN else (lambda a: a.astype(np.float32).astype(np.float64))
+    assert np.array_equal(g["vel"], f32(wl.vel))
+    assert np.array_equal(g["stress"][:, :6], f32(s0))
+    assert np.allclose(g["vol"], wl.vol, rtol=1e-7, atol=0.0)
+    assert not g["strain"].any() and not g["epsp"].any()
+
+
+@pytest.mark.parametrize("precision", [W.FP64_PLAIN, W.FP32_MIXED])
+def test_add_particles_rejects_points_outside_the_mesh(precision):
+    wl = H.small_column(precision=precision)
+    with mpm.Simulation(wl) as sim:
+        n = mpm.mpm_num_particles(sim.h)
+        upper = np.array(wl.ncells[:3], float) * wl.h
+        for bad_x in (-1e-6, upper[0], float("nan")):
+            pos = wl.pos[:7].copy()
+            pos[3, 0] = bad_x
+            with pytest.raises(mpm.MPMError) as ei:
+                mpm.mpm_add_particles(sim.h, pos, wl.vel[:7], wl.vol[:7], sim.mat)
+            assert ei.value.status == mpm.MPM_ERR_ARG
+        # the mesh is unchanged and still steps; a valid add then succeeds
+        assert mpm.mpm_num_particles(sim.h) == n
+        sim.step(2)
+        assert sim.sync() == mpm.MPM_OK
+        assert mpm.mpm_add_particles(sim.h, wl.pos[:7], wl.vel[:7], wl.vol[:7], sim.mat) == n
+        sim.step(1)
+        assert sim.sync() == mpm.MPM_OK
+
+
 def test_fp64_bar_matches_oracle():
     wl = W.elastic_bar()
     start, _ = run_oracle(wl, 0)
