@@ -333,6 +333,9 @@ cudaError_t build_group(GroupDev &g, const std::vector<mpm_ctx *> &mem, bool rel
     int max_m = 0;
     for (int i = 0; i < n; ++i) max_m = std::max(max_m, mem[i]->geo.ntiles + 1);
     G.scan_one = max_m <= SCAN1_MAX ? 1 : 0;
+    int64_t np = 0;
+    for (int i = 0; i < n; ++i) np += mem[i]->n;
+    G.bin_t = np >= ((int64_t)1 << 22) ? 128 : 256;
     // the apex band of the FP32 return is empty without cohesion
     G.apex = 0;
     for (int i = 0; i < n; ++i)

@@ -39,8 +39,6 @@
 namespace mpm {
 namespace {
 
-constexpr int BT = 256;  // bin_tiles threads
-constexpr int BT_WARPS = BT / 32;
 constexpr int BUCKET_SMEM = 1024;
 constexpr int SCAN_T = 256;
 constexpr int SCAN_ITEMS = 4;
@@ -455,12 +453,17 @@ __global__ void __launch_bounds__(SCAN1_T) bin_scan_one(const __grid_constant__ 
 }
 
 
-template <bool ONE>
-__global__ void __launch_bounds__(BT) bin_tiles(const __grid_constant__ GroupArgs G) {
+// NT threads per CTA, one tile at a time; the grid holds 2048 threads per SM
+// (NT = 256 for groups whose active tiles are about as many as the CTAs, 128
+// for large groups, where more tiles in flight per SM shorten the pass).
+template <bool ONE, int NT>
+__global__ void __launch_bounds__(NT) bin_tiles(const __grid_constant__ GroupArgs G) {
+  static_assert(NT > CELLS_PER_TILE && NT % 32 == 0 && 2048 % NT == 0, "bin_tiles block");
+  constexpr int NW = NT / 32;
   __shared__ int cnt[CELLS_PER_TILE];
   __shared__ int base[CELLS_PER_TILE];
   __shared__ int running[CELLS_PER_TILE];
-  __shared__ uint16_t wcnt[BT_WARPS][CELLS_PER_TILE + 1];
+  __shared__ uint16_t wcnt[NW][CELLS_PER_TILE + 1];
   __shared__ int sb_in[BUCKET_SMEM];
   __shared__ int sb_out[BUCKET_SMEM];
   __shared__ int s_nl;
@@ -469,7 +472,7 @@ __global__ void __launch_bounds__(BT) bin_tiles(const __grid_constant__ GroupArg
   const uint32_t lt_mask = (1u << lane) - 1u;
   __shared__ int s_work[2];
   pdl_trigger();
-  for (int k = tid; k < BT_WARPS * (CELLS_PER_TILE + 1); k += BT) (&wcnt[0][0])[k] = 0;
+  for (int k = tid; k < NW * (CELLS_PER_TILE + 1); k += NT) (&wcnt[0][0])[k] = 0;
   pdl_wait();
   // items: first the CTA's own (blockIdx.x), then gridDim.x + the work counter
   const int total = G.bin_items[G.ninst];
@@ -501,9 +504,9 @@ __global__ void __launch_bounds__(BT) bin_tiles(const __grid_constant__ GroupArg
     // arrivals sorted by storage position (positions are distinct)
     const int *sorted;
     if (nbk <= BUCKET_SMEM) {
-      for (int k = tid; k < nbk; k += BT) sb_in[k] = I.s.bucket[bs + k];
+      for (int k = tid; k < nbk; k += NT) sb_in[k] = I.s.bucket[bs + k];
       __syncthreads();
-      for (int k = tid; k < nbk; k += BT) {
+      for (int k = tid; k < nbk; k += NT) {
         const int p = sb_in[k];
         int r = 0;
         for (int j = 0; j < nbk; ++j) r += sb_in[j] < p;
@@ -512,7 +515,7 @@ __global__ void __launch_bounds__(BT) bin_tiles(const __grid_constant__ GroupArg
       sorted = sb_out;
     } else {
       const int32_t *src = I.s.bucket + bs;
-      for (int k = tid; k < nbk; k += BT) {
+      for (int k = tid; k < nbk; k += NT) {
         const int p = src[k];
         int r = 0;
         for (int j = 0; j < nbk; ++j) r += src[j] < p;
@@ -539,7 +542,7 @@ __global__ void __launch_bounds__(BT) bin_tiles(const __grid_constant__ GroupArg
     const int S = nbk + nr;
 
     // histogram of local cells (warp-aggregated shared atomics)
-    for (int c0 = 0; c0 < S; c0 += BT) {
+    for (int c0 = 0; c0 < S; c0 += NT) {
       const int s = c0 + tid;
       int d = CELLS_PER_TILE;
       if (s < S) {
@@ -564,7 +567,7 @@ __global__ void __launch_bounds__(BT) bin_tiles(const __grid_constant__ GroupArg
     __syncthreads();
 
     // stable scatter in storage order
-    for (int c0 = 0; c0 < S; c0 += BT) {
+    for (int c0 = 0; c0 < S; c0 += NT) {
       const int s = c0 + tid;
       int d = CELLS_PER_TILE;
       int pos = 0;
@@ -590,7 +593,7 @@ __global__ void __launch_bounds__(BT) bin_tiles(const __grid_constant__ GroupArg
       if (tid <= CELLS_PER_TILE) {
         int add = 0;
 #pragma unroll
-        for (int k2 = 0; k2 < BT_WARPS; ++k2) {
+        for (int k2 = 0; k2 < NW; ++k2) {
           add += wcnt[k2][tid];
           wcnt[k2][tid] = 0;
         }
@@ -632,7 +635,9 @@ cudaError_t bin_launch(const GroupArgs &G, cudaStream_t st) {
   cudaError_t e = G.scan_one ? launch_dep(bin_scan_one<ONE>, G.ninst, SCAN1_T, 0, st, G)
                              : launch_dep(bin_scan_lb<ONE>, G.nblk_s, SCAN_T, 0, st, G);
   if (e == cudaSuccess) e = launch_dep(bin_bucket<ONE>, G.nblk_m, 256, 0, st, G);
-  if (e == cudaSuccess) e = launch_dep(bin_tiles<ONE>, G.grid, BT, 0, st, G);
+  if (e == cudaSuccess)
+    e = G.bin_t == 128 ? launch_dep(bin_tiles<ONE, 128>, G.grid * 2, 128, 0, st, G)
+                       : launch_dep(bin_tiles<ONE, 256>, G.grid, 256, 0, st, G);
   return e;
 }
 

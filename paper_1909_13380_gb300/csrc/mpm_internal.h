@@ -206,6 +206,7 @@ struct GroupArgs {
   int scan_one;             // every instance has at most SCAN1_MAX tiles: one-CTA scans
   int grid;                 // CTAs of the per-tile kernels
   int apex;                 // some instance can reach the FP64 apex band (cohesion > 0): run apex_band_k
+  int bin_t;                // bin_tiles threads per CTA: 128 for groups of >= 4M particles, else 256
   InstArgs one;             // a group of one: its table entry (inst[0]) by value
 };
 
