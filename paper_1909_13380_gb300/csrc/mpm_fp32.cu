@@ -41,7 +41,7 @@ constexpr int NODE_T = 128;
 constexpr int G2P_T = MPM_G2P_T;        // G2P threads per CTA
 constexpr int G2P_SUB = 256 / G2P_T;    // G2P CTAs per 256-particle block of the group prefix
 #ifndef MPM_P2G_MINB
-#define MPM_P2G_MINB 4  // resident P2G CTAs per SM the register budget is sized for
+#define MPM_P2G_MINB 5  // resident P2G CTAs per SM the register budget is sized for
 #endif
 #ifndef MPM_G2P_MINB
 #define MPM_G2P_MINB 8  // resident G2P CTAs per SM the register budget is sized for
@@ -168,6 +168,14 @@ struct P2GRec {
   static constexpr size_t SMEM = (REC_BYTES > CELLP_BYTES ? REC_BYTES : CELLP_BYTES);
 };
 
+// Resident P2G CTAs per SM the register budget is sized for: MPM_P2G_MINB
+// (48 registers at 5), except the 3D USL kernel of a batch, which reads its
+// instance from shared memory and would spill at 48: 4 (64 registers).
+template <int D, int MODE, bool ONE>
+constexpr int p2g_min_blocks() {
+  return (D == 3 && MODE == P2G_USL && !ONE) ? 4 : MPM_P2G_MINB;
+}
+
 template <int D, int MODE>
 constexpr size_t p2g_smem() {
   return P2GRec<D, MODE>::SMEM;
@@ -183,7 +191,7 @@ constexpr int p2g_threads() {
 __device__ __forceinline__ int rec_slot(int i) { return (i & ~7) | ((i ^ (i >> 3)) & 7); }
 
 template <int D, int MODE, bool ONE>
-__global__ void __launch_bounds__(P2GRec<D, MODE>::CH, MPM_P2G_MINB)
+__global__ void __launch_bounds__(P2GRec<D, MODE>::CH, p2g_min_blocks<D, MODE, ONE>())
     p2g_tile(const __grid_constant__ GroupArgs G, int work_slot) {
   using R = P2GRec<D, MODE>;
   constexpr int NCH = p2g_channels<D, MODE>();
