@@ -43,6 +43,9 @@ constexpr int G2P_SUB = 256 / G2P_T;    // G2P CTAs per 256-particle block of th
 #ifndef MPM_P2G_MINB
 #define MPM_P2G_MINB 5  // resident P2G CTAs per SM the register budget is sized for
 #endif
+#ifndef MPM_NODE_MINB
+#define MPM_NODE_MINB 8  // resident node CTAs per SM for a single mesh (a batch's kernel: 8)
+#endif
 #ifndef MPM_G2P_MINB
 #define MPM_G2P_MINB 8  // resident G2P CTAs per SM the register budget is sized for
 #endif
@@ -455,7 +458,7 @@ __device__ __forceinline__ void gather_node(const Geo &g, const float *slots, in
 // node is computed once -- get v = P/m, a = f/m + g, v' = v + a dt and the
 // boundary conditions, written to the dense node records.
 template <int D, int NMODE, bool ONE>
-__global__ void __launch_bounds__(NODE_T, 8) node_tile(const __grid_constant__ GroupArgs G, int work_slot) {
+__global__ void __launch_bounds__(NODE_T, ONE ? MPM_NODE_MINB : 8) node_tile(const __grid_constant__ GroupArgs G, int work_slot) {
   constexpr int BN = box_nodes<D>();
   constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ;
   constexpr int NCH1 = NMODE == NODE_USL ? 1 + 2 * D : 1 + D;
@@ -700,14 +703,37 @@ __global__ void __launch_bounds__(G2P_T, MPM_G2P_MINB) g2p(const __grid_constant
       na[0] = r0.z;
       na[1] = r0.w;
     }
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
+    if constexpr (D == 3) {
+      // paired FP32 FMAs: each lane is the same single-rounding FMA as the
+      // scalar accumulation below, two per instruction
       if (GMODE != G2P_USF_STRESS) {
-        dv[k] += N * na[k];
-        vb[k] += N * nv[k];
+        const float2 NN = make_float2(N, N);
+        const float2 a01 = __ffma2_rn(NN, make_float2(na[0], na[1]), make_float2(dv[0], dv[1]));
+        const float2 v01 = __ffma2_rn(NN, make_float2(nv[0], nv[1]), make_float2(vb[0], vb[1]));
+        dv[0] = a01.x;
+        dv[1] = a01.y;
+        dv[2] = fmaf(N, na[2], dv[2]);
+        vb[0] = v01.x;
+        vb[1] = v01.y;
+        vb[2] = fmaf(N, nv[2], vb[2]);
       }
 #pragma unroll
-      for (int l = 0; l < D; ++l) L[k][l] += nv[k] * G[l];
+      for (int k = 0; k < 3; ++k) {
+        const float2 l01 = __ffma2_rn(make_float2(nv[k], nv[k]), make_float2(G[0], G[1]), make_float2(L[k][0], L[k][1]));
+        L[k][0] = l01.x;
+        L[k][1] = l01.y;
+        L[k][2] = fmaf(nv[k], G[2], L[k][2]);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        if (GMODE != G2P_USF_STRESS) {
+          dv[k] += N * na[k];
+          vb[k] += N * nv[k];
+        }
+#pragma unroll
+        for (int l = 0; l < D; ++l) L[k][l] += nv[k] * G[l];
+      }
     }
   }
 
