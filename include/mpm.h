@@ -123,9 +123,12 @@ mpm_status mpm_create_mesh(const mpm_mesh_desc *desc, mpm_handle *out);
  *   stress0    n*6 initial stresses, or NULL for zero
  *   first_id   out: id of the first new particle (ids are 0,1,2,... in
  *              insertion order), may be NULL
- * Particles outside the mesh are rejected (MPM_ERR_ARG, none added).  The
- * initial cell is computed on the host in FP64 by the rule above.  Must not
- * be called while steps are in flight (it synchronises the stream). */
+ * Particles outside the mesh (or with a non-finite position) are rejected
+ * (MPM_ERR_ARG, none added, the mesh unchanged).  The initial cell is
+ * computed in FP64 by the rule above: on the host for FP64_PLAIN, on the
+ * device for FP32_MIXED (the inputs are copied up once and every FP32 field
+ * is formed there).  The host arrays are only read during the call.  Must
+ * not be called while steps are in flight (it synchronises the stream). */
 mpm_status mpm_add_particles(mpm_handle h, int64_t n, const double *pos, const double *vel,
                              const double *vol, const mpm_material *mat, const double *cohesion,
                              const double *stress0, int64_t *first_id);
