@@ -102,6 +102,58 @@ __global__ void init_particles_k(int64_t n, int64_t n0, PBuf P, Geo g, double o0
   }
 }
 
+// The FP64 storage of new particles p (slot n0 + p): the inputs as given,
+// mass = rho V, strain and eps_p zero, alive.
+template <int D>
+__global__ void init_particles64_k(int64_t n, int64_t n0, D64State P, double rho, NewParticles in) {
+  constexpr int NS = nstress<D>();
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = n0 + p;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      P.x[k][q] = in.pos[p * D + k];
+      P.v[k][q] = in.vel[p * D + k];
+    }
+#pragma unroll
+    for (int i = 0; i < NS; ++i) {
+      P.sig[i][q] = in.stress0 ? in.stress0[p * 6 + i] : 0.0;
+      P.eps[i][q] = 0.0;
+    }
+    P.mass[q] = rho * in.vol[p];
+    P.vol[q] = in.vol[p];
+    P.epsp[q] = 0.0;
+    if (in.coh) P.coh[q] = in.coh[p];
+    P.alive[q] = 1;
+  }
+}
+
+// Copy the FP64 inputs of add_particles to one device scratch allocation
+// (freed by the caller with cudaFreeAsync), with a zeroed int32 counter after
+// them.  Stream-ordered; the host arrays are read before the call returns.
+cudaError_t upload_inputs(cudaStream_t st, int64_t n, int D, const double *pos, const double *vel, const double *vol,
+                          const double *stress0, const double *cohesion, double *&scratch, NewParticles &np,
+                          int32_t *&counter) {
+  const size_t w = (size_t)D * 2 + 1 + (stress0 ? 6 : 0) + (cohesion ? 1 : 0);  // doubles per particle
+  scratch = nullptr;
+  cudaError_t e = cudaMallocAsync((void **)&scratch, sizeof(double) * w * n + 256, st);
+  if (e != cudaSuccess) return e;
+  double *at = scratch;
+  auto put = [&](const double *src, size_t cnt, const double *&dst) -> cudaError_t {
+    dst = at;
+    at += cnt;
+    return cudaMemcpyAsync(at - cnt, src, sizeof(double) * cnt, cudaMemcpyHostToDevice, st);
+  };
+  np.stress0 = np.coh = nullptr;
+  e = put(pos, (size_t)n * D, np.pos);
+  if (e == cudaSuccess) e = put(vel, (size_t)n * D, np.vel);
+  if (e == cudaSuccess) e = put(vol, (size_t)n, np.vol);
+  if (e == cudaSuccess && stress0) e = put(stress0, (size_t)n * 6, np.stress0);
+  if (e == cudaSuccess && cohesion) e = put(cohesion, (size_t)n, np.coh);
+  counter = (int32_t *)at;  // 256 spare bytes after the inputs
+  if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(int32_t), st);
+  return e;
+}
+
 }  // namespace
 
 struct mpm_ctx {
@@ -596,25 +648,11 @@ mpm_status mpm_add_particles(mpm_handle h, int64_t n, const double *pos, const d
         CK(cp(nb[1].fld(fi), ob.fld(fi), 4 * n0), "copy");
     // the FP64 inputs go up once; one kernel forms every FP32 field
     {
-      const size_t w = (size_t)D * 2 + 1 + (stress0 ? 6 : 0) + (coh ? 1 : 0);  // doubles per particle
       double *in64 = nullptr;
       int32_t *bad = nullptr;
-      CK(cudaMallocAsync((void **)&in64, sizeof(double) * w * n + 256, h->st), "upload scratch");
       NewParticles np;
-      double *at = in64;
-      auto put = [&](const double *src, size_t cnt, const double *&dst) -> cudaError_t {
-        dst = at;
-        at += cnt;
-        return cudaMemcpyAsync(at - cnt, src, sizeof(double) * cnt, cudaMemcpyHostToDevice, h->st);
-      };
-      cudaError_t e = put(pos, (size_t)n * D, np.pos);
-      if (e == cudaSuccess) e = put(vel, (size_t)n * D, np.vel);
-      if (e == cudaSuccess) e = put(vol, (size_t)n, np.vol);
-      np.stress0 = np.coh = nullptr;
-      if (e == cudaSuccess && stress0) e = put(stress0, (size_t)n * 6, np.stress0);
-      if (e == cudaSuccess && coh) e = put(cohesion, (size_t)n, np.coh);
-      bad = (int32_t *)at;  // 256 spare bytes after the inputs
-      if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(int32_t), h->st);
+      cudaError_t e = upload_inputs(h->st, n, D, pos, vel, vol, stress0, cohesion, in64, np, bad);
+      if (in64 == nullptr) CK(e, "upload scratch");
       const int blocks = (int)std::min<int64_t>((n + 255) / 256, 8192);
       if (e == cudaSuccess) {
         if (D == 3)
@@ -693,28 +731,24 @@ mpm_status mpm_add_particles(mpm_handle h, int64_t n, const double *pos, const d
       if (coh) CK(cp(P.coh, O.coh, b8), "copy");
       CK(cp(P.alive, O.alive, 4 * n0), "copy");
     }
-    std::vector<double> f((size_t)n);
-    auto up = [&](double *dst, auto get) -> cudaError_t {
-      for (int64_t p = 0; p < n; ++p) f[p] = get(p);
-      cudaError_t e = cudaMemcpyAsync(dst + n0, f.data(), 8 * n, cudaMemcpyHostToDevice, h->st);
+    {  // the FP64 inputs go up once; one kernel fills the new slots
+      double *in64 = nullptr;
+      int32_t *unused = nullptr;
+      NewParticles np;
+      cudaError_t e = upload_inputs(h->st, n, D, pos, vel, vol, stress0, cohesion, in64, np, unused);
+      if (in64 == nullptr) CK(e, "upload scratch");
+      const int blocks = (int)std::min<int64_t>((n + 255) / 256, 8192);
+      if (e == cudaSuccess) {
+        if (D == 3)
+          init_particles64_k<3><<<blocks, 256, 0, h->st>>>(n, n0, P, mat->rho, np);
+        else
+          init_particles64_k<2><<<blocks, 256, 0, h->st>>>(n, n0, P, mat->rho, np);
+        e = cudaGetLastError();
+      }
+      cudaFreeAsync(in64, h->st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
-      return e;
-    };
-    for (int k = 0; k < D; ++k) {
-      CK(up(P.x[k], [&](int64_t p) { return pos[p * D + k]; }), "upload");
-      CK(up(P.v[k], [&](int64_t p) { return vel[p * D + k]; }), "upload");
+      CK(e, "upload");
     }
-    for (int i = 0; i < ns; ++i) {
-      CK(up(P.sig[i], [&](int64_t p) { return stress0 ? stress0[p * 6 + i] : 0.0; }), "upload");
-      CK(up(P.eps[i], [&](int64_t) { return 0.0; }), "upload");
-    }
-    CK(up(P.mass, [&](int64_t p) { return mat->rho * vol[p]; }), "upload");
-    CK(up(P.vol, [&](int64_t p) { return vol[p]; }), "upload");
-    CK(up(P.epsp, [&](int64_t) { return 0.0; }), "upload");
-    if (coh) CK(up(P.coh, [&](int64_t p) { return cohesion[p]; }), "upload");
-    std::vector<int32_t> one((size_t)n, 1);
-    CK(cudaMemcpyAsync(P.alive + n0, one.data(), 4 * n, cudaMemcpyHostToDevice, h->st), "upload");
-    CK(cudaStreamSynchronize(h->st), "upload");
     free_ptr(h->pmem64);
     h->pmem64 = nmem;
     guard.release();
