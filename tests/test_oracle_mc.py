@@ -1,6 +1,7 @@
 """Pins of the oracle's material update (CODE OVERVIEW: the Material class
-turns a strain increment into a stress; Mohr-Coulomb as the north-star
-material, returned in principal stresses after de Souza Neto et al. 2008).
+turns a strain increment into a stress; Mohr-Coulomb as the granular
+material of the column and slope workloads, returned in principal stresses
+after de Souza Neto et al. 2008).
 
 Independent pins:
   * the Jacobi eigen-solver against LAPACK (numpy.linalg.eigh);
