@@ -176,8 +176,12 @@ mpm_status mpm_read_binning(mpm_handle h, int32_t *key, int32_t *perm, int32_t *
  *   USL (4): binning, P2G, nodal solve, G2P (+ carry of dead particles)
  *   USF (7): binning, P2G mass/momentum, nodal velocity, G2P stress,
  *            P2G internal force, nodal solve, G2P advection
- * ms must hold MPM_MAX_PHASES floats.  MPM_ERR_STATE on FP64_PLAIN handles
- * or when timing is off or no step ran since it was enabled. */
+ * With cohesion, a G2P phase that updates stresses includes the FP64
+ * apex-band return that follows it.  The event nodes also serialise the
+ * step's kernels (which otherwise overlap their launches), so the phases
+ * add up to more than an untimed step.  ms must hold MPM_MAX_PHASES floats.
+ * MPM_ERR_STATE on FP64_PLAIN handles or when timing is off or no step ran
+ * since it was enabled. */
 #define MPM_MAX_PHASES 8
 mpm_status mpm_set_phase_timing(mpm_handle h, int32_t enable);
 mpm_status mpm_phase_times(mpm_handle h, float *ms, int32_t *nphase);
