@@ -153,3 +153,155 @@ def test_node_constraints_by_hand():
     vn0 = np.array([0.3, 0.0, 0.2])
     v, a, vn = oracle.constrain_node(mesh, (2, 2, 0), v0, a0, vn0)
     assert np.array_equal(vn, vn0) and np.array_equal(a, a0)
+
+
+# ---------------------------------------------------------------------------
+# One explicit step of two particles in one cell, written out by hand from the
+# textbook formulas of the two update orders (CODE OVERVIEW: explicit USF and
+# USL).  The cell touches the -x face, which is a roller, so the velocity
+# condition and the force-stage condition both act.  No oracle routine
+# supplies an expected value.
+# ---------------------------------------------------------------------------
+def _hand_shape(xp, cell, h, origin, d):
+    """N_a and dN_a/dx of the linear quad/hex at xp in `cell` (node a: bit k
+    of a set = upper node along axis k)."""
+    xi = [2.0 * ((xp[k] - origin[k]) / h - cell[k]) - 1.0 for k in range(d)]
+    N, G = [], []
+    for a in range(1 << d):
+        s = [1.0 if (a >> k) & 1 else -1.0 for k in range(d)]
+        w = [0.5 * (1.0 + s[k] * xi[k]) for k in range(d)]
+        N.append(float(np.prod(w)))
+        G.append([s[k] / h * float(np.prod([w[j] for j in range(d) if j != k])) for k in range(d)])
+    return np.array(N), np.array(G)
+
+
+_VOIGT = ((0, 3, 5), (3, 1, 4), (5, 4, 2))   # (xx, yy, zz, xy, yz, xz) -> tensor entry
+
+
+def _hand_step(scheme, d, P, mesh, E, nu, wrong=None):
+    """Expected particle state after one step.  P: dict of x (n,3), v (n,3),
+    sig (n,6), eps (n,6), m (n,), vol (n,) with every particle in `cell`.
+    `wrong` plants the slips a step-order mistake would make: "usl_strain_v"
+    (USL strain from the pre-force v = P/m) or "usf_force_old_sig" (USF
+    internal force from the stress at the start of the step)."""
+    h, origin, dt, g = mesh.h, mesh.origin, mesh.dt, np.array(mesh.g[:d])
+    cell = P["cell"]
+    nn = 1 << d
+    G_, lam = E / (2.0 * (1.0 + nu)), E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
+    x, v, sig, eps = P["x"].copy(), P["v"].copy(), P["sig"].copy(), P["eps"].copy()
+    m, vol = P["m"].copy(), P["vol"].copy()
+    npart = x.shape[0]
+    sh = [_hand_shape(x[p], cell, h, origin, d) for p in range(npart)]
+    on_roller = [((a & 1) == 0) for a in range(nn)]     # node x index 0: the -x face (roller)
+
+    def mass_momentum():
+        mi, Pi = np.zeros(nn), np.zeros((nn, d))
+        for p in range(npart):
+            N, _ = sh[p]
+            for a in range(nn):
+                mi[a] += N[a] * m[p]
+                Pi[a] += N[a] * m[p] * v[p, :d]
+        return mi, Pi
+
+    def force(s6, V):
+        f = np.zeros((nn, d))
+        for p in range(npart):
+            N, Gp = sh[p]
+            for a in range(nn):
+                for j in range(d):
+                    f[a, j] += -V[p] * sum(s6[p, _VOIGT[j][k]] * Gp[a, k] for k in range(d)) + N[a] * m[p] * g[j]
+        return f
+
+    def strain_stress(p, vel_nodes):
+        N, Gp = sh[p]
+        L = np.zeros((3, 3))
+        for a in range(nn):
+            for j in range(d):
+                for k in range(d):
+                    L[j, k] += vel_nodes[a, j] * Gp[a, k]
+        de = np.array([L[0, 0], L[1, 1], L[2, 2], 0.5 * (L[0, 1] + L[1, 0]), 0.5 * (L[1, 2] + L[2, 1]),
+                       0.5 * (L[0, 2] + L[2, 0])]) * dt
+        tr = de[0] + de[1] + de[2]
+        eps[p] += de
+        vol[p] *= 1.0 + tr
+        for i in range(3):
+            sig[p, i] += lam * tr + 2.0 * G_ * de[i]
+        for i in range(3, 6):
+            sig[p, i] += 2.0 * G_ * de[i]
+
+    def advect(acc, vnew):
+        for p in range(npart):
+            N, _ = sh[p]
+            v[p, :d] += dt * sum(N[a] * acc[a] for a in range(nn))
+            x[p, :d] += dt * sum(N[a] * vnew[a] for a in range(nn))
+
+    mi, Pi = mass_momentum()
+    vi = Pi / mi[:, None]
+    if scheme == oracle.USL:
+        ai = force(sig, vol) / mi[:, None]
+        vn = vi + ai * dt
+        for a in range(nn):
+            if on_roller[a]:
+                vi[a, 0] = ai[a, 0] = vn[a, 0] = 0.0
+        for p in range(npart):
+            strain_stress(p, vi if wrong == "usl_strain_v" else vn)
+        advect(ai, vn)
+    else:
+        for a in range(nn):                  # velocity condition on the pre-force velocity
+            if on_roller[a]:
+                vi[a, 0] = 0.0
+        sig0, vol0 = sig.copy(), vol.copy()
+        for p in range(npart):
+            strain_stress(p, vi)
+        ai = (force(sig0, vol0) if wrong == "usf_force_old_sig" else force(sig, vol)) / mi[:, None]
+        vn = vi + ai * dt
+        for a in range(nn):
+            if on_roller[a]:
+                vi[a, 0] = ai[a, 0] = vn[a, 0] = 0.0
+        advect(ai, vn)
+    return {"x": x, "v": v, "sig": sig, "eps": eps, "vol": vol}
+
+
+def _two_particle_case(d):
+    h, origin = 0.5, (0.1, -0.2, 0.3)
+    g = (1.5, -9.81, 0.7)[:d] + (0.0,) * (3 - d)
+    mesh = oracle.Mesh(dim=d, n=(3, 3, 3)[:d] + (1,) * (3 - d), h=h, origin=origin,
+                       face_bc=(oracle.BC_ROLLER, 0, 0, 0, 0, 0), g=g, dt=1e-2, scheme=oracle.USL)
+    cell = (0, 1, 1)[:d] + (0,) * (3 - d)
+    frac = np.array([[0.23, 0.61, 0.37], [0.74, 0.18, 0.82]])[:, :d]
+    pos = np.array(origin[:d]) + (np.array(cell[:d]) + frac) * h
+    vel = np.array([[0.30, -0.12, 0.21], [-0.17, 0.25, -0.08]])[:, :d]
+    sig = np.array([[120.0, -80.0, 35.0, 40.0, -22.0, 17.0], [-60.0, 150.0, -45.0, -30.0, 28.0, -11.0]])
+    if d == 2:
+        sig[:, 4:] = 0.0
+    vol = np.array([0.031, 0.027])
+    return mesh, cell, pos, vel, sig, vol
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_one_step_order_by_hand(dim):
+    E, nu, rho = 1.0e4, 0.25, 900.0
+    res = {}
+    for scheme in (oracle.USF, oracle.USL):
+        mesh, cell, pos, vel, sig, vol = _two_particle_case(dim)
+        mesh.scheme = scheme
+        st = oracle.State.create(pos, vel, vol, rho, sig0=sig)
+        P = {"x": st.x.copy(), "v": st.v.copy(), "sig": st.sig.copy(), "eps": st.eps.copy(), "m": st.m.copy(),
+             "vol": st.vol.copy(), "cell": cell}
+        expect = _hand_step(scheme, dim, P, mesh, E, nu)
+        o = oracle.Oracle(mesh, oracle.Material(E=E, nu=nu, rho=rho), st)
+        assert o.step(1) == oracle.OK
+        got = {"x": st.x, "v": st.v, "sig": st.sig, "eps": st.eps, "vol": st.vol}
+        for k in expect:
+            scale = np.abs(expect[k]).max()
+            assert np.abs(got[k] - expect[k]).max() <= 1e-13 * scale, (scheme, k)
+        # the pin discriminates: the plausible order slips move the result by
+        # far more than the tolerance
+        slip = "usl_strain_v" if scheme == oracle.USL else "usf_force_old_sig"
+        bad = _hand_step(scheme, dim, P, mesh, E, nu, wrong=slip)
+        key = "sig" if scheme == oracle.USL else "v"
+        assert np.abs(bad[key] - expect[key]).max() > 1e-4 * np.abs(expect[key]).max(), slip
+        res[scheme] = got
+    # the two orders give different stresses after one step
+    d_sig = np.abs(res[oracle.USF]["sig"] - res[oracle.USL]["sig"]).max()
+    assert d_sig > 1e-4 * np.abs(res[oracle.USL]["sig"]).max()
