@@ -1,33 +1,36 @@
 #!/usr/bin/env python
 """Throughput of the explicit MPM step on GB300.
 
-Default workload: 3D dry granular column collapse, 200 x 40 x 100 hexahedra of
-5 mm, 0.2 m cube column with 8 particles per cell (512,000 particles),
-Mohr-Coulomb, Coulomb base friction, FP32 mixed precision, USL.  A "step" is
-one explicit MPM time step of the whole path (binning sort, P2G, nodal solve
-with boundary conditions, G2P with stress update and relocation).
+Default workload: the large 3D slope -- 800 x 200 x 200 hexahedra of 0.05 m,
+a 45-degree slope section filled with 8 particles per cell (63.9M particles),
+Mohr-Coulomb with lognormal per-cell cohesion, fixed base, roller sides, FP32
+mixed precision, USL.  A "step" is one explicit MPM time step of the whole
+path (binning, P2G, nodal solve with boundary conditions, G2P with the stress
+update and relocation, and the FP64 apex-band return).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+                  [--workload slope|column3d|...] [--advance A] [--detail-out PATH]
 
-Timing: W untimed steps, then K steps each bracketed by CUDA events on the
-library's stream, with a 256 MiB buffer written between steps (L2 flushed);
-max over ranks.  Prints one JSON line (rank 0).  With N > 1 (torchrun) every
-rank runs an independent replica of the workload on its own GPU (replicas
-only: the path has no cross-instance exchange), so value = N x per-rank work
-/ max time ("weak" scaling).
+Timing: A untimed steps bring the run into its middle (the slope workload
+runs 2000 steps; A = 1000 by default), then W untimed warm-up steps, then K
+steps each bracketed by CUDA events on the library's stream, with a 256 MiB
+buffer written between steps (the L2 flushed); max over ranks.  Prints one
+JSON line (rank 0).  With N > 1 (torchrun) every rank runs an independent
+replica of the workload on its own GPU (replicas only: the path has no
+cross-instance exchange), so value = N x per-rank work / max time ("weak"
+scaling).
 
-Beside the headline the line carries: the plain FP64 GPU step on the same
-workload ("fp64_plain"); the same workload with the other update order, USF
-("other_scheme"); an end-to-end run through the C-ABI from host
-buffers ("e2e"); 256 independent 2D granular columns (5k-60k particles each)
-advanced by batched steps, against stepping them one at a time ("batched");
-a serving session ("serving"): a Poisson stream (20/s) of mixed 2D/3D column
-and slope requests of 1e4-4e6 particles served with continuous batching in
-FP32 and one at a time in plain FP64, with p50/p99 per-step and end-to-end
-latency; and the FP64 CPU oracle on a bounded sample ("cpu_baseline").
+Beside the headline the line carries the dominant kernel's and the whole
+step's HBM roofline (with the plain FP64 GPU step on the same workload), the
+other update order (USF), an end-to-end run through the C-ABI from pinned
+host buffers ("e2e"), the FP64 CPU oracle on a bounded sample
+("cpu_baseline") and the FP32 error against it after enough steps for the
+displacements to stand above the offset's resolution ("accuracy"), and short
+summaries of 256 batched 2D columns ("batched") and of a serving session
+("serving").  --detail-out writes the full detail of these as JSON.
 
 --impl reference times the FP64 CPU oracle (the parity reference) on the
-host cores on the same workload and metric.
+host cores on a bounded sample of the same workload and metric.
 """
 from __future__ import annotations
 
@@ -65,17 +68,35 @@ KERNEL_SRC = os.path.join(ROOT, "paper_1909_13380_gb300", "csrc", "mpm_fp32.cu")
 
 
 def make_workload(name: str):
+    if name == "slope":
+        return W.slope3d()
     if name == "column3d":
         return W.column3d()
     if name == "column3d_small":
         return W.column3d(ncells=(40, 16, 24), col_cells=(12, 12, 12))
     if name == "bar":
         return W.elastic_bar(precision=W.FP32_MIXED)
-    if name == "slope":
-        return W.slope3d()
     if name == "slope_1_64":
         return W.slope3d(ncells=(200, 50, 50), h=0.2, crest=8.0, plateau=8.5)
+    if name == "slope_slab":
+        return slope_slab()
     raise SystemExit(f"unknown workload {name}")
+
+
+def slope_slab():
+    """The bounded CPU sample of the slope: the same cell size (0.05 m),
+    8 particles per cell, material, lognormal cohesion and walls, on a 2 m
+    slope section four cells wide (roller sides, so a slab of the extruded
+    slope); 76,800 particles."""
+    wl = W.slope3d(ncells=(160, 4, 48), h=0.05, crest=2.0, plateau=2.0)
+    wl.name = "slope_3d_slab_160x4x48_crest2m"
+    return wl
+
+
+# The CPU sample of each workload (the oracle cannot run the full slope:
+# one oracle step of its 63.9M particles takes about a minute on one core).
+CPU_SAMPLE = {"slope": "slope_slab", "slope_1_64": "slope_1_64", "column3d": "column3d",
+              "column3d_small": "column3d_small", "bar": "bar", "slope_slab": "slope_slab"}
 
 
 # Algorithmic bytes per particle (what the method must move once: each
@@ -98,19 +119,6 @@ def load_peak():
             return float(json.load(f)["hbm_gbs"]), "measured"
     except Exception:
         return FALLBACK_HBM_GBS, "fallback"
-
-
-def binning_launches(wl) -> int:
-    """Kernels of one binning: a tile scan (one CTA per mesh, or one pass with
-    look-back), the arrival bucketing and the per-tile counting sort."""
-    return 3
-
-
-def apex_launches(wl) -> int:
-    """The FP64 apex-band kernel after each stress update, for Mohr-Coulomb
-    materials with cohesion (the band is empty without it)."""
-    m = wl.material
-    return 1 if m["model"] == W.MOHR_COULOMB and (wl.coh is not None or m["c"] != 0.0) else 0
 
 
 def kernel_hash() -> str:
@@ -218,23 +226,6 @@ def barrier(world: int):
         dist.barrier()
 
 
-def cpu_oracle_rate(wl, budget_s: float, max_steps: int):
-    """Oracle particle-steps/s on the host: steps of the full workload from its
-    initial state until `budget_s` of CPU time or `max_steps` steps.  Returns
-    the rate, the steps, the seconds and the oracle (for the accuracy check)."""
-    import oracle
-    o = oracle.from_workload(wl)
-    t0 = time.perf_counter()
-    k = 0
-    while k < max_steps:
-        o.step(1)
-        k += 1
-        if time.perf_counter() - t0 >= budget_s:
-            break
-    dt = time.perf_counter() - t0
-    return wl.n * k / dt, k, dt, o
-
-
 def _oracle_replica(args):
     """One replica of the oracle (a spawned process): the named workload's
     first steps until the time budget; returns (particles, steps, seconds)."""
@@ -272,44 +263,83 @@ def _rel_l2(a, b):
     return float(np.linalg.norm(a - b) / den) if den > 0 else float(np.linalg.norm(a))
 
 
-def accuracy_vs_oracle(wl, o, k, stream):
-    """Relative L2 errors of the GPU state after the oracle's k steps from the
-    same initial state: displacement, velocity, stress, volume change, and the
-    count of particles whose cell differs."""
+def _max_over_rms(a, b):
+    """Largest per-particle error norm over the RMS of the reference's
+    per-particle norms (a fault confined to a few particles shows here,
+    where a relative L2 over all of them dilutes it)."""
+    a = np.asarray(a, np.float64).reshape(len(a), -1)
+    b = np.asarray(b, np.float64).reshape(len(b), -1)
+    rms = float(np.sqrt(np.mean(np.sum(b * b, axis=1))))
+    e = np.sqrt(np.sum((a - b) ** 2, axis=1))
+    return float(e.max() / rms) if rms > 0 else float(e.max())
+
+
+def cpu_leg(wl_name, budget_s, max_steps, sptr):
+    """The CPU baseline: the FP64 oracle on the workload's bounded sample,
+    one thread (its state after the timed steps also gives the FP32 and FP64
+    GPU error on that sample), then one replica per host core."""
+    import oracle
     from paper_1909_13380_gb300 import mpm
-    d = wl.dim
-    s = o.state
+    name = CPU_SAMPLE[wl_name]
+    cwl = make_workload(name)
+    o = oracle.from_workload(cwl)
+    t0 = time.perf_counter()
+    k = 0
+    while k < max_steps:
+        o.step(1)
+        k += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    rate = cwl.n * k / dt
+    # accuracy of both GPU precisions against the oracle's k steps
+    d = cwl.dim
+    st = o.state
     cells = o.cells()
     nc = o.mesh.n
     ref_cell = np.where(cells[:, 0] >= 0, cells[:, 0] + nc[0] * (cells[:, 1] + nc[1] * cells[:, 2]), -1)
-    out = {"reference": "FP64 CPU oracle, same seeded initial state", "steps": k,
-           "note": "state errors (pos, vel, stress, vol) and increments since step 0 (disp, dvol); the "
-                   "GPU's increments are taken from its own step-0 state, which for FP32 holds the inputs "
-                   "rounded (offset to 3e-8 cells, V0 = m/rho from an FP32 mass)"}
-    for name, prec in (("fp32_mixed", W.FP32_MIXED), ("fp64_plain", W.FP64_PLAIN)):
-        with mpm.Simulation(wl, precision=prec, stream=stream) as g:
+    acc = {"workload": cwl.name, "particles": cwl.n, "steps": k,
+           "note": "relative L2 of the state and of its increments since step 0 (disp, dvol), and the largest "
+                   "per-particle error over the field's RMS (max_rms); the FP32 offset resolves 3e-8 cells, "
+                   "so disp errors below ~1e-7 cells x steps^-2 are that resolution, not arithmetic"}
+    for pname, prec in (("fp32_mixed", W.FP32_MIXED), ("fp64_plain", W.FP64_PLAIN)):
+        with mpm.Simulation(cwl, precision=prec, stream=sptr) as g:
             s0, _ = g.read(("pos", "vol"))
             g.step(k)
-            snap, st = g.read(("pos", "vel", "stress", "vol", "cell"))
-        out[name] = {
-            "pos_rel_l2": _rel_l2(snap["pos"], s.x[:, :d]),
-            "vel_rel_l2": _rel_l2(snap["vel"], s.v[:, :d]),
-            "stress_rel_l2": _rel_l2(snap["stress"], s.sig),
-            "vol_rel_l2": _rel_l2(snap["vol"], s.vol),
-            "disp_rel_l2": _rel_l2(snap["pos"] - s0["pos"], s.x[:, :d] - wl.pos),
-            "dvol_rel_l2": _rel_l2(snap["vol"] - s0["vol"], s.vol - wl.vol),
+            snap, gst = g.read(("pos", "vel", "stress", "vol", "cell"))
+        live = (snap["cell"] >= 0) & (ref_cell >= 0)
+        disp_g, disp_r = (snap["pos"] - s0["pos"])[live], (st.x[:, :d] - cwl.pos)[live]
+        acc[pname] = {
+            "disp": _rel_l2(disp_g, disp_r), "disp_max_rms": _max_over_rms(disp_g, disp_r),
+            "vel": _rel_l2(snap["vel"][live], st.v[live, :d]),
+            "vel_max_rms": _max_over_rms(snap["vel"][live], st.v[live, :d]),
+            "stress": _rel_l2(snap["stress"][live], st.sig[live]),
+            "stress_max_rms": _max_over_rms(snap["stress"][live], st.sig[live]),
+            "dvol": _rel_l2((snap["vol"] - s0["vol"])[live], (st.vol - cwl.vol)[live]),
             "cells_differing": int((snap["cell"] != ref_cell).sum()),
-            "status": mpm.STATUS_NAMES.get(st, st),
+            "status": mpm.STATUS_NAMES.get(gst, gst),
         }
-    return out
+    del o
+    rate_all, cores, ks = cpu_oracle_all_cores(name, budget_s, max_steps)
+    what = (f"the full {cwl.n}-particle workload" if name == wl_name else
+            f"{cwl.name} ({cwl.n} particles), the bounded sample of {wl_name}")
+    cpu = {"value": rate_all, "unit": METRIC, "cores": cores, "kind": "oracle",
+           "sample": f"one replica of the FP64 oracle per host core ({cores}), each running the first "
+                     f"{min(ks)}-{max(ks)} steps of {what} from its initial state for about {budget_s:g} s; "
+                     f"aggregate particle-steps over the slowest replica's time",
+           "single_thread": {"value": rate, "cores": 1, "steps": k, "seconds": dt}}
+    return cpu, acc
 
 
 def run_reference(args):
+    """The oracle as it stands, one thread, on the bounded sample of the
+    workload; every step is one oracle step of the sample."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    wl = make_workload(args.workload)
     import oracle
+    name = CPU_SAMPLE[args.workload]
+    wl = make_workload(name)
     o = oracle.from_workload(wl)
     t_w0 = time.perf_counter()
     for _ in range(args.warmup):
@@ -323,16 +353,25 @@ def run_reference(args):
         o.step(1)
     dt = time.perf_counter() - t0
     value = wl.n * k_timed / dt
-    sample = (f"steps {args.warmup + 1}..{args.warmup + k_timed} of the full {wl.n}-particle workload, "
-              f"FP64 oracle, one thread" + ("" if k_timed == k else f" (capped at {k_timed} of {k} steps)"))
+    sample = (f"steps {args.warmup + 1}..{args.warmup + k_timed} of {wl.name} ({wl.n} particles"
+              + ("" if name == args.workload else f", the bounded sample of {args.workload}")
+              + "), FP64 oracle, one thread" + ("" if k_timed == k else f" (capped at {k_timed} of {k} steps)"))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
             "steps": k_timed, "warmup": args.warmup, "ms_per_step": 1e3 * dt / k_timed,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": wl.name, "particles": wl.n},
+            "data": "synthetic", "config": {"workload": make_workload_name(args.workload), "sample": wl.name,
+                                            "particles": wl.n},
             "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+WORKLOAD_NAMES = {"slope": "slope_3d_800x200x200"}   # built without its 63.9M particles
+
+
+def make_workload_name(name):
+    return WORKLOAD_NAMES[name] if name in WORKLOAD_NAMES else make_workload(name).name
 
 
 def run_batched(args, flush, stream):
@@ -344,7 +383,7 @@ def run_batched(args, flush, stream):
     wls = W.columns2d_batch(count=args.batch_count)
     ntot = sum(w.n for w in wls)
     sims = [mpm.Simulation(w, stream=C.c_void_p(stream.cuda_stream)) for w in wls]
-    b = mpm.mpm_batch_create(stream.cuda_stream)
+    b = mpm.mpm_batch_create(stream.cuda_stream, max_slots=len(sims))
     k = max(1, min(args.steps, 20))
     try:
         for s_ in sims:
@@ -360,6 +399,7 @@ def run_batched(args, flush, stream):
         stream.synchronize()
         ms = [a.elapsed_time(c) for a, c in ev]
         status = mpm.mpm_batch_poll(b, len(sims))
+        kernels = mpm.mpm_batch_step_kernels(b)
         for i in range(len(sims)):
             mpm.mpm_batch_evict(b, i)
         # the same meshes stepped one at a time (each mesh its own launches)
@@ -382,7 +422,7 @@ def run_batched(args, flush, stream):
             "one_at_a_time": {"value": ntot / (ms_seq * 1e-3), "ms_per_step_of_all": ms_seq},
             "batching_speedup": ms_seq / ms_step,
             "failed": int(sum(1 for x in status if x != mpm.MPM_OK)),
-            "gpu_launches_per_batched_step": max(binning_launches(w) for w in wls) + 3 + max(apex_launches(w) for w in wls)}
+            "gpu_launches_per_batched_step": kernels}
 
 
 def serve_session(reqs, chunk):
@@ -429,6 +469,43 @@ def run_serving(args):
     return out
 
 
+
+
+def timed_steps(sim, k, stream, flush):
+    """k steps of sim, each bracketed by CUDA events on the library's stream,
+    the L2 flushed between them; returns the per-step milliseconds."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+    with torch.cuda.stream(stream):
+        for i in range(k):
+            ev[i][0].record(stream)
+            sim.step(1)
+            ev[i][1].record(stream)
+            flush.zero_()
+    stream.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def advance(sim, steps, stream, chunk=200):
+    """Untimed steps, enqueued in chunks."""
+    import torch
+    with torch.cuda.stream(stream):
+        done = 0
+        while done < steps:
+            k = min(chunk, steps - done)
+            sim.step(k)
+            done += k
+    stream.synchronize()
+
+
+def pinned_like(a):
+    import torch
+    t = torch.empty(a.shape, dtype=torch.float64, pin_memory=True)
+    out = t.numpy()
+    out[...] = a
+    return out, t
+
+
 def run_gb300(args):
     import torch
     from paper_1909_13380_gb300 import mpm
@@ -443,40 +520,32 @@ def run_gb300(args):
     stream = torch.cuda.Stream(device=device)
     sptr = C.c_void_p(stream.cuda_stream)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
+    detail = {}
 
     # ---- device-timed steps -------------------------------------------------
-    # The timed steps run the step graph as a user gets it (kernels chained by
-    # programmatic dependent launch); the per-kernel phase times come from a
-    # second pass of the same number of steps whose graph carries event nodes
-    # between the kernels (which also serialise them as plain launches).
+    # The run is first brought to its middle (A untimed steps), then W warm-up
+    # steps, then the K timed steps of the step graph as a user gets it
+    # (kernels chained by programmatic dependent launch).  Per-kernel phase
+    # times come from a second pass of K steps whose graph carries event
+    # nodes between the kernels (which also serialises them).
     sim = mpm.Simulation(wl, stream=sptr)
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            sim.step(1)
-            flush.zero_()
-    stream.synchronize()
+    advance(sim, args.advance, stream)
+    timed_steps(sim, args.warmup, stream, flush)
+    per_step_kernels = mpm.mpm_step_kernels(sim.h)
     sampler = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
     sampler.start()
     barrier(world)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    with torch.cuda.stream(stream):
-        for i in range(args.steps):
-            ev[i][0].record(stream)
-            sim.step(1)
-            ev[i][1].record(stream)
-            flush.zero_()
-    stream.synchronize()
+    step_ms = timed_steps(sim, args.steps, stream, flush)
     barrier(world)
     clocks = sampler.stop()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
     t_dev = sum(step_ms) / 1e3
+    first = args.advance + args.warmup + 1
     mpm.mpm_set_phase_timing(sim.h, True)
     phases = []
     with torch.cuda.stream(stream):
-        for i in range(min(args.warmup, 3) + args.steps):
+        for i in range(args.steps):
             sim.step(1)
-            if i >= min(args.warmup, 3):
-                phases.append(mpm.mpm_phase_times(sim.h))
+            phases.append(mpm.mpm_phase_times(sim.h))
             flush.zero_()
     stream.synchronize()
     status = sim.sync()
@@ -484,8 +553,7 @@ def run_gb300(args):
         raise SystemExit(f"step failed: {mpm.STATUS_NAMES.get(status, status)}")
     t_max = reduce_max(t_dev, world, device)
     value = world * wl.n * args.steps / t_max
-    ph = np.array(phases)
-    ph_mean = ph.mean(axis=0)
+    ph_mean = np.array(phases).mean(axis=0)
     names = ["binning", "p2g", "node", "g2p"] if wl.scheme == W.USL else \
         ["binning", "p2g_mom", "node_v", "g2p_stress", "p2g_force", "node_a", "g2p_advect"]
     ab = algorithmic_bytes(wl.dim, wl.coh is not None)
@@ -499,24 +567,16 @@ def run_gb300(args):
     mpm.mpm_set_phase_timing(sim.h, False)
     sim.close()
 
-    # ---- plain FP64 GPU step on the same workload ---------------------------
+    # ---- plain FP64 GPU step on the same workload (from its initial state) --
     fp64 = None
     if not args.no_fp64:
         k64 = max(1, min(args.steps, 10))
         s64 = mpm.Simulation(wl, precision=W.FP64_PLAIN, stream=sptr)
-        with torch.cuda.stream(stream):
-            s64.step(1)
-            e64 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k64)]
-            for i in range(k64):
-                e64[i][0].record(stream)
-                s64.step(1)
-                e64[i][1].record(stream)
-                flush.zero_()
-        stream.synchronize()
-        ms64 = sum(a.elapsed_time(b) for a, b in e64) / k64
+        timed_steps(s64, 1, stream, flush)
+        ms64 = sum(timed_steps(s64, k64, stream, flush)) / k64
         s64.close()
-        fp64 = {"value": wl.n / (ms64 * 1e-3), "unit": METRIC, "ms_per_step": ms64, "steps": k64,
-                "fp32_mixed_speedup": (wl.n * args.steps / t_dev) / (wl.n / (ms64 * 1e-3))}
+        fp64 = {"ms_per_step": ms64, "value": wl.n / (ms64 * 1e-3), "steps": k64,
+                "fp32_mixed_speedup": ms64 / (1e3 * t_dev / args.steps)}
 
     # ---- the other update order (USF when the headline is USL) --------------
     other = None
@@ -524,91 +584,99 @@ def run_gb300(args):
         osch = W.USF if wl.scheme == W.USL else W.USL
         ko = max(1, min(args.steps, 20))
         so = mpm.Simulation(wl, scheme=osch, stream=sptr)
-        with torch.cuda.stream(stream):
-            so.step(args.warmup)
-            eo = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(ko)]
-            for i in range(ko):
-                eo[i][0].record(stream)
-                so.step(1)
-                eo[i][1].record(stream)
-                flush.zero_()
-        stream.synchronize()
-        mso = sum(a.elapsed_time(b) for a, b in eo) / ko
+        advance(so, args.advance, stream)
+        timed_steps(so, args.warmup, stream, flush)
+        mso = sum(timed_steps(so, ko, stream, flush)) / ko
         sto = so.sync()
+        other = {"scheme": "USF" if osch == W.USF else "USL", "value": wl.n / (mso * 1e-3), "ms_per_step": mso,
+                 "steps": ko, "timed_steps": f"{args.advance + args.warmup + 1}..{args.advance + args.warmup + ko}",
+                 "status": mpm.STATUS_NAMES.get(sto, sto), "gpu_launches_per_step": mpm.mpm_step_kernels(so.h)}
         so.close()
-        other = {"scheme": "USF" if osch == W.USF else "USL", "value": wl.n / (mso * 1e-3), "unit": METRIC,
-                 "ms_per_step": mso, "steps": ko, "status": mpm.STATUS_NAMES.get(sto, sto),
-                 "gpu_launches_per_step": binning_launches(wl) + (6 if osch == W.USF else 3) + apex_launches(wl)}
 
-    # ---- end to end through the C-ABI with host buffers ---------------------
+    # ---- end to end through the C-ABI with pinned host buffers ---------------
     e2e = None
     if not args.no_e2e:
-        ns = 6 if wl.dim == 3 else 4
-        h2d = wl.n * 4 * (2 + 2 * wl.dim + 2 * ns + 3 + (1 if wl.coh is not None else 0))
-        d2h = wl.n * 8 * (2 * wl.dim + 6 + 6 + 1 + 1 + 1)
+        fields = ("pos", "vel", "stress")
+        pin_in = {k: pinned_like(getattr(wl, k)) for k in ("pos", "vel", "vol") + (("coh",) if wl.coh is not None
+                                                                                     else ())}
+        wl_pinned = dataclasses.replace(wl, **{k: v[0] for k, v in pin_in.items()})
+        pin_out = {k: pinned_like(np.zeros((wl.n, wl.dim if k != "stress" else 6))) for k in fields}
+        out = {k: v[0] for k, v in pin_out.items()}
+        h2d = sum(v[0].nbytes for v in pin_in.values())
+        d2h = sum(a.nbytes for a in out.values())
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        s = mpm.Simulation(wl, stream=sptr)
+        s = mpm.Simulation(wl_pinned, stream=sptr)
         s.step(args.steps)
-        snap, st = s.read()
+        snap, st = s.read(fields, out=out)
         s.close()
         t1 = time.perf_counter()
         e2e = {"value": wl.n * args.steps / (t1 - t0), "unit": METRIC,
                "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(d2h / args.steps),
-               "seconds": t1 - t0, "includes": "mesh creation, host->device upload, K steps, device->host read"}
+               "seconds": round(t1 - t0, 4),
+               "includes": "mesh creation, upload of the FP64 inputs from pinned host memory, K steps from the "
+                           "initial state, read of positions, velocities and stresses into pinned host memory"}
 
     # ---- batched small meshes and the serving loop (rank 0) -----------------
     batched = serving = None
     if rank == 0 and not args.no_batch:
         batched = run_batched(args, flush, stream)
+        detail["batched"] = batched
     if rank == 0 and not args.no_serving:
         serving = run_serving(args)
+        detail["serving"] = serving
 
-    # ---- CPU oracle baseline (rank 0, N = 1) ---------------------------------
+    # ---- CPU oracle baseline and accuracy (rank 0, N = 1) ---------------------
     cpu = accuracy = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        # one oracle step of the 63.9M-particle slope takes about a minute on
-        # one core: its bounded sample is the same slope at 1/64 volume
-        cwl = make_workload("slope_1_64") if args.workload == "slope" else wl
-        rate, k, dt, o = cpu_oracle_rate(cwl, budget_s=args.cpu_budget, max_steps=args.steps)
-        what = (f"the full {cwl.n}-particle workload" if cwl is wl else
-                f"the {cwl.n}-particle slope at 1/64 volume ({cwl.name}), standing in for the full slope")
-        accuracy = accuracy_vs_oracle(cwl, o, k, sptr)
-        del o
-        cname = "slope_1_64" if args.workload == "slope" else args.workload
-        rate_all, cores, ks = cpu_oracle_all_cores(cname, args.cpu_budget, args.steps)
-        cpu = {"value": rate_all, "unit": METRIC, "cores": cores, "kind": "oracle",
-               "sample": f"one replica of the FP64 oracle per host core ({cores}), each running the first "
-                         f"{min(ks)}-{max(ks)} steps of {what} from its initial state for about "
-                         f"{args.cpu_budget:g} s; aggregate particle-steps over the slowest replica's time",
-               "single_thread": {"value": rate, "cores": 1,
-                                 "sample": f"first {k} steps of {what}, one thread, {dt:.1f} s"}}
-        if cwl is not wl:
-            accuracy["workload"] = cwl.name
+        cpu, accuracy = cpu_leg(args.workload, args.cpu_budget, args.cpu_steps, sptr)
+        detail["accuracy"] = accuracy
 
     if rank == 0:
-        # binning (three kernels); then p2g_tile, node_tile, g2p
-        # (USF: twice each)
-        per_step = binning_launches(wl) + (3 if wl.scheme == W.USL else 6) + apex_launches(wl)
+        def short_serving(sv):
+            if not sv:
+                return None
+            out = {"requests": sv["requests"], "arrival_rate_per_s": sv["arrival_rate_per_s"]}
+            for k in ("fp32_continuous_batching", "fp64_one_at_a_time"):
+                r = sv[k]
+                out[k] = {"step_ms_p50": r["step_ms"]["p50"], "step_ms_p99": r["step_ms"]["p99"],
+                          "e2e_s_p50": r["e2e_s"]["p50"], "e2e_s_p99": r["e2e_s"]["p99"],
+                          "utilisation": r["utilisation"], "failed": r["failed"]}
+            return out
+
         line = {
             "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": wl.name, "particles": wl.n, "scheme": "USL" if wl.scheme == W.USL else "USF",
-                       "precision": "fp32_mixed", "l2": "flushed between timed steps (256 MiB write)",
+                       "precision": "fp32_mixed", "timed_steps": f"{first}..{first + args.steps - 1}",
+                       "l2": "flushed between timed steps (256 MiB write)",
                        "parallelism": "replicas" if world > 1 else "single"},
-            "roofline": {"bound": "hbm", "kernel": {"p2g": "p2g_tile", "g2p": "g2p"}[dom], "achieved": achieved, "peak": peak,
-                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                         "traffic_source": traffic_src,
-                         "algorithmic_bytes_per_particle": ab[dom], "ms_per_launch": kernels[dom]},
-            "step_roofline": {"achieved": step_gbs, "frac": step_gbs / peak, "unit": "GB/s",
-                              "algorithmic_bytes_per_particle": ab["step"]},
-            "phases_ms": dict(zip(names, [float(x) for x in ph_mean])),
-            "clocks": clocks, "gpu_launches": per_step * args.steps,
-            "e2e": e2e, "fp64_plain": fp64, "other_scheme": other, "batched": batched, "serving": serving,
-            "cpu_baseline": cpu,
-            "accuracy": accuracy,
+            "roofline": {"bound": "hbm", "kernel": {"p2g": "p2g_tile", "g2p": "g2p"}[dom], "achieved": achieved,
+                         "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": traffic, "traffic_source": traffic_src,
+                         "algorithmic_bytes_per_particle": ab[dom], "ms_per_launch": kernels[dom],
+                         "step_achieved": step_gbs, "step_frac": step_gbs / peak,
+                         "step_bytes_per_particle": ab["step"],
+                         "fp64_plain_ms_per_step": fp64["ms_per_step"] if fp64 else None,
+                         "fp32_vs_fp64_plain": fp64["fp32_mixed_speedup"] if fp64 else None},
+            "phases_ms": dict(zip(names, [round(float(x), 5) for x in ph_mean])),
+            "clocks": clocks, "gpu_launches": per_step_kernels * args.steps,
+            "e2e": e2e, "cpu_baseline": cpu,
+            "accuracy": None if not accuracy else {
+                "sample": accuracy["workload"], "steps": accuracy["steps"],
+                **{p: {k: accuracy[p][k] for k in ("disp", "vel", "stress", "dvol", "stress_max_rms",
+                                                   "cells_differing")} for p in ("fp32_mixed", "fp64_plain")}},
+            "other_scheme": None if not other else {k: other[k] for k in ("scheme", "ms_per_step", "value")},
+            "batched": None if not batched else {k: batched[k] for k in ("particles", "value", "ms_per_batched_step",
+                                                                       "batching_speedup")},
+            "serving": short_serving(serving),
         }
+        detail.update({"fp64_plain": fp64, "other_scheme": other, "e2e": e2e, "phases_ms_all": phases,
+                       "step_ms": step_ms})
+        if args.detail_out:
+            with open(args.detail_out, "w") as f:
+                json.dump(detail, f, indent=1, default=float)
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -621,14 +689,15 @@ def main(argv=None):
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--advance", type=int, default=1000, help="untimed steps before the warm-up")
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--workload", default="column3d",
-                    choices=["column3d", "column3d_small", "bar", "slope", "slope_1_64"])
+    ap.add_argument("--workload", default="slope", choices=sorted(CPU_SAMPLE))
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-usf", action="store_true", help="skip the other update order (USF)")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--cpu-steps", type=int, default=200, help="most oracle steps of the CPU sample")
     ap.add_argument("--no-batch", action="store_true", help="skip the 256 batched 2D columns")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--no-serving", action="store_true", help="skip the serving session")
@@ -636,6 +705,7 @@ def main(argv=None):
     ap.add_argument("--serve-step-scale", type=float, default=1.0 / 50)
     ap.add_argument("--serve-chunk", type=int, default=16)
     ap.add_argument("--serve-rates", default="", help="also serve the requests at these arrival rates, e.g. 2,5,10,20")
+    ap.add_argument("--detail-out", default="", help="write the full detail of every leg as JSON here")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3

@@ -152,8 +152,9 @@ mpm_status mpm_read_particles(mpm_handle h, double *pos, double *vel, double *st
 
 /* FP64 global sums over live particles (deterministic order): out[0] mass,
  * out[1..3] momentum, out[4] kinetic energy, out[5] strain energy
- * sum 1/2 V sigma:eps, out[6] number of live particles.  Synchronises. */
-mpm_status mpm_conservation(mpm_handle h, double out[7]);
+ * sum 1/2 V sigma:eps, out[6] number of live particles, out[7] total volume
+ * sum V.  Synchronises. */
+mpm_status mpm_conservation(mpm_handle h, double out[8]);
 
 /* Particle binning (step a1 of the path; ISOPARAMETRIC MESH: locating the
  * particles in cells), FP32_MIXED handles only.  Runs the binning of the
@@ -198,30 +199,55 @@ mpm_status mpm_footprint(const mpm_mesh_desc *desc, int64_t n, int32_t has_cohes
  * replay.  Meshes share no data, so each mesh's result is bit-identical to
  * stepping it alone.  The paper has no batching; it runs one simulation per
  * process (CODE OVERVIEW, DATA STRUCTURES).
- *   mpm_batch_create   stream: cudaStream_t for all batch work (NULL: a
- *                      private stream)
+ *   mpm_batch_create   hbm_budget_bytes: device bytes the admitted meshes may
+ *                      hold together, counted as mpm_footprint of each mesh
+ *                      at its admission (0: no memory budget); max_slots:
+ *                      most meshes admitted at once (>= 1); stream:
+ *                      cudaStream_t for all batch work (NULL: a private
+ *                      stream).  MPM_ERR_ARG for a negative budget or
+ *                      max_slots < 1.
  *   mpm_batch_admit    adds an idle FP32_MIXED mesh (its pending work is
  *                      finished first); from then on the mesh's own calls
  *                      run on the batch stream and mpm_step on it returns
  *                      MPM_ERR_STATE until it is evicted.  *slot receives a
- *                      stable slot id.
+ *                      stable slot id in 0..max_slots-1.  MPM_ERR_OOM when
+ *                      every slot is taken or the mesh's footprint exceeds
+ *                      what the budget has left; the mesh and the batch are
+ *                      then unchanged and the error is not latched on the
+ *                      mesh (admit it later, after an eviction).
+ *   mpm_batch_room     what is left: *free_bytes of the budget (INT64_MAX
+ *                      without a budget) and *free_slots; either may be NULL.
  *   mpm_batch_evict    removes the mesh of a slot (after the batch's pending
- *                      work); the mesh keeps its state and can be read,
- *                      stepped alone or admitted again.
+ *                      work) and returns its footprint to the budget; the
+ *                      mesh keeps its state and can be read, stepped alone or
+ *                      admitted again.
  *   mpm_batch_step     enqueues nsteps batched steps of every admitted mesh.
  *   mpm_batch_poll     synchronises and writes, for slots 0..nslots-1, the
  *                      latched status of the slot's mesh (MPM_OK,
- *                      MPM_ERR_LEFT_MESH, MPM_ERR_NONFINITE) or
- *                      MPM_ERR_STATE for an empty slot.
+ *                      MPM_ERR_LEFT_MESH, MPM_ERR_NONFINITE, MPM_ERR_TIMEOUT)
+ *                      or MPM_ERR_STATE for an empty slot, and, if
+ *                      slot_steps is not NULL, the batched steps the slot's
+ *                      mesh has taken since its admission (-1 for an empty
+ *                      slot).
+ *   mpm_batch_step_kernels  kernel launches of one batched step: the kernel
+ *                      nodes of the last captured batched-step graph
+ *                      (MPM_ERR_STATE before the first batched step).
  *   mpm_batch_destroy  evicts every mesh (they stay valid) and frees the batch.
  * A batch is not thread-safe. */
 typedef struct mpm_batch_ctx *mpm_batch;
-mpm_status mpm_batch_create(void *stream, mpm_batch *out);
+mpm_status mpm_batch_create(int64_t hbm_budget_bytes, int32_t max_slots, void *stream, mpm_batch *out);
 mpm_status mpm_batch_admit(mpm_batch b, mpm_handle mesh, int32_t *slot);
+mpm_status mpm_batch_room(mpm_batch b, int64_t *free_bytes, int32_t *free_slots);
 mpm_status mpm_batch_evict(mpm_batch b, int32_t slot);
 mpm_status mpm_batch_step(mpm_batch b, int64_t nsteps);
-mpm_status mpm_batch_poll(mpm_batch b, int32_t nslots, int32_t *slot_status);
+mpm_status mpm_batch_poll(mpm_batch b, int32_t nslots, int32_t *slot_status, int64_t *slot_steps);
+mpm_status mpm_batch_step_kernels(mpm_batch b, int32_t *kernels);
 mpm_status mpm_batch_destroy(mpm_batch b);
+
+/* Kernel launches one mpm_step of h enqueues (measurement support): the
+ * kernel nodes of the step graph the library captured for h, FP32_MIXED
+ * only.  MPM_ERR_STATE before the first captured step or for FP64_PLAIN. */
+mpm_status mpm_step_kernels(mpm_handle h, int32_t *kernels);
 
 /* Human-readable description of the last error on h (never NULL). */
 const char *mpm_last_error(mpm_handle h);
@@ -249,9 +275,10 @@ mpm_status mpm_sort_keys(const uint32_t *d_keys, int32_t *d_perm, int64_t n, int
  *   22 MiB, held on every GPU that loads the library until the process
  *   exits), so this call allocates and frees nothing.  n above
  *   MPM_SORT_STATIC_MAX_KEYS is rejected with MPM_ERR_ARG before any device
- *   work.  The first call on a device looks up the array's device address
- *   (cudaGetSymbolAddress) with that device current; make that first call
- *   before any stream capture.
+ *   work.  Every call looks up the array's device address in the current
+ *   device's context (cudaGetSymbolAddress); the first call on a device also
+ *   loads the library's device code there, so make that first call before
+ *   any stream capture.
  *   The call only enqueues work on `stream` and returns; d_perm is ready
  *   when the stream reaches that point.  All calls share the one array, so
  *   calls whose work overlaps on the GPU (different streams, or different

@@ -184,6 +184,7 @@ struct mpm_ctx {
   GroupDev grp_bin;   // the same with scratch binning outputs (mpm_read_binning)
   bool grp_valid = false;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  int32_t graph_kernels = -1;  // kernel nodes of the last captured step graph
   bool timing = false;
   bool timed_step = false;
   cudaEvent_t ev[MPM_MAX_PHASES + 1] = {};
@@ -200,7 +201,13 @@ struct mpm_batch_ctx {
   cudaStream_t st = nullptr;
   bool own_stream = false;
   int nsm = 152;
+  int64_t budget = 0;            // device bytes the admitted meshes may hold together (0: no budget)
+  int64_t used = 0;              // footprints of the admitted meshes
+  int32_t max_slots = 1;
   std::vector<mpm_ctx *> slots;  // nullptr: empty slot
+  std::vector<int64_t> slot_bytes;  // footprint of the slot's mesh at admission
+  std::vector<int64_t> slot_steps;  // batched steps since admission
+  int32_t graph_kernels = -1;
   struct Group {
     int dim, scheme;
     std::vector<mpm_ctx *> mem;
@@ -310,6 +317,20 @@ void destroy_graphs(cudaGraphExec_t g[2]) {
       cudaGraphExecDestroy(g[i]);
       g[i] = nullptr;
     }
+}
+
+// Kernel nodes of a captured graph (-1 if the graph cannot be inspected).
+int32_t count_kernel_nodes(cudaGraph_t g) {
+  size_t n = 0;
+  if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess) return -1;
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (n && cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return -1;
+  int32_t k = 0;
+  for (size_t i = 0; i < n; ++i) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+  }
+  return k;
 }
 
 // Instance arguments of mesh h whose state is in buf[c].
@@ -494,7 +515,7 @@ mpm_status mpm_create_mesh(const mpm_mesh_desc *desc, mpm_handle *out) {
     }
     h->own_stream = true;
   }
-  cudaError_t e = cudaMalloc(&h->d_cons, sizeof(double) * (8 + 7 * 1024));
+  cudaError_t e = cudaMalloc(&h->d_cons, sizeof(double) * (8 + 8 * 1024));
   if (e == cudaSuccess) e = cudaMalloc(&h->d_status, sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int32_t));
   if (d.precision == MPM_FP32_MIXED && e == cudaSuccess) {
@@ -791,6 +812,7 @@ mpm_status mpm_step(mpm_handle h, int64_t nsteps) {
           cudaError_t e2 = cudaStreamEndCapture(h->st, &g);
           if (e != cudaSuccess) return cuda_fail(h, e, "step enqueue");
           CK(e2, "graph capture");
+          h->graph_kernels = count_kernel_nodes(g);
           e = cudaGraphInstantiate(&h->graph[cur], g, 0);
           cudaGraphDestroy(g);
           CK(e, "graph instantiate");
@@ -940,12 +962,12 @@ mpm_status mpm_read_particles(mpm_handle h, double *pos, double *vel, double *st
   return device_status(h);
 }
 
-mpm_status mpm_conservation(mpm_handle h, double out[7]) {
+mpm_status mpm_conservation(mpm_handle h, double out[8]) {
   mpm_status s0 = check_handle(h);
   if (s0 != MPM_OK) return s0;
   if (!out) return fail(h, MPM_ERR_ARG, "conservation: null out");
   if (h->n == 0) {
-    for (int i = 0; i < 7; ++i) out[i] = 0.0;
+    for (int i = 0; i < 8; ++i) out[i] = 0.0;
     return device_status(h);
   }
   if (h->d.precision == MPM_FP32_MIXED)
@@ -955,9 +977,9 @@ mpm_status mpm_conservation(mpm_handle h, double out[7]) {
   else
     CK(d64_conservation(h->L64, h->d_cons, h->d_cons + 8, h->st), "conservation");
   double tmp[8];
-  CK(cudaMemcpyAsync(tmp, h->d_cons, sizeof(double) * 7, cudaMemcpyDeviceToHost, h->st), "conservation");
+  CK(cudaMemcpyAsync(tmp, h->d_cons, sizeof(double) * 8, cudaMemcpyDeviceToHost, h->st), "conservation");
   CK(cudaStreamSynchronize(h->st), "conservation");
-  for (int i = 0; i < 7; ++i) out[i] = tmp[i];
+  for (int i = 0; i < 8; ++i) out[i] = tmp[i];
   return device_status(h);
 }
 
@@ -1016,6 +1038,13 @@ mpm_status mpm_phase_times(mpm_handle h, float *ms, int32_t *nphase) {
   return MPM_OK;
 }
 
+mpm_status mpm_step_kernels(mpm_handle h, int32_t *kernels) {
+  if (!h || !kernels) return MPM_ERR_ARG;
+  if (h->d.precision != MPM_FP32_MIXED || h->graph_kernels < 0) return MPM_ERR_STATE;
+  *kernels = h->graph_kernels;
+  return MPM_OK;
+}
+
 const char *mpm_last_error(mpm_handle h) {
   if (!h) return "null handle";
   return h->err.empty() ? "no error" : h->err.c_str();
@@ -1048,10 +1077,13 @@ mpm_status mpm_destroy(mpm_handle h) {
 
 // ---- batches ---------------------------------------------------------------
 
-mpm_status mpm_batch_create(void *stream, mpm_batch *out) {
+mpm_status mpm_batch_create(int64_t hbm_budget_bytes, int32_t max_slots, void *stream, mpm_batch *out) {
   if (!out) return MPM_ERR_ARG;
   *out = nullptr;
+  if (hbm_budget_bytes < 0 || max_slots < 1) return MPM_ERR_ARG;
   mpm_batch_ctx *b = new mpm_batch_ctx();
+  b->budget = hbm_budget_bytes;
+  b->max_slots = max_slots;
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -1074,22 +1106,38 @@ mpm_status mpm_batch_admit(mpm_batch b, mpm_handle h, int32_t *slot) {
   if (s0 != MPM_OK) return s0;
   if (h->d.precision != MPM_FP32_MIXED) return fail(h, MPM_ERR_ARG, "batch: FP32_MIXED meshes only");
   if (h->batch) return fail(h, MPM_ERR_STATE, "batch: the mesh is already admitted to a batch");
-  CK(cudaStreamSynchronize(h->st), "batch admit");
-  CK(cudaStreamSynchronize(b->st), "batch admit");
-  h->st_saved = h->st;
-  h->st = b->st;
-  h->batch = b;
+  // room: a free slot, and the mesh's footprint within what the budget has left
   int s = -1;
   for (size_t i = 0; i < b->slots.size(); ++i)
     if (!b->slots[i]) {
       s = (int)i;
       break;
     }
+  if (s < 0 && (int32_t)b->slots.size() >= b->max_slots) {
+    h->err = "batch admit: every slot is taken";
+    return MPM_ERR_OOM;  // not latched: the mesh is unchanged
+  }
+  int64_t fp = 0;
+  if (mpm_footprint(&h->d, h->n, h->has_coh ? 1 : 0, &fp) != MPM_OK) return fail(h, MPM_ERR_ARG, "batch admit: footprint");
+  if (b->budget > 0 && fp > b->budget - b->used) {
+    h->err = "batch admit: the mesh does not fit the batch's memory budget";
+    return MPM_ERR_OOM;  // not latched: the mesh is unchanged
+  }
+  CK(cudaStreamSynchronize(h->st), "batch admit");
+  CK(cudaStreamSynchronize(b->st), "batch admit");
+  h->st_saved = h->st;
+  h->st = b->st;
+  h->batch = b;
   if (s < 0) {
     s = (int)b->slots.size();
     b->slots.push_back(nullptr);
+    b->slot_bytes.push_back(0);
+    b->slot_steps.push_back(0);
   }
   b->slots[s] = h;
+  b->slot_bytes[s] = fp;
+  b->slot_steps[s] = 0;
+  b->used += fp;
   b->dirty = true;
   if (slot) *slot = s;
   return MPM_OK;
@@ -1102,6 +1150,8 @@ mpm_status mpm_batch_evict(mpm_batch b, int32_t slot) {
   h->st = h->st_saved;
   h->batch = nullptr;
   b->slots[slot] = nullptr;
+  b->used -= b->slot_bytes[slot];
+  b->slot_bytes[slot] = 0;
   b->dirty = true;
   return MPM_OK;
 }
@@ -1146,6 +1196,7 @@ mpm_status mpm_batch_step(mpm_batch b, int64_t nsteps) {
         if (g) cudaGraphDestroy(g);
         return MPM_ERR_CUDA;
       }
+      b->graph_kernels = count_kernel_nodes(g);
       e = cudaGraphInstantiate(&b->graph[p], g, 0);
       cudaGraphDestroy(g);
       if (e != cudaSuccess) return MPM_ERR_CUDA;
@@ -1155,12 +1206,17 @@ mpm_status mpm_batch_step(mpm_batch b, int64_t nsteps) {
     for (auto &gr : b->groups)
       for (mpm_ctx *h : gr.mem) h->cur ^= 1;
   }
+  for (auto &gr : b->groups)
+    for (int sl : gr.slot) b->slot_steps[sl] += nsteps;
   return MPM_OK;
 }
 
-mpm_status mpm_batch_poll(mpm_batch b, int32_t nslots, int32_t *slot_status) {
+mpm_status mpm_batch_poll(mpm_batch b, int32_t nslots, int32_t *slot_status, int64_t *slot_steps) {
   if (!b || nslots < 0 || (nslots > 0 && !slot_status)) return MPM_ERR_ARG;
   for (int i = 0; i < nslots; ++i) slot_status[i] = MPM_ERR_STATE;
+  if (slot_steps)
+    for (int i = 0; i < nslots; ++i)
+      slot_steps[i] = (i < (int)b->slots.size() && b->slots[i]) ? b->slot_steps[i] : -1;
   std::vector<int32_t> bits;
   for (auto &gr : b->groups) {
     if (b->dirty) break;
@@ -1184,6 +1240,22 @@ mpm_status mpm_batch_poll(mpm_batch b, int32_t nslots, int32_t *slot_status) {
       slot_status[i] = status_of_bits(st);
     }
   }
+  return MPM_OK;
+}
+
+mpm_status mpm_batch_room(mpm_batch b, int64_t *free_bytes, int32_t *free_slots) {
+  if (!b) return MPM_ERR_ARG;
+  int32_t taken = 0;
+  for (mpm_ctx *h : b->slots) taken += h ? 1 : 0;
+  if (free_bytes) *free_bytes = b->budget > 0 ? b->budget - b->used : INT64_MAX;
+  if (free_slots) *free_slots = b->max_slots - taken;
+  return MPM_OK;
+}
+
+mpm_status mpm_batch_step_kernels(mpm_batch b, int32_t *kernels) {
+  if (!b || !kernels) return MPM_ERR_ARG;
+  if (b->graph_kernels < 0) return MPM_ERR_STATE;
+  *kernels = b->graph_kernels;
   return MPM_OK;
 }
 

@@ -955,12 +955,12 @@ cudaError_t step_dim(int scheme, const GroupArgs &G, cudaEvent_t *ev, cudaStream
 // Conservation sums (FP64, deterministic two-level), export
 // ---------------------------------------------------------------------------
 constexpr int CONS_BLOCKS = 1024;
-constexpr int CONS_VALS = 7;
+constexpr int CONS_VALS = 8;  // mass, momentum (3), kinetic and strain energy, live count, volume
 
 template <int D>
 __global__ void cons_partial(int64_t n, PBuf P, uint32_t dead_key, float inv_rho, double *part) {
   constexpr int NS = nstress<D>();
-  double acc[CONS_VALS] = {0, 0, 0, 0, 0, 0, 0};
+  double acc[CONS_VALS] = {0, 0, 0, 0, 0, 0, 0, 0};
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
     if (P.key()[q] >= dead_key) continue;
     const double m = P.mass()[q];
@@ -979,6 +979,7 @@ __global__ void cons_partial(int64_t n, PBuf P, uint32_t dead_key, float inv_rho
     const double vol = m * (double)inv_rho * (1.0 + (double)P.jm1()[q]);
     acc[5] += 0.5 * vol * se;
     acc[6] += 1.0;
+    acc[7] += vol;
   }
   __shared__ double red[CONS_VALS][256];
 #pragma unroll

@@ -258,7 +258,7 @@ constexpr int CONS_BLOCKS = 1024;
 template <int D>
 __global__ void cons64_partial(D64Launch L, double *part) {
   constexpr int NS = nstress<D>();
-  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // mass, momentum (3), KE, SE, live count, volume
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < L.n; p += (int64_t)gridDim.x * blockDim.x) {
     if (!L.P.alive[p]) continue;
     const double m = L.P.mass[p];
@@ -276,24 +276,25 @@ __global__ void cons64_partial(D64Launch L, double *part) {
     for (int i = 0; i < NS; ++i) se += (i >= 3 ? 2.0 : 1.0) * L.P.sig[i][p] * L.P.eps[i][p];
     acc[5] += 0.5 * L.P.vol[p] * se;
     acc[6] += 1.0;
+    acc[7] += L.P.vol[p];
   }
-  __shared__ double red[7][256];
+  __shared__ double red[8][256];
 #pragma unroll
-  for (int c = 0; c < 7; ++c) red[c][threadIdx.x] = acc[c];
+  for (int c = 0; c < 8; ++c) red[c][threadIdx.x] = acc[c];
   __syncthreads();
   for (int o = 128; o > 0; o >>= 1) {
     if (threadIdx.x < o)
 #pragma unroll
-      for (int c = 0; c < 7; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + o];
+      for (int c = 0; c < 8; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x < 7) part[blockIdx.x * 7 + threadIdx.x] = red[threadIdx.x][0];
+  if (threadIdx.x < 8) part[blockIdx.x * 8 + threadIdx.x] = red[threadIdx.x][0];
 }
 
 __global__ void cons64_final(const double *part, int nb, double *out) {
-  if (threadIdx.x < 7) {
+  if (threadIdx.x < 8) {
     double s = 0;
-    for (int b = 0; b < nb; ++b) s += part[b * 7 + threadIdx.x];
+    for (int b = 0; b < nb; ++b) s += part[b * 8 + threadIdx.x];
     out[threadIdx.x] = s;
   }
 }

@@ -5,15 +5,16 @@
 // counterpart in the paper.
 //
 // The scratch lives in a file-scope __device__ array.  In host code that
-// array's name is only a host-side stand-in, so its device address is looked
-// up once per device with cudaGetSymbolAddress (with the device current) and
-// cached.  Every call shares the array; the sort writes each scratch word
-// before reading it, so nothing has to be cleared between calls, but calls
-// that overlap on the GPU race.
+// array's name is only a host-side stand-in, so every call looks up its
+// device address with cudaGetSymbolAddress for the device that is current.
+// The address is not cached: a context that is torn down and created again
+// (cudaDeviceReset, for one) may load the module at another address, and a
+// cached pointer would then be a dangling one.  The lookup is cheap once the
+// module is loaded; the first call on a device loads it.  Every call shares
+// the array; the sort writes each scratch word before reading it, so nothing
+// has to be cleared between calls, but calls that overlap on the GPU race.
 #include <cuda_runtime.h>
 #include <stdint.h>
-
-#include <mutex>
 
 #include "../../include/mpm.h"
 #include "mpm_internal.h"
@@ -21,12 +22,8 @@
 namespace {
 
 constexpr size_t kScratchBytes = size_t(22) << 20;  // 22 MiB
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_sort_scratch[kScratchBytes];
-
-std::mutex g_mu;
-void *g_addr[kMaxDevices] = {};
 
 size_t keys_bytes() { return ((size_t)4 * MPM_SORT_STATIC_MAX_KEYS + 255) & ~size_t(255); }
 
@@ -39,18 +36,9 @@ extern "C" mpm_status mpm_sort_keys_static(const uint32_t *d_keys, int32_t *d_pe
   if (n == 0) return MPM_OK;
   // the carve-up below must fit the fixed array for the largest n
   if (keys_bytes() + mpm::sort_scratch_bytes(MPM_SORT_STATIC_MAX_KEYS) > kScratchBytes) return MPM_ERR_STATE;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MPM_ERR_CUDA;
+  // the array's address in the current device's context, looked up afresh
   void *base = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
-      void *p = nullptr;
-      if (cudaGetSymbolAddress(&p, g_sort_scratch) != cudaSuccess || !p) return MPM_ERR_CUDA;
-      g_addr[dev] = p;
-    }
-    base = g_addr[dev];
-  }
+  if (cudaGetSymbolAddress(&base, g_sort_scratch) != cudaSuccess || !base) return MPM_ERR_CUDA;
   uint32_t *keys_out = (uint32_t *)base;
   void *scratch = (char *)base + keys_bytes();
   cudaError_t e = mpm::sort_pairs(d_keys, nullptr, keys_out, d_perm, n, key_bits, scratch, (cudaStream_t)stream);

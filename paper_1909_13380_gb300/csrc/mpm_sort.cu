@@ -107,10 +107,11 @@ __global__ void __launch_bounds__(RS_THREADS) scan_sums_single(uint32_t *__restr
   }
 }
 
-// out[i] = exclusive prefix of in[] (uses the scanned chunk sums).
-__global__ void __launch_bounds__(RS_THREADS) scan_apply(const uint32_t *__restrict__ in, int64_t n,
-                                                         const uint32_t *__restrict__ sums,
-                                                         uint32_t *__restrict__ out) {
+// out[i] = exclusive prefix of in[] (uses the scanned chunk sums).  May run
+// in place (out == in): each thread reads its items into registers before it
+// writes the same items, so in and out are not declared __restrict__.
+__global__ void __launch_bounds__(RS_THREADS) scan_apply(const uint32_t *in, int64_t n,
+                                                         const uint32_t *__restrict__ sums, uint32_t *out) {
   __shared__ uint32_t wt[RS_WARPS];
   const int64_t base = (int64_t)blockIdx.x * RS_TILE + (int64_t)threadIdx.x * RS_ITEMS;
   uint32_t loc[RS_ITEMS];

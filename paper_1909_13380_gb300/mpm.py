@@ -99,12 +99,15 @@ def load():
             "mpm_sort_keys": [vp, vp, C.c_int64, C.c_int32, vp],
             "mpm_sort_keys_static": [vp, vp, C.c_int64, C.c_int32, vp],
             "mpm_footprint": [C.POINTER(mpm_mesh_desc), C.c_int64, C.c_int32, i64p],
-            "mpm_batch_create": [vp, C.POINTER(vp)],
+            "mpm_batch_create": [C.c_int64, C.c_int32, vp, C.POINTER(vp)],
             "mpm_batch_admit": [vp, vp, i32p],
+            "mpm_batch_room": [vp, i64p, i32p],
             "mpm_batch_evict": [vp, C.c_int32],
             "mpm_batch_step": [vp, C.c_int64],
-            "mpm_batch_poll": [vp, C.c_int32, i32p],
+            "mpm_batch_poll": [vp, C.c_int32, i32p, i64p],
+            "mpm_batch_step_kernels": [vp, i32p],
             "mpm_batch_destroy": [vp],
+            "mpm_step_kernels": [vp, i32p],
             "mpm_material_update": [C.POINTER(mpm_material), C.c_int32, C.c_int64, dp, dp, dp, dp, dp, vp],
             "mpm_set_phase_timing": [vp, C.c_int32],
             "mpm_phase_times": [vp, C.POINTER(C.c_float), i32p],
@@ -203,14 +206,26 @@ def mpm_num_particles(h) -> int:
     return n.value
 
 
-def mpm_read_particles(h, dim: int, fields=("pos", "vel", "stress", "strain", "vol", "epsp", "cell")):
-    """Particle state in insertion order; returns (dict, status)."""
+def mpm_read_particles(h, dim: int, fields=("pos", "vel", "stress", "strain", "vol", "epsp", "cell"), out=None):
+    """Particle state in insertion order; returns (dict, status).  `out` may
+    supply the destination arrays (C-contiguous, float64 -- int64 for
+    "cell" -- of the field's shape), e.g. views of pinned host memory."""
     n = mpm_num_particles(h)
+    given = out or {}
     out = {}
-    shapes = {"pos": (n, dim), "vel": (n, dim), "stress": (n, 6), "strain": (n, 6), "vol": (n,), "epsp": (n,)}
+    shapes = {"pos": (n, dim), "vel": (n, dim), "stress": (n, 6), "strain": (n, 6), "vol": (n,), "epsp": (n,),
+              "cell": (n,)}
     for k, s in shapes.items():
-        out[k] = np.empty(s) if k in fields else None
-    out["cell"] = np.empty(n, np.int64) if "cell" in fields else None
+        dt = np.int64 if k == "cell" else np.float64
+        if k not in fields:
+            out[k] = None
+        elif k in given:
+            a = given[k]
+            if a.shape != s or a.dtype != dt or not a.flags.c_contiguous:
+                raise MPMError(MPM_ERR_ARG, f"mpm_read_particles: out[{k!r}] must be C-contiguous {dt.__name__} {s}")
+            out[k] = a
+        else:
+            out[k] = np.empty(s, dt)
     cptr = None if out["cell"] is None else out["cell"].ctypes.data_as(C.POINTER(C.c_int64))
     st = load().mpm_read_particles(h, _dp(out["pos"]), _dp(out["vel"]), _dp(out["stress"]), _dp(out["strain"]),
                                    _dp(out["vol"]), _dp(out["epsp"]), cptr)
@@ -220,11 +235,12 @@ def mpm_read_particles(h, dim: int, fields=("pos", "vel", "stress", "strain", "v
 
 
 def mpm_conservation(h):
-    out = np.zeros(7)
+    out = np.zeros(8)
     st = load().mpm_conservation(h, _dp(out))
     if st in (MPM_ERR_CUDA, MPM_ERR_OOM, MPM_ERR_ARG):
         _check(h, st, "mpm_conservation")
-    return {"mass": out[0], "momentum": out[1:4].copy(), "ke": out[4], "se": out[5], "alive": int(out[6])}, st
+    return {"mass": out[0], "momentum": out[1:4].copy(), "ke": out[4], "se": out[5], "alive": int(out[6]),
+            "volume": out[7]}, st
 
 
 def mpm_read_binning(h):
@@ -288,17 +304,39 @@ def mpm_footprint(desc: mpm_mesh_desc, n: int, has_cohesion: bool = False) -> in
     return out.value
 
 
-def mpm_batch_create(stream=None):
+def mpm_batch_create(stream=None, hbm_budget_bytes: int = 0, max_slots: int = 1 << 20):
     b = C.c_void_p()
-    _check(None, load().mpm_batch_create(stream, C.byref(b)), "mpm_batch_create")
+    _check(None, load().mpm_batch_create(int(hbm_budget_bytes), int(max_slots), stream, C.byref(b)),
+           "mpm_batch_create")
     return b
 
 
 def mpm_batch_admit(b, h) -> int:
+    """Slot of the admitted mesh; raises MPMError(MPM_ERR_OOM) when the batch
+    has no free slot or not enough of its memory budget left."""
     slot = C.c_int32()
     st = load().mpm_batch_admit(b, h, C.byref(slot))
     _check(h, st, "mpm_batch_admit")
     return slot.value
+
+
+def mpm_batch_room(b):
+    """(bytes left in the batch's budget, free slots)."""
+    fb, fs = C.c_int64(), C.c_int32()
+    _check(None, load().mpm_batch_room(b, C.byref(fb), C.byref(fs)), "mpm_batch_room")
+    return fb.value, fs.value
+
+
+def mpm_batch_step_kernels(b) -> int:
+    k = C.c_int32()
+    _check(None, load().mpm_batch_step_kernels(b, C.byref(k)), "mpm_batch_step_kernels")
+    return k.value
+
+
+def mpm_step_kernels(h) -> int:
+    k = C.c_int32()
+    _check(h, load().mpm_step_kernels(h, C.byref(k)), "mpm_step_kernels")
+    return k.value
 
 
 def mpm_batch_evict(b, slot: int):
@@ -309,10 +347,16 @@ def mpm_batch_step(b, nsteps: int):
     _check(None, load().mpm_batch_step(b, int(nsteps)), "mpm_batch_step")
 
 
-def mpm_batch_poll(b, nslots: int):
+def mpm_batch_poll(b, nslots: int, with_steps: bool = False):
+    """Per-slot status (and, with_steps, the batched steps each slot's mesh
+    has taken since its admission, -1 for an empty slot)."""
     out = (C.c_int32 * max(1, nslots))()
-    _check(None, load().mpm_batch_poll(b, int(nslots), out), "mpm_batch_poll")
-    return [int(out[i]) for i in range(nslots)]
+    steps = (C.c_int64 * max(1, nslots))()
+    _check(None, load().mpm_batch_poll(b, int(nslots), out, steps), "mpm_batch_poll")
+    status = [int(out[i]) for i in range(nslots)]
+    if with_steps:
+        return status, [int(steps[i]) for i in range(nslots)]
+    return status
 
 
 def mpm_batch_destroy(b):
@@ -362,8 +406,8 @@ class Simulation:
     def sync(self):
         return mpm_sync(self.h)
 
-    def read(self, fields=("pos", "vel", "stress", "strain", "vol", "epsp", "cell")):
-        return mpm_read_particles(self.h, self.dim, fields)
+    def read(self, fields=("pos", "vel", "stress", "strain", "vol", "epsp", "cell"), out=None):
+        return mpm_read_particles(self.h, self.dim, fields, out)
 
     def conservation(self):
         return mpm_conservation(self.h)

@@ -59,9 +59,16 @@ class _Active:
 class GpuEngine:
     """The CUDA library behind the serving loop.  `batched` selects
     continuous batching (one batch over every admitted FP32 simulation) or
-    one simulation at a time (any precision)."""
+    one simulation at a time (any precision).
 
-    def __init__(self, precision=W.FP32_MIXED, batched=True, reserve_bytes=2 << 30):
+    The batch owns admission: it is created with a device-memory budget (the
+    free HBM at start, less a reserve) and a slot count, and the library
+    refuses a mesh (MPM_ERR_OOM) whose footprint exceeds what the budget has
+    left.  Meshes created for the next admission point (their upload overlaps
+    the running chunk) hold memory before they are admitted, so the room the
+    loop sees is the batch's room less their footprints."""
+
+    def __init__(self, precision=W.FP32_MIXED, batched=True, reserve_bytes=2 << 30, max_slots=4096):
         import torch
 
         from . import mpm
@@ -71,7 +78,12 @@ class GpuEngine:
         self.reserve = int(reserve_bytes)
         self.side = torch.cuda.Stream()          # uploads and result reads (and unbatched steps)
         self.bstream = torch.cuda.Stream()       # batched steps
-        self.batch = mpm.mpm_batch_create(self.bstream.cuda_stream) if batched else None
+        self.batch = None
+        if batched:
+            budget = max(1, int(torch.cuda.mem_get_info()[0]) - self.reserve)
+            self.batch = mpm.mpm_batch_create(self.bstream.cuda_stream, hbm_budget_bytes=budget,
+                                              max_slots=max_slots)
+        self.staged = {}                         # id(sim) -> footprint of meshes created, not yet admitted
         self.h2d = 0
         self.d2h = 0
 
@@ -80,15 +92,29 @@ class GpuEngine:
         return self.mpm.mpm_footprint(d, wl.n, wl.coh is not None)
 
     def free_bytes(self) -> int:
+        if self.batched:
+            room, slots = self.mpm.mpm_batch_room(self.batch)
+            return room - sum(self.staged.values()) if slots > len(self.staged) else -1
         return int(self.torch.cuda.mem_get_info()[0]) - self.reserve
 
     def create(self, wl):
         sim = self.mpm.Simulation(wl, precision=self.precision, stream=self.side.cuda_stream)
         self.h2d += wl.pos.nbytes + wl.vel.nbytes + wl.vol.nbytes + (wl.coh.nbytes if wl.coh is not None else 0)
+        if self.batched:
+            self.staged[id(sim)] = self.footprint(wl)
         return sim
 
-    def admit(self, sim) -> int:
-        return self.mpm.mpm_batch_admit(self.batch, sim.h)
+    def admit(self, sim):
+        """The slot of the admitted simulation, or None when the batch
+        refuses it (MPM_ERR_OOM: no slot or budget left yet)."""
+        try:
+            slot = self.mpm.mpm_batch_admit(self.batch, sim.h)
+        except self.mpm.MPMError as e:
+            if e.status == self.mpm.MPM_ERR_OOM:
+                return None
+            raise
+        self.staged.pop(id(sim), None)
+        return slot
 
     def evict(self, slot: int):
         self.mpm.mpm_batch_evict(self.batch, slot)
@@ -208,15 +234,19 @@ class Server:
         while nxt < len(order) or queue or active or single or staged:
             arrivals()
             admit_ready(staged)
+            refused = []
             for i, sim, t_adm in staged:
                 a = _Active(i, sim, requests[i].steps, t_adm)
                 if eng.batched:
                     slot = eng.admit(sim)
+                    if slot is None:              # the batch has no room yet: admit it later
+                        refused.append((i, sim, t_adm))
+                        continue
                     active[slot] = a
                     nslots = max(nslots, slot + 1)
                 else:
                     single.append(a)
-            staged = []
+            staged = refused
             running = list(active.values()) if eng.batched else single
             if not running:
                 if nxt < len(order):

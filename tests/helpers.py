@@ -107,3 +107,93 @@ def small_column(precision=W.FP32_MIXED, scheme=W.USL):
     its tiles are partly filled and it has a ragged last tile in x and z."""
     return W.column3d(ncells=(40, 16, 24), col_cells=(12, 12, 12), precision=precision, scheme=scheme,
                       name="granular_column_3d_small")
+
+
+def max_over_rms(a, b):
+    """Largest per-particle error norm over the RMS of the reference's
+    per-particle norms.  A fault confined to a few particles (a boundary
+    layer, the base-friction nodes) shows here; a relative L2 over all
+    particles dilutes it."""
+    a = np.asarray(a, np.float64).reshape(len(a), -1)
+    b = np.asarray(b, np.float64).reshape(len(b), -1)
+    rms = float(np.sqrt(np.mean(np.sum(b * b, axis=1)))) if len(b) else 0.0
+    e = np.sqrt(np.sum((a - b) ** 2, axis=1)) if len(a) else np.zeros(1)
+    return float(e.max() / rms) if rms > 0 else float(e.max())
+
+
+def per_particle(gpu, ref, start):
+    """max_over_rms of displacement (since `start`), velocity and stress over
+    the particles live on both sides."""
+    live = (gpu["cell"] >= 0) & (ref["cell"] >= 0)
+    return {
+        "disp": max_over_rms((gpu["pos"] - start["pos"])[live], (ref["pos"] - start["pos"])[live]),
+        "vel": max_over_rms(gpu["vel"][live], ref["vel"][live]),
+        "stress": max_over_rms(gpu["stress"][live], ref["stress"][live]),
+    }
+
+
+# Resolution of the FP32 cell offset: the offset lies in [-0.5, 0.5) cells, so
+# one rounding of it is at most 2^-26 cells; a step rounds it once.
+OFFSET_ROUNDING_CELLS = 2.0 ** -26
+
+
+def disp_excess(gpu, ref, start, h, steps, dim, rel=TOL_RUN_FP32):
+    """Per-particle displacement error beyond what the FP32 offset can
+    resolve: the largest of |d_gpu - d_ref| / (rel * rms(d_ref) + floor)
+    over the live particles, with floor = (steps + 1) * 2 * 2^-26 h sqrt(dim)
+    (the rounding of the initial offset and of every step's, twice over).
+    Values <= 1 pass."""
+    live = (gpu["cell"] >= 0) & (ref["cell"] >= 0)
+    dg = (gpu["pos"] - start["pos"])[live]
+    dr = (ref["pos"] - start["pos"])[live]
+    rms = float(np.sqrt(np.mean(np.sum(dr * dr, axis=1)))) if len(dr) else 0.0
+    floor = (steps + 1) * 2.0 * OFFSET_ROUNDING_CELLS * h * math.sqrt(dim)
+    e = np.sqrt(np.sum((dg - dr) ** 2, axis=1))
+    return float(e.max() / (rel * rms + floor)) if len(e) else 0.0
+
+
+def named_workload(name, precision=W.FP32_MIXED, scheme=W.USL):
+    """Workloads the long parity runs use (built the same way in a worker
+    process and in the test)."""
+    if name == "small_column":
+        return small_column(precision=precision, scheme=scheme)
+    if name == "slope_1_64":
+        wl = W.slope3d(ncells=(200, 50, 50), h=0.2, crest=8.0, plateau=8.5, precision=precision)
+        wl.scheme = scheme
+        return wl
+    raise ValueError(name)
+
+
+def oracle_checkpoints(job):
+    """Run the oracle on a named workload from its inputs and snapshot it at
+    the given steps (a worker of a spawned process pool: the oracle is
+    sequential, so independent runs go to separate cores)."""
+    name, scheme, checkpoints = job
+    wl = named_workload(name, scheme=scheme)
+    o = oracle_from_workload(wl, scheme)
+    out = {0: oracle_snapshot(o, wl.dim)}
+    done = 0
+    for k in sorted(checkpoints):
+        st = o.step(k - done)
+        done = k
+        snap = oracle_snapshot(o, wl.dim)
+        snap["status"] = st
+        out[k] = snap
+    return out
+
+
+def check_step(gpu, ref, start, h, dim, steps=1):
+    """The per-step FP32 bar from an identical state (or a few steps from the
+    inputs): position, velocity, stress and volume within TOL_STEP_FP32
+    (relative L2); per particle, velocity within 1e-4 and stress within 1e-3
+    of the field's RMS; and the displacement of every particle within
+    TOL_STEP_FP32 of its RMS plus the offset's rounding (disp_excess).  The
+    displacement check is what holds advection to account: positions
+    measured from the mesh origin barely move in one step."""
+    err = compare(gpu, ref, start, dim)
+    assert worst(err, STATE_KEYS) <= TOL_STEP_FP32, err
+    pp = per_particle(gpu, ref, start)
+    assert pp["vel"] <= 1e-4 and pp["stress"] <= 1e-3, pp
+    ex = disp_excess(gpu, ref, start, h, steps, dim, rel=TOL_STEP_FP32)
+    assert ex <= 1.0, ex
+    return err

@@ -140,3 +140,53 @@ def test_footprint_covers_the_allocation():
         s.sync()
         used = free0 - torch.cuda.mem_get_info()[0]
     assert est > 0.9 * used
+
+
+def test_budget_and_slots_refuse_admission_and_leave_the_batch_intact():
+    """A batch with a memory budget that holds two of three meshes, then one
+    with a single slot: the refused admission returns MPM_ERR_OOM, the mesh
+    and the batch are unchanged, and the admitted meshes still step as they
+    would alone; an eviction makes room."""
+    wls = W.columns2d_batch(count=3, seed=W.SEED_BASE + 35)
+    fps = []
+    for wl in wls:
+        d = mpm.make_desc(wl.dim, wl.ncells, wl.h, precision=W.FP32_MIXED, scheme=wl.scheme)
+        fps.append(mpm.mpm_footprint(d, wl.n, False))
+    sims = [mpm.Simulation(w) for w in wls]
+    steps = 12
+    b = mpm.mpm_batch_create(hbm_budget_bytes=sum(fps) - 1, max_slots=8)
+    try:
+        assert mpm.mpm_batch_admit(b, sims[0].h) == 0
+        assert mpm.mpm_batch_admit(b, sims[1].h) == 1
+        room, free_slots = mpm.mpm_batch_room(b)
+        assert room < fps[2] and free_slots == 6
+        with pytest.raises(mpm.MPMError) as ei:
+            mpm.mpm_batch_admit(b, sims[2].h)
+        assert ei.value.status == mpm.MPM_ERR_OOM
+        assert sims[2].sync() == mpm.MPM_OK          # not latched on the refused mesh
+        mpm.mpm_batch_step(b, steps)
+        status, taken = mpm.mpm_batch_poll(b, 3, with_steps=True)
+        assert status == [mpm.MPM_OK, mpm.MPM_OK, mpm.MPM_ERR_STATE] and taken == [steps, steps, -1]
+        for i in (0, 1):
+            snap, _ = sims[i].read()
+            assert equal(snap, alone(wls[i], steps)[0]), i
+        mpm.mpm_batch_evict(b, 0)
+        assert mpm.mpm_batch_admit(b, sims[2].h) == 0   # the evicted mesh's budget and slot are free again
+        mpm.mpm_batch_step(b, steps)
+        status, taken = mpm.mpm_batch_poll(b, 2, with_steps=True)
+        assert status == [mpm.MPM_OK, mpm.MPM_OK] and taken == [steps, 2 * steps]
+        snap, _ = sims[2].read()
+        assert equal(snap, alone(wls[2], steps)[0])
+        assert mpm.mpm_batch_step_kernels(b) >= 6
+    finally:
+        mpm.mpm_batch_destroy(b)
+    b = mpm.mpm_batch_create(max_slots=1)
+    try:
+        mpm.mpm_batch_admit(b, sims[0].h)
+        with pytest.raises(mpm.MPMError) as ei:
+            mpm.mpm_batch_admit(b, sims[1].h)
+        assert ei.value.status == mpm.MPM_ERR_OOM
+    finally:
+        mpm.mpm_batch_destroy(b)
+        for s in sims:
+            s.close()

@@ -7,6 +7,7 @@ import pytest
 
 from paper_1909_13380_gb300 import serve
 from paper_1909_13380_gb300 import workloads as W
+from tests import helpers as H
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -65,10 +66,14 @@ def test_fp64_one_at_a_time_matches_fp32_batched():
         assert all(f.status == mpm.MPM_OK for f in done)
         res[name] = {f.rid: f.result for f in done}
     for i in range(len(reqs)):
-        a, b = res["fp32"][i]["pos"], res["fp64"][i]["pos"]
-        # relative L2 error of the displacement-carrying positions, FP32 vs FP64
-        err = np.linalg.norm(a - b) / np.linalg.norm(b)
-        assert err < 1e-5, (i, err)
-        a, b = res["fp32"][i]["stress"], res["fp64"][i]["stress"]
-        err = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
-        assert err < 1e-3, (i, err)
+        wl, steps = wls[i], reqs[i].steps
+        live = np.zeros(wl.n, np.int64)
+        g = {"pos": res["fp32"][i]["pos"], "cell": live}
+        r = {"pos": res["fp64"][i]["pos"], "cell": live}
+        # displacements from the request's inputs: within 1e-3 of their RMS per
+        # particle, plus the FP32 offset's rounding over the steps taken
+        assert H.disp_excess(g, r, {"pos": wl.pos}, wl.h, steps, wl.dim) <= 1.0, i
+        for k in ("vel", "stress"):
+            a, b = res["fp32"][i][k], res["fp64"][i][k]
+            assert H.rel_l2(a, b) <= H.TOL_RUN_FP32, (i, k)
+            assert H.max_over_rms(a, b) <= 1e-2, (i, k)

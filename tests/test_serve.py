@@ -122,6 +122,34 @@ def test_admission_is_fifo_and_bounded_by_memory():
     assert any(f.admitted > f.arrival for f in done)
 
 
+class SlotLimitedEngine(FakeEngine):
+    """A batch with two slots: admission beyond them is refused (the library
+    answers MPM_ERR_OOM, the engine returns None) and must be retried."""
+
+    def admit(self, sim):
+        if len(self.slots) >= 2:
+            self.refused = getattr(self, "refused", 0) + 1
+            return None
+        return super().admit(sim)
+
+
+def test_refused_admission_is_retried_after_an_eviction():
+    reqs = W.serving_requests(count=30, rate=200.0, n_range=(1e3, 5e4), steps_range=(5, 200), step_scale=1.0)
+    wls = [TinyWl(r.n_target, r.steps) for r in reqs]
+    clock = [0.0]
+
+    def sleep(dt):
+        clock[0] += dt
+
+    eng = SlotLimitedEngine(True, 10_000_000, clock)
+    done, lat, total = serve.Server(eng, chunk=8, keep_results=True, clock=lambda: clock[0],
+                                    sleep=sleep).run(reqs, wls)
+    assert sorted(f.rid for f in done) == list(range(len(reqs)))
+    assert all(f.result["steps"] == reqs[f.rid].steps and f.status == 0 for f in done)
+    assert eng.refused > 0 and eng.max_running <= 2
+    assert eng.resident == 0
+
+
 def test_percentiles_weight_steps():
     p = serve.percentiles([1.0, 10.0], [99, 1])
     assert p["p50"] == 1.0

@@ -50,3 +50,20 @@ def test_static_sort_rejects_more_keys_than_its_scratch_holds():
     with pytest.raises(mpm.MPMError) as ei:
         mpm.mpm_sort_keys_static(dk, dp, n, 8)
     assert ei.value.status == mpm.MPM_ERR_ARG
+
+
+def test_static_sort_allocates_no_device_memory():
+    # the reason the entry point exists: once the library is loaded, a call
+    # leaves the device's free memory exactly as it found it
+    n, bits = 500_000, 24
+    keys = _keys(n, bits, 5)
+    dk = torch.from_numpy(keys.view(np.int32)).cuda()
+    got = torch.empty(n, dtype=torch.int32, device="cuda")
+    mpm.mpm_sort_keys_static(dk, got, n, bits)      # first call: loads the device code
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    mpm.mpm_sort_keys_static(dk, got, n, bits)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert np.array_equal(got.cpu().numpy(), np.argsort(keys, kind="stable").astype(np.int32))
