@@ -244,6 +244,20 @@ mpm_status mpm_batch_poll(mpm_batch b, int32_t nslots, int32_t *slot_status, int
 mpm_status mpm_batch_step_kernels(mpm_batch b, int32_t *kernels);
 mpm_status mpm_batch_destroy(mpm_batch b);
 
+/* Failure-detection test hook (the paper has no counterpart).  The FP32
+ * tile scan of meshes with more than 4095 tiles runs one pass over chunks of
+ * 1024 tiles in which each chunk waits, on the device, for the prefix its
+ * predecessors publish; every such wait is bounded and gives up with
+ * MPM_ERR_TIMEOUT (latched, reported by mpm_sync) instead of hanging.  This
+ * call makes that happen on purpose: chunk withhold_chunk (0-based; -1 = none)
+ * never publishes, and a wait polls at most spin_limit times (1..2^20; 2^20
+ * is the default).  A mesh whose scan gave up a wait is frozen: from then on
+ * its steps carry its particles over unchanged and touch nothing else, and
+ * its status stays MPM_ERR_TIMEOUT until mpm_destroy.  Other meshes are not
+ * affected.  FP32_MIXED meshes not admitted to a batch; MPM_ERR_ARG for
+ * out-of-range values. */
+mpm_status mpm_set_scan_fault(mpm_handle h, int32_t withhold_chunk, int32_t spin_limit);
+
 /* Kernel launches one mpm_step of h enqueues (measurement support): the
  * kernel nodes of the step graph the library captured for h, FP32_MIXED
  * only.  MPM_ERR_STATE before the first captured step or for FP64_PLAIN. */

@@ -185,6 +185,7 @@ struct mpm_ctx {
   bool grp_valid = false;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int32_t graph_kernels = -1;  // kernel nodes of the last captured step graph
+  int32_t lb_withhold = -1, lb_spin = LB_SPIN_LIMIT;  // tile scan test hook (mpm_set_scan_fault)
   bool timing = false;
   bool timed_step = false;
   cudaEvent_t ev[MPM_MAX_PHASES + 1] = {};
@@ -351,6 +352,8 @@ InstArgs make_inst(const mpm_ctx *h, int c, bool scratch_out) {
   I.perm_out = scratch_out ? h->perm2 : h->s.perm;
   I.ns0 = h->d.ncells[0] + 1;
   I.ns1 = I.ns0 * (h->d.ncells[1] + 1);
+  I.lb_withhold = h->lb_withhold;
+  I.lb_spin = h->lb_spin;
   return I;
 }
 
@@ -366,9 +369,9 @@ cudaError_t build_group(GroupDev &g, const std::vector<mpm_ctx *> &mem, bool rel
     const int cap = n < 8 ? 8 : n;
     for (int p = 0; p < 2; ++p)
       if ((e = cudaMalloc(&g.tab[p], sizeof(InstArgs) * cap)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&g.pfx, sizeof(int32_t) * (5 * (cap + 1) + W_COUNT))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&g.pfx, sizeof(int32_t) * (6 * (cap + 1) + W_COUNT))) != cudaSuccess) return e;
     if ((e = cudaMalloc(&g.status, sizeof(int32_t) * cap)) != cudaSuccess) return e;
-    if ((e = cudaMemset(g.pfx, 0, sizeof(int32_t) * (5 * (cap + 1) + W_COUNT))) != cudaSuccess) return e;
+    if ((e = cudaMemset(g.pfx, 0, sizeof(int32_t) * (6 * (cap + 1) + W_COUNT))) != cudaSuccess) return e;
     g.cap = cap;
   }
   g.ninst = n;
@@ -398,7 +401,8 @@ cudaError_t build_group(GroupDev &g, const std::vector<mpm_ctx *> &mem, bool rel
     G.mblk = g.pfx + 2 * (g.cap + 1);
     G.bin_items = g.pfx + 3 * (g.cap + 1);
     G.act_items = g.pfx + 4 * (g.cap + 1);
-    G.work = g.pfx + 5 * (g.cap + 1);
+    G.res_items = g.pfx + 5 * (g.cap + 1);
+    G.work = g.pfx + 6 * (g.cap + 1);
     G.nblk_p = pb[n];
     G.nblk_s = sb[n];
     G.nblk_m = mb[n];
@@ -472,8 +476,8 @@ void free_t(T *&p) {
 // Device bytes of the FP32 step storage that does not scale with particles.
 int64_t f32_fixed_bytes(const mpm_mesh_desc &d, int64_t nt, int64_t nn) {
   const int bn = d.dim == 3 ? box_nodes<3>() : box_nodes<2>();
-  int64_t b = 4 * nt * bn * (1 + 2 * d.dim) + (d.scheme == MPM_USF ? 4 * nt * bn * d.dim : 0);
-  b += 6 * 4 * (nt + 2) + 2 * 16 * (nt + 2) + 16 * nn * (d.dim == 3 ? 2 : 1) + 4096;
+  int64_t b = 4 * nt * bn * (1 + 2 * d.dim) * (d.scheme == MPM_USL ? 2 : 1) + (d.scheme == MPM_USF ? 4 * nt * bn * d.dim : 0);
+  b += 9 * 4 * (nt + 2) + 2 * 16 * (nt + 2) + 16 * nn * (d.dim == 3 ? 2 : 1) + 4096;
   return b;
 }
 
@@ -555,6 +559,12 @@ mpm_status mpm_create_mesh(const mpm_mesh_desc *desc, mpm_handle *out) {
     const size_t ti = sizeof(int32_t) * (nt + 2);
     if (e == cudaSuccess) e = cudaMalloc(&S.slots1, s1);
     if (e == cudaSuccess && s2) e = cudaMalloc(&S.slots2, s2);
+    if (e == cudaSuccess && d.scheme == MPM_USL) e = cudaMalloc(&S.slots_a, s1);
+    if (e == cudaSuccess) e = cudaMalloc(&S.fepoch, sizeof(int32_t) * nt);
+    if (e == cudaSuccess) e = cudaMalloc(&S.aepoch, sizeof(int32_t) * nt);
+    if (e == cudaSuccess) e = cudaMalloc(&S.resid, sizeof(int32_t) * (nt + 2));
+    if (e == cudaSuccess) e = cudaMemset(S.fepoch, 0xff, sizeof(int32_t) * nt);  // -1: no sums yet
+    if (e == cudaSuccess) e = cudaMemset(S.aepoch, 0xff, sizeof(int32_t) * nt);
     for (int p = 0; p < 2 && e == cudaSuccess; ++p) e = cudaMalloc(&S.tile_start[p], ti);
     if (e == cudaSuccess) e = cudaMalloc(&S.in_cnt, ti);
     if (e == cudaSuccess) e = cudaMalloc(&S.out_cnt, ti);
@@ -562,7 +572,7 @@ mpm_status mpm_create_mesh(const mpm_mesh_desc *desc, mpm_handle *out) {
     if (e == cudaSuccess) e = cudaMalloc(&S.bucket_fill, ti);
     if (e == cudaSuccess) e = cudaMalloc(&S.active, sizeof(int4) * (nt + 2));
     if (e == cudaSuccess) e = cudaMalloc(&S.bin_rec, sizeof(int4) * (nt + 2));
-    const size_t stb = sizeof(int32_t) * 8 * ((nt + 1) / 1024 + 2);
+    const size_t stb = sizeof(int32_t) * 16 * ((nt + 1) / 1024 + 2);
     if (e == cudaSuccess) e = cudaMalloc(&S.scan_tot, stb);
     if (e == cudaSuccess) e = cudaMemset(S.scan_tot, 0, stb);
     if (e == cudaSuccess) e = cudaMalloc(&S.ctr, sizeof(int32_t) * C_NCTR);
@@ -718,6 +728,9 @@ mpm_status mpm_add_particles(mpm_handle h, int64_t n, const double *pos, const d
     CK(cudaMemsetAsync(S.out_cnt, 0, ti, h->st), "binning");
     CK(cudaMemsetAsync(S.bucket_fill, 0, ti, h->st), "binning");
     CK(cudaMemsetAsync(S.ctr, 0, sizeof(int32_t) * C_STATUS, h->st), "binning");
+    // the particle set changed: no tile holds valid partial sums of the next P2G
+    CK(cudaMemsetAsync(S.fepoch, 0xff, sizeof(int32_t) * h->geo.ntiles, h->st), "binning");
+    CK(cudaMemsetAsync(S.aepoch, 0xff, sizeof(int32_t) * h->geo.ntiles, h->st), "binning");
     CK(cudaStreamSynchronize(h->st), "binning");
     for (int b = 0; b < 2; ++b) free_ptr(h->bufmem[b]);
     h->bufmem[0] = nm[0];
@@ -1038,6 +1051,21 @@ mpm_status mpm_phase_times(mpm_handle h, float *ms, int32_t *nphase) {
   return MPM_OK;
 }
 
+mpm_status mpm_set_scan_fault(mpm_handle h, int32_t withhold_chunk, int32_t spin_limit) {
+  mpm_status s0 = check_handle(h);
+  if (s0 != MPM_OK) return s0;
+  if (h->d.precision != MPM_FP32_MIXED) return fail(h, MPM_ERR_STATE, "scan fault: FP32_MIXED handles only");
+  if (h->batch) return fail(h, MPM_ERR_STATE, "scan fault: the mesh is admitted to a batch");
+  if (withhold_chunk < -1 || spin_limit < 1 || spin_limit > LB_SPIN_LIMIT)
+    return fail(h, MPM_ERR_ARG, "scan fault: bad arguments");
+  CK(cudaStreamSynchronize(h->st), "scan fault");
+  h->lb_withhold = withhold_chunk;
+  h->lb_spin = spin_limit;
+  destroy_graphs(h->graph);  // the instance (and its hook) is captured in the step graph
+  h->grp_valid = false;
+  return MPM_OK;
+}
+
 mpm_status mpm_step_kernels(mpm_handle h, int32_t *kernels) {
   if (!h || !kernels) return MPM_ERR_ARG;
   if (h->d.precision != MPM_FP32_MIXED || h->graph_kernels < 0) return MPM_ERR_STATE;
@@ -1064,7 +1092,8 @@ mpm_status mpm_destroy(mpm_handle h) {
   StepBufs &S = h->s;
   void *ptrs[] = {h->bufmem[0], h->bufmem[1], S.keys_sorted, S.perm, S.tile_start[0], S.tile_start[1], S.in_cnt,
                   S.out_cnt, S.bucket_start, S.bucket_fill, S.movers, S.bucket, S.bucket_sorted, S.active,
-                  S.bin_rec, S.scan_tot, S.ctr, S.slots1, S.slots2, S.node, h->keys2, h->perm2, h->sort_scratch,
+                  S.bin_rec, S.scan_tot, S.ctr, S.slots1, S.slots2, S.slots_a, S.fepoch, S.aepoch, S.resid, S.node,
+                  h->keys2, h->perm2, h->sort_scratch,
                   h->pmem64, h->nmem64, h->d_status, h->d_cons};
   for (void *p : ptrs)
     if (p) cudaFree(p);

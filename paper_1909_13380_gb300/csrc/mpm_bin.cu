@@ -102,25 +102,26 @@ __device__ __forceinline__ int cta_excl(int v, int *wsum, int &total) {
   return base + inc - v;
 }
 
-// The same for three values per thread at once (three scans, one set of
-// barriers); v becomes the three prefixes.
-__device__ __forceinline__ void cta_excl3(int v[3], int (*wsum)[32], int total[3]) {
+// The same for NV values per thread at once (NV scans, one set of
+// barriers); v becomes the NV prefixes.  The CTA has at most 32 warps.
+constexpr int NSCAN = 4;  // new count, arrivals, active tiles, residual P2G items
+__device__ __forceinline__ void cta_excl4(int v[NSCAN], int (*wsum)[32], int total[NSCAN]) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  int inc[3];
+  int inc[NSCAN];
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < NSCAN; ++k) {
     inc[k] = warp_incl(v[k]);
     if (lane == 31) wsum[k][w] = inc[k];
   }
   __syncthreads();
-  if (w < 3) {
+  if (w < NSCAN) {
     int s = lane < nw ? wsum[w][lane] : 0;
     s = warp_incl(s);
     if (lane < nw) wsum[w][lane] = s;
   }
   __syncthreads();
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < NSCAN; ++k) {
     total[k] = wsum[k][nw - 1];
     v[k] = (w ? wsum[k][w - 1] : 0) + inc[k] - v[k];
   }
@@ -128,39 +129,59 @@ __device__ __forceinline__ void cta_excl3(int v[3], int (*wsum)[32], int total[3
 }
 
 // Per tile e (tiles plus the dead range): new count = old count - leavers +
-// arrivals; arrivals; active flag.
-__device__ __forceinline__ void tile_counts(const InstArgs &I, int e, int &cn, int &cb, int &ca) {
+// arrivals; arrivals; active flag; residual flag: an active tile whose
+// next-step P2G the previous G2P did not complete -- its partial sums are
+// not for this step (`step`), or particles arrived from other tiles.
+// A frozen instance (a bounded wait of an earlier scan gave up, its binning
+// is not valid) has every particle in the dead range, so the step carries its
+// state over unchanged and its kernels touch nothing else.
+__device__ __forceinline__ void tile_counts(const InstArgs &I, int e, int step, bool frozen, int &cn, int &cb,
+                                            int &ca, int &cr) {
+  if (frozen) {
+    cn = e == I.ntiles ? (int)I.n : 0;
+    cb = ca = cr = 0;
+    return;
+  }
   const int in = I.s.in_cnt[e], out = I.s.out_cnt[e];
   cn = (I.old_start[e + 1] - I.old_start[e]) - out + in;
   cb = in;
   ca = (e < I.ntiles && cn > 0) ? 1 : 0;
+  cr = (ca && (in > 0 || I.s.fepoch[e] != step)) ? 1 : 0;
 }
 
 // Prefixes of the binning tiles and the active tiles over the instances, and
 // reset of the group's dynamic work counters.
 __device__ __forceinline__ void group_prefix_body(const GroupArgs &G, int *wsum) {
-  int cb = 0, ca = 0;
+  int cb = 0, ca = 0, cr = 0;
   for (int c0 = 0; c0 < G.ninst; c0 += blockDim.x) {
     const int j = c0 + threadIdx.x;
-    int b = 0, a = 0;
+    int b = 0, a = 0, r = 0;
     if (j < G.ninst) {
       const int32_t *ctr = G.inst[j].s.ctr;
-      b = __ldcg(ctr + C_BIN_ITEMS);
-      a = __ldcg(ctr + C_ACTIVE);
+      // an instance whose scan gave up a wait this step does no more work in it
+      if (!(__ldcg(ctr + C_STATUS) & ST_TIMEOUT)) {
+        b = __ldcg(ctr + C_BIN_ITEMS);
+        a = __ldcg(ctr + C_ACTIVE);
+        r = __ldcg(ctr + C_RESID);
+      }
     }
-    int tb, ta;
+    int tb, ta, tr;
     const int pb = cta_excl(b, wsum, tb) + cb;
     const int pa = cta_excl(a, wsum, ta) + ca;
+    const int pr = cta_excl(r, wsum, tr) + cr;
     if (j < G.ninst) {
       G.bin_items[j] = pb;
       G.act_items[j] = pa;
+      G.res_items[j] = pr;
     }
     cb += tb;
     ca += ta;
+    cr += tr;
   }
   if (threadIdx.x == 0) {
     G.bin_items[G.ninst] = cb;
     G.act_items[G.ninst] = ca;
+    G.res_items[G.ninst] = cr;
   }
   if (threadIdx.x < W_COUNT) G.work[threadIdx.x] = 0;
 }
@@ -168,25 +189,27 @@ __device__ __forceinline__ void group_prefix_body(const GroupArgs &G, int *wsum)
 // Scan over tiles in one pass with decoupled look-back (Merrill & Garland,
 // "Single-pass parallel prefix scan with decoupled look-back", 2016).  Each
 // block takes a ticket in start order, which names its chunk of SCAN_CHUNK
-// tiles; it publishes its chunk's totals of (count, arrivals, active), then
-// one warp reads the chunks before it 32 at a time, adding their published
-// totals up to the nearest one that has published its inclusive prefix.  A block waits only
-// on chunks whose blocks took lower tickets and are therefore already
-// running, so every wait ends; each wait is nonetheless bounded, and gives up
-// with ST_TIMEOUT set.  Then it writes new ranges, arrival offsets, the active
-// list and the counter resets of its tiles, and the block that finishes last
-// computes the group's prefixes and clears the chunk flags for the next step.
-// Per chunk k, scan_tot[8k .. 8k+7] = flag (0 none, 1 totals, 2 inclusive),
-// totals (3), inclusive prefix (3), unused.
-constexpr int LB_SPIN_LIMIT = 1 << 20;
+// tiles; it publishes its chunk's totals of (count, arrivals, active,
+// residual), then one warp reads the chunks before it 32 at a time, adding
+// their published totals up to the nearest one that has published its
+// inclusive prefix.  A block waits only on chunks whose blocks took lower
+// tickets and are therefore already running, so every wait ends; each wait
+// is nonetheless bounded, and gives up with ST_TIMEOUT set.  Then it writes
+// new ranges, arrival offsets, the active and residual lists and the counter
+// resets of its tiles, and the block that finishes last advances the step
+// index, computes the group's prefixes and clears the chunk flags for the
+// next step.
+// Per chunk k, scan_tot[SCAN_REC k ..] = flag (0 none, 1 totals, 2
+// inclusive), totals (4), inclusive prefix (4).
+constexpr int SCAN_REC = 16;
 
 __device__ __forceinline__ int ld_volatile(const int32_t *p) { return *(const volatile int32_t *)p; }
 
 template <bool ONE>
 __global__ void __launch_bounds__(SCAN_T) bin_scan_lb(const __grid_constant__ GroupArgs G) {
-  __shared__ int wsum3[3][32];
+  __shared__ int wsum4[NSCAN][32];
   __shared__ int s_ticket, s_last;
-  __shared__ int s_excl[3];
+  __shared__ int s_excl[NSCAN];
   __shared__ InstArgs sI;
   pdl_trigger();
   pdl_wait();
@@ -202,32 +225,33 @@ __global__ void __launch_bounds__(SCAN_T) bin_scan_lb(const __grid_constant__ Gr
   const int c = ONE ? tk : tk - G.sblk[i];
   const int nchunks = ONE ? G.nblk_s : G.sblk[i + 1] - G.sblk[i];
   const int m = I.ntiles + 1;
+  const int step = __ldcg(I.s.ctr + C_STEP) + 1;  // this step's index (the last block stores it)
+  const bool frozen = (__ldcg(I.s.ctr + C_STATUS) & ST_TIMEOUT) != 0;
   int32_t *st = I.s.scan_tot;
   const int e0 = c * SCAN_CHUNK + threadIdx.x * SCAN_ITEMS;
-  int cn[SCAN_ITEMS], cb[SCAN_ITEMS], ca[SCAN_ITEMS];
-  int sn = 0, sb = 0, sa = 0;
+  int cn[SCAN_ITEMS], cb[SCAN_ITEMS], ca[SCAN_ITEMS], cr[SCAN_ITEMS];
+  int pv[NSCAN] = {0, 0, 0, 0};
 #pragma unroll
   for (int r = 0; r < SCAN_ITEMS; ++r) {
     const int e = e0 + r;
-    cn[r] = cb[r] = ca[r] = 0;
-    if (e < m) tile_counts(I, e, cn[r], cb[r], ca[r]);
-    sn += cn[r];
-    sb += cb[r];
-    sa += ca[r];
+    cn[r] = cb[r] = ca[r] = cr[r] = 0;
+    if (e < m) tile_counts(I, e, step, frozen, cn[r], cb[r], ca[r], cr[r]);
+    pv[0] += cn[r];
+    pv[1] += cb[r];
+    pv[2] += ca[r];
+    pv[3] += cr[r];
   }
-  int pv[3] = {sn, sb, sa}, tot3[3];
-  cta_excl3(pv, wsum3, tot3);
-  int pn = pv[0], pb = pv[1], pa = pv[2];
-  const int tn = tot3[0], tb = tot3[1], ta = tot3[2];
+  int tot[NSCAN];
+  cta_excl4(pv, wsum4, tot);
   if (threadIdx.x < 32) {  // warp 0: publish, look back 32 chunks at a time, publish the prefix
     const int lane = threadIdx.x;
-    int32_t *me = st + 8 * c;
-    int en = 0, eb = 0, ea = 0;
+    int32_t *me = st + SCAN_REC * c;
+    int ex[NSCAN] = {0, 0, 0, 0};
+    const bool publish = c != I.lb_withhold;  // always, but for the failure-detection test hook
     if (c > 0) {
-      if (lane == 0) {
-        me[1] = tn;
-        me[2] = tb;
-        me[3] = ta;
+      if (lane == 0 && publish) {
+#pragma unroll
+        for (int k = 0; k < NSCAN; ++k) me[1 + k] = tot[k];
         __threadfence();
         atomicExch(me, 1);
       }
@@ -235,47 +259,37 @@ __global__ void __launch_bounds__(SCAN_T) bin_scan_lb(const __grid_constant__ Gr
         const int q = hi - lane;  // lane 0 is the nearest predecessor
         int f = 0;
         if (q >= 0) {
-          for (int it = 0; it < LB_SPIN_LIMIT && f == 0; ++it) f = ld_volatile(st + 8 * q);
+          for (int it = 0; it < I.lb_spin && f == 0; ++it) f = ld_volatile(st + SCAN_REC * q);
           if (f == 0) atomicOr(&I.s.ctr[C_STATUS], ST_TIMEOUT);  // gave up: this step is invalid
         }
         __threadfence();
         const unsigned inc = __ballot_sync(0xffffffffu, q >= 0 && f == 2);
         const int upto = inc ? __ffs(inc) - 1 : 31;
-        int vn = 0, vb = 0, va = 0;
+        int vals[NSCAN] = {0, 0, 0, 0};
         if (q >= 0 && lane <= upto && f != 0) {
-          const int o = (f == 2) ? 4 : 1;
-          vn = ld_volatile(st + 8 * q + o);
-          vb = ld_volatile(st + 8 * q + o + 1);
-          va = ld_volatile(st + 8 * q + o + 2);
+          const int o = (f == 2) ? 1 + NSCAN : 1;
+#pragma unroll
+          for (int k = 0; k < NSCAN; ++k) vals[k] = ld_volatile(st + SCAN_REC * q + o + k);
         }
 #pragma unroll
-        for (int d = 16; d > 0; d >>= 1) {
-          vn += __shfl_xor_sync(0xffffffffu, vn, d);
-          vb += __shfl_xor_sync(0xffffffffu, vb, d);
-          va += __shfl_xor_sync(0xffffffffu, va, d);
-        }
-        en += vn;
-        eb += vb;
-        ea += va;
+        for (int k = 0; k < NSCAN; ++k) ex[k] += __reduce_add_sync(0xffffffffu, vals[k]);
         if (inc) break;
       }
     }
     if (lane == 0) {
-      me[4] = en + tn;
-      me[5] = eb + tb;
-      me[6] = ea + ta;
-      __threadfence();
-      atomicExch(me, 2);
-      s_excl[0] = en;
-      s_excl[1] = eb;
-      s_excl[2] = ea;
+      if (publish) {
+#pragma unroll
+        for (int k = 0; k < NSCAN; ++k) me[1 + NSCAN + k] = ex[k] + tot[k];
+        __threadfence();
+        atomicExch(me, 2);
+      }
+#pragma unroll
+      for (int k = 0; k < NSCAN; ++k) s_excl[k] = ex[k];
     }
   }
   __syncthreads();
-  const int on = s_excl[0], ob = s_excl[1], oa = s_excl[2];
-  pn += on;
-  pb += ob;
-  pa += oa;
+  int pn = pv[0] + s_excl[0], pb = pv[1] + s_excl[1], pa = pv[2] + s_excl[2], pr = pv[3] + s_excl[3];
+  const int ob = s_excl[1], oa = s_excl[2], orr = s_excl[3];
 #pragma unroll
   for (int r = 0; r < SCAN_ITEMS; ++r) {
     const int e = e0 + r;
@@ -285,6 +299,7 @@ __global__ void __launch_bounds__(SCAN_T) bin_scan_lb(const __grid_constant__ Gr
       if (ca[r] || (e == I.ntiles && cn[r] > 0)) {  // a binning item (the dead range comes last)
         I.s.active[pa] = make_int4(e, pn, pn + cn[r], 0);
         I.s.bin_rec[pa] = make_int4(I.old_start[e], I.old_start[e + 1], pb, pb + cb[r]);
+        if (cr[r]) I.s.resid[pr] = pa;
       }
       I.s.in_cnt[e] = 0;
       I.s.out_cnt[e] = 0;
@@ -293,6 +308,7 @@ __global__ void __launch_bounds__(SCAN_T) bin_scan_lb(const __grid_constant__ Gr
     pn += cn[r];
     pb += cb[r];
     pa += ca[r];
+    pr += cr[r];
   }
   if (threadIdx.x == 0 && c == 0) {
     I.s.ctr[C_MOVERS_SNAP] = I.s.ctr[C_MOVERS];
@@ -302,11 +318,12 @@ __global__ void __launch_bounds__(SCAN_T) bin_scan_lb(const __grid_constant__ Gr
   __syncthreads();  // new_start of the dead range is written (last chunk)
   if (threadIdx.x == 0) {
     if (c == nchunks - 1) {
-      const int nact = oa + ta;
+      const int nact = oa + tot[2];
       I.new_start[m] = (int32_t)I.n;
-      I.s.bucket_start[m] = ob + tb;
+      I.s.bucket_start[m] = ob + tot[1];
       const int dead_start = I.new_start[I.ntiles];
       I.s.ctr[C_ACTIVE] = nact;
+      I.s.ctr[C_RESID] = orr + tot[3];
       I.s.ctr[C_DEAD_START] = dead_start;
       I.s.ctr[C_BIN_ITEMS] = nact + ((int64_t)dead_start < I.n ? 1 : 0);
     }
@@ -314,13 +331,15 @@ __global__ void __launch_bounds__(SCAN_T) bin_scan_lb(const __grid_constant__ Gr
     s_last = atomicAdd(&G.work[W_SCAN_DONE], 1) == G.nblk_s - 1;
   }
   __syncthreads();
-  if (s_last) {  // every chunk of the group has finished its look-back
+  if (s_last) {  // every chunk of the group has finished its look-back (and read the step index)
     __threadfence();
     for (int ii = 0; ii < G.ninst; ++ii) {
-      int32_t *sti = G.inst[ii].s.scan_tot;
-      for (int k = threadIdx.x; k < G.sblk[ii + 1] - G.sblk[ii]; k += blockDim.x) sti[8 * k] = 0;
+      const InstArgs &J = ONE ? I : G.inst[ii];
+      int32_t *sti = J.s.scan_tot;
+      for (int k = threadIdx.x; k < G.sblk[ii + 1] - G.sblk[ii]; k += blockDim.x) sti[SCAN_REC * k] = 0;
+      if (threadIdx.x == 0) J.s.ctr[C_STEP] = __ldcg(J.s.ctr + C_STEP) + 1;
     }
-    group_prefix_body(G, wsum3[0]);
+    group_prefix_body(G, wsum4[0]);
   }
 }
 
@@ -345,16 +364,17 @@ __global__ void bin_bucket(const __grid_constant__ GroupArgs G) {
 
 // One CTA per instance (instances of at most SCAN1_MAX tiles): the whole scan
 // over the instance's tiles in one pass -- new ranges, arrival offsets, the
-// active list, counter resets.  Warp w owns the K consecutive 32-tile chunks
-// from tile 32 K w (K = ceil(tiles / SCAN1_T) <= SCAN1_K); lane l holds tile
-// l of each chunk, so every load and store is coalesced and all the loads
-// are in flight at once.  The warps' totals go through one CTA scan, then
-// each warp scans its chunks in order with a running offset.  For a group of
-// one the CTA then writes the group's prefixes itself; otherwise the CTA that
-// finishes last (counted on a work counter, no waiting) computes them.
+// active and residual lists, counter resets.  Warp w owns the K consecutive
+// 32-tile chunks from tile 32 K w (K = ceil(tiles / SCAN1_T) <= SCAN1_K);
+// lane l holds tile l of each chunk, so every load and store is coalesced and
+// all the loads are in flight at once.  The warps' totals go through one CTA
+// scan, then each warp scans its chunks in order with a running offset.  The
+// CTA then advances the instance's step index.  For a group of one the CTA
+// writes the group's prefixes itself; otherwise the CTA that finishes last
+// (counted on a work counter, no waiting) computes them.
 template <bool ONE>
 __global__ void __launch_bounds__(SCAN1_T) bin_scan_one(const __grid_constant__ GroupArgs G) {
-  __shared__ int wsum3[3][32];
+  __shared__ int wsum4[NSCAN][32];
   __shared__ int s_last;
   __shared__ InstArgs sI;
   pdl_trigger();
@@ -366,32 +386,35 @@ __global__ void __launch_bounds__(SCAN1_T) bin_scan_one(const __grid_constant__ 
   const int lane = threadIdx.x & 31;
   const int K = (m + SCAN1_T - 1) / SCAN1_T;       // <= SCAN1_K: the host checks m <= SCAN1_MAX
   const int seg0 = (threadIdx.x >> 5) * K * 32;  // this warp's first tile
-  int cn[SCAN1_K], cb[SCAN1_K];
-  int v[3] = {0, 0, 0};  // this lane's count, arrivals, active tiles
+  const int step = __ldcg(I.s.ctr + C_STEP) + 1;  // this step's index (thread 0 stores it at the end)
+  const bool frozen = (__ldcg(I.s.ctr + C_STATUS) & ST_TIMEOUT) != 0;
+  int cn[SCAN1_K], cb[SCAN1_K], cr[SCAN1_K];
+  int v[NSCAN] = {0, 0, 0, 0};  // this lane's count, arrivals, active tiles, residual items
 #pragma unroll
   for (int r = 0; r < SCAN1_K; ++r) {
     const int e = seg0 + r * 32 + lane;
-    cn[r] = cb[r] = 0;
+    cn[r] = cb[r] = cr[r] = 0;
     if (r < K && e < m) {
-      const int in = I.s.in_cnt[e], out = I.s.out_cnt[e];
-      cn[r] = (I.old_start[e + 1] - I.old_start[e]) - out + in;
-      cb[r] = in;
-      v[2] += (e < I.ntiles && cn[r] > 0) ? 1 : 0;
+      int ca;
+      tile_counts(I, e, step, frozen, cn[r], cb[r], ca, cr[r]);
+      v[2] += ca;
     }
     v[0] += cn[r];
     v[1] += cb[r];
+    v[3] += cr[r];
   }
   // offsets of the warps: a CTA scan of the warp totals (held by lane 0)
-  int tot[3];
+  int tot[NSCAN];
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < NSCAN; ++k) {
     v[k] = __reduce_add_sync(0xffffffffu, v[k]);
     if (lane) v[k] = 0;
   }
-  cta_excl3(v, wsum3, tot);
+  cta_excl4(v, wsum4, tot);
   int on = __shfl_sync(0xffffffffu, v[0], 0);
   int ob = __shfl_sync(0xffffffffu, v[1], 0);
   int oa = __shfl_sync(0xffffffffu, v[2], 0);
+  int orr = __shfl_sync(0xffffffffu, v[3], 0);
   const unsigned lt_mask = (1u << lane) - 1u;
 #pragma unroll
   for (int r = 0; r < SCAN1_K; ++r) {
@@ -400,6 +423,7 @@ __global__ void __launch_bounds__(SCAN1_T) bin_scan_one(const __grid_constant__ 
       const int in_n = warp_incl(cn[r]), in_b = warp_incl(cb[r]);
       const bool act = e < I.ntiles && cn[r] > 0;
       const unsigned am = __ballot_sync(0xffffffffu, act);
+      const unsigned rm = __ballot_sync(0xffffffffu, cr[r] != 0);
       if (e < m) {
         const int pn = on + in_n - cn[r], pb = ob + in_b - cb[r];
         I.new_start[e] = pn;
@@ -408,6 +432,7 @@ __global__ void __launch_bounds__(SCAN1_T) bin_scan_one(const __grid_constant__ 
           const int k = oa + __popc(am & lt_mask);
           I.s.active[k] = make_int4(e, pn, pn + cn[r], 0);
           I.s.bin_rec[k] = make_int4(I.old_start[e], I.old_start[e + 1], pb, pb + cb[r]);
+          if (cr[r]) I.s.resid[orr + __popc(rm & lt_mask)] = k;
         }
         I.s.in_cnt[e] = 0;
         I.s.out_cnt[e] = 0;
@@ -416,18 +441,21 @@ __global__ void __launch_bounds__(SCAN1_T) bin_scan_one(const __grid_constant__ 
       on += __shfl_sync(0xffffffffu, in_n, 31);
       ob += __shfl_sync(0xffffffffu, in_b, 31);
       oa += __popc(am);
+      orr += __popc(rm);
     }
   }
-  const int ob_all = tot[1], oa_all = tot[2];
-  __syncthreads();  // new_start of the dead range is written
+  const int ob_all = tot[1], oa_all = tot[2], or_all = tot[3];
+  __syncthreads();  // new_start of the dead range is written; every thread has read the step index
   if (threadIdx.x == 0) {
     I.s.ctr[C_MOVERS_SNAP] = I.s.ctr[C_MOVERS];
     I.s.ctr[C_MOVERS] = 0;
     I.s.ctr[C_APEX] = 0;
+    I.s.ctr[C_STEP] = step;
     I.new_start[m] = (int32_t)I.n;
     I.s.bucket_start[m] = ob_all;
     const int dead_start = I.new_start[I.ntiles];
     I.s.ctr[C_ACTIVE] = oa_all;
+    I.s.ctr[C_RESID] = or_all;
     I.s.ctr[C_DEAD_START] = dead_start;
     const int bin_items = oa_all + ((int64_t)dead_start < I.n ? 1 : 0);
     I.s.ctr[C_BIN_ITEMS] = bin_items;
@@ -436,6 +464,8 @@ __global__ void __launch_bounds__(SCAN1_T) bin_scan_one(const __grid_constant__ 
       G.bin_items[1] = bin_items;
       G.act_items[0] = 0;
       G.act_items[1] = oa_all;
+      G.res_items[0] = 0;
+      G.res_items[1] = or_all;
     } else {
       __threadfence();
       s_last = atomicAdd(&G.work[W_SCAN_DONE], 1) == G.ninst - 1;
@@ -448,7 +478,7 @@ __global__ void __launch_bounds__(SCAN1_T) bin_scan_one(const __grid_constant__ 
   __syncthreads();
   if (s_last) {
     __threadfence();
-    group_prefix_body(G, wsum3[0]);
+    group_prefix_body(G, wsum4[0]);
   }
 }
 

@@ -193,31 +193,161 @@ constexpr int p2g_threads() {
 // multiple of eight apart, read different shared-memory banks.
 __device__ __forceinline__ int rec_slot(int i) { return (i & ~7) | ((i ^ (i >> 3)) & 7); }
 
-template <int D, int MODE, bool ONE>
+// The P2G record of one particle: offset u, and the per-particle factors of
+// the channels -- m and m v (mass, momentum), nV sig with nV = -V (internal
+// force f_k = -V sum_j sig_kj dN/dx_j).  The same arithmetic wherever a record
+// is formed (from stored state, or in G2P from the state it has just
+// computed), so a particle's contributions do not depend on where.
+template <int D, int MODE>
+__device__ __forceinline__ void p2g_record(const float *u, float mm, const float *v, float jm1, const float *sg,
+                                           float inv_rho, float f[4 * P2GRec<D, MODE>::NQ]) {
+  using R = P2GRec<D, MODE>;
+#pragma unroll
+  for (int k = 0; k < 4 * R::NQ; ++k) f[k] = 0.f;
+#pragma unroll
+  for (int k = 0; k < D; ++k) f[k] = u[k];
+  if (R::HAS_M) {
+    f[D] = mm;
+#pragma unroll
+    for (int k = 0; k < D; ++k) f[D + 1 + k] = mm * v[k];
+  }
+  if (R::HAS_F) {
+    const float nV = -mm * inv_rho * (1.f + jm1);
+    constexpr int o = R::HAS_M ? 2 * D + 1 : D;
+    if (D == 3) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) f[o + k] = nV * sg[k];
+    } else {
+      f[o] = nV * sg[0];
+      f[o + 1] = nV * sg[1];
+      f[o + 2] = nV * sg[3];
+    }
+  }
+}
+
+// Accumulate the channels of the thread's corners (my_cp + r * CPC) over the
+// records i0..i1-1 of one cell, in order (plain sequential FP32 sums).
+template <int D, int MODE>
+__device__ __forceinline__ void accumulate_cell(const float4 *rec, int i0, int i1, int my_cp, float inv_h,
+                                                float acc[P2GRec<D, MODE>::CPT][p2g_channels<D, MODE>()]) {
+  using R = P2GRec<D, MODE>;
+  constexpr int NQ = R::NQ, CH = R::CH, CPT = R::CPT, CPC = R::CPC;
+  constexpr bool HAS_M = R::HAS_M, HAS_F = R::HAS_F;
+  for (int i = i0; i < i1; ++i) {
+    const int sl = rec_slot(i);
+    float f[4 * NQ];
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) {
+      const float4 rv = rec[k * CH + sl];
+      f[4 * k] = rv.x;
+      f[4 * k + 1] = rv.y;
+      f[4 * k + 2] = rv.z;
+      f[4 * k + 3] = rv.w;
+    }
+    static_assert(CPT == (D == 3 ? 2 : 1) && CPC == 4, "corners my_cp + 4 r: z bit = r");
+    const ThreadCorners<D> tc(f, my_cp, inv_h);
+#pragma unroll
+    for (int r = 0; r < CPT; ++r) {
+      float N, Gr[D];
+      tc.corner(r, N, Gr);
+      if (HAS_M) {
+        acc[r][0] = fmaf(f[D], N, acc[r][0]);
+#pragma unroll
+        for (int k = 0; k < D; ++k) acc[r][1 + k] = fmaf(f[D + 1 + k], N, acc[r][1 + k]);
+      }
+      if (HAS_F) {
+        constexpr int o = HAS_M ? 2 * D + 1 : D;
+        constexpr int a0 = HAS_M ? 1 + D : 0;
+        if (D == 3) {
+          // nV sig: xx yy zz xy yz xz
+          const float t3[3][3] = {{f[o], f[o + 3], f[o + 5]}, {f[o + 3], f[o + 1], f[o + 4]},
+                                  {f[o + 5], f[o + 4], f[o + 2]}};
+#pragma unroll
+          for (int k = 0; k < D; ++k)
+#pragma unroll
+            for (int jj = 0; jj < D; ++jj) acc[r][a0 + k] = fmaf(t3[k][jj], Gr[jj], acc[r][a0 + k]);
+        } else {
+          const float t2[2][2] = {{f[o], f[o + 2]}, {f[o + 2], f[o + 1]}};
+#pragma unroll
+          for (int k = 0; k < D; ++k)
+#pragma unroll
+            for (int jj = 0; jj < D; ++jj) acc[r][a0 + k] = fmaf(t2[k][jj], Gr[jj], acc[r][a0 + k]);
+        }
+      }
+    }
+  }
+}
+
+// Cell sums (cellP[cell][corner][channel]) -> the tile's node box, summed in
+// ascending local cell order with compensated (TwoSum) accumulation, written
+// to the tile's slot.  Every thread of the CTA (nthreads) takes part.
+template <int D, int NCH>
+__device__ __forceinline__ void cells_to_slot(const float *cellP, float *slots_out, int t, int nthreads) {
+  constexpr int BN = box_nodes<D>();
+  constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ;
+  constexpr int NV = (1 << D) * NCH;
+  for (int b = threadIdx.x; b < BN; b += nthreads) {
+    const int bx = b % (TX + 1);
+    const int by = (b / (TX + 1)) % (TY + 1);
+    const int bz = D == 3 ? b / ((TX + 1) * (TY + 1)) : 0;
+    TwoAcc<float> ta[NCH];
+#pragma unroll
+    for (int ch = 0; ch < NCH; ++ch) ta[ch].init();
+#pragma unroll
+    for (int dz = (D == 3 ? 1 : 0); dz >= 0; --dz)
+#pragma unroll
+      for (int dy = 1; dy >= 0; --dy)
+#pragma unroll
+        for (int dx = 1; dx >= 0; --dx) {
+          const int cx = bx - dx, cy = by - dy, cz = bz - dz;
+          if (cx < 0 || cx >= TX || cy < 0 || cy >= TY || cz < 0 || cz >= TZ) continue;
+          const int cl = cx + TX * (cy + TY * cz);
+          const int a = dx + 2 * dy + 4 * dz;
+#pragma unroll
+          for (int ch = 0; ch < NCH; ++ch) ta[ch].add(cellP[cl * NV + a * NCH + ch]);
+        }
+#pragma unroll
+    for (int ch = 0; ch < NCH; ++ch) slots_out[((int64_t)t * NCH + ch) * BN + b] = ta[ch].value();
+  }
+}
+
+// P2G over tiles.  Plain (RES false): the work items are the active tiles,
+// every particle of a tile is staged, the box goes to slots1 (slots2 for the
+// USF force stage).  Residual (RES, USL): the items are the active tiles whose
+// next-step P2G the previous G2P did not complete (the scan's residual
+// list): a tile without valid sums for this step (fepoch != step) sums all
+// its particles into slots1 (fepoch = step); a tile with valid sums sums only
+// the particles that arrived from other tiles -- those outside the tile's old
+// range -- into slots_a (aepoch = step).  Staged particles are compacted in
+// binning order, so the cells' runs stay contiguous.
+template <int D, int MODE, bool ONE, bool RES>
 __global__ void __launch_bounds__(P2GRec<D, MODE>::CH, p2g_min_blocks<D, MODE, ONE>())
     p2g_tile(const __grid_constant__ GroupArgs G, int work_slot) {
+  static_assert(!RES || MODE == P2G_USL, "the residual P2G is the USL one");
   using R = P2GRec<D, MODE>;
   constexpr int NCH = p2g_channels<D, MODE>();
   constexpr int NV = R::NV;
   constexpr int CH = R::CH;
   constexpr int NQ = R::NQ;
   constexpr int CPT = R::CPT, CPC = R::CPC;
-  constexpr int BN = box_nodes<D>();
-  constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ;
-  constexpr bool HAS_M = R::HAS_M, HAS_F = R::HAS_F;
+  constexpr int NW = CH / 32;
   extern __shared__ float4 sm4[];
   float4 *rec = sm4;                              // [NQ][CH] float4
   float *cellP = reinterpret_cast<float *>(sm4);  // [64][NV], after the chunks
   __shared__ int cs[CELLS_PER_TILE], ce[CELLS_PER_TILE], stamp[CELLS_PER_TILE];
   __shared__ int s_work[2];
+  __shared__ int ccell[RES ? CH : 1];
+  __shared__ int wkeep[NW + 1];
   __shared__ InstArgs sI;
   const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
   const int my_cell = tid / CPC, my_cp = tid % CPC;  // corners my_cp + r * CPC
   pdl_trigger();
   if (tid < CELLS_PER_TILE) stamp[tid] = -1;
   pdl_wait();
+  const int32_t *items = RES ? G.res_items : G.act_items;
   // items: first the CTA's own (blockIdx.x), then gridDim.x + the work counter
-  const int total = G.act_items[G.ninst];
+  const int total = items[G.ninst];
   if (tid == 0) s_work[0] = blockIdx.x;
   __syncthreads();
   int chunk_id = 0, loaded = -1;
@@ -228,7 +358,7 @@ __global__ void __launch_bounds__(P2GRec<D, MODE>::CH, p2g_min_blocks<D, MODE, O
     // the next work item is fetched now and published at the end of this one
     int wnext = 0;
     if (tid == 0) wnext = (int)gridDim.x + atomicAdd(&G.work[work_slot], 1);
-    const int ii = ONE ? 0 : find_inst(G.act_items, G.ninst, wi);
+    const int ii = ONE ? 0 : find_inst(items, G.ninst, wi);
     if (!ONE && ii != loaded) {  // uniform
       copy_inst(G.inst, ii, &sI);
       loaded = ii;
@@ -236,9 +366,20 @@ __global__ void __launch_bounds__(P2GRec<D, MODE>::CH, p2g_min_blocks<D, MODE, O
     }
     const InstArgs &I = inst_ref<ONE>(G, sI);
     const Geo &g = I.geo;
-    float *slots_out = MODE == P2G_FORCE ? I.s.slots2 : I.s.slots1;
-    const int4 ar = I.s.active[ONE ? wi : wi - G.act_items[ii]];
+    const int local = ONE ? wi : wi - items[ii];
+    const int aidx = RES ? I.s.resid[local] : local;
+    const int4 ar = I.s.active[aidx];
     const int t = ar.x, s = ar.y, e = ar.z;
+    int os = 0, oe = 0, step = 0;
+    bool full = true;
+    if (RES) {
+      const int4 br = I.s.bin_rec[aidx];
+      os = br.x;
+      oe = br.y;
+      step = I.s.ctr[C_STEP];
+      full = I.s.fepoch[t] != step;  // uniform
+    }
+    float *slots_out = MODE == P2G_FORCE ? I.s.slots2 : (RES && !full ? I.s.slots_a : I.s.slots1);
     float acc[CPT][NCH];
 #pragma unroll
     for (int r = 0; r < CPT; ++r)
@@ -249,36 +390,69 @@ __global__ void __launch_bounds__(P2GRec<D, MODE>::CH, p2g_min_blocks<D, MODE, O
       // ---- stage this chunk: particle q = c0 + tid
       const int q = c0 + tid;
       const int c1 = min(e, c0 + CH);
-      if (q < c1) {
+      if constexpr (RES) {
+        int j = 0, lc = 0;
+        bool keep = false;
+        if (q < c1) {
+          j = I.perm_out[q];
+          lc = I.keys_out[q] & (CELLS_PER_TILE - 1);
+          keep = full || j < os || j >= oe;
+        }
+        // compaction in binning order: warp counts, then offsets over the warps
+        const unsigned km = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0) wkeep[warp] = __popc(km);
+        __syncthreads();
+        int base = 0, nkeep = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+          const int c = wkeep[w];
+          base += w < warp ? c : 0;
+          nkeep += c;
+        }
+        const int idx = base + __popc(km & ((1u << lane) - 1u));
+        if (keep) {
+          const PBuf &A = I.A;
+          float u[D], v[D], sg[6];
+#pragma unroll
+          for (int k = 0; k < D; ++k) {
+            u[k] = A.off(k)[j];
+            v[k] = A.vel(k)[j];
+          }
+#pragma unroll
+          for (int k = 0; k < 6; ++k) sg[k] = k < nstress<D>() ? A.sig(k)[j] : 0.f;
+          float f[4 * NQ];
+          p2g_record<D, MODE>(u, A.mass()[j], v, A.jm1()[j], sg, g.inv_rho, f);
+          const int sl = rec_slot(idx);
+#pragma unroll
+          for (int k = 0; k < NQ; ++k)
+            rec[k * CH + sl] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
+          ccell[idx] = lc;
+        }
+        __syncthreads();
+        if (keep) {  // run boundaries of the cell among the staged particles
+          if (idx == 0 || ccell[idx - 1] != lc) {
+            cs[lc] = idx;
+            stamp[lc] = chunk_id;
+          }
+          if (idx == nkeep - 1 || ccell[idx + 1] != lc) ce[lc] = idx + 1;
+        }
+      } else if (q < c1) {
         const int j = I.perm_out[q];
         const int lc = I.keys_out[q] & (CELLS_PER_TILE - 1);
+        // FORCE (USF) reads the stress updated earlier this step, stored in
+        // binning order; USL and MOM read the state at the start of the step
+        const PBuf &S = (MODE == P2G_FORCE) ? I.B : I.A;
+        const int js = (MODE == P2G_FORCE) ? q : j;
+        float u[D], v[D], sg[6];
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          u[k] = I.A.off(k)[j];
+          v[k] = R::HAS_M ? I.A.vel(k)[j] : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) sg[k] = (R::HAS_F && k < nstress<D>()) ? S.sig(k)[js] : 0.f;
         float f[4 * NQ];
-#pragma unroll
-        for (int k = 0; k < 4 * NQ; ++k) f[k] = 0.f;
-#pragma unroll
-        for (int k = 0; k < D; ++k) f[k] = I.A.off(k)[j];
-        const float mm = I.A.mass()[j];
-        if (HAS_M) {
-          f[D] = mm;
-#pragma unroll
-          for (int k = 0; k < D; ++k) f[D + 1 + k] = mm * I.A.vel(k)[j];
-        }
-        if (HAS_F) {
-          // FORCE (USF) reads the stress updated earlier this step, stored in
-          // binning order; USL reads the stress at the start of the step
-          const PBuf &S = (MODE == P2G_FORCE) ? I.B : I.A;
-          const int js = (MODE == P2G_FORCE) ? q : j;
-          const float nV = -mm * g.inv_rho * (1.f + S.jm1()[js]);
-          constexpr int o = HAS_M ? 2 * D + 1 : D;
-          if (D == 3) {
-#pragma unroll
-            for (int k = 0; k < 6; ++k) f[o + k] = nV * S.sig(k)[js];
-          } else {
-            f[o] = nV * S.sig(0)[js];
-            f[o + 1] = nV * S.sig(1)[js];
-            f[o + 2] = nV * S.sig(3)[js];
-          }
-        }
+        p2g_record<D, MODE>(u, I.A.mass()[j], v, R::HAS_F ? S.jm1()[js] : 0.f, sg, g.inv_rho, f);
         const int sl = rec_slot(tid);
 #pragma unroll
         for (int k = 0; k < NQ; ++k) rec[k * CH + sl] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
@@ -293,52 +467,7 @@ __global__ void __launch_bounds__(P2GRec<D, MODE>::CH, p2g_min_blocks<D, MODE, O
       }
       __syncthreads();
       // ---- accumulate my (cell, corner) pairs over the cell's particles in order
-      if (stamp[my_cell] == chunk_id) {
-        const int i0 = cs[my_cell], i1 = ce[my_cell];
-        for (int i = i0; i < i1; ++i) {
-          const int sl = rec_slot(i);
-          float f[4 * NQ];
-#pragma unroll
-          for (int k = 0; k < NQ; ++k) {
-            const float4 rv = rec[k * CH + sl];
-            f[4 * k] = rv.x;
-            f[4 * k + 1] = rv.y;
-            f[4 * k + 2] = rv.z;
-            f[4 * k + 3] = rv.w;
-          }
-          static_assert(CPT == (D == 3 ? 2 : 1) && CPC == 4, "corners my_cp + 4 r: z bit = r");
-          const ThreadCorners<D> tc(f, my_cp, g.inv_h);
-#pragma unroll
-          for (int r = 0; r < CPT; ++r) {
-            float N, Gr[D];
-            tc.corner(r, N, Gr);
-            if (HAS_M) {
-              acc[r][0] = fmaf(f[D], N, acc[r][0]);
-#pragma unroll
-              for (int k = 0; k < D; ++k) acc[r][1 + k] = fmaf(f[D + 1 + k], N, acc[r][1 + k]);
-            }
-            if (HAS_F) {
-              constexpr int o = HAS_M ? 2 * D + 1 : D;
-              constexpr int a0 = HAS_M ? 1 + D : 0;
-              if (D == 3) {
-                // nV sig: xx yy zz xy yz xz
-                const float t3[3][3] = {{f[o], f[o + 3], f[o + 5]}, {f[o + 3], f[o + 1], f[o + 4]},
-                                        {f[o + 5], f[o + 4], f[o + 2]}};
-#pragma unroll
-                for (int k = 0; k < D; ++k)
-#pragma unroll
-                  for (int jj = 0; jj < D; ++jj) acc[r][a0 + k] = fmaf(t3[k][jj], Gr[jj], acc[r][a0 + k]);
-              } else {
-                const float t2[2][2] = {{f[o], f[o + 2]}, {f[o + 2], f[o + 1]}};
-#pragma unroll
-                for (int k = 0; k < D; ++k)
-#pragma unroll
-                  for (int jj = 0; jj < D; ++jj) acc[r][a0 + k] = fmaf(t2[k][jj], Gr[jj], acc[r][a0 + k]);
-              }
-            }
-          }
-        }
-      }
+      if (stamp[my_cell] == chunk_id) accumulate_cell<D, MODE>(rec, cs[my_cell], ce[my_cell], my_cp, g.inv_h, acc);
       ++chunk_id;
       __syncthreads();  // the next chunk overwrites the records
     }
@@ -349,30 +478,16 @@ __global__ void __launch_bounds__(P2GRec<D, MODE>::CH, p2g_min_blocks<D, MODE, O
 #pragma unroll
       for (int ch = 0; ch < NCH; ++ch) cellP[my_cell * NV + (my_cp + r * CPC) * NCH + ch] = acc[r][ch];
     __syncthreads();
-    for (int b = tid; b < BN; b += CH) {
-      const int bx = b % (TX + 1);
-      const int by = (b / (TX + 1)) % (TY + 1);
-      const int bz = D == 3 ? b / ((TX + 1) * (TY + 1)) : 0;
-      TwoAcc<float> ta[NCH];
-#pragma unroll
-      for (int ch = 0; ch < NCH; ++ch) ta[ch].init();
-#pragma unroll
-      for (int dz = (D == 3 ? 1 : 0); dz >= 0; --dz)
-#pragma unroll
-        for (int dy = 1; dy >= 0; --dy)
-#pragma unroll
-          for (int dx = 1; dx >= 0; --dx) {
-            const int cx = bx - dx, cy = by - dy, cz = bz - dz;
-            if (cx < 0 || cx >= TX || cy < 0 || cy >= TY || cz < 0 || cz >= TZ) continue;
-            const int cl = cx + TX * (cy + TY * cz);
-            const int a = dx + 2 * dy + 4 * dz;
-#pragma unroll
-            for (int ch = 0; ch < NCH; ++ch) ta[ch].add(cellP[cl * NV + a * NCH + ch]);
-          }
-#pragma unroll
-      for (int ch = 0; ch < NCH; ++ch) slots_out[((int64_t)t * NCH + ch) * BN + b] = ta[ch].value();
+    cells_to_slot<D, NCH>(cellP, slots_out, t, CH);
+    if (tid == 0) {
+      if (RES) {
+        if (full)
+          I.s.fepoch[t] = step;
+        else
+          I.s.aepoch[t] = step;
+      }
+      s_work[(it + 1) & 1] = wnext;
     }
-    if (tid == 0) s_work[(it + 1) & 1] = wnext;
     __syncthreads();
   }
 }
@@ -451,6 +566,39 @@ __device__ __forceinline__ void gather_node(const Geo &g, const float *slots, in
   for (int c = 0; c < NOUT; ++c) out[c] = acc[c].value();
 }
 
+// USL: sum channels of node I over the active tiles `act` in ascending tile
+// order, taking each tile's sums of the particles that stayed (slots1) when
+// they are for this step (bit of fmask27, the 3 x 3 x 3 neighbourhood of tc)
+// and of the particles that arrived (slots_a) when those are (amask27).
+template <int D, int NOUT>
+__device__ __forceinline__ void gather_node_usl(const Geo &g, const float *slots, const float *slots_a, const int I[3],
+                                                const int lo[3], const int hi[3], const int tc[3], unsigned act,
+                                                unsigned fmask27, unsigned amask27, float out[NOUT]) {
+  constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ;
+  constexpr int BN = box_nodes<D>();
+  TwoAcc<float> acc[NOUT];
+#pragma unroll
+  for (int c = 0; c < NOUT; ++c) acc[c].init();
+  int idx = 0;
+  for (int z = lo[2]; z <= hi[2]; ++z)
+    for (int y = lo[1]; y <= hi[1]; ++y)
+      for (int x = lo[0]; x <= hi[0]; ++x, ++idx) {
+        if (!((act >> idx) & 1u)) continue;
+        const int nb = (z - tc[2] + 1) * 9 + (y - tc[1] + 1) * 3 + (x - tc[0] + 1);
+        const int t2 = x + g.nt[0] * (y + g.nt[1] * z);
+        const int bx = I[0] - x * TX, by = I[1] - y * TY, bz = D == 3 ? I[2] - z * TZ : 0;
+        const int bl = bx + (TX + 1) * (by + (TY + 1) * bz);
+        if ((fmask27 >> nb) & 1u)
+#pragma unroll
+          for (int c = 0; c < NOUT; ++c) acc[c].add(slots[((int64_t)t2 * NOUT + c) * BN + bl]);
+        if ((amask27 >> nb) & 1u)
+#pragma unroll
+          for (int c = 0; c < NOUT; ++c) acc[c].add(slots_a[((int64_t)t2 * NOUT + c) * BN + bl]);
+      }
+#pragma unroll
+  for (int c = 0; c < NOUT; ++c) out[c] = acc[c].value();
+}
+
 // Work items dealt to the warps of the grid in turn (the work per item is
 // uniform): a 32-node slice of an active tile's box when there are few
 // active tiles, a whole box (four slices in turn) when there are enough to
@@ -494,8 +642,9 @@ __global__ void __launch_bounds__(NODE_T, ONE ? MPM_NODE_MINB : 8) node_tile(con
     const int t = I.s.active[ONE ? item : item - G.act_items[ii]].x;
     int tc[3];
     tile_coords(g, t, tc);
-    // activity of the 27 tiles around t, one lane each
-    bool nact = false;
+    // activity of the 27 tiles around t, one lane each (USL: and whether
+    // their stayers' and arrivals' sums are for this step)
+    bool nact = false, fv = false, av = false;
     if (lane < 27) {
       const int d[3] = {lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1};
       const int n3[3] = {tc[0] + d[0], tc[1] + d[1], tc[2] + d[2]};
@@ -505,9 +654,15 @@ __global__ void __launch_bounds__(NODE_T, ONE ? MPM_NODE_MINB : 8) node_tile(con
       if (in) {
         const int t2 = n3[0] + g.nt[0] * (n3[1] + g.nt[1] * n3[2]);
         nact = I.new_start[t2 + 1] > I.new_start[t2];
+        if (NMODE == NODE_USL) {
+          const int step = I.s.ctr[C_STEP];
+          fv = I.s.fepoch[t2] == step;
+          av = I.s.aepoch[t2] == step;
+        }
       }
     }
     const unsigned nmask = __ballot_sync(0xffffffffu, nact);
+    const unsigned fmask27 = __ballot_sync(0xffffffffu, fv), amask27 = __ballot_sync(0xffffffffu, av);
     // One warp walking a whole box whose lower neighbours are all active
     // computes just the nodes at local 1..T on every axis: a node on a lower
     // face (a local coordinate 0) is held by the active lower neighbour
@@ -533,7 +688,7 @@ __global__ void __launch_bounds__(NODE_T, ONE ? MPM_NODE_MINB : 8) node_tile(con
       for (int k = 0; k < D; ++k) v[k] = a[k] = vn[k] = 0.f;
       float c1[1 + 2 * D];
       if (NMODE == NODE_USL)
-        gather_node<D, 1 + 2 * D>(g, I.s.slots1, NCH1, Ig, lo, hi, act, c1);
+        gather_node_usl<D, 1 + 2 * D>(g, I.s.slots1, I.s.slots_a, Ig, lo, hi, tc, act, fmask27, amask27, c1);
       else
         gather_node<D, 1 + D>(g, I.s.slots1, NCH1, Ig, lo, hi, act, c1);
       const float m = c1[0];
@@ -858,6 +1013,410 @@ __global__ void __launch_bounds__(G2P_T, MPM_G2P_MINB) g2p(const __grid_constant
   if (status) atomicOr(&I.s.ctr[C_STATUS], status);
 }
 
+// Every field of particle j of A copied to slot q of B (a particle that left
+// the mesh earlier is carried over unchanged).
+template <int D>
+__device__ __forceinline__ void copy_particle(const PBuf &A, const PBuf &B, int j, int64_t q) {
+  constexpr int NS = nstress<D>();
+  B.key()[q] = A.key()[j];
+  B.id()[q] = A.id()[j];
+  B.mass()[q] = A.mass()[j];
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    B.off(k)[q] = A.off(k)[j];
+    B.vel(k)[q] = A.vel(k)[j];
+  }
+  if (A.coh()) B.coh()[q] = A.coh()[j];
+#pragma unroll
+  for (int i = 0; i < NS; ++i) {
+    B.sig(i)[q] = A.sig(i)[j];
+    B.eps(i)[q] = A.eps(i)[j];
+  }
+  B.jm1()[q] = A.jm1()[j];
+  B.epsp()[q] = A.epsp()[j];
+}
+
+__device__ __forceinline__ int warp_incl(int x) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+
+// ---------------------------------------------------------------------------
+// USL G2P fused with the next step's P2G: one CTA per active tile (and one
+// item for the particles that left the mesh earlier).  The CTA loads the node
+// records of the tile's box into shared memory once; then, in chunks of one
+// particle per thread (binning order), each thread runs the particle's whole
+// G2P update -- FLIP velocity, advection and relocation, strain, stress,
+// volume -- from the box, with the particle's state copied to shared memory
+// by cp.async while the node gather runs.  A particle that stays in the tile
+// then forms its P2G record for the next step (the same arithmetic as P2G
+// from the stored state); the chunk's records are sorted by their new local
+// cell (stable: counts per warp, then a scan), and each thread of a (cell,
+// corner pair) adds its cell's records in order to its running sums in
+// shared memory.  At the end the cells go to the tile's node box and the box
+// to slots1, valid for the next step (fepoch = step + 1).  Particles that
+// leave the tile are left to the next step's residual P2G (they arrive in
+// another tile), as are tiles whose FP64 apex-band returns change a stress
+// after this kernel (apex_band_k invalidates their sums).  Summing in
+// binning order, chunk after chunk, gives each (cell, corner) the order the
+// plain P2G would use, so a tile that no particle enters has the same sums.
+// ---------------------------------------------------------------------------
+#ifndef MPM_G2PF_MINB
+#define MPM_G2PF_MINB 3  // resident fused G2P CTAs per SM the register budget is sized for
+#endif
+template <int D>
+struct G2PF {
+  using R = P2GRec<D, P2G_USL>;
+  static constexpr int T = R::CH;  // threads: a particle each in G2P, a (cell, corner pair) each in P2G
+  static constexpr int NCH = 1 + 2 * D, NV = R::NV, NQ = R::NQ, NS = nstress<D>();
+  static constexpr int NREC = D == 3 ? 2 : 1;  // float4 node records per node
+  static constexpr int BN = box_nodes<D>();
+  // staged state: sig, eps, J-1, eps_p, velocity, mass, id, cohesion
+  static constexpr int S_SIG = 0, S_EPS = NS, S_JM1 = 2 * NS, S_EPSP = 2 * NS + 1, S_VEL = 2 * NS + 2,
+                       S_MASS = S_VEL + D, S_ID = S_MASS + 1, S_COH = S_ID + 1, NSTG = S_COH + 1;
+  static constexpr size_t STG_BYTES = sizeof(float) * NSTG * T;
+  static constexpr size_t REC_BYTES = sizeof(float4) * NQ * T;
+  static constexpr size_t UNION_BYTES = ((STG_BYTES > REC_BYTES ? STG_BYTES : REC_BYTES) + 15) / 16 * 16;
+  static constexpr size_t CELLP_BYTES = (sizeof(float) * CELLS_PER_TILE * NV + 15) / 16 * 16;
+  static constexpr size_t NODES_BYTES = sizeof(float4) * BN * NREC;
+  static constexpr size_t SMEM = UNION_BYTES + CELLP_BYTES + NODES_BYTES;
+};
+
+template <int D, bool ONE>
+__global__ void __launch_bounds__(G2PF<D>::T, MPM_G2PF_MINB) g2p_tile(const __grid_constant__ GroupArgs G) {
+  using F = G2PF<D>;
+  constexpr int T = F::T, NCH = F::NCH, NV = F::NV, NQ = F::NQ, NS = F::NS, NREC = F::NREC, BN = F::BN;
+  constexpr int NC = 1 << D;
+  constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ;
+  constexpr int CPT = F::R::CPT, CPC = F::R::CPC;
+  constexpr int NW = T / 32;
+  extern __shared__ float4 sm4[];
+  float *stg = reinterpret_cast<float *>(sm4);  // [NSTG][T] staged state, then (aliased) the records
+  float4 *rec = sm4;                            // [NQ][T]
+  float *cellP = reinterpret_cast<float *>(reinterpret_cast<char *>(sm4) + F::UNION_BYTES);  // [64][NV]
+  float4 *nodes_s = reinterpret_cast<float4 *>(reinterpret_cast<char *>(sm4) + F::UNION_BYTES + F::CELLP_BYTES);
+  __shared__ int cnt_s[CELLS_PER_TILE], cs[CELLS_PER_TILE];
+  __shared__ uint16_t wpre[NW][CELLS_PER_TILE + 1];  // per warp: counts by new cell, then offsets
+  __shared__ int s_work[2];
+  __shared__ InstArgs sI;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  const int my_cell = tid / CPC, my_cp = tid % CPC;  // corners my_cp + r * CPC
+  pdl_trigger();
+  pdl_wait();
+  // items: first the CTA's own (blockIdx.x), then gridDim.x + the work counter
+  const int total = G.bin_items[G.ninst];
+  if (tid == 0) s_work[0] = blockIdx.x;
+  __syncthreads();
+  int loaded = -1;
+
+  for (int it = 0;; ++it) {
+    const int wi = s_work[it & 1];
+    if (wi >= total) break;
+    int wnext = 0;
+    if (tid == 0) wnext = (int)gridDim.x + atomicAdd(&G.work[W_G2P], 1);
+    const int ii = ONE ? 0 : find_inst(G.bin_items, G.ninst, wi);
+    if (!ONE && ii != loaded) {  // uniform
+      copy_inst(G.inst, ii, &sI);
+      loaded = ii;
+      __syncthreads();
+    }
+    const InstArgs &I = inst_ref<ONE>(G, sI);
+    const Geo &g = I.geo;
+    const int4 ar = I.s.active[ONE ? wi : wi - G.bin_items[ii]];
+    const int t = ar.x, s = ar.y, e = ar.z;
+    if (t >= I.ntiles) {  // the particles that left the mesh earlier: carried over unchanged
+      for (int q = s + tid; q < e; q += T) copy_particle<D>(I.A, I.B, I.perm_out[q], q);
+      if (tid == 0) s_work[(it + 1) & 1] = wnext;
+      __syncthreads();
+      continue;
+    }
+    const int step = I.s.ctr[C_STEP];
+    int tc[3];
+    tile_coords(g, t, tc);
+    // the node records of the tile's box (nodes beyond the mesh: zeros, never read)
+    for (int b = tid; b < BN * NREC; b += T) {
+      const int bn = b / NREC, r = b - bn * NREC;
+      const int bx = bn % (TX + 1), by = (bn / (TX + 1)) % (TY + 1), bz = D == 3 ? bn / ((TX + 1) * (TY + 1)) : 0;
+      const int I0 = tc[0] * TX + bx, I1 = tc[1] * TY + by, I2 = D == 3 ? tc[2] * TZ + bz : 0;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (I0 <= g.nc[0] && I1 <= g.nc[1] && (D == 2 || I2 <= g.nc[2]))
+        v = I.s.node[(int64_t)NREC * (I0 + I.ns0 * I1 + I.ns1 * I2) + r];
+      nodes_s[b] = v;
+    }
+#pragma unroll
+    for (int r = 0; r < CPT; ++r)
+#pragma unroll
+      for (int ch = 0; ch < NCH; ++ch) cellP[my_cell * NV + (my_cp + r * CPC) * NCH + ch] = 0.f;
+    __syncthreads();
+
+    for (int c0 = s; c0 < e; c0 += T) {
+      const int q = c0 + tid;
+      int lcn = CELLS_PER_TILE;  // new local cell of a particle that stays in the tile; none otherwise
+      float f[4 * NQ];           // its record for the next step's P2G
+#pragma unroll
+      for (int k = 0; k < 4 * NQ; ++k) f[k] = 0.f;
+      if (q < e) {
+        const int j = I.perm_out[q];
+        const uint32_t key = I.keys_out[q];
+        const bool has_coh = I.A.coh() != nullptr;
+        // the state (all but the offset) travels to this thread's shared
+        // column while the node gather runs
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+          cp_async4(&stg[(F::S_SIG + i) * T + tid], I.A.sig(i) + j);
+          cp_async4(&stg[(F::S_EPS + i) * T + tid], I.A.eps(i) + j);
+        }
+        cp_async4(&stg[F::S_JM1 * T + tid], I.A.jm1() + j);
+        cp_async4(&stg[F::S_EPSP * T + tid], I.A.epsp() + j);
+#pragma unroll
+        for (int k = 0; k < D; ++k) cp_async4(&stg[(F::S_VEL + k) * T + tid], I.A.vel(k) + j);
+        cp_async4(&stg[F::S_MASS * T + tid], I.A.mass() + j);
+        cp_async4(&stg[F::S_ID * T + tid], I.A.id() + j);
+        if (has_coh) cp_async4(&stg[F::S_COH * T + tid], I.A.coh() + j);
+        cp_async_commit();
+        int lc[3];
+        local_coords<D>(key, lc);
+        int cell[3] = {tc[0] * TX + lc[0], tc[1] * TY + lc[1], D == 3 ? tc[2] * TZ + lc[2] : 0};
+        float u[D], w0[D], w1[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) u[k] = I.A.off(k)[j];
+        corner_weights<D>(u, w0, w1);
+        float dv[D], vb[D], L[D][D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          dv[k] = vb[k] = 0.f;
+#pragma unroll
+          for (int l = 0; l < D; ++l) L[k][l] = 0.f;
+        }
+        const int b0 = lc[0] + (TX + 1) * (lc[1] + (TY + 1) * lc[2]);
+#pragma unroll
+        for (int a = 0; a < NC; ++a) {
+          float N, Gd[D];
+          corner_shape<D>(a, w0, w1, g.inv_h, N, Gd);
+          const int b = b0 + (a & 1) + (TX + 1) * ((a >> 1) & 1) + (D == 3 ? (TX + 1) * (TY + 1) * ((a >> 2) & 1) : 0);
+          float nv[D], na[D];
+          if (D == 3) {
+            const float4 r0 = nodes_s[2 * b], r1 = nodes_s[2 * b + 1];
+            nv[0] = r0.x;
+            nv[1] = r0.y;
+            nv[D - 1] = r0.z;
+            na[0] = r1.x;
+            na[1] = r1.y;
+            na[D - 1] = r1.z;
+          } else {
+            const float4 r0 = nodes_s[b];
+            nv[0] = r0.x;
+            nv[1] = r0.y;
+            na[0] = r0.z;
+            na[1] = r0.w;
+          }
+          if constexpr (D == 3) {
+            // paired FP32 FMAs: each lane is the same single-rounding FMA as
+            // the scalar form, two per instruction
+            const float2 NN = make_float2(N, N);
+            const float2 a01 = __ffma2_rn(NN, make_float2(na[0], na[1]), make_float2(dv[0], dv[1]));
+            const float2 v01 = __ffma2_rn(NN, make_float2(nv[0], nv[1]), make_float2(vb[0], vb[1]));
+            dv[0] = a01.x;
+            dv[1] = a01.y;
+            dv[2] = fmaf(N, na[2], dv[2]);
+            vb[0] = v01.x;
+            vb[1] = v01.y;
+            vb[2] = fmaf(N, nv[2], vb[2]);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+              const float2 l01 =
+                  __ffma2_rn(make_float2(nv[k], nv[k]), make_float2(Gd[0], Gd[1]), make_float2(L[k][0], L[k][1]));
+              L[k][0] = l01.x;
+              L[k][1] = l01.y;
+              L[k][2] = fmaf(nv[k], Gd[2], L[k][2]);
+            }
+          } else {
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+              dv[k] += N * na[k];
+              vb[k] += N * nv[k];
+#pragma unroll
+              for (int l = 0; l < D; ++l) L[k][l] += nv[k] * Gd[l];
+            }
+          }
+        }
+        float v0[D], sg[6], ep[6];
+        cp_async_wait_all();
+#pragma unroll
+        for (int k = 0; k < D; ++k) v0[k] = stg[(F::S_VEL + k) * T + tid];
+        const float mass = stg[F::S_MASS * T + tid];
+        const int32_t pid = __float_as_int(stg[F::S_ID * T + tid]);
+        const float coh = has_coh ? stg[F::S_COH * T + tid] : I.mat.c;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) sg[i] = ep[i] = 0.f;
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+          sg[i] = stg[(F::S_SIG + i) * T + tid];
+          ep[i] = stg[(F::S_EPS + i) * T + tid];
+        }
+        const float jm1 = stg[F::S_JM1 * T + tid];
+        float epsp = stg[F::S_EPSP * T + tid];
+
+        int status = 0;
+        // FLIP velocity, advection in cell units, relocation
+        bool dead = false;
+        float vk[D], un[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          vk[k] = v0[k] + g.dt * dv[k];
+          I.B.vel(k)[q] = vk[k];
+          if (!isfinite(vk[k])) status |= ST_NONFINITE;
+          un[k] = u[k] + g.dt * vb[k] * g.inv_h;
+          if (!isfinite(un[k])) {
+            status |= ST_NONFINITE;
+            dead = true;
+            un[k] = 0.f;
+          }
+          // one cell crossing is an exact subtraction (Sterbenz), so the
+          // offset stays in [-0.5, 0.5) and the cell is exact
+          if (un[k] >= 0.5f) {
+            un[k] -= 1.f;
+            cell[k] += 1;
+          } else if (un[k] < -0.5f) {
+            un[k] += 1.f;
+            cell[k] -= 1;
+          }
+          if (!(un[k] >= -0.5f && un[k] < 0.5f)) {  // more than one cell per step
+            const float sh = floorf(un[k] + 0.5f);
+            un[k] -= sh;
+            cell[k] += (int)sh;
+            if (un[k] >= 0.5f) {
+              un[k] -= 1.f;
+              cell[k] += 1;
+            } else if (un[k] < -0.5f) {
+              un[k] += 1.f;
+              cell[k] -= 1;
+            }
+          }
+          if (cell[k] < 0 || cell[k] >= g.nc[k]) dead = true;
+          I.B.off(k)[q] = un[k];
+        }
+        uint32_t nkey = g.dead_key;
+        int l2 = 0;
+        if (!dead) {
+          const int t2 = cell[0] / TX + g.nt[0] * (cell[1] / TY + g.nt[1] * (D == 3 ? cell[2] / TZ : 0));
+          l2 = cell[0] % TX + TX * (cell[1] % TY + TY * (D == 3 ? cell[2] % TZ : 0));
+          nkey = (uint32_t)t2 * CELLS_PER_TILE + (uint32_t)l2;
+        } else {
+          status |= ST_LEFT_MESH;
+        }
+        I.B.key()[q] = nkey;
+        I.B.mass()[q] = mass;
+        I.B.id()[q] = pid;
+        if (has_coh) I.B.coh()[q] = coh;
+        // tile movers for the next step's binning; one append per warp
+        const int tn = min((int)(nkey >> LOCAL_BITS), I.ntiles);
+        const bool mover = tn != t;
+        const unsigned am = __activemask();
+        const unsigned mv = __ballot_sync(am, mover);
+        if (mover) {
+          const int leader = __ffs(mv) - 1;
+          int base = 0;
+          if (lane == leader) base = atomicAdd(&I.s.ctr[C_MOVERS], __popc(mv));
+          base = __shfl_sync(mv, base, leader);
+          atomicAdd(&I.s.in_cnt[tn], 1);
+          atomicAdd(&I.s.out_cnt[t], 1);
+          I.s.movers[base + __popc(mv & lt_mask)] = (int32_t)q;
+        }
+        // strain increment de = sym(L) dt, strain, volume ratio, stress
+        float de[6] = {0, 0, 0, 0, 0, 0};
+        de[0] = L[0][0] * g.dt;
+        de[1] = L[1][1] * g.dt;
+        de[3] = 0.5f * (L[0][1] + L[1][0]) * g.dt;
+        if (D == 3) {
+          de[2] = L[D - 1][D - 1] * g.dt;
+          de[4] = 0.5f * (L[1][D - 1] + L[D - 1][1]) * g.dt;
+          de[5] = 0.5f * (L[0][D - 1] + L[D - 1][0]) * g.dt;
+        }
+#pragma unroll
+        for (int i = 0; i < NS; ++i) I.B.eps(i)[q] = ep[i] + de[i];
+        // V = V0 (1 + jm1):  (1 + jm1)(1 + tr) - 1 = jm1 + tr + jm1 tr
+        const float tr = de[0] + de[1] + de[2];
+        const float jn = jm1 + (tr + jm1 * tr);
+        I.B.jm1()[q] = jn;
+        // a trial in the apex band keeps its trial stress here and is queued
+        // for the FP64 return (apex_band_k, which also drops this tile's sums)
+        if (material_update_inline(I.mat, coh, sg, de, epsp)) I.s.bucket_sorted[atomicAdd(&I.s.ctr[C_APEX], 1)] = (int32_t)q;
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+          I.B.sig(i)[q] = sg[i];
+          if (!isfinite(sg[i])) status |= ST_NONFINITE;
+        }
+        I.B.epsp()[q] = epsp;
+        if (status) atomicOr(&I.s.ctr[C_STATUS], status);
+        if (!mover) {  // stays in the tile: its record for the next step's P2G
+          lcn = l2;
+          p2g_record<D, P2G_USL>(un, mass, vk, jn, sg, g.inv_rho, f);
+        }
+      }
+      // ---- the chunk's records sorted by new local cell (stable), then summed
+      for (int k = lane; k <= CELLS_PER_TILE; k += 32) wpre[warp][k] = 0;
+      __syncwarp();
+      const unsigned peers = __match_any_sync(0xffffffffu, lcn);
+      const int rank = __popc(peers & lt_mask);
+      if (rank == 0) wpre[warp][lcn] = (uint16_t)__popc(peers);
+      __syncthreads();  // every warp's counts are in; every thread has read its staged state
+      if (tid < CELLS_PER_TILE) {  // per cell: the warps' counts -> offsets within the cell
+        int run = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+          const int c = wpre[w][tid];
+          wpre[w][tid] = (uint16_t)run;
+          run += c;
+        }
+        cnt_s[tid] = run;
+      }
+      __syncthreads();
+      if (warp == 0) {  // cell starts: exclusive scan of the 64 counts
+        const int a = cnt_s[lane], b = cnt_s[lane + 32];
+        const int ia = warp_incl(a);
+        const int ta = __shfl_sync(0xffffffffu, ia, 31);
+        const int ib = warp_incl(b);
+        cs[lane] = ia - a;
+        cs[lane + 32] = ta + ib - b;
+      }
+      __syncthreads();
+      if (lcn < CELLS_PER_TILE) {
+        const int sl = rec_slot(cs[lcn] + wpre[warp][lcn] + rank);
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) rec[k * T + sl] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
+      }
+      __syncthreads();
+      {
+        float acc[CPT][NCH];
+#pragma unroll
+        for (int r = 0; r < CPT; ++r)
+#pragma unroll
+          for (int ch = 0; ch < NCH; ++ch) acc[r][ch] = cellP[my_cell * NV + (my_cp + r * CPC) * NCH + ch];
+        const int i0 = cs[my_cell];
+        accumulate_cell<D, P2G_USL>(rec, i0, i0 + cnt_s[my_cell], my_cp, g.inv_h, acc);
+#pragma unroll
+        for (int r = 0; r < CPT; ++r)
+#pragma unroll
+          for (int ch = 0; ch < NCH; ++ch) cellP[my_cell * NV + (my_cp + r * CPC) * NCH + ch] = acc[r][ch];
+      }
+      __syncthreads();  // the records are read; the next chunk stages over them
+    }
+    cells_to_slot<D, NCH>(cellP, I.s.slots1, t, T);
+    if (tid == 0) {
+      I.s.fepoch[t] = step + 1;
+      s_work[(it + 1) & 1] = wnext;
+    }
+    __syncthreads();
+  }
+}
+
 // FP64 apex-band returns of the particles G2P queued (rare: trials within
 // 1e-3 (|p| + c cot phi) of the apex, cohesive materials only).  G2P stored
 // their trial stress; this completes it in place and adds the plastic strain
@@ -887,24 +1446,47 @@ __global__ void __launch_bounds__(APEX_T) apex_band_k(const __grid_constant__ Gr
       }
       I.B.epsp()[q] = epsp;
       if (status) atomicOr(&I.s.ctr[C_STATUS], status);
+      // the fused USL G2P summed this particle's trial stress into its tile's
+      // sums for the next step: those sums are no longer valid
+      const uint32_t k2 = I.B.key()[q];
+      if (k2 < I.geo.dead_key) I.s.fepoch[k2 >> LOCAL_BITS] = -1;
     }
   }
 }
 
-template <int D, int MODE>
+template <int D, int MODE, bool RES = false>
 cudaError_t launch_p2g(const GroupArgs &G, int work_slot, cudaStream_t st) {
-  return G.ninst == 1
-             ? launch_dep(p2g_tile<D, MODE, true>, G.grid, p2g_threads<D>(), p2g_smem<D, MODE>(), st, G, work_slot)
-             : launch_dep(p2g_tile<D, MODE, false>, G.grid, p2g_threads<D>(), p2g_smem<D, MODE>(), st, G, work_slot);
+  return G.ninst == 1 ? launch_dep(p2g_tile<D, MODE, true, RES>, G.grid, p2g_threads<D>(), p2g_smem<D, MODE>(), st,
+                                   G, work_slot)
+                      : launch_dep(p2g_tile<D, MODE, false, RES>, G.grid, p2g_threads<D>(), p2g_smem<D, MODE>(), st,
+                                   G, work_slot);
 }
 
-template <int D, int MODE>
+template <int D, int MODE, bool RES = false>
 cudaError_t prepare_p2g() {
-  cudaError_t e = cudaFuncSetAttribute(p2g_tile<D, MODE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(p2g_tile<D, MODE, true, RES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)p2g_smem<D, MODE>());
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(p2g_tile<D, MODE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(p2g_tile<D, MODE, false, RES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)p2g_smem<D, MODE>());
+}
+
+template <int D>
+cudaError_t prepare_g2p_tile() {
+  cudaError_t e = cudaFuncSetAttribute(g2p_tile<D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)G2PF<D>::SMEM);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(g2p_tile<D, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G2PF<D>::SMEM);
+}
+
+// The fused USL G2P (and, for cohesive materials, the FP64 apex-band return).
+template <int D>
+cudaError_t launch_g2p_tile(const GroupArgs &G, cudaStream_t st) {
+  cudaError_t e = G.ninst == 1 ? launch_dep(g2p_tile<D, true>, G.grid, G2PF<D>::T, G2PF<D>::SMEM, st, G)
+                               : launch_dep(g2p_tile<D, false>, G.grid, G2PF<D>::T, G2PF<D>::SMEM, st, G);
+  if (e != cudaSuccess || !G.apex) return e;
+  return G.ninst == 1 ? launch_dep(apex_band_k<D, true>, G.grid / 8, APEX_T, 0, st, G)
+                      : launch_dep(apex_band_k<D, false>, G.grid / 8, APEX_T, 0, st, G);
 }
 
 template <int D, int NMODE>
@@ -928,12 +1510,12 @@ cudaError_t step_dim(int scheme, const GroupArgs &G, cudaEvent_t *ev, cudaStream
   cudaError_t e;
   // phase events 0 (start) and 1 (after binning) are recorded by the
   // caller; 2.. follow each kernel here
-  if (scheme == 1) {  // USL
-    if ((e = launch_p2g<D, P2G_USL>(G, W_P2G, st)) != cudaSuccess) return e;
+  if (scheme == 1) {  // USL: residual P2G, nodes, G2P fused with the next step's P2G
+    if ((e = launch_p2g<D, P2G_USL, true>(G, W_P2G, st)) != cudaSuccess) return e;
     if ((e = phase_mark(ev, 2, st)) != cudaSuccess) return e;
     if ((e = launch_node<D, NODE_USL>(G, W_NODE, st)) != cudaSuccess) return e;
     if ((e = phase_mark(ev, 3, st)) != cudaSuccess) return e;
-    if ((e = launch_g2p<D, G2P_USL>(G, st)) != cudaSuccess) return e;
+    if ((e = launch_g2p_tile<D>(G, st)) != cudaSuccess) return e;
     return phase_mark(ev, 4, st);
   }
   // USF
@@ -1071,13 +1653,15 @@ __global__ void mat_update_f32_k(MatConst<float> m, MatConst<double> md, int64_t
 cudaError_t f32_prepare(int dim) {
   cudaError_t e;
   if (dim == 3) {
-    if ((e = prepare_p2g<3, P2G_USL>()) != cudaSuccess) return e;
+    if ((e = prepare_p2g<3, P2G_USL, true>()) != cudaSuccess) return e;
     if ((e = prepare_p2g<3, P2G_MOM>()) != cudaSuccess) return e;
-    return prepare_p2g<3, P2G_FORCE>();
+    if ((e = prepare_p2g<3, P2G_FORCE>()) != cudaSuccess) return e;
+    return prepare_g2p_tile<3>();
   }
-  if ((e = prepare_p2g<2, P2G_USL>()) != cudaSuccess) return e;
+  if ((e = prepare_p2g<2, P2G_USL, true>()) != cudaSuccess) return e;
   if ((e = prepare_p2g<2, P2G_MOM>()) != cudaSuccess) return e;
-  return prepare_p2g<2, P2G_FORCE>();
+  if ((e = prepare_p2g<2, P2G_FORCE>()) != cudaSuccess) return e;
+  return prepare_g2p_tile<2>();
 }
 
 __global__ void gather_status_k(const InstArgs *tab, int ninst, int32_t *out) {

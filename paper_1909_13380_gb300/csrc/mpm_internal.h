@@ -113,6 +113,8 @@ enum {
   C_BIN_ITEMS = 9,  // active tiles + 1 if the dead range is non-empty
   C_DEAD_START = 10,
   C_APEX = 11,      // particles queued by G2P for the FP64 apex-band return (in StepBufs::bucket_sorted)
+  C_STEP = 12,      // step index, advanced by the tile scan (the epoch of the nodal partial sums)
+  C_RESID = 13,     // binning items that need the residual P2G this step (USL)
   C_NCTR = 16
 };
 
@@ -135,6 +137,15 @@ struct StepBufs {
   int32_t *ctr;            // C_NCTR counters
   float *slots1;           // ntiles * box * channels (P2G USL / MOM)
   float *slots2;           // ntiles * box * D        (P2G FORCE, USF)
+  // USL: slots1 of a tile holds the next step's P2G of the particles that
+  // stay in it, summed by the G2P that moved them (fepoch = the step those
+  // sums are for), or the P2G of all its particles; slots_a the P2G of the
+  // particles that arrived from other tiles (aepoch).  A tile's sums count
+  // in a step only while their epoch equals that step's index (C_STEP).
+  float *slots_a;          // ntiles * box * (1 + 2D)  (USL arrivals)
+  int32_t *fepoch;         // ntiles
+  int32_t *aepoch;         // ntiles
+  int32_t *resid;          // ntiles + 2: binning items (active tiles) whose P2G is not complete
   // dense node values, one 16-byte record per node in 2D (v'x v'y ax ay) and
   // two in 3D (v'x v'y v'z -, ax ay az -); v' is v in the USF velocity stage
   float4 *node;
@@ -167,6 +178,9 @@ struct InstArgs {
   uint32_t *keys_out;        // binning order keys (s.keys_sorted, or scratch)
   int32_t *perm_out;         // binning permutation (s.perm, or scratch)
   int ns0, ns1;              // node strides (nx+1), (nx+1)(ny+1)
+  // failure detection test hook of the look-back tile scan: the chunk whose
+  // flag is withheld (-1: none) and the polls a wait makes before it gives up
+  int lb_withhold, lb_spin;
 };
 
 // Copy the table entry of instance ii into the block's shared copy (every
@@ -181,6 +195,11 @@ __device__ __forceinline__ void copy_inst(const InstArgs *tab, int ii, InstArgs 
   for (int i = threadIdx.x; i < (int)(sizeof(InstArgs) / 8); i += blockDim.x) d[i] = __ldg(src + i);
 }
 
+// Polls a wait of the look-back tile scan makes before it gives up (and sets
+// ST_TIMEOUT); every wait is on a block that is already running, so it ends
+// long before this.
+constexpr int LB_SPIN_LIMIT = 1 << 20;
+
 // Largest tile count (plus the dead range) scanned by one CTA per instance
 // (1024 threads, at most MPM_SCAN1_K tiles each); larger instances take the
 // look-back scan over many CTAs.
@@ -192,7 +211,8 @@ constexpr int SCAN1_MAX = 1024 * MPM_SCAN1_K;
 // Per-group launch description.  The prefix arrays map a block (or a work
 // item) to its instance: entry i is the first block (item) of instance i and
 // entry ninst the total.
-enum { W_BIN = 0, W_P2G = 1, W_NODE = 2, W_P2G2 = 3, W_NODE2 = 4, W_SCAN_DONE = 5, W_SCAN_TICKET = 6, W_COUNT = 8 };
+enum { W_BIN = 0, W_P2G = 1, W_NODE = 2, W_P2G2 = 3, W_NODE2 = 4, W_SCAN_DONE = 5, W_SCAN_TICKET = 6, W_G2P = 7,
+       W_COUNT = 8 };
 struct GroupArgs {
   const InstArgs *inst;     // device table
   int ninst;
@@ -201,6 +221,7 @@ struct GroupArgs {
   const int32_t *mblk;      // blocks of the mover bucketing (host-computed)
   int32_t *bin_items;       // device-computed prefix of binning tiles
   int32_t *act_items;       // device-computed prefix of active tiles
+  int32_t *res_items;       // device-computed prefix of residual P2G items (USL)
   int32_t *work;            // W_COUNT dynamic work counters
   int nblk_p, nblk_s, nblk_m;
   int scan_one;             // every instance has at most SCAN1_MAX tiles: one-CTA scans

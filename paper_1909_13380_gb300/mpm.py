@@ -108,6 +108,7 @@ def load():
             "mpm_batch_step_kernels": [vp, i32p],
             "mpm_batch_destroy": [vp],
             "mpm_step_kernels": [vp, i32p],
+            "mpm_set_scan_fault": [vp, C.c_int32, C.c_int32],
             "mpm_material_update": [C.POINTER(mpm_material), C.c_int32, C.c_int64, dp, dp, dp, dp, dp, vp],
             "mpm_set_phase_timing": [vp, C.c_int32],
             "mpm_phase_times": [vp, C.POINTER(C.c_float), i32p],
@@ -331,6 +332,10 @@ def mpm_batch_step_kernels(b) -> int:
     k = C.c_int32()
     _check(None, load().mpm_batch_step_kernels(b, C.byref(k)), "mpm_batch_step_kernels")
     return k.value
+
+
+def mpm_set_scan_fault(h, withhold_chunk: int, spin_limit: int = 1 << 20):
+    _check(h, load().mpm_set_scan_fault(h, int(withhold_chunk), int(spin_limit)), "mpm_set_scan_fault")
 
 
 def mpm_step_kernels(h) -> int:
