@@ -158,6 +158,32 @@ __device__ __forceinline__ void bc_full(int faces, const int *bc, const T *mu, T
 }
 
 // ---------------------------------------------------------------------------
+// Explicitly rounded operations for the material update.  Whether the
+// compiler contracts a product and a sum into one FMA depends on the code
+// around them, so the same source, inlined into two kernels (a mesh stepped
+// alone, and in a batch), could round differently.  Written with explicit
+// round-to-nearest operations -- never contracted or reassociated -- the
+// material update rounds the same way in every kernel.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float xm(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double xm(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float xa(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double xa(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float xs(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double xs(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float xf(float a, float b, float c) { return __fmaf_rn(a, b, c); }  // a b + c
+__device__ __forceinline__ double xf(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float xd(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ double xd(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ float xsqrt(float a) { return __fsqrt_rn(a); }
+__device__ __forceinline__ double xsqrt(double a) { return __dsqrt_rn(a); }
+// a b + c d + e f, and the dot product of two 3-vectors
+template <typename T>
+__device__ __forceinline__ T xdot3(T a, T b, T c, T d, T e, T f) {
+  return xf(e, f, xf(c, d, xm(a, b)));
+}
+
+// ---------------------------------------------------------------------------
 // Symmetric 3x3 eigen-decomposition by cyclic Jacobi rotations (Golub & Van
 // Loan, symmetric Schur decomposition).  A is overwritten (diagonal ->
 // eigenvalues), Q accumulates the eigenvectors as columns.
@@ -167,22 +193,22 @@ __device__ __forceinline__ void jacobi_rot(T A[3][3], T Q[3][3]) {
   constexpr int o = 3 - p - q;
   const T apq = A[p][q];
   if (apq == T(0)) return;
-  const T theta = (A[q][q] - A[p][p]) / (T(2) * apq);
-  const T t = (theta >= T(0) ? T(1) : T(-1)) / (fabs(theta) + sqrt(theta * theta + T(1)));
+  const T theta = xd(xs(A[q][q], A[p][p]), xm(T(2), apq));
+  const T t = xd(theta >= T(0) ? T(1) : T(-1), xa(fabs(theta), xsqrt(xf(theta, theta, T(1)))));
   // any c, s with c^2 + s^2 = 1 keep Q orthogonal; rsqrt is exact enough here
-  const T c = sizeof(T) == 4 ? (T)rsqrtf((float)(t * t + T(1))) : T(1) / sqrt(t * t + T(1));
-  const T s = t * c;
+  const T c = sizeof(T) == 4 ? (T)rsqrtf((float)xf(t, t, T(1))) : xd(T(1), xsqrt(xf(t, t, T(1))));
+  const T s = xm(t, c);
   const T aop = A[o][p], aoq = A[o][q];
-  A[p][p] -= t * apq;
-  A[q][q] += t * apq;
+  A[p][p] = xs(A[p][p], xm(t, apq));
+  A[q][q] = xa(A[q][q], xm(t, apq));
   A[p][q] = A[q][p] = T(0);
-  A[o][p] = A[p][o] = c * aop - s * aoq;
-  A[o][q] = A[q][o] = s * aop + c * aoq;
+  A[o][p] = A[p][o] = xs(xm(c, aop), xm(s, aoq));
+  A[o][q] = A[q][o] = xa(xm(s, aop), xm(c, aoq));
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
     const T vp = Q[r][p], vq = Q[r][q];
-    Q[r][p] = c * vp - s * vq;
-    Q[r][q] = s * vp + c * vq;
+    Q[r][p] = xs(xm(c, vp), xm(s, vq));
+    Q[r][q] = xa(xm(s, vp), xm(c, vq));
   }
 }
 
@@ -198,9 +224,9 @@ __device__ __forceinline__ void eig_sym3(const T s[6], T lam[3], T Q[3][3]) {
   // that crosses the bound leaves far less in practice
   const T tol = sizeof(T) == 4 ? T(1e-12) : T(1e-32);
   for (int sweep = 0; sweep < (sizeof(T) == 4 ? 6 : 20); ++sweep) {
-    const T off = A[0][1] * A[0][1] + A[0][2] * A[0][2] + A[1][2] * A[1][2];
-    const T dia = A[0][0] * A[0][0] + A[1][1] * A[1][1] + A[2][2] * A[2][2];
-    if (off <= tol * dia || off == T(0)) break;
+    const T off = xdot3(A[0][1], A[0][1], A[0][2], A[0][2], A[1][2], A[1][2]);
+    const T dia = xdot3(A[0][0], A[0][0], A[1][1], A[1][1], A[2][2], A[2][2]);
+    if (off <= xm(tol, dia) || off == T(0)) break;
     jacobi_rot<T, 0, 1>(A, Q);
     jacobi_rot<T, 0, 2>(A, Q);
     jacobi_rot<T, 1, 2>(A, Q);
@@ -208,6 +234,15 @@ __device__ __forceinline__ void eig_sym3(const T s[6], T lam[3], T Q[3][3]) {
   lam[0] = A[0][0];
   lam[1] = A[1][1];
   lam[2] = A[2][2];
+}
+
+// Mean stress p, deviator diagonal d, and J2 of a Voigt stress.
+__device__ __forceinline__ void mean_dev_j2(const float s[6], float &p, float d[3], float &j2) {
+  p = xm(xa(xa(s[0], s[1]), s[2]), 1.f / 3.f);
+  d[0] = xs(s[0], p);
+  d[1] = xs(s[1], p);
+  d[2] = xs(s[2], p);
+  j2 = xf(s[5], s[5], xf(s[4], s[4], xf(s[3], s[3], xm(0.5f, xdot3(d[0], d[0], d[1], d[1], d[2], d[2])))));
 }
 
 // Symmetric 3x3 eigen-decomposition in closed form with deflation (FP32).
@@ -222,9 +257,8 @@ __device__ __forceinline__ void eig_sym3(const T s[6], T lam[3], T Q[3][3]) {
 // rotation (stable tangent formula), which keeps a near-double pair accurate.
 // Eigenvalues come back as p + r mu, eigenvectors as the columns of Q.
 __device__ __forceinline__ void eig_sym3_closed(const float s[6], float lam[3], float Q[3][3]) {
-  const float p = (s[0] + s[1] + s[2]) * (1.f / 3.f);
-  const float d0 = s[0] - p, d1 = s[1] - p, d2 = s[2] - p;
-  const float j2 = 0.5f * (d0 * d0 + d1 * d1 + d2 * d2) + s[3] * s[3] + s[4] * s[4] + s[5] * s[5];
+  float p, dv[3], j2;
+  mean_dev_j2(s, p, dv, j2);
   if (!(j2 > 1e-30f)) {  // isotropic (or a deviator below any stress of interest)
     lam[0] = s[0];
     lam[1] = s[1];
@@ -235,34 +269,38 @@ __device__ __forceinline__ void eig_sym3_closed(const float s[6], float lam[3], 
       for (int c = 0; c < 3; ++c) Q[r][c] = (r == c) ? 1.f : 0.f;
     return;
   }
-  const float r = sqrtf(j2 * (1.f / 3.f));
-  const float ir = 1.f / r;
-  const float A[3][3] = {{d0 * ir, s[3] * ir, s[5] * ir}, {s[3] * ir, d1 * ir, s[4] * ir}, {s[5] * ir, s[4] * ir, d2 * ir}};
-  const float det = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[1][2]) - A[0][1] * (A[0][1] * A[2][2] - A[1][2] * A[0][2]) +
-                    A[0][2] * (A[0][1] * A[1][2] - A[1][1] * A[0][2]);
-  const float c3 = fminf(1.f, fmaxf(-1.f, 0.5f * det));
-  const float th = acosf(c3) * (1.f / 3.f);
+  const float r = xsqrt(xm(j2, 1.f / 3.f));
+  const float ir = xd(1.f, r);
+  const float A[3][3] = {{xm(dv[0], ir), xm(s[3], ir), xm(s[5], ir)},
+                         {xm(s[3], ir), xm(dv[1], ir), xm(s[4], ir)},
+                         {xm(s[5], ir), xm(s[4], ir), xm(dv[2], ir)}};
+  const float m0 = xs(xm(A[1][1], A[2][2]), xm(A[1][2], A[1][2]));
+  const float m1 = xs(xm(A[0][1], A[2][2]), xm(A[1][2], A[0][2]));
+  const float m2 = xs(xm(A[0][1], A[1][2]), xm(A[1][1], A[0][2]));
+  const float det = xa(xs(xm(A[0][0], m0), xm(A[0][1], m1)), xm(A[0][2], m2));
+  const float c3 = fminf(1.f, fmaxf(-1.f, xm(0.5f, det)));
+  const float th = xm(acosf(c3), 1.f / 3.f);
   float sn, cs;
   sincosf(th, &sn, &cs);
   const float sq3 = 1.7320508f;
-  const float mu1 = 2.f * cs, mu3 = -cs - sq3 * sn, mu2 = -cs + sq3 * sn;
-  const float mud0 = (mu1 - mu2 >= mu2 - mu3) ? mu1 : mu3;
+  const float mu1 = xm(2.f, cs), mu3 = xs(-cs, xm(sq3, sn)), mu2 = xa(-cs, xm(sq3, sn));
+  const float mud0 = (xs(mu1, mu2) >= xs(mu2, mu3)) ? mu1 : mu3;
   // eigenvector of the distinct value: largest cross product of two rows
   float R[3][3];
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
-    for (int j = 0; j < 3; ++j) R[i][j] = A[i][j] - (i == j ? mud0 : 0.f);
+    for (int j = 0; j < 3; ++j) R[i][j] = i == j ? xs(A[i][j], mud0) : A[i][j];
   float n[3], best = -1.f;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     const int a = k == 2 ? 1 : 0, b = k == 0 ? 1 : 2;  // row pairs (0,1) (0,2) (1,2)
-    const float cx = R[a][1] * R[b][2] - R[a][2] * R[b][1];
-    const float cy = R[a][2] * R[b][0] - R[a][0] * R[b][2];
-    const float cz = R[a][0] * R[b][1] - R[a][1] * R[b][0];
-    const float m2 = cx * cx + cy * cy + cz * cz;
-    if (m2 > best) {
-      best = m2;
+    const float cx = xs(xm(R[a][1], R[b][2]), xm(R[a][2], R[b][1]));
+    const float cy = xs(xm(R[a][2], R[b][0]), xm(R[a][0], R[b][2]));
+    const float cz = xs(xm(R[a][0], R[b][1]), xm(R[a][1], R[b][0]));
+    const float m2c = xdot3(cx, cx, cy, cy, cz, cz);
+    if (m2c > best) {
+      best = m2c;
       n[0] = cx;
       n[1] = cy;
       n[2] = cz;
@@ -273,48 +311,49 @@ __device__ __forceinline__ void eig_sym3_closed(const float s[6], float lam[3], 
     return;
   }
   const float inr = rsqrtf(best);
-  n[0] *= inr;
-  n[1] *= inr;
-  n[2] *= inr;
+  n[0] = xm(n[0], inr);
+  n[1] = xm(n[1], inr);
+  n[2] = xm(n[2], inr);
   // orthonormal basis e1, e2 of the plane orthogonal to n
   float e1[3];
   if (fabsf(n[0]) >= fabsf(n[1])) {
-    const float k = rsqrtf(n[0] * n[0] + n[2] * n[2]);
-    e1[0] = -n[2] * k;
+    const float k = rsqrtf(xf(n[2], n[2], xm(n[0], n[0])));
+    e1[0] = xm(-n[2], k);
     e1[1] = 0.f;
-    e1[2] = n[0] * k;
+    e1[2] = xm(n[0], k);
   } else {
-    const float k = rsqrtf(n[1] * n[1] + n[2] * n[2]);
+    const float k = rsqrtf(xf(n[2], n[2], xm(n[1], n[1])));
     e1[0] = 0.f;
-    e1[1] = n[2] * k;
-    e1[2] = -n[1] * k;
+    e1[1] = xm(n[2], k);
+    e1[2] = xm(-n[1], k);
   }
-  const float e2[3] = {n[1] * e1[2] - n[2] * e1[1], n[2] * e1[0] - n[0] * e1[2], n[0] * e1[1] - n[1] * e1[0]};
+  const float e2[3] = {xs(xm(n[1], e1[2]), xm(n[2], e1[1])), xs(xm(n[2], e1[0]), xm(n[0], e1[2])),
+                       xs(xm(n[0], e1[1]), xm(n[1], e1[0]))};
   float An[3], A1[3], A2[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    An[i] = A[i][0] * n[0] + A[i][1] * n[1] + A[i][2] * n[2];
-    A1[i] = A[i][0] * e1[0] + A[i][1] * e1[1] + A[i][2] * e1[2];
-    A2[i] = A[i][0] * e2[0] + A[i][1] * e2[1] + A[i][2] * e2[2];
+    An[i] = xdot3(A[i][0], n[0], A[i][1], n[1], A[i][2], n[2]);
+    A1[i] = xdot3(A[i][0], e1[0], A[i][1], e1[1], A[i][2], e1[2]);
+    A2[i] = xdot3(A[i][0], e2[0], A[i][1], e2[1], A[i][2], e2[2]);
   }
-  const float mud = n[0] * An[0] + n[1] * An[1] + n[2] * An[2];  // Rayleigh quotient
-  const float b11 = e1[0] * A1[0] + e1[1] * A1[1] + e1[2] * A1[2];
-  const float b22 = e2[0] * A2[0] + e2[1] * A2[1] + e2[2] * A2[2];
-  const float b12 = e1[0] * A2[0] + e1[1] * A2[1] + e1[2] * A2[2];
+  const float mud = xdot3(n[0], An[0], n[1], An[1], n[2], An[2]);  // Rayleigh quotient
+  const float b11 = xdot3(e1[0], A1[0], e1[1], A1[1], e1[2], A1[2]);
+  const float b22 = xdot3(e2[0], A2[0], e2[1], A2[1], e2[2], A2[2]);
+  const float b12 = xdot3(e1[0], A2[0], e1[1], A2[1], e1[2], A2[2]);
   float t = 0.f;
   if (b12 != 0.f) {
-    const float tj = (b22 - b11) / (2.f * b12);
-    t = (tj >= 0.f ? 1.f : -1.f) / (fabsf(tj) + sqrtf(tj * tj + 1.f));
+    const float tj = xd(xs(b22, b11), xm(2.f, b12));
+    t = xd(tj >= 0.f ? 1.f : -1.f, xa(fabsf(tj), xsqrt(xf(tj, tj, 1.f))));
   }
-  const float c = rsqrtf(t * t + 1.f), sr = t * c;
-  lam[0] = p + r * mud;
-  lam[1] = p + r * (b11 - t * b12);
-  lam[2] = p + r * (b22 + t * b12);
+  const float c = rsqrtf(xf(t, t, 1.f)), sr = xm(t, c);
+  lam[0] = xf(r, mud, p);
+  lam[1] = xf(r, xs(b11, xm(t, b12)), p);
+  lam[2] = xf(r, xf(t, b12, b22), p);
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     Q[i][0] = n[i];
-    Q[i][1] = c * e1[i] - sr * e2[i];
-    Q[i][2] = sr * e1[i] + c * e2[i];
+    Q[i][1] = xs(xm(c, e1[i]), xm(sr, e2[i]));
+    Q[i][2] = xa(xm(sr, e1[i]), xm(c, e2[i]));
   }
 }
 
@@ -340,6 +379,13 @@ __device__ __forceinline__ void sort3_desc(T lam[3], T Q[3][3]) {
   sw(0, 1);
 }
 
+// The Mohr-Coulomb function of a pair of principal stresses a >= b:
+// (a - b) + (a + b) sin(phi) - 2 c cos(phi).
+template <typename T>
+__device__ __forceinline__ T mc_f(const MatConst<T> &m, T c, T a, T b) {
+  return xs(xf(xa(a, b), m.sphi, xs(a, b)), xm(xm(T(2), c), m.cphi));
+}
+
 // Mohr-Coulomb return in principal stresses (tension positive, perfect
 // plasticity): yield f = (s1 - s3) + (s1 + s3) sin(phi) - 2 c cos(phi);
 // plastic potential of the same form with psi.  Order of de Souza Neto et
@@ -352,7 +398,7 @@ __device__ __forceinline__ void sort3_desc(T lam[3], T Q[3][3]) {
 template <typename T>
 __device__ __forceinline__ int mc_principal(const MatConst<T> &m, T c, const T s[3], T r[3],
                                             T &depsp) {
-  const T f13 = (s[0] - s[2]) + (s[0] + s[2]) * m.sphi - T(2) * c * m.cphi;
+  const T f13 = mc_f(m, c, s[0], s[2]);
   if (!(f13 > T(0))) {
     r[0] = s[0];
     r[1] = s[1];
@@ -360,51 +406,52 @@ __device__ __forceinline__ int mc_principal(const MatConst<T> &m, T c, const T s
     depsp = T(0);
     return 0;
   }
-  const T G2 = T(2) * m.G;
-  const T l2 = T(2) * m.lam * m.spsi;
-  const T up = G2 * (T(1) + m.spsi), dn = G2 * (T(1) - m.spsi);
+  const T G2 = xm(T(2), m.G);
+  const T l2 = xm(xm(T(2), m.lam), m.spsi);
+  const T up = xm(G2, xa(T(1), m.spsi)), dn = xm(G2, xs(T(1), m.spsi));
   // D N for the planes 1-3 (a), 2-3 (b), 1-2 (c)
-  const T DNa[3] = {l2 + up, l2, l2 - dn};
-  const T DNb[3] = {l2, l2 + up, l2 - dn};
-  const T DNc[3] = {l2 + up, l2 - dn, l2};
-  const T a = T(4) * m.G * (T(1) + m.sphi * m.spsi) + T(4) * m.lam * m.sphi * m.spsi;
+  const T DNa[3] = {xa(l2, up), l2, xs(l2, dn)};
+  const T DNb[3] = {l2, xa(l2, up), xs(l2, dn)};
+  const T DNc[3] = {xa(l2, up), xs(l2, dn), l2};
+  const T ll = xm(xm(xm(T(4), m.lam), m.sphi), m.spsi);
+  const T a = xf(xm(T(4), m.G), xf(m.sphi, m.spsi, T(1)), ll);
   int branch = 1;
-  const T g = f13 / a;
+  const T g = xd(f13, a);
 #pragma unroll
-  for (int i = 0; i < 3; ++i) r[i] = s[i] - g * DNa[i];
+  for (int i = 0; i < 3; ++i) r[i] = xs(s[i], xm(g, DNa[i]));
   if (!(r[0] >= r[1] && r[1] >= r[2])) {
-    const T crit = (T(1) - m.spsi) * (s[0] - s[1]) - (T(1) + m.spsi) * (s[1] - s[2]);
+    const T crit = xs(xm(xs(T(1), m.spsi), xs(s[0], s[1])), xm(xa(T(1), m.spsi), xs(s[1], s[2])));
     if (crit <= T(0)) {
-      const T fb = (s[1] - s[2]) + (s[1] + s[2]) * m.sphi - T(2) * c * m.cphi;
-      const T b = T(4) * m.lam * m.sphi * m.spsi + G2 * (T(1) - m.sphi) * (T(1) - m.spsi);
-      const T det = a * a - b * b;
-      const T ga = (a * f13 - b * fb) / det, gb = (a * fb - b * f13) / det;
+      const T fb = mc_f(m, c, s[1], s[2]);
+      const T b = xf(xm(G2, xs(T(1), m.sphi)), xs(T(1), m.spsi), ll);
+      const T det = xs(xm(a, a), xm(b, b));
+      const T ga = xd(xs(xm(a, f13), xm(b, fb)), det), gb = xd(xs(xm(a, fb), xm(b, f13)), det);
 #pragma unroll
-      for (int i = 0; i < 3; ++i) r[i] = s[i] - ga * DNa[i] - gb * DNb[i];
+      for (int i = 0; i < 3; ++i) r[i] = xs(xs(s[i], xm(ga, DNa[i])), xm(gb, DNb[i]));
       branch = 2;
     } else {
-      const T fc = (s[0] - s[1]) + (s[0] + s[1]) * m.sphi - T(2) * c * m.cphi;
-      const T b = T(4) * m.lam * m.sphi * m.spsi + G2 * (T(1) + m.sphi) * (T(1) + m.spsi);
-      const T det = a * a - b * b;
-      const T ga = (a * f13 - b * fc) / det, gc = (a * fc - b * f13) / det;
+      const T fc = mc_f(m, c, s[0], s[1]);
+      const T b = xf(xm(G2, xa(T(1), m.sphi)), xa(T(1), m.spsi), ll);
+      const T det = xs(xm(a, a), xm(b, b));
+      const T ga = xd(xs(xm(a, f13), xm(b, fc)), det), gc = xd(xs(xm(a, fc), xm(b, f13)), det);
 #pragma unroll
-      for (int i = 0; i < 3; ++i) r[i] = s[i] - ga * DNa[i] - gc * DNc[i];
+      for (int i = 0; i < 3; ++i) r[i] = xs(xs(s[i], xm(ga, DNa[i])), xm(gc, DNc[i]));
       branch = 3;
     }
     if (m.sphi > T(0) && !(r[0] >= r[2])) {
       branch = 4;
-      const T pa = c * m.cphi / m.sphi;
+      const T pa = xd(xm(c, m.cphi), m.sphi);
       r[0] = r[1] = r[2] = pa;
     }
   }
   T sq = T(0);
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    const T d0 = s[i] - r[i], d1 = s[(i + 1) % 3] - r[(i + 1) % 3], d2 = s[(i + 2) % 3] - r[(i + 2) % 3];
-    const T e = (d0 - m.nu * (d1 + d2)) / m.E;
-    sq += e * e;
+    const T d0 = xs(s[i], r[i]), d1 = xs(s[(i + 1) % 3], r[(i + 1) % 3]), d2 = xs(s[(i + 2) % 3], r[(i + 2) % 3]);
+    const T e = xd(xs(d0, xm(m.nu, xa(d1, d2))), m.E);
+    sq = xf(e, e, sq);
   }
-  depsp = sqrt(T(2) / T(3) * sq);
+  depsp = xsqrt(xm(T(2) / T(3), sq));
   return branch;
 }
 
@@ -416,18 +463,19 @@ __device__ __forceinline__ int mc_principal(const MatConst<T> &m, T c, const T s
 // is not clearly elastic goes through the full return (accurate eigenpairs,
 // then the yield check), so the result is the same as without the filter.
 __device__ __forceinline__ bool clearly_elastic(const MatConst<float> &m, float c, const float s[6]) {
-  const float p = (s[0] + s[1] + s[2]) * (1.f / 3.f);
-  const float d0 = s[0] - p, d1 = s[1] - p, d2 = s[2] - p;
-  const float j2 = 0.5f * (d0 * d0 + d1 * d1 + d2 * d2) + s[3] * s[3] + s[4] * s[4] + s[5] * s[5];
-  const float j3 = d0 * (d1 * d2 - s[4] * s[4]) - s[3] * (s[3] * d2 - s[4] * s[5]) + s[5] * (s[3] * s[4] - d1 * s[5]);
-  const float r = sqrtf(j2 * (1.f / 3.f));
-  float c3 = r > 0.f ? j3 / (2.f * r * r * r) : 0.f;
+  float p, d[3], j2;
+  mean_dev_j2(s, p, d, j2);
+  const float j3 = xa(xs(xm(d[0], xs(xm(d[1], d[2]), xm(s[4], s[4]))), xm(s[3], xs(xm(s[3], d[2]), xm(s[4], s[5])))),
+                      xm(s[5], xs(xm(s[3], s[4]), xm(d[1], s[5]))));
+  const float r = xsqrt(xm(j2, 1.f / 3.f));
+  float c3 = r > 0.f ? xd(j3, xm(xm(xm(2.f, r), r), r)) : 0.f;
   c3 = fminf(1.f, fmaxf(-1.f, c3));
-  const float th = acosf(c3) * (1.f / 3.f);
-  const float s1 = p + 2.f * r * cosf(th);
-  const float s3 = p + 2.f * r * cosf(th + 2.0943951f);
-  const float f = (s1 - s3) + (s1 + s3) * m.sphi - 2.f * c * m.cphi;
-  const float margin = 4e-3f * (r + fabsf(p)) + 1e-3f * c;
+  const float th = xm(acosf(c3), 1.f / 3.f);
+  const float r2 = xm(2.f, r);
+  const float s1 = xf(r2, cosf(th), p);
+  const float s3 = xf(r2, cosf(xa(th, 2.0943951f)), p);
+  const float f = mc_f(m, c, s1, s3);
+  const float margin = xf(1e-3f, c, xm(4e-3f, xa(r, fabsf(p))));
   return f < -margin;
 }
 
@@ -439,12 +487,12 @@ __device__ __forceinline__ bool clearly_elastic(const MatConst<float> &m, float 
 // whose bound stays below zero by more than the FP32 rounding of p and J2 is
 // inside the surface whatever its Lode angle.
 __device__ __forceinline__ bool bounded_elastic(const MatConst<float> &m, float c, const float s[6]) {
-  const float p = (s[0] + s[1] + s[2]) * (1.f / 3.f);
-  const float d0 = s[0] - p, d1 = s[1] - p, d2 = s[2] - p;
-  const float j2 = 0.5f * (d0 * d0 + d1 * d1 + d2 * d2) + s[3] * s[3] + s[4] * s[4] + s[5] * s[5];
-  const float r = sqrtf(j2 * (1.f / 3.f));
-  const float fmax = 2.f * r * sqrtf(3.f + m.sphi * m.sphi) + 2.f * p * m.sphi - 2.f * c * m.cphi;
-  return fmax < -1e-4f * (r + fabsf(p) + c);
+  float p, d[3], j2;
+  mean_dev_j2(s, p, d, j2);
+  const float r = xsqrt(xm(j2, 1.f / 3.f));
+  const float fmax = xs(xf(xm(2.f, r), xsqrt(xf(m.sphi, m.sphi, 3.f)), xm(xm(2.f, p), m.sphi)),
+                        xm(xm(2.f, c), m.cphi));
+  return fmax < xm(-1e-4f, xa(xa(r, fabsf(p)), c));
 }
 
 // Trial stress -> returned stress (Voigt 6) for Mohr-Coulomb in precision T.
@@ -470,12 +518,12 @@ __device__ __forceinline__ int mc_return(const MatConst<T> &m, T c, const T st[6
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       const T n0 = Q[0][i], n1 = Q[1][i], n2 = Q[2][i];
-      out[0] += r[i] * n0 * n0;
-      out[1] += r[i] * n1 * n1;
-      out[2] += r[i] * n2 * n2;
-      out[3] += r[i] * n0 * n1;
-      out[4] += r[i] * n1 * n2;
-      out[5] += r[i] * n0 * n2;
+      out[0] = xf(xm(r[i], n0), n0, out[0]);
+      out[1] = xf(xm(r[i], n1), n1, out[1]);
+      out[2] = xf(xm(r[i], n2), n2, out[2]);
+      out[3] = xf(xm(r[i], n0), n1, out[3]);
+      out[4] = xf(xm(r[i], n1), n2, out[4]);
+      out[5] = xf(xm(r[i], n0), n2, out[5]);
     }
   }
   return br;
@@ -484,12 +532,12 @@ __device__ __forceinline__ int mc_return(const MatConst<T> &m, T c, const T st[6
 // Elastic trial sigma + D : de (isotropic, tensor shear strain).
 template <typename T>
 __device__ __forceinline__ void elastic_trial(const MatConst<T> &m, const T sig[6], const T de[6], T st[6]) {
-  const T tr = de[0] + de[1] + de[2];
-  const T lt = m.lam * tr, G2 = T(2) * m.G;
+  const T tr = xa(xa(de[0], de[1]), de[2]);
+  const T lt = xm(m.lam, tr), G2 = xm(T(2), m.G);
 #pragma unroll
-  for (int i = 0; i < 3; ++i) st[i] = sig[i] + lt + G2 * de[i];
+  for (int i = 0; i < 3; ++i) st[i] = xf(G2, de[i], xa(sig[i], lt));
 #pragma unroll
-  for (int i = 3; i < 6; ++i) st[i] = sig[i] + G2 * de[i];
+  for (int i = 3; i < 6; ++i) st[i] = xf(G2, de[i], sig[i]);
 }
 
 // Distance of the trial stress from the apex c cot(phi) within which the
@@ -499,12 +547,13 @@ __device__ __forceinline__ void elastic_trial(const MatConst<T> &m, const T sig[
 // apex is the zero stress and FP32 loses nothing near it.
 __device__ __forceinline__ bool near_apex(const float st[6], const MatConst<float> &m, float c) {
   if (!(m.sphi > 0.f) || c == 0.f) return false;  // c = 0: |sigma|^2 >= 3 p^2, the band is empty
-  const float pa = c * m.cphi / m.sphi;
-  const float p = (st[0] + st[1] + st[2]) * (1.f / 3.f);
-  const float d0 = st[0] - pa, d1 = st[1] - pa, d2 = st[2] - pa;
-  const float dist2 = d0 * d0 + d1 * d1 + d2 * d2 + 2.f * (st[3] * st[3] + st[4] * st[4] + st[5] * st[5]);
-  const float band = 1e-3f * (fabsf(p) + pa);
-  return dist2 < band * band;
+  const float pa = xd(xm(c, m.cphi), m.sphi);
+  const float p = xm(xa(xa(st[0], st[1]), st[2]), 1.f / 3.f);
+  const float d0 = xs(st[0], pa), d1 = xs(st[1], pa), d2 = xs(st[2], pa);
+  const float sh = xdot3(st[3], st[3], st[4], st[4], st[5], st[5]);
+  const float dist2 = xf(2.f, sh, xdot3(d0, d0, d1, d1, d2, d2));
+  const float band = xm(1e-3f, xa(fabsf(p), pa));
+  return dist2 < xm(band, band);
 }
 
 // The FP64 return near the apex, kept out of line: it is rare, and inlining

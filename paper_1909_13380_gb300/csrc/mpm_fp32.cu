@@ -225,15 +225,14 @@ __device__ __forceinline__ void p2g_record(const float *u, float mm, const float
   }
 }
 
-// Accumulate the channels of the thread's corners (my_cp + r * CPC) over the
-// records i0..i1-1 of one cell, in order (plain sequential FP32 sums).
+// Add record i to the channels of the thread's corners (my_cp + r * CPC).
 template <int D, int MODE>
-__device__ __forceinline__ void accumulate_cell(const float4 *rec, int i0, int i1, int my_cp, float inv_h,
-                                                float acc[P2GRec<D, MODE>::CPT][p2g_channels<D, MODE>()]) {
+__device__ __forceinline__ void accumulate_rec(const float4 *rec, int i, int my_cp, float inv_h,
+                                               float acc[P2GRec<D, MODE>::CPT][p2g_channels<D, MODE>()]) {
   using R = P2GRec<D, MODE>;
   constexpr int NQ = R::NQ, CH = R::CH, CPT = R::CPT, CPC = R::CPC;
   constexpr bool HAS_M = R::HAS_M, HAS_F = R::HAS_F;
-  for (int i = i0; i < i1; ++i) {
+  {
     const int sl = rec_slot(i);
     float f[4 * NQ];
 #pragma unroll
@@ -276,6 +275,14 @@ __device__ __forceinline__ void accumulate_cell(const float4 *rec, int i0, int i
       }
     }
   }
+}
+
+// Accumulate the records i0..i1-1 of one cell, in order (plain sequential
+// FP32 sums per channel).
+template <int D, int MODE>
+__device__ __forceinline__ void accumulate_cell(const float4 *rec, int i0, int i1, int my_cp, float inv_h,
+                                                float acc[P2GRec<D, MODE>::CPT][p2g_channels<D, MODE>()]) {
+  for (int i = i0; i < i1; ++i) accumulate_rec<D, MODE>(rec, i, my_cp, inv_h, acc);
 }
 
 // Cell sums (cellP[cell][corner][channel]) -> the tile's node box, summed in
@@ -1056,15 +1063,18 @@ __device__ __forceinline__ int warp_incl(int x) {
 // by cp.async while the node gather runs.  A particle that stays in the tile
 // then forms its P2G record for the next step (the same arithmetic as P2G
 // from the stored state); the chunk's records are sorted by their new local
-// cell (stable: counts per warp, then a scan), and each thread of a (cell,
-// corner pair) adds its cell's records in order to its running sums in
-// shared memory.  At the end the cells go to the tile's node box and the box
-// to slots1, valid for the next step (fepoch = step + 1).  Particles that
-// leave the tile are left to the next step's residual P2G (they arrive in
-// another tile), as are tiles whose FP64 apex-band returns change a stress
-// after this kernel (apex_band_k invalidates their sums).  Summing in
-// binning order, chunk after chunk, gives each (cell, corner) the order the
-// plain P2G would use, so a tile that no particle enters has the same sums.
+// cell: each thread of a (cell, corner pair) adds, to its running sums in
+// shared memory, the records of the particles of its cell that stayed in it
+// (the chunk is in binning order, so they form the cell's run), then those of
+// the particles that moved into it from another cell of the tile (listed per
+// warp, in binning order).  At the end the cells go to the tile's node box
+// and the box to slots1, valid for the next step (fepoch = step + 1).
+// Particles that leave the tile are left to the next step's residual P2G
+// (they arrive in another tile), as are tiles whose FP64 apex-band returns
+// change a stress after this kernel (apex_band_k invalidates their sums).
+// While no particle changes cell, each (cell, corner) sums in the order the
+// plain P2G of the stored state uses, so the sums are the same.  Two
+// barriers per chunk.
 // ---------------------------------------------------------------------------
 #ifndef MPM_G2PF_MINB
 #define MPM_G2PF_MINB 3  // resident fused G2P CTAs per SM the register budget is sized for
@@ -1079,12 +1089,11 @@ struct G2PF {
   // staged state: sig, eps, J-1, eps_p, velocity, mass, id, cohesion
   static constexpr int S_SIG = 0, S_EPS = NS, S_JM1 = 2 * NS, S_EPSP = 2 * NS + 1, S_VEL = 2 * NS + 2,
                        S_MASS = S_VEL + D, S_ID = S_MASS + 1, S_COH = S_ID + 1, NSTG = S_COH + 1;
-  static constexpr size_t STG_BYTES = sizeof(float) * NSTG * T;
+  static constexpr size_t STG_BYTES = (sizeof(float) * NSTG * T + 15) / 16 * 16;
   static constexpr size_t REC_BYTES = sizeof(float4) * NQ * T;
-  static constexpr size_t UNION_BYTES = ((STG_BYTES > REC_BYTES ? STG_BYTES : REC_BYTES) + 15) / 16 * 16;
   static constexpr size_t CELLP_BYTES = (sizeof(float) * CELLS_PER_TILE * NV + 15) / 16 * 16;
   static constexpr size_t NODES_BYTES = sizeof(float4) * BN * NREC;
-  static constexpr size_t SMEM = UNION_BYTES + CELLP_BYTES + NODES_BYTES;
+  static constexpr size_t SMEM = REC_BYTES + STG_BYTES + CELLP_BYTES + NODES_BYTES;
 };
 
 template <int D, bool ONE>
@@ -1096,24 +1105,29 @@ __global__ void __launch_bounds__(G2PF<D>::T, MPM_G2PF_MINB) g2p_tile(const __gr
   constexpr int CPT = F::R::CPT, CPC = F::R::CPC;
   constexpr int NW = T / 32;
   extern __shared__ float4 sm4[];
-  float *stg = reinterpret_cast<float *>(sm4);  // [NSTG][T] staged state, then (aliased) the records
-  float4 *rec = sm4;                            // [NQ][T]
-  float *cellP = reinterpret_cast<float *>(reinterpret_cast<char *>(sm4) + F::UNION_BYTES);  // [64][NV]
-  float4 *nodes_s = reinterpret_cast<float4 *>(reinterpret_cast<char *>(sm4) + F::UNION_BYTES + F::CELLP_BYTES);
-  __shared__ int cnt_s[CELLS_PER_TILE], cs[CELLS_PER_TILE];
-  __shared__ uint16_t wpre[NW][CELLS_PER_TILE + 1];  // per warp: counts by new cell, then offsets
+  float4 *rec = sm4;                                                                  // [NQ][T] P2G records
+  float *stg = reinterpret_cast<float *>(reinterpret_cast<char *>(sm4) + F::REC_BYTES);  // [NSTG][T] state
+  float *cellP = reinterpret_cast<float *>(reinterpret_cast<char *>(sm4) + F::REC_BYTES + F::STG_BYTES);  // [64][NV]
+  float4 *nodes_s =
+      reinterpret_cast<float4 *>(reinterpret_cast<char *>(sm4) + F::REC_BYTES + F::STG_BYTES + F::CELLP_BYTES);
+  __shared__ int cs[CELLS_PER_TILE], ce[CELLS_PER_TILE], stamp[CELLS_PER_TILE];  // runs of the old cells
+  __shared__ uint8_t kind[T];      // 1: stays in its cell, 2: moves to another cell of the tile, 0: neither
+  __shared__ uint8_t ncell[T];     // new local cell of a kind-2 particle
+  __shared__ uint8_t mvw[NW][32];  // per warp: its kind-2 particles, in binning order
+  __shared__ int cntw[NW];
   __shared__ int s_work[2];
   __shared__ InstArgs sI;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned lt_mask = (1u << lane) - 1u;
   const int my_cell = tid / CPC, my_cp = tid % CPC;  // corners my_cp + r * CPC
   pdl_trigger();
+  if (tid < CELLS_PER_TILE) stamp[tid] = -1;
   pdl_wait();
   // items: first the CTA's own (blockIdx.x), then gridDim.x + the work counter
   const int total = G.bin_items[G.ninst];
   if (tid == 0) s_work[0] = blockIdx.x;
   __syncthreads();
-  int loaded = -1;
+  int loaded = -1, chunk_id = 0;
 
   for (int it = 0;; ++it) {
     const int wi = s_work[it & 1];
@@ -1157,10 +1171,9 @@ __global__ void __launch_bounds__(G2PF<D>::T, MPM_G2PF_MINB) g2p_tile(const __gr
 
     for (int c0 = s; c0 < e; c0 += T) {
       const int q = c0 + tid;
-      int lcn = CELLS_PER_TILE;  // new local cell of a particle that stays in the tile; none otherwise
-      float f[4 * NQ];           // its record for the next step's P2G
-#pragma unroll
-      for (int k = 0; k < 4 * NQ; ++k) f[k] = 0.f;
+      const int c1 = min(e, c0 + T);
+      int kd = 0;                 // kind of this thread's particle
+      unsigned lcn = 0;           // its new local cell
       if (q < e) {
         const int j = I.perm_out[q];
         const uint32_t key = I.keys_out[q];
@@ -1182,6 +1195,14 @@ __global__ void __launch_bounds__(G2PF<D>::T, MPM_G2PF_MINB) g2p_tile(const __gr
         cp_async_commit();
         int lc[3];
         local_coords<D>(key, lc);
+        {  // runs of the old cells within the chunk (binning order groups them)
+          const int lo = key & (CELLS_PER_TILE - 1);
+          if (q == c0 || (int)(I.keys_out[q - 1] & (CELLS_PER_TILE - 1)) != lo) {
+            cs[lo] = tid;
+            stamp[lo] = chunk_id;
+          }
+          if (q == c1 - 1 || (int)(I.keys_out[q + 1] & (CELLS_PER_TILE - 1)) != lo) ce[lo] = tid + 1;
+        }
         int cell[3] = {tc[0] * TX + lc[0], tc[1] * TY + lc[1], D == 3 ? tc[2] * TZ + lc[2] : 0};
         float u[D], w0[D], w1[D];
 #pragma unroll
@@ -1356,57 +1377,51 @@ __global__ void __launch_bounds__(G2PF<D>::T, MPM_G2PF_MINB) g2p_tile(const __gr
         I.B.epsp()[q] = epsp;
         if (status) atomicOr(&I.s.ctr[C_STATUS], status);
         if (!mover) {  // stays in the tile: its record for the next step's P2G
-          lcn = l2;
+          float f[4 * NQ];
           p2g_record<D, P2G_USL>(un, mass, vk, jn, sg, g.inv_rho, f);
+          const int sl = rec_slot(tid);
+#pragma unroll
+          for (int k = 0; k < NQ; ++k)
+            rec[k * T + sl] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
+          lcn = (unsigned)l2;
+          kd = l2 == (int)(key & (CELLS_PER_TILE - 1)) ? 1 : 2;
         }
       }
-      // ---- the chunk's records sorted by new local cell (stable), then summed
-      for (int k = lane; k <= CELLS_PER_TILE; k += 32) wpre[warp][k] = 0;
-      __syncwarp();
-      const unsigned peers = __match_any_sync(0xffffffffu, lcn);
-      const int rank = __popc(peers & lt_mask);
-      if (rank == 0) wpre[warp][lcn] = (uint16_t)__popc(peers);
-      __syncthreads();  // every warp's counts are in; every thread has read its staged state
-      if (tid < CELLS_PER_TILE) {  // per cell: the warps' counts -> offsets within the cell
-        int run = 0;
-#pragma unroll
-        for (int w = 0; w < NW; ++w) {
-          const int c = wpre[w][tid];
-          wpre[w][tid] = (uint16_t)run;
-          run += c;
-        }
-        cnt_s[tid] = run;
+      // the particles that moved to another cell of the tile, per warp in order
+      const unsigned mv2 = __ballot_sync(0xffffffffu, kd == 2);
+      if (kd == 2) {
+        mvw[warp][__popc(mv2 & lt_mask)] = (uint8_t)tid;
+        ncell[tid] = (uint8_t)lcn;
       }
+      kind[tid] = (uint8_t)kd;
+      if (lane == 0) cntw[warp] = __popc(mv2);
       __syncthreads();
-      if (warp == 0) {  // cell starts: exclusive scan of the 64 counts
-        const int a = cnt_s[lane], b = cnt_s[lane + 32];
-        const int ia = warp_incl(a);
-        const int ta = __shfl_sync(0xffffffffu, ia, 31);
-        const int ib = warp_incl(b);
-        cs[lane] = ia - a;
-        cs[lane + 32] = ta + ib - b;
-      }
-      __syncthreads();
-      if (lcn < CELLS_PER_TILE) {
-        const int sl = rec_slot(cs[lcn] + wpre[warp][lcn] + rank);
-#pragma unroll
-        for (int k = 0; k < NQ; ++k) rec[k * T + sl] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
-      }
-      __syncthreads();
-      {
+      {  // my (cell, corner pair): the cell's stayers in order, then the particles that moved in
         float acc[CPT][NCH];
 #pragma unroll
         for (int r = 0; r < CPT; ++r)
 #pragma unroll
           for (int ch = 0; ch < NCH; ++ch) acc[r][ch] = cellP[my_cell * NV + (my_cp + r * CPC) * NCH + ch];
-        const int i0 = cs[my_cell];
-        accumulate_cell<D, P2G_USL>(rec, i0, i0 + cnt_s[my_cell], my_cp, g.inv_h, acc);
+        if (stamp[my_cell] == chunk_id) {
+          const int i1 = ce[my_cell];
+          for (int i = cs[my_cell]; i < i1; ++i)
+            if (kind[i] == 1) accumulate_rec<D, P2G_USL>(rec, i, my_cp, g.inv_h, acc);
+        }
+#pragma unroll 1
+        for (int w = 0; w < NW; ++w) {
+          const int nw = cntw[w];
+          for (int k = 0; k < nw; ++k) {
+            const int i = mvw[w][k];
+            if (ncell[i] == my_cell) accumulate_rec<D, P2G_USL>(rec, i, my_cp, g.inv_h, acc);
+          }
+        }
 #pragma unroll
         for (int r = 0; r < CPT; ++r)
 #pragma unroll
           for (int ch = 0; ch < NCH; ++ch) cellP[my_cell * NV + (my_cp + r * CPC) * NCH + ch] = acc[r][ch];
       }
-      __syncthreads();  // the records are read; the next chunk stages over them
+      ++chunk_id;
+      __syncthreads();  // the records are read; the next chunk writes over them
     }
     cells_to_slot<D, NCH>(cellP, I.s.slots1, t, T);
     if (tid == 0) {
