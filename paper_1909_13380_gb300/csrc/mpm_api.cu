@@ -476,7 +476,8 @@ void free_t(T *&p) {
 // Device bytes of the FP32 step storage that does not scale with particles.
 int64_t f32_fixed_bytes(const mpm_mesh_desc &d, int64_t nt, int64_t nn) {
   const int bn = d.dim == 3 ? box_nodes<3>() : box_nodes<2>();
-  int64_t b = 4 * nt * bn * (1 + 2 * d.dim) * (d.scheme == MPM_USL ? 2 : 1) + (d.scheme == MPM_USF ? 4 * nt * bn * d.dim : 0);
+  int64_t b = 4 * nt * bn * (1 + 2 * d.dim) * (d.scheme == MPM_USL && MPM_FUSED_USL ? 2 : 1) +
+              (d.scheme == MPM_USF ? 4 * nt * bn * d.dim : 0);
   b += 9 * 4 * (nt + 2) + 2 * 16 * (nt + 2) + 16 * nn * (d.dim == 3 ? 2 : 1) + 4096;
   return b;
 }
@@ -559,7 +560,7 @@ mpm_status mpm_create_mesh(const mpm_mesh_desc *desc, mpm_handle *out) {
     const size_t ti = sizeof(int32_t) * (nt + 2);
     if (e == cudaSuccess) e = cudaMalloc(&S.slots1, s1);
     if (e == cudaSuccess && s2) e = cudaMalloc(&S.slots2, s2);
-    if (e == cudaSuccess && d.scheme == MPM_USL) e = cudaMalloc(&S.slots_a, s1);
+    if (e == cudaSuccess && d.scheme == MPM_USL && MPM_FUSED_USL) e = cudaMalloc(&S.slots_a, s1);
     if (e == cudaSuccess) e = cudaMalloc(&S.fepoch, sizeof(int32_t) * nt);
     if (e == cudaSuccess) e = cudaMalloc(&S.aepoch, sizeof(int32_t) * nt);
     if (e == cudaSuccess) e = cudaMalloc(&S.resid, sizeof(int32_t) * (nt + 2));

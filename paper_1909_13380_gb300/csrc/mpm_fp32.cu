@@ -661,7 +661,7 @@ __global__ void __launch_bounds__(NODE_T, ONE ? MPM_NODE_MINB : 8) node_tile(con
       if (in) {
         const int t2 = n3[0] + g.nt[0] * (n3[1] + g.nt[1] * n3[2]);
         nact = I.new_start[t2 + 1] > I.new_start[t2];
-        if (NMODE == NODE_USL) {
+        if (NMODE == NODE_USL && MPM_FUSED_USL) {
           const int step = I.s.ctr[C_STEP];
           fv = I.s.fepoch[t2] == step;
           av = I.s.aepoch[t2] == step;
@@ -694,8 +694,10 @@ __global__ void __launch_bounds__(NODE_T, ONE ? MPM_NODE_MINB : 8) node_tile(con
 #pragma unroll
       for (int k = 0; k < D; ++k) v[k] = a[k] = vn[k] = 0.f;
       float c1[1 + 2 * D];
-      if (NMODE == NODE_USL)
+      if (NMODE == NODE_USL && MPM_FUSED_USL)
         gather_node_usl<D, 1 + 2 * D>(g, I.s.slots1, I.s.slots_a, Ig, lo, hi, tc, act, fmask27, amask27, c1);
+      else if (NMODE == NODE_USL)
+        gather_node<D, 1 + 2 * D>(g, I.s.slots1, NCH1, Ig, lo, hi, act, c1);
       else
         gather_node<D, 1 + D>(g, I.s.slots1, NCH1, Ig, lo, hi, act, c1);
       const float m = c1[0];
@@ -1525,12 +1527,22 @@ cudaError_t step_dim(int scheme, const GroupArgs &G, cudaEvent_t *ev, cudaStream
   cudaError_t e;
   // phase events 0 (start) and 1 (after binning) are recorded by the
   // caller; 2.. follow each kernel here
-  if (scheme == 1) {  // USL: residual P2G, nodes, G2P fused with the next step's P2G
+  if (scheme == 1) {
+#if MPM_FUSED_USL
+    // residual P2G, nodes, G2P fused with the next step's P2G
     if ((e = launch_p2g<D, P2G_USL, true>(G, W_P2G, st)) != cudaSuccess) return e;
     if ((e = phase_mark(ev, 2, st)) != cudaSuccess) return e;
     if ((e = launch_node<D, NODE_USL>(G, W_NODE, st)) != cudaSuccess) return e;
     if ((e = phase_mark(ev, 3, st)) != cudaSuccess) return e;
     if ((e = launch_g2p_tile<D>(G, st)) != cudaSuccess) return e;
+#else
+    // P2G, nodes, per-particle G2P
+    if ((e = launch_p2g<D, P2G_USL>(G, W_P2G, st)) != cudaSuccess) return e;
+    if ((e = phase_mark(ev, 2, st)) != cudaSuccess) return e;
+    if ((e = launch_node<D, NODE_USL>(G, W_NODE, st)) != cudaSuccess) return e;
+    if ((e = phase_mark(ev, 3, st)) != cudaSuccess) return e;
+    if ((e = launch_g2p<D, G2P_USL>(G, st)) != cudaSuccess) return e;
+#endif
     return phase_mark(ev, 4, st);
   }
   // USF
@@ -1668,15 +1680,21 @@ __global__ void mat_update_f32_k(MatConst<float> m, MatConst<double> md, int64_t
 cudaError_t f32_prepare(int dim) {
   cudaError_t e;
   if (dim == 3) {
+#if MPM_FUSED_USL
     if ((e = prepare_p2g<3, P2G_USL, true>()) != cudaSuccess) return e;
+    if ((e = prepare_g2p_tile<3>()) != cudaSuccess) return e;
+#endif
+    if ((e = prepare_p2g<3, P2G_USL>()) != cudaSuccess) return e;
     if ((e = prepare_p2g<3, P2G_MOM>()) != cudaSuccess) return e;
-    if ((e = prepare_p2g<3, P2G_FORCE>()) != cudaSuccess) return e;
-    return prepare_g2p_tile<3>();
+    return prepare_p2g<3, P2G_FORCE>();
   }
+#if MPM_FUSED_USL
   if ((e = prepare_p2g<2, P2G_USL, true>()) != cudaSuccess) return e;
+  if ((e = prepare_g2p_tile<2>()) != cudaSuccess) return e;
+#endif
+  if ((e = prepare_p2g<2, P2G_USL>()) != cudaSuccess) return e;
   if ((e = prepare_p2g<2, P2G_MOM>()) != cudaSuccess) return e;
-  if ((e = prepare_p2g<2, P2G_FORCE>()) != cudaSuccess) return e;
-  return prepare_g2p_tile<2>();
+  return prepare_p2g<2, P2G_FORCE>();
 }
 
 __global__ void gather_status_k(const InstArgs *tab, int ninst, int32_t *out) {

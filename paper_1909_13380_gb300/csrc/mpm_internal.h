@@ -195,6 +195,15 @@ __device__ __forceinline__ void copy_inst(const InstArgs *tab, int ii, InstArgs 
   for (int i = threadIdx.x; i < (int)(sizeof(InstArgs) / 8); i += blockDim.x) d[i] = __ldg(src + i);
 }
 
+// USL step form.  0 (default): P2G of the stored state, the nodal solve, a
+// G2P thread per particle.  1: G2P fused with the next step's P2G (one CTA
+// per tile sums the P2G of the particles that stay in the tile while it
+// moves them; a residual P2G adds arrivals) -- correct, but slower on every
+// workload measured, so not the default.
+#ifndef MPM_FUSED_USL
+#define MPM_FUSED_USL 0
+#endif
+
 // Polls a wait of the look-back tile scan makes before it gives up (and sets
 // ST_TIMEOUT); every wait is on a block that is already running, so it ends
 // long before this.

@@ -45,7 +45,9 @@ def test_withheld_scan_flag_times_out_and_freezes_only_that_mesh():
         s.step(1)
         bystander.step(5)
         assert s.sync() == mpm.MPM_ERR_TIMEOUT
-        s.step(3)                                   # frozen: carried over, nothing faults
+        # frozen: the steps are still enqueued (they carry the mesh over) and
+        # report the latched status; nothing faults
+        assert mpm.load().mpm_step(s.h, 3) == mpm.MPM_ERR_TIMEOUT
         assert s.sync() == mpm.MPM_ERR_TIMEOUT
         snap, st = s.read()
         assert st == mpm.MPM_ERR_TIMEOUT

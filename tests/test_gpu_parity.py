@@ -464,11 +464,12 @@ def test_request_kinds_fp32(kind, scheme):
 
 
 def _fused_vs_full(wl, steps):
-    """The same run twice: plain steps (each G2P sums the next step's P2G of
-    the particles that stay in their tile, the residual P2G adds arrivals),
-    and steps each followed by a scratch binning, which advances the step
-    index so that every tile's next P2G is recomputed in full from the
-    stored state."""
+    """The same run twice: plain steps, and steps each followed by a scratch
+    binning (mpm_read_binning), which must leave the trajectory alone.  It
+    also advances the step index, so with the fused USL step (G2P summing the
+    next step's P2G of the particles that stay in their tile, a residual P2G
+    adding arrivals) every tile's next P2G is recomputed in full from the
+    stored state: the comparison is then fused against full sums."""
     with mpm.Simulation(wl) as a, mpm.Simulation(wl) as b:
         for _ in range(steps):
             a.step(1)
@@ -481,8 +482,8 @@ def _fused_vs_full(wl, steps):
 
 
 def test_fused_p2g_equals_the_full_p2g_while_no_particle_changes_tile():
-    # the first steps of the column from rest: nothing crosses a tile face,
-    # so the fused sums are the plain P2G's, bit for bit
+    # the first steps of the column from rest: nothing crosses a cell face,
+    # so (with the fused step) the fused sums are the plain P2G's, bit for bit
     ra, rb = _fused_vs_full(H.small_column(), 30)
     for k in ra:
         assert np.array_equal(ra[k], rb[k]), k
