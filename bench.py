@@ -111,12 +111,11 @@ def algorithmic_bytes(dim: int, coh: bool):
     p2g = 4 + 4 * dim + 4 * dim + 4 * ns + 8 + box
     g2p = read + write + nodes_per_particle * 4 * 2 * dim
     step = (212 if dim == 3 else 174) + (4 if coh else 0)
-    # USL: G2P fused with the next step's P2G also writes the tile's node box
-    return {"p2g": p2g, "g2p": g2p, "g2p_fused": g2p + box, "step": step}
+    return {"p2g": p2g, "g2p": g2p, "step": step}
 
 
-# The kernel behind each timed phase (USL: the G2P fused with the next P2G).
-KERNEL_NAMES = {"p2g": "p2g_tile", "g2p": "g2p", "g2p_fused": "g2p_tile"}
+# The kernel behind each timed phase.
+KERNEL_NAMES = {"p2g": "p2g_tile", "g2p": "g2p"}
 
 
 def load_peak():
@@ -563,7 +562,7 @@ def run_gb300(args):
         ["binning", "p2g_mom", "node_v", "g2p_stress", "p2g_force", "node_a", "g2p_advect"]
     ab = algorithmic_bytes(wl.dim, wl.coh is not None)
     peak, peak_kind = load_peak()
-    kernels = {"p2g": ph_mean[1], "g2p_fused": ph_mean[3]} if wl.scheme == W.USL else \
+    kernels = {"p2g": ph_mean[1], "g2p": ph_mean[3]} if wl.scheme == W.USL else \
         {"p2g": ph_mean[1] + ph_mean[4], "g2p": ph_mean[3] + ph_mean[6]}
     dom = max(kernels, key=kernels.get)
     achieved = ab[dom] * wl.n / (kernels[dom] * 1e-3) / 1e9

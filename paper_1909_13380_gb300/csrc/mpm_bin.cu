@@ -531,6 +531,27 @@ __global__ void __launch_bounds__(NT) bin_tiles(const __grid_constant__ GroupArg
     const int nbk = be - bs;
     const uint32_t *knew = I.A.key();
 
+    // No arrivals, and the old range still holds only this tile's keys in
+    // ascending order (no particle left the tile or changed cell out of
+    // order): the stable sort is the identity on the range.
+    if (nbk == 0 && t < ntiles) {
+      const int nr = oe - os;
+      bool sorted = true;
+      for (int k = tid; k < nr; k += NT) {
+        const uint32_t kk = knew[os + k];
+        sorted = sorted && (int)(kk >> LOCAL_BITS) == t && (k == 0 || knew[os + k - 1] <= kk);
+      }
+      if (__syncthreads_and(sorted)) {
+        for (int k = tid; k < nr; k += NT) {
+          I.perm_out[ns + k] = os + k;
+          I.keys_out[ns + k] = knew[os + k];
+        }
+        if (tid == 0) s_work[(it + 1) & 1] = wnext;
+        __syncthreads();
+        continue;
+      }
+    }
+
     // arrivals sorted by storage position (positions are distinct)
     const int *sorted;
     if (nbk <= BUCKET_SMEM) {

@@ -158,25 +158,28 @@ __device__ __forceinline__ void bc_full(int faces, const int *bc, const T *mu, T
 }
 
 // ---------------------------------------------------------------------------
-// Explicitly rounded operations for the material update.  Whether the
+// Explicitly rounded operations for the FP32 material update.  Whether the
 // compiler contracts a product and a sum into one FMA depends on the code
 // around them, so the same source, inlined into two kernels (a mesh stepped
 // alone, and in a batch), could round differently.  Written with explicit
 // round-to-nearest operations -- never contracted or reassociated -- the
-// material update rounds the same way in every kernel.
+// FP32 material update rounds the same way in every kernel.  The FP64
+// overloads are the plain operators: the FP64 plain step runs one mesh at a
+// time, and the FP64 apex-band return is one out-of-line function, so each
+// is compiled once, and the FP64 pipe keeps its fused multiply-adds.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float xm(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ double xm(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double xm(double a, double b) { return a * b; }
 __device__ __forceinline__ float xa(float a, float b) { return __fadd_rn(a, b); }
-__device__ __forceinline__ double xa(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double xa(double a, double b) { return a + b; }
 __device__ __forceinline__ float xs(float a, float b) { return __fsub_rn(a, b); }
-__device__ __forceinline__ double xs(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double xs(double a, double b) { return a - b; }
 __device__ __forceinline__ float xf(float a, float b, float c) { return __fmaf_rn(a, b, c); }  // a b + c
-__device__ __forceinline__ double xf(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ double xf(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float xd(float a, float b) { return __fdiv_rn(a, b); }
-__device__ __forceinline__ double xd(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ double xd(double a, double b) { return a / b; }
 __device__ __forceinline__ float xsqrt(float a) { return __fsqrt_rn(a); }
-__device__ __forceinline__ double xsqrt(double a) { return __dsqrt_rn(a); }
+__device__ __forceinline__ double xsqrt(double a) { return sqrt(a); }
 // a b + c d + e f, and the dot product of two 3-vectors
 template <typename T>
 __device__ __forceinline__ T xdot3(T a, T b, T c, T d, T e, T f) {

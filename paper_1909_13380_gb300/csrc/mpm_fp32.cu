@@ -318,9 +318,192 @@ __device__ __forceinline__ void cells_to_slot(const float *cellP, float *slots_o
   }
 }
 
-// P2G over tiles.  Plain (RES false): the work items are the active tiles,
-// every particle of a tile is staged, the box goes to slots1 (slots2 for the
-// USF force stage).  Residual (RES, USL): the items are the active tiles whose
+template <int D, int MODE, bool ONE>
+__global__ void __launch_bounds__(P2GRec<D, MODE>::CH, p2g_min_blocks<D, MODE, ONE>())
+    p2g_tile(const __grid_constant__ GroupArgs G, int work_slot) {
+  using R = P2GRec<D, MODE>;
+  constexpr int NCH = p2g_channels<D, MODE>();
+  constexpr int NV = R::NV;
+  constexpr int CH = R::CH;
+  constexpr int NQ = R::NQ;
+  constexpr int CPT = R::CPT, CPC = R::CPC;
+  constexpr int BN = box_nodes<D>();
+  constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ;
+  constexpr bool HAS_M = R::HAS_M, HAS_F = R::HAS_F;
+  extern __shared__ float4 sm4[];
+  float4 *rec = sm4;                              // [NQ][CH] float4
+  float *cellP = reinterpret_cast<float *>(sm4);  // [64][NV], after the chunks
+  __shared__ int cs[CELLS_PER_TILE], ce[CELLS_PER_TILE], stamp[CELLS_PER_TILE];
+  __shared__ int s_work[2];
+  __shared__ InstArgs sI;
+  const int tid = threadIdx.x;
+  const int my_cell = tid / CPC, my_cp = tid % CPC;  // corners my_cp + r * CPC
+  pdl_trigger();
+  if (tid < CELLS_PER_TILE) stamp[tid] = -1;
+  pdl_wait();
+  // items: first the CTA's own (blockIdx.x), then gridDim.x + the work counter
+  const int total = G.act_items[G.ninst];
+  if (tid == 0) s_work[0] = blockIdx.x;
+  __syncthreads();
+  int chunk_id = 0, loaded = -1;
+
+  for (int it = 0;; ++it) {
+    const int wi = s_work[it & 1];
+    if (wi >= total) break;
+    // the next work item is fetched now and published at the end of this one
+    int wnext = 0;
+    if (tid == 0) wnext = (int)gridDim.x + atomicAdd(&G.work[work_slot], 1);
+    const int ii = ONE ? 0 : find_inst(G.act_items, G.ninst, wi);
+    if (!ONE && ii != loaded) {  // uniform
+      copy_inst(G.inst, ii, &sI);
+      loaded = ii;
+      __syncthreads();
+    }
+    const InstArgs &I = inst_ref<ONE>(G, sI);
+    const Geo &g = I.geo;
+    float *slots_out = MODE == P2G_FORCE ? I.s.slots2 : I.s.slots1;
+    const int4 ar = I.s.active[ONE ? wi : wi - G.act_items[ii]];
+    const int t = ar.x, s = ar.y, e = ar.z;
+    float acc[CPT][NCH];
+#pragma unroll
+    for (int r = 0; r < CPT; ++r)
+#pragma unroll
+      for (int ch = 0; ch < NCH; ++ch) acc[r][ch] = 0.f;
+
+    for (int c0 = s; c0 < e; c0 += CH) {
+      // ---- stage this chunk: particle q = c0 + tid
+      const int q = c0 + tid;
+      const int c1 = min(e, c0 + CH);
+      if (q < c1) {
+        const int j = I.perm_out[q];
+        const int lc = I.keys_out[q] & (CELLS_PER_TILE - 1);
+        float f[4 * NQ];
+#pragma unroll
+        for (int k = 0; k < 4 * NQ; ++k) f[k] = 0.f;
+#pragma unroll
+        for (int k = 0; k < D; ++k) f[k] = I.A.off(k)[j];
+        const float mm = I.A.mass()[j];
+        if (HAS_M) {
+          f[D] = mm;
+#pragma unroll
+          for (int k = 0; k < D; ++k) f[D + 1 + k] = mm * I.A.vel(k)[j];
+        }
+        if (HAS_F) {
+          // FORCE (USF) reads the stress updated earlier this step, stored in
+          // binning order; USL reads the stress at the start of the step
+          const PBuf &S = (MODE == P2G_FORCE) ? I.B : I.A;
+          const int js = (MODE == P2G_FORCE) ? q : j;
+          const float nV = -mm * g.inv_rho * (1.f + S.jm1()[js]);
+          constexpr int o = HAS_M ? 2 * D + 1 : D;
+          if (D == 3) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) f[o + k] = nV * S.sig(k)[js];
+          } else {
+            f[o] = nV * S.sig(0)[js];
+            f[o + 1] = nV * S.sig(1)[js];
+            f[o + 2] = nV * S.sig(3)[js];
+          }
+        }
+        const int sl = rec_slot(tid);
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) rec[k * CH + sl] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
+        // run boundaries of the cell within the chunk
+        const bool first = q == c0 || (int)(I.keys_out[q - 1] & (CELLS_PER_TILE - 1)) != lc;
+        const bool last = q == c1 - 1 || (int)(I.keys_out[q + 1] & (CELLS_PER_TILE - 1)) != lc;
+        if (first) {
+          cs[lc] = tid;
+          stamp[lc] = chunk_id;
+        }
+        if (last) ce[lc] = tid + 1;
+      }
+      __syncthreads();
+      // ---- accumulate my (cell, corner) pairs over the cell's particles in order
+      if (stamp[my_cell] == chunk_id) {
+        const int i0 = cs[my_cell], i1 = ce[my_cell];
+        for (int i = i0; i < i1; ++i) {
+          const int sl = rec_slot(i);
+          float f[4 * NQ];
+#pragma unroll
+          for (int k = 0; k < NQ; ++k) {
+            const float4 rv = rec[k * CH + sl];
+            f[4 * k] = rv.x;
+            f[4 * k + 1] = rv.y;
+            f[4 * k + 2] = rv.z;
+            f[4 * k + 3] = rv.w;
+          }
+          static_assert(CPT == (D == 3 ? 2 : 1) && CPC == 4, "corners my_cp + 4 r: z bit = r");
+          const ThreadCorners<D> tc(f, my_cp, g.inv_h);
+#pragma unroll
+          for (int r = 0; r < CPT; ++r) {
+            float N, Gr[D];
+            tc.corner(r, N, Gr);
+            if (HAS_M) {
+              acc[r][0] = fmaf(f[D], N, acc[r][0]);
+#pragma unroll
+              for (int k = 0; k < D; ++k) acc[r][1 + k] = fmaf(f[D + 1 + k], N, acc[r][1 + k]);
+            }
+            if (HAS_F) {
+              constexpr int o = HAS_M ? 2 * D + 1 : D;
+              constexpr int a0 = HAS_M ? 1 + D : 0;
+              if (D == 3) {
+                // nV sig: xx yy zz xy yz xz
+                const float t3[3][3] = {{f[o], f[o + 3], f[o + 5]}, {f[o + 3], f[o + 1], f[o + 4]},
+                                        {f[o + 5], f[o + 4], f[o + 2]}};
+#pragma unroll
+                for (int k = 0; k < D; ++k)
+#pragma unroll
+                  for (int jj = 0; jj < D; ++jj) acc[r][a0 + k] = fmaf(t3[k][jj], Gr[jj], acc[r][a0 + k]);
+              } else {
+                const float t2[2][2] = {{f[o], f[o + 2]}, {f[o + 2], f[o + 1]}};
+#pragma unroll
+                for (int k = 0; k < D; ++k)
+#pragma unroll
+                  for (int jj = 0; jj < D; ++jj) acc[r][a0 + k] = fmaf(t2[k][jj], Gr[jj], acc[r][a0 + k]);
+              }
+            }
+          }
+        }
+      }
+      ++chunk_id;
+      __syncthreads();  // the next chunk overwrites the records
+    }
+
+    // ---- cells -> node box (ascending local cell order), compensated; -> slot
+#pragma unroll
+    for (int r = 0; r < CPT; ++r)
+#pragma unroll
+      for (int ch = 0; ch < NCH; ++ch) cellP[my_cell * NV + (my_cp + r * CPC) * NCH + ch] = acc[r][ch];
+    __syncthreads();
+    for (int b = tid; b < BN; b += CH) {
+      const int bx = b % (TX + 1);
+      const int by = (b / (TX + 1)) % (TY + 1);
+      const int bz = D == 3 ? b / ((TX + 1) * (TY + 1)) : 0;
+      TwoAcc<float> ta[NCH];
+#pragma unroll
+      for (int ch = 0; ch < NCH; ++ch) ta[ch].init();
+#pragma unroll
+      for (int dz = (D == 3 ? 1 : 0); dz >= 0; --dz)
+#pragma unroll
+        for (int dy = 1; dy >= 0; --dy)
+#pragma unroll
+          for (int dx = 1; dx >= 0; --dx) {
+            const int cx = bx - dx, cy = by - dy, cz = bz - dz;
+            if (cx < 0 || cx >= TX || cy < 0 || cy >= TY || cz < 0 || cz >= TZ) continue;
+            const int cl = cx + TX * (cy + TY * cz);
+            const int a = dx + 2 * dy + 4 * dz;
+#pragma unroll
+            for (int ch = 0; ch < NCH; ++ch) ta[ch].add(cellP[cl * NV + a * NCH + ch]);
+          }
+#pragma unroll
+      for (int ch = 0; ch < NCH; ++ch) slots_out[((int64_t)t * NCH + ch) * BN + b] = ta[ch].value();
+    }
+    if (tid == 0) s_work[(it + 1) & 1] = wnext;
+    __syncthreads();
+  }
+}
+
+
+// Residual P2G of the fused USL step (RES): the items are the active tiles whose
 // next-step P2G the previous G2P did not complete (the scan's residual
 // list): a tile without valid sums for this step (fepoch != step) sums all
 // its particles into slots1 (fepoch = step); a tile with valid sums sums only
@@ -329,8 +512,8 @@ __device__ __forceinline__ void cells_to_slot(const float *cellP, float *slots_o
 // binning order, so the cells' runs stay contiguous.
 template <int D, int MODE, bool ONE, bool RES>
 __global__ void __launch_bounds__(P2GRec<D, MODE>::CH, p2g_min_blocks<D, MODE, ONE>())
-    p2g_tile(const __grid_constant__ GroupArgs G, int work_slot) {
-  static_assert(!RES || MODE == P2G_USL, "the residual P2G is the USL one");
+    p2g_resid(const __grid_constant__ GroupArgs G, int work_slot) {
+  static_assert(RES && MODE == P2G_USL, "the residual P2G is the USL one");
   using R = P2GRec<D, MODE>;
   constexpr int NCH = p2g_channels<D, MODE>();
   constexpr int NV = R::NV;
@@ -1473,18 +1656,31 @@ __global__ void __launch_bounds__(APEX_T) apex_band_k(const __grid_constant__ Gr
 
 template <int D, int MODE, bool RES = false>
 cudaError_t launch_p2g(const GroupArgs &G, int work_slot, cudaStream_t st) {
-  return G.ninst == 1 ? launch_dep(p2g_tile<D, MODE, true, RES>, G.grid, p2g_threads<D>(), p2g_smem<D, MODE>(), st,
-                                   G, work_slot)
-                      : launch_dep(p2g_tile<D, MODE, false, RES>, G.grid, p2g_threads<D>(), p2g_smem<D, MODE>(), st,
-                                   G, work_slot);
+  if constexpr (RES)
+    return G.ninst == 1 ? launch_dep(p2g_resid<D, MODE, true, true>, G.grid, p2g_threads<D>(), p2g_smem<D, MODE>(),
+                                     st, G, work_slot)
+                        : launch_dep(p2g_resid<D, MODE, false, true>, G.grid, p2g_threads<D>(), p2g_smem<D, MODE>(),
+                                     st, G, work_slot);
+  else
+    return G.ninst == 1
+               ? launch_dep(p2g_tile<D, MODE, true>, G.grid, p2g_threads<D>(), p2g_smem<D, MODE>(), st, G, work_slot)
+               : launch_dep(p2g_tile<D, MODE, false>, G.grid, p2g_threads<D>(), p2g_smem<D, MODE>(), st, G, work_slot);
 }
 
 template <int D, int MODE, bool RES = false>
 cudaError_t prepare_p2g() {
-  cudaError_t e = cudaFuncSetAttribute(p2g_tile<D, MODE, true, RES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)p2g_smem<D, MODE>());
+  cudaError_t e;
+  if constexpr (RES) {
+    e = cudaFuncSetAttribute(p2g_resid<D, MODE, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)p2g_smem<D, MODE>());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(p2g_resid<D, MODE, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)p2g_smem<D, MODE>());
+  }
+  e = cudaFuncSetAttribute(p2g_tile<D, MODE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)p2g_smem<D, MODE>());
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(p2g_tile<D, MODE, false, RES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(p2g_tile<D, MODE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)p2g_smem<D, MODE>());
 }
 

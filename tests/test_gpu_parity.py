@@ -494,13 +494,13 @@ def test_fused_p2g_with_arrivals():
     # arrivals' sums go to their own slots, so only the summation order of
     # the nodes differs from the full P2G
     h = 1.0
-    cells = W.box_cells((6, 0), (8, 8))
+    cells = W.box_cells((6, 1), (8, 7))
     pos = np.repeat((cells + 0.5) * h, 50, axis=0)
     rng = np.random.default_rng(4)
     pos += rng.uniform(-0.45, 0.45, pos.shape) * h
-    vel = np.tile([0.6, 0.05], (pos.shape[0], 1))
+    vel = np.stack([np.full(pos.shape[0], 0.6), rng.uniform(-0.02, 0.02, pos.shape[0])], axis=1)
     wl = W.Workload(name="crossing_fused", dim=2, ncells=(32, 8, 1), h=h, origin=(0, 0, 0), face_bc=(0,) * 6,
-                    face_mu=(0,) * 6, gravity=(0, -1e-3, 0), dt=1.0, scheme=W.USL, precision=W.FP32_MIXED,
+                    face_mu=(0,) * 6, gravity=(0, 0, 0), dt=1.0, scheme=W.USL, precision=W.FP32_MIXED,
                     material=dict(model=0, E=1e-4, nu=0.2, rho=1.0, phi=0, c=0, psi=0), pos=pos, vel=vel,
                     vol=np.full(pos.shape[0], 1.0 / 50))
     ra, rb = _fused_vs_full(wl, 6)
