@@ -27,7 +27,7 @@ _LIB = os.path.join(_LIB_DIR, "libmpm_oracle.so")
 OK, ARG, LEFT_MESH, NONFINITE = 0, -1, -4, -5
 BC_FREE, BC_ROLLER, BC_FIXED, BC_FRICTION = 0, 1, 2, 3
 USF, USL = 0, 1
-LINEAR_ELASTIC, MOHR_COULOMB = 0, 1
+LINEAR_ELASTIC, MOHR_COULOMB, PLANE_STRESS_ELASTIC = 0, 1, 2
 
 
 class _Mesh(C.Structure):
@@ -42,6 +42,8 @@ class _Mesh(C.Structure):
         ("dt", C.c_double),
         ("scheme", C.c_int32),
         ("mass_tol", C.c_double),
+        ("face_traction", (C.c_double * 3) * 6),
+        ("damping", C.c_double),
     ]
 
 
@@ -130,6 +132,8 @@ class Mesh:
     dt: float = 1e-5
     scheme: int = USL
     mass_tol: float = 1e-12
+    face_traction: tuple = ((0.0, 0.0, 0.0),) * 6   # per face, force per unit length (area)
+    damping: float = 0.0                            # alpha of a = f / m - alpha v
 
     def c_struct(self) -> _Mesh:
         s = _Mesh()
@@ -143,6 +147,10 @@ class Mesh:
             s.face_bc[f] = int(self.face_bc[f])
             s.face_mu[f] = float(self.face_mu[f])
         s.h, s.dt, s.scheme, s.mass_tol = float(self.h), float(self.dt), int(self.scheme), float(self.mass_tol)
+        for f in range(6):
+            for k in range(3):
+                s.face_traction[f][k] = float(self.face_traction[f][k])
+        s.damping = float(self.damping)
         return s
 
     @property
@@ -326,6 +334,7 @@ def constrain_node(mesh: Mesh, ijk, v, a, vn):
 def from_workload(wl, scheme=None) -> Oracle:
     """Oracle on a workload from paper_1909_13380_gb300.workloads (inputs only)."""
     mesh = Mesh(dim=wl.dim, n=wl.ncells, h=wl.h, origin=wl.origin, face_bc=wl.face_bc, face_mu=wl.face_mu,
-                g=wl.gravity, dt=wl.dt, scheme=wl.scheme if scheme is None else scheme)
+                g=wl.gravity, dt=wl.dt, scheme=wl.scheme if scheme is None else scheme,
+                face_traction=wl.face_traction, damping=wl.damping)
     st = State.create(wl.pos, wl.vel, wl.vol, wl.material["rho"], coh=wl.coh)
     return Oracle(mesh, Material(**wl.material), st)

@@ -41,7 +41,20 @@
  *       volume update V <- V (1 + tr de).
  *   R6  a particle exactly on a cell face belongs to the higher cell (floor);
  *       a particle at or beyond the upper mesh bound has left the mesh.
- *   R7  2D is plane strain: the stress keeps its zz component, strain zz = 0.
+ *   R7  2D is plane strain: the stress keeps its zz component, strain zz = 0,
+ *       unless the material is the plane-stress elastic one (R8).
+ *   R8  plane stress (BENCHMARK AND PERFORMANCE: the plate with a hole is a
+ *       "plane strip (plane stress)"): stress zz = 0 and the in-plane
+ *       stiffness has lambda* = 2 lambda G / (lambda + 2 G) in place of
+ *       lambda; the area follows the in-plane trace of the strain increment.
+ *   R9  a uniform traction on an end of the body (the plate's "uniform
+ *       tension ... applied at the ends"): a constant force on the nodes of
+ *       the mesh face that coincides with that end, traction times the
+ *       node's tributary length (area in 3D): h per tangent axis, half of
+ *       it at the face's own edges.
+ *   R10 a quasi-static protocol (the plate's static stress field; the paper
+ *       gives none): mass-proportional viscous damping of the nodal motion,
+ *       a = f / m - alpha v, so the explicit run settles to equilibrium.
  *
  * Layout: every particle vector is stored with 3 components and every
  * stress/strain with 6 Voigt components (xx, yy, zz, xy, yz, xz; tensor
@@ -61,7 +74,7 @@
 
 enum { OM_BC_FREE = 0, OM_BC_ROLLER = 1, OM_BC_FIXED = 2, OM_BC_FRICTION = 3 };
 enum { OM_USF = 0, OM_USL = 1 };
-enum { OM_LINEAR_ELASTIC = 0, OM_MOHR_COULOMB = 1 };
+enum { OM_LINEAR_ELASTIC = 0, OM_MOHR_COULOMB = 1, OM_PLANE_STRESS_ELASTIC = 2 };
 
 typedef struct {
   int32_t dim;        /* 2 (4-node quad, plane strain) or 3 (8-node hex) */
@@ -74,10 +87,12 @@ typedef struct {
   double dt;
   int32_t scheme;     /* OM_USF / OM_USL */
   double mass_tol;    /* R2 */
+  double face_traction[6][3]; /* R9: traction on each face (force per length / area) */
+  double damping;     /* R10: alpha, 1/s */
 } om_mesh;
 
 typedef struct {
-  int32_t model;      /* OM_LINEAR_ELASTIC / OM_MOHR_COULOMB */
+  int32_t model;      /* OM_LINEAR_ELASTIC / OM_MOHR_COULOMB / OM_PLANE_STRESS_ELASTIC (2D) */
   double E, nu, rho;
   double phi, c, psi; /* radians, Pa, radians */
 } om_material;
@@ -462,11 +477,21 @@ int oracle_mc_return(double E, double nu, double phi, double psi, double c, cons
   return branch;
 }
 
-/* sigma <- sigma + D : de (trial), then the material's return. */
+/* sigma <- sigma + D : de (trial), then the material's return.  Plane stress
+ * (R8): lambda* = 2 lambda G / (lambda + 2 G), and sigma_zz stays 0. */
 static void stress_update(const om_material *mat, double coh, double sig[6], const double de[6],
                           double *epsp) {
   double G = mat->E / (2.0 * (1.0 + mat->nu));
   double lam = mat->E * mat->nu / ((1.0 + mat->nu) * (1.0 - 2.0 * mat->nu));
+  if (mat->model == OM_PLANE_STRESS_ELASTIC) {
+    double ls = 2.0 * lam * G / (lam + 2.0 * G);
+    double tr2 = de[0] + de[1];
+    sig[0] += ls * tr2 + 2.0 * G * de[0];
+    sig[1] += ls * tr2 + 2.0 * G * de[1];
+    sig[2] = 0.0;
+    sig[3] += 2.0 * G * de[3];
+    return;
+  }
   double tr = de[0] + de[1] + de[2];
   double st[6];
   for (int i = 0; i < 3; ++i) st[i] = sig[i] + lam * tr + 2.0 * G * de[i];
@@ -525,9 +550,27 @@ static void material_point_update(const om_mesh *M, const om_material *mat, doub
   (void)M;
 }
 
+/* Force of the face tractions on node ijk (R9): for every face f the node
+ * lies on, traction_f times the node's tributary length (area): h per
+ * tangent axis of the face, h / 2 where the node is at the face's edge. */
+static void face_force(const om_mesh *M, const int ijk[3], int faces, double ft[3]) {
+  ft[0] = ft[1] = ft[2] = 0.0;
+  for (int f = 0; f < 2 * M->dim; ++f) {
+    if (!(faces >> f & 1)) continue;
+    double trib = 1.0;
+    for (int k = 0; k < M->dim; ++k) {
+      if (k == f / 2) continue;
+      trib *= (ijk[k] == 0 || ijk[k] == M->n[k]) ? 0.5 * M->h : M->h;
+    }
+    for (int k = 0; k < 3; ++k) ft[k] += M->face_traction[f][k] * trib;
+  }
+}
+
 /* Nodal solve: v = P/m, a = f/m, v' = v + a dt for active nodes (R2); the
  * constraints follow. stage: 0 = velocity only (USF stage one),
- * 1 = USL (v from P), 2 = USF force stage (v already set). */
+ * 1 = USL (v from P), 2 = USF force stage (v already set).  The force
+ * includes the face tractions (R9), and the damping (R10) takes alpha v
+ * from the acceleration: a = (f + f_traction) / m - alpha v. */
 static void node_solve(const om_mesh *M, double *nm, double *nP, double *nf, double *nv,
                        double *na, double *nvn, int stage) {
   int64_t nx = nodes_along(M, 0), ny = nodes_along(M, 1), nz = nodes_along(M, 2);
@@ -544,9 +587,11 @@ static void node_solve(const om_mesh *M, double *nm, double *nP, double *nf, dou
           constrain_velocity(M, faces, v);
           continue;
         }
+        double ft[3];
+        face_force(M, ijk, faces, ft);
         for (int k = 0; k < 3; ++k) {
           if (stage == 1) v[k] = active ? nP[3 * i + k] / nm[i] : 0.0;
-          a[k] = active ? nf[3 * i + k] / nm[i] : 0.0;
+          a[k] = active ? (nf[3 * i + k] + ft[k]) / nm[i] - M->damping * v[k] : 0.0;
           vn[k] = active ? v[k] + a[k] * M->dt : 0.0;
         }
         if (!active) {

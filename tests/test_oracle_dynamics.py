@@ -305,3 +305,67 @@ def test_one_step_order_by_hand(dim):
     # the two orders give different stresses after one step
     d_sig = np.abs(res[oracle.USF]["sig"] - res[oracle.USL]["sig"]).max()
     assert d_sig > 1e-4 * np.abs(res[oracle.USL]["sig"]).max()
+
+
+# ---------------------------------------------------------------------------
+# Plane stress, face tractions and damping: the quasi-static plate with a
+# hole of BENCHMARK AND PERFORMANCE (Table 1).
+# ---------------------------------------------------------------------------
+def test_plane_stress_update_is_the_uniaxial_law():
+    # uniaxial stress sigma along x in plane stress: strains sigma/E and
+    # -nu sigma/E; the textbook plane-stress matrix E/(1 - nu^2) [[1, nu],
+    # [nu, 1]] maps them back to (sigma, 0), with sigma_zz = 0 and the shear
+    # 2 G eps_xy
+    E, nu = 2.0e7, 0.3
+    mat = oracle.Material(model=oracle.PLANE_STRESS_ELASTIC, E=E, nu=nu, rho=1000.0)
+    sig0 = np.array([10.0, -4.0, 0.0, 3.0, 0.0, 0.0])
+    de = np.array([1e-4, -nu * 1e-4, 0.0, 2e-5, 0.0, 0.0])
+    out, depsp = oracle.stress_update(mat, 0.0, sig0, de)
+    D = E / (1 - nu * nu)
+    expect = sig0 + np.array([D * (de[0] + nu * de[1]), D * (nu * de[0] + de[1]), 0.0,
+                              E / (1 + nu) * de[3], 0.0, 0.0])
+    assert np.allclose(out, expect, rtol=1e-13, atol=1e-9)
+    assert out[1] == pytest.approx(sig0[1], abs=1e-9) and out[2] == 0.0 and depsp == 0.0
+
+
+@pytest.mark.parametrize("scheme", [oracle.USF, oracle.USL])
+def test_face_traction_with_damping_settles_to_the_applied_stress(scheme):
+    # a plane-stress bar, roller on -x and -y, traction t on +x, damped to
+    # rest: the stress is uniform, sigma_xx = t, sigma_yy = 0, and the strain
+    # is the uniaxial plane-stress strain t / E (plane strain would give
+    # (1 - nu^2) t / E)
+    E, nu, rho, h, t = 1e6, 0.3, 1000.0, 0.1, 50.0
+    pos = W.gauss_fill(W.box_cells((0, 0), (12, 2)), h, (0.0, 0.0), 2)
+    c = math.sqrt(E / (rho * (1 - nu * nu)))
+    trac = [(0.0, 0.0, 0.0)] * 6
+    trac[1] = (t, 0.0, 0.0)
+    mesh = oracle.Mesh(dim=2, n=(12, 2, 1), h=h, face_bc=(oracle.BC_ROLLER, 0, oracle.BC_ROLLER, 0, 0, 0),
+                       dt=0.2 * h / c, scheme=scheme, face_traction=tuple(trac),
+                       damping=2.0 * math.pi * c / (2.0 * 1.2))
+    st = oracle.State.create(pos, np.zeros_like(pos), np.full(len(pos), h * h / 4), rho)
+    o = oracle.Oracle(mesh, oracle.Material(model=oracle.PLANE_STRESS_ELASTIC, E=E, nu=nu, rho=rho), st)
+    assert o.step(4000) == oracle.OK
+    assert np.allclose(st.sig[:, 0], t, rtol=2e-3)
+    assert np.abs(st.sig[:, 1]).max() < 2e-3 * t and not st.sig[:, 2].any()
+    assert np.allclose(st.eps[:, 0], t / E, rtol=2e-3)
+    assert o.conservation()["ke"] < 1e-12 * rho * 1.2 * 0.2 * c * c
+
+
+@pytest.mark.slow
+def test_plate_with_hole_stress_concentration():
+    """BENCHMARK AND PERFORMANCE, Table 1: the quarter strip damped to rest
+    under the end traction; the extreme particle stresses at the hole against
+    Howland's factors (3.14 for sigma_xx, -1.11 for sigma_yy; the paper's
+    USF MPM gave 3.13 and -1.08), and the far field carrying the traction."""
+    ref = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "plate_with_hole_table1.json")))
+    wl = W.plate_with_hole()
+    assert abs(wl.n - 40156) <= 5          # the paper's 40,156 material points
+    o = oracle.from_workload(wl)
+    assert o.step(4000) == oracle.OK
+    s0 = wl.meta["sigma0"]
+    sx, sy = o.state.sig[:, 0] / s0, o.state.sig[:, 1] / s0
+    x = o.state.x[:, 0]
+    assert sx.max() == pytest.approx(ref["howland"]["max_sxx"], rel=3e-2)
+    assert sy.min() == pytest.approx(ref["howland"]["max_syy"], rel=5e-2)
+    assert abs(sx.min()) < 0.25
+    assert np.mean(sx[x > 3.5]) == pytest.approx(1.0, abs=2e-3)
