@@ -66,7 +66,7 @@ typedef enum {
 enum { MPM_BC_FREE = 0, MPM_BC_ROLLER = 1, MPM_BC_FIXED = 2, MPM_BC_FRICTION = 3 };
 enum { MPM_USF = 0, MPM_USL = 1 };
 enum { MPM_FP64_PLAIN = 0, MPM_FP32_MIXED = 1 };
-enum { MPM_LINEAR_ELASTIC = 0, MPM_MOHR_COULOMB = 1 };
+enum { MPM_LINEAR_ELASTIC = 0, MPM_MOHR_COULOMB = 1, MPM_PLANE_STRESS_ELASTIC = 2 };
 
 /* Background mesh and step parameters (CODE OVERVIEW: Mesh, Node, Cell;
  * the explicit USF/USL algorithm).
@@ -104,7 +104,11 @@ typedef struct {
 
 /* Material of the particles (CODE OVERVIEW: Material).  Linear elastic uses
  * E, nu; Mohr-Coulomb adds friction angle phi, cohesion c and dilation
- * angle psi (perfect plasticity).  rho gives particle mass rho * volume. */
+ * angle psi (perfect plasticity).  MPM_PLANE_STRESS_ELASTIC (2D meshes only;
+ * BENCHMARK AND PERFORMANCE: the plate with a hole is a plane-stress strip)
+ * is linear elastic with stress zz = 0: in-plane stiffness with
+ * lambda* = 2 lambda G / (lambda + 2 G).  rho gives particle mass
+ * rho * volume. */
 typedef struct {
   int32_t model;
   double E, nu, rho;
@@ -243,6 +247,24 @@ mpm_status mpm_batch_step(mpm_batch b, int64_t nsteps);
 mpm_status mpm_batch_poll(mpm_batch b, int32_t nslots, int32_t *slot_status, int64_t *slot_steps);
 mpm_status mpm_batch_step_kernels(mpm_batch b, int32_t *kernels);
 mpm_status mpm_batch_destroy(mpm_batch b);
+
+/* Loads of a quasi-static run (BENCHMARK AND PERFORMANCE: a strip "subjected
+ * to uniform tension ... applied at the ends"; the paper gives no protocol
+ * for reaching the static state).
+ *   face_traction  18 doubles, the traction (force per unit length in 2D,
+ *                  per unit area in 3D; dim components used) on each face
+ *                  -x,+x,-y,+y,-z,+z, or NULL for none.  It acts on the
+ *                  nodes of that mesh face, so the loaded end of the body
+ *                  must lie on it: each active node gets the traction times
+ *                  its tributary length (area), h per tangent axis, h / 2 at
+ *                  the face's own edges.
+ *   damping        alpha >= 0 of a mass-proportional viscous damping of the
+ *                  nodes, a = (f + f_traction) / m - alpha v, which brings
+ *                  an explicit run to rest; 0 for none.
+ * Both act from the next step on, in both precisions and both schemes (the
+ * USF velocity stage is undamped).  Not for a mesh admitted to a batch.
+ * MPM_ERR_ARG for a negative or non-finite value. */
+mpm_status mpm_set_loads(mpm_handle h, const double *face_traction, double damping);
 
 /* Failure-detection test hook (the paper has no counterpart).  The FP32
  * tile scan of meshes with more than 4095 tiles runs one pass over chunks of

@@ -10,6 +10,8 @@
 // step) is replayed from a captured CUDA graph when the stream allows capture.
 #include <cuda_runtime.h>
 #include <math.h>
+
+#include <cmath>
 #include <stdint.h>
 #include <stdio.h>
 #include <string.h>
@@ -186,6 +188,8 @@ struct mpm_ctx {
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int32_t graph_kernels = -1;  // kernel nodes of the last captured step graph
   int32_t lb_withhold = -1, lb_spin = LB_SPIN_LIMIT;  // tile scan test hook (mpm_set_scan_fault)
+  int loads = 0;                                     // face tractions and damping (mpm_set_loads)
+  double damp = 0.0, trac[6][3] = {};
   bool timing = false;
   bool timed_step = false;
   cudaEvent_t ev[MPM_MAX_PHASES + 1] = {};
@@ -299,7 +303,9 @@ MatConst<T> mat_const(const mpm_material &m) {
   c.E = (T)m.E;
   c.nu = (T)m.nu;
   c.G = (T)(m.E / (2.0 * (1.0 + m.nu)));
-  c.lam = (T)(m.E * m.nu / ((1.0 + m.nu) * (1.0 - 2.0 * m.nu)));
+  const double G = m.E / (2.0 * (1.0 + m.nu)), lam = m.E * m.nu / ((1.0 + m.nu) * (1.0 - 2.0 * m.nu));
+  // plane stress: the in-plane stiffness with lambda* = 2 lambda G / (lambda + 2 G)
+  c.lam = (T)(m.model == MPM_PLANE_STRESS_ELASTIC ? 2.0 * lam * G / (lam + 2.0 * G) : lam);
   c.sphi = (T)sin(m.phi);
   c.cphi = (T)cos(m.phi);
   c.spsi = (T)sin(m.psi);
@@ -632,8 +638,10 @@ mpm_status mpm_add_particles(mpm_handle h, int64_t n, const double *pos, const d
   if (s0 != MPM_OK) return s0;
   if (h->batch) return fail(h, MPM_ERR_STATE, "add_particles: the mesh is admitted to a batch");
   if (n < 0 || !mat || (n > 0 && (!pos || !vel || !vol))) return fail(h, MPM_ERR_ARG, "add_particles: bad arguments");
-  if (mat->model != MPM_LINEAR_ELASTIC && mat->model != MPM_MOHR_COULOMB)
+  if (mat->model != MPM_LINEAR_ELASTIC && mat->model != MPM_MOHR_COULOMB && mat->model != MPM_PLANE_STRESS_ELASTIC)
     return fail(h, MPM_ERR_ARG, "unknown material model");
+  if (mat->model == MPM_PLANE_STRESS_ELASTIC && h->d.dim != 2)
+    return fail(h, MPM_ERR_ARG, "plane stress is a 2D material");
   if (!(mat->E > 0) || !(mat->nu > -1.0 && mat->nu < 0.5) || !(mat->rho > 0))
     return fail(h, MPM_ERR_ARG, "material constants out of range");
   if (h->has_mat && memcmp(&h->mat, mat, sizeof(mpm_material)) != 0)
@@ -856,6 +864,10 @@ mpm_status mpm_step(mpm_handle h, int64_t nsteps) {
       L.mu[f] = h->d.face_mu[f];
     }
     L.mat = mat_const<double>(h->mat);
+    L.loads = h->loads;
+    L.damp = h->damp;
+    for (int f = 0; f < 6; ++f)
+      for (int k = 0; k < 3; ++k) L.trac[f][k] = h->trac[f][k];
     L.status = h->d_status;
     for (int64_t s = 0; s < nsteps; ++s) CK(d64_step(L, h->st), "step enqueue");
   }
@@ -1049,6 +1061,34 @@ mpm_status mpm_phase_times(mpm_handle h, float *ms, int32_t *nphase) {
   CK(cudaEventSynchronize(h->ev[np]), "phase timing");
   for (int i = 0; i < np; ++i) CK(cudaEventElapsedTime(&ms[i], h->ev[i], h->ev[i + 1]), "phase timing");
   *nphase = np;
+  return MPM_OK;
+}
+
+mpm_status mpm_set_loads(mpm_handle h, const double *face_traction, double damping) {
+  mpm_status s0 = check_handle(h);
+  if (s0 != MPM_OK) return s0;
+  if (h->batch) return fail(h, MPM_ERR_STATE, "set_loads: the mesh is admitted to a batch");
+  if (!(damping >= 0.0) || !std::isfinite(damping)) return fail(h, MPM_ERR_ARG, "set_loads: damping must be >= 0");
+  double t[6][3] = {};
+  int any = damping > 0.0;
+  for (int f = 0; f < 6; ++f)
+    for (int k = 0; k < 3; ++k) {
+      t[f][k] = face_traction ? face_traction[3 * f + k] : 0.0;
+      if (!std::isfinite(t[f][k])) return fail(h, MPM_ERR_ARG, "set_loads: traction not finite");
+      if (f >= 2 * h->d.dim || k >= h->d.dim) t[f][k] = 0.0;
+      any |= t[f][k] != 0.0;
+    }
+  CK(cudaStreamSynchronize(h->st), "set_loads");
+  h->loads = any;
+  h->damp = damping;
+  memcpy(h->trac, t, sizeof(t));
+  Geo &g = h->geo;
+  g.loads = any;
+  g.damp = (float)damping;
+  for (int f = 0; f < 6; ++f)
+    for (int k = 0; k < 3; ++k) g.trac[f][k] = (float)t[f][k];
+  destroy_graphs(h->graph);  // the instance (and its loads) is captured in the step graph
+  h->grp_valid = false;
   return MPM_OK;
 }
 

@@ -25,8 +25,8 @@ enum { ST_LEFT_MESH = 1, ST_NONFINITE = 2, ST_TIMEOUT = 4 };
 // ---------------------------------------------------------------------------
 template <typename T>
 struct MatConst {
-  int model;          // 0 linear elastic, 1 Mohr-Coulomb
-  T E, nu, G, lam;    // elastic constants
+  int model;          // 0 linear elastic, 1 Mohr-Coulomb, 2 plane-stress linear elastic (2D)
+  T E, nu, G, lam;    // elastic constants (plane stress: lam = 2 lambda G / (lambda + 2 G))
   T sphi, cphi, spsi; // sin(phi), cos(phi), sin(psi)
   T c;                // cohesion (default when no per-particle value)
 };
@@ -184,6 +184,32 @@ __device__ __forceinline__ double xsqrt(double a) { return sqrt(a); }
 template <typename T>
 __device__ __forceinline__ T xdot3(T a, T b, T c, T d, T e, T f) {
   return xf(e, f, xf(c, d, xm(a, b)));
+}
+
+// ---------------------------------------------------------------------------
+// Loads of a quasi-static run (the plate with a hole of BENCHMARK AND
+// PERFORMANCE: uniform tension at the ends of a plane-stress strip).  A
+// uniform traction on an end of the body acts as forces on the nodes of the
+// mesh face that coincides with it: for every face f the node lies on,
+// traction_f times the node's tributary length (area in 3D), h per tangent
+// axis and h / 2 at the face's own edges.  The explicit run is brought to
+// rest by mass-proportional viscous damping, a = f / m - alpha v.
+// ---------------------------------------------------------------------------
+template <int D, typename T>
+__device__ __forceinline__ void face_force(int faces, const int I[3], const int nc[3], T h, const T (*trac)[3],
+                                           T ft[D]) {
+#pragma unroll
+  for (int k = 0; k < D; ++k) ft[k] = T(0);
+#pragma unroll
+  for (int f = 0; f < 2 * D; ++f) {
+    if (!((faces >> f) & 1)) continue;
+    T trib = T(1);
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+      if (k != f / 2) trib *= (I[k] == 0 || I[k] == nc[k]) ? T(0.5) * h : h;
+#pragma unroll
+    for (int k = 0; k < D; ++k) ft[k] += trac[f][k] * trib;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -584,6 +610,7 @@ __device__ __forceinline__ bool material_update_inline(const MatConst<float> &m,
   elastic_trial<float>(m, sig, de, st);
 #pragma unroll
   for (int i = 0; i < 6; ++i) sig[i] = st[i];
+  if (m.model == 2) sig[2] = 0.f;  // plane stress
   if (m.model != 1 || bounded_elastic(m, c, st) || clearly_elastic(m, c, st)) return false;
   if (near_apex(st, m, c)) return true;
   float d;
@@ -609,6 +636,7 @@ __device__ __forceinline__ void material_update(const MatConst<double> &m, doubl
   if (m.model != 1) {
 #pragma unroll
     for (int i = 0; i < 6; ++i) sig[i] = st[i];
+    if (m.model == 2) sig[2] = 0.0;  // plane stress
     return;
   }
   double d;

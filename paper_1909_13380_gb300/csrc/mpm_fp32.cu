@@ -890,9 +890,11 @@ __global__ void __launch_bounds__(NODE_T, ONE ? MPM_NODE_MINB : 8) node_tile(con
 #pragma unroll
         for (int k = 0; k < D; ++k) v[k] = c1[1 + k] * inv_m;
         if (NMODE == NODE_USL) {
+          float ft[D];
+          if (g.loads) face_force<D, float>(faces, Ig, g.nc, g.h, g.trac, ft);
 #pragma unroll
           for (int k = 0; k < D; ++k) {
-            a[k] = c1[1 + D + k] * inv_m + g.g[k];
+            a[k] = g.loads ? (c1[1 + D + k] + ft[k]) * inv_m + g.g[k] - g.damp * v[k] : c1[1 + D + k] * inv_m + g.g[k];
             vn[k] = v[k] + a[k] * g.dt;
           }
           bc_full<D, float>(faces, g.bc, g.mu, g.dt, v, a, vn);
@@ -902,9 +904,11 @@ __global__ void __launch_bounds__(NODE_T, ONE ? MPM_NODE_MINB : 8) node_tile(con
           float f[D];
           gather_node<D, D>(g, I.s.slots2, D, Ig, lo, hi, act, f);
           bc_velocity<D, float>(faces, g.bc, v);
+          float ft[D];
+          if (g.loads) face_force<D, float>(faces, Ig, g.nc, g.h, g.trac, ft);
 #pragma unroll
           for (int k = 0; k < D; ++k) {
-            a[k] = f[k] * inv_m + g.g[k];
+            a[k] = g.loads ? (f[k] + ft[k]) * inv_m + g.g[k] - g.damp * v[k] : f[k] * inv_m + g.g[k];
             vn[k] = v[k] + a[k] * g.dt;
           }
           bc_full<D, float>(faces, g.bc, g.mu, g.dt, v, a, vn);

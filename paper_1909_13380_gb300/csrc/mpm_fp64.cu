@@ -128,9 +128,11 @@ __global__ void node64(D64Launch L) {
       continue;
     }
     if (active) {
+      double ft[D];
+      if (L.loads) face_force<D, double>(faces, I, L.nc, L.h, L.trac, ft);
 #pragma unroll
       for (int k = 0; k < D; ++k) {
-        a[k] = L.N.f[k][i] / m;
+        a[k] = L.loads ? (L.N.f[k][i] + ft[k]) / m - L.damp * v[k] : L.N.f[k][i] / m;
         vn[k] = v[k] + a[k] * L.dt;
       }
       bc_full<D, double>(faces, L.bc, L.mu, L.dt, v, a, vn);

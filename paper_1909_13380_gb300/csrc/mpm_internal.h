@@ -97,6 +97,9 @@ struct Geo {
   float g[3];
   int bc[6];
   float mu[6];
+  int loads;           // face tractions or damping present (mpm_set_loads)
+  float damp;          // alpha of a = f / m - alpha v
+  float trac[6][3];    // traction per face
 };
 
 // Counters of a step (int32, in StepBufs::ctr).
@@ -333,6 +336,8 @@ struct D64Launch {
   int bc[6];
   double mu[6];
   MatConst<double> mat;
+  int loads;
+  double damp, trac[6][3];
   D64State P;
   D64Nodes N;
   int64_t nnodes;

@@ -26,7 +26,7 @@ STATUS_NAMES = {0: "MPM_OK", -1: "MPM_ERR_ARG", -2: "MPM_ERR_OOM", -3: "MPM_ERR_
 MPM_BC_FREE, MPM_BC_ROLLER, MPM_BC_FIXED, MPM_BC_FRICTION = 0, 1, 2, 3
 MPM_USF, MPM_USL = 0, 1
 MPM_FP64_PLAIN, MPM_FP32_MIXED = 0, 1
-MPM_LINEAR_ELASTIC, MPM_MOHR_COULOMB = 0, 1
+MPM_LINEAR_ELASTIC, MPM_MOHR_COULOMB, MPM_PLANE_STRESS_ELASTIC = 0, 1, 2
 
 
 class MPMError(RuntimeError):
@@ -109,6 +109,7 @@ def load():
             "mpm_batch_destroy": [vp],
             "mpm_step_kernels": [vp, i32p],
             "mpm_set_scan_fault": [vp, C.c_int32, C.c_int32],
+            "mpm_set_loads": [vp, dp, C.c_double],
             "mpm_material_update": [C.POINTER(mpm_material), C.c_int32, C.c_int64, dp, dp, dp, dp, dp, vp],
             "mpm_set_phase_timing": [vp, C.c_int32],
             "mpm_phase_times": [vp, C.POINTER(C.c_float), i32p],
@@ -334,6 +335,12 @@ def mpm_batch_step_kernels(b) -> int:
     return k.value
 
 
+def mpm_set_loads(h, face_traction=None, damping: float = 0.0):
+    """face_traction: 6 x 3 tractions (faces -x,+x,-y,+y,-z,+z) or None."""
+    t = None if face_traction is None else np.ascontiguousarray(face_traction, np.float64).reshape(18)
+    _check(h, load().mpm_set_loads(h, _dp(t), float(damping)), "mpm_set_loads")
+
+
 def mpm_set_scan_fault(h, withhold_chunk: int, spin_limit: int = 1 << 20):
     _check(h, load().mpm_set_scan_fault(h, int(withhold_chunk), int(spin_limit)), "mpm_set_scan_fault")
 
@@ -401,6 +408,10 @@ class Simulation:
         try:
             if wl.n:
                 mpm_add_particles(self.h, wl.pos, wl.vel, wl.vol, self.mat, wl.coh, stress0)
+            trac = getattr(wl, "face_traction", None)
+            damp = float(getattr(wl, "damping", 0.0))
+            if damp > 0.0 or (trac is not None and np.any(np.asarray(trac) != 0.0)):
+                mpm_set_loads(self.h, trac, damp)
         except Exception:
             mpm_destroy(self.h)
             raise

@@ -21,7 +21,7 @@ import numpy as np
 FREE, ROLLER, FIXED, FRICTION = 0, 1, 2, 3
 USF, USL = 0, 1
 FP64_PLAIN, FP32_MIXED = 0, 1
-LINEAR_ELASTIC, MOHR_COULOMB = 0, 1
+LINEAR_ELASTIC, MOHR_COULOMB, PLANE_STRESS_ELASTIC = 0, 1, 2
 SEED_BASE = 1909133800
 
 
@@ -45,6 +45,8 @@ class Workload:
     coh: np.ndarray | None = None   # (n,) float64 per-particle cohesion, or None
     steps: int = 1
     meta: dict = field(default_factory=dict)
+    face_traction: tuple = ((0.0, 0.0, 0.0),) * 6   # per face: force per unit length (2D) or area (3D)
+    damping: float = 0.0                            # alpha of the nodal damping a = f / m - alpha v
 
     @property
     def n(self) -> int:
@@ -311,3 +313,40 @@ def random_particles(mesh_cells, h, n, seed, dim=3, margin=1, vel_scale=0.1, sig
         sig[:, :4] = sig_scale * rng.standard_normal((n, 4))
     vol = (h ** dim / 4.0) * (0.5 + rng.random(n))
     return pos, vel, sig, vol
+
+
+def plate_with_hole(h=0.0625, per_axis=4, E=1e6, nu=0.3, rho=1000.0, sigma0=100.0, radius=0.5,
+                    precision=FP64_PLAIN, scheme=USF, dt=None, damping=None, steps=4000) -> Workload:
+    """The validation problem of the paper's benchmark: a plane-stress strip
+    8 m long and 5 m wide with a centred hole of radius 0.5 m under uniform
+    tension sigma0 at its ends, modelled by its quarter x in [0, 4],
+    y in [0, 2.5] (the hole's centre at the origin): rollers on x = 0 and
+    y = 0 (symmetry), the traction (sigma0, 0) on the +x face, cells of
+    0.0625 m filled with per_axis^2 = 16 particles each at the centres of a
+    regular sub-grid, the particles inside the hole left out (40,156
+    particles).  The elastic constants do not change the static stress
+    field; dt is a fifth of the time a plane-stress wave takes to cross a
+    cell, and the viscous damping alpha (a = f / m - alpha v) twice the
+    lowest frequency of a fixed-free bar of the strip's half length."""
+    nx, ny = int(round(4.0 / h)), int(round(2.5 / h))
+    cells = box_cells((0, 0), (nx, ny)).astype(np.float64)
+    sub = (np.arange(per_axis) + 0.5) / per_axis
+    sx, sy = np.meshgrid(sub, sub, indexing="xy")
+    offs = np.stack([sx.ravel(), sy.ravel()], axis=1)
+    pos = ((cells[:, None, :] + offs[None, :, :]) * h).reshape(-1, 2)
+    pos = pos[pos[:, 0] ** 2 + pos[:, 1] ** 2 >= radius ** 2]
+    vol = np.full(pos.shape[0], (h / per_axis) ** 2)
+    c = math.sqrt(E / (rho * (1.0 - nu * nu)))
+    if dt is None:
+        dt = 0.2 * h / c
+    if damping is None:
+        damping = 2.0 * math.pi * c / (2.0 * 4.0)
+    trac = [(0.0, 0.0, 0.0)] * 6
+    trac[1] = (sigma0, 0.0, 0.0)
+    return Workload(
+        name=f"plate_with_hole_quarter_{nx}x{ny}", dim=2, ncells=(nx, ny, 1), h=h, origin=(0.0, 0.0, 0.0),
+        face_bc=(ROLLER, FREE, ROLLER, FREE, FREE, FREE), face_mu=(0.0,) * 6, gravity=(0.0, 0.0, 0.0), dt=dt,
+        scheme=scheme, precision=precision,
+        material=dict(model=PLANE_STRESS_ELASTIC, E=E, nu=nu, rho=rho, phi=0.0, c=0.0, psi=0.0),
+        pos=pos, vel=np.zeros_like(pos), vol=vol, steps=steps, face_traction=tuple(trac), damping=damping,
+        meta=dict(sigma0=sigma0, radius=radius))

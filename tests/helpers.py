@@ -161,6 +161,8 @@ def named_workload(name, precision=W.FP32_MIXED, scheme=W.USL):
         wl = W.slope3d(ncells=(200, 50, 50), h=0.2, crest=8.0, plateau=8.5, precision=precision)
         wl.scheme = scheme
         return wl
+    if name == "plate_with_hole":
+        return W.plate_with_hole(precision=precision, scheme=scheme)
     raise ValueError(name)
 
 

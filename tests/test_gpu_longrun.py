@@ -37,8 +37,9 @@ from paper_1909_13380_gb300 import mpm  # noqa: E402
 COLUMN_CHECKS = (2000, 4000, 5000, 8000, 12000)
 FP32_LAST = 5000          # the column workload's full run (5,000 steps)
 SLOPE_CHECKS = (100, 200)
+PLATE_CHECKS = (1000, 4000)
 JOBS = {("small_column", W.USL): COLUMN_CHECKS, ("small_column", W.USF): COLUMN_CHECKS,
-        ("slope_1_64", W.USL): SLOPE_CHECKS}
+        ("slope_1_64", W.USL): SLOPE_CHECKS, ("plate_with_hole", W.USF): PLATE_CHECKS}
 
 
 @pytest.fixture(scope="module")
@@ -124,3 +125,38 @@ def test_slope_1_64_two_hundred_steps(oracle_runs):
         assert H.disp_excess(g, r, start, wl.h, k, 3) <= 1.0, k
         assert H.cell_mismatch_in_band(g, r, wl.h, 1e-4)[1] == 0, k
     assert err["disp"] <= H.TOL_RUN_FP32, err
+
+
+def test_plate_with_hole_to_rest(oracle_runs):
+    """The quarter plate with a hole (40,153 particles, plane stress, end
+    traction, viscous damping, USF as in the paper): FP32 and FP64 against the
+    oracle half-way to rest and at rest, and Table 1's stress concentration
+    from the GPU's own stresses."""
+    import json
+    import os
+    table = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "plate_with_hole_table1.json")))
+    wl = H.named_workload("plate_with_hole", scheme=W.USF)
+    ref = oracle_runs(("plate_with_hole", W.USF))
+    start = ref[0]
+    s0 = wl.meta["sigma0"]
+    g64 = gpu_checkpoints(wl, W.FP64_PLAIN, W.USF, PLATE_CHECKS)
+    g32 = gpu_checkpoints(wl, W.FP32_MIXED, W.USF, PLATE_CHECKS)
+    for k in PLATE_CHECKS:
+        r = ref[k]
+        err = H.compare(g64[k], r, start, 2)
+        assert max(err.values()) <= H.TOL_RUN_FP64, (k, err)
+        g = g32[k]
+        assert g["status"] == mpm.MPM_OK
+        err = H.compare(g, r, start, 2)
+        # at rest the velocity is the residue of the damped motion (1e-6 m/s):
+        # the fields that carry the result are the stress and the displacement
+        keys = H.RUN_KEYS if k < PLATE_CHECKS[-1] else ("disp", "stress", "dvol")
+        assert H.worst(err, keys) <= H.TOL_RUN_FP32, (k, err)
+        pp = H.per_particle(g, r, start)
+        assert pp["stress"] <= 1e-3, (k, pp)
+        assert H.disp_excess(g, r, start, wl.h, k, 2) <= 1.0, k
+    for g in (g64[PLATE_CHECKS[-1]], g32[PLATE_CHECKS[-1]]):
+        sx = g["stress"][:, 0] / s0
+        assert sx.max() == pytest.approx(table["howland"]["max_sxx"], rel=3e-2)
+        assert g["stress"][:, 1].min() / s0 == pytest.approx(table["howland"]["max_syy"], rel=5e-2)
+        assert np.mean(sx[g["pos"][:, 0] > 3.5]) == pytest.approx(1.0, abs=2e-3)
