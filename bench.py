@@ -60,7 +60,6 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 # ncu DRAM traffic summaries by workload: (file, particles it was taken on)
 TRAFFIC_FILES = {
-    "column3d": (os.path.join(ROOT, "profiles", "dram_traffic_column3d_512k.txt"), 512000),
     "slope_1_64": (os.path.join(ROOT, "profiles", "dram_traffic_slope3d_1m.txt"), 1000000),
     "slope": (os.path.join(ROOT, "profiles", "dram_traffic_slope3d_1m.txt"), 1000000),
 }
