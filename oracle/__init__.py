@@ -105,6 +105,15 @@ def lib():
             L.oracle_step.restype = C.c_int
             L.oracle_step.argtypes = [C.POINTER(_Mesh), C.POINTER(_Material), C.c_int64,
                                       dp, dp, dp, dp, dp, dp, dp, dp, ip, dp, C.c_int64]
+            L.oracle_iso_natural.restype = C.c_int
+            L.oracle_iso_natural.argtypes = [C.POINTER(_Mesh), dp, ip, dp, dp]
+            L.oracle_iso_locate.restype = C.c_int
+            L.oracle_iso_locate.argtypes = [C.POINTER(_Mesh), dp, dp, ip, dp]
+            L.oracle_iso_basis.restype = None
+            L.oracle_iso_basis.argtypes = [C.POINTER(_Mesh), dp, ip, dp, dp, dp]
+            L.oracle_step_mapped.restype = C.c_int
+            L.oracle_step_mapped.argtypes = [C.POINTER(_Mesh), dp, C.POINTER(_Material), C.c_int64,
+                                             dp, dp, dp, dp, dp, dp, dp, dp, ip, ip, dp, C.c_int64]
             L.oracle_conservation.restype = None
             L.oracle_conservation.argtypes = [C.c_int64, dp, dp, dp, dp, dp, ip, dp]
             _lib = L
@@ -217,10 +226,27 @@ class State:
 
 @dataclass
 class Oracle:
+    """The explicit step on a Cartesian mesh, or on a mapped one when X (node
+    coordinates, one row of 3 per node, x fastest) is given: then `cell`
+    holds each particle's (ix, iy, iz), located at construction by the walk."""
     mesh: Mesh
     material: Material
     state: State
     _work: np.ndarray = field(default=None, repr=False)
+    X: np.ndarray | None = None
+    cell: np.ndarray | None = None
+
+    def __post_init__(self):
+        if self.X is not None:
+            self.X = _nodes3(self.mesh, self.X)
+            if self.cell is None:
+                self.cell = np.zeros((self.state.n, 3), np.int32)
+                c = np.zeros(3, np.int32)
+                for p in range(self.state.n):    # walk on from the previous particle's cell
+                    st, c, _ = locate_mapped(self.mesh, self.X, self.state.x[p], c)
+                    if st != OK:
+                        raise ValueError(f"particle {p} lies outside the mapped mesh")
+                    self.cell[p] = c
 
     def step(self, nsteps: int = 1) -> int:
         L = lib()
@@ -231,6 +257,10 @@ class Oracle:
         coh = _dp(s.coh) if s.coh is not None else C.cast(None, C.POINTER(C.c_double))
         if s.n == 0:
             return OK
+        if self.X is not None:
+            return int(L.oracle_step_mapped(C.byref(ms), _dp(self.X), C.byref(mt), s.n, _dp(s.x), _dp(s.v),
+                                            _dp(s.sig), _dp(s.eps), _dp(s.m), _dp(s.vol), _dp(s.epsp), coh,
+                                            _ip(s.alive), _ip(self.cell), _dp(self._work), int(nsteps)))
         return int(L.oracle_step(C.byref(ms), C.byref(mt), s.n, _dp(s.x), _dp(s.v), _dp(s.sig),
                                  _dp(s.eps), _dp(s.m), _dp(s.vol), _dp(s.epsp), coh, _ip(s.alive),
                                  _dp(self._work), int(nsteps)))
@@ -257,7 +287,10 @@ class Oracle:
 
     def cells(self) -> np.ndarray:
         """Integer cell (ix, iy, iz) of every particle by the oracle's locate
-        rule; -1 rows for particles outside the mesh."""
+        rule (on a mapped mesh: the cell the walk keeps); -1 rows for
+        particles outside the mesh."""
+        if self.X is not None:
+            return np.where(self.state.alive[:, None] == 1, self.cell, -1).astype(np.int32)
         return locate(self.mesh, self.state.x)
 
 
@@ -285,6 +318,49 @@ def locate_one(mesh: Mesh, x):
     xi = np.zeros(3)
     st = L.oracle_locate(C.byref(mesh.c_struct()), _dp(x3), _ip(c), _dp(xi))
     return st, c.copy(), xi.copy()
+
+
+def _nodes3(mesh: Mesh, X):
+    """Node coordinates as 3 per node (X may hold dim per node)."""
+    X = np.asarray(X, np.float64).reshape(mesh.num_nodes, -1)
+    if X.shape[1] == 3:
+        return np.ascontiguousarray(X)
+    out = np.zeros((mesh.num_nodes, 3))
+    out[:, : X.shape[1]] = X
+    return out
+
+
+def natural_mapped(mesh: Mesh, X, cell, x):
+    """(iterations or -1, xi (3,)) of x in a cell of a mapped mesh."""
+    xi = np.zeros(3)
+    x3 = np.zeros(3)
+    x3[: len(x)] = x
+    c = np.ascontiguousarray(cell, np.int32)
+    it = lib().oracle_iso_natural(C.byref(mesh.c_struct()), _dp(_nodes3(mesh, X)), _ip(c),
+                                  _dp(x3), _dp(xi))
+    return int(it), xi
+
+
+def locate_mapped(mesh: Mesh, X, x, start=(0, 0, 0)):
+    """(status, cell (3,), xi (3,)) by the neighbourhood walk from `start`."""
+    xi = np.zeros(3)
+    x3 = np.zeros(3)
+    x3[: len(x)] = x
+    c = np.array(list(start) + [0] * (3 - len(start)), np.int32)
+    st = lib().oracle_iso_locate(C.byref(mesh.c_struct()), _dp(_nodes3(mesh, X)), _dp(x3),
+                                 _ip(c), _dp(xi))
+    return int(st), c.copy(), xi
+
+
+def basis_mapped(mesh: Mesh, X, cell, xi):
+    """N (8,) and dN/dx (8, 3) at natural coordinates xi of a mapped cell."""
+    N = np.zeros(8)
+    G = np.zeros(24)
+    x3 = np.zeros(3)
+    x3[: len(xi)] = xi
+    lib().oracle_iso_basis(C.byref(mesh.c_struct()), _dp(_nodes3(mesh, X)),
+                           _ip(np.ascontiguousarray(cell, np.int32)), _dp(x3), _dp(N), _dp(G))
+    return N, G.reshape(8, 3)
 
 
 def shape(dim: int, xi):
@@ -337,4 +413,4 @@ def from_workload(wl, scheme=None) -> Oracle:
                 g=wl.gravity, dt=wl.dt, scheme=wl.scheme if scheme is None else scheme,
                 face_traction=wl.face_traction, damping=wl.damping)
     st = State.create(wl.pos, wl.vel, wl.vol, wl.material["rho"], coh=wl.coh)
-    return Oracle(mesh, Material(**wl.material), st)
+    return Oracle(mesh, Material(**wl.material), st, X=getattr(wl, "node_xyz", None))

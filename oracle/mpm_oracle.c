@@ -55,6 +55,17 @@
  *   R10 a quasi-static protocol (the plate's static stress field; the paper
  *       gives none): mass-proportional viscous damping of the nodal motion,
  *       a = f / m - alpha v, so the explicit run settles to equilibrium.
+ *   R11 mapped (isoparametric) mesh (ISOPARAMETRIC MESH): the logical grid
+ *       of cells is the Cartesian one with moved nodes; the natural
+ *       coordinates of a point are the root of x(xi) = x, found by Newton-
+ *       Raphson from the affine guess; a particle keeps the cell the
+ *       neighbourhood walk last found for it; a point on a face shared by
+ *       two cells belongs to the higher one (xi = 1 is outside, as R6).
+ *   R12 on a mapped mesh the face conditions act along the global axes
+ *       (roller: the component along the logical face's axis), which is the
+ *       paper's nodal condition wherever the face is a plane normal to that
+ *       axis, and fixed faces hold for any shape; face tractions (R9) are
+ *       not defined there.
  *
  * Layout: every particle vector is stored with 3 components and every
  * stress/strain with 6 Voigt components (xx, yy, zz, xy, yz, xz; tensor
@@ -184,22 +195,216 @@ static int64_t cell_node(const om_mesh *M, const int32_t cell[3], int a) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* Isoparametric (mapped) cells (ISOPARAMETRIC MESH).  The logical grid of  */
+/* cells is the Cartesian one, but node i sits at X[3 i .. 3 i + 2], so a   */
+/* cell is the image of [-1, 1]^d under x(xi) = sum_a N_a(xi) X_a.  A point */
+/* is placed in a cell by inverting that map with Newton-Raphson from the   */
+/* affine guess xi0 = J(0)^-1 (x - x(0)), and particles are located by a    */
+/* neighbourhood walk from their current cell.                              */
+/* ------------------------------------------------------------------------ */
+
+/* Coordinates of the 2^d nodes of a cell (node a: bit k = upper along k). */
+static void iso_cell_nodes(const om_mesh *M, const double *X, const int32_t cell[3], double xa[8][3]) {
+  int nn = 1 << M->dim;
+  for (int a = 0; a < nn; ++a) {
+    int64_t i = cell_node(M, cell, a);
+    for (int k = 0; k < 3; ++k) xa[a][k] = X[3 * i + k];
+  }
+}
+
+/* x(xi) and the Jacobian J[j][k] = dx_j / dxi_k of the cell's map. */
+static void iso_map(int dim, const double xa[8][3], const double xi[3], double x[3], double J[3][3]) {
+  double N[8], dN[24];
+  oracle_shape(dim, xi, N, dN);
+  for (int j = 0; j < 3; ++j) {
+    x[j] = 0.0;
+    for (int k = 0; k < 3; ++k) J[j][k] = (j == k && j >= dim) ? 1.0 : 0.0;
+  }
+  for (int a = 0; a < (1 << dim); ++a)
+    for (int j = 0; j < dim; ++j) {
+      x[j] += N[a] * xa[a][j];
+      for (int k = 0; k < dim; ++k) J[j][k] += xa[a][j] * dN[3 * a + k];
+    }
+}
+
+/* Inverse of the leading dim x dim block of J (cofactors); 0 if singular. */
+static int iso_inverse(int dim, const double J[3][3], double Ji[3][3]) {
+  for (int j = 0; j < 3; ++j)
+    for (int k = 0; k < 3; ++k) Ji[j][k] = (j == k) ? 1.0 : 0.0;
+  if (dim == 2) {
+    double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    if (!(det != 0.0) || !isfinite(det)) return 0;
+    Ji[0][0] = J[1][1] / det;
+    Ji[0][1] = -J[0][1] / det;
+    Ji[1][0] = -J[1][0] / det;
+    Ji[1][1] = J[0][0] / det;
+    return 1;
+  }
+  double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+  double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+  double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+  double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+  if (!(det != 0.0) || !isfinite(det)) return 0;
+  Ji[0][0] = c00 / det;
+  Ji[1][0] = c01 / det;
+  Ji[2][0] = c02 / det;
+  Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+  Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+  Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+  Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+  Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+  Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+  return 1;
+}
+
+/* The affine guess of x's natural coordinates in a cell: the map
+ * linearised at the cell centre, xi0 = J(0)^-1 (x - x(0)).  0 if J(0) is
+ * singular. */
+static int iso_affine(const om_mesh *M, const double xa[8][3], const double x[3], double xi[3]) {
+  double x0[3], J[3][3], Ji[3][3];
+  xi[0] = xi[1] = xi[2] = 0.0;
+  iso_map(M->dim, xa, xi, x0, J);
+  if (!iso_inverse(M->dim, J, Ji)) return 0;
+  for (int j = 0; j < M->dim; ++j)
+    for (int k = 0; k < M->dim; ++k) xi[j] += Ji[j][k] * (x[k] - x0[k]);
+  return 1;
+}
+
+/* Natural coordinates of x in a cell: Newton-Raphson on x(xi) = x from the
+ * affine guess.  Returns the iterations taken, or -1 if the map is singular
+ * or Newton does not converge (50 iterations), with xi then the affine
+ * guess.  Far outside the cell the extrapolated map may have other roots:
+ * only a root inside (or near) the cell means anything. */
+int oracle_iso_natural(const om_mesh *M, const double *X, const int32_t cell[3], const double x[3],
+                       double xi[3]) {
+  double xa[8][3], J[3][3], Ji[3][3];
+  iso_cell_nodes(M, X, cell, xa);
+  if (!iso_affine(M, xa, x, xi)) return -1;
+  double guess[3] = {xi[0], xi[1], xi[2]};
+  int done = 0;
+  for (int it = 1; it <= 50; ++it) {
+    double xm[3], r[3], step = 0.0;
+    iso_map(M->dim, xa, xi, xm, J);
+    if (!iso_inverse(M->dim, J, Ji)) break;
+    for (int k = 0; k < M->dim; ++k) r[k] = xm[k] - x[k];
+    for (int j = 0; j < M->dim; ++j) {
+      double d = 0.0;
+      for (int k = 0; k < M->dim; ++k) d += Ji[j][k] * r[k];
+      xi[j] -= d;
+      if (fabs(d) > step) step = fabs(d);
+    }
+    if (!isfinite(step)) break;
+    /* converged to rounding: the residual's rounding, divided by J, keeps
+     * the last steps near 1e-15; one more step after 1e-12 */
+    if (step < 1e-12) {
+      if (done) return it;
+      done = 1;
+    }
+  }
+  for (int j = 0; j < 3; ++j) xi[j] = guess[j];
+  return -1;
+}
+
+/* Locate x by a neighbourhood walk from `cell` (updated).  In the current
+ * cell take the affine guess of xi; while it lies well outside the cell
+ * (beyond [-2, 2] on some axis) it sets the direction, otherwise Newton's
+ * root does.  If some xi_k lies outside [-1, 1), step to the neighbour along
+ * the axis of the largest excess (the next largest when that neighbour is
+ * beyond the grid) and repeat.  A point on a face shared by two cells
+ * belongs to the higher one (xi = 1 is outside); a point that needs a step
+ * beyond the grid on every axis it lies outside of has left the mesh. */
+int oracle_iso_locate(const om_mesh *M, const double *X, const double x[3], int32_t cell[3], double xi[3]) {
+  int limit = 2 * (M->n[0] + M->n[1] + M->n[2]) + 8;
+  for (int s = 0; s < limit; ++s) {
+    double xa[8][3];
+    iso_cell_nodes(M, X, cell, xa);
+    if (!iso_affine(M, xa, x, xi)) return OM_LEFT_MESH;
+    int far = 0, conv = 0;
+    for (int k = 0; k < M->dim; ++k) far |= fabs(xi[k]) > 2.0;
+    if (!far) conv = oracle_iso_natural(M, X, cell, x, xi) >= 0;
+    double excess[3] = {0.0, 0.0, 0.0};
+    int dir[3] = {0, 0, 0}, any = 0;
+    for (int k = 0; k < M->dim; ++k) {
+      if (xi[k] < -1.0) {
+        excess[k] = -1.0 - xi[k];
+        dir[k] = -1;
+      } else if (xi[k] >= 1.0) {
+        excess[k] = xi[k] - 1.0;
+        dir[k] = 1;
+      }
+      any |= dir[k] != 0;
+    }
+    if (!any) return conv ? OM_OK : OM_LEFT_MESH;
+    int moved = 0;
+    for (int tries = 0; tries < M->dim && !moved; ++tries) {
+      int best = -1;
+      for (int k = 0; k < M->dim; ++k)
+        if (dir[k] != 0 && (best < 0 || excess[k] > excess[best])) best = k;
+      if (best < 0) break;
+      int c = cell[best] + dir[best];
+      if (c >= 0 && c < M->n[best]) {
+        cell[best] = c;
+        moved = 1;
+      } else {
+        dir[best] = 0;
+      }
+    }
+    if (!moved) return OM_LEFT_MESH;
+  }
+  return OM_LEFT_MESH;
+}
+
+/* Shape values and physical gradients of a point in a mapped cell:
+ * dN_a/dx_j = sum_k dN_a/dxi_k dxi_k/dx_j = sum_k dN_a/dxi_k Ji[k][j]. */
+void oracle_iso_basis(const om_mesh *M, const double *X, const int32_t cell[3], const double xi[3],
+                      double N[8], double G[24]) {
+  double xa[8][3], xm[3], J[3][3], Ji[3][3], dN[24];
+  iso_cell_nodes(M, X, cell, xa);
+  iso_map(M->dim, xa, xi, xm, J);
+  iso_inverse(M->dim, J, Ji);
+  oracle_shape(M->dim, xi, N, dN);
+  for (int a = 0; a < 8; ++a)
+    for (int j = 0; j < 3; ++j) {
+      double g = 0.0;
+      if (a < (1 << M->dim) && j < M->dim)
+        for (int k = 0; k < M->dim; ++k) g += dN[3 * a + k] * Ji[k][j];
+      G[3 * a + j] = g;
+    }
+}
+
+/* The basis of particle p.  Cartesian mesh (X == NULL): its cell by the
+ * floor rule, G = dN/dxi (the caller multiplies by 2/h).  Mapped mesh: the
+ * cell it is stored in (pcell), xi by Newton-Raphson, G = dN/dx. */
+static int particle_basis(const om_mesh *M, const double *X, const int32_t *pcell, int64_t p, const double *x,
+                          int32_t cell[3], double N[8], double G[24]) {
+  double xi[3];
+  if (!X) {
+    if (oracle_locate(M, x, cell, xi) != OM_OK) return OM_LEFT_MESH;
+    oracle_shape(M->dim, xi, N, G);
+    return OM_OK;
+  }
+  for (int k = 0; k < 3; ++k) cell[k] = pcell[3 * p + k];
+  if (oracle_iso_natural(M, X, cell, x, xi) < 0) return OM_LEFT_MESH;
+  oracle_iso_basis(M, X, cell, xi, N, G);
+  return OM_OK;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Particle -> grid (INTRODUCTION: "transferred from the material points to */
 /* the nodes using mapping functions"; DATA STRUCTURES: nodal aggregation)  */
 /*   m_i = sum_p N_ip m_p                                                   */
 /*   P_i = sum_p N_ip m_p v_p                                               */
 /*   f_i = sum_p [ -V_p sigma_p . grad N_ip + N_ip m_p g ]                  */
 /* ------------------------------------------------------------------------ */
-static void p2g(const om_mesh *M, int64_t np, const double *x, const double *v,
-                const double *sig, const double *m, const double *vol, const int32_t *alive,
+static void p2g(const om_mesh *M, const double *X, const int32_t *pcell, int64_t np, const double *x,
+                const double *v, const double *sig, const double *m, const double *vol, const int32_t *alive,
                 double *nm, double *nP, double *nf, int want_mass_mom, int want_force) {
   int nn = 1 << M->dim;
   for (int64_t p = 0; p < np; ++p) {
     if (!alive[p]) continue;
     int32_t cell[3];
-    double xi[3], N[8], dN[24];
-    if (oracle_locate(M, x + 3 * p, cell, xi) != OM_OK) continue;
-    oracle_shape(M->dim, xi, N, dN);
+    double N[8], dN[24];
+    if (particle_basis(M, X, pcell, p, x + 3 * p, cell, N, dN) != OM_OK) continue;
     for (int a = 0; a < nn; ++a) {
       int64_t i = cell_node(M, cell, a);
       if (want_mass_mom) {
@@ -208,7 +413,7 @@ static void p2g(const om_mesh *M, int64_t np, const double *x, const double *v,
       }
       if (want_force) {
         double grad[3];
-        for (int k = 0; k < 3; ++k) grad[k] = dN[3 * a + k] * 2.0 / M->h;
+        for (int k = 0; k < 3; ++k) grad[k] = X ? dN[3 * a + k] : dN[3 * a + k] * 2.0 / M->h;
         for (int j = 0; j < 3; ++j) {
           double sg = 0.0;
           for (int k = 0; k < 3; ++k) sg += voigt_at(sig + 6 * p, j, k) * grad[k];
@@ -230,7 +435,7 @@ void oracle_p2g(const om_mesh *M, int64_t np, const double *x, const double *v,
   memset(nm, 0, sizeof(double) * nnodes);
   memset(nP, 0, sizeof(double) * 3 * nnodes);
   memset(nf, 0, sizeof(double) * 3 * nnodes);
-  p2g(M, np, x, v, sig, m, vol, alive, nm, nP, nf, 1, 1);
+  p2g(M, NULL, NULL, np, x, v, sig, m, vol, alive, nm, nP, nf, 1, 1);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -524,14 +729,15 @@ static int finite6(const double *s) {
 /* Strain increment from the nodal velocity field vel (3 per node):
  *   L_jk = sum_a vel_a,j dN_a/dx_k ;  de = dt (L + L^T) / 2  (Voigt, tensor
  * shear).  In 2D only the in-plane components are non-zero (R7). */
-static void strain_increment(const om_mesh *M, const int32_t cell[3], const double dN[24],
+static void strain_increment(const om_mesh *M, int mapped, const int32_t cell[3], const double dN[24],
                              const double *vel, double de[6]) {
   double L[3][3] = {{0}};
   int nn = 1 << M->dim;
   for (int a = 0; a < nn; ++a) {
     int64_t i = cell_node(M, cell, a);
     for (int j = 0; j < M->dim; ++j)
-      for (int k = 0; k < M->dim; ++k) L[j][k] += vel[3 * i + j] * dN[3 * a + k] * 2.0 / M->h;
+      for (int k = 0; k < M->dim; ++k)
+        L[j][k] += mapped ? vel[3 * i + j] * dN[3 * a + k] : vel[3 * i + j] * dN[3 * a + k] * 2.0 / M->h;
   }
   de[0] = L[0][0] * M->dt;
   de[1] = L[1][1] * M->dt;
@@ -609,8 +815,8 @@ static void node_solve(const om_mesh *M, double *nm, double *nP, double *nf, dou
  * stress, P2G of forces from the new stress, nodal acceleration with the
  * full constraints, then per particle FLIP velocity, position, relocation.
  */
-static int step_once(const om_mesh *M, const om_material *mat, int64_t np, double *x, double *v,
-                     double *sig, double *eps, const double *m, double *vol, double *epsp,
+static int step_once(const om_mesh *M, const double *X, int32_t *pcell, const om_material *mat, int64_t np,
+                     double *x, double *v, double *sig, double *eps, const double *m, double *vol, double *epsp,
                      const double *coh, int32_t *alive, double *work) {
   int64_t N = oracle_num_nodes(M);
   double *nm = work, *nP = work + N, *nf = work + 4 * N, *nv = work + 7 * N, *na = work + 10 * N,
@@ -620,31 +826,29 @@ static int step_once(const om_mesh *M, const om_material *mat, int64_t np, doubl
   int nn = 1 << M->dim;
 
   if (M->scheme == OM_USL) {
-    p2g(M, np, x, v, sig, m, vol, alive, nm, nP, nf, 1, 1);
+    p2g(M, X, pcell, np, x, v, sig, m, vol, alive, nm, nP, nf, 1, 1);
     node_solve(M, nm, nP, nf, nv, na, nvn, 1);
   } else {
-    p2g(M, np, x, v, sig, m, vol, alive, nm, nP, nf, 1, 0);
+    p2g(M, X, pcell, np, x, v, sig, m, vol, alive, nm, nP, nf, 1, 0);
     node_solve(M, nm, nP, nf, nv, na, nvn, 0);
     for (int64_t p = 0; p < np; ++p) {
       if (!alive[p]) continue;
       int32_t cell[3];
-      double xi[3], N8[8], dN[24], de[6];
-      if (oracle_locate(M, x + 3 * p, cell, xi) != OM_OK) continue;
-      oracle_shape(M->dim, xi, N8, dN);
-      strain_increment(M, cell, dN, nv, de);
+      double N8[8], dN[24], de[6];
+      if (particle_basis(M, X, pcell, p, x + 3 * p, cell, N8, dN) != OM_OK) continue;
+      strain_increment(M, X != NULL, cell, dN, nv, de);
       material_point_update(M, mat, coh ? coh[p] : mat->c, de, sig + 6 * p, eps + 6 * p, vol + p,
                             epsp + p);
     }
-    p2g(M, np, x, v, sig, m, vol, alive, nm, nP, nf, 0, 1);
+    p2g(M, X, pcell, np, x, v, sig, m, vol, alive, nm, nP, nf, 0, 1);
     node_solve(M, nm, nP, nf, nv, na, nvn, 2);
   }
 
   for (int64_t p = 0; p < np; ++p) {
     if (!alive[p]) continue;
     int32_t cell[3];
-    double xi[3], N8[8], dN[24];
-    if (oracle_locate(M, x + 3 * p, cell, xi) != OM_OK) continue;
-    oracle_shape(M->dim, xi, N8, dN);
+    double N8[8], dN[24];
+    if (particle_basis(M, X, pcell, p, x + 3 * p, cell, N8, dN) != OM_OK) continue;
     double dv[3] = {0, 0, 0}, vb[3] = {0, 0, 0};
     for (int a = 0; a < nn; ++a) {
       int64_t i = cell_node(M, cell, a);
@@ -655,7 +859,7 @@ static int step_once(const om_mesh *M, const om_material *mat, int64_t np, doubl
     }
     if (M->scheme == OM_USL) {
       double de[6];
-      strain_increment(M, cell, dN, nvn, de);
+      strain_increment(M, X != NULL, cell, dN, nvn, de);
       material_point_update(M, mat, coh ? coh[p] : mat->c, de, sig + 6 * p, eps + 6 * p, vol + p,
                             epsp + p);
     }
@@ -665,7 +869,16 @@ static int step_once(const om_mesh *M, const om_material *mat, int64_t np, doubl
     }
     int32_t c2[3];
     double xi2[3];
-    if (oracle_locate(M, x + 3 * p, c2, xi2) != OM_OK) {
+    int where;
+    if (X) {  /* the neighbourhood walk from the particle's cell */
+      for (int k = 0; k < 3; ++k) c2[k] = cell[k];
+      where = oracle_iso_locate(M, X, x + 3 * p, c2, xi2);
+      if (where == OM_OK)
+        for (int k = 0; k < 3; ++k) pcell[3 * p + k] = c2[k];
+    } else {
+      where = oracle_locate(M, x + 3 * p, c2, xi2);
+    }
+    if (where != OM_OK) {
       alive[p] = 0;
       status = OM_LEFT_MESH;
     }
@@ -686,7 +899,25 @@ int oracle_step(const om_mesh *M, const om_material *mat, int64_t np, double *x,
   if (!M || !mat || (M->dim != 2 && M->dim != 3) || M->h <= 0.0 || M->dt <= 0.0) return OM_ARG;
   int status = OM_OK;
   for (int64_t s = 0; s < nsteps; ++s) {
-    int st = step_once(M, mat, np, x, v, sig, eps, m, vol, epsp, coh, alive, work);
+    int st = step_once(M, NULL, NULL, mat, np, x, v, sig, eps, m, vol, epsp, coh, alive, work);
+    if (status == OM_OK) status = st;
+  }
+  return status;
+}
+
+/* The same steps on a mapped mesh (node coordinates X, 3 per node): pcell
+ * (3 per particle) holds each particle's cell, located beforehand with
+ * oracle_iso_locate and kept up to date by the walk after advection. */
+int oracle_step_mapped(const om_mesh *M, const double *X, const om_material *mat, int64_t np, double *x,
+                       double *v, double *sig, double *eps, const double *m, double *vol, double *epsp,
+                       const double *coh, int32_t *alive, int32_t *pcell, double *work, int64_t nsteps) {
+  if (!M || !X || !pcell || !mat || (M->dim != 2 && M->dim != 3) || M->dt <= 0.0) return OM_ARG;
+  for (int f = 0; f < 6; ++f)  /* R12 */
+    for (int k = 0; k < 3; ++k)
+      if (M->face_traction[f][k] != 0.0) return OM_ARG;
+  int status = OM_OK;
+  for (int64_t s = 0; s < nsteps; ++s) {
+    int st = step_once(M, X, pcell, mat, np, x, v, sig, eps, m, vol, epsp, coh, alive, work);
     if (status == OM_OK) status = st;
   }
   return status;

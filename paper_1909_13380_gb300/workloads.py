@@ -47,6 +47,7 @@ class Workload:
     meta: dict = field(default_factory=dict)
     face_traction: tuple = ((0.0, 0.0, 0.0),) * 6   # per face: force per unit length (2D) or area (3D)
     damping: float = 0.0                            # alpha of the nodal damping a = f / m - alpha v
+    node_xyz: np.ndarray | None = None              # mapped mesh: (nodes, dim) node coordinates, x fastest
 
     @property
     def n(self) -> int:
@@ -350,3 +351,86 @@ def plate_with_hole(h=0.0625, per_axis=4, E=1e6, nu=0.3, rho=1000.0, sigma0=100.
         material=dict(model=PLANE_STRESS_ELASTIC, E=E, nu=nu, rho=rho, phi=0.0, c=0.0, psi=0.0),
         pos=pos, vel=np.zeros_like(pos), vol=vol, steps=steps, face_traction=tuple(trac), damping=damping,
         meta=dict(sigma0=sigma0, radius=radius))
+
+
+# ---------------------------------------------------------------------------
+# Mapped (isoparametric) meshes: the logical grid of cells is the Cartesian
+# one, the nodes are moved (ISOPARAMETRIC MESH: non-prismatic boundaries).
+# ---------------------------------------------------------------------------
+def cartesian_node_xyz(ncells, h, origin=(0.0, 0.0, 0.0), dim=3) -> np.ndarray:
+    """Node coordinates of the Cartesian grid, one row per node, x fastest."""
+    axes = [origin[k] + h * np.arange(ncells[k] + 1) for k in range(dim)]
+    grids = np.meshgrid(*axes[::-1], indexing="ij")
+    return np.stack([g.ravel() for g in grids[::-1]], axis=1)
+
+
+def rotation(dim: int, angles) -> np.ndarray:
+    """Rotation matrix: angle (2D), or rotations about x, then y, then z (3D)."""
+    if dim == 2:
+        c, s = math.cos(angles), math.sin(angles)
+        return np.array([[c, -s], [s, c]])
+    ax, ay, az = angles
+    Rx = np.array([[1, 0, 0], [0, math.cos(ax), -math.sin(ax)], [0, math.sin(ax), math.cos(ax)]])
+    Ry = np.array([[math.cos(ay), 0, math.sin(ay)], [0, 1, 0], [-math.sin(ay), 0, math.cos(ay)]])
+    Rz = np.array([[math.cos(az), -math.sin(az), 0], [math.sin(az), math.cos(az), 0], [0, 0, 1]])
+    return Rz @ Ry @ Rx
+
+
+def rotated(wl: Workload, R: np.ndarray, name=None) -> Workload:
+    """The same problem turned rigidly about the origin: a mapped mesh whose
+    nodes, particles, velocities and gravity are the Cartesian ones times R.
+    Boundary faces must be free or fixed (a turned roller acts along the
+    logical face's axis)."""
+    d = wl.dim
+    X = cartesian_node_xyz(wl.ncells, wl.h, wl.origin, d) @ R.T
+    g = np.zeros(3)
+    g[:d] = np.asarray(wl.gravity[:d]) @ R.T
+    return Workload(**{**wl.__dict__, "name": name or wl.name + "_rotated", "pos": wl.pos @ R.T,
+                       "vel": wl.vel @ R.T, "gravity": tuple(g), "node_xyz": X})
+
+
+def terrain(points: np.ndarray, dim: int, amp: float, wavelength: float, height: float) -> np.ndarray:
+    """The terrain-following map of a box of the given height: the vertical
+    coordinate v -> v + b(x) (1 - v / height), b(x) = amp sin(2 pi x / wavelength),
+    so the base follows the bumps b and the top stays flat."""
+    p = np.array(points, np.float64)
+    up = dim - 1
+    b = amp * np.sin(2.0 * math.pi * p[:, 0] / wavelength)
+    p[:, up] = p[:, up] + b * (1.0 - p[:, up] / height)
+    return p
+
+
+def terrain_column(dim=2, ncells=None, col_cells=None, h=0.005, amp=None, wavelength=None,
+                   precision=FP64_PLAIN, scheme=USL, steps=2000, name=None) -> Workload:
+    """A granular column collapsing on bumpy ground: the mesh follows the
+    terrain (mapped cells, the base a sine of amplitude amp), the column's
+    particles are the Cartesian 2-point Gauss positions moved by the same
+    map.  Mohr-Coulomb as the 3D column; the base fixed (no slip on the
+    irregular ground), a roller on x = 0 (a vertical plane under the map),
+    the other faces free."""
+    if ncells is None:
+        ncells = (60, 24) if dim == 2 else (40, 8, 24)
+    if col_cells is None:
+        col_cells = (12, 12) if dim == 2 else (12, 8, 12)
+    nodes = ncells[: dim]
+    height = nodes[dim - 1] * h
+    amp = 2.5 * h if amp is None else amp
+    wavelength = 16.0 * h if wavelength is None else wavelength
+    cells = box_cells((0,) * dim, col_cells)
+    flat = gauss_fill(cells, h, (0.0, 0.0, 0.0), dim)
+    pos = terrain(flat, dim, amp, wavelength, height)
+    # the map stretches the vertical by 1 - b(x) / height (its Jacobian
+    # determinant): each particle keeps that share of its Gauss volume
+    stretch = 1.0 - amp * np.sin(2.0 * math.pi * flat[:, 0] / wavelength) / height
+    X = terrain(cartesian_node_xyz(ncells, h, (0.0, 0.0, 0.0), dim), dim, amp, wavelength, height)
+    bc = [FREE] * 6
+    bc[0] = ROLLER
+    bc[2 * (dim - 1)] = FIXED
+    g = [0.0, 0.0, 0.0]
+    g[dim - 1] = -9.81
+    nm = name or f"terrain_column_{dim}d_" + "x".join(str(c) for c in ncells[:dim])
+    return Workload(
+        name=nm, dim=dim, ncells=tuple(ncells[:dim]) + (1,) * (3 - dim), h=h, origin=(0.0, 0.0, 0.0),
+        face_bc=tuple(bc), face_mu=(0.0,) * 6, gravity=tuple(g), dt=1e-5, scheme=scheme, precision=precision,
+        material=_mc(), pos=pos, vel=np.zeros_like(pos), vol=stretch * h ** dim / (1 << dim),
+        steps=steps, node_xyz=X, meta=dict(amp=amp, wavelength=wavelength))

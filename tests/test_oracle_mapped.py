@@ -1,0 +1,289 @@
+"""Pins of the oracle's mapped (isoparametric) mesh (ISOPARAMETRIC MESH:
+natural coordinates by Newton-Raphson from an affine guess, inverse bilinear
+in 2D, particles located by a neighbourhood walk).
+
+  * the inverse map undoes the forward map x(xi) = sum_a N_a(xi) X_a, which
+    the test evaluates itself, on randomly distorted cells; in 2D it equals
+    the closed-form inverse bilinear interpolation (a quadratic); on affine
+    cells the affine guess is already the answer;
+  * the walk finds the cell a brute-force search over every cell finds, from
+    any start, and reports points outside the mesh as outside;
+  * the physical gradients dN/dx reproduce linear fields (sum_a X_a (x)
+    grad N_a = I) and match central differences of N along x;
+  * a mapped mesh whose nodes sit on the Cartesian grid steps like the
+    Cartesian oracle; the whole problem turned rigidly about the origin steps
+    into the turned result (positions, velocities and stresses R . R^T);
+  * the terrain column: particles stay located, mass is conserved.
+"""
+import math
+from dataclasses import replace
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1909_13380_gb300 import workloads as W
+
+
+def corners(dim):
+    return np.array([[1.0 if (a >> k) & 1 else -1.0 for k in range(dim)] for a in range(1 << dim)])
+
+
+def forward(Xa, xi):
+    """x(xi) of a cell from its corner coordinates, by the tensor-product
+    definition of the linear element (independent of the oracle's shapes)."""
+    dim = Xa.shape[1]
+    w = np.array([np.prod([(1.0 + c[k] * xi[k]) / 2.0 for k in range(dim)]) for c in corners(dim)])
+    return w @ Xa
+
+
+def distorted_mesh(dim, n, h, amp, seed):
+    """Cartesian node coordinates moved by up to amp * h per axis (interior
+    and boundary alike): convex, non-degenerate cells for amp < 1/4."""
+    X = W.cartesian_node_xyz(n + (1,) * (3 - dim), h, (0.0, 0.0, 0.0), dim)
+    rng = np.random.default_rng(seed)
+    return X + rng.uniform(-amp * h, amp * h, X.shape)
+
+
+def cell_corners(mesh, X, c):
+    dim = mesh.dim
+    nx, ny = mesh.n[0] + 1, mesh.n[1] + 1
+    idx = []
+    for a in range(1 << dim):
+        i = c[0] + (a & 1)
+        j = c[1] + ((a >> 1) & 1)
+        k = c[2] + ((a >> 2) & 1) if dim == 3 else 0
+        idx.append(i + nx * (j + ny * k))
+    return X[idx][:, :dim]
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_inverse_map_round_trip(dim):
+    n = (6, 5, 4)[:dim]
+    mesh = oracle.Mesh(dim=dim, n=n + (1,) * (3 - dim), h=0.1)
+    X = distorted_mesh(dim, n, 0.1, 0.2, seed=11 + dim)
+    rng = np.random.default_rng(3)
+    for _ in range(200):
+        c = [int(rng.integers(0, n[k])) for k in range(dim)] + [0] * (3 - dim)
+        xi = rng.uniform(-1.0, 1.0, dim)
+        x = forward(cell_corners(mesh, X, c), xi)
+        it, got = oracle.natural_mapped(mesh, X, c, x)
+        assert it > 0
+        assert np.allclose(got[:dim], xi, rtol=0, atol=1e-12)
+
+
+def inverse_bilinear(Xa, x):
+    """The closed-form inverse of the 2D bilinear map: with x = a0 + a1 xi +
+    a2 eta + a3 xi eta, eliminating xi leaves A eta^2 + B eta + C = 0."""
+    X0, X1, X2, X3 = Xa
+    a0 = (X0 + X1 + X2 + X3) / 4.0
+    a1 = (-X0 + X1 - X2 + X3) / 4.0
+    a2 = (-X0 - X1 + X2 + X3) / 4.0
+    a3 = (X0 - X1 - X2 + X3) / 4.0
+    d = x - a0
+
+    def cross(u, v):
+        return u[0] * v[1] - u[1] * v[0]
+
+    A, B, Cq = cross(a3, a2), cross(d, a3) + cross(a1, a2), cross(d, a1)
+    if abs(A) < 1e-14 * (abs(B) + 1e-300):
+        etas = [-Cq / B]
+    else:
+        disc = math.sqrt(B * B - 4.0 * A * Cq)
+        etas = [(-B + disc) / (2.0 * A), (-B - disc) / (2.0 * A)]
+    eta = min(etas, key=lambda e: abs(e))
+    u = a1 + a3 * eta
+    xi = np.dot(d - a2 * eta, u) / np.dot(u, u)
+    return np.array([xi, eta])
+
+
+def test_2d_inverse_equals_inverse_bilinear():
+    n = (6, 5)
+    mesh = oracle.Mesh(dim=2, n=n + (1,), h=0.1)
+    X = distorted_mesh(2, n, 0.1, 0.22, seed=5)
+    rng = np.random.default_rng(4)
+    for _ in range(300):
+        c = [int(rng.integers(0, n[0])), int(rng.integers(0, n[1])), 0]
+        Xa = cell_corners(mesh, X, c)
+        x = forward(Xa, rng.uniform(-1.0, 1.0, 2))
+        it, got = oracle.natural_mapped(mesh, X, c, x)
+        assert it > 0
+        assert np.allclose(got[:2], inverse_bilinear(Xa, x), rtol=0, atol=1e-11)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_affine_cells_are_exact_from_the_guess(dim):
+    # a sheared, stretched grid: every cell is a parallelogram/parallelepiped
+    n = (4, 3, 3)[:dim]
+    mesh = oracle.Mesh(dim=dim, n=n + (1,) * (3 - dim), h=1.0)
+    A = np.array([[0.3, 0.05, 0.02], [0.08, 0.25, -0.04], [0.0, 0.06, 0.2]])[:dim, :dim]
+    X = W.cartesian_node_xyz(n + (1,) * (3 - dim), 1.0, (0.0, 0.0, 0.0), dim) @ A.T + 0.7
+    rng = np.random.default_rng(6)
+    for _ in range(50):
+        c = [int(rng.integers(0, n[k])) for k in range(dim)] + [0] * (3 - dim)
+        xi = rng.uniform(-1.0, 1.0, dim)
+        x = forward(cell_corners(mesh, X, c), xi)
+        it, got = oracle.natural_mapped(mesh, X, c, x)
+        # Newton's first step is already below rounding: it stops at its check
+        assert 1 <= it <= 2
+        assert np.allclose(got[:dim], xi, rtol=0, atol=1e-13)
+
+
+def brute_force_cell(mesh, X, x):
+    """The cell whose natural coordinates of x lie in [-1, 1) on every axis,
+    by trying every cell; None if none does."""
+    dim = mesh.dim
+    found = None
+    for c in W.box_cells((0,) * dim, mesh.n[:dim]):
+        c3 = list(c) + [0] * (3 - dim)
+        it, xi = oracle.natural_mapped(mesh, X, c3, x)
+        if it > 0 and np.all(xi[:dim] >= -1.0) and np.all(xi[:dim] < 1.0):
+            assert found is None, "cells overlap"
+            found = c3
+    return found
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_walk_equals_brute_force(dim):
+    n = (7, 5, 4)[:dim]
+    h = 0.1
+    mesh = oracle.Mesh(dim=dim, n=n + (1,) * (3 - dim), h=h)
+    X = distorted_mesh(dim, n, h, 0.2, seed=21 + dim)
+    rng = np.random.default_rng(7 + dim)
+    span = np.array(n) * h
+    inside = outside = 0
+    for _ in range(120 if dim == 2 else 60):
+        x = rng.uniform(-0.1 * span, 1.1 * span)
+        start = [int(rng.integers(0, n[k])) for k in range(dim)] + [0] * (3 - dim)
+        st, c, xi = oracle.locate_mapped(mesh, X, x, start)
+        ref = brute_force_cell(mesh, X, x)
+        if ref is None:
+            assert st == oracle.LEFT_MESH
+            outside += 1
+        else:
+            assert st == oracle.OK and list(c) == ref, (x, start)
+            assert np.allclose(forward(cell_corners(mesh, X, c), xi[:dim]), x, atol=1e-12)
+            inside += 1
+    assert inside > 20 and outside > 5
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_physical_gradients(dim):
+    n = (5, 4, 3)[:dim]
+    h = 0.1
+    mesh = oracle.Mesh(dim=dim, n=n + (1,) * (3 - dim), h=h)
+    X = distorted_mesh(dim, n, h, 0.2, seed=31 + dim)
+    rng = np.random.default_rng(8)
+    nn = 1 << dim
+    for _ in range(40):
+        c = [int(rng.integers(0, n[k])) for k in range(dim)] + [0] * (3 - dim)
+        Xa = cell_corners(mesh, X, c)
+        xi = rng.uniform(-0.9, 0.9, dim)
+        x = forward(Xa, xi)
+        N, G = oracle.basis_mapped(mesh, X, c, xi)
+        # partition of unity, reproduction of x and of linear fields
+        assert abs(N[:nn].sum() - 1.0) < 1e-14
+        assert np.allclose(N[:nn] @ Xa, x, atol=1e-14)
+        assert np.allclose(Xa.T @ G[:nn, :dim], np.eye(dim), atol=1e-11)
+        assert np.allclose(G[:nn].sum(axis=0), 0.0, atol=1e-9)
+        # central differences of N_a along each physical axis
+        eps = 1e-6 * h
+        for j in range(dim):
+            Ns = []
+            for sgn in (1.0, -1.0):
+                xs = x.copy()
+                xs[j] += sgn * eps
+                it, xis = oracle.natural_mapped(mesh, X, c, xs)
+                assert it > 0
+                Ns.append(oracle.basis_mapped(mesh, X, c, xis[:dim])[0][:nn])
+            fd = (Ns[0] - Ns[1]) / (2.0 * eps)
+            assert np.allclose(G[:nn, j], fd, rtol=0, atol=1e-6 / h)
+
+
+def small_column(dim, scheme):
+    if dim == 2:
+        wl = W.column2d(6, 8, h=0.01, precision=W.FP64_PLAIN, scheme=scheme, mesh_cells=(14, 12))
+    else:
+        wl = W.column3d(ncells=(10, 6, 10), col_cells=(4, 3, 5), h=0.01, precision=W.FP64_PLAIN, scheme=scheme)
+    return wl
+
+
+def run(wl, steps):
+    o = oracle.from_workload(wl)
+    st = o.step(steps)
+    return o, st
+
+
+@pytest.mark.parametrize("scheme", [W.USF, W.USL])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_cartesian_nodes_step_like_the_cartesian_mesh(dim, scheme):
+    wl = small_column(dim, scheme)
+    mapped = replace(wl, node_xyz=W.cartesian_node_xyz(wl.ncells, wl.h, wl.origin, dim))
+    a, sa = run(wl, 150)
+    b, sb = run(mapped, 150)
+    assert sa == sb == oracle.OK
+    for k in ("x", "v", "sig", "eps", "vol"):
+        u, w = getattr(a.state, k), getattr(b.state, k)
+        scale = np.max(np.abs(u)) + 1e-300
+        assert np.max(np.abs(u - w)) <= 1e-9 * scale, k
+    assert np.array_equal(a.cells(), b.cells())
+
+
+@pytest.mark.parametrize("scheme", [W.USF, W.USL])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_rotated_problem_steps_into_the_rotated_result(dim, scheme):
+    wl = small_column(dim, scheme)
+    # fixed base, every other face free: conditions that turn with the body
+    bc = [W.FREE] * 6
+    bc[2 * (dim - 1)] = W.FIXED
+    wl = replace(wl, face_bc=tuple(bc), face_mu=(0.0,) * 6)
+    R = W.rotation(dim, 0.5 if dim == 2 else (0.3, -0.4, 0.7))
+    a, sa = run(wl, 200)
+    b, sb = run(W.rotated(wl, R), 200)
+    assert sa == sb == oracle.OK
+    d = dim
+    assert np.max(np.abs(a.state.x[:, :d] @ R.T - b.state.x[:, :d])) <= 1e-12 * 10 + 1e-9 * wl.h
+    vs = np.max(np.abs(a.state.v))
+    assert vs > 1e-3
+    assert np.max(np.abs(a.state.v[:, :d] @ R.T - b.state.v[:, :d])) <= 1e-8 * vs
+
+    def tensor(v):
+        t = np.zeros((v.shape[0], 3, 3))
+        for i, (j, k) in enumerate([(0, 0), (1, 1), (2, 2), (0, 1), (1, 2), (0, 2)]):
+            t[:, j, k] = t[:, k, j] = v[:, i]
+        return t
+
+    Rf = np.eye(3)
+    Rf[:d, :d] = R
+    sa_t = np.einsum("ij,pjk,lk->pil", Rf, tensor(a.state.sig), Rf)
+    ss = np.max(np.abs(a.state.sig))
+    assert np.max(np.abs(sa_t - tensor(b.state.sig))) <= 1e-8 * ss
+    assert np.allclose(a.state.vol, b.state.vol, rtol=1e-10, atol=0)
+    assert np.array_equal(a.state.alive, b.state.alive)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_terrain_column(dim):
+    wl = W.terrain_column(dim, ncells=(40, 16) if dim == 2 else (16, 4, 12),
+                          col_cells=(8, 8) if dim == 2 else (6, 4, 6))
+    o = oracle.from_workload(wl)
+    m0 = o.conservation()["mass"]
+    assert np.all(o.cells() >= 0)
+    assert o.step(300) == oracle.OK
+    c = o.conservation()
+    assert c["alive"] == wl.n and c["mass"] == pytest.approx(m0, rel=1e-15)
+    # the column has started to fall and spread: v along gravity is negative
+    assert np.mean(o.state.v[:, dim - 1]) < 0
+    # every particle's stored cell contains it
+    for p in range(0, wl.n, max(1, wl.n // 50)):
+        it, xi = oracle.natural_mapped(o.mesh, o.X, o.cell[p], o.state.x[p, :dim])
+        assert it > 0 and np.all(xi[:dim] >= -1.0) and np.all(xi[:dim] < 1.0)
+
+
+def test_tractions_are_not_defined_on_mapped_meshes():
+    wl = small_column(2, W.USL)
+    trac = [(0.0, 0.0, 0.0)] * 6
+    trac[1] = (5.0, 0.0, 0.0)
+    mapped = replace(wl, node_xyz=W.cartesian_node_xyz(wl.ncells, wl.h, wl.origin, 2), face_traction=tuple(trac))
+    o = oracle.from_workload(mapped)
+    assert o.step(1) == oracle.ARG
