@@ -509,6 +509,56 @@ def pinned_like(a):
     return out, t
 
 
+def run_mapped(args, stream, sptr, flush):
+    """The FP64 step on a mapped (isoparametric) mesh: a granular column on
+    terrain-following cells (983,040 particles, 160 x 48 x 64 cells), timed
+    like the headline, beside the Cartesian FP64 step of the same particle
+    count; and the paper's locate case, 150,000 particles placed in a mesh of
+    23,000 mapped cells (the add call: upload, initialisation and the
+    neighbourhood walk of every particle, wall clock, best of 3)."""
+    from paper_1909_13380_gb300 import mpm
+
+    h = 0.005
+    wl = W.terrain_column(3, ncells=(160, 48, 64), col_cells=(80, 48, 32), h=h)
+    flat = dataclasses.replace(wl, node_xyz=None, pos=W.gauss_fill(W.box_cells((0, 0, 0), (80, 48, 32)), h,
+                                                                   (0.0, 0.0, 0.0), 3),
+                               vol=np.full(wl.n, h ** 3 / 8.0), name="granular_column_3d_160x48x64_flat")
+    k = max(1, min(args.steps, 20))
+    out = {"workload": wl.name, "particles": wl.n, "scheme": "USL", "steps": k}
+    for key, w in (("ms_per_step", wl), ("cartesian_fp64_ms", flat)):
+        sim = mpm.Simulation(w, stream=sptr)
+        advance(sim, 20, stream)
+        timed_steps(sim, args.warmup, stream, flush)
+        out[key] = sum(timed_steps(sim, k, stream, flush)) / k
+        st = sim.sync()
+        sim.close()
+        if st != mpm.MPM_OK:
+            raise SystemExit(f"mapped leg: {mpm.STATUS_NAMES.get(st, st)}")
+    loc = W.terrain_column(3, ncells=(40, 24, 24), col_cells=(40, 24, 20), h=h)
+    best = None
+    for _ in range(3):
+        empty = dataclasses.replace(loc, pos=loc.pos[:0], vel=loc.vel[:0], vol=loc.vol[:0])
+        with mpm.Simulation(empty, stream=sptr) as sim:
+            stream.synchronize()
+            t0 = time.perf_counter()
+            mpm.mpm_add_particles(sim.h, loc.pos, loc.vel, loc.vol, sim.mat)
+            t = time.perf_counter() - t0
+        best = t if best is None else min(best, t)
+    out.update({"locate_particles": loc.n, "locate_cells": 40 * 24 * 24, "locate_ms": 1e3 * best})
+    return out
+
+
+def short_floats(obj, digits=6):
+    """The JSON line with every float to `digits` significant digits."""
+    if isinstance(obj, float):
+        return float(f"{obj:.{digits}g}")
+    if isinstance(obj, dict):
+        return {k: short_floats(v, digits) for k, v in obj.items()}
+    if isinstance(obj, (list, tuple)):
+        return [short_floats(v, digits) for v in obj]
+    return obj
+
+
 def run_gb300(args):
     import torch
     from paper_1909_13380_gb300 import mpm
@@ -619,6 +669,12 @@ def run_gb300(args):
                "seconds": round(t1 - t0, 4),
                "includes": "create, upload (pinned), K steps, read pos/vel/stress (pinned)"}
 
+    # ---- the mapped (isoparametric) FP64 step (rank 0) ------------------------
+    mapped = None
+    if rank == 0 and not args.no_mapped:
+        mapped = run_mapped(args, stream, sptr, flush)
+        detail["mapped"] = mapped
+
     # ---- batched small meshes and the serving loop (rank 0) -----------------
     batched = serving = None
     if rank == 0 and not args.no_batch:
@@ -673,7 +729,11 @@ def run_gb300(args):
             "batched": None if not batched else {k: batched[k] for k in ("particles", "value", "ms_per_batched_step",
                                                                        "batching_speedup")},
             "serving": short_serving(serving),
+            "mapped": None if not mapped else {k: mapped[k] for k in ("workload", "ms_per_step", "cartesian_fp64_ms",
+                                                                      "locate_particles", "locate_cells",
+                                                                      "locate_ms")},
         }
+        line = short_floats(line)
         detail.update({"fp64_plain": fp64, "other_scheme": other, "e2e": e2e, "phases_ms_all": phases,
                        "step_ms": step_ms})
         if args.detail_out:
@@ -703,6 +763,7 @@ def main(argv=None):
     ap.add_argument("--no-batch", action="store_true", help="skip the 256 batched 2D columns")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--no-serving", action="store_true", help="skip the serving session")
+    ap.add_argument("--no-mapped", action="store_true", help="skip the FP64 step on a mapped mesh")
     ap.add_argument("--serve-requests", type=int, default=32)
     ap.add_argument("--serve-step-scale", type=float, default=1.0 / 50)
     ap.add_argument("--serve-chunk", type=int, default=16)

@@ -33,8 +33,9 @@
  *     beyond the upper mesh bound has left the mesh.
  *   - Host pointers are copied; the caller keeps ownership.  The library
  *     owns all device memory of a handle and frees it in mpm_destroy.
- *   - Every call returns an mpm_status.  MPM_ERR_ARG leaves the handle as it
- *     was; every other error is sticky per handle until mpm_destroy.
+ *   - Every call returns an mpm_status.  MPM_ERR_ARG and MPM_ERR_STATE (a
+ *     call rejected before it did anything) leave the handle as it was;
+ *     every other error is sticky per handle until mpm_destroy.
  *     mpm_last_error gives a message.  Device-side conditions
  *     (a particle left the mesh, a non-finite value) are latched in a device
  *     status word and reported at the next synchronising call.
@@ -86,7 +87,8 @@ enum { MPM_LINEAR_ELASTIC = 0, MPM_MOHR_COULOMB = 1, MPM_PLANE_STRESS_ELASTIC = 
  *              sums, FP64 only in the Mohr-Coulomb return near the apex and
  *              in the conservation sums.
  *   mass_tol   a node is active when its mass exceeds this (e.g. 1e-12 kg)
- *   stream     cudaStream_t to enqueue on (NULL: the legacy default stream) */
+ *   stream     cudaStream_t to enqueue on (NULL: the handle creates its own
+ *              non-blocking stream and destroys it in mpm_destroy) */
 typedef struct {
   int32_t dim;
   int32_t ncells[3];
@@ -136,6 +138,38 @@ mpm_status mpm_create_mesh(const mpm_mesh_desc *desc, mpm_handle *out);
 mpm_status mpm_add_particles(mpm_handle h, int64_t n, const double *pos, const double *vel,
                              const double *vol, const mpm_material *mat, const double *cohesion,
                              const double *stress0, int64_t *first_id);
+
+/* Mapped (isoparametric) mesh (ISOPARAMETRIC MESH: cells that follow
+ * non-prismatic geometry such as a landslide's terrain), FP64_PLAIN handles
+ * only, before the first mpm_add_particles (MPM_ERR_STATE otherwise).
+ *   node_xyz   host, (nodes, dim) row-major doubles: the coordinates of node
+ *              ix + (nx+1) (iy + (ny+1) iz) -- the logical grid of
+ *              mpm_mesh_desc keeps its cells, only the nodes move.  Read
+ *              during the call; the handle keeps a device copy.
+ * Every cell must keep the orientation of the logical grid (the Jacobian
+ * determinant of its map positive at each corner) and the coordinates must
+ * be finite (MPM_ERR_ARG, nothing changed).  A cell is then the image of
+ * [-1, 1]^dim under x(xi) = sum_a N_a(xi) X_a, and:
+ *   - a particle's natural coordinates are the root of x(xi) = x, by
+ *     Newton-Raphson from the inverse bilinear solution (2D) or the affine
+ *     guess (3D); shape gradients are dN/dx = dN/dxi J^-1;
+ *   - mpm_add_particles locates new particles by a neighbourhood walk from
+ *     the Cartesian cell of desc.origin and desc.h (which serve no other
+ *     purpose on a mapped mesh); a particle in no cell rejects the call
+ *     (MPM_ERR_ARG, none added);
+ *   - each step, after advection, the walk moves from a particle's cell to
+ *     the neighbour across the face its natural coordinates leave by until
+ *     they lie in [-1, 1) (xi = 1 belongs to the next cell); a particle that
+ *     would leave the grid has left the mesh (MPM_ERR_LEFT_MESH);
+ *   - face conditions act along the global axes (a roller zeroes the
+ *     component along its logical face's axis): exact for fixed faces and
+ *     for faces that stay planes normal to that axis.  Face tractions are
+ *     not defined: mpm_set_loads rejects them, and a mesh that carries them
+ *     rejects this call (MPM_ERR_ARG).  Damping is allowed.
+ * mpm_read_particles' cell is the walk's cell.  mpm_footprint does not
+ * include the mapped storage: 24 bytes per node and 4 + 8 dim per particle.
+ * Calling it again before the first particles replaces the coordinates. */
+mpm_status mpm_set_node_coordinates(mpm_handle h, const double *node_xyz);
 
 /* Enqueue nsteps explicit steps on desc.stream and return without waiting.
  * Returns a latched error, if any, or MPM_OK.  Zero particles is valid. */

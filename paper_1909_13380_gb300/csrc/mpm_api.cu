@@ -197,6 +197,7 @@ struct mpm_ctx {
   D64Launch L64{};
   void *pmem64 = nullptr;
   void *nmem64 = nullptr;
+  double *X64 = nullptr;  // mapped mesh: node coordinates, 3 per node (mpm_set_node_coordinates)
   // shared
   int32_t *d_status = nullptr;  // FP64 path status word (FP32 path: s.ctr[C_STATUS])
   double *d_cons = nullptr;     // 8 results + partials
@@ -229,7 +230,8 @@ namespace {
 
 mpm_status fail(mpm_ctx *h, mpm_status s, const std::string &msg) {
   if (h) {
-    if (s != MPM_ERR_ARG && (h->sticky == MPM_OK || s == MPM_ERR_CUDA)) h->sticky = s;
+    // a rejected call (malformed, or not valid in this state) changed nothing
+    if (s != MPM_ERR_ARG && s != MPM_ERR_STATE && (h->sticky == MPM_OK || s == MPM_ERR_CUDA)) h->sticky = s;
     h->err = msg;
   }
   return s;
@@ -273,12 +275,12 @@ void carve32(void *mem, int dim, bool coh, int64_t cap, PBuf &b) {
   b.has_coh = coh ? 1 : 0;
 }
 
-int nfields64(int dim, bool coh) {
+int nfields64(int dim, bool coh, bool mapped) {
   const int ns = dim == 3 ? 6 : 4;
-  return 2 * dim + 2 * ns + 3 + (coh ? 1 : 0);  // + alive (int, counted apart)
+  return 2 * dim + 2 * ns + 3 + (coh ? 1 : 0) + (mapped ? dim : 0);  // + alive, cell (int, counted apart)
 }
 
-void carve64(void *mem, int dim, bool coh, int64_t cap, D64State &P) {
+void carve64(void *mem, int dim, bool coh, bool mapped, int64_t cap, D64State &P) {
   char *p = (char *)mem;
   const size_t f = al256(8 * cap);
   memset(&P, 0, sizeof(P));
@@ -291,10 +293,18 @@ void carve64(void *mem, int dim, bool coh, int64_t cap, D64State &P) {
   P.vol = (double *)p; p += f;
   P.epsp = (double *)p; p += f;
   if (coh) { P.coh = (double *)p; p += f; }
+  if (mapped)
+    for (int k = 0; k < dim; ++k) { P.xi[k] = (double *)p; p += f; }
   P.alive = (int32_t *)p;
+  p += al256(4 * cap);
+  if (mapped) P.cell = (int32_t *)p;
 }
 
-size_t buf64_bytes(int dim, bool coh, int64_t cap) { return al256(8 * cap) * nfields64(dim, coh) + al256(4 * cap); }
+size_t buf64_bytes(int dim, bool coh, bool mapped, int64_t cap) {
+  return al256(8 * cap) * nfields64(dim, coh, mapped) + al256(4 * cap) * (mapped ? 2 : 1);
+}
+
+
 
 template <typename T>
 MatConst<T> mat_const(const mpm_material &m) {
@@ -311,6 +321,33 @@ MatConst<T> mat_const(const mpm_material &m) {
   c.spsi = (T)sin(m.psi);
   c.c = (T)m.c;
   return c;
+}
+
+// The FP64 launch parameters from the handle (particle/node storage is kept
+// in h->L64 as it is allocated).
+void fill_launch64(const mpm_ctx *h, D64Launch &L) {
+  L.dim = h->d.dim;
+  L.scheme = h->d.scheme;
+  L.n = h->n;
+  for (int k = 0; k < 3; ++k) {
+    L.nc[k] = h->d.ncells[k];
+    L.origin[k] = h->d.origin[k];
+    L.g[k] = h->d.gravity[k];
+  }
+  L.h = h->d.h;
+  L.dt = h->d.dt;
+  L.mass_tol = h->d.mass_tol;
+  for (int f = 0; f < 6; ++f) {
+    L.bc[f] = h->d.face_bc[f];
+    L.mu[f] = h->d.face_mu[f];
+  }
+  L.mat = mat_const<double>(h->mat);
+  L.loads = h->loads;
+  L.damp = h->damp;
+  for (int f = 0; f < 6; ++f)
+    for (int k = 0; k < 3; ++k) L.trac[f][k] = h->trac[f][k];
+  L.status = h->d_status;
+  L.X = h->X64;
 }
 
 int tile_dim(int dim, int k) {
@@ -627,7 +664,7 @@ mpm_status mpm_footprint(const mpm_mesh_desc *desc, int64_t n, int32_t has_cohes
     *bytes = 2 * (int64_t)buf32_bytes(d.dim, coh, n) + 7 * 4 * n + (int64_t)sort_scratch_bytes(n) +
              f32_fixed_bytes(d, nt, nn);
   else
-    *bytes = (int64_t)buf64_bytes(d.dim, coh, n) + 8 * nn * (1 + 5 * d.dim) + 65536;
+    *bytes = (int64_t)buf64_bytes(d.dim, coh, false, n) + 8 * nn * (1 + 5 * d.dim) + 65536;
   return MPM_OK;
 }
 
@@ -652,8 +689,9 @@ mpm_status mpm_add_particles(mpm_handle h, int64_t n, const double *pos, const d
   const int D = h->d.dim;
   const mpm_mesh_desc &d = h->d;
   // FP64 storage: reject points outside the mesh on the host (the FP32
-  // storage is converted and checked on the device, init_particles_k)
-  if (h->d.precision != MPM_FP32_MIXED)
+  // storage is converted and checked on the device, init_particles_k; a
+  // mapped mesh locates them on the device, d64_locate)
+  if (h->d.precision != MPM_FP32_MIXED && !h->X64)
     for (int64_t p = 0; p < n; ++p)
       for (int k = 0; k < D; ++k) {
         const double s = (pos[p * D + k] - d.origin[k]) / d.h;
@@ -754,9 +792,10 @@ mpm_status mpm_add_particles(mpm_handle h, int64_t n, const double *pos, const d
     const int64_t cap = n1;
     DevGuard guard;
     void *&nmem = guard.p[0];
-    CK(cudaMalloc(&nmem, buf64_bytes(D, coh, cap)), "particle storage");
+    const bool mapped = h->X64 != nullptr;
+    CK(cudaMalloc(&nmem, buf64_bytes(D, coh, mapped, cap)), "particle storage");
     D64State P;
-    carve64(nmem, D, coh, cap, P);
+    carve64(nmem, D, coh, mapped, cap, P);
     const D64State &O = h->L64.P;
     if (n0 > 0) {
       const size_t b8 = 8 * n0;
@@ -773,12 +812,16 @@ mpm_status mpm_add_particles(mpm_handle h, int64_t n, const double *pos, const d
       CK(cp(P.epsp, O.epsp, b8), "copy");
       if (coh) CK(cp(P.coh, O.coh, b8), "copy");
       CK(cp(P.alive, O.alive, 4 * n0), "copy");
+      if (mapped) {
+        CK(cp(P.cell, O.cell, 4 * n0), "copy");
+        for (int k = 0; k < D; ++k) CK(cp(P.xi[k], O.xi[k], b8), "copy");
+      }
     }
     {  // the FP64 inputs go up once; one kernel fills the new slots
       double *in64 = nullptr;
-      int32_t *unused = nullptr;
+      int32_t *bad = nullptr;
       NewParticles np;
-      cudaError_t e = upload_inputs(h->st, n, D, pos, vel, vol, stress0, cohesion, in64, np, unused);
+      cudaError_t e = upload_inputs(h->st, n, D, pos, vel, vol, stress0, cohesion, in64, np, bad);
       if (in64 == nullptr) CK(e, "upload scratch");
       const int blocks = (int)std::min<int64_t>((n + 255) / 256, 8192);
       if (e == cudaSuccess) {
@@ -788,9 +831,18 @@ mpm_status mpm_add_particles(mpm_handle h, int64_t n, const double *pos, const d
           init_particles64_k<2><<<blocks, 256, 0, h->st>>>(n, n0, P, mat->rho, np);
         e = cudaGetLastError();
       }
+      int32_t nbad = 0;
+      if (e == cudaSuccess && mapped) {  // the initial cells by the neighbourhood walk
+        D64Launch L = h->L64;
+        fill_launch64(h, L);
+        L.P = P;
+        e = d64_locate(L, n0, n, bad, h->st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&nbad, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st);
+      }
       cudaFreeAsync(in64, h->st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
       CK(e, "upload");
+      if (nbad > 0) return fail(h, MPM_ERR_ARG, "a particle lies outside the mapped mesh");
     }
     free_ptr(h->pmem64);
     h->pmem64 = nmem;
@@ -848,27 +900,7 @@ mpm_status mpm_step(mpm_handle h, int64_t nsteps) {
     if (h->timing) h->timed_step = true;
   } else {
     D64Launch &L = h->L64;
-    L.dim = h->d.dim;
-    L.scheme = h->d.scheme;
-    L.n = h->n;
-    for (int k = 0; k < 3; ++k) {
-      L.nc[k] = h->d.ncells[k];
-      L.origin[k] = h->d.origin[k];
-      L.g[k] = h->d.gravity[k];
-    }
-    L.h = h->d.h;
-    L.dt = h->d.dt;
-    L.mass_tol = h->d.mass_tol;
-    for (int f = 0; f < 6; ++f) {
-      L.bc[f] = h->d.face_bc[f];
-      L.mu[f] = h->d.face_mu[f];
-    }
-    L.mat = mat_const<double>(h->mat);
-    L.loads = h->loads;
-    L.damp = h->damp;
-    for (int f = 0; f < 6; ++f)
-      for (int k = 0; k < 3; ++k) L.trac[f][k] = h->trac[f][k];
-    L.status = h->d_status;
+    fill_launch64(h, L);
     for (int64_t s = 0; s < nsteps; ++s) CK(d64_step(L, h->st), "step enqueue");
   }
   return h->sticky;
@@ -931,14 +963,21 @@ mpm_status mpm_read_particles(mpm_handle h, double *pos, double *vel, double *st
       if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
       return e;
     };
+    const bool mapped = h->X64 != nullptr;
     if (cell)
       for (int64_t p = 0; p < n; ++p) cell[p] = 0;
+    if (cell && mapped) {  // the cells the neighbourhood walk keeps
+      std::vector<int32_t> c32((size_t)n);
+      CK(cudaMemcpyAsync(c32.data(), P.cell, 4 * n, cudaMemcpyDeviceToHost, h->st), "read");
+      CK(cudaStreamSynchronize(h->st), "read");
+      for (int64_t p = 0; p < n; ++p) cell[p] = alive[p] ? c32[p] : -1;
+    }
     for (int k = 0; k < D; ++k) {
-      if (pos || cell) {
+      if (pos || (cell && !mapped)) {
         CK(get(P.x[k]), "read");
         if (pos)
           for (int64_t p = 0; p < n; ++p) pos[p * D + k] = col[p];
-        if (cell) {
+        if (cell && !mapped) {
           int64_t mul = 1;
           for (int j = 0; j < k; ++j) mul *= h->d.ncells[j];
           for (int64_t p = 0; p < n; ++p) {
@@ -1076,6 +1115,7 @@ mpm_status mpm_set_loads(mpm_handle h, const double *face_traction, double dampi
       t[f][k] = face_traction ? face_traction[3 * f + k] : 0.0;
       if (!std::isfinite(t[f][k])) return fail(h, MPM_ERR_ARG, "set_loads: traction not finite");
       if (f >= 2 * h->d.dim || k >= h->d.dim) t[f][k] = 0.0;
+      if (t[f][k] != 0.0 && h->X64) return fail(h, MPM_ERR_ARG, "set_loads: no face tractions on a mapped mesh");
       any |= t[f][k] != 0.0;
     }
   CK(cudaStreamSynchronize(h->st), "set_loads");
@@ -1089,6 +1129,67 @@ mpm_status mpm_set_loads(mpm_handle h, const double *face_traction, double dampi
     for (int k = 0; k < 3; ++k) g.trac[f][k] = (float)t[f][k];
   destroy_graphs(h->graph);  // the instance (and its loads) is captured in the step graph
   h->grp_valid = false;
+  return MPM_OK;
+}
+
+mpm_status mpm_set_node_coordinates(mpm_handle h, const double *node_xyz) {
+  mpm_status s0 = check_handle(h);
+  if (s0 != MPM_OK) return s0;
+  if (h->d.precision != MPM_FP64_PLAIN) return fail(h, MPM_ERR_STATE, "node coordinates: FP64_PLAIN meshes only");
+  if (h->n > 0) return fail(h, MPM_ERR_STATE, "node coordinates: set before the first particles");
+  if (!node_xyz) return fail(h, MPM_ERR_ARG, "node coordinates: null");
+  for (int f = 0; f < 6; ++f)
+    for (int k = 0; k < 3; ++k)
+      if (h->trac[f][k] != 0.0) return fail(h, MPM_ERR_ARG, "node coordinates: the mesh carries face tractions");
+  const int D = h->d.dim;
+  const int64_t nx = h->d.ncells[0] + 1, ny = h->d.ncells[1] + 1, nz = D == 3 ? h->d.ncells[2] + 1 : 1;
+  const int64_t nn = nx * ny * nz;
+  std::vector<double> X3((size_t)(3 * nn), 0.0);
+  for (int64_t i = 0; i < nn; ++i)
+    for (int k = 0; k < D; ++k) {
+      const double v = node_xyz[i * D + k];
+      if (!std::isfinite(v)) return fail(h, MPM_ERR_ARG, "node coordinates: not finite");
+      X3[3 * i + k] = v;
+    }
+  // every cell must map the reference cell one-to-one and keep its
+  // orientation: the Jacobian determinant of the map is positive at each of
+  // the cell's corners (there it is the cross product of the edges meeting
+  // at the corner)
+  auto at = [&](int64_t i, int64_t j, int64_t k, int c) { return X3[3 * (i + nx * (j + ny * k)) + c]; };
+  for (int64_t k = 0; k + 1 < nz || (D == 2 && k == 0); ++k)
+    for (int64_t j = 0; j + 1 < ny; ++j)
+      for (int64_t i = 0; i + 1 < nx; ++i)
+        for (int a = 0; a < (1 << D); ++a) {
+          const int64_t ci = i + (a & 1), cj = j + ((a >> 1) & 1), ck = k + ((a >> 2) & 1);
+          double e[3][3];  // edges from the corner along +axis (reversed at upper corners)
+          for (int ax = 0; ax < D; ++ax) {
+            const int up = (a >> ax) & 1;
+            int64_t o[3] = {ci, cj, ck};
+            o[ax] += up ? -1 : 1;
+            for (int c = 0; c < D; ++c) {
+              const double d = at(o[0], o[1], o[2], c) - at(ci, cj, ck, c);
+              e[ax][c] = up ? -d : d;
+            }
+          }
+          double det;
+          if (D == 2)
+            det = e[0][0] * e[1][1] - e[0][1] * e[1][0];
+          else
+            det = e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) -
+                  e[0][1] * (e[1][0] * e[2][2] - e[1][2] * e[2][0]) +
+                  e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0]);
+          if (!(det > 0.0)) return fail(h, MPM_ERR_ARG, "node coordinates: a cell is degenerate or inverted");
+        }
+  double *dX = nullptr;
+  CK(cudaStreamSynchronize(h->st), "node coordinates");
+  CK(cudaMalloc(&dX, sizeof(double) * 3 * nn), "node coordinates");
+  cudaError_t e = cudaMemcpy(dX, X3.data(), sizeof(double) * 3 * nn, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(dX);
+    return cuda_fail(h, e, "node coordinates");
+  }
+  if (h->X64) cudaFree(h->X64);
+  h->X64 = dX;
   return MPM_OK;
 }
 
@@ -1135,7 +1236,7 @@ mpm_status mpm_destroy(mpm_handle h) {
                   S.out_cnt, S.bucket_start, S.bucket_fill, S.movers, S.bucket, S.bucket_sorted, S.active,
                   S.bin_rec, S.scan_tot, S.ctr, S.slots1, S.slots2, S.slots_a, S.fepoch, S.aepoch, S.resid, S.node,
                   h->keys2, h->perm2, h->sort_scratch,
-                  h->pmem64, h->nmem64, h->d_status, h->d_cons};
+                  h->pmem64, h->nmem64, h->X64, h->d_status, h->d_cons};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (int i = 0; i <= MPM_MAX_PHASES; ++i)

@@ -324,6 +324,10 @@ struct D64State {
   double *x[3], *v[3], *sig[6], *eps[6];
   double *mass, *vol, *epsp, *coh;
   int32_t *alive;
+  // mapped mesh only (ISOPARAMETRIC MESH), else null: each particle's cell
+  // (linear id ix + nx (iy + ny iz)) and its natural coordinates there
+  int32_t *cell;
+  double *xi[3];
 };
 struct D64Nodes {
   double *m, *P[3], *f[3], *v[3], *a[3], *vn[3];
@@ -342,8 +346,13 @@ struct D64Launch {
   D64Nodes N;
   int64_t nnodes;
   int32_t *status;
+  const double *X;  // mapped mesh: node coordinates, 3 per node (x fastest); null: Cartesian
 };
 cudaError_t d64_step(const D64Launch &L, cudaStream_t st);
+// Locate particles n0 .. n0 + n - 1 of a mapped mesh (L.X set) by the
+// neighbourhood walk from their Cartesian guess cell; fills P.cell and P.xi
+// and counts the ones found in no cell in *bad.
+cudaError_t d64_locate(const D64Launch &L, int64_t n0, int64_t n, int32_t *bad, cudaStream_t st);
 cudaError_t d64_conservation(const D64Launch &L, double *d_out, double *d_partials, cudaStream_t st);
 
 // --- material update primitive (mpm_fp64.cu / mpm_fp32.cu) -------------------

@@ -110,6 +110,7 @@ def load():
             "mpm_step_kernels": [vp, i32p],
             "mpm_set_scan_fault": [vp, C.c_int32, C.c_int32],
             "mpm_set_loads": [vp, dp, C.c_double],
+            "mpm_set_node_coordinates": [vp, dp],
             "mpm_material_update": [C.POINTER(mpm_material), C.c_int32, C.c_int64, dp, dp, dp, dp, dp, vp],
             "mpm_set_phase_timing": [vp, C.c_int32],
             "mpm_phase_times": [vp, C.POINTER(C.c_float), i32p],
@@ -341,6 +342,12 @@ def mpm_set_loads(h, face_traction=None, damping: float = 0.0):
     _check(h, load().mpm_set_loads(h, _dp(t), float(damping)), "mpm_set_loads")
 
 
+def mpm_set_node_coordinates(h, node_xyz):
+    """node_xyz: (nodes, dim) coordinates of a mapped mesh's nodes, x fastest."""
+    X = np.ascontiguousarray(node_xyz, np.float64)
+    _check(h, load().mpm_set_node_coordinates(h, _dp(X)), "mpm_set_node_coordinates")
+
+
 def mpm_set_scan_fault(h, withhold_chunk: int, spin_limit: int = 1 << 20):
     _check(h, load().mpm_set_scan_fault(h, int(withhold_chunk), int(spin_limit)), "mpm_set_scan_fault")
 
@@ -406,6 +413,9 @@ class Simulation:
         self.mat = make_material(**wl.material)
         self.h = mpm_create_mesh(self.desc)
         try:
+            X = getattr(wl, "node_xyz", None)
+            if X is not None:
+                mpm_set_node_coordinates(self.h, np.asarray(X)[:, : wl.dim])
             if wl.n:
                 mpm_add_particles(self.h, wl.pos, wl.vel, wl.vol, self.mat, wl.coh, stress0)
             trac = getattr(wl, "face_traction", None)

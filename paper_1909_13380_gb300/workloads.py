@@ -434,3 +434,38 @@ def terrain_column(dim=2, ncells=None, col_cells=None, h=0.005, amp=None, wavele
         face_bc=tuple(bc), face_mu=(0.0,) * 6, gravity=tuple(g), dt=1e-5, scheme=scheme, precision=precision,
         material=_mc(), pos=pos, vel=np.zeros_like(pos), vol=stretch * h ** dim / (1 << dim),
         steps=steps, node_xyz=X, meta=dict(amp=amp, wavelength=wavelength))
+
+
+def warp(points: np.ndarray, dim: int, h: float, amp: float = 0.2, wavelength: float = 7.0) -> np.ndarray:
+    """A smooth warp of space: coordinate k moves by amp h sin(2 pi x_j /
+    (wavelength h) + 0.7 k), j the next axis; its Jacobian stays within
+    2 pi amp / wavelength of the identity, so warped cells keep their
+    orientation."""
+    p = np.array(points, np.float64)
+    out = p.copy()
+    w = 2.0 * math.pi / (wavelength * h)
+    for k in range(dim):
+        out[:, k] += amp * h * np.sin(w * p[:, (k + 1) % dim] + 0.7 * k)
+    return out
+
+
+def warped_box(ncells=(12, 10, 8), h=0.1, n=3000, seed=SEED_BASE + 51, dim=3, scheme=USL, steps=100,
+               drift=(1.0, 0.6, -0.4), name=None) -> Workload:
+    """Elastic particles scattered in a box whose nodes are moved by warp():
+    a mapped mesh of curved-sided cells.  The particles (uniform random,
+    2 cells clear of the boundary, where the mesh's piecewise-linear faces
+    depart from the warp) are moved by the same warp; they drift at `drift`
+    m/s (about a cell per 100 steps) plus a small random velocity, with a
+    random initial stress (meta["stress0"]); a soft solid (E = 10 kPa: the
+    elastic wave crosses a cell in several steps), free faces, no gravity."""
+    ncells = tuple(ncells[:dim])
+    pos, vel, sig, vol = random_particles(ncells, h, n, seed, dim=dim, margin=2, vel_scale=0.05, sig_scale=10.0)
+    pos = warp(pos, dim, h)
+    vel = vel + np.asarray(drift[:dim])
+    X = warp(cartesian_node_xyz(ncells + (1,) * (3 - dim), h, (0.0, 0.0, 0.0), dim), dim, h)
+    nm = name or f"warped_box_{dim}d_" + "x".join(str(c) for c in ncells)
+    return Workload(
+        name=nm, dim=dim, ncells=ncells + (1,) * (3 - dim), h=h, origin=(0.0, 0.0, 0.0), face_bc=(FREE,) * 6,
+        face_mu=(0.0,) * 6, gravity=(0.0, 0.0, 0.0), dt=1e-3, scheme=scheme, precision=FP64_PLAIN,
+        material=dict(model=LINEAR_ELASTIC, E=1e4, nu=0.3, rho=1000.0, phi=0.0, c=0.0, psi=0.0),
+        pos=pos, vel=vel, vol=vol, steps=steps, node_xyz=X, meta=dict(stress0=sig))

@@ -1,0 +1,190 @@
+"""The mapped (isoparametric) FP64 path on the GPU (ISOPARAMETRIC MESH)
+against the oracle, through the C-ABI, on the same seeded inputs:
+
+  * initial cells: the device walk from the Cartesian guess finds the
+    oracle's cell for every particle (bit-exact cell ids);
+  * a terrain-following granular column (2D and 3D, USF and USL), a warped
+    box whose particles all cross cells, and a column turned rigidly in
+    space: state within the FP64 bar (1e-9 relative L2) after the run,
+    cells identical;
+  * nodes on the Cartesian grid: the mapped path equals the Cartesian one;
+  * particles leaving the mapped mesh, and the entry point's error cases.
+"""
+from dataclasses import replace
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1909_13380_gb300 import workloads as W
+from tests import helpers as H
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - collected only with -m gpu on a GPU machine
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1909_13380_gb300 import mpm  # noqa: E402
+
+
+def stress0(wl):
+    return wl.meta.get("stress0") if wl.meta else None
+
+
+def run_gpu(wl, steps):
+    with mpm.Simulation(wl, stress0=stress0(wl)) as sim:
+        if steps:
+            sim.step(steps)
+        return sim.read()
+
+
+def run_oracle(wl, steps):
+    o = oracle.from_workload(wl)
+    s0 = stress0(wl)
+    if s0 is not None:
+        o.state.sig[:] = s0
+    st = o.step(steps) if steps else oracle.OK
+    return o, H.oracle_snapshot(o, wl.dim), st
+
+
+def assert_cells(gpu, ref):
+    assert np.array_equal(gpu["cell"], ref["cell"])
+
+
+def check_run(wl, steps):
+    _, start, _ = run_oracle(wl, 0)
+    gpu, st = run_gpu(wl, steps)
+    o, ref, rst = run_oracle(wl, steps)
+    assert st == mpm.MPM_OK and rst == oracle.OK
+    err = H.compare(gpu, ref, start, wl.dim)
+    assert max(err.values()) <= H.TOL_RUN_FP64, err
+    pp = H.per_particle(gpu, ref, start)
+    assert max(pp.values()) <= 1e-7, pp
+    assert_cells(gpu, ref)
+    return gpu, ref, start
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_initial_cells_match_the_oracle(dim):
+    for wl in (W.terrain_column(dim), W.warped_box(dim=dim)):
+        gpu, st = run_gpu(wl, 0)
+        _, ref, _ = run_oracle(wl, 0)
+        assert st == mpm.MPM_OK
+        assert np.all(gpu["cell"] >= 0)
+        assert_cells(gpu, ref)
+
+
+@pytest.mark.parametrize("scheme", [W.USL, W.USF])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_terrain_column(dim, scheme):
+    wl = W.terrain_column(dim, scheme=scheme)
+    gpu, ref, start = check_run(wl, 400)
+    # the column has started to slump over the bumps
+    assert np.mean(gpu["vel"][:, dim - 1]) < 0.0
+
+
+@pytest.mark.parametrize("scheme", [W.USL, W.USF])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_warped_box_particles_cross_cells(dim, scheme):
+    wl = W.warped_box(dim=dim, scheme=scheme)
+    gpu0, _ = run_gpu(wl, 0)
+    gpu, ref, start = check_run(wl, 100)
+    moved = gpu["cell"] != gpu0["cell"]
+    assert moved.mean() > 0.9
+
+
+def test_rotated_column():
+    wl = W.column3d(ncells=(10, 6, 10), col_cells=(4, 3, 5), h=0.01, precision=W.FP64_PLAIN, scheme=W.USL)
+    bc = [W.FREE] * 6
+    bc[4] = W.FIXED
+    wl = replace(wl, face_bc=tuple(bc), face_mu=(0.0,) * 6)
+    R = W.rotation(3, (0.3, -0.4, 0.7))
+    check_run(W.rotated(wl, R), 200)
+
+
+@pytest.mark.parametrize("scheme", [W.USL, W.USF])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_cartesian_nodes_equal_the_cartesian_path(dim, scheme):
+    if dim == 2:
+        wl = W.column2d(6, 8, h=0.01, precision=W.FP64_PLAIN, scheme=scheme, mesh_cells=(14, 12))
+    else:
+        wl = H.small_column(precision=W.FP64_PLAIN, scheme=scheme)
+    mapped = replace(wl, node_xyz=W.cartesian_node_xyz(wl.ncells, wl.h, wl.origin, dim))
+    a, sa = run_gpu(wl, 150)
+    b, sb = run_gpu(mapped, 150)
+    assert sa == sb == mpm.MPM_OK
+    for k in ("pos", "vel", "stress", "vol"):
+        assert H.rel_l2(b[k], a[k]) <= 1e-10, k
+    assert np.array_equal(a["cell"], b["cell"])
+
+
+def test_particles_leave_the_mapped_mesh():
+    wl = W.warped_box(dim=3)
+    vel = wl.vel.copy()
+    vel[:40, 0] = 60.0     # these cross the +x face within 100 steps
+    wl = replace(wl, vel=vel)
+    gpu, st = run_gpu(wl, 100)
+    o, ref, rst = run_oracle(wl, 100)
+    assert st == mpm.MPM_ERR_LEFT_MESH and rst == oracle.LEFT_MESH
+    gone = gpu["cell"] < 0
+    assert 0 < gone.sum() <= 40
+    assert np.array_equal(gone, ref["cell"] < 0)
+    assert np.all(np.isnan(gpu["pos"][gone]))
+
+
+def test_node_coordinate_errors():
+    wl = W.warped_box(dim=2)
+    X = np.asarray(wl.node_xyz)[:, :2]
+    # FP32 meshes have no mapped form
+    with mpm.Simulation(replace(wl, precision=W.FP32_MIXED, node_xyz=None)) as sim:
+        with pytest.raises(mpm.MPMError) as ei:
+            mpm.mpm_set_node_coordinates(sim.h, X)
+        assert ei.value.status == mpm.MPM_ERR_STATE
+    with mpm.Simulation(wl, stress0=stress0(wl)) as sim:
+        # after the first particles
+        with pytest.raises(mpm.MPMError) as ei:
+            mpm.mpm_set_node_coordinates(sim.h, X)
+        assert ei.value.status == mpm.MPM_ERR_STATE
+        # no face tractions on a mapped mesh; damping is fine
+        trac = np.zeros((6, 3))
+        trac[1, 0] = 5.0
+        with pytest.raises(mpm.MPMError) as ei:
+            mpm.mpm_set_loads(sim.h, trac, 0.0)
+        assert ei.value.status == mpm.MPM_ERR_ARG
+        mpm.mpm_set_loads(sim.h, None, 0.5)
+        # a point outside the mapped mesh rejects the whole add
+        n = mpm.mpm_num_particles(sim.h)
+        pos = wl.pos[:5].copy()
+        pos[2] = (-0.5, 0.3)
+        with pytest.raises(mpm.MPMError) as ei:
+            mpm.mpm_add_particles(sim.h, pos, wl.vel[:5], wl.vol[:5], sim.mat)
+        assert ei.value.status == mpm.MPM_ERR_ARG
+        assert mpm.mpm_num_particles(sim.h) == n
+        sim.step(2)
+        assert sim.sync() == mpm.MPM_OK
+    empty = replace(wl, pos=wl.pos[:0], vel=wl.vel[:0], vol=wl.vol[:0], node_xyz=None)
+    with mpm.Simulation(empty) as sim:
+        inverted = X.copy()
+        nx = wl.ncells[0] + 1
+        inverted[[nx + 3, nx + 4]] = inverted[[nx + 4, nx + 3]]   # swap two nodes of a row
+        for bad in (inverted, np.where(np.arange(X.size).reshape(X.shape) == 7, np.nan, X)):
+            with pytest.raises(mpm.MPMError) as ei:
+                mpm.mpm_set_node_coordinates(sim.h, bad)
+            assert ei.value.status == mpm.MPM_ERR_ARG
+        mpm.mpm_set_node_coordinates(sim.h, X)
+        assert mpm.mpm_add_particles(sim.h, wl.pos, wl.vel, wl.vol, sim.mat) == 0
+
+
+def test_locate_150k_particles_in_23k_cells():
+    """The paper's locate case (ISOPARAMETRIC MESH: 150,000 particles in a
+    mesh of 23,000 cells): a terrain mesh of 40 x 24 x 24 = 23,040 cells
+    holding about 150,000 particles; the cells equal the oracle's on a
+    sample of the particles."""
+    wl = W.terrain_column(3, ncells=(40, 24, 24), col_cells=(40, 24, 20), h=0.005)
+    assert 140_000 <= wl.n <= 160_000
+    gpu, st = run_gpu(wl, 0)
+    assert st == mpm.MPM_OK and np.all(gpu["cell"] >= 0)
+    o = oracle.from_workload(replace(wl, pos=wl.pos[::97], vel=wl.vel[::97], vol=wl.vol[::97]))
+    ref = H.oracle_snapshot(o, 3)["cell"]
+    assert np.array_equal(gpu["cell"][::97], ref)
