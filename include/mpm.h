@@ -140,8 +140,9 @@ mpm_status mpm_add_particles(mpm_handle h, int64_t n, const double *pos, const d
                              const double *stress0, int64_t *first_id);
 
 /* Mapped (isoparametric) mesh (ISOPARAMETRIC MESH: cells that follow
- * non-prismatic geometry such as a landslide's terrain), FP64_PLAIN handles
- * only, before the first mpm_add_particles (MPM_ERR_STATE otherwise).
+ * non-prismatic geometry such as a landslide's terrain), FP64_PLAIN and
+ * FP32_MIXED handles, before the first mpm_add_particles and outside a
+ * batch (MPM_ERR_STATE otherwise).
  *   node_xyz   host, (nodes, dim) row-major doubles: the coordinates of node
  *              ix + (nx+1) (iy + (ny+1) iz) -- the logical grid of
  *              mpm_mesh_desc keeps its cells, only the nodes move.  Read
@@ -150,25 +151,35 @@ mpm_status mpm_add_particles(mpm_handle h, int64_t n, const double *pos, const d
  * determinant of its map positive at each corner) and the coordinates must
  * be finite (MPM_ERR_ARG, nothing changed).  A cell is then the image of
  * [-1, 1]^dim under x(xi) = sum_a N_a(xi) X_a, and:
- *   - a particle's natural coordinates are the root of x(xi) = x, by
- *     Newton-Raphson from the inverse bilinear solution (2D) or the affine
- *     guess (3D); shape gradients are dN/dx = dN/dxi J^-1;
+ *   - a particle's natural coordinates are the root of x(xi) = x; shape
+ *     gradients are dN/dx = dN/dxi J^-1;
  *   - mpm_add_particles locates new particles by a neighbourhood walk from
  *     the Cartesian cell of desc.origin and desc.h (which serve no other
- *     purpose on a mapped mesh); a particle in no cell rejects the call
- *     (MPM_ERR_ARG, none added);
- *   - each step, after advection, the walk moves from a particle's cell to
- *     the neighbour across the face its natural coordinates leave by until
- *     they lie in [-1, 1) (xi = 1 belongs to the next cell); a particle that
- *     would leave the grid has left the mesh (MPM_ERR_LEFT_MESH);
+ *     purpose on a mapped mesh), solving for xi by Newton-Raphson from the
+ *     inverse bilinear solution (2D) or the affine guess (3D), in FP64; a
+ *     particle in no cell rejects the call (MPM_ERR_ARG, none added);
+ *   - each step, after advection, a particle moves from its cell to the
+ *     neighbour across the face its natural coordinates leave by until they
+ *     lie in [-1, 1) (xi = 1 belongs to the next cell); a particle that
+ *     would leave the grid has left the mesh (MPM_ERR_LEFT_MESH).  FP64:
+ *     the walk above from the new position.  FP32_MIXED: the offset is
+ *     xi / 2 and every cell holds its corners relative to its centre in
+ *     FP32 (rounded once from FP64); the particle's new offset is solved in
+ *     the frame of its own cell and carried into each neighbour's frame
+ *     through the node they share, at most 8 cells per step (beyond that
+ *     the particle is dropped as having left the mesh);
  *   - face conditions act along the global axes (a roller zeroes the
  *     component along its logical face's axis): exact for fixed faces and
  *     for faces that stay planes normal to that axis.  Face tractions are
  *     not defined: mpm_set_loads rejects them, and a mesh that carries them
- *     rejects this call (MPM_ERR_ARG).  Damping is allowed.
- * mpm_read_particles' cell is the walk's cell.  mpm_footprint does not
- * include the mapped storage: 24 bytes per node and 4 + 8 dim per particle.
- * Calling it again before the first particles replaces the coordinates. */
+ *     rejects this call (MPM_ERR_ARG).  Damping is allowed;
+ *   - a mapped FP32_MIXED mesh is stepped alone: mpm_batch_admit rejects it
+ *     (MPM_ERR_STATE).
+ * mpm_read_particles' position is x(xi) of the particle's cell and its cell
+ * the walk's.  mpm_footprint does not include the mapped storage: 24 bytes
+ * per node, and per particle 4 + 8 dim (FP64_PLAIN), or per cell 32 (2D) or
+ * 96 (3D) bytes (FP32_MIXED).  Calling it again before the first particles
+ * replaces the coordinates. */
 mpm_status mpm_set_node_coordinates(mpm_handle h, const double *node_xyz);
 
 /* Enqueue nsteps explicit steps on desc.stream and return without waiting.

@@ -22,6 +22,7 @@
 
 #include "../../include/mpm.h"
 #include "mpm_internal.h"
+#include "mpm_iso.cuh"
 
 using namespace mpm;
 
@@ -54,9 +55,11 @@ struct NewParticles {
 // cell = floor((x - origin) / h) and offset s - cell - 0.5 in FP64 (the same
 // IEEE operations as the oracle's locate), the offset rounded to FP32 and
 // kept inside [-0.5, 0.5); key, id, FP32 velocity, stress (zero without
-// stress0), mass = rho V, cohesion; strain, J-1 and eps_p zero.  Points
-// outside the mesh (or not finite) are counted in *bad and leave their slot
-// unwritten.
+// stress0), mass = rho V, cohesion; strain, J-1 and eps_p zero.  On a
+// mapped mesh (g.X) the cell is found by the FP64 neighbourhood walk from
+// the Cartesian cell of origin and h (clamped to the grid) and the offset is
+// half the natural coordinates there.  Points outside the mesh (or not
+// finite) are counted in *bad and leave their slot unwritten.
 template <int D>
 __global__ void init_particles_k(int64_t n, int64_t n0, PBuf P, Geo g, double o0, double o1, double o2, double h,
                                  double rho, NewParticles in, int32_t *bad) {
@@ -67,16 +70,35 @@ __global__ void init_particles_k(int64_t n, int64_t n0, PBuf P, Geo g, double o0
     int c[3] = {0, 0, 0};
     float u[3] = {0.f, 0.f, 0.f};
     bool ok = true;
+    if (g.X) {
+      double x[D], xi[D];
 #pragma unroll
-    for (int k = 0; k < D; ++k) {
-      const double sk = (in.pos[p * D + k] - org[k]) / h;
-      const double f = floor(sk);
-      ok = ok && sk >= 0.0 && f < (double)g.nc[k];
-      c[k] = ok ? (int)f : 0;
-      float uk = (float)(sk - f - 0.5);
-      if (uk >= 0.5f) uk = __int_as_float(0x3effffff);  // the float below 0.5
-      if (uk < -0.5f) uk = -0.5f;
-      u[k] = uk;
+      for (int k = 0; k < D; ++k) {
+        x[k] = in.pos[p * D + k];
+        ok = ok && isfinite(x[k]);
+        const double f = ok ? floor((x[k] - org[k]) / h) : 0.0;
+        c[k] = f < 0.0 ? 0 : (f >= (double)g.nc[k] ? g.nc[k] - 1 : (int)f);
+      }
+      ok = ok && iso::walk<D>(iso::IsoGrid{g.X, {g.nc[0], g.nc[1], g.nc[2]}}, x, c, xi);
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        float uk = ok ? (float)(0.5 * xi[k]) : 0.f;
+        if (uk >= 0.5f) uk = __int_as_float(0x3effffff);  // the float below 0.5
+        if (uk < -0.5f) uk = -0.5f;
+        u[k] = uk;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const double sk = (in.pos[p * D + k] - org[k]) / h;
+        const double f = floor(sk);
+        ok = ok && sk >= 0.0 && f < (double)g.nc[k];
+        c[k] = ok ? (int)f : 0;
+        float uk = (float)(sk - f - 0.5);
+        if (uk >= 0.5f) uk = __int_as_float(0x3effffff);  // the float below 0.5
+        if (uk < -0.5f) uk = -0.5f;
+        u[k] = uk;
+      }
     }
     if (!ok) {
       atomicAdd(bad, 1);
@@ -172,7 +194,7 @@ struct mpm_ctx {
   std::string err;
   mpm_status sticky = MPM_OK;
   // FP32 mixed
-  Geo geo;
+  Geo geo{};
   int key_bits = 1;
   int64_t nnodes = 0;
   void *bufmem[2] = {nullptr, nullptr};
@@ -198,6 +220,7 @@ struct mpm_ctx {
   void *pmem64 = nullptr;
   void *nmem64 = nullptr;
   double *X64 = nullptr;  // mapped mesh: node coordinates, 3 per node (mpm_set_node_coordinates)
+  float4 *cgeo32 = nullptr;  // mapped FP32 mesh: corner positions per cell (Geo::cgeo)
   // shared
   int32_t *d_status = nullptr;  // FP64 path status word (FP32 path: s.ctr[C_STATUS])
   double *d_cons = nullptr;     // 8 results + partials
@@ -453,6 +476,7 @@ cudaError_t build_group(GroupDev &g, const std::vector<mpm_ctx *> &mem, bool rel
     int max_m = 0;
     for (int i = 0; i < n; ++i) max_m = std::max(max_m, mem[i]->geo.ntiles + 1);
     G.scan_one = max_m <= SCAN1_MAX ? 1 : 0;
+    G.mapped = (n == 1 && mem[0]->geo.cgeo) ? 1 : 0;  // mapped meshes are never batched
     int64_t np = 0;
     for (int i = 0; i < n; ++i) np += mem[i]->n;
     G.bin_t = np >= ((int64_t)1 << 22) ? 128 : 256;
@@ -1135,7 +1159,7 @@ mpm_status mpm_set_loads(mpm_handle h, const double *face_traction, double dampi
 mpm_status mpm_set_node_coordinates(mpm_handle h, const double *node_xyz) {
   mpm_status s0 = check_handle(h);
   if (s0 != MPM_OK) return s0;
-  if (h->d.precision != MPM_FP64_PLAIN) return fail(h, MPM_ERR_STATE, "node coordinates: FP64_PLAIN meshes only");
+  if (h->batch) return fail(h, MPM_ERR_STATE, "node coordinates: the mesh is admitted to a batch");
   if (h->n > 0) return fail(h, MPM_ERR_STATE, "node coordinates: set before the first particles");
   if (!node_xyz) return fail(h, MPM_ERR_ARG, "node coordinates: null");
   for (int f = 0; f < 6; ++f)
@@ -1180,16 +1204,51 @@ mpm_status mpm_set_node_coordinates(mpm_handle h, const double *node_xyz) {
                   e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0]);
           if (!(det > 0.0)) return fail(h, MPM_ERR_ARG, "node coordinates: a cell is degenerate or inverted");
         }
+  // FP32 path: per cell the corners relative to the cell's centre, in units
+  // of h, computed in FP64 and rounded once (Geo::cgeo)
+  std::vector<float4> cg;
+  if (h->d.precision == MPM_FP32_MIXED) {
+    const int nf = D == 3 ? CGEO_F4<3>() : CGEO_F4<2>();
+    const int64_t ncx = h->d.ncells[0], ncy = h->d.ncells[1], ncz = D == 3 ? h->d.ncells[2] : 1;
+    cg.assign((size_t)(ncx * ncy * ncz * nf), make_float4(0.f, 0.f, 0.f, 0.f));
+    for (int64_t k = 0; k < ncz; ++k)
+      for (int64_t j = 0; j < ncy; ++j)
+        for (int64_t i = 0; i < ncx; ++i) {
+          double ctr[3] = {0.0, 0.0, 0.0}, xa[8][3];
+          for (int a = 0; a < (1 << D); ++a)
+            for (int c = 0; c < D; ++c) {
+              xa[a][c] = at(i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1), c);
+              ctr[c] += xa[a][c];
+            }
+          float f[24] = {};
+          for (int a = 0; a < (1 << D); ++a)
+            for (int c = 0; c < D; ++c) f[D * a + c] = (float)((xa[a][c] - ctr[c] / (1 << D)) / h->d.h);
+          float4 *dst = &cg[(size_t)((i + ncx * (j + ncy * k)) * nf)];
+          for (int m = 0; m < nf; ++m) dst[m] = make_float4(f[4 * m], f[4 * m + 1], f[4 * m + 2], f[4 * m + 3]);
+        }
+  }
   double *dX = nullptr;
+  float4 *dG = nullptr;
   CK(cudaStreamSynchronize(h->st), "node coordinates");
   CK(cudaMalloc(&dX, sizeof(double) * 3 * nn), "node coordinates");
   cudaError_t e = cudaMemcpy(dX, X3.data(), sizeof(double) * 3 * nn, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !cg.empty()) {
+    e = cudaMalloc(&dG, sizeof(float4) * cg.size());
+    if (e == cudaSuccess) e = cudaMemcpy(dG, cg.data(), sizeof(float4) * cg.size(), cudaMemcpyHostToDevice);
+  }
   if (e != cudaSuccess) {
     cudaFree(dX);
+    if (dG) cudaFree(dG);
     return cuda_fail(h, e, "node coordinates");
   }
   if (h->X64) cudaFree(h->X64);
+  if (h->cgeo32) cudaFree(h->cgeo32);
   h->X64 = dX;
+  h->cgeo32 = dG;
+  h->geo.X = h->d.precision == MPM_FP32_MIXED ? dX : nullptr;
+  h->geo.cgeo = dG;
+  destroy_graphs(h->graph);  // the instance (and its geometry) is captured in the step graph
+  h->grp_valid = false;
   return MPM_OK;
 }
 
@@ -1236,7 +1295,7 @@ mpm_status mpm_destroy(mpm_handle h) {
                   S.out_cnt, S.bucket_start, S.bucket_fill, S.movers, S.bucket, S.bucket_sorted, S.active,
                   S.bin_rec, S.scan_tot, S.ctr, S.slots1, S.slots2, S.slots_a, S.fepoch, S.aepoch, S.resid, S.node,
                   h->keys2, h->perm2, h->sort_scratch,
-                  h->pmem64, h->nmem64, h->X64, h->d_status, h->d_cons};
+                  h->pmem64, h->nmem64, h->X64, h->cgeo32, h->d_status, h->d_cons};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (int i = 0; i <= MPM_MAX_PHASES; ++i)
@@ -1277,6 +1336,7 @@ mpm_status mpm_batch_admit(mpm_batch b, mpm_handle h, int32_t *slot) {
   if (s0 != MPM_OK) return s0;
   if (h->d.precision != MPM_FP32_MIXED) return fail(h, MPM_ERR_ARG, "batch: FP32_MIXED meshes only");
   if (h->batch) return fail(h, MPM_ERR_STATE, "batch: the mesh is already admitted to a batch");
+  if (h->geo.cgeo) return fail(h, MPM_ERR_STATE, "batch: mapped meshes are stepped alone");
   // room: a free slot, and the mesh's footprint within what the budget has left
   int s = -1;
   for (size_t i = 0; i < b->slots.size(); ++i)

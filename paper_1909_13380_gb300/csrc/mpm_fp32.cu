@@ -30,6 +30,7 @@
 #include <stdint.h>
 
 #include "mpm_internal.h"
+#include "mpm_iso.cuh"
 
 namespace mpm {
 namespace {
@@ -143,6 +144,118 @@ struct ThreadCorners {
 };
 
 // ---------------------------------------------------------------------------
+// Mapped (isoparametric) cells (ISOPARAMETRIC MESH) in the FP32 path.  A
+// particle's offset u is half its natural coordinates (u in [-0.5, 0.5)^D);
+// relative to the cell's centre and in units of h the cell maps u to
+// x(u) = sum_a N_a(u) P_a, P_a its corners (Geo::cgeo), with Jacobian
+// J = dx/du = sum_a P_a (x) dN_a/du.  A shape gradient is then
+// dN_a/dx = (dN_a/du K) / h with K = J^-1, so the transfers run the
+// Cartesian arithmetic on dN/du and multiply by K once per particle.  Every
+// position is kept in the frame of the particle's own cell, so FP32 resolves
+// it as finely as the Cartesian offset does.
+// ---------------------------------------------------------------------------
+template <int D>
+__device__ __forceinline__ int cell_lin(const Geo &g, const int c[3]) {
+  return c[0] + g.nc[0] * (c[1] + g.nc[1] * (D == 3 ? c[2] : 0));
+}
+
+template <int D>
+__device__ __forceinline__ void load_cgeo(const Geo &g, int cid, float P[1 << D][D]) {
+  constexpr int NF = CGEO_F4<D>();
+  float f[4 * NF];
+#pragma unroll
+  for (int m = 0; m < NF; ++m) {
+    const float4 q = __ldg(g.cgeo + (int64_t)NF * cid + m);
+    f[4 * m] = q.x;
+    f[4 * m + 1] = q.y;
+    f[4 * m + 2] = q.z;
+    f[4 * m + 3] = q.w;
+  }
+#pragma unroll
+  for (int a = 0; a < (1 << D); ++a)
+#pragma unroll
+    for (int k = 0; k < D; ++k) P[a][k] = f[D * a + k];
+}
+
+// x(u) and J(u) of a mapped cell.
+template <int D>
+__device__ __forceinline__ void cgeo_map(const float P[1 << D][D], const float u[D], float x[D], float J[D][D]) {
+  float w0[D], w1[D];
+  corner_weights<D>(u, w0, w1);
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    x[k] = 0.f;
+#pragma unroll
+    for (int m = 0; m < D; ++m) J[k][m] = 0.f;
+  }
+#pragma unroll
+  for (int a = 0; a < (1 << D); ++a) {
+    float N, G[D];
+    corner_shape<D>(a, w0, w1, 1.f, N, G);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      x[k] = fmaf(N, P[a][k], x[k]);
+#pragma unroll
+      for (int m = 0; m < D; ++m) J[k][m] = fmaf(P[a][k], G[m], J[k][m]);
+    }
+  }
+}
+
+// K = J^-1 by cofactors; false if J is singular or not finite.
+template <int D>
+__device__ __forceinline__ bool inv_jac(const float J[D][D], float K[D][D]) {
+  if constexpr (D == 2) {
+    const float det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    if (!(fabsf(det) > 0.f) || !isfinite(det)) return false;
+    const float r = 1.f / det;
+    K[0][0] = J[1][1] * r;
+    K[0][1] = -J[0][1] * r;
+    K[1][0] = -J[1][0] * r;
+    K[1][1] = J[0][0] * r;
+  } else {
+    float C[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const int i1 = (i + 1) % 3, i2 = (i + 2) % 3, j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+        C[i][j] = J[i1][j1] * J[i2][j2] - J[i1][j2] * J[i2][j1];
+      }
+    const float det = J[0][0] * C[0][0] + J[0][1] * C[0][1] + J[0][2] * C[0][2];
+    if (!(fabsf(det) > 0.f) || !isfinite(det)) return false;
+    const float r = 1.f / det;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) K[i][j] = C[j][i] * r;
+  }
+  return true;
+}
+
+// Newton-Raphson in one cell for the offset whose image is T (the cell's
+// frame), from un: at most 8 iterations, until a step is below 1e-7 cell.
+template <int D>
+__device__ __forceinline__ void cgeo_solve(const float P[1 << D][D], const float T[D], float un[D]) {
+  for (int it = 0; it < 8; ++it) {
+    float x[D], J[D][D], K[D][D];
+    cgeo_map<D>(P, un, x, J);
+    if (!inv_jac<D>(J, K)) return;
+    float r[D], st = 0.f;
+#pragma unroll
+    for (int k = 0; k < D; ++k) r[k] = x[k] - T[k];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      float d = 0.f;
+#pragma unroll
+      for (int m = 0; m < D; ++m) d = fmaf(K[k][m], r[m], d);
+      un[k] -= d;
+      st = fmaxf(st, fabsf(d));
+    }
+    if (!(st > 1e-7f)) return;  // converged, or not finite (the caller checks)
+  }
+}
+
+// ---------------------------------------------------------------------------
 // P2G: one CTA per tile; each thread owns CPT corners of one cell (3D: two
 // corners, 256 threads; 2D: one corner, 256 threads).  The tile's particles
 // (binning order, so grouped by cell) are staged in shared memory in chunks
@@ -156,10 +269,12 @@ struct ThreadCorners {
 // Value index v = corner * NCH + channel; channels USL (m, P_k, f_k), MOM
 // (m, P_k), FORCE (f_k).
 // ---------------------------------------------------------------------------
-template <int D, int MODE>
+template <int D, int MODE, bool MAP = false>
 struct P2GRec {
   static constexpr bool HAS_M = MODE != P2G_FORCE, HAS_F = MODE != P2G_MOM;
-  static constexpr int NSV = D == 3 ? 6 : 3;                   // nV sig (xx yy zz xy yz xz | xx yy xy)
+  // nV sig (xx yy zz xy yz xz | xx yy xy); on a mapped mesh the full D x D
+  // matrix nV sig K^T (row-major), K the inverse of the cell map's Jacobian
+  static constexpr int NSV = MAP ? D * D : (D == 3 ? 6 : 3);
   static constexpr int NF = D + (HAS_M ? 1 + D : 0) + (HAS_F ? NSV : 0);
   static constexpr int NQ = (NF + 3) / 4;                      // float4 chunks per particle
   static constexpr int CPT = D == 3 ? 2 : 1;                   // corners per thread
@@ -318,10 +433,10 @@ __device__ __forceinline__ void cells_to_slot(const float *cellP, float *slots_o
   }
 }
 
-template <int D, int MODE, bool ONE>
-__global__ void __launch_bounds__(P2GRec<D, MODE>::CH, p2g_min_blocks<D, MODE, ONE>())
+template <int D, int MODE, bool ONE, bool MAP = false>
+__global__ void __launch_bounds__(P2GRec<D, MODE>::CH, MAP ? 4 : p2g_min_blocks<D, MODE, ONE>())
     p2g_tile(const __grid_constant__ GroupArgs G, int work_slot) {
-  using R = P2GRec<D, MODE>;
+  using R = P2GRec<D, MODE, MAP>;
   constexpr int NCH = p2g_channels<D, MODE>();
   constexpr int NV = R::NV;
   constexpr int CH = R::CH;
@@ -364,6 +479,8 @@ __global__ void __launch_bounds__(P2GRec<D, MODE>::CH, p2g_min_blocks<D, MODE, O
     float *slots_out = MODE == P2G_FORCE ? I.s.slots2 : I.s.slots1;
     const int4 ar = I.s.active[ONE ? wi : wi - G.act_items[ii]];
     const int t = ar.x, s = ar.y, e = ar.z;
+    int tco[3] = {0, 0, 0};
+    if (MAP) tile_coords(g, t, tco);
     float acc[CPT][NCH];
 #pragma unroll
     for (int r = 0; r < CPT; ++r)
@@ -395,7 +512,46 @@ __global__ void __launch_bounds__(P2GRec<D, MODE>::CH, p2g_min_blocks<D, MODE, O
           const int js = (MODE == P2G_FORCE) ? q : j;
           const float nV = -mm * g.inv_rho * (1.f + S.jm1()[js]);
           constexpr int o = HAS_M ? 2 * D + 1 : D;
-          if (D == 3) {
+          if constexpr (MAP) {
+            // nV sig K^T at the particle's offset, K = J^-1 of its cell's map
+            int l3[3], cc[3];
+            local_coords<D>((uint32_t)lc, l3);
+            cc[0] = tco[0] * TX + l3[0];
+            cc[1] = tco[1] * TY + l3[1];
+            cc[2] = D == 3 ? tco[2] * TZ + l3[2] : 0;
+            float P[1 << D][D], xl[D], J[D][D], K[D][D];
+            load_cgeo<D>(g, cell_lin<D>(g, cc), P);
+            cgeo_map<D>(P, f, xl, J);
+            if (!inv_jac<D>(J, K)) {
+#pragma unroll
+              for (int a = 0; a < D; ++a)
+#pragma unroll
+                for (int b = 0; b < D; ++b) K[a][b] = 0.f;
+            }
+            float sm[D][D];
+            if (D == 3) {
+              const float s0 = S.sig(0)[js], s1 = S.sig(1)[js], s2 = S.sig(2)[js];
+              const float s3 = S.sig(3)[js], s4 = S.sig(4)[js], s5 = S.sig(5)[js];
+              const float t3[3][3] = {{s0, s3, s5}, {s3, s1, s4}, {s5, s4, s2}};
+#pragma unroll
+              for (int a = 0; a < D; ++a)
+#pragma unroll
+                for (int b = 0; b < D; ++b) sm[a][b] = t3[a][b];
+            } else {
+              sm[0][0] = S.sig(0)[js];
+              sm[1][1] = S.sig(1)[js];
+              sm[0][1] = sm[1][0] = S.sig(3)[js];
+            }
+#pragma unroll
+            for (int k = 0; k < D; ++k)
+#pragma unroll
+              for (int m = 0; m < D; ++m) {
+                float acc_km = 0.f;
+#pragma unroll
+                for (int jj = 0; jj < D; ++jj) acc_km = fmaf(sm[k][jj], K[m][jj], acc_km);
+                f[o + D * k + m] = nV * acc_km;
+              }
+          } else if (D == 3) {
 #pragma unroll
             for (int k = 0; k < 6; ++k) f[o + k] = nV * S.sig(k)[js];
           } else {
@@ -445,7 +601,12 @@ __global__ void __launch_bounds__(P2GRec<D, MODE>::CH, p2g_min_blocks<D, MODE, O
             if (HAS_F) {
               constexpr int o = HAS_M ? 2 * D + 1 : D;
               constexpr int a0 = HAS_M ? 1 + D : 0;
-              if (D == 3) {
+              if constexpr (MAP) {
+#pragma unroll
+                for (int k = 0; k < D; ++k)
+#pragma unroll
+                  for (int m = 0; m < D; ++m) acc[r][a0 + k] = fmaf(f[o + D * k + m], Gr[m], acc[r][a0 + k]);
+              } else if (D == 3) {
                 // nV sig: xx yy zz xy yz xz
                 const float t3[3][3] = {{f[o], f[o + 3], f[o + 5]}, {f[o + 3], f[o + 1], f[o + 4]},
                                         {f[o + 5], f[o + 4], f[o + 2]}};
@@ -943,8 +1104,8 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // they land while the node gather runs, and the thread waits only on its own
 // copies.
 // ---------------------------------------------------------------------------
-template <int D, int GMODE, bool ONE>
-__global__ void __launch_bounds__(G2P_T, MPM_G2P_MINB) g2p(const __grid_constant__ GroupArgs G) {
+template <int D, int GMODE, bool ONE, bool MAP = false>
+__global__ void __launch_bounds__(G2P_T, MAP ? 4 : MPM_G2P_MINB) g2p(const __grid_constant__ GroupArgs G) {
   constexpr int NC = 1 << D;
   constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ;
   constexpr int NS = nstress<D>();
@@ -1022,6 +1183,21 @@ __global__ void __launch_bounds__(G2P_T, MPM_G2P_MINB) g2p(const __grid_constant
 #pragma unroll
   for (int k = 0; k < D; ++k) u[k] = I.A.off(k)[j];
   corner_weights<D>(u, w0, w1);
+  // mapped cell: its corners, the image of u and K = J^-1 at u
+  float Pc[1 << D][D], K[D][D], xl[D];
+  bool bad_cell = false;
+  if constexpr (MAP) {
+    float J[D][D];
+    load_cgeo<D>(g, cell_lin<D>(g, cell), Pc);
+    cgeo_map<D>(Pc, u, xl, J);
+    if (!inv_jac<D>(J, K)) {
+      bad_cell = true;
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = 0; b < D; ++b) K[a][b] = 0.f;
+    }
+  }
   float dv[D], vb[D], L[D][D];
 #pragma unroll
   for (int k = 0; k < D; ++k) {
@@ -1088,6 +1264,23 @@ __global__ void __launch_bounds__(G2P_T, MPM_G2P_MINB) g2p(const __grid_constant
     }
   }
 
+  if constexpr (MAP) {  // velocity gradient: (sum_a v_a (x) dN_a/du) K / h
+    float Lm[D][D];
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+#pragma unroll
+      for (int l = 0; l < D; ++l) {
+        float sacc = 0.f;
+#pragma unroll
+        for (int m = 0; m < D; ++m) sacc = fmaf(L[k][m], K[m][l], sacc);
+        Lm[k][l] = sacc;
+      }
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+#pragma unroll
+      for (int l = 0; l < D; ++l) L[k][l] = Lm[k][l];
+  }
+
   // Every load of the particle's state is issued before the first store: the
   // compiler cannot tell A from B, so a load placed after a store would wait
   // for the value before it (one memory latency per field).
@@ -1113,12 +1306,81 @@ __global__ void __launch_bounds__(G2P_T, MPM_G2P_MINB) g2p(const __grid_constant
     epsp = stg[2 * NS + 1][threadIdx.x];
   }
 
-  int status = 0;
+  int status = bad_cell ? ST_NONFINITE : 0;
   // FLIP velocity, advection in cell units, relocation
   if (KIN) {
     bool dead = false;
+    if constexpr (MAP) {
+      // the target x(u) + dt vb / h in the cell's frame; Newton from the
+      // step K dt vb / h; a solution outside [-0.5, 0.5) moves to the
+      // neighbour across the face of the largest excess, the target into the
+      // neighbour's frame (the shared node seen from both centres), and
+      // solves again -- at most 8 cells per step
+      float T[D], un[D];
 #pragma unroll
-    for (int k = 0; k < D; ++k) {
+      for (int k = 0; k < D; ++k) {
+        const float vk = v0[k] + g.dt * dv[k];
+        I.B.vel(k)[q] = vk;
+        if (!isfinite(vk)) status |= ST_NONFINITE;
+        T[k] = g.dt * vb[k] * g.inv_h;
+      }
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        float d = 0.f;
+#pragma unroll
+        for (int m = 0; m < D; ++m) d = fmaf(K[k][m], T[m], d);
+        un[k] = u[k] + d;
+      }
+#pragma unroll
+      for (int k = 0; k < D; ++k) T[k] += xl[k];
+      bool found = false;
+      for (int hop = 0; hop < 8; ++hop) {
+        cgeo_solve<D>(Pc, T, un);
+        bool fin = true;
+#pragma unroll
+        for (int k = 0; k < D; ++k) fin = fin && isfinite(un[k]);
+        if (!fin) {
+          status |= ST_NONFINITE;
+          dead = true;
+          break;
+        }
+        int best = -1;
+        float ex = -1.f;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          const float e = un[k] >= 0.5f ? un[k] - 0.5f : (un[k] < -0.5f ? -0.5f - un[k] : -1.f);
+          if (e >= 0.f && e > ex) {
+            ex = e;
+            best = k;
+          }
+        }
+        if (best < 0) {
+          found = true;
+          break;
+        }
+        const int sgn = un[best] >= 0.5f ? 1 : -1;
+        cell[best] += sgn;
+        if (cell[best] < 0 || cell[best] >= g.nc[best]) {
+          dead = true;
+          break;
+        }
+        float Pn[1 << D][D];
+        load_cgeo<D>(g, cell_lin<D>(g, cell), Pn);
+        const int ao = sgn > 0 ? (1 << best) : 0, an = sgn > 0 ? 0 : (1 << best);
+#pragma unroll
+        for (int k = 0; k < D; ++k) T[k] -= Pc[ao][k] - Pn[an][k];
+        un[best] -= (float)sgn;
+#pragma unroll
+        for (int a = 0; a < (1 << D); ++a)
+#pragma unroll
+          for (int k = 0; k < D; ++k) Pc[a][k] = Pn[a][k];
+      }
+      if (!found) dead = true;
+#pragma unroll
+      for (int k = 0; k < D; ++k) I.B.off(k)[q] = dead ? 0.f : un[k];
+    }
+#pragma unroll
+    for (int k = 0; k < (MAP ? 0 : D); ++k) {
       const float vk = v0[k] + g.dt * dv[k];
       I.B.vel(k)[q] = vk;
       if (!isfinite(vk)) status |= ST_NONFINITE;
@@ -1665,10 +1927,16 @@ cudaError_t launch_p2g(const GroupArgs &G, int work_slot, cudaStream_t st) {
                                      st, G, work_slot)
                         : launch_dep(p2g_resid<D, MODE, false, true>, G.grid, p2g_threads<D>(), p2g_smem<D, MODE>(),
                                      st, G, work_slot);
-  else
+  else {
+    // a mapped mesh (always a group of one) needs K only for the force
+    if constexpr (MODE != P2G_MOM)
+      if (G.mapped)
+        return launch_dep(p2g_tile<D, MODE, true, true>, G.grid, p2g_threads<D>(), P2GRec<D, MODE, true>::SMEM, st,
+                          G, work_slot);
     return G.ninst == 1
                ? launch_dep(p2g_tile<D, MODE, true>, G.grid, p2g_threads<D>(), p2g_smem<D, MODE>(), st, G, work_slot)
                : launch_dep(p2g_tile<D, MODE, false>, G.grid, p2g_threads<D>(), p2g_smem<D, MODE>(), st, G, work_slot);
+  }
 }
 
 template <int D, int MODE, bool RES = false>
@@ -1684,6 +1952,11 @@ cudaError_t prepare_p2g() {
   e = cudaFuncSetAttribute(p2g_tile<D, MODE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)p2g_smem<D, MODE>());
   if (e != cudaSuccess) return e;
+  if constexpr (MODE != P2G_MOM) {
+    e = cudaFuncSetAttribute(p2g_tile<D, MODE, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)P2GRec<D, MODE, true>::SMEM);
+    if (e != cudaSuccess) return e;
+  }
   return cudaFuncSetAttribute(p2g_tile<D, MODE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)p2g_smem<D, MODE>());
 }
@@ -1715,8 +1988,9 @@ cudaError_t launch_node(const GroupArgs &G, int work_slot, cudaStream_t st) {
 template <int D, int GMODE>
 cudaError_t launch_g2p(const GroupArgs &G, cudaStream_t st) {
   const int nb = G.nblk_p * G2P_SUB;
-  cudaError_t e = G.ninst == 1 ? launch_dep(g2p<D, GMODE, true>, nb, G2P_T, 0, st, G)
-                               : launch_dep(g2p<D, GMODE, false>, nb, G2P_T, 0, st, G);
+  cudaError_t e = G.mapped         ? launch_dep(g2p<D, GMODE, true, true>, nb, G2P_T, 0, st, G)
+                  : G.ninst == 1 ? launch_dep(g2p<D, GMODE, true>, nb, G2P_T, 0, st, G)
+                                 : launch_dep(g2p<D, GMODE, false>, nb, G2P_T, 0, st, G);
   if (e != cudaSuccess || !G.apex || GMODE == G2P_USF_ADVECT) return e;
   return G.ninst == 1 ? launch_dep(apex_band_k<D, true>, G.grid / 8, APEX_T, 0, st, G)
                       : launch_dep(apex_band_k<D, false>, G.grid / 8, APEX_T, 0, st, G);
@@ -1831,11 +2105,21 @@ __global__ void export_k(int64_t n, PBuf P, Geo g, double o0, double o1, double 
       c[1] = tc[1] * TY + lc[1];
       c[2] = D == 3 ? tc[2] * TZ + lc[2] : 0;
     }
-    if (pos)
+    if (pos && g.X && !dead) {  // mapped: x(xi) of the cell, xi = 2 off
+      double xi[D], xa[1 << D][D], x[D], J[D][D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) xi[k] = 2.0 * (double)P.off(k)[q];
+      const iso::IsoGrid M{g.X, {g.nc[0], g.nc[1], g.nc[2]}};
+      iso::cell_xyz<D>(M, c, xa);
+      iso::cell_map<D>(xa, xi, x, J);
+#pragma unroll
+      for (int k = 0; k < D; ++k) pos[id * D + k] = x[k];
+    } else if (pos) {
 #pragma unroll
       for (int k = 0; k < D; ++k)
         pos[id * D + k] = dead ? __longlong_as_double(0x7ff8000000000000ll)
                                : org[k] + ((double)c[k] + 0.5 + (double)P.off(k)[q]) * h;
+    }
     if (vel)
 #pragma unroll
       for (int k = 0; k < D; ++k) vel[id * D + k] = P.vel(k)[q];

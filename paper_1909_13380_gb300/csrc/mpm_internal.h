@@ -100,7 +100,16 @@ struct Geo {
   int loads;           // face tractions or damping present (mpm_set_loads)
   float damp;          // alpha of a = f / m - alpha v
   float trac[6][3];    // traction per face
+  // Mapped (isoparametric) mesh, else both null (ISOPARAMETRIC MESH).  cgeo:
+  // per cell (id cx + nc0 (cy + nc1 cz)) the positions of its 2^D corners
+  // relative to the cell's centre, in units of h, corner a's component k at
+  // float D a + k of the cell's CGEO_F4<D> float4s.  The offset of a particle
+  // is then half its natural coordinates, u = xi / 2.  X: the FP64 node
+  // coordinates (3 per node) for the initial location and the export.
+  const float4 *cgeo;
+  const double *X;
 };
+template <int D> constexpr int CGEO_F4() { return D == 3 ? 6 : 2; }
 
 // Counters of a step (int32, in StepBufs::ctr).
 enum {
@@ -240,6 +249,7 @@ struct GroupArgs {
   int grid;                 // CTAs of the per-tile kernels
   int apex;                 // some instance can reach the FP64 apex band (cohesion > 0): run apex_band_k
   int bin_t;                // bin_tiles threads per CTA: 128 for groups of >= 4M particles, else 256
+  int mapped;               // the instances have mapped cells (Geo::cgeo; a group of one)
   InstArgs one;             // a group of one: its table entry (inst[0]) by value
 };
 
@@ -315,6 +325,8 @@ cudaError_t f32_group_step(int dim, int scheme, const GroupArgs &G, cudaEvent_t 
 cudaError_t gather_status(const InstArgs *tab, int ninst, int32_t *out, cudaStream_t st);
 cudaError_t f32_conservation(int dim, int64_t n, const PBuf &P, uint32_t dead_key, float inv_rho,
                              double *d_out, double *d_partials, cudaStream_t st);
+// Positions: origin + (cell + 0.5 + off) h, or on a mapped mesh (g.X) the
+// map of the cell at natural coordinates 2 off, in FP64.
 cudaError_t f32_export(int dim, int64_t n, const PBuf &P, const Geo &g, const double origin[3], double h,
                        double rho, double *pos, double *vel, double *sig, double *eps, double *vol,
                        double *epsp, int64_t *cell, cudaStream_t st);

@@ -137,17 +137,18 @@ def per_particle(gpu, ref, start):
 OFFSET_ROUNDING_CELLS = 2.0 ** -26
 
 
-def disp_excess(gpu, ref, start, h, steps, dim, rel=TOL_RUN_FP32):
+def disp_excess(gpu, ref, start, h, steps, dim, rel=TOL_RUN_FP32, unit=None):
     """Per-particle displacement error beyond what the FP32 offset can
     resolve: the largest of |d_gpu - d_ref| / (rel * rms(d_ref) + floor)
-    over the live particles, with floor = (steps + 1) * 2 * 2^-26 h sqrt(dim)
-    (the rounding of the initial offset and of every step's, twice over).
-    Values <= 1 pass."""
+    over the live particles, with floor = (steps + 1) * 2 * unit h sqrt(dim)
+    (the rounding of the initial offset and of every step's, twice over;
+    unit = 2^-26 cell for the Cartesian offset).  Values <= 1 pass."""
+    unit = OFFSET_ROUNDING_CELLS if unit is None else unit
     live = (gpu["cell"] >= 0) & (ref["cell"] >= 0)
     dg = (gpu["pos"] - start["pos"])[live]
     dr = (ref["pos"] - start["pos"])[live]
     rms = float(np.sqrt(np.mean(np.sum(dr * dr, axis=1)))) if len(dr) else 0.0
-    floor = (steps + 1) * 2.0 * OFFSET_ROUNDING_CELLS * h * math.sqrt(dim)
+    floor = (steps + 1) * 2.0 * unit * h * math.sqrt(dim)
     e = np.sqrt(np.sum((dg - dr) ** 2, axis=1))
     return float(e.max() / (rel * rms + floor)) if len(e) else 0.0
 

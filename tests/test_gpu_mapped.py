@@ -188,3 +188,111 @@ def test_locate_150k_particles_in_23k_cells():
     o = oracle.from_workload(replace(wl, pos=wl.pos[::97], vel=wl.vel[::97], vol=wl.vol[::97]))
     ref = H.oracle_snapshot(o, 3)["cell"]
     assert np.array_equal(gpu["cell"][::97], ref)
+
+
+# ---- the FP32 mixed path on mapped meshes ------------------------------------
+# The offset is xi / 2, solved in FP32 in the frame of the particle's cell:
+# each step's solve rounds the offset by about 2^-24 cell (the map's value is
+# a sum of 2^D rounded products), so the displacement floor takes 2^-23 cell
+# per step where the Cartesian offset takes 2^-26.
+MAPPED_ROUNDING_CELLS = 2.0 ** -23
+
+
+def fp32(wl):
+    return replace(wl, precision=W.FP32_MIXED)
+
+
+def cells_in_band(gpu, o, band):
+    """Particles whose FP32 cell differs from the oracle's must have, in the
+    oracle's cell, a natural coordinate within `band` of a face (xi = +-1)."""
+    diff = np.nonzero((gpu["cell"] != H.oracle_snapshot(o, o.mesh.dim)["cell"]) & (gpu["cell"] >= 0))[0]
+    far = 0
+    for p in diff:
+        it, xi = oracle.natural_mapped(o.mesh, o.X, o.cell[p], o.state.x[p, : o.mesh.dim])
+        d = np.min(1.0 - np.abs(xi[: o.mesh.dim]))
+        far += int(d > band)
+    return len(diff), far
+
+
+def check_fp32_run(wl, steps):
+    _, start, _ = run_oracle(wl, 0)
+    g1, s1 = run_gpu(wl, 1)
+    _, r1, _ = run_oracle(wl, 1)
+    assert s1 == mpm.MPM_OK
+    err1 = H.compare(g1, r1, start, wl.dim)
+    assert H.worst(err1, H.STATE_KEYS) <= H.TOL_STEP_FP32, err1
+    pp = H.per_particle(g1, r1, start)
+    assert pp["vel"] <= 1e-4 and pp["stress"] <= 1e-3, pp
+    assert H.disp_excess(g1, r1, start, wl.h, 1, wl.dim, rel=H.TOL_STEP_FP32, unit=MAPPED_ROUNDING_CELLS) <= 1.0
+    gpu, st = run_gpu(wl, steps)
+    o, ref, rst = run_oracle(wl, steps)
+    assert st == mpm.MPM_OK and rst == oracle.OK
+    err = H.compare(gpu, ref, start, wl.dim)
+    assert H.worst(err, H.RUN_KEYS) <= H.TOL_RUN_FP32, err
+    ex = H.disp_excess(gpu, ref, start, wl.h, steps, wl.dim, unit=MAPPED_ROUNDING_CELLS)
+    assert ex <= 1.0, (ex, err)
+    ndiff, far = cells_in_band(gpu, o, 1e-4)
+    assert far == 0, (ndiff, far)
+    return gpu, ref, start
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_fp32_initial_cells_and_positions(dim):
+    for wl in (fp32(W.terrain_column(dim)), fp32(W.warped_box(dim=dim))):
+        gpu, st = run_gpu(wl, 0)
+        _, ref, _ = run_oracle(wl, 0)
+        assert st == mpm.MPM_OK
+        assert_cells(gpu, ref)
+        # the offset xi / 2 rounds to FP32 once: positions within that of the inputs
+        assert np.abs(gpu["pos"] - wl.pos).max() <= 4.0 * 2.0 ** -24 * wl.h
+
+
+@pytest.mark.parametrize("scheme", [W.USL, W.USF])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_fp32_terrain_column(dim, scheme):
+    gpu, _, _ = check_fp32_run(fp32(W.terrain_column(dim, scheme=scheme)), 400)
+    assert np.mean(gpu["vel"][:, dim - 1]) < 0.0
+
+
+@pytest.mark.parametrize("scheme", [W.USL, W.USF])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_fp32_warped_box_particles_cross_cells(dim, scheme):
+    wl = fp32(W.warped_box(dim=dim, scheme=scheme))
+    gpu0, _ = run_gpu(wl, 0)
+    gpu, _, _ = check_fp32_run(wl, 100)
+    assert (gpu["cell"] != gpu0["cell"]).mean() > 0.9
+
+
+def test_fp32_rotated_column():
+    wl = W.column3d(ncells=(10, 6, 10), col_cells=(4, 3, 5), h=0.01, precision=W.FP32_MIXED, scheme=W.USL)
+    bc = [W.FREE] * 6
+    bc[4] = W.FIXED
+    wl = replace(wl, face_bc=tuple(bc), face_mu=(0.0,) * 6)
+    check_fp32_run(W.rotated(wl, W.rotation(3, (0.3, -0.4, 0.7))), 200)
+
+
+def test_fp32_particles_leave_the_mapped_mesh():
+    wl = fp32(W.warped_box(dim=3))
+    vel = wl.vel.copy()
+    vel[:40, 0] = 60.0
+    wl = replace(wl, vel=vel)
+    gpu, st = run_gpu(wl, 100)
+    o, ref, rst = run_oracle(wl, 100)
+    assert st == mpm.MPM_ERR_LEFT_MESH and rst == oracle.LEFT_MESH
+    gone = gpu["cell"] < 0
+    assert 0 < gone.sum() <= 40
+    assert np.array_equal(gone, ref["cell"] < 0)
+
+
+def test_fp32_mapped_mesh_is_not_batched():
+    wl = fp32(W.warped_box(dim=2))
+    b = mpm.mpm_batch_create(None, max_slots=2)
+    try:
+        with mpm.Simulation(wl, stress0=stress0(wl)) as sim:
+            with pytest.raises(mpm.MPMError) as ei:
+                mpm.mpm_batch_admit(b, sim.h)
+            assert ei.value.status == mpm.MPM_ERR_STATE
+            sim.step(3)
+            assert sim.sync() == mpm.MPM_OK
+    finally:
+        mpm.mpm_batch_destroy(b)
