@@ -510,12 +510,13 @@ def pinned_like(a):
 
 
 def run_mapped(args, stream, sptr, flush):
-    """The FP64 step on a mapped (isoparametric) mesh: a granular column on
-    terrain-following cells (983,040 particles, 160 x 48 x 64 cells), timed
-    like the headline, beside the Cartesian FP64 step of the same particle
-    count; and the paper's locate case, 150,000 particles placed in a mesh of
-    23,000 mapped cells (the add call: upload, initialisation and the
-    neighbourhood walk of every particle, wall clock, best of 3)."""
+    """The step on a mapped (isoparametric) mesh: a granular column on
+    terrain-following cells (983,040 particles, 160 x 48 x 64 cells), FP32
+    mixed and plain FP64, timed like the headline, beside the Cartesian steps
+    of the same particle count; and the paper's locate case, 150,000
+    particles placed in a mesh of 23,000 mapped cells (the add call: upload,
+    initialisation and the neighbourhood walk of every particle, wall clock,
+    best of 3)."""
     from paper_1909_13380_gb300 import mpm
 
     h = 0.005
@@ -525,7 +526,9 @@ def run_mapped(args, stream, sptr, flush):
                                vol=np.full(wl.n, h ** 3 / 8.0), name="granular_column_3d_160x48x64_flat")
     k = max(1, min(args.steps, 20))
     out = {"workload": wl.name, "particles": wl.n, "scheme": "USL", "steps": k}
-    for key, w in (("ms_per_step", wl), ("cartesian_fp64_ms", flat)):
+    f32 = dict(precision=W.FP32_MIXED)
+    for key, w in (("fp32_ms", dataclasses.replace(wl, **f32)), ("cartesian_fp32_ms", dataclasses.replace(flat, **f32)),
+                   ("fp64_ms", wl), ("cartesian_fp64_ms", flat)):
         sim = mpm.Simulation(w, stream=sptr)
         advance(sim, 20, stream)
         timed_steps(sim, args.warmup, stream, flush)
@@ -729,7 +732,8 @@ def run_gb300(args):
             "batched": None if not batched else {k: batched[k] for k in ("particles", "value", "ms_per_batched_step",
                                                                        "batching_speedup")},
             "serving": short_serving(serving),
-            "mapped": None if not mapped else {k: mapped[k] for k in ("workload", "ms_per_step", "cartesian_fp64_ms",
+            "mapped": None if not mapped else {k: mapped[k] for k in ("workload", "fp32_ms", "cartesian_fp32_ms",
+                                                                      "fp64_ms", "cartesian_fp64_ms",
                                                                       "locate_particles", "locate_cells",
                                                                       "locate_ms")},
         }
