@@ -1358,9 +1358,18 @@ __global__ void __launch_bounds__(G2P_T, MAP ? 4 : MPM_G2P_MINB) g2p(const __gri
           found = true;
           break;
         }
-        const int sgn = un[best] >= 0.5f ? 1 : -1;
-        cell[best] += sgn;
-        if (cell[best] < 0 || cell[best] >= g.nc[best]) {
+        // (indices stay compile-time constants: selects, not local memory)
+        int sgn = 0;
+        bool off_grid = false;
+#pragma unroll
+        for (int k = 0; k < D; ++k)
+          if (k == best) {
+            sgn = un[k] >= 0.5f ? 1 : -1;
+            cell[k] += sgn;
+            un[k] -= (float)sgn;
+            off_grid = cell[k] < 0 || cell[k] >= g.nc[k];
+          }
+        if (off_grid) {
           dead = true;
           break;
         }
@@ -1368,8 +1377,12 @@ __global__ void __launch_bounds__(G2P_T, MAP ? 4 : MPM_G2P_MINB) g2p(const __gri
         load_cgeo<D>(g, cell_lin<D>(g, cell), Pn);
         const int ao = sgn > 0 ? (1 << best) : 0, an = sgn > 0 ? 0 : (1 << best);
 #pragma unroll
-        for (int k = 0; k < D; ++k) T[k] -= Pc[ao][k] - Pn[an][k];
-        un[best] -= (float)sgn;
+        for (int a = 0; a < (1 << D); ++a)
+#pragma unroll
+          for (int k = 0; k < D; ++k) {
+            if (a == ao) T[k] -= Pc[a][k];
+            if (a == an) T[k] += Pn[a][k];
+          }
 #pragma unroll
         for (int a = 0; a < (1 << D); ++a)
 #pragma unroll
