@@ -168,9 +168,14 @@ mpm_status mpm_add_particles(mpm_handle h, int64_t n, const double *pos, const d
  *     the frame of its own cell and carried into each neighbour's frame
  *     through the node they share, at most 8 cells per step (beyond that
  *     the particle is dropped as having left the mesh);
- *   - face conditions act along the global axes (a roller zeroes the
- *     component along its logical face's axis): exact for fixed faces and
- *     for faces that stay planes normal to that axis.  Face tractions are
+ *   - face conditions act along each face's outward normal at the node
+ *     (nodal conditions on irregular surfaces): the normals of the boundary
+ *     facets next to the node (2D edges, weighted by length; 3D bilinear
+ *     facets, the cross product of their edges at the node) summed and
+ *     normalised.  A roller removes the velocity along the node's roller
+ *     normals (made orthonormal in face order: -x,+x,-y,+y,-z,+z); a
+ *     friction face applies the Coulomb rule to w = n . v' and the part of
+ *     v' tangent to n; a fixed face zeroes the velocity.  Face tractions are
  *     not defined: mpm_set_loads rejects them, and a mesh that carries them
  *     rejects this call (MPM_ERR_ARG).  Damping is allowed;
  *   - a mapped FP32_MIXED mesh is stepped alone: mpm_batch_admit rejects it

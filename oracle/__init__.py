@@ -111,6 +111,8 @@ def lib():
             L.oracle_iso_locate.argtypes = [C.POINTER(_Mesh), dp, dp, ip, dp]
             L.oracle_iso_basis.restype = None
             L.oracle_iso_basis.argtypes = [C.POINTER(_Mesh), dp, ip, dp, dp, dp]
+            L.oracle_face_normal.restype = None
+            L.oracle_face_normal.argtypes = [C.POINTER(_Mesh), dp, C.c_int32, ip, dp]
             L.oracle_step_mapped.restype = C.c_int
             L.oracle_step_mapped.argtypes = [C.POINTER(_Mesh), dp, C.POINTER(_Material), C.c_int64,
                                              dp, dp, dp, dp, dp, dp, dp, dp, ip, ip, dp, C.c_int64]
@@ -350,6 +352,14 @@ def locate_mapped(mesh: Mesh, X, x, start=(0, 0, 0)):
     st = lib().oracle_iso_locate(C.byref(mesh.c_struct()), _dp(_nodes3(mesh, X)), _dp(x3),
                                  _ip(c), _dp(xi))
     return int(st), c.copy(), xi
+
+
+def face_normal(mesh: Mesh, X, face: int, ijk):
+    """Outward unit normal (3,) of logical face `face` at its node ijk."""
+    n = np.zeros(3)
+    c = np.array(list(ijk) + [0] * (3 - len(ijk)), np.int32)
+    lib().oracle_face_normal(C.byref(mesh.c_struct()), _dp(_nodes3(mesh, X)), int(face), _ip(c), _dp(n))
+    return n
 
 
 def basis_mapped(mesh: Mesh, X, cell, xi):

@@ -61,11 +61,13 @@
  *       Raphson from the affine guess; a particle keeps the cell the
  *       neighbourhood walk last found for it; a point on a face shared by
  *       two cells belongs to the higher one (xi = 1 is outside, as R6).
- *   R12 on a mapped mesh the face conditions act along the global axes
- *       (roller: the component along the logical face's axis), which is the
- *       paper's nodal condition wherever the face is a plane normal to that
- *       axis, and fixed faces hold for any shape; face tractions (R9) are
- *       not defined there.
+ *   R12 on a mapped mesh ("nodal boundary conditions on irregular
+ *       surfaces") a node of a logical face takes the face's outward normal
+ *       there (face_normal: the facet normals next to the node summed and
+ *       normalised); a roller removes the velocity along the roller
+ *       normals of the node (made orthonormal in face order), a friction
+ *       face applies R3 with that normal; fixed faces as before; face
+ *       tractions (R9) are not defined there.
  *
  * Layout: every particle vector is stored with 3 components and every
  * stress/strain with 6 Voigt components (xx, yy, zz, xy, yz, xz; tensor
@@ -519,6 +521,149 @@ static void constrain_full(const om_mesh *M, int faces, double v[3], double a[3]
   }
 }
 
+/* ---- conditions on the faces of a mapped mesh (R12) ---------------------- */
+
+/* Outward unit normal of logical face f at its node ijk: the sum of the
+ * outward normals of the boundary facets next to the node -- in 2D the
+ * boundary edges, each normal as long as its edge; in 3D the bilinear facets,
+ * each the cross product of its two edges at the node -- normalised.  The
+ * inward direction is the mesh edge from the node into the mesh. */
+static void face_normal(const om_mesh *M, const double *X, int f, const int ijk[3], double n[3]) {
+  const int k = f / 2, up = f & 1;
+  const double *x0 = X + 3 * node_index(M, ijk);
+  int in3[3] = {ijk[0], ijk[1], ijk[2]};
+  in3[k] += up ? -1 : 1;
+  const double *xi = X + 3 * node_index(M, in3);
+  double din[3], acc[3] = {0.0, 0.0, 0.0};
+  for (int c = 0; c < 3; ++c) din[c] = xi[c] - x0[c];
+  if (M->dim == 2) {
+    const int t = 1 - k;
+    for (int sgn = -1; sgn <= 1; sgn += 2) {
+      int nb[3] = {ijk[0], ijk[1], 0};
+      nb[t] += sgn;
+      if (nb[t] < 0 || nb[t] > M->n[t]) continue;
+      const double *xb = X + 3 * node_index(M, nb);
+      double e0 = xb[0] - x0[0], e1 = xb[1] - x0[1];
+      double q0 = e1, q1 = -e0; /* perpendicular, |q| = |e| */
+      if (q0 * din[0] + q1 * din[1] > 0.0) { q0 = -q0; q1 = -q1; }
+      acc[0] += q0;
+      acc[1] += q1;
+    }
+  } else {
+    const int t1 = (k + 1) % 3, t2 = (k + 2) % 3;
+    for (int s1 = -1; s1 <= 1; s1 += 2)
+      for (int s2 = -1; s2 <= 1; s2 += 2) {
+        int a3[3] = {ijk[0], ijk[1], ijk[2]}, b3[3] = {ijk[0], ijk[1], ijk[2]};
+        a3[t1] += s1;
+        b3[t2] += s2;
+        if (a3[t1] < 0 || a3[t1] > M->n[t1] || b3[t2] < 0 || b3[t2] > M->n[t2]) continue;
+        const double *xa = X + 3 * node_index(M, a3), *xb = X + 3 * node_index(M, b3);
+        double ea[3], eb[3], q[3];
+        for (int c = 0; c < 3; ++c) {
+          ea[c] = xa[c] - x0[c];
+          eb[c] = xb[c] - x0[c];
+        }
+        q[0] = ea[1] * eb[2] - ea[2] * eb[1];
+        q[1] = ea[2] * eb[0] - ea[0] * eb[2];
+        q[2] = ea[0] * eb[1] - ea[1] * eb[0];
+        if (q[0] * din[0] + q[1] * din[1] + q[2] * din[2] > 0.0)
+          for (int c = 0; c < 3; ++c) q[c] = -q[c];
+        for (int c = 0; c < 3; ++c) acc[c] += q[c];
+      }
+  }
+  double len = sqrt(acc[0] * acc[0] + acc[1] * acc[1] + acc[2] * acc[2]);
+  for (int c = 0; c < 3; ++c) n[c] = acc[c] / len;
+}
+
+void oracle_face_normal(const om_mesh *M, const double *X, int32_t f, const int32_t ijk[3], double n[3]) {
+  int c[3] = {ijk[0], ijk[1], ijk[2]};
+  face_normal(M, X, f, c, n);
+}
+
+static double dot3(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+/* The roller normals of a node, made orthonormal in face order (Gram-Schmidt),
+ * so that removing each removes the velocity along every roller normal. */
+static int roller_basis(const om_mesh *M, const double *X, int faces, const int ijk[3], double B[3][3]) {
+  int nb = 0;
+  for (int f = 0; f < 2 * M->dim; ++f) {
+    if (!((faces >> f & 1) && M->face_bc[f] == OM_BC_ROLLER)) continue;
+    double n[3];
+    face_normal(M, X, f, ijk, n);
+    for (int b = 0; b < nb; ++b) {
+      double d = dot3(n, B[b]);
+      for (int c = 0; c < 3; ++c) n[c] -= d * B[b][c];
+    }
+    double len = sqrt(dot3(n, n));
+    if (!(len > 1e-12)) continue; /* parallel to an earlier roller normal */
+    for (int c = 0; c < 3; ++c) B[nb][c] = n[c] / len;
+    ++nb;
+  }
+  return nb;
+}
+
+/* The velocity stage and the full constraint of a node of a mapped mesh:
+ * the Cartesian rules with the face's outward normal n in place of the face
+ * axis -- a roller removes the components along the roller normals, a
+ * friction face acts on w = n . v' and the part of v' tangent to it. */
+static void constrain_velocity_mapped(const om_mesh *M, const double *X, int faces, const int ijk[3], double v[3]) {
+  for (int f = 0; f < 2 * M->dim; ++f)
+    if ((faces >> f & 1) && M->face_bc[f] == OM_BC_FIXED) {
+      v[0] = v[1] = v[2] = 0.0;
+      return;
+    }
+  double B[3][3];
+  int nb = roller_basis(M, X, faces, ijk, B);
+  for (int b = 0; b < nb; ++b) {
+    double d = dot3(v, B[b]);
+    for (int c = 0; c < 3; ++c) v[c] -= d * B[b][c];
+  }
+  for (int f = 0; f < 2 * M->dim; ++f) {
+    if (!((faces >> f & 1) && M->face_bc[f] == OM_BC_FRICTION)) continue;
+    double n[3];
+    face_normal(M, X, f, ijk, n);
+    double w = dot3(v, n);
+    if (w > 0.0)
+      for (int c = 0; c < 3; ++c) v[c] -= w * n[c];
+  }
+}
+
+static void constrain_full_mapped(const om_mesh *M, const double *X, int faces, const int ijk[3], double v[3],
+                                  double a[3], double vn[3]) {
+  for (int f = 0; f < 2 * M->dim; ++f)
+    if ((faces >> f & 1) && M->face_bc[f] == OM_BC_FIXED) {
+      for (int k = 0; k < 3; ++k) v[k] = a[k] = vn[k] = 0.0;
+      return;
+    }
+  double B[3][3];
+  int nb = roller_basis(M, X, faces, ijk, B);
+  for (int b = 0; b < nb; ++b) {
+    double dv = dot3(v, B[b]), da = dot3(a, B[b]), dn = dot3(vn, B[b]);
+    for (int c = 0; c < 3; ++c) {
+      v[c] -= dv * B[b][c];
+      a[c] -= da * B[b][c];
+      vn[c] -= dn * B[b][c];
+    }
+  }
+  for (int f = 0; f < 2 * M->dim; ++f) {
+    if (!((faces >> f & 1) && M->face_bc[f] == OM_BC_FRICTION)) continue;
+    double n[3];
+    face_normal(M, X, f, ijk, n);
+    double w = dot3(vn, n);
+    if (!(w > 0.0)) continue;
+    for (int c = 0; c < 3; ++c) vn[c] -= w * n[c];
+    double tnorm = sqrt(dot3(vn, vn));
+    double cap = M->face_mu[f] * w;
+    for (int c = 0; c < 3; ++c) {
+      if (tnorm <= cap)
+        vn[c] = 0.0;
+      else
+        vn[c] -= cap * vn[c] / tnorm;
+    }
+    for (int c = 0; c < M->dim; ++c) a[c] = (vn[c] - v[c]) / M->dt;
+  }
+}
+
 /* Exposed for unit tests of a single node: node ijk, in/out v, a, v'. */
 void oracle_constrain_node(const om_mesh *M, const int32_t ijk[3], double v[3], double a[3],
                            double vn[3]) {
@@ -777,7 +922,7 @@ static void face_force(const om_mesh *M, const int ijk[3], int faces, double ft[
  * 1 = USL (v from P), 2 = USF force stage (v already set).  The force
  * includes the face tractions (R9), and the damping (R10) takes alpha v
  * from the acceleration: a = (f + f_traction) / m - alpha v. */
-static void node_solve(const om_mesh *M, double *nm, double *nP, double *nf, double *nv,
+static void node_solve(const om_mesh *M, const double *X, double *nm, double *nP, double *nf, double *nv,
                        double *na, double *nvn, int stage) {
   int64_t nx = nodes_along(M, 0), ny = nodes_along(M, 1), nz = nodes_along(M, 2);
   for (int64_t kz = 0; kz < nz; ++kz)
@@ -790,7 +935,10 @@ static void node_solve(const om_mesh *M, double *nm, double *nP, double *nf, dou
         double *v = nv + 3 * i, *a = na + 3 * i, *vn = nvn + 3 * i;
         if (stage == 0) {
           for (int k = 0; k < 3; ++k) v[k] = active ? nP[3 * i + k] / nm[i] : 0.0;
-          constrain_velocity(M, faces, v);
+          if (X && faces)
+            constrain_velocity_mapped(M, X, faces, ijk, v);
+          else
+            constrain_velocity(M, faces, v);
           continue;
         }
         double ft[3];
@@ -804,7 +952,10 @@ static void node_solve(const om_mesh *M, double *nm, double *nP, double *nf, dou
           for (int k = 0; k < 3; ++k) v[k] = a[k] = vn[k] = 0.0;
           continue;
         }
-        constrain_full(M, faces, v, a, vn);
+        if (X && faces)
+          constrain_full_mapped(M, X, faces, ijk, v, a, vn);
+        else
+          constrain_full(M, faces, v, a, vn);
       }
 }
 
@@ -827,10 +978,10 @@ static int step_once(const om_mesh *M, const double *X, int32_t *pcell, const om
 
   if (M->scheme == OM_USL) {
     p2g(M, X, pcell, np, x, v, sig, m, vol, alive, nm, nP, nf, 1, 1);
-    node_solve(M, nm, nP, nf, nv, na, nvn, 1);
+    node_solve(M, X, nm, nP, nf, nv, na, nvn, 1);
   } else {
     p2g(M, X, pcell, np, x, v, sig, m, vol, alive, nm, nP, nf, 1, 0);
-    node_solve(M, nm, nP, nf, nv, na, nvn, 0);
+    node_solve(M, X, nm, nP, nf, nv, na, nvn, 0);
     for (int64_t p = 0; p < np; ++p) {
       if (!alive[p]) continue;
       int32_t cell[3];
@@ -841,7 +992,7 @@ static int step_once(const om_mesh *M, const double *X, int32_t *pcell, const om
                             epsp + p);
     }
     p2g(M, X, pcell, np, x, v, sig, m, vol, alive, nm, nP, nf, 0, 1);
-    node_solve(M, nm, nP, nf, nv, na, nvn, 2);
+    node_solve(M, X, nm, nP, nf, nv, na, nvn, 2);
   }
 
   for (int64_t p = 0; p < np; ++p) {

@@ -221,6 +221,9 @@ struct mpm_ctx {
   void *nmem64 = nullptr;
   double *X64 = nullptr;  // mapped mesh: node coordinates, 3 per node (mpm_set_node_coordinates)
   float4 *cgeo32 = nullptr;  // mapped FP32 mesh: corner positions per cell (Geo::cgeo)
+  double *fn64 = nullptr;    // mapped FP64 mesh: face normals (D64Launch::fnorm)
+  float4 *fn32 = nullptr;    // mapped FP32 mesh: face normals (Geo::fnorm)
+  int64_t fnoff[6] = {};     // offset of each face's table
   // shared
   int32_t *d_status = nullptr;  // FP64 path status word (FP32 path: s.ctr[C_STATUS])
   double *d_cons = nullptr;     // 8 results + partials
@@ -371,6 +374,8 @@ void fill_launch64(const mpm_ctx *h, D64Launch &L) {
     for (int k = 0; k < 3; ++k) L.trac[f][k] = h->trac[f][k];
   L.status = h->d_status;
   L.X = h->X64;
+  L.fnorm = h->fn64;
+  for (int f = 0; f < 6; ++f) L.fnoff[f] = h->fnoff[f];
 }
 
 int tile_dim(int dim, int k) {
@@ -1204,6 +1209,67 @@ mpm_status mpm_set_node_coordinates(mpm_handle h, const double *node_xyz) {
                   e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0]);
           if (!(det > 0.0)) return fail(h, MPM_ERR_ARG, "node coordinates: a cell is degenerate or inverted");
         }
+  // Outward unit normal of every face at each of its nodes (ISOPARAMETRIC
+  // MESH: nodal conditions on irregular surfaces): the normals of the
+  // boundary facets next to the node -- 2D edges (as long as the edge), 3D
+  // bilinear facets (the cross product of their two edges at the node) --
+  // summed, oriented away from the mesh edge that leads inside, normalised.
+  // Face f's table runs over the node's indices along the other axes in
+  // increasing axis order (Geo::fnorm).
+  const int64_t ncl[3] = {h->d.ncells[0], h->d.ncells[1], D == 3 ? h->d.ncells[2] : 0};
+  std::vector<double> fnv;
+  int64_t fnoff[6] = {0, 0, 0, 0, 0, 0};
+  for (int f = 0; f < 2 * D; ++f) {
+    const int k = f / 2, up = f & 1;
+    int ax[2] = {0, 0}, na = 0;
+    for (int c = 0; c < D; ++c)
+      if (c != k) ax[na++] = c;
+    const int64_t n1 = ncl[ax[0]] + 1, n2 = D == 3 ? ncl[ax[1]] + 1 : 1;
+    fnoff[f] = (int64_t)fnv.size() / 3;
+    for (int64_t i2 = 0; i2 < n2; ++i2)
+      for (int64_t i1 = 0; i1 < n1; ++i1) {
+        int64_t ijk[3] = {0, 0, 0};
+        ijk[k] = up ? ncl[k] : 0;
+        ijk[ax[0]] = i1;
+        if (D == 3) ijk[ax[1]] = i2;
+        int64_t in[3] = {ijk[0], ijk[1], ijk[2]};
+        in[k] += up ? -1 : 1;
+        double din[3], acc[3] = {0.0, 0.0, 0.0};
+        for (int c = 0; c < 3; ++c) din[c] = at(in[0], in[1], in[2], c) - at(ijk[0], ijk[1], ijk[2], c);
+        auto edge = [&](int axis, int sgn, double e[3]) -> bool {
+          int64_t nb[3] = {ijk[0], ijk[1], ijk[2]};
+          nb[axis] += sgn;
+          if (nb[axis] < 0 || nb[axis] > ncl[axis]) return false;
+          for (int c = 0; c < 3; ++c) e[c] = at(nb[0], nb[1], nb[2], c) - at(ijk[0], ijk[1], ijk[2], c);
+          return true;
+        };
+        if (D == 2) {
+          for (int sgn = -1; sgn <= 1; sgn += 2) {
+            double e[3];
+            if (!edge(ax[0], sgn, e)) continue;
+            double q0 = e[1], q1 = -e[0];
+            if (q0 * din[0] + q1 * din[1] > 0.0) {
+              q0 = -q0;
+              q1 = -q1;
+            }
+            acc[0] += q0;
+            acc[1] += q1;
+          }
+        } else {
+          for (int s1 = -1; s1 <= 1; s1 += 2)
+            for (int s2 = -1; s2 <= 1; s2 += 2) {
+              double ea[3], eb[3];
+              if (!edge(ax[0], s1, ea) || !edge(ax[1], s2, eb)) continue;
+              double q[3] = {ea[1] * eb[2] - ea[2] * eb[1], ea[2] * eb[0] - ea[0] * eb[2],
+                             ea[0] * eb[1] - ea[1] * eb[0]};
+              const double sd = q[0] * din[0] + q[1] * din[1] + q[2] * din[2];
+              for (int c = 0; c < 3; ++c) acc[c] += sd > 0.0 ? -q[c] : q[c];
+            }
+        }
+        const double len = std::sqrt(acc[0] * acc[0] + acc[1] * acc[1] + acc[2] * acc[2]);
+        for (int c = 0; c < 3; ++c) fnv.push_back(acc[c] / len);
+      }
+  }
   // FP32 path: per cell the corners relative to the cell's centre, in units
   // of h, computed in FP64 and rounded once (Geo::cgeo)
   std::vector<float4> cg;
@@ -1227,8 +1293,9 @@ mpm_status mpm_set_node_coordinates(mpm_handle h, const double *node_xyz) {
           for (int m = 0; m < nf; ++m) dst[m] = make_float4(f[4 * m], f[4 * m + 1], f[4 * m + 2], f[4 * m + 3]);
         }
   }
-  double *dX = nullptr;
-  float4 *dG = nullptr;
+  double *dX = nullptr, *dN64 = nullptr;
+  float4 *dG = nullptr, *dN32 = nullptr;
+  const size_t nfn = fnv.size() / 3;
   CK(cudaStreamSynchronize(h->st), "node coordinates");
   CK(cudaMalloc(&dX, sizeof(double) * 3 * nn), "node coordinates");
   cudaError_t e = cudaMemcpy(dX, X3.data(), sizeof(double) * 3 * nn, cudaMemcpyHostToDevice);
@@ -1236,17 +1303,38 @@ mpm_status mpm_set_node_coordinates(mpm_handle h, const double *node_xyz) {
     e = cudaMalloc(&dG, sizeof(float4) * cg.size());
     if (e == cudaSuccess) e = cudaMemcpy(dG, cg.data(), sizeof(float4) * cg.size(), cudaMemcpyHostToDevice);
   }
+  if (e == cudaSuccess && h->d.precision == MPM_FP32_MIXED) {
+    std::vector<float4> f4(nfn);
+    for (size_t i = 0; i < nfn; ++i)
+      f4[i] = make_float4((float)fnv[3 * i], (float)fnv[3 * i + 1], (float)fnv[3 * i + 2], 0.f);
+    e = cudaMalloc(&dN32, sizeof(float4) * nfn);
+    if (e == cudaSuccess) e = cudaMemcpy(dN32, f4.data(), sizeof(float4) * nfn, cudaMemcpyHostToDevice);
+  } else if (e == cudaSuccess) {
+    e = cudaMalloc(&dN64, sizeof(double) * 3 * nfn);
+    if (e == cudaSuccess) e = cudaMemcpy(dN64, fnv.data(), sizeof(double) * 3 * nfn, cudaMemcpyHostToDevice);
+  }
   if (e != cudaSuccess) {
     cudaFree(dX);
     if (dG) cudaFree(dG);
+    if (dN32) cudaFree(dN32);
+    if (dN64) cudaFree(dN64);
     return cuda_fail(h, e, "node coordinates");
   }
   if (h->X64) cudaFree(h->X64);
   if (h->cgeo32) cudaFree(h->cgeo32);
+  if (h->fn64) cudaFree(h->fn64);
+  if (h->fn32) cudaFree(h->fn32);
   h->X64 = dX;
   h->cgeo32 = dG;
+  h->fn64 = dN64;
+  h->fn32 = dN32;
+  for (int f = 0; f < 6; ++f) {
+    h->fnoff[f] = fnoff[f];
+    h->geo.fnoff[f] = (int)fnoff[f];
+  }
   h->geo.X = h->d.precision == MPM_FP32_MIXED ? dX : nullptr;
   h->geo.cgeo = dG;
+  h->geo.fnorm = dN32;
   destroy_graphs(h->graph);  // the instance (and its geometry) is captured in the step graph
   h->grp_valid = false;
   return MPM_OK;
@@ -1295,7 +1383,7 @@ mpm_status mpm_destroy(mpm_handle h) {
                   S.out_cnt, S.bucket_start, S.bucket_fill, S.movers, S.bucket, S.bucket_sorted, S.active,
                   S.bin_rec, S.scan_tot, S.ctr, S.slots1, S.slots2, S.slots_a, S.fepoch, S.aepoch, S.resid, S.node,
                   h->keys2, h->perm2, h->sort_scratch,
-                  h->pmem64, h->nmem64, h->X64, h->cgeo32, h->d_status, h->d_cons};
+                  h->pmem64, h->nmem64, h->X64, h->cgeo32, h->fn64, h->fn32, h->d_status, h->d_cons};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (int i = 0; i <= MPM_MAX_PHASES; ++i)

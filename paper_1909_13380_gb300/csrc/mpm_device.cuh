@@ -157,6 +157,125 @@ __device__ __forceinline__ void bc_full(int faces, const int *bc, const T *mu, T
   }
 }
 
+// The same conditions on a node of a mapped mesh (ISOPARAMETRIC MESH: nodal
+// conditions on irregular surfaces): nrm[f] is the outward unit normal of
+// face f at the node (read only for the node's faces).  A roller removes the
+// velocity along the roller normals, made orthonormal in face order; a
+// friction face acts on w = n . v' and on the part of v' tangent to n.  With
+// n = +-e_k these are the axis rules above.
+template <int D, typename T>
+__device__ __forceinline__ T dotn(const T a[D], const T b[D]) {
+  T s = T(0);
+#pragma unroll
+  for (int k = 0; k < D; ++k) s += a[k] * b[k];
+  return s;
+}
+
+template <int D, typename T>
+__device__ __forceinline__ int roller_basis_n(int faces, const int *bc, const T nrm[6][3], T B[D][D]) {
+  int nb = 0;
+#pragma unroll
+  for (int f = 0; f < 2 * D; ++f) {
+    if (!(((faces >> f) & 1) && bc[f] == BC_ROLLER)) continue;
+    T n[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) n[k] = nrm[f][k];
+#pragma unroll
+    for (int b = 0; b < D; ++b)
+      if (b < nb) {
+        const T d = dotn<D, T>(n, B[b]);
+#pragma unroll
+        for (int k = 0; k < D; ++k) n[k] -= d * B[b][k];
+      }
+    const T len = sqrt(dotn<D, T>(n, n));
+    if (!(len > T(1e-6))) continue;  // along an earlier roller normal
+#pragma unroll
+    for (int b = 0; b < D; ++b)
+      if (b == nb)
+#pragma unroll
+        for (int k = 0; k < D; ++k) B[b][k] = n[k] / len;
+    ++nb;
+  }
+  return nb;
+}
+
+template <int D, typename T>
+__device__ __forceinline__ void bc_velocity_n(int faces, const int *bc, const T nrm[6][3], T v[D]) {
+#pragma unroll
+  for (int f = 0; f < 2 * D; ++f)
+    if (((faces >> f) & 1) && bc[f] == BC_FIXED) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) v[k] = T(0);
+      return;
+    }
+  T B[D][D];
+  const int nb = roller_basis_n<D, T>(faces, bc, nrm, B);
+#pragma unroll
+  for (int b = 0; b < D; ++b)
+    if (b < nb) {
+      const T d = dotn<D, T>(v, B[b]);
+#pragma unroll
+      for (int k = 0; k < D; ++k) v[k] -= d * B[b][k];
+    }
+#pragma unroll
+  for (int f = 0; f < 2 * D; ++f) {
+    if (!(((faces >> f) & 1) && bc[f] == BC_FRICTION)) continue;
+    const T w = dotn<D, T>(v, nrm[f]);
+    if (w > T(0))
+#pragma unroll
+      for (int k = 0; k < D; ++k) v[k] -= w * nrm[f][k];
+  }
+}
+
+template <int D, typename T>
+__device__ __forceinline__ void bc_full_n(int faces, const int *bc, const T *mu, T dt, const T nrm[6][3], T v[D],
+                                          T a[D], T vn[D]) {
+#pragma unroll
+  for (int f = 0; f < 2 * D; ++f)
+    if (((faces >> f) & 1) && bc[f] == BC_FIXED) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) v[k] = a[k] = vn[k] = T(0);
+      return;
+    }
+  T B[D][D];
+  const int nb = roller_basis_n<D, T>(faces, bc, nrm, B);
+#pragma unroll
+  for (int b = 0; b < D; ++b)
+    if (b < nb) {
+      const T dv = dotn<D, T>(v, B[b]), da = dotn<D, T>(a, B[b]), dn = dotn<D, T>(vn, B[b]);
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        v[k] -= dv * B[b][k];
+        a[k] -= da * B[b][k];
+        vn[k] -= dn * B[b][k];
+      }
+    }
+#pragma unroll
+  for (int f = 0; f < 2 * D; ++f) {
+    if (!(((faces >> f) & 1) && bc[f] == BC_FRICTION)) continue;
+    const T w = dotn<D, T>(vn, nrm[f]);
+    if (!(w > T(0))) continue;
+#pragma unroll
+    for (int k = 0; k < D; ++k) vn[k] -= w * nrm[f][k];
+    const T tn = sqrt(dotn<D, T>(vn, vn));
+    const T cap = mu[f] * w;
+#pragma unroll
+    for (int k = 0; k < D; ++k) vn[k] = (tn <= cap) ? T(0) : vn[k] - cap * vn[k] / tn;
+#pragma unroll
+    for (int k = 0; k < D; ++k) a[k] = (vn[k] - v[k]) / dt;
+  }
+}
+
+// Index of node I within the table of face f: its indices along the face's
+// other axes in increasing axis order (nc: cells per axis).
+template <int D>
+__device__ __forceinline__ int64_t face_node_index(int f, const int I[3], const int nc[3]) {
+  const int k = f >> 1;
+  if (D == 2) return I[1 - k];
+  const int t1 = k == 0 ? 1 : 0, t2 = k == 2 ? 1 : 2;
+  return (int64_t)I[t1] + (int64_t)(nc[t1] + 1) * I[t2];
+}
+
 // ---------------------------------------------------------------------------
 // Explicitly rounded operations for the FP32 material update.  Whether the
 // compiler contracts a product and a sum into one FMA depends on the code

@@ -956,7 +956,7 @@ __device__ __forceinline__ void gather_node_usl(const Geo &g, const float *slots
 // fill the grid.  The nodes whose lowest active holder is the tile -- every
 // node is computed once -- get v = P/m, a = f/m + g, v' = v + a dt and the
 // boundary conditions, written to the dense node records.
-template <int D, int NMODE, bool ONE>
+template <int D, int NMODE, bool ONE, bool MAP = false>
 __global__ void __launch_bounds__(NODE_T, ONE ? MPM_NODE_MINB : 8) node_tile(const __grid_constant__ GroupArgs G, int work_slot) {
   constexpr int BN = box_nodes<D>();
   constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ;
@@ -1046,6 +1046,18 @@ __global__ void __launch_bounds__(NODE_T, ONE ? MPM_NODE_MINB : 8) node_tile(con
         gather_node<D, 1 + D>(g, I.s.slots1, NCH1, Ig, lo, hi, act, c1);
       const float m = c1[0];
       const int faces = node_faces<D>(g, Ig);
+      // a mapped mesh's boundary node: its faces' outward normals
+      float nrm[6][3];
+      if (MAP && faces) {
+#pragma unroll
+        for (int f = 0; f < 2 * D; ++f)
+          if ((faces >> f) & 1) {
+            const float4 q = __ldg(g.fnorm + g.fnoff[f] + face_node_index<D>(f, Ig, g.nc));
+            nrm[f][0] = q.x;
+            nrm[f][1] = q.y;
+            nrm[f][2] = q.z;
+          }
+      }
       if (m > g.mass_tol) {
         const float inv_m = 1.f / m;
 #pragma unroll
@@ -1058,13 +1070,22 @@ __global__ void __launch_bounds__(NODE_T, ONE ? MPM_NODE_MINB : 8) node_tile(con
             a[k] = g.loads ? (c1[1 + D + k] + ft[k]) * inv_m + g.g[k] - g.damp * v[k] : c1[1 + D + k] * inv_m + g.g[k];
             vn[k] = v[k] + a[k] * g.dt;
           }
-          bc_full<D, float>(faces, g.bc, g.mu, g.dt, v, a, vn);
+          if (MAP && faces)
+            bc_full_n<D, float>(faces, g.bc, g.mu, g.dt, nrm, v, a, vn);
+          else
+            bc_full<D, float>(faces, g.bc, g.mu, g.dt, v, a, vn);
         } else if (NMODE == NODE_USF_V) {
-          bc_velocity<D, float>(faces, g.bc, v);
+          if (MAP && faces)
+            bc_velocity_n<D, float>(faces, g.bc, nrm, v);
+          else
+            bc_velocity<D, float>(faces, g.bc, v);
         } else {
           float f[D];
           gather_node<D, D>(g, I.s.slots2, D, Ig, lo, hi, act, f);
-          bc_velocity<D, float>(faces, g.bc, v);
+          if (MAP && faces)
+            bc_velocity_n<D, float>(faces, g.bc, nrm, v);
+          else
+            bc_velocity<D, float>(faces, g.bc, v);
           float ft[D];
           if (g.loads) face_force<D, float>(faces, Ig, g.nc, g.h, g.trac, ft);
 #pragma unroll
@@ -1072,7 +1093,10 @@ __global__ void __launch_bounds__(NODE_T, ONE ? MPM_NODE_MINB : 8) node_tile(con
             a[k] = g.loads ? (f[k] + ft[k]) * inv_m + g.g[k] - g.damp * v[k] : f[k] * inv_m + g.g[k];
             vn[k] = v[k] + a[k] * g.dt;
           }
-          bc_full<D, float>(faces, g.bc, g.mu, g.dt, v, a, vn);
+          if (MAP && faces)
+            bc_full_n<D, float>(faces, g.bc, g.mu, g.dt, nrm, v, a, vn);
+          else
+            bc_full<D, float>(faces, g.bc, g.mu, g.dt, v, a, vn);
         }
       }
       const int gi = Ig[0] + I.ns0 * Ig[1] + I.ns1 * Ig[2];
@@ -1994,6 +2018,7 @@ cudaError_t launch_g2p_tile(const GroupArgs &G, cudaStream_t st) {
 
 template <int D, int NMODE>
 cudaError_t launch_node(const GroupArgs &G, int work_slot, cudaStream_t st) {
+  if (G.mapped) return launch_dep(node_tile<D, NMODE, true, true>, G.grid, NODE_T, 0, st, G, work_slot);
   return G.ninst == 1 ? launch_dep(node_tile<D, NMODE, true>, G.grid, NODE_T, 0, st, G, work_slot)
                       : launch_dep(node_tile<D, NMODE, false>, G.grid, NODE_T, 0, st, G, work_slot);
 }

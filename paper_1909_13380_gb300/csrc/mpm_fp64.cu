@@ -164,8 +164,22 @@ __global__ void node64(D64Launch L) {
       v[k] = STAGE == 2 ? L.N.v[k][i] : (active ? L.N.P[k][i] / m : 0.0);
       a[k] = vn[k] = 0.0;
     }
+    double nrm[6][3];  // a mapped mesh's boundary node: its faces' outward normals
+    if (L.fnorm && faces) {
+#pragma unroll
+      for (int f = 0; f < 2 * D; ++f)
+        if ((faces >> f) & 1) {
+          const double *q = L.fnorm + 3 * (L.fnoff[f] + face_node_index<D>(f, I, L.nc));
+          nrm[f][0] = q[0];
+          nrm[f][1] = q[1];
+          nrm[f][2] = q[2];
+        }
+    }
     if (STAGE == 0) {
-      bc_velocity<D, double>(faces, L.bc, v);
+      if (L.fnorm && faces)
+        bc_velocity_n<D, double>(faces, L.bc, nrm, v);
+      else
+        bc_velocity<D, double>(faces, L.bc, v);
 #pragma unroll
       for (int k = 0; k < D; ++k) L.N.v[k][i] = v[k];
       continue;
@@ -178,7 +192,10 @@ __global__ void node64(D64Launch L) {
         a[k] = L.loads ? (L.N.f[k][i] + ft[k]) / m - L.damp * v[k] : L.N.f[k][i] / m;
         vn[k] = v[k] + a[k] * L.dt;
       }
-      bc_full<D, double>(faces, L.bc, L.mu, L.dt, v, a, vn);
+      if (L.fnorm && faces)
+        bc_full_n<D, double>(faces, L.bc, L.mu, L.dt, nrm, v, a, vn);
+      else
+        bc_full<D, double>(faces, L.bc, L.mu, L.dt, v, a, vn);
     } else {
 #pragma unroll
       for (int k = 0; k < D; ++k) v[k] = 0.0;

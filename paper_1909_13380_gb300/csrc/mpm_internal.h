@@ -108,6 +108,11 @@ struct Geo {
   // coordinates (3 per node) for the initial location and the export.
   const float4 *cgeo;
   const double *X;
+  // mapped mesh: outward unit normal of face f at its node (i1, i2) -- the
+  // node's indices along the face's two other axes, in increasing axis order
+  // (2D: the one other axis) -- at fnorm[fnoff[f] + i1 + (n_i1 + 1) i2]
+  const float4 *fnorm;
+  int fnoff[6];
 };
 template <int D> constexpr int CGEO_F4() { return D == 3 ? 6 : 2; }
 
@@ -359,6 +364,8 @@ struct D64Launch {
   int64_t nnodes;
   int32_t *status;
   const double *X;  // mapped mesh: node coordinates, 3 per node (x fastest); null: Cartesian
+  const double *fnorm;  // mapped mesh: face normals (3 per face node, laid out as Geo::fnorm)
+  int64_t fnoff[6];
 };
 cudaError_t d64_step(const D64Launch &L, cudaStream_t st);
 // Locate particles n0 .. n0 + n - 1 of a mapped mesh (L.X set) by the

@@ -405,9 +405,9 @@ def terrain_column(dim=2, ncells=None, col_cells=None, h=0.005, amp=None, wavele
     """A granular column collapsing on bumpy ground: the mesh follows the
     terrain (mapped cells, the base a sine of amplitude amp), the column's
     particles are the Cartesian 2-point Gauss positions moved by the same
-    map.  Mohr-Coulomb as the 3D column; the base fixed (no slip on the
-    irregular ground), a roller on x = 0 (a vertical plane under the map),
-    the other faces free."""
+    map.  Mohr-Coulomb as the 3D column; a Coulomb base (mu 0.4) along the
+    bumpy ground's normals, a roller on x = 0 (a vertical plane under the
+    map), the other faces free."""
     if ncells is None:
         ncells = (60, 24) if dim == 2 else (40, 8, 24)
     if col_cells is None:
@@ -425,13 +425,15 @@ def terrain_column(dim=2, ncells=None, col_cells=None, h=0.005, amp=None, wavele
     X = terrain(cartesian_node_xyz(ncells, h, (0.0, 0.0, 0.0), dim), dim, amp, wavelength, height)
     bc = [FREE] * 6
     bc[0] = ROLLER
-    bc[2 * (dim - 1)] = FIXED
+    bc[2 * (dim - 1)] = FRICTION
+    mu = [0.0] * 6
+    mu[2 * (dim - 1)] = 0.4
     g = [0.0, 0.0, 0.0]
     g[dim - 1] = -9.81
     nm = name or f"terrain_column_{dim}d_" + "x".join(str(c) for c in ncells[:dim])
     return Workload(
         name=nm, dim=dim, ncells=tuple(ncells[:dim]) + (1,) * (3 - dim), h=h, origin=(0.0, 0.0, 0.0),
-        face_bc=tuple(bc), face_mu=(0.0,) * 6, gravity=tuple(g), dt=1e-5, scheme=scheme, precision=precision,
+        face_bc=tuple(bc), face_mu=tuple(mu), gravity=tuple(g), dt=1e-5, scheme=scheme, precision=precision,
         material=_mc(), pos=pos, vel=np.zeros_like(pos), vol=stretch * h ** dim / (1 << dim),
         steps=steps, node_xyz=X, meta=dict(amp=amp, wavelength=wavelength))
 

@@ -3,10 +3,12 @@ against the oracle, through the C-ABI, on the same seeded inputs:
 
   * initial cells: the device walk from the Cartesian guess finds the
     oracle's cell for every particle (bit-exact cell ids);
-  * a terrain-following granular column (2D and 3D, USF and USL), a warped
-    box whose particles all cross cells, and a column turned rigidly in
-    space: state within the FP64 bar (1e-9 relative L2) after the run,
-    cells identical;
+  * a terrain-following granular column on a Coulomb base along the bumpy
+    ground's normals (2D and 3D, USF and USL), a warped box whose particles
+    all cross cells, and columns turned rigidly in space with their rollers
+    and Coulomb base: state within the FP64 bar (1e-9 relative L2) after the
+    run, cells identical; the FP32 mixed path on the same meshes within the
+    FP32 bars;
   * nodes on the Cartesian grid: the mapped path equals the Cartesian one;
   * particles leaving the mapped mesh, and the entry point's error cases.
 """
@@ -94,13 +96,27 @@ def test_warped_box_particles_cross_cells(dim, scheme):
     assert moved.mean() > 0.9
 
 
-def test_rotated_column():
-    wl = W.column3d(ncells=(10, 6, 10), col_cells=(4, 3, 5), h=0.01, precision=W.FP64_PLAIN, scheme=W.USL)
-    bc = [W.FREE] * 6
-    bc[4] = W.FIXED
-    wl = replace(wl, face_bc=tuple(bc), face_mu=(0.0,) * 6)
-    R = W.rotation(3, (0.3, -0.4, 0.7))
-    check_run(W.rotated(wl, R), 200)
+def turned_column(precision, bcs, dim=3, scheme=W.USL):
+    if dim == 3:
+        wl = W.column3d(ncells=(10, 6, 10), col_cells=(4, 3, 5), h=0.01, precision=precision, scheme=scheme)
+    else:
+        wl = W.column2d(6, 8, h=0.01, precision=precision, scheme=scheme, mesh_cells=(14, 12))
+    if bcs == "fixed_base":
+        bc = [W.FREE] * 6
+        bc[2 * (dim - 1)] = W.FIXED
+        wl = replace(wl, face_bc=tuple(bc), face_mu=(0.0,) * 6)
+    # else the column's own walls: rollers and a Coulomb base, along the turned normals
+    return W.rotated(wl, W.rotation(dim, (0.3, -0.4, 0.7) if dim == 3 else 0.5))
+
+
+@pytest.mark.parametrize("bcs", ["fixed_base", "rollers_and_friction"])
+def test_rotated_column(bcs):
+    check_run(turned_column(W.FP64_PLAIN, bcs), 200)
+
+
+@pytest.mark.parametrize("scheme", [W.USL, W.USF])
+def test_rotated_2d_column_with_rollers_and_friction(scheme):
+    check_run(turned_column(W.FP64_PLAIN, "rollers_and_friction", dim=2, scheme=scheme), 300)
 
 
 @pytest.mark.parametrize("scheme", [W.USL, W.USF])
@@ -263,12 +279,14 @@ def test_fp32_warped_box_particles_cross_cells(dim, scheme):
     assert (gpu["cell"] != gpu0["cell"]).mean() > 0.9
 
 
-def test_fp32_rotated_column():
-    wl = W.column3d(ncells=(10, 6, 10), col_cells=(4, 3, 5), h=0.01, precision=W.FP32_MIXED, scheme=W.USL)
-    bc = [W.FREE] * 6
-    bc[4] = W.FIXED
-    wl = replace(wl, face_bc=tuple(bc), face_mu=(0.0,) * 6)
-    check_fp32_run(W.rotated(wl, W.rotation(3, (0.3, -0.4, 0.7))), 200)
+@pytest.mark.parametrize("bcs", ["fixed_base", "rollers_and_friction"])
+def test_fp32_rotated_column(bcs):
+    check_fp32_run(turned_column(W.FP32_MIXED, bcs), 200)
+
+
+@pytest.mark.parametrize("scheme", [W.USL, W.USF])
+def test_fp32_rotated_2d_column_with_rollers_and_friction(scheme):
+    check_fp32_run(turned_column(W.FP32_MIXED, "rollers_and_friction", dim=2, scheme=scheme), 300)
 
 
 def test_fp32_particles_leave_the_mapped_mesh():

@@ -11,8 +11,12 @@ in 2D, particles located by a neighbourhood walk).
   * the physical gradients dN/dx reproduce linear fields (sum_a X_a (x)
     grad N_a = I) and match central differences of N along x;
   * a mapped mesh whose nodes sit on the Cartesian grid steps like the
-    Cartesian oracle; the whole problem turned rigidly about the origin steps
-    into the turned result (positions, velocities and stresses R . R^T);
+    Cartesian oracle; the whole problem turned rigidly about the origin --
+    rollers and a Coulomb base included, whose normals turn with the mesh --
+    steps into the turned result (positions, velocities and stresses R . R^T);
+  * face normals: on a turned mesh R times the axis; on a circular arc of a
+    polar mesh the radius; a block on a turned frictional plane under
+    vertical gravity slides with g (sin theta - mu cos theta);
   * the terrain column: particles stay located, mass is conserved.
 """
 import math
@@ -229,14 +233,16 @@ def test_cartesian_nodes_step_like_the_cartesian_mesh(dim, scheme):
     assert np.array_equal(a.cells(), b.cells())
 
 
+@pytest.mark.parametrize("bcs", ["fixed_base", "rollers_and_friction"])
 @pytest.mark.parametrize("scheme", [W.USF, W.USL])
 @pytest.mark.parametrize("dim", [2, 3])
-def test_rotated_problem_steps_into_the_rotated_result(dim, scheme):
+def test_rotated_problem_steps_into_the_rotated_result(dim, scheme, bcs):
     wl = small_column(dim, scheme)
-    # fixed base, every other face free: conditions that turn with the body
-    bc = [W.FREE] * 6
-    bc[2 * (dim - 1)] = W.FIXED
-    wl = replace(wl, face_bc=tuple(bc), face_mu=(0.0,) * 6)
+    if bcs == "fixed_base":
+        bc = [W.FREE] * 6
+        bc[2 * (dim - 1)] = W.FIXED
+        wl = replace(wl, face_bc=tuple(bc), face_mu=(0.0,) * 6)
+    # else the column's own walls: rollers and a Coulomb base (mu 0.4)
     R = W.rotation(dim, 0.5 if dim == 2 else (0.3, -0.4, 0.7))
     a, sa = run(wl, 200)
     b, sb = run(W.rotated(wl, R), 200)
@@ -278,6 +284,80 @@ def test_terrain_column(dim):
     for p in range(0, wl.n, max(1, wl.n // 50)):
         it, xi = oracle.natural_mapped(o.mesh, o.X, o.cell[p], o.state.x[p, :dim])
         assert it > 0 and np.all(xi[:dim] >= -1.0) and np.all(xi[:dim] < 1.0)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_face_normals_turn_with_the_mesh(dim):
+    n = (5, 4, 3)[:dim]
+    mesh = oracle.Mesh(dim=dim, n=n + (1,) * (3 - dim), h=0.1)
+    R = W.rotation(dim, 0.7 if dim == 2 else (0.4, -0.9, 0.3))
+    X = W.cartesian_node_xyz(n + (1,) * (3 - dim), 0.1, (0.0, 0.0, 0.0), dim) @ R.T
+    for f in range(2 * dim):
+        k, up = f // 2, f % 2
+        axis = np.zeros(dim)
+        axis[k] = 1.0 if up else -1.0
+        want = R @ axis
+        for node in W.box_cells((0,) * dim, tuple(m + 1 for m in n)):
+            if node[k] != (n[k] if up else 0):
+                continue
+            got = oracle.face_normal(mesh, X, f, node)
+            assert np.allclose(got[:dim], want, atol=1e-14), (f, node)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_face_normal_of_a_circular_arc_is_the_radius(dim):
+    # polar mesh: x index = radius 1..2, y index = angle 0..60 degrees (3D: z straight)
+    nr, nt, nz = 4, 6, 3
+    r = 1.0 + np.arange(nr + 1) / nr
+    th = np.radians(60.0) * np.arange(nt + 1) / nt
+    if dim == 2:
+        X = np.array([[ri * math.cos(t), ri * math.sin(t)] for t in th for ri in r])
+        mesh = oracle.Mesh(dim=2, n=(nr, nt, 1), h=0.1)
+        nodes = [(nr, j) for j in range(1, nt)]
+    else:
+        X = np.array([[ri * math.cos(t), ri * math.sin(t), 0.25 * kz] for kz in range(nz + 1) for t in th for ri in r])
+        mesh = oracle.Mesh(dim=3, n=(nr, nt, nz), h=0.1)
+        nodes = [(nr, j, kz) for kz in range(nz + 1) for j in range(1, nt)]
+    for node in nodes:   # the outer arc (+x face), away from its ends in angle
+        t = th[node[1]]
+        got = oracle.face_normal(mesh, X, 1, node)
+        want = np.array([math.cos(t), math.sin(t), 0.0])
+        assert np.allclose(got, want, atol=1e-14), node
+        # the inner arc (-x face) points to the centre
+        inner = (0,) + tuple(node[1:])
+        assert np.allclose(oracle.face_normal(mesh, X, 0, inner), -want, atol=1e-14), node
+
+
+@pytest.mark.parametrize("scheme", [oracle.USF, oracle.USL])
+def test_block_on_a_turned_frictional_plane(scheme):
+    # the mesh (and its Coulomb base) turned by -theta, gravity vertical: the
+    # block slides down the base with g (sin theta - mu cos theta), or sticks
+    th, g, h = math.radians(30.0), 9.81, 0.05
+    R = W.rotation(2, -th)
+    X = W.cartesian_node_xyz((40, 8, 1), h, (0.0, 0.0, 0.0), 2) @ R.T
+    pos = W.gauss_fill(W.box_cells((2, 0), (10, 4)), h, (0.0, 0.0), 2) @ R.T
+    down = R @ np.array([1.0, 0.0])
+    res = {}
+    for mu in (0.2, 0.8):
+        mesh = oracle.Mesh(dim=2, n=(40, 8, 1), h=h, face_bc=(0, 0, 3, 0, 0, 0), face_mu=(0, 0, mu, 0, 0, 0),
+                           g=(0.0, -g, 0.0), dt=1e-5, scheme=scheme)
+        st = oracle.State.create(pos, np.zeros_like(pos), np.full(len(pos), h * h / 4), 1000.0)
+        o = oracle.Oracle(mesh, oracle.Material(E=5e7, nu=0.3, rho=1000.0), st, X=X)
+        M = st.m.sum()
+        n = 5000
+        vs = []
+        for _ in range(n):
+            assert o.step(1) == oracle.OK
+            vs.append(np.sum(st.m[:, None] * st.v[:, :2], axis=0) @ down / M)
+        t = (np.arange(n) + 1) * 1e-5
+        res[mu] = (np.polyfit(t[n // 2:], np.array(vs[n // 2:]), 1)[0], vs[-1])
+        # the block stays on the base: its distance from the base plane stays positive
+        normal = R @ np.array([0.0, 1.0])
+        assert (st.x[:, :2] @ normal).min() > 0.0
+    a_slip = g * (math.sin(th) - 0.2 * math.cos(th))
+    assert res[0.2][0] == pytest.approx(a_slip, rel=1e-2)
+    assert abs(res[0.8][0]) < 0.05 * a_slip
+    assert abs(res[0.8][1]) < 0.1 * abs(res[0.2][1])
 
 
 def test_tractions_are_not_defined_on_mapped_meshes():
