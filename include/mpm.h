@@ -178,8 +178,8 @@ mpm_status mpm_add_particles(mpm_handle h, int64_t n, const double *pos, const d
  *     v' tangent to n; a fixed face zeroes the velocity.  Face tractions are
  *     not defined: mpm_set_loads rejects them, and a mesh that carries them
  *     rejects this call (MPM_ERR_ARG).  Damping is allowed;
- *   - a mapped FP32_MIXED mesh is stepped alone: mpm_batch_admit rejects it
- *     (MPM_ERR_STATE).
+ *   - in a batch, mapped and Cartesian meshes step in groups of their own
+ *     kind; every mesh's result is the same as stepping it alone.
  * mpm_read_particles' position is x(xi) of the particle's cell and its cell
  * the walk's.  mpm_footprint does not include the mapped storage: 24 bytes
  * per node, and per particle 4 + 8 dim (FP64_PLAIN), or per cell 32 (2D) or

@@ -242,6 +242,7 @@ struct mpm_batch_ctx {
   int32_t graph_kernels = -1;
   struct Group {
     int dim, scheme;
+    bool mapped;  // mapped FP32 meshes step in groups of their own (the MAP kernels)
     std::vector<mpm_ctx *> mem;
     std::vector<int> slot;
     GroupDev dev;
@@ -481,7 +482,7 @@ cudaError_t build_group(GroupDev &g, const std::vector<mpm_ctx *> &mem, bool rel
     int max_m = 0;
     for (int i = 0; i < n; ++i) max_m = std::max(max_m, mem[i]->geo.ntiles + 1);
     G.scan_one = max_m <= SCAN1_MAX ? 1 : 0;
-    G.mapped = (n == 1 && mem[0]->geo.cgeo) ? 1 : 0;  // mapped meshes are never batched
+    G.mapped = (n > 0 && mem[0]->geo.cgeo) ? 1 : 0;  // a group is all mapped or all Cartesian
     int64_t np = 0;
     for (int i = 0; i < n; ++i) np += mem[i]->n;
     G.bin_t = np >= ((int64_t)1 << 22) ? 128 : 256;
@@ -1424,7 +1425,6 @@ mpm_status mpm_batch_admit(mpm_batch b, mpm_handle h, int32_t *slot) {
   if (s0 != MPM_OK) return s0;
   if (h->d.precision != MPM_FP32_MIXED) return fail(h, MPM_ERR_ARG, "batch: FP32_MIXED meshes only");
   if (h->batch) return fail(h, MPM_ERR_STATE, "batch: the mesh is already admitted to a batch");
-  if (h->geo.cgeo) return fail(h, MPM_ERR_STATE, "batch: mapped meshes are stepped alone");
   // room: a free slot, and the mesh's footprint within what the budget has left
   int s = -1;
   for (size_t i = 0; i < b->slots.size(); ++i)
@@ -1487,10 +1487,11 @@ mpm_status mpm_batch_step(mpm_batch b, int64_t nsteps) {
       mpm_ctx *h = b->slots[i];
       if (!h || h->n == 0) continue;
       mpm_batch_ctx::Group *gp = nullptr;
+      const bool mapped = h->geo.cgeo != nullptr;
       for (auto &g : b->groups)
-        if (g.dim == h->d.dim && g.scheme == h->d.scheme) gp = &g;
+        if (g.dim == h->d.dim && g.scheme == h->d.scheme && g.mapped == mapped) gp = &g;
       if (!gp) {
-        b->groups.push_back(mpm_batch_ctx::Group{h->d.dim, h->d.scheme, {}, {}, GroupDev()});
+        b->groups.push_back(mpm_batch_ctx::Group{h->d.dim, h->d.scheme, mapped, {}, {}, GroupDev()});
         gp = &b->groups.back();
       }
       gp->mem.push_back(h);

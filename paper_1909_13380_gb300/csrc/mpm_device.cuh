@@ -162,12 +162,14 @@ __device__ __forceinline__ void bc_full(int faces, const int *bc, const T *mu, T
 // face f at the node (read only for the node's faces).  A roller removes the
 // velocity along the roller normals, made orthonormal in face order; a
 // friction face acts on w = n . v' and on the part of v' tangent to n.  With
-// n = +-e_k these are the axis rules above.
+// n = +-e_k these are the axis rules above.  Products and sums are written
+// as explicit FMAs, so every kernel that inlines them (a mesh alone or in a
+// batch) rounds them alike.
 template <int D, typename T>
 __device__ __forceinline__ T dotn(const T a[D], const T b[D]) {
   T s = T(0);
 #pragma unroll
-  for (int k = 0; k < D; ++k) s += a[k] * b[k];
+  for (int k = 0; k < D; ++k) s = fma(a[k], b[k], s);
   return s;
 }
 
@@ -185,7 +187,7 @@ __device__ __forceinline__ int roller_basis_n(int faces, const int *bc, const T 
       if (b < nb) {
         const T d = dotn<D, T>(n, B[b]);
 #pragma unroll
-        for (int k = 0; k < D; ++k) n[k] -= d * B[b][k];
+        for (int k = 0; k < D; ++k) n[k] = fma(-d, B[b][k], n[k]);
       }
     const T len = sqrt(dotn<D, T>(n, n));
     if (!(len > T(1e-6))) continue;  // along an earlier roller normal
@@ -215,7 +217,7 @@ __device__ __forceinline__ void bc_velocity_n(int faces, const int *bc, const T 
     if (b < nb) {
       const T d = dotn<D, T>(v, B[b]);
 #pragma unroll
-      for (int k = 0; k < D; ++k) v[k] -= d * B[b][k];
+      for (int k = 0; k < D; ++k) v[k] = fma(-d, B[b][k], v[k]);
     }
 #pragma unroll
   for (int f = 0; f < 2 * D; ++f) {
@@ -223,7 +225,7 @@ __device__ __forceinline__ void bc_velocity_n(int faces, const int *bc, const T 
     const T w = dotn<D, T>(v, nrm[f]);
     if (w > T(0))
 #pragma unroll
-      for (int k = 0; k < D; ++k) v[k] -= w * nrm[f][k];
+      for (int k = 0; k < D; ++k) v[k] = fma(-w, nrm[f][k], v[k]);
   }
 }
 
@@ -245,9 +247,9 @@ __device__ __forceinline__ void bc_full_n(int faces, const int *bc, const T *mu,
       const T dv = dotn<D, T>(v, B[b]), da = dotn<D, T>(a, B[b]), dn = dotn<D, T>(vn, B[b]);
 #pragma unroll
       for (int k = 0; k < D; ++k) {
-        v[k] -= dv * B[b][k];
-        a[k] -= da * B[b][k];
-        vn[k] -= dn * B[b][k];
+        v[k] = fma(-dv, B[b][k], v[k]);
+        a[k] = fma(-da, B[b][k], a[k]);
+        vn[k] = fma(-dn, B[b][k], vn[k]);
       }
     }
 #pragma unroll
@@ -256,7 +258,7 @@ __device__ __forceinline__ void bc_full_n(int faces, const int *bc, const T *mu,
     const T w = dotn<D, T>(vn, nrm[f]);
     if (!(w > T(0))) continue;
 #pragma unroll
-    for (int k = 0; k < D; ++k) vn[k] -= w * nrm[f][k];
+    for (int k = 0; k < D; ++k) vn[k] = fma(-w, nrm[f][k], vn[k]);
     const T tn = sqrt(dotn<D, T>(vn, vn));
     const T cap = mu[f] * w;
 #pragma unroll

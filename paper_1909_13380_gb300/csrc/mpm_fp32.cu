@@ -201,17 +201,19 @@ __device__ __forceinline__ void cgeo_map(const float P[1 << D][D], const float u
   }
 }
 
-// K = J^-1 by cofactors; false if J is singular or not finite.
+// K = J^-1 by cofactors; false if J is singular or not finite.  Explicitly
+// rounded operations (never contracted into FMAs), so that a mesh alone and
+// in a batch round alike.
 template <int D>
 __device__ __forceinline__ bool inv_jac(const float J[D][D], float K[D][D]) {
   if constexpr (D == 2) {
-    const float det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    const float det = __fsub_rn(__fmul_rn(J[0][0], J[1][1]), __fmul_rn(J[0][1], J[1][0]));
     if (!(fabsf(det) > 0.f) || !isfinite(det)) return false;
-    const float r = 1.f / det;
-    K[0][0] = J[1][1] * r;
-    K[0][1] = -J[0][1] * r;
-    K[1][0] = -J[1][0] * r;
-    K[1][1] = J[0][0] * r;
+    const float r = __frcp_rn(det);
+    K[0][0] = __fmul_rn(J[1][1], r);
+    K[0][1] = -__fmul_rn(J[0][1], r);
+    K[1][0] = -__fmul_rn(J[1][0], r);
+    K[1][1] = __fmul_rn(J[0][0], r);
   } else {
     float C[3][3];
 #pragma unroll
@@ -219,15 +221,16 @@ __device__ __forceinline__ bool inv_jac(const float J[D][D], float K[D][D]) {
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
         const int i1 = (i + 1) % 3, i2 = (i + 2) % 3, j1 = (j + 1) % 3, j2 = (j + 2) % 3;
-        C[i][j] = J[i1][j1] * J[i2][j2] - J[i1][j2] * J[i2][j1];
+        C[i][j] = __fsub_rn(__fmul_rn(J[i1][j1], J[i2][j2]), __fmul_rn(J[i1][j2], J[i2][j1]));
       }
-    const float det = J[0][0] * C[0][0] + J[0][1] * C[0][1] + J[0][2] * C[0][2];
+    const float det =
+        __fadd_rn(__fadd_rn(__fmul_rn(J[0][0], C[0][0]), __fmul_rn(J[0][1], C[0][1])), __fmul_rn(J[0][2], C[0][2]));
     if (!(fabsf(det) > 0.f) || !isfinite(det)) return false;
-    const float r = 1.f / det;
+    const float r = __frcp_rn(det);
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-      for (int j = 0; j < 3; ++j) K[i][j] = C[j][i] * r;
+      for (int j = 0; j < 3; ++j) K[i][j] = __fmul_rn(C[j][i], r);
   }
   return true;
 }
@@ -1965,11 +1968,13 @@ cudaError_t launch_p2g(const GroupArgs &G, int work_slot, cudaStream_t st) {
                         : launch_dep(p2g_resid<D, MODE, false, true>, G.grid, p2g_threads<D>(), p2g_smem<D, MODE>(),
                                      st, G, work_slot);
   else {
-    // a mapped mesh (always a group of one) needs K only for the force
+    // a mapped mesh needs K only for the force
     if constexpr (MODE != P2G_MOM)
       if (G.mapped)
-        return launch_dep(p2g_tile<D, MODE, true, true>, G.grid, p2g_threads<D>(), P2GRec<D, MODE, true>::SMEM, st,
-                          G, work_slot);
+        return G.ninst == 1 ? launch_dep(p2g_tile<D, MODE, true, true>, G.grid, p2g_threads<D>(),
+                                         P2GRec<D, MODE, true>::SMEM, st, G, work_slot)
+                            : launch_dep(p2g_tile<D, MODE, false, true>, G.grid, p2g_threads<D>(),
+                                         P2GRec<D, MODE, true>::SMEM, st, G, work_slot);
     return G.ninst == 1
                ? launch_dep(p2g_tile<D, MODE, true>, G.grid, p2g_threads<D>(), p2g_smem<D, MODE>(), st, G, work_slot)
                : launch_dep(p2g_tile<D, MODE, false>, G.grid, p2g_threads<D>(), p2g_smem<D, MODE>(), st, G, work_slot);
@@ -1991,6 +1996,9 @@ cudaError_t prepare_p2g() {
   if (e != cudaSuccess) return e;
   if constexpr (MODE != P2G_MOM) {
     e = cudaFuncSetAttribute(p2g_tile<D, MODE, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)P2GRec<D, MODE, true>::SMEM);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(p2g_tile<D, MODE, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)P2GRec<D, MODE, true>::SMEM);
     if (e != cudaSuccess) return e;
   }
@@ -2018,7 +2026,9 @@ cudaError_t launch_g2p_tile(const GroupArgs &G, cudaStream_t st) {
 
 template <int D, int NMODE>
 cudaError_t launch_node(const GroupArgs &G, int work_slot, cudaStream_t st) {
-  if (G.mapped) return launch_dep(node_tile<D, NMODE, true, true>, G.grid, NODE_T, 0, st, G, work_slot);
+  if (G.mapped)
+    return G.ninst == 1 ? launch_dep(node_tile<D, NMODE, true, true>, G.grid, NODE_T, 0, st, G, work_slot)
+                        : launch_dep(node_tile<D, NMODE, false, true>, G.grid, NODE_T, 0, st, G, work_slot);
   return G.ninst == 1 ? launch_dep(node_tile<D, NMODE, true>, G.grid, NODE_T, 0, st, G, work_slot)
                       : launch_dep(node_tile<D, NMODE, false>, G.grid, NODE_T, 0, st, G, work_slot);
 }
@@ -2026,9 +2036,10 @@ cudaError_t launch_node(const GroupArgs &G, int work_slot, cudaStream_t st) {
 template <int D, int GMODE>
 cudaError_t launch_g2p(const GroupArgs &G, cudaStream_t st) {
   const int nb = G.nblk_p * G2P_SUB;
-  cudaError_t e = G.mapped         ? launch_dep(g2p<D, GMODE, true, true>, nb, G2P_T, 0, st, G)
-                  : G.ninst == 1 ? launch_dep(g2p<D, GMODE, true>, nb, G2P_T, 0, st, G)
-                                 : launch_dep(g2p<D, GMODE, false>, nb, G2P_T, 0, st, G);
+  cudaError_t e = G.mapped ? (G.ninst == 1 ? launch_dep(g2p<D, GMODE, true, true>, nb, G2P_T, 0, st, G)
+                                            : launch_dep(g2p<D, GMODE, false, true>, nb, G2P_T, 0, st, G))
+                           : G.ninst == 1 ? launch_dep(g2p<D, GMODE, true>, nb, G2P_T, 0, st, G)
+                                          : launch_dep(g2p<D, GMODE, false>, nb, G2P_T, 0, st, G);
   if (e != cudaSuccess || !G.apex || GMODE == G2P_USF_ADVECT) return e;
   return G.ninst == 1 ? launch_dep(apex_band_k<D, true>, G.grid / 8, APEX_T, 0, st, G)
                       : launch_dep(apex_band_k<D, false>, G.grid / 8, APEX_T, 0, st, G);

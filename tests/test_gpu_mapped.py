@@ -302,15 +302,25 @@ def test_fp32_particles_leave_the_mapped_mesh():
     assert np.array_equal(gone, ref["cell"] < 0)
 
 
-def test_fp32_mapped_mesh_is_not_batched():
-    wl = fp32(W.warped_box(dim=2))
-    b = mpm.mpm_batch_create(None, max_slots=2)
+def test_fp32_mapped_meshes_in_a_batch_equal_their_runs_alone():
+    # mapped meshes (terrain, warped; 2D and 3D) and a Cartesian one in one
+    # batch: groups of their own kind, every result bit for bit its run alone
+    wls = [fp32(W.terrain_column(2)), fp32(W.warped_box(dim=2)), fp32(W.terrain_column(3)),
+           H.small_column(), fp32(W.warped_box(dim=3, scheme=W.USF))]
+    steps = 30
+    alone = [run_gpu(w, steps)[0] for w in wls]
+    sims = [mpm.Simulation(w, stress0=stress0(w)) for w in wls]
+    b = mpm.mpm_batch_create()
     try:
-        with mpm.Simulation(wl, stress0=stress0(wl)) as sim:
-            with pytest.raises(mpm.MPMError) as ei:
-                mpm.mpm_batch_admit(b, sim.h)
-            assert ei.value.status == mpm.MPM_ERR_STATE
-            sim.step(3)
-            assert sim.sync() == mpm.MPM_OK
+        for s_ in sims:
+            mpm.mpm_batch_admit(b, s_.h)
+        mpm.mpm_batch_step(b, steps)
+        assert mpm.mpm_batch_poll(b, len(wls)) == [mpm.MPM_OK] * len(wls)
+        for k, s_ in enumerate(sims):
+            snap, st = s_.read()
+            for f in ("pos", "vel", "stress", "strain", "vol", "cell"):
+                assert np.array_equal(snap[f], alone[k][f]), (k, f)
     finally:
         mpm.mpm_batch_destroy(b)
+        for s_ in sims:
+            s_.close()
