@@ -187,6 +187,22 @@ mpm_status mpm_add_particles(mpm_handle h, int64_t n, const double *pos, const d
  * replaces the coordinates. */
 mpm_status mpm_set_node_coordinates(mpm_handle h, const double *node_xyz);
 
+/* Far-field stresses on the faces of a mapped 2D mesh (BENCHMARK AND
+ * PERFORMANCE: the plate's uniform tension at its ends, where one logical
+ * face of a mesh fitted to the hole runs along the loaded end and a free
+ * edge).  face_stress: host, 6 faces (-x,+x,-y,+y,-z,+z) x 6 Voigt
+ * components (xx, yy, zz, xy, yz, xz), read during the call; NULL clears.
+ * The load of face f is the traction sigma_f . n of that uniform stress on
+ * each boundary edge of the face, lumped half to each end node (n the edge's
+ * outward normal): node a gets sum over its edges e of sigma_f . n_e |e| / 2.
+ * Added to the nodal force like the tractions of mpm_set_loads (whose
+ * damping applies too).  Mapped 2D meshes only, after
+ * mpm_set_node_coordinates (MPM_ERR_ARG otherwise; a Cartesian face takes
+ * sigma . n as a traction through mpm_set_loads); MPM_ERR_STATE while the
+ * mesh is admitted to a batch.  mpm_set_node_coordinates is not valid once
+ * face stresses are set (MPM_ERR_STATE). */
+mpm_status mpm_set_face_stress(mpm_handle h, const double *face_stress);
+
 /* Enqueue nsteps explicit steps on desc.stream and return without waiting.
  * Returns a latched error, if any, or MPM_OK.  Zero particles is valid. */
 mpm_status mpm_step(mpm_handle h, int64_t nsteps);

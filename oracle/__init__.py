@@ -44,6 +44,7 @@ class _Mesh(C.Structure):
         ("mass_tol", C.c_double),
         ("face_traction", (C.c_double * 3) * 6),
         ("damping", C.c_double),
+        ("face_stress", (C.c_double * 6) * 6),
     ]
 
 
@@ -145,6 +146,7 @@ class Mesh:
     mass_tol: float = 1e-12
     face_traction: tuple = ((0.0, 0.0, 0.0),) * 6   # per face, force per unit length (area)
     damping: float = 0.0                            # alpha of a = f / m - alpha v
+    face_stress: tuple = ((0.0,) * 6,) * 6          # mapped 2D mesh: uniform stress loading each face
 
     def c_struct(self) -> _Mesh:
         s = _Mesh()
@@ -162,6 +164,9 @@ class Mesh:
             for k in range(3):
                 s.face_traction[f][k] = float(self.face_traction[f][k])
         s.damping = float(self.damping)
+        for f in range(6):
+            for k in range(6):
+                s.face_stress[f][k] = float(self.face_stress[f][k])
         return s
 
     @property
@@ -421,6 +426,7 @@ def from_workload(wl, scheme=None) -> Oracle:
     """Oracle on a workload from paper_1909_13380_gb300.workloads (inputs only)."""
     mesh = Mesh(dim=wl.dim, n=wl.ncells, h=wl.h, origin=wl.origin, face_bc=wl.face_bc, face_mu=wl.face_mu,
                 g=wl.gravity, dt=wl.dt, scheme=wl.scheme if scheme is None else scheme,
-                face_traction=wl.face_traction, damping=wl.damping)
+                face_traction=wl.face_traction, damping=wl.damping,
+                face_stress=getattr(wl, "face_stress", ((0.0,) * 6,) * 6))
     st = State.create(wl.pos, wl.vel, wl.vol, wl.material["rho"], coh=wl.coh)
     return Oracle(mesh, Material(**wl.material), st, X=getattr(wl, "node_xyz", None))

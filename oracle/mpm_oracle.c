@@ -68,6 +68,13 @@
  *       normals of the node (made orthonormal in face order), a friction
  *       face applies R3 with that normal; fixed faces as before; face
  *       tractions (R9) are not defined there.
+ *   R13 a far-field stress on a face of a mapped 2D mesh (the plate's
+ *       "uniform tension" at its end, when one logical face runs along the
+ *       loaded end and a free edge): the traction sigma . n of a uniform
+ *       stress sigma on each boundary edge of the face, lumped to the edge's
+ *       two nodes -- node a gets sum over its edges e of sigma . n_e |e| / 2
+ *       (n_e the outward normal).  On a Cartesian face it would be the
+ *       traction sigma . n of R9.
  *
  * Layout: every particle vector is stored with 3 components and every
  * stress/strain with 6 Voigt components (xx, yy, zz, xy, yz, xz; tensor
@@ -102,6 +109,7 @@ typedef struct {
   double mass_tol;    /* R2 */
   double face_traction[6][3]; /* R9: traction on each face (force per length / area) */
   double damping;     /* R10: alpha, 1/s */
+  double face_stress[6][6];   /* R13: a uniform stress loading each face of a mapped 2D mesh (Voigt) */
 } om_mesh;
 
 typedef struct {
@@ -917,6 +925,36 @@ static void face_force(const om_mesh *M, const int ijk[3], int faces, double ft[
   }
 }
 
+/* R13: the force of the face stresses on node ijk of a mapped 2D mesh, added
+ * to ft -- for each face f of the node and each boundary edge e of f at the
+ * node: sigma_f . (n_e |e|) / 2, n_e |e| the edge vector turned outward. */
+static void face_stress_force(const om_mesh *M, const double *X, const int ijk[3], int faces, double ft[3]) {
+  if (M->dim != 2) return;
+  const double *x0 = X + 3 * node_index(M, ijk);
+  for (int f = 0; f < 4; ++f) {
+    if (!(faces >> f & 1)) continue;
+    const double *S = M->face_stress[f]; /* xx yy zz xy yz xz */
+    if (S[0] == 0.0 && S[1] == 0.0 && S[3] == 0.0) continue;
+    const int k = f / 2, t = 1 - k;
+    int in3[3] = {ijk[0], ijk[1], 0};
+    in3[k] += (f & 1) ? -1 : 1;
+    const double *xin = X + 3 * node_index(M, in3);
+    for (int sgn = -1; sgn <= 1; sgn += 2) {
+      int nb[3] = {ijk[0], ijk[1], 0};
+      nb[t] += sgn;
+      if (nb[t] < 0 || nb[t] > M->n[t]) continue;
+      const double *xb = X + 3 * node_index(M, nb);
+      double q0 = xb[1] - x0[1], q1 = -(xb[0] - x0[0]); /* the edge turned, |q| = |e| */
+      if (q0 * (xin[0] - x0[0]) + q1 * (xin[1] - x0[1]) > 0.0) {
+        q0 = -q0;
+        q1 = -q1;
+      }
+      ft[0] += 0.5 * (S[0] * q0 + S[3] * q1);
+      ft[1] += 0.5 * (S[3] * q0 + S[1] * q1);
+    }
+  }
+}
+
 /* Nodal solve: v = P/m, a = f/m, v' = v + a dt for active nodes (R2); the
  * constraints follow. stage: 0 = velocity only (USF stage one),
  * 1 = USL (v from P), 2 = USF force stage (v already set).  The force
@@ -943,6 +981,7 @@ static void node_solve(const om_mesh *M, const double *X, double *nm, double *nP
         }
         double ft[3];
         face_force(M, ijk, faces, ft);
+        if (X && faces) face_stress_force(M, X, ijk, faces, ft);
         for (int k = 0; k < 3; ++k) {
           if (stage == 1) v[k] = active ? nP[3 * i + k] / nm[i] : 0.0;
           a[k] = active ? (nf[3 * i + k] + ft[k]) / nm[i] - M->damping * v[k] : 0.0;
@@ -1066,6 +1105,9 @@ int oracle_step_mapped(const om_mesh *M, const double *X, const om_material *mat
   for (int f = 0; f < 6; ++f)  /* R12 */
     for (int k = 0; k < 3; ++k)
       if (M->face_traction[f][k] != 0.0) return OM_ARG;
+  for (int f = 0; f < 6; ++f)  /* R13: 2D only */
+    for (int k = 0; k < 6; ++k)
+      if (M->face_stress[f][k] != 0.0 && M->dim != 2) return OM_ARG;
   int status = OM_OK;
   for (int64_t s = 0; s < nsteps; ++s) {
     int st = step_once(M, X, pcell, mat, np, x, v, sig, eps, m, vol, epsp, coh, alive, work);

@@ -224,6 +224,10 @@ struct mpm_ctx {
   double *fn64 = nullptr;    // mapped FP64 mesh: face normals (D64Launch::fnorm)
   float4 *fn32 = nullptr;    // mapped FP32 mesh: face normals (Geo::fnorm)
   int64_t fnoff[6] = {};     // offset of each face's table
+  double *fl64 = nullptr;    // mapped 2D mesh under face stresses: force per face node (D64Launch::fload)
+  float4 *fl32 = nullptr;    // the same in FP32 (Geo::fload)
+  double fstress[6][6] = {}; // the face stresses (mpm_set_face_stress)
+  bool has_fstress = false;
   // shared
   int32_t *d_status = nullptr;  // FP64 path status word (FP32 path: s.ctr[C_STATUS])
   double *d_cons = nullptr;     // 8 results + partials
@@ -376,6 +380,7 @@ void fill_launch64(const mpm_ctx *h, D64Launch &L) {
   L.status = h->d_status;
   L.X = h->X64;
   L.fnorm = h->fn64;
+  L.fload = h->fl64;
   for (int f = 0; f < 6; ++f) L.fnoff[f] = h->fnoff[f];
 }
 
@@ -1149,11 +1154,11 @@ mpm_status mpm_set_loads(mpm_handle h, const double *face_traction, double dampi
       any |= t[f][k] != 0.0;
     }
   CK(cudaStreamSynchronize(h->st), "set_loads");
-  h->loads = any;
+  h->loads = any || h->has_fstress;
   h->damp = damping;
   memcpy(h->trac, t, sizeof(t));
   Geo &g = h->geo;
-  g.loads = any;
+  g.loads = h->loads;
   g.damp = (float)damping;
   for (int f = 0; f < 6; ++f)
     for (int k = 0; k < 3; ++k) g.trac[f][k] = (float)t[f][k];
@@ -1171,6 +1176,7 @@ mpm_status mpm_set_node_coordinates(mpm_handle h, const double *node_xyz) {
   for (int f = 0; f < 6; ++f)
     for (int k = 0; k < 3; ++k)
       if (h->trac[f][k] != 0.0) return fail(h, MPM_ERR_ARG, "node coordinates: the mesh carries face tractions");
+  if (h->has_fstress) return fail(h, MPM_ERR_STATE, "node coordinates: set them before the face stresses");
   const int D = h->d.dim;
   const int64_t nx = h->d.ncells[0] + 1, ny = h->d.ncells[1] + 1, nz = D == 3 ? h->d.ncells[2] + 1 : 1;
   const int64_t nn = nx * ny * nz;
@@ -1341,6 +1347,95 @@ mpm_status mpm_set_node_coordinates(mpm_handle h, const double *node_xyz) {
   return MPM_OK;
 }
 
+mpm_status mpm_set_face_stress(mpm_handle h, const double *face_stress) {
+  mpm_status s0 = check_handle(h);
+  if (s0 != MPM_OK) return s0;
+  if (h->batch) return fail(h, MPM_ERR_STATE, "face stress: the mesh is admitted to a batch");
+  if (!h->X64 || h->d.dim != 2) return fail(h, MPM_ERR_ARG, "face stress: mapped 2D meshes only");
+  double S[6][6] = {};
+  bool any = false;
+  for (int f = 0; f < 6; ++f)
+    for (int k = 0; k < 6; ++k) {
+      S[f][k] = face_stress ? face_stress[6 * f + k] : 0.0;
+      if (!std::isfinite(S[f][k])) return fail(h, MPM_ERR_ARG, "face stress: not finite");
+      if (f >= 4) S[f][k] = 0.0;
+      any |= S[f][k] != 0.0;
+    }
+  // node coordinates back from the device copy (3 per node)
+  const int64_t nx = h->d.ncells[0] + 1, ny = h->d.ncells[1] + 1;
+  std::vector<double> X3((size_t)(3 * nx * ny));
+  CK(cudaStreamSynchronize(h->st), "face stress");
+  CK(cudaMemcpy(X3.data(), h->X64, sizeof(double) * X3.size(), cudaMemcpyDeviceToHost), "face stress");
+  auto at = [&](int64_t i, int64_t j, int c) { return X3[3 * (i + nx * j) + c]; };
+  // the force of face f's stress on each of its nodes: for each boundary
+  // edge of f at the node, sigma_f . (the edge turned outward) / 2 -- the
+  // traction sigma . n of the uniform stress over the edge, half to each end
+  const int64_t nn = h->fnoff[3] + (h->d.ncells[0] + 1);  // the four faces' tables
+  std::vector<double> fl((size_t)(3 * nn), 0.0);
+  for (int f = 0; f < 4; ++f) {
+    const double *sf = S[f];
+    if (sf[0] == 0.0 && sf[1] == 0.0 && sf[3] == 0.0) continue;
+    const int k = f / 2, t = 1 - k, up = f & 1;
+    const int64_t nt_ = h->d.ncells[t] + 1;
+    for (int64_t it = 0; it < nt_; ++it) {
+      int64_t ij[2];
+      ij[k] = up ? h->d.ncells[k] : 0;
+      ij[t] = it;
+      int64_t in[2] = {ij[0], ij[1]};
+      in[k] += up ? -1 : 1;
+      const double dx = at(in[0], in[1], 0) - at(ij[0], ij[1], 0), dy = at(in[0], in[1], 1) - at(ij[0], ij[1], 1);
+      double fx = 0.0, fy = 0.0;
+      for (int sgn = -1; sgn <= 1; sgn += 2) {
+        int64_t nb[2] = {ij[0], ij[1]};
+        nb[t] += sgn;
+        if (nb[t] < 0 || nb[t] > h->d.ncells[t]) continue;
+        double qx = at(nb[0], nb[1], 1) - at(ij[0], ij[1], 1), qy = -(at(nb[0], nb[1], 0) - at(ij[0], ij[1], 0));
+        if (qx * dx + qy * dy > 0.0) {
+          qx = -qx;
+          qy = -qy;
+        }
+        fx += 0.5 * (sf[0] * qx + sf[3] * qy);
+        fy += 0.5 * (sf[3] * qx + sf[1] * qy);
+      }
+      const int64_t e = h->fnoff[f] + it;
+      fl[3 * e] += fx;
+      fl[3 * e + 1] += fy;
+    }
+  }
+  double *d64 = nullptr;
+  float4 *d32 = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (any && h->d.precision == MPM_FP32_MIXED) {
+    std::vector<float4> f4((size_t)nn);
+    for (int64_t i = 0; i < nn; ++i) f4[i] = make_float4((float)fl[3 * i], (float)fl[3 * i + 1], 0.f, 0.f);
+    e = cudaMalloc(&d32, sizeof(float4) * nn);
+    if (e == cudaSuccess) e = cudaMemcpy(d32, f4.data(), sizeof(float4) * nn, cudaMemcpyHostToDevice);
+  } else if (any) {
+    e = cudaMalloc(&d64, sizeof(double) * 3 * nn);
+    if (e == cudaSuccess) e = cudaMemcpy(d64, fl.data(), sizeof(double) * 3 * nn, cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) {
+    if (d32) cudaFree(d32);
+    if (d64) cudaFree(d64);
+    return cuda_fail(h, e, "face stress");
+  }
+  if (h->fl64) cudaFree(h->fl64);
+  if (h->fl32) cudaFree(h->fl32);
+  h->fl64 = d64;
+  h->fl32 = d32;
+  memcpy(h->fstress, S, sizeof(S));
+  h->has_fstress = any;
+  bool trac_any = false;
+  for (int f = 0; f < 6; ++f)
+    for (int k = 0; k < 3; ++k) trac_any |= h->trac[f][k] != 0.0;
+  h->loads = any || trac_any || h->damp > 0.0;
+  h->geo.loads = h->loads;
+  h->geo.fload = d32;
+  destroy_graphs(h->graph);  // the instance (and its loads) is captured in the step graph
+  h->grp_valid = false;
+  return MPM_OK;
+}
+
 mpm_status mpm_set_scan_fault(mpm_handle h, int32_t withhold_chunk, int32_t spin_limit) {
   mpm_status s0 = check_handle(h);
   if (s0 != MPM_OK) return s0;
@@ -1384,7 +1479,8 @@ mpm_status mpm_destroy(mpm_handle h) {
                   S.out_cnt, S.bucket_start, S.bucket_fill, S.movers, S.bucket, S.bucket_sorted, S.active,
                   S.bin_rec, S.scan_tot, S.ctr, S.slots1, S.slots2, S.slots_a, S.fepoch, S.aepoch, S.resid, S.node,
                   h->keys2, h->perm2, h->sort_scratch,
-                  h->pmem64, h->nmem64, h->X64, h->cgeo32, h->fn64, h->fn32, h->d_status, h->d_cons};
+                  h->pmem64, h->nmem64, h->X64, h->cgeo32, h->fn64, h->fn32, h->fl64, h->fl32, h->d_status,
+                  h->d_cons};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (int i = 0; i <= MPM_MAX_PHASES; ++i)

@@ -154,6 +154,19 @@ struct ThreadCorners {
 // position is kept in the frame of the particle's own cell, so FP32 resolves
 // it as finely as the Cartesian offset does.
 // ---------------------------------------------------------------------------
+// Face-stress forces of a mapped mesh's boundary node (Geo::fload), added to ft.
+template <int D>
+__device__ __forceinline__ void add_face_loads(const Geo &g, int faces, const int I[3], float ft[D]) {
+#pragma unroll
+  for (int f = 0; f < 2 * D; ++f)
+    if ((faces >> f) & 1) {
+      const float4 q = __ldg(g.fload + g.fnoff[f] + face_node_index<D>(f, I, g.nc));
+      ft[0] += q.x;
+      ft[1] += q.y;
+      if (D == 3) ft[D - 1] += q.z;
+    }
+}
+
 template <int D>
 __device__ __forceinline__ int cell_lin(const Geo &g, const int c[3]) {
   return c[0] + g.nc[0] * (c[1] + g.nc[1] * (D == 3 ? c[2] : 0));
@@ -1068,6 +1081,7 @@ __global__ void __launch_bounds__(NODE_T, ONE ? MPM_NODE_MINB : 8) node_tile(con
         if (NMODE == NODE_USL) {
           float ft[D];
           if (g.loads) face_force<D, float>(faces, Ig, g.nc, g.h, g.trac, ft);
+          if (MAP && g.loads && g.fload && faces) add_face_loads<D>(g, faces, Ig, ft);
 #pragma unroll
           for (int k = 0; k < D; ++k) {
             a[k] = g.loads ? (c1[1 + D + k] + ft[k]) * inv_m + g.g[k] - g.damp * v[k] : c1[1 + D + k] * inv_m + g.g[k];
@@ -1091,6 +1105,7 @@ __global__ void __launch_bounds__(NODE_T, ONE ? MPM_NODE_MINB : 8) node_tile(con
             bc_velocity<D, float>(faces, g.bc, v);
           float ft[D];
           if (g.loads) face_force<D, float>(faces, Ig, g.nc, g.h, g.trac, ft);
+          if (MAP && g.loads && g.fload && faces) add_face_loads<D>(g, faces, Ig, ft);
 #pragma unroll
           for (int k = 0; k < D; ++k) {
             a[k] = g.loads ? (f[k] + ft[k]) * inv_m + g.g[k] - g.damp * v[k] : f[k] * inv_m + g.g[k];

@@ -187,6 +187,14 @@ __global__ void node64(D64Launch L) {
     if (active) {
       double ft[D];
       if (L.loads) face_force<D, double>(faces, I, L.nc, L.h, L.trac, ft);
+      if (L.loads && L.fload && faces)  // face stresses on a mapped mesh
+#pragma unroll
+        for (int f = 0; f < 2 * D; ++f)
+          if ((faces >> f) & 1) {
+            const double *q = L.fload + 3 * (L.fnoff[f] + face_node_index<D>(f, I, L.nc));
+#pragma unroll
+            for (int k = 0; k < D; ++k) ft[k] += q[k];
+          }
 #pragma unroll
       for (int k = 0; k < D; ++k) {
         a[k] = L.loads ? (L.N.f[k][i] + ft[k]) / m - L.damp * v[k] : L.N.f[k][i] / m;

@@ -113,6 +113,9 @@ struct Geo {
   // (2D: the one other axis) -- at fnorm[fnoff[f] + i1 + (n_i1 + 1) i2]
   const float4 *fnorm;
   int fnoff[6];
+  // mapped 2D mesh under face stresses: the force on each face node, laid out
+  // as fnorm (null: none)
+  const float4 *fload;
 };
 template <int D> constexpr int CGEO_F4() { return D == 3 ? 6 : 2; }
 
@@ -365,6 +368,7 @@ struct D64Launch {
   int32_t *status;
   const double *X;  // mapped mesh: node coordinates, 3 per node (x fastest); null: Cartesian
   const double *fnorm;  // mapped mesh: face normals (3 per face node, laid out as Geo::fnorm)
+  const double *fload;  // mapped 2D mesh: face-stress force per face node (same layout), or null
   int64_t fnoff[6];
 };
 cudaError_t d64_step(const D64Launch &L, cudaStream_t st);

@@ -111,6 +111,7 @@ def load():
             "mpm_set_scan_fault": [vp, C.c_int32, C.c_int32],
             "mpm_set_loads": [vp, dp, C.c_double],
             "mpm_set_node_coordinates": [vp, dp],
+            "mpm_set_face_stress": [vp, dp],
             "mpm_material_update": [C.POINTER(mpm_material), C.c_int32, C.c_int64, dp, dp, dp, dp, dp, vp],
             "mpm_set_phase_timing": [vp, C.c_int32],
             "mpm_phase_times": [vp, C.POINTER(C.c_float), i32p],
@@ -348,6 +349,12 @@ def mpm_set_node_coordinates(h, node_xyz):
     _check(h, load().mpm_set_node_coordinates(h, _dp(X)), "mpm_set_node_coordinates")
 
 
+def mpm_set_face_stress(h, face_stress=None):
+    """face_stress: 6 x 6 (faces -x,+x,-y,+y,-z,+z; Voigt xx yy zz xy yz xz) or None."""
+    S = None if face_stress is None else np.ascontiguousarray(face_stress, np.float64).reshape(36)
+    _check(h, load().mpm_set_face_stress(h, _dp(S)), "mpm_set_face_stress")
+
+
 def mpm_set_scan_fault(h, withhold_chunk: int, spin_limit: int = 1 << 20):
     _check(h, load().mpm_set_scan_fault(h, int(withhold_chunk), int(spin_limit)), "mpm_set_scan_fault")
 
@@ -422,6 +429,9 @@ class Simulation:
             damp = float(getattr(wl, "damping", 0.0))
             if damp > 0.0 or (trac is not None and np.any(np.asarray(trac) != 0.0)):
                 mpm_set_loads(self.h, trac, damp)
+            fs = getattr(wl, "face_stress", None)
+            if fs is not None and np.any(np.asarray(fs) != 0.0):
+                mpm_set_face_stress(self.h, fs)
         except Exception:
             mpm_destroy(self.h)
             raise

@@ -48,6 +48,7 @@ class Workload:
     face_traction: tuple = ((0.0, 0.0, 0.0),) * 6   # per face: force per unit length (2D) or area (3D)
     damping: float = 0.0                            # alpha of the nodal damping a = f / m - alpha v
     node_xyz: np.ndarray | None = None              # mapped mesh: (nodes, dim) node coordinates, x fastest
+    face_stress: tuple = ((0.0,) * 6,) * 6          # mapped 2D mesh: uniform stress (Voigt) loading each face
 
     @property
     def n(self) -> int:
@@ -471,3 +472,69 @@ def warped_box(ncells=(12, 10, 8), h=0.1, n=3000, seed=SEED_BASE + 51, dim=3, sc
         face_mu=(0.0,) * 6, gravity=(0.0, 0.0, 0.0), dt=1e-3, scheme=scheme, precision=FP64_PLAIN,
         material=dict(model=LINEAR_ELASTIC, E=1e4, nu=0.3, rho=1000.0, phi=0.0, c=0.0, psi=0.0),
         pos=pos, vel=vel, vol=vol, steps=steps, node_xyz=X, meta=dict(stress0=sig))
+
+
+def ogrid_map(i, j, nr, nt, radius=0.5, length=4.0, width=2.5, grading=3.0):
+    """The quarter plate with a hole as one logical grid (an O-grid): logical
+    (i, j) in [0, nr] x [0, nt] (reals) to the plane.  j runs around the
+    hole's circle at uniform angle (0 to 90 degrees) and along the outer
+    boundary -- up the loaded end x = length (y from 0 to width), then along
+    the free edge y = width back to x = 0 -- with nodes spread in proportion to
+    the two lengths; i runs along the segment joining the two, graded towards
+    the hole: s = (exp(grading i / nr) - 1) / (exp(grading) - 1)."""
+    i = np.asarray(i, np.float64)
+    j = np.asarray(j, np.float64)
+    n1 = max(1, int(round(nt * width / (width + length))))
+    up = j <= n1
+    ox = np.where(up, length, length - length * (j - n1) / (nt - n1))
+    oy = np.where(up, width * j / n1, width)
+    th = 0.5 * math.pi * j / nt
+    ix, iy = radius * np.cos(th), radius * np.sin(th)
+    s = np.expm1(grading * i / nr) / math.expm1(grading)
+    return np.stack([ix + s * (ox - ix), iy + s * (oy - iy)], axis=-1)
+
+
+def plate_with_hole_ogrid(nr=20, nt=32, per_axis=2, grading=3.5, E=1e6, nu=0.3, rho=1000.0, sigma0=100.0, radius=0.5,
+                          precision=FP64_PLAIN, scheme=USF, steps=None, damping=None, cfl=0.4) -> Workload:
+    """The plate of plate_with_hole on a mapped mesh that fits the hole: the
+    O-grid of ogrid_map (nr cells along the rays, nt around), the logical
+    faces -x the hole (free), -y the symmetry line y = 0 and +y the symmetry
+    line x = 0 (rollers along their normals), +x the loaded end and the free
+    edge, loaded by the far-field stress sigma0 e_x e_x (traction sigma0 on
+    the end, none on the edge).  per_axis^2 particles per cell at the regular
+    sub-grid of its logical square, placed and weighted (volume = the map's
+    Jacobian times the logical area) by the smooth map.  Plane stress; dt the
+    fraction cfl of the wave's crossing time of the smallest cell edge,
+    damping as plate_with_hole's, run for the same physical time; h (a
+    length unit only, on a mapped mesh) the longest cell edge."""
+    I, J = np.meshgrid(np.arange(nr + 1), np.arange(nt + 1), indexing="xy")
+    X = ogrid_map(I.ravel(), J.ravel(), nr, nt, radius, grading=grading).reshape(-1, 2)
+    sub = (np.arange(per_axis) + 0.5) / per_axis
+    ci, cj = np.meshgrid(np.arange(nr), np.arange(nt), indexing="xy")
+    li = (ci.ravel()[:, None, None] + sub[None, None, :]).repeat(per_axis, axis=1)
+    lj = (cj.ravel()[:, None, None] + sub[None, :, None]).repeat(per_axis, axis=2)
+    li, lj = li.ravel(), lj.ravel()
+    om = lambda a, b: ogrid_map(a, b, nr, nt, radius, grading=grading)  # noqa: E731
+    pos = om(li, lj)
+    eps = 1e-6
+    dxi = (om(li + eps, lj) - om(li - eps, lj)) / (2 * eps)
+    dxj = (om(li, lj + eps) - om(li, lj - eps)) / (2 * eps)
+    vol = np.abs(dxi[:, 0] * dxj[:, 1] - dxi[:, 1] * dxj[:, 0]) / per_axis ** 2
+    Xg = X.reshape(nt + 1, nr + 1, 2)
+    edges = np.concatenate([np.linalg.norm(np.diff(Xg, axis=0), axis=-1).ravel(),
+                            np.linalg.norm(np.diff(Xg, axis=1), axis=-1).ravel()])
+    c = math.sqrt(E / (rho * (1.0 - nu * nu)))
+    dt = cfl * edges.min() / c
+    if damping is None:
+        damping = 2.0 * math.pi * c / (2.0 * 4.0)
+    if steps is None:   # plate_with_hole's 4000 steps of 0.2 h / c, h = 0.0625
+        steps = int(math.ceil(4000 * 0.2 * 0.0625 / c / dt))
+    fs = [(0.0,) * 6] * 6
+    fs[1] = (sigma0, 0.0, 0.0, 0.0, 0.0, 0.0)
+    return Workload(
+        name=f"plate_with_hole_ogrid_{nr}x{nt}", dim=2, ncells=(nr, nt, 1), h=edges.max(), origin=(0.0, 0.0, 0.0),
+        face_bc=(FREE, FREE, ROLLER, ROLLER, FREE, FREE), face_mu=(0.0,) * 6, gravity=(0.0, 0.0, 0.0), dt=dt,
+        scheme=scheme, precision=precision,
+        material=dict(model=PLANE_STRESS_ELASTIC, E=E, nu=nu, rho=rho, phi=0.0, c=0.0, psi=0.0),
+        pos=pos, vel=np.zeros_like(pos), vol=vol, steps=steps, damping=damping, node_xyz=X, face_stress=tuple(fs),
+        meta=dict(sigma0=sigma0, radius=radius))
