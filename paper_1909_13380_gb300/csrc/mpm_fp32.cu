@@ -1163,6 +1163,13 @@ __global__ void __launch_bounds__(G2P_T, MAP ? 4 : MPM_G2P_MINB) g2p(const __gri
   const int64_t q = (int64_t)(unit - (ONE ? 0 : G.pblk[ii])) * 256 + (blockIdx.x % G2P_SUB) * G2P_T + threadIdx.x;
   if (q >= I.n) return;
   const int j = I.perm_out[q];
+  // USF stages: the binning key travels with the permutation (both
+  // coalesced, both in flight at once), so the cell and its node records are
+  // known while the state and the offset are still on their way (measured:
+  // USF stress stage 1.71 -> 1.60 ms, advection 1.49 -> 1.45 ms on the 64M
+  // slope; the USL kernel, which spills more with it, keeps its order)
+  uint32_t key = 0;
+  if constexpr (GMODE != G2P_USL) key = I.keys_out[q];
   const int dead_start = I.s.ctr[C_DEAD_START];
   // the particle's state (all but its offset) travels to this thread's
   // shared-memory column while the node gather runs, without holding
@@ -1215,12 +1222,21 @@ __global__ void __launch_bounds__(G2P_T, MAP ? 4 : MPM_G2P_MINB) g2p(const __gri
     }
     return;
   }
-  const uint32_t key = I.keys_out[q];
+  if constexpr (GMODE == G2P_USL) key = I.keys_out[q];
   const int t = key >> LOCAL_BITS;
   int tc[3], lc[3];
   tile_coords(g, t, tc);
   local_coords<D>(key, lc);
   int cell[3] = {tc[0] * TX + lc[0], tc[1] * TY + lc[1], D == 3 ? tc[2] * TZ + lc[2] : 0};
+  if constexpr (GMODE != G2P_USL) {  // the cell's node records into L1 while the offset loads
+    const int gp = cell[0] + I.ns0 * cell[1] + I.ns1 * cell[2];
+#pragma unroll
+    for (int r = 0; r < (D == 3 ? 4 : 2); ++r) {
+      const float4 *nr = I.s.node + (D == 3 ? 2 : 1) * (gp + I.ns0 * (r & 1) + (D == 3 ? I.ns1 * (r >> 1) : 0));
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(nr));
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(nr + (D == 3 ? 3 : 1)));
+    }
+  }
   float u[D], w0[D], w1[D];
 #pragma unroll
   for (int k = 0; k < D; ++k) u[k] = I.A.off(k)[j];
