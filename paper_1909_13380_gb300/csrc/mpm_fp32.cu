@@ -1053,13 +1053,24 @@ __global__ void __launch_bounds__(NODE_T, ONE ? MPM_NODE_MINB : 8) node_tile(con
       float v[D], a[D], vn[D];
 #pragma unroll
       for (int k = 0; k < D; ++k) v[k] = a[k] = vn[k] = 0.f;
+      const int gi = Ig[0] + I.ns0 * Ig[1] + I.ns1 * Ig[2];
       float c1[1 + 2 * D];
-      if (NMODE == NODE_USL && MPM_FUSED_USL)
+      if (NMODE == NODE_USL && MPM_FUSED_USL) {
         gather_node_usl<D, 1 + 2 * D>(g, I.s.slots1, I.s.slots_a, Ig, lo, hi, tc, act, fmask27, amask27, c1);
-      else if (NMODE == NODE_USL)
+      } else if (NMODE == NODE_USL) {
         gather_node<D, 1 + 2 * D>(g, I.s.slots1, NCH1, Ig, lo, hi, act, c1);
-      else
+      } else if (NMODE == NODE_USF_V) {
         gather_node<D, 1 + D>(g, I.s.slots1, NCH1, Ig, lo, hi, act, c1);
+      } else {
+        // the USF force stage: the node's mass and its constrained velocity
+        // as the velocity stage left them in its record (the same values a
+        // second gather of the mass and momentum would give)
+        const float4 r = I.s.node[(D == 3 ? 2 : 1) * gi];
+        c1[0] = D == 3 ? r.w : r.z;
+        c1[1] = r.x;
+        c1[2] = r.y;
+        if (D == 3) c1[D] = r.z;
+      }
       const float m = c1[0];
       const int faces = node_faces<D>(g, Ig);
       // a mapped mesh's boundary node: its faces' outward normals
@@ -1077,7 +1088,7 @@ __global__ void __launch_bounds__(NODE_T, ONE ? MPM_NODE_MINB : 8) node_tile(con
       if (m > g.mass_tol) {
         const float inv_m = 1.f / m;
 #pragma unroll
-        for (int k = 0; k < D; ++k) v[k] = c1[1 + k] * inv_m;
+        for (int k = 0; k < D; ++k) v[k] = NMODE == NODE_USF_A ? c1[1 + k] : c1[1 + k] * inv_m;
         if (NMODE == NODE_USL) {
           float ft[D];
           if (g.loads) face_force<D, float>(faces, Ig, g.nc, g.h, g.trac, ft);
@@ -1099,10 +1110,6 @@ __global__ void __launch_bounds__(NODE_T, ONE ? MPM_NODE_MINB : 8) node_tile(con
         } else {
           float f[D];
           gather_node<D, D>(g, I.s.slots2, D, Ig, lo, hi, act, f);
-          if (MAP && faces)
-            bc_velocity_n<D, float>(faces, g.bc, nrm, v);
-          else
-            bc_velocity<D, float>(faces, g.bc, v);
           float ft[D];
           if (g.loads) face_force<D, float>(faces, Ig, g.nc, g.h, g.trac, ft);
           if (MAP && g.loads && g.fload && faces) add_face_loads<D>(g, faces, Ig, ft);
@@ -1117,13 +1124,16 @@ __global__ void __launch_bounds__(NODE_T, ONE ? MPM_NODE_MINB : 8) node_tile(con
             bc_full<D, float>(faces, g.bc, g.mu, g.dt, v, a, vn);
         }
       }
-      const int gi = Ig[0] + I.ns0 * Ig[1] + I.ns1 * Ig[2];
       const float *w = NMODE == NODE_USF_V ? v : vn;
+      // the velocity stage keeps the node's mass where the force stage reads
+      // it (3D: the spare fourth component; 2D: the acceleration slot, unused
+      // until the force stage writes it)
+      const float ms = NMODE == NODE_USF_V ? m : 0.f;
       if (D == 3) {
-        I.s.node[2 * gi] = make_float4(w[0], w[1], w[D - 1], 0.f);
+        I.s.node[2 * gi] = make_float4(w[0], w[1], w[D - 1], ms);
         I.s.node[2 * gi + 1] = make_float4(a[0], a[1], a[D - 1], 0.f);
       } else {
-        I.s.node[gi] = make_float4(w[0], w[1], a[0], a[1]);
+        I.s.node[gi] = make_float4(w[0], w[1], NMODE == NODE_USF_V ? ms : a[0], a[1]);
       }
     } while (0);
     if (!ONE) __syncwarp();  // the instance copy may be replaced next
