@@ -50,6 +50,12 @@ constexpr int G2P_SUB = 256 / G2P_T;    // G2P CTAs per 256-particle block of th
 #ifndef MPM_G2P_MINB
 #define MPM_G2P_MINB 8  // resident G2P CTAs per SM the register budget is sized for
 #endif
+#ifndef MPM_G2P_USL_EARLY
+#define MPM_G2P_USL_EARLY 0  // USL G2P: load the key with the permutation (as the USF stages do)
+#endif
+#ifndef MPM_G2P_USL_PREFETCH
+#define MPM_G2P_USL_PREFETCH 0  // USL G2P: prefetch the cell's node records into L1
+#endif
 
 // Instance of item x: the largest i with prefix[i] <= x (prefix[0] = 0).
 __device__ __forceinline__ int find_inst(const int32_t *prefix, int ninst, int x) {
@@ -1179,7 +1185,7 @@ __global__ void __launch_bounds__(G2P_T, MAP ? 4 : MPM_G2P_MINB) g2p(const __gri
   // USF stress stage 1.71 -> 1.60 ms, advection 1.49 -> 1.45 ms on the 64M
   // slope; the USL kernel, which spills more with it, keeps its order)
   uint32_t key = 0;
-  if constexpr (GMODE != G2P_USL) key = I.keys_out[q];
+  if constexpr (GMODE != G2P_USL || MPM_G2P_USL_EARLY) key = I.keys_out[q];
   const int dead_start = I.s.ctr[C_DEAD_START];
   // the particle's state (all but its offset) travels to this thread's
   // shared-memory column while the node gather runs, without holding
@@ -1232,13 +1238,13 @@ __global__ void __launch_bounds__(G2P_T, MAP ? 4 : MPM_G2P_MINB) g2p(const __gri
     }
     return;
   }
-  if constexpr (GMODE == G2P_USL) key = I.keys_out[q];
+  if constexpr (GMODE == G2P_USL && !MPM_G2P_USL_EARLY) key = I.keys_out[q];
   const int t = key >> LOCAL_BITS;
   int tc[3], lc[3];
   tile_coords(g, t, tc);
   local_coords<D>(key, lc);
   int cell[3] = {tc[0] * TX + lc[0], tc[1] * TY + lc[1], D == 3 ? tc[2] * TZ + lc[2] : 0};
-  if constexpr (GMODE != G2P_USL) {  // the cell's node records into L1 while the offset loads
+  if constexpr (GMODE != G2P_USL || MPM_G2P_USL_PREFETCH) {  // the cell's node records into L1 while the offset loads
     const int gp = cell[0] + I.ns0 * cell[1] + I.ns1 * cell[2];
 #pragma unroll
     for (int r = 0; r < (D == 3 ? 4 : 2); ++r) {

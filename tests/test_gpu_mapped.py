@@ -152,7 +152,7 @@ def test_particles_leave_the_mapped_mesh():
 def test_node_coordinate_errors():
     wl = W.warped_box(dim=2)
     X = np.asarray(wl.node_xyz)[:, :2]
-    # FP32 meshes have no mapped form
+    # an FP32 mesh that already holds particles
     with mpm.Simulation(replace(wl, precision=W.FP32_MIXED, node_xyz=None)) as sim:
         with pytest.raises(mpm.MPMError) as ei:
             mpm.mpm_set_node_coordinates(sim.h, X)
