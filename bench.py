@@ -646,9 +646,22 @@ def run_gb300(args):
         advance(so, args.advance, stream)
         timed_steps(so, args.warmup, stream, flush)
         mso = sum(timed_steps(so, ko, stream, flush)) / ko
+        # per-kernel phases of the same steps, as for the headline
+        mpm.mpm_set_phase_timing(so.h, True)
+        oph = []
+        with torch.cuda.stream(stream):
+            for _ in range(ko):
+                so.step(1)
+                oph.append(mpm.mpm_phase_times(so.h))
+                flush.zero_()
+        stream.synchronize()
+        mpm.mpm_set_phase_timing(so.h, False)
         sto = so.sync()
+        onames = ["binning", "p2g", "node", "g2p"] if osch == W.USL else \
+            ["binning", "p2g_mom", "node_v", "g2p_stress", "p2g_force", "node_a", "g2p_advect"]
         other = {"scheme": "USF" if osch == W.USF else "USL", "value": wl.n / (mso * 1e-3), "ms_per_step": mso,
                  "steps": ko, "timed_steps": f"{args.advance + args.warmup + 1}..{args.advance + args.warmup + ko}",
+                 "phases_ms": dict(zip(onames, [round(float(x), 5) for x in np.array(oph).mean(axis=0)])),
                  "status": mpm.STATUS_NAMES.get(sto, sto), "gpu_launches_per_step": mpm.mpm_step_kernels(so.h)}
         so.close()
 
@@ -731,7 +744,8 @@ def run_gb300(args):
                 "sample": accuracy["workload"], "steps": accuracy["steps"],
                 **{p: {k: accuracy[p][k] for k in ("disp", "vel", "stress", "dvol", "stress_max_rms",
                                                    "cells_differing")} for p in ("fp32_mixed", "fp64_plain")}},
-            "other_scheme": None if not other else {k: other[k] for k in ("scheme", "ms_per_step", "value")},
+            "other_scheme": None if not other else {k: other[k] for k in ("scheme", "ms_per_step", "value",
+                                                                          "phases_ms")},
             "batched": None if not batched else {k: batched[k] for k in ("particles", "value", "ms_per_batched_step",
                                                                        "batching_speedup")},
             "serving": short_serving(serving),

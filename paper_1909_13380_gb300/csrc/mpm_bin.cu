@@ -31,6 +31,7 @@
 // Every kernel runs over a table of independent instances (a single mesh is
 // a table of one); blocks and work items map to instances through prefix
 // arrays.
+#include <climits>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -297,7 +298,7 @@ __global__ void __launch_bounds__(SCAN_T) bin_scan_lb(const __grid_constant__ Gr
       I.new_start[e] = pn;
       I.s.bucket_start[e] = pb;
       if (ca[r] || (e == I.ntiles && cn[r] > 0)) {  // a binning item (the dead range comes last)
-        I.s.active[pa] = make_int4(e, pn, pn + cn[r], 0);
+        I.s.active[pa] = make_int4(e, pn, pn + cn[r], INT_MIN);
         I.s.bin_rec[pa] = make_int4(I.old_start[e], I.old_start[e + 1], pb, pb + cb[r]);
         if (cr[r]) I.s.resid[pr] = pa;
       }
@@ -430,7 +431,7 @@ __global__ void __launch_bounds__(SCAN1_T) bin_scan_one(const __grid_constant__ 
         I.s.bucket_start[e] = pb;
         if (act || (e == I.ntiles && cn[r] > 0)) {  // a binning item (the dead range comes last)
           const int k = oa + __popc(am & lt_mask);
-          I.s.active[k] = make_int4(e, pn, pn + cn[r], 0);
+          I.s.active[k] = make_int4(e, pn, pn + cn[r], INT_MIN);
           I.s.bin_rec[k] = make_int4(I.old_start[e], I.old_start[e + 1], pb, pb + cb[r]);
           if (cr[r]) I.s.resid[orr + __popc(rm & lt_mask)] = k;
         }
@@ -546,6 +547,8 @@ __global__ void __launch_bounds__(NT) bin_tiles(const __grid_constant__ GroupArg
           I.perm_out[ns + k] = os + k;
           I.keys_out[ns + k] = knew[os + k];
         }
+        // the range moved as a whole: P2G maps positions to slots without the permutation
+        if (tid == 0) reinterpret_cast<int *>(I.s.active + local)[3] = os - ns;
         if (tid == 0) s_work[(it + 1) & 1] = wnext;
         __syncthreads();
         continue;

@@ -26,6 +26,7 @@
 //              cell, written in binning order so the next step reads
 //              contiguously; particles that change tile are counted and
 //              listed for the next step's binning.
+#include <climits>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -49,12 +50,6 @@ constexpr int G2P_SUB = 256 / G2P_T;    // G2P CTAs per 256-particle block of th
 #endif
 #ifndef MPM_G2P_MINB
 #define MPM_G2P_MINB 8  // resident G2P CTAs per SM the register budget is sized for
-#endif
-#ifndef MPM_G2P_USL_EARLY
-#define MPM_G2P_USL_EARLY 0  // USL G2P: load the key with the permutation (as the USF stages do)
-#endif
-#ifndef MPM_G2P_USL_PREFETCH
-#define MPM_G2P_USL_PREFETCH 0  // USL G2P: prefetch the cell's node records into L1
 #endif
 
 // Instance of item x: the largest i with prefix[i] <= x (prefix[0] = 0).
@@ -325,6 +320,31 @@ constexpr int p2g_threads() {
   return P2GRec<D, P2G_USL>::CH;
 }
 
+// 4- and 16-byte asynchronous global -> shared copies (each thread later reads only
+// what it copied itself, so a wait on its own copies is all it needs).
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// The active-tile record (tile, new start, new end, slot shift or INT_MIN) of
+// P2G work item w.
+template <bool ONE>
+__device__ __forceinline__ const int4 *act_rec(const GroupArgs &G, int w) {
+  if constexpr (ONE) {
+    return G.one.s.active + w;
+  } else {
+    const int i = find_inst(G.act_items, G.ninst, w);
+    return G.inst[i].s.active + (w - G.act_items[i]);
+  }
+}
+
 // Slot of particle i of a chunk: the low three bits are XORed with the next
 // three, so that the cells of a warp, whose current particles are often a
 // multiple of eight apart, read different shared-memory banks.
@@ -472,6 +492,7 @@ __global__ void __launch_bounds__(P2GRec<D, MODE>::CH, MAP ? 4 : p2g_min_blocks<
   float *cellP = reinterpret_cast<float *>(sm4);  // [64][NV], after the chunks
   __shared__ int cs[CELLS_PER_TILE], ce[CELLS_PER_TILE], stamp[CELLS_PER_TILE];
   __shared__ int s_work[2];
+  __shared__ int4 s_ar[2];  // the item's active-tile record; the next one lands during the box phase
   __shared__ InstArgs sI;
   const int tid = threadIdx.x;
   const int my_cell = tid / CPC, my_cp = tid % CPC;  // corners my_cp + r * CPC
@@ -480,7 +501,10 @@ __global__ void __launch_bounds__(P2GRec<D, MODE>::CH, MAP ? 4 : p2g_min_blocks<
   pdl_wait();
   // items: first the CTA's own (blockIdx.x), then gridDim.x + the work counter
   const int total = G.act_items[G.ninst];
-  if (tid == 0) s_work[0] = blockIdx.x;
+  if (tid == 0) {
+    s_work[0] = blockIdx.x;
+    if ((int)blockIdx.x < total) s_ar[0] = *act_rec<ONE>(G, blockIdx.x);
+  }
   __syncthreads();
   int chunk_id = 0, loaded = -1;
 
@@ -499,7 +523,7 @@ __global__ void __launch_bounds__(P2GRec<D, MODE>::CH, MAP ? 4 : p2g_min_blocks<
     const InstArgs &I = inst_ref<ONE>(G, sI);
     const Geo &g = I.geo;
     float *slots_out = MODE == P2G_FORCE ? I.s.slots2 : I.s.slots1;
-    const int4 ar = I.s.active[ONE ? wi : wi - G.act_items[ii]];
+    const int4 ar = s_ar[it & 1];
     const int t = ar.x, s = ar.y, e = ar.z;
     int tco[3] = {0, 0, 0};
     if (MAP) tile_coords(g, t, tco);
@@ -514,7 +538,10 @@ __global__ void __launch_bounds__(P2GRec<D, MODE>::CH, MAP ? 4 : p2g_min_blocks<
       const int q = c0 + tid;
       const int c1 = min(e, c0 + CH);
       if (q < c1) {
-        const int j = I.perm_out[q];
+        // the binning moved the tile's range as a whole (slot q + dj holds
+        // position q): the loads need not wait for the permutation
+        const int dj = s_ar[it & 1].w;
+        const int j = dj != INT_MIN ? q + dj : I.perm_out[q];
         const int lc = I.keys_out[q] & (CELLS_PER_TILE - 1);
         float f[4 * NQ];
 #pragma unroll
@@ -656,6 +683,10 @@ __global__ void __launch_bounds__(P2GRec<D, MODE>::CH, MAP ? 4 : p2g_min_blocks<
     for (int r = 0; r < CPT; ++r)
 #pragma unroll
       for (int ch = 0; ch < NCH; ++ch) cellP[my_cell * NV + (my_cp + r * CPC) * NCH + ch] = acc[r][ch];
+    if (tid == 0 && wnext < total) {  // the next item's record, in flight during the box phase
+      cp_async16(&s_ar[(it + 1) & 1], act_rec<ONE>(G, wnext));
+      cp_async_commit();
+    }
     __syncthreads();
     for (int b = tid; b < BN; b += CH) {
       const int bx = b % (TX + 1);
@@ -680,7 +711,10 @@ __global__ void __launch_bounds__(P2GRec<D, MODE>::CH, MAP ? 4 : p2g_min_blocks<
 #pragma unroll
       for (int ch = 0; ch < NCH; ++ch) slots_out[((int64_t)t * NCH + ch) * BN + b] = ta[ch].value();
     }
-    if (tid == 0) s_work[(it + 1) & 1] = wnext;
+    if (tid == 0) {
+      s_work[(it + 1) & 1] = wnext;
+      cp_async_wait_all();
+    }
     __syncthreads();
   }
 }
@@ -1146,14 +1180,6 @@ __global__ void __launch_bounds__(NODE_T, ONE ? MPM_NODE_MINB : 8) node_tile(con
   }
 }
 
-// 4-byte asynchronous global -> shared copies (each thread later reads only
-// what it copied itself, so a wait on its own copies is all it needs).
-__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // ---------------------------------------------------------------------------
 // G2P: one thread per particle in binning order, G2P_T-thread CTAs.  Right
@@ -1176,17 +1202,14 @@ __global__ void __launch_bounds__(G2P_T, MAP ? 4 : MPM_G2P_MINB) g2p(const __gri
   if (!ONE) __syncthreads();
   const InstArgs &I = inst_ref<ONE>(G, sI);
   const Geo &g = I.geo;
+  // the binning key travels with the permutation (both coalesced, in flight
+  // at once): the cell, its node records and whether the particle is still
+  // in the mesh are known while the offset and the state are on their way
   const int64_t q = (int64_t)(unit - (ONE ? 0 : G.pblk[ii])) * 256 + (blockIdx.x % G2P_SUB) * G2P_T + threadIdx.x;
   if (q >= I.n) return;
   const int j = I.perm_out[q];
-  // USF stages: the binning key travels with the permutation (both
-  // coalesced, both in flight at once), so the cell and its node records are
-  // known while the state and the offset are still on their way (measured:
-  // USF stress stage 1.71 -> 1.60 ms, advection 1.49 -> 1.45 ms on the 64M
-  // slope; the USL kernel, which spills more with it, keeps its order)
-  uint32_t key = 0;
-  if constexpr (GMODE != G2P_USL || MPM_G2P_USL_EARLY) key = I.keys_out[q];
-  const int dead_start = I.s.ctr[C_DEAD_START];
+  const uint32_t key = I.keys_out[q];
+  const bool gone = (int)(key >> LOCAL_BITS) >= I.ntiles;  // left the mesh in an earlier step
   // the particle's state (all but its offset) travels to this thread's
   // shared-memory column while the node gather runs, without holding
   // registers: stress-stage fields (sig, eps, J-1, eps_p), then kinematic
@@ -1196,7 +1219,7 @@ __global__ void __launch_bounds__(G2P_T, MAP ? 4 : MPM_G2P_MINB) g2p(const __gri
   constexpr int S_COH = KIN ? S_ID + 1 : S_VEL;
   __shared__ float stg[S_COH + 1][G2P_T];
   const bool has_coh = I.A.coh() != nullptr;
-  if (q < dead_start) {
+  if (!gone) {
     if (STR) {
 #pragma unroll
       for (int i = 0; i < NS; ++i) {
@@ -1215,9 +1238,9 @@ __global__ void __launch_bounds__(G2P_T, MAP ? 4 : MPM_G2P_MINB) g2p(const __gri
     if (has_coh) cp_async4(&stg[S_COH][threadIdx.x], I.A.coh() + j);
     cp_async_commit();
   }
-  if (q >= dead_start) {  // left the mesh earlier: carried over unchanged
+  if (gone) {  // carried over unchanged
     if (GMODE != G2P_USF_STRESS) {
-      I.B.key()[q] = I.A.key()[j];
+      I.B.key()[q] = key;
       I.B.id()[q] = I.A.id()[j];
       I.B.mass()[q] = I.A.mass()[j];
 #pragma unroll
@@ -1238,13 +1261,12 @@ __global__ void __launch_bounds__(G2P_T, MAP ? 4 : MPM_G2P_MINB) g2p(const __gri
     }
     return;
   }
-  if constexpr (GMODE == G2P_USL && !MPM_G2P_USL_EARLY) key = I.keys_out[q];
   const int t = key >> LOCAL_BITS;
   int tc[3], lc[3];
   tile_coords(g, t, tc);
   local_coords<D>(key, lc);
   int cell[3] = {tc[0] * TX + lc[0], tc[1] * TY + lc[1], D == 3 ? tc[2] * TZ + lc[2] : 0};
-  if constexpr (GMODE != G2P_USL || MPM_G2P_USL_PREFETCH) {  // the cell's node records into L1 while the offset loads
+  {  // the cell's node records into L1 while the offset loads
     const int gp = cell[0] + I.ns0 * cell[1] + I.ns1 * cell[2];
 #pragma unroll
     for (int r = 0; r < (D == 3 ? 4 : 2); ++r) {

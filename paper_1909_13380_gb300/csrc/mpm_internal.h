@@ -150,8 +150,10 @@ struct StepBufs {
   int32_t *movers;         // n: storage slots of tile movers
   int32_t *bucket;         // n: movers grouped by destination tile
   int32_t *bucket_sorted;  // n: scratch for large buckets (binning), then the apex-band queue (G2P)
-  int4 *active;            // ntiles + 2: active tiles in ascending order, (tile, new start, new end, -),
-                           // then the dead range (tile = ntiles) when it is not empty: the binning items
+  int4 *active;            // ntiles + 2: active tiles in ascending order, (tile, new start, new end,
+                           // old start - new start when the binning moved the tile's range as a whole,
+                           // else INT_MIN), then the dead range (tile = ntiles) when it is not empty:
+                           // the binning items
   int4 *bin_rec;           // ntiles + 2: per binning item (old start, old end, bucket start, bucket end)
   int32_t *scan_tot;       // 8 per chunk of the tile scan (look-back flag, totals, prefix)
   int32_t *ctr;            // C_NCTR counters
