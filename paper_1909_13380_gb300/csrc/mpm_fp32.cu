@@ -27,6 +27,7 @@
 //              contiguously; particles that change tile are counted and
 //              listed for the next step's binning.
 #include <climits>
+#include <type_traits>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -143,6 +144,38 @@ struct ThreadCorners {
     }
   }
 };
+
+// Four corners per thread (3D): the x bit is the thread's (cp & 1), corner r
+// has y bit r & 1 and z bit r >> 1.  The products are those of
+// ThreadCorners (and so of corner_shape), formed once per y bit.
+struct ThreadCorners4 {
+  float wxy[2], gx[2], gy[2], gz[2], wz[2];
+  __device__ __forceinline__ ThreadCorners4(const float *u, int cp, float inv_h) {
+    const bool ux = cp & 1;
+    const float wx = ux ? 0.5f + u[0] : 0.5f - u[0];
+    const float ty = inv_h * wx;
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const float wy = b ? 0.5f + u[1] : 0.5f - u[1];
+      wxy[b] = wx * wy;
+      const float tx = inv_h * wy;
+      gx[b] = ux ? tx : -tx;
+      gy[b] = b ? ty : -ty;
+      gz[b] = ty * wy;
+    }
+    wz[0] = 0.5f - u[2];
+    wz[1] = 0.5f + u[2];
+  }
+  __device__ __forceinline__ void corner(int r, float &N, float G[3]) const {
+    const int b = r & 1, z = r >> 1;
+    N = wxy[b] * wz[z];
+    G[0] = gx[b] * wz[z];
+    G[1] = gy[b] * wz[z];
+    G[2] = z ? gz[b] : -gz[b];
+  }
+};
+template <int D, int CPT>
+using CornersOf = typename std::conditional<CPT == 4, ThreadCorners4, ThreadCorners<D>>::type;
 
 // ---------------------------------------------------------------------------
 // Mapped (isoparametric) cells (ISOPARAMETRIC MESH) in the FP32 path.  A
@@ -286,17 +319,22 @@ __device__ __forceinline__ void cgeo_solve(const float P[1 << D][D], const float
 // Value index v = corner * NCH + channel; channels USL (m, P_k, f_k), MOM
 // (m, P_k), FORCE (f_k).
 // ---------------------------------------------------------------------------
-template <int D, int MODE, bool MAP = false>
+// WIDE (3D): four corners per thread, two threads per cell, 128 threads per
+// tile, each staging two particles of a chunk.
+template <int D, int MODE, bool MAP = false, bool WIDE = false>
 struct P2GRec {
+  static_assert(!WIDE || D == 3, "four corners per thread: 3D");
   static constexpr bool HAS_M = MODE != P2G_FORCE, HAS_F = MODE != P2G_MOM;
   // nV sig (xx yy zz xy yz xz | xx yy xy); on a mapped mesh the full D x D
   // matrix nV sig K^T (row-major), K the inverse of the cell map's Jacobian
   static constexpr int NSV = MAP ? D * D : (D == 3 ? 6 : 3);
   static constexpr int NF = D + (HAS_M ? 1 + D : 0) + (HAS_F ? NSV : 0);
   static constexpr int NQ = (NF + 3) / 4;                      // float4 chunks per particle
-  static constexpr int CPT = D == 3 ? 2 : 1;                   // corners per thread
+  static constexpr int CPT = D == 3 ? (WIDE ? 4 : 2) : 1;      // corners per thread
   static constexpr int CPC = (1 << D) / CPT;                   // threads per cell
-  static constexpr int CH = CELLS_PER_TILE * CPC;              // threads = particles per chunk
+  static constexpr int NT = CELLS_PER_TILE * CPC;              // threads
+  static constexpr int CH = 256;                               // particles per chunk
+  static constexpr int PPT = CH / NT;                          // particles each thread stages
   static constexpr int NV = (1 << D) * p2g_channels<D, MODE>();
   static constexpr size_t REC_BYTES = sizeof(float4) * NQ * CH;
   static constexpr size_t CELLP_BYTES = sizeof(float) * CELLS_PER_TILE * NV;
@@ -310,6 +348,9 @@ template <int D, int MODE, bool ONE>
 constexpr int p2g_min_blocks() {
   return (D == 3 && MODE == P2G_USL && !ONE) ? 4 : MPM_P2G_MINB;
 }
+#ifndef MPM_P2G_WIDE_MINB
+#define MPM_P2G_WIDE_MINB 8  // resident 128-thread P2G CTAs per SM (64 registers)
+#endif
 
 template <int D, int MODE>
 constexpr size_t p2g_smem() {
@@ -317,8 +358,17 @@ constexpr size_t p2g_smem() {
 }
 template <int D>
 constexpr int p2g_threads() {
-  return P2GRec<D, P2G_USL>::CH;
+  return P2GRec<D, P2G_USL>::NT;
 }
+// Four corners per thread: the Cartesian 3D mass and momentum P2G of USF
+// (64M slope 786 -> 759 us; with the seven channels of USL it was slower,
+// 1116 -> 1268 us at 64 registers, and the force-only P2G no faster).
+template <int D, int MODE, bool MAP>
+constexpr bool p2g_wide() {
+  return D == 3 && !MAP && MODE == P2G_MOM;
+}
+template <int D, int MODE, bool MAP>
+using P2GTile = P2GRec<D, MODE, MAP, p2g_wide<D, MODE, MAP>()>;
 
 // 4- and 16-byte asynchronous global -> shared copies (each thread later reads only
 // what it copied itself, so a wait on its own copies is all it needs).
@@ -476,12 +526,13 @@ __device__ __forceinline__ void cells_to_slot(const float *cellP, float *slots_o
 }
 
 template <int D, int MODE, bool ONE, bool MAP = false>
-__global__ void __launch_bounds__(P2GRec<D, MODE>::CH, MAP ? 4 : p2g_min_blocks<D, MODE, ONE>())
+__global__ void __launch_bounds__(P2GTile<D, MODE, MAP>::NT,
+                                  MAP ? 4 : (p2g_wide<D, MODE, MAP>() ? MPM_P2G_WIDE_MINB : p2g_min_blocks<D, MODE, ONE>()))
     p2g_tile(const __grid_constant__ GroupArgs G, int work_slot) {
-  using R = P2GRec<D, MODE, MAP>;
+  using R = P2GTile<D, MODE, MAP>;
   constexpr int NCH = p2g_channels<D, MODE>();
   constexpr int NV = R::NV;
-  constexpr int CH = R::CH;
+  constexpr int CH = R::CH, NT = R::NT, PPT = R::PPT;
   constexpr int NQ = R::NQ;
   constexpr int CPT = R::CPT, CPC = R::CPC;
   constexpr int BN = box_nodes<D>();
@@ -534,9 +585,12 @@ __global__ void __launch_bounds__(P2GRec<D, MODE>::CH, MAP ? 4 : p2g_min_blocks<
       for (int ch = 0; ch < NCH; ++ch) acc[r][ch] = 0.f;
 
     for (int c0 = s; c0 < e; c0 += CH) {
-      // ---- stage this chunk: particle q = c0 + tid
-      const int q = c0 + tid;
+      // ---- stage this chunk: particles q = c0 + ps, ps = tid + pp * NT
       const int c1 = min(e, c0 + CH);
+#pragma unroll
+      for (int pp = 0; pp < PPT; ++pp) {
+      const int ps = tid + pp * NT;
+      const int q = c0 + ps;
       if (q < c1) {
         // the binning moved the tile's range as a whole (slot q + dj holds
         // position q): the loads need not wait for the permutation
@@ -609,17 +663,18 @@ __global__ void __launch_bounds__(P2GRec<D, MODE>::CH, MAP ? 4 : p2g_min_blocks<
             f[o + 2] = nV * S.sig(3)[js];
           }
         }
-        const int sl = rec_slot(tid);
+        const int sl = rec_slot(ps);
 #pragma unroll
         for (int k = 0; k < NQ; ++k) rec[k * CH + sl] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
         // run boundaries of the cell within the chunk
         const bool first = q == c0 || (int)(I.keys_out[q - 1] & (CELLS_PER_TILE - 1)) != lc;
         const bool last = q == c1 - 1 || (int)(I.keys_out[q + 1] & (CELLS_PER_TILE - 1)) != lc;
         if (first) {
-          cs[lc] = tid;
+          cs[lc] = ps;
           stamp[lc] = chunk_id;
         }
-        if (last) ce[lc] = tid + 1;
+        if (last) ce[lc] = ps + 1;
+      }
       }
       __syncthreads();
       // ---- accumulate my (cell, corner) pairs over the cell's particles in order
@@ -636,8 +691,9 @@ __global__ void __launch_bounds__(P2GRec<D, MODE>::CH, MAP ? 4 : p2g_min_blocks<
             f[4 * k + 2] = rv.z;
             f[4 * k + 3] = rv.w;
           }
-          static_assert(CPT == (D == 3 ? 2 : 1) && CPC == 4, "corners my_cp + 4 r: z bit = r");
-          const ThreadCorners<D> tc(f, my_cp, g.inv_h);
+          static_assert(CPT == 4 ? (D == 3 && CPC == 2) : (CPT == (D == 3 ? 2 : 1) && CPC == 4),
+                        "corners my_cp + CPC r");
+          const CornersOf<D, CPT> tc(f, my_cp, g.inv_h);
 #pragma unroll
           for (int r = 0; r < CPT; ++r) {
             float N, Gr[D];
@@ -688,7 +744,7 @@ __global__ void __launch_bounds__(P2GRec<D, MODE>::CH, MAP ? 4 : p2g_min_blocks<
       cp_async_commit();
     }
     __syncthreads();
-    for (int b = tid; b < BN; b += CH) {
+    for (int b = tid; b < BN; b += NT) {
       const int bx = b % (TX + 1);
       const int by = (b / (TX + 1)) % (TY + 1);
       const int bz = D == 3 ? b / ((TX + 1) * (TY + 1)) : 0;
@@ -949,7 +1005,11 @@ __device__ __forceinline__ unsigned node_tiles_mask(const Geo &g, unsigned nmask
 
 // Sum channels of node I over the slots of the active tiles `act` (from
 // node_tiles_mask), in ascending tile order, so that the value does not depend on
-// which tile computes it.
+// which tile computes it.  For up to four channels the loads of two holders
+// are issued together before their sums, so a node held by two tiles (a box
+// face node) waits for one memory latency, not two (measured: USF nodal
+// stages 287 -> 277 and 316 -> 305 us on the 64M-particle slope; the same
+// form of the USL gather, seven channels, was slower: 316 -> 349 us).
 template <int D, int NOUT>
 __device__ __forceinline__ void gather_node(const Geo &g, const float *slots, int nch, const int I[3], const int lo[3],
                                             const int hi[3], unsigned act, float out[NOUT]) {
@@ -958,17 +1018,49 @@ __device__ __forceinline__ void gather_node(const Geo &g, const float *slots, in
   TwoAcc<float> acc[NOUT];
 #pragma unroll
   for (int c = 0; c < NOUT; ++c) acc[c].init();
-  int idx = 0;
-  for (int z = lo[2]; z <= hi[2]; ++z)
-    for (int y = lo[1]; y <= hi[1]; ++y)
-      for (int x = lo[0]; x <= hi[0]; ++x, ++idx) {
-        if (!((act >> idx) & 1u)) continue;
-        const int t2 = x + g.nt[0] * (y + g.nt[1] * z);
-        const int bx = I[0] - x * TX, by = I[1] - y * TY, bz = D == 3 ? I[2] - z * TZ : 0;
-        const int bl = bx + (TX + 1) * (by + (TY + 1) * bz);
+  if constexpr (NOUT > 4) {
+    int idx = 0;
+    for (int z = lo[2]; z <= hi[2]; ++z)
+      for (int y = lo[1]; y <= hi[1]; ++y)
+        for (int x = lo[0]; x <= hi[0]; ++x, ++idx) {
+          if (!((act >> idx) & 1u)) continue;
+          const int t2 = x + g.nt[0] * (y + g.nt[1] * z);
+          const int bx = I[0] - x * TX, by = I[1] - y * TY, bz = D == 3 ? I[2] - z * TZ : 0;
+          const int bl = bx + (TX + 1) * (by + (TY + 1) * bz);
 #pragma unroll
-        for (int c = 0; c < NOUT; ++c) acc[c].add(slots[((int64_t)t2 * nch + c) * BN + bl]);
-      }
+          for (int c = 0; c < NOUT; ++c) acc[c].add(slots[((int64_t)t2 * nch + c) * BN + bl]);
+        }
+  } else {
+    // the active holders in ascending tile order, as 3-bit offsets from lo
+    unsigned codes = 0;
+    int nh = 0, idx = 0;
+    for (int z = lo[2]; z <= hi[2]; ++z)
+      for (int y = lo[1]; y <= hi[1]; ++y)
+        for (int x = lo[0]; x <= hi[0]; ++x, ++idx)
+          if ((act >> idx) & 1u) {
+            codes |= (unsigned)((x - lo[0]) | ((y - lo[1]) << 1) | ((z - lo[2]) << 2)) << (3 * nh);
+            ++nh;
+          }
+    for (int h0 = 0; h0 < nh; h0 += 2) {
+      float v[2][NOUT];
+#pragma unroll
+      for (int k = 0; k < 2; ++k)
+        if (h0 + k < nh) {
+          const unsigned cd = (codes >> (3 * (h0 + k))) & 7u;
+          const int x = lo[0] + (int)(cd & 1u), y = lo[1] + (int)((cd >> 1) & 1u), z = lo[2] + (int)(cd >> 2);
+          const int t2 = x + g.nt[0] * (y + g.nt[1] * z);
+          const int bx = I[0] - x * TX, by = I[1] - y * TY, bz = D == 3 ? I[2] - z * TZ : 0;
+          const int bl = bx + (TX + 1) * (by + (TY + 1) * bz);
+#pragma unroll
+          for (int c = 0; c < NOUT; ++c) v[k][c] = slots[((int64_t)t2 * nch + c) * BN + bl];
+        }
+#pragma unroll
+      for (int k = 0; k < 2; ++k)
+        if (h0 + k < nh)
+#pragma unroll
+          for (int c = 0; c < NOUT; ++c) acc[c].add(v[k][c]);
+    }
+  }
 #pragma unroll
   for (int c = 0; c < NOUT; ++c) out[c] = acc[c].value();
 }
@@ -1006,6 +1098,124 @@ __device__ __forceinline__ void gather_node_usl(const Geo &g, const float *slots
   for (int c = 0; c < NOUT; ++c) out[c] = acc[c].value();
 }
 
+// The slot entries a tile needs for the nodes it owns when all its lower
+// neighbours are active (its box's nodes at local 1..T on every axis): for
+// each holder offset hd = dx + 2 dy + 4 dz (d in {0, 1}^D: ascending tile
+// order), the owned nodes with b_k = T_k wherever d_k = 1, indexed over the
+// other axes (x fastest).  They number exactly the box's nodes.
+template <int D>
+struct OwnEntries {
+  __host__ __device__ static constexpr int T(int k) {
+    return k == 0 ? Tile<D>::TX : (k == 1 ? Tile<D>::TY : (D == 3 ? Tile<D>::TZ : 1));
+  }
+  __host__ __device__ static constexpr int count(int hd) {
+    int n = 1;
+    for (int k = 0; k < D; ++k)
+      if (!((hd >> k) & 1)) n *= T(k);
+    return n;
+  }
+  __host__ __device__ static constexpr int base(int hd) {
+    int b = 0;
+    for (int h = 0; h < hd; ++h) b += count(h);
+    return b;
+  }
+  static_assert(base(1 << D) == box_nodes<D>(), "one entry per box node");
+  // entry of owned node b (local 1..T) and holder hd (b_k = T_k where d_k = 1)
+  __device__ static __forceinline__ int entry(int hd, const int b[3]) {
+    int e = 0, st = 1;
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+      if (!((hd >> k) & 1)) {
+        e += (b[k] - 1) * st;
+        st *= T(k);
+      }
+    return base(hd) + e;
+  }
+};
+
+// Stage the slot entries (NST channels of `slots`) of the nodes tile tc owns
+// into sv[c][entry], two entries per lane with their loads in flight together,
+// so the warp waits for two memory latencies per tile rather than one per
+// holder of each of its nodes.  Entries of inactive holders are not loaded
+// (never read).
+template <int D, int NST>
+__device__ __forceinline__ void stage_own_entries(const Geo &g, const float *slots, const int tc[3], unsigned nmask,
+                                                  int lane, float (*sv)[box_nodes<D>()]) {
+  using E = OwnEntries<D>;
+  constexpr int BN = box_nodes<D>();
+  constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY;
+  constexpr int NI = (BN + 31) / 32;  // entries per lane
+  constexpr int SG = 2;               // entries whose loads are in flight together
+#pragma unroll
+  for (int i0 = 0; i0 < NI; i0 += SG) {
+    float v[SG][NST];
+    int ent[SG];
+#pragma unroll
+    for (int i = 0; i < SG; ++i) {
+      const int e = lane + 32 * (i0 + i);
+      ent[i] = -1;
+      if (i0 + i >= NI || e >= BN) continue;
+      int hd = 0;
+#pragma unroll
+      for (int h = 1; h < (1 << D); ++h)
+        if (e >= E::base(h)) hd = h;
+      int r = e - E::base(hd), bh[3] = {0, 0, 0}, d[3] = {0, 0, 0};
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        d[k] = (hd >> k) & 1;
+        if (!d[k]) {
+          bh[k] = 1 + r % E::T(k);  // the node's local coordinate, also the holder's (d_k = 0)
+          r /= E::T(k);
+        }
+      }
+      const int nb = (d[2] + 1) * 9 + (d[1] + 1) * 3 + (d[0] + 1);
+      if (!((nmask >> nb) & 1u)) continue;
+      ent[i] = e;
+      const int t2 = (tc[0] + d[0]) + g.nt[0] * ((tc[1] + d[1]) + g.nt[1] * (tc[2] + d[2]));
+      const int bl = bh[0] + (TX + 1) * (bh[1] + (TY + 1) * bh[2]);
+#pragma unroll
+      for (int c = 0; c < NST; ++c) v[i][c] = slots[((int64_t)t2 * NST + c) * BN + bl];
+    }
+#pragma unroll
+    for (int i = 0; i < SG; ++i)
+      if (ent[i] >= 0)
+#pragma unroll
+        for (int c = 0; c < NST; ++c) sv[c][ent[i]] = v[i][c];
+  }
+}
+
+// Sum the staged entries of owned node b (local 1..T) over its active
+// holders in ascending tile order (the order of gather_node).
+template <int D, int NOUT>
+__device__ __forceinline__ void combine_own_entries(const float (*sv)[box_nodes<D>()], const int b[3], unsigned nmask,
+                                                    float out[NOUT]) {
+  using E = OwnEntries<D>;
+  // the tile itself (hd = 0) holds every node it owns and comes first: its
+  // entry starts the sums (what adding it to zero gives)
+  TwoAcc<float> acc[NOUT];
+  const int e0 = E::entry(0, b);
+#pragma unroll
+  for (int c = 0; c < NOUT; ++c) {
+    acc[c].hi = sv[c][e0];
+    acc[c].lo = 0.f;
+  }
+#pragma unroll
+  for (int hd = 1; hd < (1 << D); ++hd) {
+    bool holds = true;
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+      if ((hd >> k) & 1) holds = holds && b[k] == E::T(k);
+    const int nb = (((hd >> 2) & 1) + 1) * 9 + (((hd >> 1) & 1) + 1) * 3 + ((hd & 1) + 1);
+    if (holds && ((nmask >> nb) & 1u)) {
+      const int e = E::entry(hd, b);
+#pragma unroll
+      for (int c = 0; c < NOUT; ++c) acc[c].add(sv[c][e]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NOUT; ++c) out[c] = acc[c].value();
+}
+
 // Work items dealt to the warps of the grid in turn (the work per item is
 // uniform): a 32-node slice of an active tile's box when there are few
 // active tiles, a whole box (four slices in turn) when there are enough to
@@ -1024,7 +1234,16 @@ __global__ void __launch_bounds__(NODE_T, ONE ? MPM_NODE_MINB : 8) node_tile(con
   // neighbourhood-mask bits of the lower neighbours (offsets in {-1, 0}^D, not all 0)
   constexpr unsigned LOWER = D == 3 ? (1u << 0) | (1u << 1) | (1u << 3) | (1u << 4) | (1u << 9) | (1u << 10) | (1u << 12)
                                     : (1u << 9) | (1u << 10) | (1u << 12);
+  // channels staged per owned-node walk: the sums the node needs (the USF
+  // force stage gathers only the forces; its mass and velocity are in the
+  // record).  Staged: the USF stages (64M slope 275 -> 216 and 305 -> 232
+  // us); the seven-channel USL sums were slower staged (311 -> 420 us) and
+  // gather per node.
+  constexpr int NST = NMODE == NODE_USF_A ? D : NCH1;
+  constexpr bool STAGE = !MAP && NMODE != NODE_USL;
   __shared__ InstArgs sI[NW];
+  __shared__ float sv_all[STAGE ? NW * NST * BN : 1];
+  float(*const sv)[BN] = reinterpret_cast<float(*)[BN]>(sv_all + (STAGE ? (threadIdx.x >> 5) * NST * BN : 0));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const InstArgs &I = inst_ref<ONE>(G, sI[warp]);
   (void)work_slot;
@@ -1076,6 +1295,12 @@ __global__ void __launch_bounds__(NODE_T, ONE ? MPM_NODE_MINB : 8) node_tile(con
     // along that axis, whose index is lower.  Otherwise, and for one slice
     // per warp, the walk is in box order with the ownership test below.
     const bool own_only = split == 1 && (nmask & LOWER) == LOWER;  // warp-uniform
+    // such a walk stages the slot entries of all its nodes first
+    const bool staged = STAGE && own_only;
+    if (staged) {
+      stage_own_entries<D, NST>(g, NMODE == NODE_USF_A ? I.s.slots2 : I.s.slots1, tc, nmask, lane, sv);
+      __syncwarp();
+    }
     for (int sl = slice0; sl < (split == 1 ? (own_only ? NOWN : NSL) : slice0 + 1); ++sl) do {  // a node per lane
       const int b = sl * 32 + lane;
       if (b >= BN) break;  // break: nothing to write for this lane
@@ -1087,8 +1312,9 @@ __global__ void __launch_bounds__(NODE_T, ONE ? MPM_NODE_MINB : 8) node_tile(con
 #pragma unroll
       for (int k = 0; k < D; ++k) inside = inside && Ig[k] <= g.nc[k];
       if (!inside) break;
-      int lo[3], hi[3], first;
-      const unsigned act = node_tiles_mask<D>(g, nmask, Ig, tc, lo, hi, first);
+      int lo[3], hi[3], first = t;
+      unsigned act = 0;
+      if (!staged) act = node_tiles_mask<D>(g, nmask, Ig, tc, lo, hi, first);  // (a staged walk owns its nodes)
       if (first != t) break;  // a lower active tile computes this node
       float v[D], a[D], vn[D];
 #pragma unroll
@@ -1097,6 +1323,9 @@ __global__ void __launch_bounds__(NODE_T, ONE ? MPM_NODE_MINB : 8) node_tile(con
       float c1[1 + 2 * D];
       if (NMODE == NODE_USL && MPM_FUSED_USL) {
         gather_node_usl<D, 1 + 2 * D>(g, I.s.slots1, I.s.slots_a, Ig, lo, hi, tc, act, fmask27, amask27, c1);
+      } else if (NMODE != NODE_USF_A && staged) {
+        const int bb[3] = {bx, by, bz};
+        combine_own_entries<D, NCH1>(sv, bb, nmask, c1);
       } else if (NMODE == NODE_USL) {
         gather_node<D, 1 + 2 * D>(g, I.s.slots1, NCH1, Ig, lo, hi, act, c1);
       } else if (NMODE == NODE_USF_V) {
@@ -1149,7 +1378,12 @@ __global__ void __launch_bounds__(NODE_T, ONE ? MPM_NODE_MINB : 8) node_tile(con
             bc_velocity<D, float>(faces, g.bc, v);
         } else {
           float f[D];
-          gather_node<D, D>(g, I.s.slots2, D, Ig, lo, hi, act, f);
+          if (staged) {
+            const int bb[3] = {bx, by, bz};
+            combine_own_entries<D, D>(sv, bb, nmask, f);
+          } else {
+            gather_node<D, D>(g, I.s.slots2, D, Ig, lo, hi, act, f);
+          }
           float ft[D];
           if (g.loads) face_force<D, float>(faces, Ig, g.nc, g.h, g.trac, ft);
           if (MAP && g.loads && g.fload && faces) add_face_loads<D>(g, faces, Ig, ft);
@@ -1176,7 +1410,7 @@ __global__ void __launch_bounds__(NODE_T, ONE ? MPM_NODE_MINB : 8) node_tile(con
         I.s.node[gi] = make_float4(w[0], w[1], NMODE == NODE_USF_V ? ms : a[0], a[1]);
       }
     } while (0);
-    if (!ONE) __syncwarp();  // the instance copy may be replaced next
+    __syncwarp();  // the instance copy and the staged entries may be replaced next
   }
 }
 
@@ -2044,9 +2278,16 @@ cudaError_t launch_p2g(const GroupArgs &G, int work_slot, cudaStream_t st) {
                                          P2GRec<D, MODE, true>::SMEM, st, G, work_slot)
                             : launch_dep(p2g_tile<D, MODE, false, true>, G.grid, p2g_threads<D>(),
                                          P2GRec<D, MODE, true>::SMEM, st, G, work_slot);
+    // as many CTAs as are resident (G.grid is 8 per SM): a CTA's first item
+    // is its block index, and a CTA waiting for a free slot would hold its
+    // item back until the end of the pass
+    constexpr int nt = P2GTile<D, MODE, false>::NT;
+    constexpr bool wide = p2g_wide<D, MODE, false>();
+    const int grid1 = G.grid / 8 * (wide ? MPM_P2G_WIDE_MINB : p2g_min_blocks<D, MODE, true>());
+    const int gridn = G.grid / 8 * (wide ? MPM_P2G_WIDE_MINB : p2g_min_blocks<D, MODE, false>());
     return G.ninst == 1
-               ? launch_dep(p2g_tile<D, MODE, true>, G.grid, p2g_threads<D>(), p2g_smem<D, MODE>(), st, G, work_slot)
-               : launch_dep(p2g_tile<D, MODE, false>, G.grid, p2g_threads<D>(), p2g_smem<D, MODE>(), st, G, work_slot);
+               ? launch_dep(p2g_tile<D, MODE, true>, grid1, nt, p2g_smem<D, MODE>(), st, G, work_slot)
+               : launch_dep(p2g_tile<D, MODE, false>, gridn, nt, p2g_smem<D, MODE>(), st, G, work_slot);
   }
 }
 
