@@ -320,7 +320,9 @@ __device__ __forceinline__ void cgeo_solve(const float P[1 << D][D], const float
 // (m, P_k), FORCE (f_k).
 // ---------------------------------------------------------------------------
 // WIDE (3D): four corners per thread, two threads per cell, 128 threads per
-// tile, each staging two particles of a chunk.
+// tile, each staging several particles of a chunk.  The four-channel
+// mass/momentum P2G stages 512 particles a chunk (64M slope 758 -> 730 us);
+// the USL and force P2G were slower so (1117 -> 1155, 872 -> 897 us).
 template <int D, int MODE, bool MAP = false, bool WIDE = false>
 struct P2GRec {
   static_assert(!WIDE || D == 3, "four corners per thread: 3D");
@@ -333,7 +335,7 @@ struct P2GRec {
   static constexpr int CPT = D == 3 ? (WIDE ? 4 : 2) : 1;      // corners per thread
   static constexpr int CPC = (1 << D) / CPT;                   // threads per cell
   static constexpr int NT = CELLS_PER_TILE * CPC;              // threads
-  static constexpr int CH = 256;                               // particles per chunk
+  static constexpr int CH = (WIDE && MODE == P2G_MOM) ? 512 : 256;  // particles per chunk
   static constexpr int PPT = CH / NT;                          // particles each thread stages
   static constexpr int NV = (1 << D) * p2g_channels<D, MODE>();
   static constexpr size_t REC_BYTES = sizeof(float4) * NQ * CH;
@@ -369,6 +371,16 @@ constexpr bool p2g_wide() {
 }
 template <int D, int MODE, bool MAP>
 using P2GTile = P2GRec<D, MODE, MAP, p2g_wide<D, MODE, MAP>()>;
+
+// Resident G2P CTAs per SM the register budget is sized for: MPM_G2P_MINB
+// (64 registers at 8) for the 3D USL and USF stress kernels; nine (56
+// registers) for the USF advection stage and in 2D, which measured faster
+// so (64M slope advection 1348 -> 1262 us, 256 batched 2D columns 0.507 ->
+// 0.494 ms per step) while the 3D USL G2P was slower (2348 -> 2395 us).
+template <int D, int GMODE, bool MAP>
+constexpr int g2p_min_blocks() {
+  return MAP ? 4 : ((D == 3 && GMODE != G2P_USF_ADVECT) ? MPM_G2P_MINB : 9);
+}
 
 // 4- and 16-byte asynchronous global -> shared copies (each thread later reads only
 // what it copied itself, so a wait on its own copies is all it needs).
@@ -1423,7 +1435,7 @@ __global__ void __launch_bounds__(NODE_T, ONE ? MPM_NODE_MINB : 8) node_tile(con
 // copies.
 // ---------------------------------------------------------------------------
 template <int D, int GMODE, bool ONE, bool MAP = false>
-__global__ void __launch_bounds__(G2P_T, MAP ? 4 : MPM_G2P_MINB) g2p(const __grid_constant__ GroupArgs G) {
+__global__ void __launch_bounds__(G2P_T, g2p_min_blocks<D, GMODE, MAP>()) g2p(const __grid_constant__ GroupArgs G) {
   constexpr int NC = 1 << D;
   constexpr int TX = Tile<D>::TX, TY = Tile<D>::TY, TZ = Tile<D>::TZ;
   constexpr int NS = nstress<D>();
@@ -2286,8 +2298,8 @@ cudaError_t launch_p2g(const GroupArgs &G, int work_slot, cudaStream_t st) {
     const int grid1 = G.grid / 8 * (wide ? MPM_P2G_WIDE_MINB : p2g_min_blocks<D, MODE, true>());
     const int gridn = G.grid / 8 * (wide ? MPM_P2G_WIDE_MINB : p2g_min_blocks<D, MODE, false>());
     return G.ninst == 1
-               ? launch_dep(p2g_tile<D, MODE, true>, grid1, nt, p2g_smem<D, MODE>(), st, G, work_slot)
-               : launch_dep(p2g_tile<D, MODE, false>, gridn, nt, p2g_smem<D, MODE>(), st, G, work_slot);
+               ? launch_dep(p2g_tile<D, MODE, true>, grid1, nt, P2GTile<D, MODE, false>::SMEM, st, G, work_slot)
+               : launch_dep(p2g_tile<D, MODE, false>, gridn, nt, P2GTile<D, MODE, false>::SMEM, st, G, work_slot);
   }
 }
 
@@ -2302,7 +2314,7 @@ cudaError_t prepare_p2g() {
                                 (int)p2g_smem<D, MODE>());
   }
   e = cudaFuncSetAttribute(p2g_tile<D, MODE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)p2g_smem<D, MODE>());
+                           (int)P2GTile<D, MODE, false>::SMEM);
   if (e != cudaSuccess) return e;
   if constexpr (MODE != P2G_MOM) {
     e = cudaFuncSetAttribute(p2g_tile<D, MODE, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -2313,7 +2325,7 @@ cudaError_t prepare_p2g() {
     if (e != cudaSuccess) return e;
   }
   return cudaFuncSetAttribute(p2g_tile<D, MODE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)p2g_smem<D, MODE>());
+                              (int)P2GTile<D, MODE, false>::SMEM);
 }
 
 template <int D>
