@@ -307,9 +307,11 @@ __device__ __forceinline__ void cgeo_solve(const float P[1 << D][D], const float
 
 // ---------------------------------------------------------------------------
 // P2G: one CTA per tile; each thread owns CPT corners of one cell (3D: two
-// corners, 256 threads; 2D: one corner, 256 threads).  The tile's particles
-// (binning order, so grouped by cell) are staged in shared memory in chunks
-// of one particle per thread: offset u, and the per-particle factors of the
+// corners, 256 threads, or four and 128 threads for the USF mass/momentum
+// P2G; 2D: one corner, 256 threads).  The tile's particles (binning order,
+// so grouped by cell) are staged in shared memory in chunks of 256
+// particles (512 in the USF mass/momentum P2G), one to four per thread:
+// offset u, and the per-particle factors of the
 // channels -- m and m v (mass, momentum), nV sig with nV = -V (internal
 // force f_k = -V sum_j sig_kj dN/dx_j).  Then the thread of (cell c, corner
 // a) runs over the particles of c in binning order and accumulates its
